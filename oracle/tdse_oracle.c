@@ -1,0 +1,524 @@
+/*
+ * Serial CPU oracle for the finite-difference TDSE propagation path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header or
+ * table generator with the CUDA library: it builds its own grid, Hamiltonian
+ * coefficients, pulse and absorber from the paper's formulas.
+ *
+ * Precision: REAL is `double` by default.  Compiling with -DORC_LONG_DOUBLE
+ * makes every state vector, Hamiltonian coefficient and reduction `long
+ * double`; that build measures the rounding floor of the double build.  The
+ * pulse E(t) and the absorber mask are evaluated in double in both builds
+ * (the paper evaluates them in double on the host, Sec. 5 "Pulse").
+ * Build with -ffp-contract=off so x86 and Arm give bit-identical results.
+ *
+ * Paper map (arXiv 1308.1856):
+ *   grid, stencils, block-tridiagonal H ... Sec. 2, Eqs. (tdse-radial-field),
+ *                                            (tdse-potential), the 4th-order
+ *                                            difference formulas, (h_matrix)
+ *   box boundary (zero beyond the box) ..... Sec. 2.1 first paragraph
+ *   absorber (applied as a per-step mask) .. Sec. 2.1
+ *   sin^2 pulse ............................ Sec. 3, Eq. (EField)
+ *   Taylor propagator ...................... Sec. 5 "Taylor.c", Eq. (Taylor)
+ *   Runge-Kutta (classic RK4) .............. Sec. 5 "RungeKutta.c", Eq. (RKDeriv)
+ *   Lanczos propagator ..................... Sec. 5 "Lanczos.c", Appendix
+ *                                            "Lanczos methods"
+ *   observables ............................ Sec. 4, Eqs. (p_g), (p_b),
+ *                                            (yield_1), (Norm), (Dipole)
+ *
+ * Readings where the paper is silent or garbled (each is also listed in the
+ * design notes):
+ *   - grid r_j = j*h + offset, j = 1..N (the "Start = 1" setting); finite
+ *     difference neighbours outside 1..N are zero ("zero ghost"), optionally
+ *     the odd reflection f_{-1} = -f_{1} at the origin ("odd ghost");
+ *   - the 3-point stencil is the standard (f_{j+1} - 2 f_j + f_{j-1})/h^2;
+ *   - Eq. (Taylor) prints the factor -i dt/p; the Taylor series of
+ *     exp(-i H dt) needs -i dt/(p+1), which is what is computed here;
+ *   - Taylor and Lanczos take the field at mid-step t_n + dt/2;
+ *   - the envelope of Eq. (EField) is read as sin^2(pi t / T), T = 2 pi n_c /
+ *     omega, with carrier sin(omega t + phi), and E = 0 outside [0, T];
+ *   - the Lanczos listing of the appendix is garbled; the standard three-term
+ *     recurrence is used, without re-orthogonalisation; the Krylov space is
+ *     truncated when beta_j <= 1e-13 * max(1, max|alpha|);
+ *   - the small exponential exp(-i T dt) e_1 is formed from a Jacobi
+ *     eigendecomposition of the real symmetric tridiagonal T;
+ *   - the absorber is the mask M(r) = cos^{1/8}(pi/2 (r - r_a)/(R - r_a)) for
+ *     r > r_a (R = r_N), applied once after every full step;
+ *   - integrals are h * sum over grid points; p_g is |<psi_0|psi>|^2.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef ORC_LONG_DOUBLE
+typedef long double REAL;
+#define RSQRT sqrtl
+#define RFABS fabsl
+#define RCOS cosl
+#define RSIN sinl
+#else
+typedef double REAL;
+#define RSQRT sqrt
+#define RFABS fabs
+#define RCOS cos
+#define RSIN sin
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Complex numbers as a plain pair of REALs.                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct { REAL re, im; } cplx;
+
+static cplx c_make(REAL re, REAL im) { cplx z; z.re = re; z.im = im; return z; }
+static cplx c_add(cplx a, cplx b) { return c_make(a.re + b.re, a.im + b.im); }
+static cplx c_sub(cplx a, cplx b) { return c_make(a.re - b.re, a.im - b.im); }
+static cplx c_scale(REAL s, cplx a) { return c_make(s * a.re, s * a.im); }
+static cplx c_mul(cplx a, cplx b) {
+  return c_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+/* multiplication by -i: (-i)(x + i y) = y - i x */
+static cplx c_mul_minus_i(cplx a) { return c_make(a.im, -a.re); }
+
+/* ------------------------------------------------------------------------ */
+/* Public parameter structs (mirrored by the Python ctypes wrapper).         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int N;               /* radial points per partial wave                      */
+  int L;               /* lmax; partial waves l = 0..L                        */
+  int stencil;         /* 3 or 5                                              */
+  int ghost;           /* 0 = zero beyond the box, 1 = odd reflection at r=0  */
+  double h;            /* grid spacing dr                                     */
+  double offset;       /* constant shift of every grid point                  */
+  double Z;            /* nuclear charge for V(r) = -Z/r                      */
+  const double *vtable;/* optional V(r_j), length N; NULL selects -Z/r        */
+} orc_grid;
+
+typedef struct {
+  double E0;           /* peak field (a.u.); 0 = field-free                   */
+  double omega;        /* carrier frequency (a.u.)                            */
+  double ncycles;      /* number of carrier cycles under the envelope         */
+  double cep;          /* carrier phase                                       */
+} orc_pulse;
+
+typedef struct {
+  int on;              /* 0 = no absorber                                     */
+  double r_a;          /* mask is 1 for r <= r_a, decays to r_N               */
+} orc_mask;
+
+enum { ORC_TAYLOR = 0, ORC_RK4 = 1, ORC_LANCZOS = 2 };
+#define ORC_MAX_KRYLOV 64
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OOM = -2 };
+
+/* ------------------------------------------------------------------------ */
+/* Grid and operator coefficients, Sec. 2.                                   */
+/* ------------------------------------------------------------------------ */
+static REAL grid_r(const orc_grid *g, int j /* 1-based */) {
+  return (REAL)j * (REAL)g->h + (REAL)g->offset;
+}
+
+static REAL potential(const orc_grid *g, int j /* 1-based */) {
+  if (g->vtable) return (REAL)g->vtable[j - 1];
+  return -(REAL)g->Z / grid_r(g, j);
+}
+
+/* kappa_l = k_{l,l-1}(m=0) = sqrt(l^2 / (4 l^2 - 1)), Eq. (tdse-potential). */
+static REAL kappa(int l) {
+  REAL ll = (REAL)l * (REAL)l;
+  return RSQRT(ll / (4 * ll - 1));
+}
+
+/* Value of partial wave l at radial index j (1-based), honouring the box:
+ * zero outside 1..N except the optional odd reflection f_{-1} = -f_1. */
+static cplx f_at(const orc_grid *g, const cplx *F, int l, int j) {
+  if (j >= 1 && j <= g->N) return F[(size_t)l * g->N + (j - 1)];
+  if (g->ghost == 1 && j == -1) return c_scale(-1, F[(size_t)l * g->N + 0]);
+  return c_make(0, 0);
+}
+
+/*
+ * y = H(E) x for the length-gauge Hamiltonian of Eq. (h_matrix):
+ *   diagonal blocks h_l = -1/2 d^2/dr^2 + l(l+1)/(2 r^2) + V(r)
+ *   off-diagonal blocks d_{l,l+-1} = r E kappa, Eq. (tdse-radial-field) and
+ *   the length-gauge coupled equation of Sec. 2.
+ * The second derivative is the 5-point formula of Sec. 2 or the standard
+ * 3-point formula.
+ */
+static void apply_H(const orc_grid *g, REAL E, const cplx *x, cplx *y) {
+  const int N = g->N, L = g->L;
+  const REAL h = (REAL)g->h;
+  for (int l = 0; l <= L; ++l) {
+    for (int j = 1; j <= N; ++j) {
+      const REAL r = grid_r(g, j);
+      cplx d2;
+      if (g->stencil == 5) {
+        /* d2f/dr2 = [-f_{j+2} + 16 f_{j+1} - 30 f_j + 16 f_{j-1} - f_{j-2}] / (12 h^2) */
+        cplx s = c_scale(-1, f_at(g, x, l, j + 2));
+        s = c_add(s, c_scale(16, f_at(g, x, l, j + 1)));
+        s = c_add(s, c_scale(-30, f_at(g, x, l, j)));
+        s = c_add(s, c_scale(16, f_at(g, x, l, j - 1)));
+        s = c_add(s, c_scale(-1, f_at(g, x, l, j - 2)));
+        d2 = c_scale(1 / (12 * h * h), s);
+      } else {
+        /* d2f/dr2 = [f_{j+1} - 2 f_j + f_{j-1}] / h^2 */
+        cplx s = f_at(g, x, l, j + 1);
+        s = c_add(s, c_scale(-2, f_at(g, x, l, j)));
+        s = c_add(s, f_at(g, x, l, j - 1));
+        d2 = c_scale(1 / (h * h), s);
+      }
+      const REAL centrifugal = (REAL)l * (REAL)(l + 1) / (2 * r * r);
+      cplx v = c_scale(-0.5, d2);
+      v = c_add(v, c_scale(centrifugal + potential(g, j), f_at(g, x, l, j)));
+      if (l >= 1) v = c_add(v, c_scale(r * E * kappa(l), f_at(g, x, l - 1, j)));
+      if (l < L) v = c_add(v, c_scale(r * E * kappa(l + 1), f_at(g, x, l + 1, j)));
+      y[(size_t)l * N + (j - 1)] = v;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pulse, Sec. 3 Eq. (EField) with the Hann (sin^2) envelope.                */
+/* ------------------------------------------------------------------------ */
+double orc_field(const orc_pulse *p, double t) {
+  if (p->E0 == 0.0 || p->omega <= 0.0) return 0.0;
+  const double T = 2.0 * M_PI * p->ncycles / p->omega;
+  if (t < 0.0 || t > T) return 0.0;
+  const double env = sin(M_PI * t / T);
+  return p->E0 * env * env * sin(p->omega * t + p->cep);
+}
+
+/* Absorbing mask value at radius r (Sec. 2.1, applied as a mask). */
+double orc_mask_value(const orc_mask *m, double r, double R) {
+  if (!m->on || r <= m->r_a) return 1.0;
+  const double x = 0.5 * M_PI * (r - m->r_a) / (R - m->r_a);
+  return pow(cos(x), 0.125);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Helpers on whole vectors.                                                 */
+/* ------------------------------------------------------------------------ */
+static size_t dim(const orc_grid *g) { return (size_t)(g->L + 1) * g->N; }
+
+static REAL vec_norm(const cplx *x, size_t n) {
+  REAL s = 0;
+  for (size_t i = 0; i < n; ++i) s += x[i].re * x[i].re + x[i].im * x[i].im;
+  return RSQRT(s);
+}
+
+static void load_state(const double *in, cplx *out, size_t n) {
+  for (size_t i = 0; i < n; ++i) out[i] = c_make((REAL)in[2 * i], (REAL)in[2 * i + 1]);
+}
+
+static void store_state(const cplx *in, double *out, size_t n) {
+  for (size_t i = 0; i < n; ++i) { out[2 * i] = (double)in[i].re; out[2 * i + 1] = (double)in[i].im; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Taylor propagator, Eq. (Taylor):                                          */
+/*   F_{n+1} = sum_{p=0}^{P} F^{(p)},  F^{(0)} = F_n,                        */
+/*   F^{(p)} = (-i dt / p) H F^{(p-1)}     (factor read as 1/p, see header)  */
+/* ------------------------------------------------------------------------ */
+static void taylor_step(const orc_grid *g, REAL E, int P, REAL dt, cplx *psi,
+                        cplx *term, cplx *tmp) {
+  const size_t n = dim(g);
+  memcpy(term, psi, n * sizeof(cplx));
+  for (int p = 1; p <= P; ++p) {
+    apply_H(g, E, term, tmp);
+    const REAL s = dt / (REAL)p;
+    for (size_t i = 0; i < n; ++i) {
+      term[i] = c_scale(s, c_mul_minus_i(tmp[i]));
+      psi[i] = c_add(psi[i], term[i]);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Classic RK4, Eq. (RKDeriv) with dF/dt = -i H(t) F (Eq. (tdse_matrix)):    */
+/* c = (0, 1/2, 1/2, 1), a_{21} = a_{32} = 1/2, a_{43} = 1, b = (1,2,2,1)/6. */
+/* ------------------------------------------------------------------------ */
+static void rk4_step(const orc_grid *g, const REAL Ec[4], REAL dt, cplx *psi,
+                     cplx *k, cplx *g_arg, cplx *acc) {
+  static const REAL a_prev[4] = {0, 0.5, 0.5, 1.0};   /* a_{i,i-1}          */
+  static const REAL b[4] = {1, 2, 2, 1};              /* times 1/6          */
+  const size_t n = dim(g);
+  for (size_t i = 0; i < n; ++i) acc[i] = c_make(0, 0);
+  for (int s = 0; s < 4; ++s) {
+    /* g = F_n + dt * a_{s,s-1} k_{s-1}; the classic tableau has one nonzero a per row */
+    for (size_t i = 0; i < n; ++i)
+      g_arg[i] = (s == 0) ? psi[i] : c_add(psi[i], c_scale(dt * a_prev[s], k[i]));
+    apply_H(g, Ec[s], g_arg, k);
+    for (size_t i = 0; i < n; ++i) {
+      k[i] = c_mul_minus_i(k[i]);          /* k_s = -i H(t_n + c_s dt) g */
+      acc[i] = c_add(acc[i], c_scale(b[s], k[i]));
+    }
+  }
+  for (size_t i = 0; i < n; ++i) psi[i] = c_add(psi[i], c_scale(dt / 6, acc[i]));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi eigendecomposition of a small real symmetric matrix (cyclic        */
+/* Jacobi rotations).  A (n x n, row major) is overwritten; eigenvalues go   */
+/* to w, eigenvectors to the columns of V.                                   */
+/* ------------------------------------------------------------------------ */
+static void jacobi_eig(int n, REAL *A, REAL *w, REAL *V) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1 : 0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    REAL off = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off == 0) break;
+    for (int p = 0; p < n; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const REAL apq = A[p * n + q];
+        if (apq == 0) continue;
+        const REAL app = A[p * n + p], aqq = A[q * n + q];
+        /* rotation angle that annihilates A[p][q] */
+        const REAL theta = (aqq - app) / (2 * apq);
+        const REAL t = (theta >= 0 ? 1 : -1) / (RFABS(theta) + RSQRT(theta * theta + 1));
+        const REAL c = 1 / RSQRT(t * t + 1), s = t * c;
+        for (int k = 0; k < n; ++k) {       /* A <- A J  (columns p, q) */
+          const REAL akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {       /* A <- J^T A (rows p, q) */
+          const REAL apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {       /* V <- V J */
+          const REAL vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lanczos propagator, Sec. 5 "Lanczos.c" and Appendix "Lanczos methods":     */
+/*   q_1 = F/||F||, beta_0 = 0, q_0 = 0                                      */
+/*   for j = 1..m: w = H q_j - beta_{j-1} q_{j-1}; alpha_j = Re<q_j, w>;     */
+/*                 w -= alpha_j q_j; beta_j = ||w||; q_{j+1} = w / beta_j    */
+/*   F_{n+1} = ||F|| Q exp(-i T dt) e_1,  T = tridiag(beta, alpha, beta).    */
+/* Returns the Krylov dimension actually used.                               */
+/* ------------------------------------------------------------------------ */
+static int lanczos_step(const orc_grid *g, REAL E, int m, REAL dt, cplx *psi,
+                        cplx *Q /* (m+1) * n */, cplx *w, REAL *alpha, REAL *beta) {
+  const size_t n = dim(g);
+  const REAL nrm = vec_norm(psi, n);
+  if (nrm == 0) return 0;
+  for (size_t i = 0; i < n; ++i) Q[i] = c_scale(1 / nrm, psi[i]);
+  int k = m;                                   /* dimension of the space */
+  REAL amax = 0;
+  for (int j = 0; j < m; ++j) {
+    cplx *qj = Q + (size_t)j * n;
+    apply_H(g, E, qj, w);
+    if (j > 0) {
+      const cplx *qprev = Q + (size_t)(j - 1) * n;
+      for (size_t i = 0; i < n; ++i) w[i] = c_sub(w[i], c_scale(beta[j - 1], qprev[i]));
+    }
+    REAL a = 0;                                /* Re <q_j, w> */
+    for (size_t i = 0; i < n; ++i) a += qj[i].re * w[i].re + qj[i].im * w[i].im;
+    alpha[j] = a;
+    if (RFABS(a) > amax) amax = RFABS(a);
+    for (size_t i = 0; i < n; ++i) w[i] = c_sub(w[i], c_scale(a, qj[i]));
+    if (j == m - 1) break;                     /* beta_m is not needed */
+    const REAL b = vec_norm(w, n);
+    beta[j] = b;
+    if (b <= (REAL)1e-13 * (amax > 1 ? amax : 1)) { k = j + 1; break; }
+    cplx *qnext = Q + (size_t)(j + 1) * n;
+    for (size_t i = 0; i < n; ++i) qnext[i] = c_scale(1 / b, w[i]);
+  }
+
+  /* c = exp(-i T dt) e_1 through T = V diag(lambda) V^T */
+  /* k <= m <= ORC_MAX_KRYLOV, checked by the callers */
+  REAL A[ORC_MAX_KRYLOV * ORC_MAX_KRYLOV], V[ORC_MAX_KRYLOV * ORC_MAX_KRYLOV];
+  REAL lam[ORC_MAX_KRYLOV];
+  cplx c[ORC_MAX_KRYLOV];
+  memset(A, 0, sizeof(A));
+  for (int i = 0; i < k; ++i) {
+    A[i * k + i] = alpha[i];
+    if (i + 1 < k) { A[i * k + i + 1] = beta[i]; A[(i + 1) * k + i] = beta[i]; }
+  }
+  jacobi_eig(k, A, lam, V);
+  for (int i = 0; i < k; ++i) {
+    cplx s = c_make(0, 0);
+    for (int e = 0; e < k; ++e) {
+      const REAL ph = -lam[e] * dt;            /* exp(-i lambda dt) */
+      s = c_add(s, c_scale(V[i * k + e] * V[0 * k + e], c_make(RCOS(ph), RSIN(ph))));
+    }
+    c[i] = s;
+  }
+  /* F_{n+1} = ||F|| sum_j c_j q_j */
+  for (size_t i = 0; i < n; ++i) {
+    cplx s = c_make(0, 0);
+    for (int j = 0; j < k; ++j) s = c_add(s, c_mul(c[j], Q[(size_t)j * n + i]));
+    psi[i] = c_scale(nrm, s);
+  }
+  return k;
+}
+
+static void apply_mask(const orc_grid *g, const orc_mask *m, cplx *psi) {
+  if (!m || !m->on) return;
+  const double R = (double)grid_r(g, g->N);
+  for (int j = 1; j <= g->N; ++j) {
+    const REAL mv = (REAL)orc_mask_value(m, (double)grid_r(g, j), R);
+    if (mv == 1) continue;
+    for (int l = 0; l <= g->L; ++l) {
+      cplx *z = &psi[(size_t)l * g->N + (j - 1)];
+      *z = c_scale(mv, *z);
+    }
+  }
+}
+
+static int check_grid(const orc_grid *g) {
+  if (!g || g->N < 1 || g->L < 0 || g->h <= 0) return 0;
+  if (g->stencil != 3 && g->stencil != 5) return 0;
+  if (g->ghost != 0 && g->ghost != 1) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported entry points (double in / double out).                           */
+/* ------------------------------------------------------------------------ */
+
+/* y = H(E) x; x, y interleaved complex, length 2 (L+1) N doubles, l-major. */
+int orc_apply_H(const orc_grid *g, double E, const double *x, double *y) {
+  if (!check_grid(g)) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  cplx *X = (cplx *)malloc(n * sizeof(cplx)), *Y = (cplx *)malloc(n * sizeof(cplx));
+  if (!X || !Y) { free(X); free(Y); return ORC_ERR_OOM; }
+  load_state(x, X, n);
+  apply_H(g, (REAL)E, X, Y);
+  store_state(Y, y, n);
+  free(X); free(Y);
+  return ORC_OK;
+}
+
+/*
+ * Advance psi (in place, interleaved complex) by nsteps steps of size dt
+ * starting at time t0.  method: 0 Taylor (order = P), 1 RK4 (order ignored),
+ * 2 Lanczos (order = Krylov dimension m).  The mask (if on) is applied after
+ * every full step.  min_krylov (may be NULL) receives the smallest Krylov
+ * dimension used by any step.
+ */
+int orc_propagate(const orc_grid *g, const orc_pulse *pulse, const orc_mask *mask,
+                  int method, int order, double dt, double t0, long nsteps,
+                  double *psi_io, int *min_krylov) {
+  if (!check_grid(g) || !pulse || nsteps < 0 || !(dt > 0)) return ORC_ERR_ARG;
+  if (method == ORC_TAYLOR && order < 1) return ORC_ERR_ARG;
+  if (method == ORC_LANCZOS && order < 1) return ORC_ERR_ARG;
+  if (method < 0 || method > 2) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  const int nvec = (method == ORC_LANCZOS) ? order + 3 : 4;
+  cplx *buf = (cplx *)malloc((size_t)nvec * n * sizeof(cplx));
+  if (!buf) return ORC_ERR_OOM;
+  cplx *psi = buf, *w1 = buf + n, *w2 = buf + 2 * n, *w3 = buf + 3 * n;
+  REAL alpha[ORC_MAX_KRYLOV], beta[ORC_MAX_KRYLOV];
+  if (method == ORC_LANCZOS && order > ORC_MAX_KRYLOV) { free(buf); return ORC_ERR_ARG; }
+  load_state(psi_io, psi, n);
+  int kmin = order;
+  for (long s = 0; s < nsteps; ++s) {
+    const double tn = t0 + (double)s * dt;
+    if (method == ORC_TAYLOR) {
+      taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt, psi, w1, w2);
+    } else if (method == ORC_RK4) {
+      const REAL Ec[4] = {(REAL)orc_field(pulse, tn), (REAL)orc_field(pulse, tn + 0.5 * dt),
+                          (REAL)orc_field(pulse, tn + 0.5 * dt), (REAL)orc_field(pulse, tn + dt)};
+      rk4_step(g, Ec, (REAL)dt, psi, w1, w2, w3);
+    } else {
+      const int k = lanczos_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt,
+                                 psi, w2 /* Q: order+1 vectors */, w1, alpha, beta);
+      if (k < kmin) kmin = k;
+    }
+    apply_mask(g, mask, psi);
+  }
+  store_state(psi, psi_io, n);
+  if (min_krylov) *min_krylov = kmin;
+  free(buf);
+  return ORC_OK;
+}
+
+/*
+ * Lanczos coefficients for one step from psi: alpha[0..k-1], beta[0..k-2];
+ * returns k (the Krylov dimension kept), or a negative status.
+ */
+int orc_lanczos_coefficients(const orc_grid *g, double E, int m, const double *psi_in,
+                             double *alpha_out, double *beta_out) {
+  if (!check_grid(g) || m < 1 || m > ORC_MAX_KRYLOV) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  cplx *buf = (cplx *)malloc((size_t)(m + 3) * n * sizeof(cplx));
+  if (!buf) return ORC_ERR_OOM;
+  REAL alpha[ORC_MAX_KRYLOV], beta[ORC_MAX_KRYLOV];
+  cplx *psi = buf, *w = buf + n, *Q = buf + 2 * n;
+  load_state(psi_in, psi, n);
+  const int k = lanczos_step(g, (REAL)E, m, (REAL)1e-300, psi, Q, w, alpha, beta);
+  for (int i = 0; i < k; ++i) alpha_out[i] = (double)alpha[i];
+  for (int i = 0; i + 1 < k; ++i) beta_out[i] = (double)beta[i];
+  free(buf);
+  return k;
+}
+
+/*
+ * Observables of Sec. 4, every integral as h * sum over grid points:
+ *   out[0] norm      = h sum_l sum_j |f_{l,j}|^2
+ *   out[1] dipole    = 2 sum_{l<L} kappa_{l+1} h sum_j r_j Re(conj(f_{l,j}) f_{l+1,j})  Eq. (Dipole)
+ *   out[2] yield     = 1 - h sum_l sum_{r_j <= r_b} |f_{l,j}|^2                         Eq. (yield_1)
+ *   out[3] p_ground  = |h sum_j conj(ref0_j) f_{0,j}|^2                                 Eq. (p_g)
+ *   out[4 + l] P_l   = h sum_j |f_{l,j}|^2
+ * ref0 is the l = 0 reference wave (N interleaved complex values) or NULL.
+ */
+int orc_observables(const orc_grid *g, const double *psi_in, const double *ref0,
+                    double r_b, double *out) {
+  if (!check_grid(g) || !out) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  cplx *F = (cplx *)malloc(n * sizeof(cplx));
+  if (!F) return ORC_ERR_OOM;
+  load_state(psi_in, F, n);
+  const REAL h = (REAL)g->h;
+  const int N = g->N, L = g->L;
+  REAL norm = 0, inside = 0, dip = 0;
+  for (int l = 0; l <= L; ++l) {
+    REAL pl = 0;
+    for (int j = 1; j <= N; ++j) {
+      const cplx z = F[(size_t)l * N + (j - 1)];
+      const REAL a = z.re * z.re + z.im * z.im;
+      pl += a;
+      if (grid_r(g, j) <= (REAL)r_b) inside += a;
+    }
+    out[4 + l] = (double)(h * pl);
+    norm += pl;
+  }
+  for (int l = 0; l < L; ++l) {
+    REAL s = 0;
+    for (int j = 1; j <= N; ++j) {
+      const cplx a = F[(size_t)l * N + (j - 1)], b = F[(size_t)(l + 1) * N + (j - 1)];
+      s += grid_r(g, j) * (a.re * b.re + a.im * b.im);   /* r Re(conj(a) b) */
+    }
+    dip += 2 * kappa(l + 1) * h * s;
+  }
+  REAL pg = 0;
+  if (ref0) {
+    cplx ov = c_make(0, 0);
+    for (int j = 1; j <= N; ++j) {
+      const cplx r0 = c_make((REAL)ref0[2 * (j - 1)], -(REAL)ref0[2 * (j - 1) + 1]);
+      ov = c_add(ov, c_mul(r0, F[j - 1]));
+    }
+    ov = c_scale(h, ov);
+    pg = ov.re * ov.re + ov.im * ov.im;
+  }
+  out[0] = (double)(h * norm);
+  out[1] = (double)dip;
+  out[2] = (double)(1 - h * inside);
+  out[3] = (double)pg;
+  free(F);
+  return ORC_OK;
+}
+
+/* Precision of REAL in this build, in bytes (8 or the platform's long double). */
+int orc_real_bytes(void) { return (int)sizeof(REAL); }

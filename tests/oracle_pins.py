@@ -1,0 +1,319 @@
+"""Checks that pin the CPU oracle to facts that do not come from the oracle.
+
+Each ``check_*`` function raises AssertionError on failure and takes the key of
+the oracle build to test (``"f64"`` normally; the mutation test registers
+planted-mistake builds under other keys and expects some check to fail).
+
+Pins used (arXiv 1308.1856 passages in brackets):
+  * H is real symmetric; the off-diagonal blocks are diagonal with entries
+    r E k_{l,l+1}, where k comes from numerical quadrature of
+    <Y_l0|cos(theta)|Y_{l+1,0}> (not from the closed form) [Sec. 2, Eqs.
+    (tdse-potential), (h_matrix)];
+  * the difference formulas are exact on low-degree polynomials and have the
+    textbook leading truncation term on the next degree [Sec. 2];
+  * hydrogen levels -1/(2 n^2) are approached as dr -> 0 at the observed
+    orders, and the paper's printed ground-state energies hold [Sec. 6];
+  * a grid eigenstate evolves by the scalar Taylor / RK4 polynomial or the
+    exact phase [Eqs. (Taylor), (RKDeriv), Lanczos section];
+  * Taylor and Lanczos agree with the dense matrix exponential / dense
+    polynomial computed by scipy/numpy on tiny grids;
+  * time-order: RK4 converges at order 4 and the mid-step field makes Taylor
+    and Lanczos converge at order 2, against scipy's DOP853 reference;
+  * norm conservation (Lanczos), p_i + p_b = 1 [Eq. (Norm)];
+  * the dipole agrees with a brute-force angular quadrature of z |psi|^2
+    [Eq. (Dipole)]; populations sum to the norm; p_g of the reference is 1;
+  * the sin^2 pulse vanishes at its end points, has zero area, is odd about
+    T/2 and peaks at E0 [Sec. 3]; the cos^(1/8) mask is 1 inside and near 0
+    at the box edge [Sec. 2.1].
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import scipy.integrate as si
+import scipy.linalg as sl
+import scipy.special as sp
+
+import oracle
+from oracle import Grid, Mask, Pulse
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_values() -> dict:
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        return json.load(f)
+
+
+def _rand_state(L, N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((L + 1, N)) + 1j * rng.standard_normal((L + 1, N))
+
+
+def _lowest(grid: Grid, l: int, prec: str, count: int = 1):
+    band = oracle.band_H(grid, 0.0, l, prec)
+    return sl.eig_banded(band, select="i", select_range=(0, count - 1), eigvals_only=True)
+
+
+# --------------------------------------------------------------------------
+def check_symmetric(prec="f64"):
+    for stencil in (3, 5):
+        for ghost in ((0, 1) if stencil == 5 else (0,)):
+            g = Grid(N=13, h=0.3, L=3, stencil=stencil, ghost=ghost, offset=-0.02, Z=1.0)
+            H = oracle.dense_H(g, 0.07, prec)
+            scale = np.abs(H).max()
+            assert np.abs(H - H.T).max() <= 1e-15 * scale, "H is not symmetric"
+            x = _rand_state(3, 13, 5)
+            y = oracle.apply_H(g, 0.07, x, prec)
+            lin = (oracle.apply_H(g, 0.07, x.real.astype(complex), prec)
+                   + 1j * oracle.apply_H(g, 0.07, x.imag.astype(complex), prec))
+            assert np.abs(y - lin).max() <= 1e-14 * scale, "H is not a real operator"
+
+
+def _k_quadrature(l: int, lp: int) -> float:
+    """<Y_l0| cos theta |Y_lp0> by Gauss-Legendre quadrature over x = cos theta."""
+    x, w = np.polynomial.legendre.leggauss(64)
+    yl = math.sqrt((2 * l + 1) / (4 * math.pi)) * sp.eval_legendre(l, x)
+    ylp = math.sqrt((2 * lp + 1) / (4 * math.pi)) * sp.eval_legendre(lp, x)
+    return float(2 * math.pi * np.sum(w * yl * x * ylp))
+
+
+def check_coupling_blocks(prec="f64"):
+    N, L, E = 6, 6, 0.3
+    g = Grid(N=N, h=0.5, L=L, stencil=3, Z=0.0, offset=0.1)
+    H = oracle.dense_H(g, E, prec)
+    r = g.r()
+    for l in range(L + 1):
+        for lp in range(L + 1):
+            blk = H[l * N:(l + 1) * N, lp * N:(lp + 1) * N]
+            if abs(l - lp) == 1:
+                want = np.diag(r * E * _k_quadrature(l, lp))
+                assert np.abs(blk - want).max() <= 1e-13, f"coupling block ({l},{lp})"
+            elif l != lp:
+                assert np.abs(blk).max() == 0.0, f"block ({l},{lp}) must vanish"
+
+
+def check_stencil_polynomials(prec="f64"):
+    h, N, off = 0.1, 40, 0.37
+    for stencil in (3, 5):
+        g = Grid(N=N, h=h, L=0, stencil=stencil, Z=0.0, offset=off)
+        r = g.r()
+        b = stencil // 2
+        inner = slice(b, N - b)
+        if stencil == 5:
+            # exact through degree 5; on r^6 the formula's leading error h^4/90 f^(6)
+            cases = [(r ** 5, -0.5 * 20 * r ** 3), (r ** 6, -15 * r ** 4 + 4 * h ** 4)]
+        else:
+            # exact through degree 3; on r^4 the error is h^2/12 f^(4) exactly
+            cases = [(r ** 3, -0.5 * 6 * r), (r ** 4, -6 * r ** 2 - h ** 2)]
+        for f, want in cases:
+            y = oracle.apply_H(g, 0.0, f[None, :].astype(complex), prec)[0].real
+            tol = 1e-12 * np.abs(f).max() / h ** 2
+            assert np.abs(y[inner] - want[inner]).max() <= tol, f"{stencil}-point stencil"
+
+
+def check_hydrogen_paper_values(prec="f64"):
+    pv = paper_values()
+    for key in ("ground_state_no_offset", "ground_state_offset"):
+        e = pv[key]
+        g = Grid(N=e["N"], h=e["dr"], L=0, stencil=e["stencil"], offset=e["offset"], Z=1.0)
+        E = _lowest(g, 0, prec)[0]
+        assert abs(E - e["energy"]) <= e["tolerance"], f"{key}: {E}"
+
+
+def check_hydrogen_convergence(prec="f64"):
+    hs = (0.4, 0.2, 0.1, 0.05)
+
+    def errs(l, stencil, ghost, box, exact):
+        out = []
+        for h in hs:
+            g = Grid(N=int(round(box / h)), h=h, L=l, stencil=stencil, ghost=ghost, Z=1.0)
+            out.append(_lowest(g, l, prec)[0] - exact)
+        return np.array(out)
+
+    e = errs(0, 3, 0, 400.0, -0.5)                     # 1s, 3-point: order 2
+    rat = e[:-1] / e[1:]
+    assert np.all((rat > 3.5) & (rat < 4.3)), f"3-pt 1s ratios {rat}"
+    e = errs(0, 5, 0, 400.0, -0.5)                     # 1s, 5-point, zero ghost: order 1
+    rat = e[:-1] / e[1:]
+    assert np.all((rat > 1.8) & (rat < 2.2)), f"5-pt 1s ratios {rat}"
+    e = errs(0, 5, 1, 400.0, -0.5)                     # 1s, 5-point, odd ghost: -> order 2
+    rat = e[:-1] / e[1:]
+    assert 3.5 < rat[-1] < 4.3 and abs(e[-1]) < 1e-3, f"5-pt odd-ghost ratios {rat}"
+    e = errs(1, 3, 0, 120.0, -0.125)                   # 2p, 3-point: order 2
+    rat = e[:-1] / e[1:]
+    assert np.all((rat > 3.5) & (rat < 4.3)), f"3-pt 2p ratios {rat}"
+    e = errs(1, 5, 0, 120.0, -0.125)                   # 2p, 5-point: order 3
+    rat = e[:-1] / e[1:]
+    assert np.all((rat > 6.5) & (rat < 9.0)), f"5-pt 2p ratios {rat}"
+    g = Grid(N=2400, h=0.05, L=2, stencil=5, Z=1.0)    # 3d level
+    assert abs(_lowest(g, 2, prec)[0] + 1.0 / 18.0) < 1e-6
+
+
+def check_field_free_eigenstate(prec="f64"):
+    g = Grid(N=40, h=0.25, L=2, stencil=5, Z=1.0)
+    H = oracle.dense_H(g, 0.0, prec)
+    lam, V = np.linalg.eigh(H)
+    dt, P = 0.05, 8
+    for idx in (0, 7, 41):
+        phi = 2.5 * V[:, idx].reshape(3, 40).astype(complex) * np.exp(0.3j)
+        z = -1j * lam[idx] * dt
+        taylor = sum(z ** p / math.factorial(p) for p in range(P + 1))
+        rk4 = sum(z ** p / math.factorial(p) for p in range(5))
+        out, _ = oracle.propagate(g, phi, "taylor", P, dt, 3, precision=prec)
+        assert np.abs(out - taylor ** 3 * phi).max() <= 1e-12, "Taylor on an eigenstate"
+        out, _ = oracle.propagate(g, phi, "rk4", 4, dt, 3, precision=prec)
+        assert np.abs(out - rk4 ** 3 * phi).max() <= 1e-12, "RK4 on an eigenstate"
+        out, k = oracle.propagate(g, phi, "lanczos", 6, dt, 3, precision=prec)
+        assert k == 1, "Lanczos must stop at dimension 1 on an eigenstate"
+        assert np.abs(out - np.exp(3 * z) * phi).max() <= 1e-12, "Lanczos on an eigenstate"
+
+
+def check_dense_expm(prec="f64"):
+    g = Grid(N=10, h=0.4, L=2, stencil=5, Z=1.0)
+    pulse = Pulse(E0=0.3, omega=0.9, ncycles=2)
+    t0, dt = 5.2, 0.02
+    Em = oracle.field(pulse, t0 + dt / 2, prec)
+    assert abs(Em) > 0.05
+    H = oracle.dense_H(g, Em, prec)
+    psi = _rand_state(2, 10, 11)
+    v = psi.reshape(-1)
+    want = sl.expm(-1j * dt * H) @ v
+    for m in (12, 16):
+        out, _ = oracle.propagate(g, psi, "lanczos", m, dt, 1, t0=t0, pulse=pulse, precision=prec)
+        assert np.abs(out.reshape(-1) - want).max() <= 1e-12 * np.abs(want).max(), f"Lanczos m={m}"
+    # alpha_1 is the Rayleigh quotient, beta_1 the residual norm, and over the
+    # whole space the extreme Ritz values are the extreme eigenvalues of H
+    alpha, beta = oracle.lanczos_coefficients(g, Em, 4, psi, prec)
+    q = v / np.linalg.norm(v)
+    ray = float(np.vdot(q, H @ q).real)
+    assert abs(alpha[0] - ray) <= 1e-13 * abs(ray), "alpha_1 must be <q|H|q>"
+    assert abs(beta[0] - np.linalg.norm(H @ q - ray * q)) <= 1e-12 * abs(beta[0])
+    alpha, beta = oracle.lanczos_coefficients(g, Em, 30, psi, prec)
+    ritz = np.linalg.eigvalsh(np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1))
+    ev = np.linalg.eigvalsh(H)
+    assert abs(ritz[0] - ev[0]) <= 1e-9 * abs(ev).max() and abs(ritz[-1] - ev[-1]) <= 1e-9 * abs(ev).max()
+    P = 6
+    term, acc = v.copy(), v.copy()
+    for p in range(1, P + 1):
+        term = (-1j * dt / p) * (H @ term)
+        acc = acc + term
+    out, _ = oracle.propagate(g, psi, "taylor", P, dt, 1, t0=t0, pulse=pulse, precision=prec)
+    assert np.abs(out.reshape(-1) - acc).max() <= 1e-13 * np.abs(acc).max(), "Taylor polynomial"
+    # for a field-free (time-independent) H, classic RK4 is the order-4 Taylor polynomial
+    a, _ = oracle.propagate(g, psi, "rk4", 4, dt, 2, precision=prec)
+    b, _ = oracle.propagate(g, psi, "taylor", 4, dt, 2, precision=prec)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), "RK4 == Taylor-4 without field"
+
+
+def check_time_order(prec="f64"):
+    g = Grid(N=12, h=0.4, L=2, stencil=5, Z=1.0)
+    pulse = Pulse(E0=2.0, omega=3.0, ncycles=2)
+    H0 = oracle.dense_H(g, 0.0, prec)
+    D = oracle.dense_H(g, 1.0, prec) - H0            # H(E) = H0 + E D (length gauge)
+    psi = _rand_state(2, 12, 3)
+    psi /= np.linalg.norm(psi)
+    t0, t1 = 1.0, 2.0
+
+    def rhs(t, y):
+        return -1j * ((H0 + oracle.field(pulse, t, prec) * D) @ y)
+
+    ref = si.solve_ivp(rhs, (t0, t1), psi.reshape(-1), method="DOP853", rtol=1e-13,
+                       atol=1e-13).y[:, -1]
+    for method, order, lo, hi in (("rk4", 4, 12.0, 20.0), ("taylor", 12, 3.5, 4.5),
+                                  ("lanczos", 12, 3.5, 4.5)):
+        err = []
+        for nsteps in (40, 80, 160):
+            out, _ = oracle.propagate(g, psi, method, order, (t1 - t0) / nsteps, nsteps,
+                                      t0=t0, pulse=pulse, precision=prec)
+            err.append(np.linalg.norm(out.reshape(-1) - ref))
+        rat = np.array(err[:-1]) / np.array(err[1:])
+        assert np.all((rat > lo) & (rat < hi)), f"{method} dt-halving ratios {rat}"
+
+
+def check_norm_and_yield(prec="f64"):
+    g = Grid(N=500, h=0.2, L=4, stencil=3, Z=1.0)
+    r = g.r()
+    psi = np.zeros((5, 500), dtype=complex)
+    psi[0] = 2 * r * np.exp(-r)
+    psi /= math.sqrt(0.2 * np.vdot(psi, psi).real)
+    pulse = Pulse(E0=0.0534, omega=0.057, ncycles=2)
+    out, _ = oracle.propagate(g, psi, "lanczos", 12, 0.05, 50, pulse=pulse, precision=prec)
+    ob = oracle.observables(g, out, psi[0], r_b=10.0, precision=prec)
+    assert abs(ob["norm"] - 1.0) <= 5e-13, "Lanczos must conserve the norm"
+    # p_i(r_b) + p_b(r_b) = norm (= 1 without absorber), Eq. (Norm)
+    outside = 0.2 * float(np.sum(np.abs(out[:, r > 10.0]) ** 2))
+    assert abs(ob["yield"] - outside - (1 - ob["norm"])) <= 1e-14
+    assert abs(oracle.observables(g, out, None, r_b=1e9, precision=prec)["yield"]
+               - (1 - ob["norm"])) <= 1e-15
+    assert oracle.observables(g, out, None, r_b=0.0, precision=prec)["yield"] == 1.0
+
+
+def check_observables(prec="f64"):
+    N, L, h = 60, 5, 0.1
+    g = Grid(N=N, h=h, L=L, stencil=5, Z=1.0, offset=0.05)
+    r = g.r()
+    psi = _rand_state(L, N, 21)
+    ob = oracle.observables(g, psi, None, precision=prec)
+    assert abs(ob["l_pop"].sum() - ob["norm"]) <= 1e-13 * ob["norm"]
+    assert abs(ob["norm"] - h * np.sum(np.abs(psi) ** 2)) <= 1e-13 * ob["norm"]
+    # dipole by brute-force angular quadrature of z |psi|^2 (r f = sum_l f_l Y_l0)
+    x, w = np.polynomial.legendre.leggauss(32)
+    Y = np.array([math.sqrt((2 * l + 1) / (4 * math.pi)) * sp.eval_legendre(l, x)
+                  for l in range(L + 1)])                     # (L+1, nx)
+    amp = psi.T @ Y                                           # (N, nx)
+    z = h * np.sum(r[:, None] * 2 * math.pi * w[None, :] * x[None, :] * np.abs(amp) ** 2)
+    assert abs(ob["dipole"] - z) <= 1e-12 * max(1.0, abs(z)), f"dipole {ob['dipole']} vs {z}"
+    even = psi.copy()
+    even[1::2] = 0
+    assert oracle.observables(g, even, None, precision=prec)["dipole"] == 0.0
+    # p_g: overlap with a complex reference wave, normalised with h sum |ref|^2 = 1
+    rng = np.random.default_rng(4)
+    ref = rng.standard_normal(N) * np.exp(1j * rng.uniform(0, 2 * math.pi, N))
+    ref /= math.sqrt(h * np.sum(np.abs(ref) ** 2))
+    st = psi.copy() * 0.1
+    st[0] = np.exp(0.7j) * ref
+    pg = oracle.observables(g, st, ref, precision=prec)["p_ground"]
+    assert abs(pg - 1.0) <= 1e-13, f"p_g of the reference itself is {pg}"
+
+
+def check_pulse(prec="f64"):
+    for nc in (2, 3, 4):
+        p = Pulse(E0=0.0534, omega=0.057, ncycles=nc)
+        T = 2 * math.pi * nc / 0.057
+        assert abs(oracle.field(p, 0.0, prec)) <= 1e-18
+        assert abs(oracle.field(p, T, prec)) <= 1e-15 * 0.0534
+        assert oracle.field(p, -1.0, prec) == 0.0 and oracle.field(p, T + 1.0, prec) == 0.0
+        t = np.linspace(0, T, 20001)
+        e = np.array([oracle.field(p, tt, prec) for tt in t])
+        area = float(np.sum(0.5 * (e[1:] + e[:-1])) * (t[1] - t[0]))
+        assert abs(area) <= 1e-9 * 0.0534 * T, "sin^2 pulse must have zero area"
+        for tt in (13.7, 55.1, T / 3):
+            assert abs(oracle.field(p, T - tt, prec) + oracle.field(p, tt, prec)) <= 1e-14
+        assert np.abs(e).max() <= 0.0534
+        q = Pulse(E0=0.0534, omega=0.057, ncycles=nc, cep=math.pi / 2)
+        assert abs(oracle.field(q, T / 2, prec) - 0.0534 * (-1) ** nc) <= 1e-15
+
+
+def check_mask(prec="f64"):
+    m = Mask(r_a=350.0)
+    R = 400.0
+    for r in (0.05, 100.0, 350.0):
+        assert oracle.mask_value(m, r, R, prec) == 1.0
+    assert oracle.mask_value(m, R, R, prec) < 0.01
+    # M^8 = cos(pi/2 x), so arccos(M^8) grows linearly in r over the absorber
+    rs = np.linspace(351.0, 399.0, 9)
+    ang = np.array([math.acos(oracle.mask_value(m, r, R, prec) ** 8) for r in rs])
+    slope = np.diff(ang) / np.diff(rs)
+    assert np.abs(slope - (math.pi / 2) / (R - 350.0)).max() <= 1e-9
+    off = Mask(r_a=350.0, on=False)
+    assert oracle.mask_value(off, R, R, prec) == 1.0
+
+
+ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
+              check_hydrogen_paper_values, check_hydrogen_convergence,
+              check_field_free_eigenstate, check_dense_expm, check_time_order,
+              check_norm_and_yield, check_observables, check_pulse, check_mask]

@@ -1,0 +1,68 @@
+"""Plant plausible mistakes in a copy of the oracle source and check that the
+pins catch every one of them (CPU only; the oracle itself is not modified)."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "tdse_oracle.c")
+
+# (name, text in tdse_oracle.c, replacement, the pin expected to catch it)
+MUTANTS = [
+    ("coupling_sign", "c_scale(r * E * kappa(l), f_at(g, x, l - 1, j))",
+     "c_scale(-r * E * kappa(l), f_at(g, x, l - 1, j))", P.check_symmetric),
+    ("kappa_formula", "return RSQRT(ll / (4 * ll - 1));", "return RSQRT(ll / (4 * ll + 1));",
+     P.check_coupling_blocks),
+    ("stencil5_coefficient", "s = c_add(s, c_scale(16, f_at(g, x, l, j + 1)));",
+     "s = c_add(s, c_scale(15, f_at(g, x, l, j + 1)));", P.check_stencil_polynomials),
+    ("stencil3_coefficient", "s = c_add(s, c_scale(-2, f_at(g, x, l, j)));",
+     "s = c_add(s, c_scale(-1.999, f_at(g, x, l, j)));", P.check_stencil_polynomials),
+    ("centrifugal", "(REAL)l * (REAL)(l + 1) / (2 * r * r)", "(REAL)l * (REAL)l / (2 * r * r)",
+     P.check_hydrogen_convergence),
+    ("coulomb_sign", "return -(REAL)g->Z / grid_r(g, j);", "return (REAL)g->Z / grid_r(g, j);",
+     P.check_hydrogen_paper_values),
+    ("odd_ghost_always", "if (g->ghost == 1 && j == -1)", "if (j == -1)",
+     P.check_hydrogen_paper_values),
+    ("taylor_printed_factor", "const REAL s = dt / (REAL)p;",
+     "const REAL s = dt / (REAL)(p > 1 ? p - 1 : 1);", P.check_field_free_eigenstate),
+    ("rk4_weights", "static const REAL b[4] = {1, 2, 2, 1};",
+     "static const REAL b[4] = {2, 1, 2, 1};", P.check_field_free_eigenstate),
+    ("rk4_stage_time", "(REAL)orc_field(pulse, tn + dt)};", "(REAL)orc_field(pulse, tn + 0.5 * dt)};",
+     P.check_time_order),
+    ("taylor_field_time", "taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt)",
+     "taylor_step(g, (REAL)orc_field(pulse, tn)", P.check_time_order),
+    ("lanczos_drop_beta", "w[i] = c_sub(w[i], c_scale(beta[j - 1], qprev[i]));",
+     "w[i] = w[i];", P.check_dense_expm),
+    ("lanczos_alpha_sign", "a += qj[i].re * w[i].re + qj[i].im * w[i].im;",
+     "a += qj[i].re * w[i].re - qj[i].im * w[i].im;", P.check_dense_expm),
+    ("lanczos_norm_rescale", "psi[i] = c_scale(nrm, s);", "psi[i] = s;",
+     P.check_field_free_eigenstate),
+    ("dipole_factor", "dip += 2 * kappa(l + 1) * h * s;", "dip += kappa(l + 1) * h * s;",
+     P.check_observables),
+    ("p_ground_conjugate", "-(REAL)ref0[2 * (j - 1) + 1]", "(REAL)ref0[2 * (j - 1) + 1]",
+     P.check_observables),
+    ("norm_weight", "out[0] = (double)(h * norm);", "out[0] = (double)(norm);",
+     P.check_observables),
+    ("yield_radius", "if (grid_r(g, j) <= (REAL)r_b) inside += a;", "inside += a;",
+     P.check_norm_and_yield),
+    ("mask_exponent", "pow(cos(x), 0.125)", "pow(cos(x), 0.25)", P.check_mask),
+    ("envelope_period", "sin(M_PI * t / T);", "sin(2.0 * M_PI * t / T);", P.check_pulse),
+]
+
+
+@pytest.mark.parametrize("name,old,new,check", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, check):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique/found"
+    path = tmp_path / f"mut_{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"libmut_{name}.so"
+    subprocess.run(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-o", str(so), str(path), "-lm"], check=True)
+    key = f"mutant-{name}"
+    oracle.register_library(key, str(so))
+    with pytest.raises(AssertionError):
+        check(key)
