@@ -1,0 +1,191 @@
+/*
+ * tdse.h - C ABI of the GB300 finite-difference TDSE propagation library.
+ *
+ * The library advances the partial-wave radial wavefunction of a one-electron
+ * (hydrogen / single-active-electron) atom in a linearly polarised laser field,
+ * in the length gauge, with hand-written sm_103a CUDA kernels.  It follows
+ * arXiv 1308.1856 (CLTDSE):
+ *
+ *   state vector F, l-major  ............ Sec. 2, the vector F of Eq. (h_matrix)
+ *   Hamiltonian H(t) ..................... Sec. 2, Eqs. (tdse-radial-field),
+ *                                          (tdse-potential), (h_matrix)
+ *   dF/dt = -i H(t) F .................... Eq. (tdse_matrix)
+ *   Taylor / Runge-Kutta / Lanczos ....... Sec. 5 "TDSE": Eq. (Taylor),
+ *                                          Eq. (RKDeriv), Appendix "Lanczos methods"
+ *   pulse ................................ Sec. 3, Eq. (EField)
+ *   absorber ............................. Sec. 2.1 (applied as a mask)
+ *   observables .......................... Sec. 4: Eqs. (p_g), (p_b), (yield_1),
+ *                                          (Norm), (Dipole)
+ *
+ * Conventions
+ *   - Atomic units.  Grid r_j = j*dr + offset, j = 1..N; partial waves
+ *     l = 0..lmax with m = 0.  Finite-difference neighbours beyond the box are
+ *     zero; the optional odd ghost sets f(-dr) = -f(dr).
+ *   - Complex numbers are interleaved (re, im) doubles.  A state holds
+ *     (lmax+1)*N complex values, l-major: element (l, j) sits at
+ *     2*(l*N + (j-1)) (re) and the next double (im).
+ *   - Ownership: the handle owns all device memory it allocates and one CUDA
+ *     stream (or borrows the caller's through tdse_set_stream).  Every host
+ *     pointer stays the caller's; inputs are copied before the call returns.
+ *     Device pointers passed to tdse_apply_h / tdse_*_state_device are the
+ *     caller's and must hold the stated number of bytes.
+ *   - Asynchrony: tdse_propagate and tdse_apply_h only enqueue work on the
+ *     handle's stream.  tdse_get_state, tdse_observables and tdse_sync wait
+ *     for it.
+ *   - Errors: every call returns a tdse_status; tdse_last_error() gives a
+ *     message.  After TDSE_ERR_CUDA the handle is poisoned: later calls return
+ *     TDSE_ERR_STATE.  Non-finite values found by a norm reduction are
+ *     reported as TDSE_ERR_NONFINITE by the next synchronising call.
+ */
+#ifndef TDSE_H
+#define TDSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdse tdse_t;
+
+typedef enum {
+  TDSE_OK = 0,
+  TDSE_ERR_ARG = -1,        /* invalid argument; nothing was changed         */
+  TDSE_ERR_OOM = -2,        /* device or host allocation failed              */
+  TDSE_ERR_CUDA = -3,       /* a CUDA call failed; the handle is poisoned     */
+  TDSE_ERR_NONFINITE = -4,  /* the state holds Inf/NaN (e.g. unstable dt)     */
+  TDSE_ERR_STATE = -7       /* handle poisoned by an earlier CUDA error       */
+} tdse_status;
+
+enum { TDSE_STENCIL_3 = 3, TDSE_STENCIL_5 = 5 };
+enum { TDSE_TAYLOR = 0, TDSE_RK4 = 1, TDSE_LANCZOS = 2 };
+enum { TDSE_GHOST_ZERO = 0, TDSE_GHOST_ODD = 1 };
+/* largest Krylov dimension tdse_propagate accepts for TDSE_LANCZOS */
+#define TDSE_MAX_KRYLOV 32
+
+typedef struct {
+  int ghost;            /* TDSE_GHOST_ZERO (default) or TDSE_GHOST_ODD          */
+  double offset;        /* constant grid shift (default 0)                       */
+  int absorber;         /* 1: multiply by the cos^(1/8) mask after every step    */
+  double absorber_r;    /* mask is 1 for r <= absorber_r and falls to r_N        */
+  double r_b;           /* yield radius: yield = 1 - sum_{r_j <= r_b} |f|^2 dr   */
+} tdse_opts;
+
+/*
+ * Create a handle for N radial points of spacing dr and partial waves
+ * l = 0..lmax with a 3- or 5-point second derivative (Sec. 2).  The potential
+ * is -Z/r, or v_table[j-1] = V(r_j) (length N, host, copied) when v_table is
+ * not NULL.  The state starts as P(r) = 2 r exp(-r) in l = 0, scaled so that
+ * dr * sum |P|^2 = 1; that wave is also the reference of p_ground.  Options
+ * start at: zero ghost, offset 0, no absorber, r_b = 10.
+ * Errors: TDSE_ERR_ARG (N < 1, lmax < 0, dr <= 0, stencil not 3/5),
+ * TDSE_ERR_OOM, TDSE_ERR_CUDA.  *out is NULL on error.
+ */
+int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double *v_table,
+                tdse_t **out);
+
+/* Release everything the handle owns (NULL is accepted). */
+int tdse_destroy(tdse_t *h);
+
+/* Message for the last error on this handle (static storage, never NULL). */
+const char *tdse_last_error(const tdse_t *h);
+
+/*
+ * Replace the options (ghost, offset, absorber, r_b).  Changing ghost or
+ * offset rebuilds the operator tables and the initial 1s state is NOT
+ * recomputed.  Errors: TDSE_ERR_ARG (ghost not 0/1, absorber_r outside the
+ * box while absorber is on).
+ */
+int tdse_set_options(tdse_t *h, const tdse_opts *opts);
+
+/* Use the caller's CUDA stream (a cudaStream_t; NULL restores the handle's own). */
+int tdse_set_stream(tdse_t *h, void *cuda_stream);
+
+/*
+ * Length-gauge pulse E(t) = E0 sin^2(pi t / T) sin(omega t + cep) for
+ * 0 <= t <= T = 2 pi ncycles / omega, zero elsewhere (Sec. 3, Eq. (EField)
+ * with the Hann envelope).  E0 = 0 switches the field off.
+ * Errors: TDSE_ERR_ARG (E0 != 0 with omega <= 0 or ncycles <= 0).
+ */
+int tdse_set_pulse(tdse_t *h, double E0, double omega, double ncycles, double cep);
+
+/* Evaluate the pulse set by tdse_set_pulse at time t (host arithmetic). */
+double tdse_field(const tdse_t *h, double t);
+
+/* Current time of the state; tdse_propagate advances it by nsteps * dt. */
+int tdse_set_time(tdse_t *h, double t);
+double tdse_get_time(const tdse_t *h);
+
+/* Copy a state in from / out to HOST memory ((lmax+1)*N interleaved complex). */
+int tdse_set_state(tdse_t *h, const double *F_host);
+int tdse_get_state(tdse_t *h, double *F_host);
+
+/* The same from / to DEVICE memory of the caller (16*(lmax+1)*N bytes, 16-byte aligned). */
+int tdse_set_state_device(tdse_t *h, const void *F_dev);
+int tdse_get_state_device(tdse_t *h, void *F_dev);
+
+/* Reference l = 0 wave of p_ground (N interleaved complex, host, copied). */
+int tdse_set_reference(tdse_t *h, const double *f0_host);
+
+/*
+ * Advance the state by nsteps steps of size dt (asynchronous).
+ *   TDSE_TAYLOR  - Taylor polynomial of exp(-i H dt) of degree `order`
+ *                  (Eq. (Taylor); evaluated in Horner form), field at mid-step;
+ *   TDSE_RK4     - classic fourth-order Runge-Kutta (Eq. (RKDeriv)), field at
+ *                  the stage times; `order` is ignored;
+ *   TDSE_LANCZOS - Lanczos with Krylov dimension `order` (Appendix "Lanczos
+ *                  methods"), field at mid-step; the Krylov space is cut when
+ *                  beta_j <= 1e-13 max(1, max|alpha|).
+ * The absorber, if on, multiplies the state by the mask after every step.
+ * Errors: TDSE_ERR_ARG (dt <= 0, nsteps < 0, order < 1 for Taylor/Lanczos,
+ * order > TDSE_MAX_KRYLOV for Lanczos), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps);
+
+/*
+ * Observables of the current state (synchronises the stream), Sec. 4, each
+ * integral taken as dr * sum over grid points:
+ *   norm     = dr sum_l sum_j |f_lj|^2
+ *   l_pop[l] = dr sum_j |f_lj|^2                       (lmax+1 doubles)
+ *   dipole   = 2 sum_{l<lmax} kappa_{l+1} dr sum_j r_j Re(conj(f_lj) f_{l+1,j})
+ *   yield    = 1 - dr sum_l sum_{r_j <= r_b} |f_lj|^2
+ *   p_ground = |dr sum_j conj(ref_j) f_0j|^2
+ * Any output pointer may be NULL.  Returns TDSE_ERR_NONFINITE if the state
+ * holds Inf/NaN.
+ */
+int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, double *yield,
+                     double *p_ground);
+
+/*
+ * y = H(E) x on caller-owned DEVICE buffers (asynchronous on the handle's
+ * stream); x and y hold (lmax+1)*N interleaved complex doubles, 16-byte
+ * aligned, and must not overlap.  This is the bare operator of Eq. (h_matrix).
+ */
+int tdse_apply_h(tdse_t *h, double E, const void *x_dev, void *y_dev);
+
+/* Wait for the handle's stream; reports pending TDSE_ERR_NONFINITE. */
+int tdse_sync(tdse_t *h);
+
+/* Number of kernel launches this handle has issued (for launch accounting). */
+long long tdse_launch_count(const tdse_t *h);
+
+/* Kernel kinds for per-kernel timing. */
+enum {
+  TDSE_K_APPLY_H = 0, TDSE_K_TAYLOR_STAGE, TDSE_K_RK_STAGE, TDSE_K_NORM, TDSE_K_LANCZOS_A,
+  TDSE_K_LANCZOS_B, TDSE_K_LANCZOS_EXPM, TDSE_K_LANCZOS_COMBINE, TDSE_K_OBSERVABLES,
+  TDSE_K_COUNT
+};
+
+/*
+ * Per-kernel timing: while enabled, every launch is bracketed by a pair of
+ * CUDA events recorded on the handle's stream.  tdse_profile_read waits for
+ * the stream and returns, for one kernel kind, the summed event time (ms) and
+ * the number of launches since profiling was enabled; enable = 0 stops it,
+ * enable = 1 (re)starts it with zeroed totals.  Timing adds small gaps between
+ * launches, so time the throughput of a run with profiling off.
+ */
+int tdse_profile(tdse_t *h, int enable);
+int tdse_profile_read(tdse_t *h, int kind, double *total_ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDSE_H */

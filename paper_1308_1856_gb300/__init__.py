@@ -1,0 +1,147 @@
+"""GB300-native finite-difference TDSE propagation (arXiv 1308.1856 hot path).
+
+The compute path is the CUDA library ``libtdse.so`` (C ABI in include/tdse.h).
+``TDSE`` below is a thin convenience wrapper over the C calls: numpy/torch
+arrays in, status codes turned into exceptions.  PyTorch is used only for
+device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _binding as C
+from ._binding import (TDSE_LANCZOS, TDSE_RK4, TDSE_TAYLOR, TDSE_GHOST_ODD, TDSE_GHOST_ZERO,
+                       TDSE_MAX_KRYLOV)
+
+METHODS = {"taylor": TDSE_TAYLOR, "rk4": TDSE_RK4, "lanczos": TDSE_LANCZOS}
+
+
+class TDSEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tdse status {code}: {msg}")
+        self.code = code
+
+
+class TDSE:
+    """One wavefunction on an (N, lmax) grid, owned by a libtdse handle."""
+
+    def __init__(self, N: int, dr: float, lmax: int, stencil: int = 5, Z: float = 1.0,
+                 v_table: Optional[np.ndarray] = None):
+        self.N, self.dr, self.lmax, self.stencil = int(N), float(dr), int(lmax), int(stencil)
+        h = ctypes.c_void_p()
+        vt = None
+        if v_table is not None:
+            self._vt = np.ascontiguousarray(v_table, dtype=np.float64)
+            vt = self._vt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = C.tdse_create(self.N, self.dr, self.lmax, self.stencil, float(Z), vt, ctypes.byref(h))
+        if rc != 0:
+            raise TDSEError(rc, "tdse_create failed")
+        self.h = h
+
+    # -- helpers -----------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise TDSEError(rc, C.tdse_last_error(self.h).decode())
+
+    @property
+    def shape(self):
+        return (self.lmax + 1, self.N)
+
+    def close(self):
+        if getattr(self, "h", None):
+            C.tdse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C calls -------------------------------------------------------------------
+    def set_options(self, ghost=0, offset=0.0, absorber=False, absorber_r=0.0, r_b=10.0):
+        o = C.tdse_opts(int(ghost), float(offset), 1 if absorber else 0, float(absorber_r), float(r_b))
+        self._check(C.tdse_set_options(self.h, ctypes.byref(o)))
+
+    def set_stream(self, stream_ptr: int):
+        self._check(C.tdse_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)))
+
+    def set_pulse(self, E0, omega, ncycles, cep=0.0):
+        self._check(C.tdse_set_pulse(self.h, float(E0), float(omega), float(ncycles), float(cep)))
+
+    def field(self, t: float) -> float:
+        return C.tdse_field(self.h, float(t))
+
+    @property
+    def time(self) -> float:
+        return C.tdse_get_time(self.h)
+
+    @time.setter
+    def time(self, t: float):
+        self._check(C.tdse_set_time(self.h, float(t)))
+
+    def set_state(self, F: np.ndarray):
+        a = np.ascontiguousarray(F, dtype=np.complex128)
+        if a.size != self.N * (self.lmax + 1):
+            raise ValueError("state has the wrong size")
+        self._check(C.tdse_set_state(self.h, ctypes.c_void_p(a.ctypes.data)))
+
+    def get_state(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape, dtype=np.complex128)
+        self._check(C.tdse_get_state(self.h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_state_ptr(self, host_ptr: int):
+        """Copy a state from a host address (e.g. a pinned torch tensor)."""
+        self._check(C.tdse_set_state(self.h, ctypes.c_void_p(host_ptr)))
+
+    def get_state_ptr(self, host_ptr: int):
+        self._check(C.tdse_get_state(self.h, ctypes.c_void_p(host_ptr)))
+
+    def set_state_device(self, dev_ptr: int):
+        self._check(C.tdse_set_state_device(self.h, ctypes.c_void_p(dev_ptr)))
+
+    def get_state_device(self, dev_ptr: int):
+        self._check(C.tdse_get_state_device(self.h, ctypes.c_void_p(dev_ptr)))
+
+    def set_reference(self, f0: np.ndarray):
+        a = np.ascontiguousarray(f0, dtype=np.complex128).reshape(self.N)
+        self._check(C.tdse_set_reference(self.h, ctypes.c_void_p(a.ctypes.data)))
+
+    def propagate(self, method: str, order: int, dt: float, nsteps: int):
+        self._check(C.tdse_propagate(self.h, METHODS[method], int(order), float(dt), int(nsteps)))
+
+    def observables(self) -> dict:
+        norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
+        lp = np.zeros(self.lmax + 1)
+        self._check(C.tdse_observables(self.h, ctypes.byref(norm), ctypes.c_void_p(lp.ctypes.data),
+                                       ctypes.byref(dip), ctypes.byref(yld), ctypes.byref(pg)))
+        return {"norm": norm.value, "dipole": dip.value, "yield": yld.value,
+                "p_ground": pg.value, "l_pop": lp}
+
+    def apply_h(self, E: float, x_dev: int, y_dev: int):
+        self._check(C.tdse_apply_h(self.h, float(E), ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev)))
+
+    def sync(self):
+        self._check(C.tdse_sync(self.h))
+
+    @property
+    def launches(self) -> int:
+        return C.tdse_launch_count(self.h)
+
+    def profile(self, enable: bool):
+        self._check(C.tdse_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total ms, launches)} since profiling was enabled."""
+        out = {}
+        for k, name in enumerate(C.KERNEL_KINDS):
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            self._check(C.tdse_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out

@@ -1,0 +1,118 @@
+"""ctypes binding of libtdse (include/tdse.h), argument marshalling only.
+
+The functions carry the C names and signatures.  Every step of the
+propagation runs in the CUDA library; this module only converts arguments.
+Importing it fails loudly when the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+TDSE_OK = 0
+TDSE_ERR_ARG = -1
+TDSE_ERR_OOM = -2
+TDSE_ERR_CUDA = -3
+TDSE_ERR_NONFINITE = -4
+TDSE_ERR_STATE = -7
+TDSE_STENCIL_3, TDSE_STENCIL_5 = 3, 5
+TDSE_TAYLOR, TDSE_RK4, TDSE_LANCZOS = 0, 1, 2
+TDSE_GHOST_ZERO, TDSE_GHOST_ODD = 0, 1
+TDSE_MAX_KRYLOV = 32
+
+# Every symbol include/tdse.h declares: name -> (restype, argtypes)
+_c_int, _c_double, _c_long, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class tdse_opts(ctypes.Structure):
+    _fields_ = [("ghost", ctypes.c_int), ("offset", ctypes.c_double), ("absorber", ctypes.c_int),
+                ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double)]
+
+
+SIGNATURES = {
+    "tdse_create": (_c_int, [_c_int, _c_double, _c_int, _c_int, _c_double, _dp,
+                             ctypes.POINTER(_vp)]),
+    "tdse_destroy": (_c_int, [_vp]),
+    "tdse_last_error": (ctypes.c_char_p, [_vp]),
+    "tdse_set_options": (_c_int, [_vp, ctypes.POINTER(tdse_opts)]),
+    "tdse_set_stream": (_c_int, [_vp, _vp]),
+    "tdse_set_pulse": (_c_int, [_vp, _c_double, _c_double, _c_double, _c_double]),
+    "tdse_field": (_c_double, [_vp, _c_double]),
+    "tdse_set_time": (_c_int, [_vp, _c_double]),
+    "tdse_get_time": (_c_double, [_vp]),
+    "tdse_set_state": (_c_int, [_vp, _vp]),
+    "tdse_get_state": (_c_int, [_vp, _vp]),
+    "tdse_set_state_device": (_c_int, [_vp, _vp]),
+    "tdse_get_state_device": (_c_int, [_vp, _vp]),
+    "tdse_set_reference": (_c_int, [_vp, _vp]),
+    "tdse_propagate": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long]),
+    "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
+    "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
+    "tdse_sync": (_c_int, [_vp]),
+    "tdse_launch_count": (ctypes.c_longlong, [_vp]),
+    "tdse_profile": (_c_int, [_vp, _c_int]),
+    "tdse_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libtdse.so; raise if it is missing (there is no CPU fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"libtdse is not built ({path}); run paper_1308_1856_gb300/build.py "
+                              "or __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _fn(name):
+    def call(*args):
+        return getattr(load(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+tdse_create = _fn("tdse_create")
+tdse_destroy = _fn("tdse_destroy")
+tdse_last_error = _fn("tdse_last_error")
+tdse_set_options = _fn("tdse_set_options")
+tdse_set_stream = _fn("tdse_set_stream")
+tdse_set_pulse = _fn("tdse_set_pulse")
+tdse_field = _fn("tdse_field")
+tdse_set_time = _fn("tdse_set_time")
+tdse_get_time = _fn("tdse_get_time")
+tdse_set_state = _fn("tdse_set_state")
+tdse_get_state = _fn("tdse_get_state")
+tdse_set_state_device = _fn("tdse_set_state_device")
+tdse_get_state_device = _fn("tdse_get_state_device")
+tdse_set_reference = _fn("tdse_set_reference")
+tdse_propagate = _fn("tdse_propagate")
+tdse_observables = _fn("tdse_observables")
+tdse_apply_h = _fn("tdse_apply_h")
+tdse_sync = _fn("tdse_sync")
+tdse_launch_count = _fn("tdse_launch_count")
+tdse_profile = _fn("tdse_profile")
+tdse_profile_read = _fn("tdse_profile_read")
+
+KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
+                "lanczos_expm", "lanczos_combine", "observables"]

@@ -1,0 +1,605 @@
+// C ABI of libtdse (declared in include/tdse.h): handle, tables, pulse and the
+// host-side step plans that enqueue the FP64 kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tdse_internal.cuh"
+
+using namespace tdse_dev;
+
+struct tdse {
+  Geometry g;
+  double Z = 1.0;
+  std::vector<double> vtab;   // empty: -Z/r
+  tdse_opts opts;
+  double E0 = 0.0, omega = 0.0, ncycles = 0.0, cep = 0.0;
+  double t = 0.0;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  // device memory
+  double2 *psi = nullptr, *ref0 = nullptr, *work = nullptr;
+  size_t work_vecs = 0;
+  double *diag = nullptr, *rj = nullptr, *kappa = nullptr, *mask = nullptr;
+  int mask_start = 0;
+  Reduction *red = nullptr;
+  LanczosScalars *ls = nullptr;
+  int *status = nullptr;
+  double *obs_partials = nullptr, *obs_out = nullptr;
+  // bookkeeping
+  std::string err;
+  bool poisoned = false;
+  long long launches = 0;
+  // per-kernel timing (tdse_profile)
+  bool profiling = false;
+  struct Mark { int kind; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  size_t nmarks = 0;
+  double prof_ms[TDSE_K_COUNT] = {0};
+  long long prof_n[TDSE_K_COUNT] = {0};
+};
+
+namespace {
+
+const char *kNoHandle = "null handle";
+
+size_t npts(const tdse *h) { return (size_t)h->g.N * (h->g.L + 1); }
+
+int fail(tdse *h, int code, const std::string &msg) {
+  if (h) {
+    h->err = msg;
+    if (code == TDSE_ERR_CUDA) h->poisoned = true;
+  }
+  return code;
+}
+
+int cuda_fail(tdse *h, cudaError_t e, const char *what) {
+  return fail(h, TDSE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TDSE_CUDA(h, call, what)                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+#define TDSE_LAUNCH(h, kind, call, what)          \
+  do {                                            \
+    cudaEvent_t b_ = prof_begin(h, kind);         \
+    cudaError_t e_ = (call);                      \
+    ++(h)->launches;                              \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    if (b_) cudaEventRecord(b_, (h)->stream);     \
+  } while (0)
+
+// Record the start event of a profiled launch; returns the stop event to record after it.
+cudaEvent_t prof_begin(tdse *h, int kind) {
+  if (!h->profiling) return nullptr;
+  if (h->nmarks == h->marks.size()) {
+    tdse::Mark m;
+    m.kind = kind;
+    if (cudaEventCreate(&m.a) != cudaSuccess || cudaEventCreate(&m.b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    h->marks.push_back(m);
+  }
+  tdse::Mark &m = h->marks[h->nmarks++];
+  m.kind = kind;
+  cudaEventRecord(m.a, h->stream);
+  return m.b;
+}
+
+int check_usable(tdse *h) {
+  if (!h) return TDSE_ERR_ARG;
+  if (h->poisoned) return TDSE_ERR_STATE;
+  return TDSE_OK;
+}
+
+OperatorView view(const tdse *h) {
+  OperatorView op;
+  op.diag = h->diag;
+  op.rj = h->rj;
+  op.kappa = h->kappa;
+  op.mask = h->mask;
+  op.mask_start = (h->opts.absorber) ? h->mask_start : h->g.N;
+  return op;
+}
+
+// Grid r_j = j*dr + offset (j = 1..N) and the tables of the operator.
+int build_tables(tdse *h) {
+  const Geometry &g = h->g;
+  const int N = g.N, L = g.L;
+  std::vector<double> r(N), d((size_t)(L + 1) * N), kap(L + 2), msk(N, 1.0);
+  for (int j = 0; j < N; ++j) r[j] = (double)(j + 1) * g.dr + h->opts.offset;
+  for (int j = 0; j < N; ++j)
+    if (!(r[j] > 0.0)) return fail(h, TDSE_ERR_ARG, "grid offset puts a point at r <= 0");
+  for (int l = 0; l <= L; ++l) {
+    const double cent = 0.5 * (double)l * (double)(l + 1);
+    for (int j = 0; j < N; ++j) {
+      const double V = h->vtab.empty() ? -h->Z / r[j] : h->vtab[j];
+      d[(size_t)l * N + j] = g.c0 + cent / (r[j] * r[j]) + V;
+    }
+    // odd reflection f(-dr) = -f(dr) folds c2 * f_{-1} into the first diagonal entry
+    if (g.stencil == 5 && h->opts.ghost == TDSE_GHOST_ODD) d[(size_t)l * N] -= g.c2;
+  }
+  kap[0] = 0.0;
+  for (int l = 1; l <= L; ++l) {
+    const double ll = (double)l * (double)l;
+    kap[l] = std::sqrt(ll / (4.0 * ll - 1.0));   // k_{l,l-1}(m=0), Eq. (tdse-potential)
+  }
+  kap[L + 1] = 0.0;
+  int mstart = N;
+  if (h->opts.absorber) {
+    const double R = r[N - 1], ra = h->opts.absorber_r;
+    for (int j = 0; j < N; ++j) {
+      if (r[j] > ra) {
+        if (mstart == N) mstart = j;
+        msk[j] = std::pow(std::cos(0.5 * M_PI * (r[j] - ra) / (R - ra)), 0.125);
+      }
+    }
+  }
+  h->mask_start = mstart;
+  cudaStream_t s = h->stream;
+  TDSE_CUDA(h, cudaMemcpyAsync(h->rj, r.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy r");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->diag, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice, s), "copy diag");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->kappa, kap.data(), sizeof(double) * (L + 2), cudaMemcpyHostToDevice, s), "copy kappa");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->mask, msk.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy mask");
+  TDSE_CUDA(h, cudaStreamSynchronize(s), "sync tables");
+  return TDSE_OK;
+}
+
+void free_all(tdse *h) {
+  cudaFree(h->psi);
+  cudaFree(h->ref0);
+  cudaFree(h->work);
+  cudaFree(h->diag);
+  cudaFree(h->rj);
+  cudaFree(h->kappa);
+  cudaFree(h->mask);
+  cudaFree(h->red);
+  cudaFree(h->ls);
+  cudaFree(h->status);
+  cudaFree(h->obs_partials);
+  cudaFree(h->obs_out);
+  for (auto &m : h->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+int ensure_work(tdse *h, size_t nvec) {
+  if (h->work_vecs >= nvec) return TDSE_OK;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before realloc");
+  cudaFree(h->work);
+  h->work = nullptr;
+  h->work_vecs = 0;
+  cudaError_t e = cudaMalloc(&h->work, sizeof(double2) * npts(h) * nvec);
+  if (e != cudaSuccess) {
+    h->work = nullptr;
+    cudaGetLastError();
+    return fail(h, TDSE_ERR_OOM, "work vectors: " + std::string(cudaGetErrorString(e)));
+  }
+  h->work_vecs = nvec;
+  return TDSE_OK;
+}
+
+double field_at(const tdse *h, double t) {
+  if (h->E0 == 0.0 || h->omega <= 0.0) return 0.0;
+  const double T = 2.0 * M_PI * h->ncycles / h->omega;
+  if (t < 0.0 || t > T) return 0.0;
+  const double env = std::sin(M_PI * t / T);
+  return h->E0 * env * env * std::sin(h->omega * t + h->cep);
+}
+
+int check_status_word(tdse *h) {
+  int st = 0;
+  TDSE_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read status");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync status");
+  if (st & kStatusNonFinite) {
+    const int zero = 0;
+    TDSE_CUDA(h, cudaMemcpyAsync(h->status, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream), "clear status");
+    TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync status");
+    return fail(h, TDSE_ERR_NONFINITE, "state holds Inf/NaN (unstable step size?)");
+  }
+  return TDSE_OK;
+}
+
+// ---- step plans ------------------------------------------------------------
+int taylor_steps(tdse *h, int P, double dt, long nsteps) {
+  int rc = ensure_work(h, 2);
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const size_t G = npts(h);
+  double2 *buf[2] = {h->work, h->work + G};
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const double2 *in = h->psi;
+    for (int k = P; k >= 1; --k) {
+      const bool last = (k == 1);
+      double2 *out = last ? ((P == 1) ? buf[0] : h->psi) : buf[(P - k) & 1];
+      TDSE_LAUNCH(h, TDSE_K_TAYLOR_STAGE, launch_taylor_stage(h->g, op, E, dt / (double)k, in, h->psi, out, last, h->stream),
+                  "taylor stage");
+      in = out;
+    }
+    if (P == 1)
+      TDSE_CUDA(h, cudaMemcpyAsync(h->psi, buf[0], sizeof(double2) * G, cudaMemcpyDeviceToDevice, h->stream),
+                "taylor copy");
+  }
+  return TDSE_OK;
+}
+
+int rk4_steps(tdse *h, double dt, long nsteps) {
+  int rc = ensure_work(h, 3);
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const size_t G = npts(h);
+  double2 *ga = h->work, *gb = h->work + G, *acc = h->work + 2 * G;
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double tn = t0 + (double)n * dt;
+    const double E1 = field_at(h, tn), E2 = field_at(h, tn + 0.5 * dt), E4 = field_at(h, tn + dt);
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E1, 1, dt, h->psi, h->psi, h->psi, acc, ga, nullptr, h->stream), "rk stage 1");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 2, dt, ga, h->psi, acc, acc, gb, nullptr, h->stream), "rk stage 2");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 3, dt, gb, h->psi, acc, acc, ga, nullptr, h->stream), "rk stage 3");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E4, 4, dt, ga, h->psi, acc, nullptr, nullptr, h->psi, h->stream), "rk stage 4");
+  }
+  return TDSE_OK;
+}
+
+int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
+  // work slot 0: z; slots 1..m-1: U_1..U_{m-1} (U_0 is psi itself)
+  int rc = ensure_work(h, (size_t)(m > 1 ? m : 1));
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const size_t G = npts(h);
+  double2 *z = h->work;
+  auto U = [&](int j) -> double2 * { return j == 0 ? h->psi : h->work + (size_t)j * G; };
+  const double t0 = h->t;
+  if (nsteps > 0)
+    TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
+  for (long n = 0; n < nsteps; ++n) {
+    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    for (int j = 0; j < m; ++j) {
+      TDSE_LAUNCH(h, TDSE_K_LANCZOS_A, launch_lanczos_a(h->g, op, E, j, U(j), j > 0 ? U(j - 1) : nullptr, z, h->red, h->ls, h->stream),
+                  "lanczos a");
+      if (j + 1 < m)
+        TDSE_LAUNCH(h, TDSE_K_LANCZOS_B, launch_lanczos_b(h->g, j, z, U(j), U(j + 1), h->red, h->ls, h->stream), "lanczos b");
+    }
+    TDSE_LAUNCH(h, TDSE_K_LANCZOS_EXPM, launch_lanczos_expm(m, dt, h->ls, h->stream), "lanczos expm");
+    TDSE_LAUNCH(h, TDSE_K_LANCZOS_COMBINE, launch_lanczos_combine(h->g, op, m, h->psi, h->work + G, G, h->red, h->ls, h->status, h->stream),
+                "lanczos combine");
+  }
+  return TDSE_OK;
+}
+
+void initial_state(const tdse *h, std::vector<double> &F) {
+  const int N = h->g.N;
+  F.assign(2 * npts(h), 0.0);
+  double s = 0.0;
+  for (int j = 0; j < N; ++j) {
+    const double r = (double)(j + 1) * h->g.dr + h->opts.offset;
+    const double p = 2.0 * r * std::exp(-r);
+    F[2 * j] = p;
+    s += p * p;
+  }
+  const double scale = 1.0 / std::sqrt(h->g.dr * s);
+  for (int j = 0; j < N; ++j) F[2 * j] *= scale;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double *v_table,
+                tdse_t **out) {
+  if (!out) return TDSE_ERR_ARG;
+  *out = nullptr;
+  if (N < 1 || lmax < 0 || !(dr > 0.0) || (stencil != 3 && stencil != 5) || !std::isfinite(Z))
+    return TDSE_ERR_ARG;
+  const size_t G = (size_t)N * (lmax + 1);
+  const dim3 sg = stencil_grid(N, lmax);
+  const size_t eb = (G + 1023) / 1024;
+  if ((size_t)sg.x * sg.y > (size_t)kMaxPartials || eb > (size_t)kMaxPartials) return TDSE_ERR_ARG;
+  tdse *h = new (std::nothrow) tdse();
+  if (!h) return TDSE_ERR_OOM;
+  h->g.N = N;
+  h->g.L = lmax;
+  h->g.stencil = stencil;
+  h->g.dr = dr;
+  const double h2 = dr * dr;
+  if (stencil == 5) {       // -1/2 of [-f(j+2) + 16 f(j+1) - 30 f(j) + 16 f(j-1) - f(j-2)] / (12 h^2)
+    h->g.c0 = 30.0 / (24.0 * h2);
+    h->g.c1 = -16.0 / (24.0 * h2);
+    h->g.c2 = 1.0 / (24.0 * h2);
+  } else {                  // -1/2 of [f(j+1) - 2 f(j) + f(j-1)] / h^2
+    h->g.c0 = 1.0 / h2;
+    h->g.c1 = -0.5 / h2;
+    h->g.c2 = 0.0;
+  }
+  h->Z = Z;
+  if (v_table) h->vtab.assign(v_table, v_table + N);
+  std::memset(&h->opts, 0, sizeof(h->opts));
+  h->opts.ghost = TDSE_GHOST_ZERO;
+  h->opts.r_b = 10.0;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    h->own_stream = nullptr;
+    delete h;
+    cudaGetLastError();
+    return TDSE_ERR_CUDA;
+  }
+  h->stream = h->own_stream;
+  const int nbx = observables_blocks(h->g);
+  const size_t obs_n = (size_t)5 * nbx * (lmax + 1) + 2;
+  bool ok = cudaMalloc(&h->psi, sizeof(double2) * G) == cudaSuccess &&
+            cudaMalloc(&h->ref0, sizeof(double2) * N) == cudaSuccess &&
+            cudaMalloc(&h->diag, sizeof(double) * G) == cudaSuccess &&
+            cudaMalloc(&h->rj, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&h->kappa, sizeof(double) * (lmax + 2)) == cudaSuccess &&
+            cudaMalloc(&h->mask, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&h->red, sizeof(Reduction)) == cudaSuccess &&
+            cudaMalloc(&h->ls, sizeof(LanczosScalars)) == cudaSuccess &&
+            cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->obs_partials, sizeof(double) * obs_n) == cudaSuccess &&
+            cudaMalloc(&h->obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return TDSE_ERR_OOM;
+  }
+  if (cudaMemsetAsync(h->red, 0, sizeof(Reduction), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->ls, 0, sizeof(LanczosScalars), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->obs_partials, 0, sizeof(double) * obs_n, h->stream) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return TDSE_ERR_CUDA;
+  }
+  int rc = build_tables(h);
+  if (rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  std::vector<double> F;
+  initial_state(h, F);
+  if (cudaMemcpy(h->psi, F.data(), sizeof(double) * F.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->ref0, F.data(), sizeof(double2) * N, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return TDSE_ERR_CUDA;
+  }
+  *out = h;
+  return TDSE_OK;
+}
+
+int tdse_destroy(tdse_t *h) {
+  if (!h) return TDSE_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return TDSE_OK;
+}
+
+const char *tdse_last_error(const tdse_t *h) {
+  if (!h) return kNoHandle;
+  return h->err.c_str();
+}
+
+int tdse_set_options(tdse_t *h, const tdse_opts *o) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!o) return fail(h, TDSE_ERR_ARG, "null options");
+  if (o->ghost != TDSE_GHOST_ZERO && o->ghost != TDSE_GHOST_ODD)
+    return fail(h, TDSE_ERR_ARG, "ghost must be 0 or 1");
+  const double rfirst = h->g.dr + o->offset, rlast = h->g.N * h->g.dr + o->offset;
+  if (!(rfirst > 0.0)) return fail(h, TDSE_ERR_ARG, "offset puts the first point at r <= 0");
+  if (o->absorber && !(o->absorber_r >= 0.0 && o->absorber_r < rlast))
+    return fail(h, TDSE_ERR_ARG, "absorber radius outside the box");
+  if (!std::isfinite(o->r_b)) return fail(h, TDSE_ERR_ARG, "r_b must be finite");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  h->opts = *o;
+  return build_tables(h);
+}
+
+int tdse_set_stream(tdse_t *h, void *cuda_stream) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync old stream");
+  h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+  return TDSE_OK;
+}
+
+int tdse_set_pulse(tdse_t *h, double E0, double omega, double ncycles, double cep) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!std::isfinite(E0) || !std::isfinite(omega) || !std::isfinite(ncycles) || !std::isfinite(cep))
+    return fail(h, TDSE_ERR_ARG, "non-finite pulse parameter");
+  if (E0 != 0.0 && (!(omega > 0.0) || !(ncycles > 0.0)))
+    return fail(h, TDSE_ERR_ARG, "pulse needs omega > 0 and ncycles > 0");
+  h->E0 = E0;
+  h->omega = omega;
+  h->ncycles = ncycles;
+  h->cep = cep;
+  return TDSE_OK;
+}
+
+double tdse_field(const tdse_t *h, double t) { return h ? field_at(h, t) : 0.0; }
+
+int tdse_set_time(tdse_t *h, double t) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!std::isfinite(t)) return fail(h, TDSE_ERR_ARG, "non-finite time");
+  h->t = t;
+  return TDSE_OK;
+}
+
+double tdse_get_time(const tdse_t *h) { return h ? h->t : 0.0; }
+
+int tdse_set_state(tdse_t *h, const double *F) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!F) return fail(h, TDSE_ERR_ARG, "null state");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyHostToDevice, h->stream), "set state");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync set state");
+  return TDSE_OK;
+}
+
+int tdse_get_state(tdse_t *h, double *F) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!F) return fail(h, TDSE_ERR_ARG, "null state");
+  TDSE_CUDA(h, cudaMemcpyAsync(F, h->psi, sizeof(double2) * npts(h), cudaMemcpyDeviceToHost, h->stream), "get state");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync get state");
+  return TDSE_OK;
+}
+
+int tdse_set_state_device(tdse_t *h, const void *F) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!F || ((uintptr_t)F & 15)) return fail(h, TDSE_ERR_ARG, "device state must be 16-byte aligned");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyDeviceToDevice, h->stream), "set state");
+  return TDSE_OK;
+}
+
+int tdse_get_state_device(tdse_t *h, void *F) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!F || ((uintptr_t)F & 15)) return fail(h, TDSE_ERR_ARG, "device state must be 16-byte aligned");
+  TDSE_CUDA(h, cudaMemcpyAsync(F, h->psi, sizeof(double2) * npts(h), cudaMemcpyDeviceToDevice, h->stream), "get state");
+  return TDSE_OK;
+}
+
+int tdse_set_reference(tdse_t *h, const double *f0) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!f0) return fail(h, TDSE_ERR_ARG, "null reference");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->ref0, f0, sizeof(double2) * h->g.N, cudaMemcpyHostToDevice, h->stream), "set ref");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync set ref");
+  return TDSE_OK;
+}
+
+int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  switch (method) {
+    case TDSE_TAYLOR:
+      if (order < 1) return fail(h, TDSE_ERR_ARG, "Taylor order must be >= 1");
+      rc = taylor_steps(h, order, dt, nsteps);
+      break;
+    case TDSE_RK4:
+      rc = rk4_steps(h, dt, nsteps);
+      break;
+    case TDSE_LANCZOS:
+      if (order < 1 || order > TDSE_MAX_KRYLOV)
+        return fail(h, TDSE_ERR_ARG, "Krylov dimension must be in 1..TDSE_MAX_KRYLOV");
+      rc = lanczos_steps(h, order, dt, nsteps);
+      break;
+    default:
+      return fail(h, TDSE_ERR_ARG, "unknown method");
+  }
+  if (rc) return rc;
+  h->t += (double)nsteps * dt;
+  return TDSE_OK;
+}
+
+int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, double *yield,
+                     double *p_ground) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  const int L = h->g.L;
+  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES, launch_observables(h->g, view(h), h->psi, h->ref0, h->opts.r_b, h->obs_partials, 5,
+                                    h->obs_out, h->stream),
+              "observables");
+  std::vector<double> out(L + 5);
+  TDSE_CUDA(h, cudaMemcpyAsync(out.data(), h->obs_out, sizeof(double) * (L + 5), cudaMemcpyDeviceToHost, h->stream),
+            "read observables");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync observables");
+  rc = check_status_word(h);
+  if (rc) return rc;
+  if (norm) *norm = out[0];
+  if (dipole) *dipole = out[1];
+  if (yield) *yield = out[2];
+  if (p_ground) *p_ground = out[3];
+  if (l_pop) std::memcpy(l_pop, out.data() + 4, sizeof(double) * (L + 1));
+  if (!std::isfinite(out[0])) return fail(h, TDSE_ERR_NONFINITE, "state holds Inf/NaN (unstable step size?)");
+  return TDSE_OK;
+}
+
+int tdse_apply_h(tdse_t *h, double E, const void *x, void *y) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!x || !y || ((uintptr_t)x & 15) || ((uintptr_t)y & 15))
+    return fail(h, TDSE_ERR_ARG, "x and y must be 16-byte aligned device pointers");
+  const size_t bytes = sizeof(double2) * npts(h);
+  const char *xa = (const char *)x, *ya = (const char *)y;
+  if (xa < ya + bytes && ya < xa + bytes) return fail(h, TDSE_ERR_ARG, "x and y overlap");
+  if (!std::isfinite(E)) return fail(h, TDSE_ERR_ARG, "non-finite field");
+  TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), E, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
+  return TDSE_OK;
+}
+
+int tdse_sync(tdse_t *h) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  return check_status_word(h);
+}
+
+long long tdse_launch_count(const tdse_t *h) { return h ? h->launches : 0; }
+
+namespace {
+int prof_collect(tdse *h) {
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync profile");
+  for (size_t i = 0; i < h->nmarks; ++i) {
+    float ms = 0.f;
+    TDSE_CUDA(h, cudaEventElapsedTime(&ms, h->marks[i].a, h->marks[i].b), "event time");
+    h->prof_ms[h->marks[i].kind] += ms;
+    h->prof_n[h->marks[i].kind] += 1;
+  }
+  h->nmarks = 0;
+  return TDSE_OK;
+}
+}  // namespace
+
+int tdse_profile(tdse_t *h, int enable) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (h->profiling) {
+    rc = prof_collect(h);
+    if (rc) return rc;
+  }
+  if (enable) {
+    for (int k = 0; k < TDSE_K_COUNT; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_n[k] = 0;
+    }
+  }
+  h->profiling = enable != 0;
+  return TDSE_OK;
+}
+
+int tdse_profile_read(tdse_t *h, int kind, double *total_ms, long long *launches) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (kind < 0 || kind >= TDSE_K_COUNT) return fail(h, TDSE_ERR_ARG, "unknown kernel kind");
+  if (h->profiling) {
+    rc = prof_collect(h);
+    if (rc) return rc;
+  }
+  if (total_ms) *total_ms = h->prof_ms[kind];
+  if (launches) *launches = h->prof_n[kind];
+  return TDSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,561 @@
+// FP64 kernels of the finite-difference TDSE path (sm_103a).
+//
+// Every stencil kernel evaluates the length-gauge Hamiltonian of Eq. (h_matrix)
+// (arXiv 1308.1856, Sec. 2):
+//   (H x)_{l,j} = D_{l,j} x_{l,j} + c1 (x_{l,j-1} + x_{l,j+1}) [+ c2 (x_{l,j-2} + x_{l,j+2})]
+//               + E r_j (kappa_l x_{l-1,j} + kappa_{l+1} x_{l+1,j})
+// with D_{l,j} = c0 + l(l+1)/(2 r_j^2) + V(r_j) read from a table, H real and
+// symmetric, so the real and imaginary parts go through the same real operator.
+//
+// Work decomposition: one thread owns one radial index j and kRowsPerThread
+// consecutive partial waves l; it walks l upwards keeping x_{l-1,j}, x_{l,j},
+// x_{l+1,j} in registers, so each l-neighbour is loaded once and the coupling
+// coefficient kappa_{l+1} E r_j is shared by rows l and l+1.  The radial
+// neighbours come from L1/L2 (neighbouring threads load the same lines).
+//
+// On GB300 an FP64 instruction issues at 2 lanes/clock/SM, so these kernels
+// are FP64-issue bound: the arithmetic is written with explicit __dmul_rn /
+// __dadd_rn / __fma_rn so that each grid point costs a known number of FP64
+// instructions (5-point Taylor stage: 17).
+#include <cuda_runtime.h>
+
+#include "tdse_internal.cuh"
+
+namespace tdse_dev {
+
+namespace {
+
+__device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed shuffle tree + fixed warp order); the result
+// is valid in every thread.  `sh` needs blockDim/32 + 1 doubles.
+__device__ double block_sum(double v, double *sh) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  v = warp_sum(v);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double s = (tid < (nthreads >> 5)) ? sh[tid] : 0.0;
+    s = warp_sum(s);
+    if (tid == 0) sh[nthreads >> 5] = s;
+  }
+  __syncthreads();
+  const double r = sh[nthreads >> 5];
+  __syncthreads();
+  return r;
+}
+
+// Publish this block's partial and report whether this block arrived last.
+// The last block then reduces all partials in index order (deterministic).
+__device__ bool publish_partial(double block_value, Reduction *red, unsigned nblocks) {
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (tid == 0) {
+    red->partial[bid] = block_value;
+    __threadfence();
+    const unsigned t = atomicAdd(&red->ticket, 1u);
+    s_last = (t == nblocks - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Called by every thread of the last block: fixed-order sum of all partials.
+__device__ double reduce_partials(Reduction *red, unsigned nblocks, double *sh) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned k = tid; k < nblocks; k += nthreads) s += __ldcg(&red->partial[k]);
+  s = block_sum(s, sh);
+  if (tid == 0) red->ticket = 0u;
+  return s;
+}
+
+struct StencilIn {
+  const double2 *__restrict__ x;
+  const double *__restrict__ diag;
+  const double *__restrict__ rj;
+  const double *__restrict__ kappa;
+  int N, L;
+  double c1, c2, E;
+};
+
+// (H x) at (l, i) from the register window; 15 FP64 instructions (5-point).
+template <int ST>
+__device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *row, int i,
+                                           double d, double2 prev, double2 cur, double2 next,
+                                           double a_cur, double a_next) {
+  const double2 z = make_double2(0.0, 0.0);
+  const double2 m1 = (i >= 1) ? ldg2(row + i - 1) : z;
+  const double2 p1 = (i + 1 < in.N) ? ldg2(row + i + 1) : z;
+  double tx = __dmul_rn(d, cur.x);
+  double ty = __dmul_rn(d, cur.y);
+  tx = __fma_rn(in.c1, __dadd_rn(m1.x, p1.x), tx);
+  ty = __fma_rn(in.c1, __dadd_rn(m1.y, p1.y), ty);
+  if (ST == 5) {
+    const double2 m2 = (i >= 2) ? ldg2(row + i - 2) : z;
+    const double2 p2 = (i + 2 < in.N) ? ldg2(row + i + 2) : z;
+    tx = __fma_rn(in.c2, __dadd_rn(m2.x, p2.x), tx);
+    ty = __fma_rn(in.c2, __dadd_rn(m2.y, p2.y), ty);
+  }
+  tx = __fma_rn(a_cur, prev.x, tx);
+  ty = __fma_rn(a_cur, prev.y, ty);
+  tx = __fma_rn(a_next, next.x, tx);
+  ty = __fma_rn(a_next, next.y, ty);
+  return make_double2(tx, ty);
+}
+
+// Walk rows l0 .. l0+kRowsPerThread-1 of column i and call f(l, idx, Hx, x_center).
+template <int ST, typename F>
+__device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, F &&f) {
+  const int N = in.N, L = in.L;
+  const double2 z = make_double2(0.0, 0.0);
+  const double Er = __dmul_rn(in.E, in.rj[i]);
+  double2 prev = (l0 > 0) ? ldg2(in.x + (size_t)(l0 - 1) * N + i) : z;
+  double2 cur = ldg2(in.x + (size_t)l0 * N + i);
+  double a_cur = __dmul_rn(in.kappa[l0], Er);
+  const int l1 = min(l0 + kRowsPerThread, L + 1);
+  for (int l = l0; l < l1; ++l) {
+    const size_t idx = (size_t)l * N + i;
+    const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
+    const double a_next = __dmul_rn(in.kappa[l + 1], Er);
+    const double d = __ldg(in.diag + idx);
+    const double2 t = h_point<ST>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
+    f(l, idx, t, cur);
+    prev = cur;
+    cur = next;
+    a_cur = a_next;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y = H(E) x
+template <int ST>
+__global__ void __launch_bounds__(kBlockJ) apply_h_kernel(StencilIn in, double2 *__restrict__ y) {
+  const int i = blockIdx.x * kBlockJ + threadIdx.x;
+  const int l0 = blockIdx.y * kRowsPerThread;
+  if (i >= in.N || l0 > in.L) return;
+  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
+}
+
+// Horner stage of the Taylor polynomial (Eq. (Taylor)):
+//   v_out = psi + (-i s) H v_in,  s = dt / k.
+// The last stage (k = 1) writes psi itself and applies the absorber mask.
+template <int ST>
+__global__ void __launch_bounds__(kBlockJ)
+    taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
+                        double2 *__restrict__ out, const double *__restrict__ mask,
+                        int mask_start, int final_stage) {
+  const int i = blockIdx.x * kBlockJ + threadIdx.x;
+  const int l0 = blockIdx.y * kRowsPerThread;
+  if (i >= in.N || l0 > in.L) return;
+  const bool masked = final_stage && i >= mask_start;
+  const double mv = masked ? mask[i] : 1.0;
+  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) {
+    const double2 p = psi[idx];
+    double2 o;
+    o.x = __fma_rn(s, t.y, p.x);     // (-i s)(tx + i ty) = s ty - i s tx
+    o.y = __fma_rn(-s, t.x, p.y);
+    if (masked) { o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
+    out[idx] = o;
+  });
+}
+
+// Stage `stage` (1..4) of classic RK4 (Eq. (RKDeriv)) with k = -i H(t_n + c dt) g:
+//   stages 1-3: g_next = psi + (dt a) k,  acc_out = acc_in + (dt b) k  (acc_in = psi at stage 1)
+//   stage 4:    psi    = acc_in + (dt b) k, then the absorber mask.
+template <int ST>
+__global__ void __launch_bounds__(kBlockJ)
+    rk_stage_kernel(StencilIn in, int stage, double ca, double cb,
+                    const double2 *__restrict__ psi, const double2 *__restrict__ acc_in,
+                    double2 *__restrict__ acc_out, double2 *__restrict__ g_next,
+                    double2 *__restrict__ psi_out, const double *__restrict__ mask,
+                    int mask_start) {
+  const int i = blockIdx.x * kBlockJ + threadIdx.x;
+  const int l0 = blockIdx.y * kRowsPerThread;
+  if (i >= in.N || l0 > in.L) return;
+  const bool masked = (stage == 4) && i >= mask_start;
+  const double mv = masked ? mask[i] : 1.0;
+  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) {
+    const double2 a = acc_in[idx];
+    if (stage < 4) {
+      const double2 p = psi[idx];
+      g_next[idx] = make_double2(__fma_rn(ca, t.y, p.x), __fma_rn(-ca, t.x, p.y));
+      acc_out[idx] = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
+    } else {
+      double2 o = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
+      if (masked) { o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
+      psi_out[idx] = o;
+    }
+  });
+}
+
+// Lanczos iteration j, first half (Appendix "Lanczos methods"):
+//   z = H q_j - beta_{j-1} q_{j-1},   q_j = sigma_j U_j,
+//   beta_{j-1} q_{j-1} = (sigma_{j-1} / sigma_j) U_{j-1},
+//   alpha_j = Re <q_j, z> = sigma_j Re <U_j, z>  (grid reduction; last block stores it).
+template <int ST>
+__global__ void __launch_bounds__(kBlockJ)
+    lanczos_a_kernel(StencilIn in, int j, const double2 *__restrict__ uprev,
+                     double2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
+  __shared__ double sh[kBlockJ / 32 + 1];
+  const int i = blockIdx.x * kBlockJ + threadIdx.x;
+  const int l0 = blockIdx.y * kRowsPerThread;
+  const double sig = ls->sigma[j];
+  const double cprev = (j > 0) ? ls->sigma[j - 1] / sig : 0.0;
+  double acc = 0.0;
+  if (i < in.N && l0 <= in.L) {
+    walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2 u) {
+      double2 o;
+      if (j > 0) {
+        const double2 up = uprev[idx];
+        o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, up.x));
+        o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, up.y));
+      } else {
+        o.x = __dmul_rn(sig, t.x);
+        o.y = __dmul_rn(sig, t.y);
+      }
+      z[idx] = o;
+      acc = __fma_rn(u.x, o.x, acc);
+      acc = __fma_rn(u.y, o.y, acc);
+    });
+  }
+  const double b = block_sum(acc, sh);
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  if (publish_partial(b, red, nblocks)) {
+    const double s = reduce_partials(red, nblocks, sh);
+    if (threadIdx.x == 0) ls->alpha[j] = s * sig;
+  }
+}
+
+// Elementwise kernels: each thread owns kElems elements spaced by the block size.
+constexpr int kElemThreads = 256;
+constexpr int kElems = 4;
+
+// Lanczos iteration j, second half: U_{j+1} = z - alpha_j sigma_j U_j; beta_j = ||U_{j+1}||.
+__global__ void __launch_bounds__(kElemThreads)
+    lanczos_b_kernel(size_t G, int j, const double2 *__restrict__ z, const double2 *__restrict__ u,
+                     double2 *__restrict__ unext, Reduction *red, LanczosScalars *ls) {
+  __shared__ double sh[kElemThreads / 32 + 1];
+  const double c = -ls->alpha[j] * ls->sigma[j];
+  double acc = 0.0;
+  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const size_t idx = base + (size_t)e * kElemThreads;
+    if (idx < G) {
+      const double2 zz = z[idx], uu = u[idx];
+      const double2 o = make_double2(__fma_rn(c, uu.x, zz.x), __fma_rn(c, uu.y, zz.y));
+      unext[idx] = o;
+      acc = __fma_rn(o.x, o.x, acc);
+      acc = __fma_rn(o.y, o.y, acc);
+    }
+  }
+  const double b = block_sum(acc, sh);
+  if (publish_partial(b, red, gridDim.x)) {
+    const double s = reduce_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      const double beta = sqrt(s);
+      ls->beta[j] = beta;
+      ls->sigma[j + 1] = (beta > 0.0) ? 1.0 / beta : 0.0;
+    }
+  }
+}
+
+// ||x||^2 -> Lanczos start scalars (sigma_0 = 1/||psi||, psinorm) and the
+// non-finite status bit.
+__global__ void __launch_bounds__(kElemThreads)
+    norm_kernel(size_t G, const double2 *__restrict__ x, Reduction *red, LanczosScalars *ls,
+                int *status) {
+  __shared__ double sh[kElemThreads / 32 + 1];
+  double acc = 0.0;
+  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const size_t idx = base + (size_t)e * kElemThreads;
+    if (idx < G) {
+      const double2 v = x[idx];
+      acc = __fma_rn(v.x, v.x, acc);
+      acc = __fma_rn(v.y, v.y, acc);
+    }
+  }
+  const double b = block_sum(acc, sh);
+  if (publish_partial(b, red, gridDim.x)) {
+    const double s = reduce_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      red->normsq = s;
+      const double nrm = sqrt(s);
+      ls->psinorm = nrm;
+      ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      if (!isfinite(s)) atomicOr(status, kStatusNonFinite);
+    }
+  }
+}
+
+// psi_new = sum_{j<k} coef_j U_j  (U_0 = psi, read and written in place by
+// the same thread), then the absorber mask and ||psi_new||^2 for the next step.
+__global__ void __launch_bounds__(kElemThreads)
+    lanczos_combine_kernel(size_t G, int N, double2 *psi, const double2 *__restrict__ work,
+                           size_t stride, const double *__restrict__ mask, int mask_start,
+                           Reduction *red, LanczosScalars *ls, int *status) {
+  __shared__ double sh[kElemThreads / 32 + 1];
+  __shared__ double2 coef[kMaxKrylov];
+  __shared__ int s_k;
+  if (threadIdx.x < kMaxKrylov) coef[threadIdx.x] = ls->coef[threadIdx.x];
+  if (threadIdx.x == 0) s_k = ls->kdim;
+  __syncthreads();
+  const int k = s_k;
+  double acc = 0.0;
+  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const size_t idx = base + (size_t)e * kElemThreads;
+    if (idx < G) {
+      const double2 u0 = psi[idx];
+      double ox = __fma_rn(coef[0].x, u0.x, __dmul_rn(-coef[0].y, u0.y));
+      double oy = __fma_rn(coef[0].x, u0.y, __dmul_rn(coef[0].y, u0.x));
+      for (int jj = 1; jj < k; ++jj) {
+        const double2 u = work[(size_t)(jj - 1) * stride + idx];
+        const double2 c = coef[jj];
+        ox = __fma_rn(c.x, u.x, ox);
+        ox = __fma_rn(-c.y, u.y, ox);
+        oy = __fma_rn(c.x, u.y, oy);
+        oy = __fma_rn(c.y, u.x, oy);
+      }
+      const int jr = (int)(idx % (size_t)N);
+      if (jr >= mask_start) {
+        const double mv = mask[jr];
+        ox = __dmul_rn(mv, ox);
+        oy = __dmul_rn(mv, oy);
+      }
+      psi[idx] = make_double2(ox, oy);
+      acc = __fma_rn(ox, ox, acc);
+      acc = __fma_rn(oy, oy, acc);
+    }
+  }
+  const double b = block_sum(acc, sh);
+  if (publish_partial(b, red, gridDim.x)) {
+    const double s = reduce_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      red->normsq = s;
+      const double nrm = sqrt(s);
+      ls->psinorm = nrm;
+      ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      if (!isfinite(s)) atomicOr(status, kStatusNonFinite);
+    }
+  }
+}
+
+// Observables (Sec. 4): per block of row l, partial sums of
+//   q0: sum |f|^2, q1: sum_{r_j <= r_b} |f|^2, q2: sum r_j Re(conj(f_l) f_{l+1}),
+//   q3, q4: sum conj(ref_j) f_{0,j} (row 0 only).
+// Partials are laid out [q][row][bx]; the last block combines them in index
+// order into out = {norm, dipole, yield, p_ground, l_pop[0..L]}.
+constexpr int kObsThreads = 256;
+constexpr int kObsQ = 5;
+
+__global__ void __launch_bounds__(kObsThreads)
+    observables_kernel(const double2 *__restrict__ psi, const double2 *__restrict__ ref0,
+                       const double *__restrict__ rj, const double *__restrict__ kappa,
+                       int N, int L, double dr, double r_b, double *partials,
+                       unsigned *ticket, double *out) {
+  __shared__ double sh[kObsThreads / 32 + 1];
+  __shared__ unsigned s_last;
+  const int l = blockIdx.y;
+  const int nbx = gridDim.x;
+  double q[kObsQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * kObsThreads + threadIdx.x; i < N; i += nbx * kObsThreads) {
+    const size_t idx = (size_t)l * N + i;
+    const double2 f = psi[idx];
+    const double a = __fma_rn(f.x, f.x, __dmul_rn(f.y, f.y));
+    const double r = rj[i];
+    q[0] += a;
+    if (r <= r_b) q[1] += a;
+    if (l < L) {
+      const double2 g = psi[idx + N];
+      q[2] = __fma_rn(r, __fma_rn(f.x, g.x, __dmul_rn(f.y, g.y)), q[2]);
+    }
+    if (l == 0 && ref0) {
+      const double2 c = ref0[i];
+      q[3] += __fma_rn(c.x, f.x, __dmul_rn(c.y, f.y));    // Re(conj(c) f)
+      q[4] += __fma_rn(c.x, f.y, __dmul_rn(-c.y, f.x));   // Im(conj(c) f)
+    }
+  }
+  const size_t nb = (size_t)nbx * (L + 1);
+  const size_t bid = (size_t)l * nbx + blockIdx.x;
+  for (int k = 0; k < kObsQ; ++k) {
+    const double b = block_sum(q[k], sh);
+    if (threadIdx.x == 0) partials[(size_t)k * nb + bid] = b;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == nb - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: per-row sums in fixed order (thread t handles rows t, t+256, ...)
+  double norm_part = 0.0, inside_part = 0.0, dip_part = 0.0;
+  for (int row = threadIdx.x; row <= L; row += kObsThreads) {
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (int bx = 0; bx < nbx; ++bx) {
+      const size_t o = (size_t)row * nbx + bx;
+      p0 += __ldcg(&partials[0 * nb + o]);
+      p1 += __ldcg(&partials[1 * nb + o]);
+      p2 += __ldcg(&partials[2 * nb + o]);
+    }
+    out[4 + row] = dr * p0;
+    norm_part += p0;
+    inside_part += p1;
+    if (row < L) dip_part += 2.0 * kappa[row + 1] * dr * p2;
+  }
+  const double norm = block_sum(norm_part, sh);
+  const double inside = block_sum(inside_part, sh);
+  const double dip = block_sum(dip_part, sh);
+  if (threadIdx.x == 0) {
+    double ore = 0.0, oim = 0.0;
+    for (int bx = 0; bx < nbx; ++bx) {
+      ore += __ldcg(&partials[3 * nb + bx]);
+      oim += __ldcg(&partials[4 * nb + bx]);
+    }
+    ore *= dr;
+    oim *= dr;
+    out[0] = dr * norm;
+    out[1] = dip;
+    out[2] = 1.0 - dr * inside;
+    out[3] = ore * ore + oim * oim;
+    *ticket = 0u;
+  }
+}
+
+StencilIn make_in(const Geometry &g, const OperatorView &op, double E, const double2 *x) {
+  StencilIn in;
+  in.x = x;
+  in.diag = op.diag;
+  in.rj = op.rj;
+  in.kappa = op.kappa;
+  in.N = g.N;
+  in.L = g.L;
+  in.c1 = g.c1;
+  in.c2 = g.c2;
+  in.E = E;
+  return in;
+}
+
+inline unsigned elem_blocks(size_t G) {
+  const size_t per = (size_t)kElemThreads * kElems;
+  return (unsigned)((G + per - 1) / per);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_apply_h(const Geometry &g, const OperatorView &op, double E,
+                           const double2 *x, double2 *y, cudaStream_t s) {
+  const StencilIn in = make_in(g, op, E, x);
+  const dim3 grid = stencil_grid(g.N, g.L);
+  if (g.stencil == 5)
+    apply_h_kernel<5><<<grid, kBlockJ, 0, s>>>(in, y);
+  else
+    apply_h_kernel<3><<<grid, kBlockJ, 0, s>>>(in, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, double E, double s,
+                                const double2 *v_in, const double2 *psi, double2 *v_out,
+                                bool final_stage, cudaStream_t st) {
+  const StencilIn in = make_in(g, op, E, v_in);
+  const dim3 grid = stencil_grid(g.N, g.L);
+  if (g.stencil == 5)
+    taylor_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, op.mask_start,
+                                                     final_stage ? 1 : 0);
+  else
+    taylor_stage_kernel<3><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, op.mask_start,
+                                                     final_stage ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E, int stage,
+                            double dt, const double2 *gin, const double2 *psi,
+                            const double2 *acc_in, double2 *acc_out, double2 *g_next,
+                            double2 *psi_out, cudaStream_t st) {
+  // classic tableau: a_{s+1,s} = (1/2, 1/2, 1), b = (1, 2, 2, 1) / 6
+  static const double a_next[4] = {0.5, 0.5, 1.0, 0.0};
+  static const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const StencilIn in = make_in(g, op, E, gin);
+  const dim3 grid = stencil_grid(g.N, g.L);
+  const double ca = dt * a_next[stage - 1], cb = dt * b[stage - 1];
+  if (g.stencil == 5)
+    rk_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next,
+                                                 psi_out, op.mask, op.mask_start);
+  else
+    rk_stage_kernel<3><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next,
+                                                 psi_out, op.mask, op.mask_start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const Geometry &g, const double2 *x, Reduction *red,
+                        LanczosScalars *ls, int *status, cudaStream_t st) {
+  const size_t G = (size_t)g.N * (g.L + 1);
+  norm_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(G, x, red, ls, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E, int j,
+                             const double2 *u, const double2 *uprev, double2 *z,
+                             Reduction *red, LanczosScalars *ls, cudaStream_t st) {
+  const StencilIn in = make_in(g, op, E, u);
+  const dim3 grid = stencil_grid(g.N, g.L);
+  if (g.stencil == 5)
+    lanczos_a_kernel<5><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
+  else
+    lanczos_a_kernel<3><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
+                             double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st) {
+  const size_t G = (size_t)g.N * (g.L + 1);
+  lanczos_b_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(G, j, z, u, unext, red, ls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,
+                                   double2 *psi, const double2 *work, size_t stride,
+                                   Reduction *red, LanczosScalars *ls, int *status,
+                                   cudaStream_t st) {
+  (void)m;
+  const size_t G = (size_t)g.N * (g.L + 1);
+  lanczos_combine_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(
+      G, g.N, psi, work, stride, op.mask, op.mask_start, red, ls, status);
+  return cudaGetLastError();
+}
+
+int observables_blocks(const Geometry &g) {
+  const int per_row = (g.N + kObsThreads - 1) / kObsThreads;
+  return per_row < 8 ? per_row : 8;
+}
+
+cudaError_t launch_observables(const Geometry &g, const OperatorView &op, const double2 *psi,
+                               const double2 *ref0, double r_b, double *partials, int nq,
+                               double *out, cudaStream_t st) {
+  (void)nq;
+  const int nbx = observables_blocks(g);
+  const dim3 grid(nbx, g.L + 1);
+  // partials: kObsQ * nbx * (L+1) doubles followed by one unsigned ticket
+  unsigned *ticket = reinterpret_cast<unsigned *>(partials + (size_t)kObsQ * nbx * (g.L + 1));
+  observables_kernel<<<grid, kObsThreads, 0, st>>>(psi, ref0, op.rj, op.kappa, g.N, g.L, g.dr,
+                                                   r_b, partials, ticket, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tdse_dev
