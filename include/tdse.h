@@ -185,6 +185,37 @@ enum {
 int tdse_profile(tdse_t *h, int enable);
 int tdse_profile_read(tdse_t *h, int kind, double *total_ms, long long *launches);
 
+/*
+ * Observables of a caller-held device state WITHOUT allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (code running inside another component's graph
+ * capture or real-time loop, where an allocation would synchronise the device
+ * or break the capture, or an embedding that forbids the library from owning
+ * device memory) and so cannot create a handle.
+ *
+ * Same quantities as tdse_observables, for the grid r_j = j*dr + offset:
+ * out_dev (device, lmax+5 doubles, 8-byte aligned) receives
+ * {norm, dipole, yield, p_ground, l_pop[0..lmax]}.  psi_dev holds (lmax+1)*N
+ * interleaved complex doubles (device, 16-byte aligned); ref0_dev holds the N
+ * complex values of the p_ground reference (device) or is NULL (p_ground = 0).
+ * The work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * Scratch: the block partial sums live in one fixed file-scope device array
+ * (room for lmax <= TDSE_NOALLOC_MAX_LMAX, about 80 KB), which every GPU that
+ * loads the library keeps until the process exits.  The first call on each
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  All calls share the array: calls whose kernels can
+ * overlap on the GPU (unordered streams) race; calls ordered on one stream
+ * are safe.  Nothing is allocated or freed.
+ * Errors: TDSE_ERR_ARG (N < 1, dr <= 0, r_1 <= 0, lmax < 0 or
+ * lmax > TDSE_NOALLOC_MAX_LMAX, NULL or misaligned pointers), TDSE_ERR_CUDA.
+ */
+#define TDSE_NOALLOC_MAX_LMAX 255
+int tdse_observables_noalloc(int N, double dr, int lmax, double offset, double r_b,
+                             const void *psi_dev, const void *ref0_dev, double *out_dev,
+                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,8 @@ SIGNATURES = {
     "tdse_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_profile": (_c_int, [_vp, _c_int]),
     "tdse_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "tdse_observables_noalloc": (_c_int, [_c_int, _c_double, _c_int, _c_double, _c_double,
+                                          _vp, _vp, _vp, _vp]),
 }
 
 _LIB = None
@@ -113,6 +115,8 @@ tdse_sync = _fn("tdse_sync")
 tdse_launch_count = _fn("tdse_launch_count")
 tdse_profile = _fn("tdse_profile")
 tdse_profile_read = _fn("tdse_profile_read")
+tdse_observables_noalloc = _fn("tdse_observables_noalloc")
+TDSE_NOALLOC_MAX_LMAX = 255
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
                 "lanczos_expm", "lanczos_combine", "observables"]
