@@ -35,6 +35,9 @@ struct tdse {
   std::string err;
   bool poisoned = false;
   long long launches = 0;
+  // ||psi|| in the Lanczos scalars is current (the last work on psi was a
+  // Lanczos step, whose combine kernel leaves it there)
+  bool lanczos_norm_valid = false;
   // per-kernel timing (tdse_profile)
   bool profiling = false;
   struct Mark { int kind; cudaEvent_t a, b; };
@@ -263,7 +266,7 @@ int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
   double2 *z = h->work;
   auto U = [&](int j) -> double2 * { return j == 0 ? h->psi : h->work + (size_t)j * G; };
   const double t0 = h->t;
-  if (nsteps > 0)
+  if (nsteps > 0 && !h->lanczos_norm_valid)
     TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
   for (long n = 0; n < nsteps; ++n) {
     const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
@@ -305,14 +308,23 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
   if (N < 1 || lmax < 0 || !(dr > 0.0) || (stencil != 3 && stencil != 5) || !std::isfinite(Z))
     return TDSE_ERR_ARG;
   const size_t G = (size_t)N * (lmax + 1);
-  const dim3 sg = stencil_grid(N, lmax);
-  const size_t eb = (G + 1023) / 1024;
-  if ((size_t)sg.x * sg.y > (size_t)kMaxPartials || eb > (size_t)kMaxPartials) return TDSE_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    return TDSE_ERR_CUDA;
+  }
+  // one partial per block of the persistent grids; the final pass reads at most
+  // 16 per thread (128 threads)
+  if ((size_t)sms * kStencilBlocksPerSM > (size_t)16 * 128 ||
+      (size_t)sms * kElemBlocksPerSM > (size_t)16 * 128)
+    return TDSE_ERR_CUDA;
   tdse *h = new (std::nothrow) tdse();
   if (!h) return TDSE_ERR_OOM;
   h->g.N = N;
   h->g.L = lmax;
   h->g.stencil = stencil;
+  h->g.sms = sms;
   h->g.dr = dr;
   const double h2 = dr * dr;
   if (stencil == 5) {       // -1/2 of [-f(j+2) + 16 f(j+1) - 30 f(j) + 16 f(j-1) - f(j-2)] / (12 h^2)
@@ -398,6 +410,7 @@ const char *tdse_last_error(const tdse_t *h) {
 int tdse_set_options(tdse_t *h, const tdse_opts *o) {
   int rc = check_usable(h);
   if (rc) return rc;
+  h->lanczos_norm_valid = false;
   if (!o) return fail(h, TDSE_ERR_ARG, "null options");
   if (o->ghost != TDSE_GHOST_ZERO && o->ghost != TDSE_GHOST_ODD)
     return fail(h, TDSE_ERR_ARG, "ghost must be 0 or 1");
@@ -448,6 +461,7 @@ double tdse_get_time(const tdse_t *h) { return h ? h->t : 0.0; }
 int tdse_set_state(tdse_t *h, const double *F) {
   int rc = check_usable(h);
   if (rc) return rc;
+  h->lanczos_norm_valid = false;
   if (!F) return fail(h, TDSE_ERR_ARG, "null state");
   TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyHostToDevice, h->stream), "set state");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync set state");
@@ -466,6 +480,7 @@ int tdse_get_state(tdse_t *h, double *F) {
 int tdse_set_state_device(tdse_t *h, const void *F) {
   int rc = check_usable(h);
   if (rc) return rc;
+  h->lanczos_norm_valid = false;
   if (!F || ((uintptr_t)F & 15)) return fail(h, TDSE_ERR_ARG, "device state must be 16-byte aligned");
   TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyDeviceToDevice, h->stream), "set state");
   return TDSE_OK;
@@ -491,6 +506,7 @@ int tdse_set_reference(tdse_t *h, const double *f0) {
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
   int rc = check_usable(h);
   if (rc) return rc;
+  if (nsteps > 0 && method != TDSE_LANCZOS) h->lanczos_norm_valid = false;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
   switch (method) {
     case TDSE_TAYLOR:
@@ -504,6 +520,7 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
       if (order < 1 || order > TDSE_MAX_KRYLOV)
         return fail(h, TDSE_ERR_ARG, "Krylov dimension must be in 1..TDSE_MAX_KRYLOV");
       rc = lanczos_steps(h, order, dt, nsteps);
+      if (rc == TDSE_OK && nsteps > 0) h->lanczos_norm_valid = true;
       break;
     default:
       return fail(h, TDSE_ERR_ARG, "unknown method");

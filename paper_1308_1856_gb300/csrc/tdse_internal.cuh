@@ -20,9 +20,10 @@
 namespace tdse_dev {
 
 constexpr int kMaxKrylov = TDSE_MAX_KRYLOV;
-constexpr int kBlockJ = 128;        // threads per block along r
-constexpr int kRowsPerThread = 4;   // consecutive l rows handled by one thread
-constexpr int kMaxPartials = 8192;  // block partial slots of one grid reduction
+constexpr int kBlockJ = 128;            // threads per block of the stencil kernels
+constexpr int kStencilBlocksPerSM = 8;  // persistent stencil grid: 8 x 4 warps per SM
+constexpr int kElemBlocksPerSM = 4;     // persistent elementwise grid: 4 x 8 warps per SM
+constexpr int kMaxPartials = 16384;     // block partial slots of one grid reduction
 
 // Scalars of one Lanczos step, resident in device memory.
 struct LanczosScalars {
@@ -48,14 +49,10 @@ enum : int { kStatusNonFinite = 1 };
 
 struct Geometry {
   int N, L, stencil;
+  int sms;                        // multiprocessors of the device (persistent grids)
   double dr;
   double c0, c1, c2;              // -1/2 d2/dr2 coefficients (c2 = 0 for 3 points)
 };
-
-// Launch shape shared by the stencil kernels.
-inline dim3 stencil_grid(int N, int L) {
-  return dim3((N + kBlockJ - 1) / kBlockJ, (L + 1 + kRowsPerThread - 1) / kRowsPerThread);
-}
 
 // ---- launchers (tdse_kernels_fp64.cu) -------------------------------------
 struct OperatorView {

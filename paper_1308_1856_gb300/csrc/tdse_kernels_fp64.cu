@@ -7,11 +7,16 @@
 // with D_{l,j} = c0 + l(l+1)/(2 r_j^2) + V(r_j) read from a table, H real and
 // symmetric, so the real and imaginary parts go through the same real operator.
 //
-// Work decomposition: one thread owns one radial index j and kRowsPerThread
-// consecutive partial waves l; it walks l upwards keeping x_{l-1,j}, x_{l,j},
-// x_{l+1,j} in registers, so each l-neighbour is loaded once and the coupling
-// coefficient kappa_{l+1} E r_j is shared by rows l and l+1.  The radial
-// neighbours come from L1/L2 (neighbouring threads load the same lines).
+// Work decomposition: the grid is persistent (a few blocks per SM) and the
+// (L+1) x N points are cut into segments of 32 consecutive radial points of
+// one partial wave, ordered radial-group-major.  Warp w takes the contiguous
+// range [w T / W, (w+1) T / W) of the T segments, so every warp gets the same
+// amount of work to within one segment and the assignment (hence every
+// reduction order) is fixed.  Inside a range a lane owns one radial index j
+// and walks l upwards keeping x_{l-1,j}, x_{l,j}, x_{l+1,j} in registers, so
+// each l-neighbour is loaded once and the coupling coefficient
+// kappa_{l+1} E r_j is shared by rows l and l+1.  The radial neighbours come
+// from L1/L2 (neighbouring lanes load the same lines).
 //
 // On GB300 an FP64 instruction issues at 2 lanes/clock/SM, so these kernels
 // are FP64-issue bound: the arithmetic is written with explicit __dmul_rn /
@@ -52,29 +57,23 @@ __device__ double block_sum(double v, double *sh) {
   return r;
 }
 
-// Publish this block's partial and report whether this block arrived last.
-// The last block then reduces all partials in index order (deterministic).
-__device__ bool publish_partial(double block_value, Reduction *red, unsigned nblocks) {
-  __shared__ unsigned s_last;
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const unsigned bid = blockIdx.x + blockIdx.y * gridDim.x;
-  if (tid == 0) {
-    red->partial[bid] = block_value;
-    __threadfence();
-    const unsigned t = atomicAdd(&red->ticket, 1u);
-    s_last = (t == nblocks - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
 // Called by every thread of the last block: fixed-order sum of all partials.
-__device__ double reduce_partials(Reduction *red, unsigned nblocks, double *sh) {
+// Each thread first issues all its loads (independent, so their latencies
+// overlap) and then adds them in index order.
+constexpr int kMaxPartialsPerThread = 16;
+__device__ double reduce_partials(Reduction *red, unsigned nparts, double *sh) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nthreads = blockDim.x * blockDim.y;
   __threadfence();
+  double v[kMaxPartialsPerThread];
+#pragma unroll
+  for (int r = 0; r < kMaxPartialsPerThread; ++r) {
+    const unsigned k = tid + (unsigned)r * nthreads;
+    v[r] = (k < nparts) ? __ldcg(&red->partial[k]) : 0.0;
+  }
   double s = 0.0;
-  for (unsigned k = tid; k < nblocks; k += nthreads) s += __ldcg(&red->partial[k]);
+#pragma unroll
+  for (int r = 0; r < kMaxPartialsPerThread; ++r) s += v[r];
   s = block_sum(s, sh);
   if (tid == 0) red->ticket = 0u;
   return s;
@@ -114,37 +113,75 @@ __device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *r
   return make_double2(tx, ty);
 }
 
-// Walk rows l0 .. l0+kRowsPerThread-1 of column i and call f(l, idx, Hx, x_center).
+// Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).
 template <int ST, typename F>
-__device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, F &&f) {
+__device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const double2 z = make_double2(0.0, 0.0);
   const double Er = __dmul_rn(in.E, in.rj[i]);
   double2 prev = (l0 > 0) ? ldg2(in.x + (size_t)(l0 - 1) * N + i) : z;
   double2 cur = ldg2(in.x + (size_t)l0 * N + i);
   double a_cur = __dmul_rn(in.kappa[l0], Er);
-  const int l1 = min(l0 + kRowsPerThread, L + 1);
   for (int l = l0; l < l1; ++l) {
     const size_t idx = (size_t)l * N + i;
     const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
     const double a_next = __dmul_rn(in.kappa[l + 1], Er);
     const double d = __ldg(in.diag + idx);
     const double2 t = h_point<ST>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
-    f(l, idx, t, cur);
+    f(i, idx, t, cur);
     prev = cur;
     cur = next;
     a_cur = a_next;
   }
 }
 
+// Global warp index and warp count of a 1-D persistent launch.
+__device__ __forceinline__ int warp_id() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+__device__ __forceinline__ int warp_count() { return gridDim.x * (blockDim.x >> 5); }
+
+// Visit this warp's share of the 32-point row segments (see the file header).
+template <int ST, typename F>
+__device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const long long W = warp_count(), w = warp_id();
+  const int Lp1 = in.L + 1;
+  const long long NJ = (in.N + 31) >> 5;
+  const long long total = NJ * Lp1;
+  long long s = total * w / W;
+  const long long s_end = total * (w + 1) / W;
+  while (s < s_end) {
+    const int jg = (int)(s / Lp1);
+    const int l0 = (int)(s - (long long)jg * Lp1);
+    const long long left = s_end - s;
+    const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
+    const int i = jg * 32 + lane;
+    if (i < in.N) walk_rows<ST>(in, i, l0, l1, f);
+    s += l1 - l0;
+  }
+}
+
+// Sum v over the block (fixed shuffle tree and warp order), store it as this
+// block's partial and report whether this block is the last to finish.  The
+// last block then adds all block partials in block order, so the result does
+// not depend on timing.
+__device__ bool publish_block_partial(double v, Reduction *red, double *sh) {
+  __shared__ unsigned s_last;
+  const double b = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    red->partial[blockIdx.x] = b;
+    __threadfence();
+    const unsigned t = atomicAdd(&red->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
 // ---------------------------------------------------------------------------
 // y = H(E) x
 template <int ST>
 __global__ void __launch_bounds__(kBlockJ) apply_h_kernel(StencilIn in, double2 *__restrict__ y) {
-  const int i = blockIdx.x * kBlockJ + threadIdx.x;
-  const int l0 = blockIdx.y * kRowsPerThread;
-  if (i >= in.N || l0 > in.L) return;
-  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
+  for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
 }
 
 // Horner stage of the Taylor polynomial (Eq. (Taylor)):
@@ -155,17 +192,14 @@ __global__ void __launch_bounds__(kBlockJ)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
                         int mask_start, int final_stage) {
-  const int i = blockIdx.x * kBlockJ + threadIdx.x;
-  const int l0 = blockIdx.y * kRowsPerThread;
-  if (i >= in.N || l0 > in.L) return;
-  const bool masked = final_stage && i >= mask_start;
-  const double mv = masked ? mask[i] : 1.0;
-  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) {
+  const int mstart = final_stage ? mask_start : in.N;
+  for_my_segments<ST>(in, [&](int i, size_t idx, double2 t, double2) {
+    const bool masked = i >= mstart;
     const double2 p = psi[idx];
     double2 o;
     o.x = __fma_rn(s, t.y, p.x);     // (-i s)(tx + i ty) = s ty - i s tx
     o.y = __fma_rn(-s, t.x, p.y);
-    if (masked) { o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
+    if (masked) { const double mv = mask[i]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
     out[idx] = o;
   });
 }
@@ -180,12 +214,8 @@ __global__ void __launch_bounds__(kBlockJ)
                     double2 *__restrict__ acc_out, double2 *__restrict__ g_next,
                     double2 *__restrict__ psi_out, const double *__restrict__ mask,
                     int mask_start) {
-  const int i = blockIdx.x * kBlockJ + threadIdx.x;
-  const int l0 = blockIdx.y * kRowsPerThread;
-  if (i >= in.N || l0 > in.L) return;
-  const bool masked = (stage == 4) && i >= mask_start;
-  const double mv = masked ? mask[i] : 1.0;
-  walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2) {
+  const int mstart = (stage == 4) ? mask_start : in.N;
+  for_my_segments<ST>(in, [&](int i, size_t idx, double2 t, double2) {
     const double2 a = acc_in[idx];
     if (stage < 4) {
       const double2 p = psi[idx];
@@ -193,7 +223,7 @@ __global__ void __launch_bounds__(kBlockJ)
       acc_out[idx] = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
     } else {
       double2 o = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
-      if (masked) { o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
+      if (i >= mstart) { const double mv = mask[i]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
       psi_out[idx] = o;
     }
   });
@@ -208,38 +238,48 @@ __global__ void __launch_bounds__(kBlockJ)
     lanczos_a_kernel(StencilIn in, int j, const double2 *__restrict__ uprev,
                      double2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kBlockJ / 32 + 1];
-  const int i = blockIdx.x * kBlockJ + threadIdx.x;
-  const int l0 = blockIdx.y * kRowsPerThread;
   const double sig = ls->sigma[j];
   const double cprev = (j > 0) ? ls->sigma[j - 1] / sig : 0.0;
   double acc = 0.0;
-  if (i < in.N && l0 <= in.L) {
-    walk_rows<ST>(in, i, l0, [&](int, size_t idx, double2 t, double2 u) {
-      double2 o;
-      if (j > 0) {
-        const double2 up = uprev[idx];
-        o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, up.x));
-        o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, up.y));
-      } else {
-        o.x = __dmul_rn(sig, t.x);
-        o.y = __dmul_rn(sig, t.y);
-      }
-      z[idx] = o;
-      acc = __fma_rn(u.x, o.x, acc);
-      acc = __fma_rn(u.y, o.y, acc);
-    });
-  }
-  const double b = block_sum(acc, sh);
-  const unsigned nblocks = gridDim.x * gridDim.y;
-  if (publish_partial(b, red, nblocks)) {
-    const double s = reduce_partials(red, nblocks, sh);
+  for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2 u) {
+    double2 o;
+    if (j > 0) {
+      const double2 up = uprev[idx];
+      o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, up.x));
+      o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, up.y));
+    } else {
+      o.x = __dmul_rn(sig, t.x);
+      o.y = __dmul_rn(sig, t.y);
+    }
+    z[idx] = o;
+    acc = __fma_rn(u.x, o.x, acc);
+    acc = __fma_rn(u.y, o.y, acc);
+  });
+  if (publish_block_partial(acc, red, sh)) {
+    const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) ls->alpha[j] = s * sig;
   }
 }
 
-// Elementwise kernels: each thread owns kElems elements spaced by the block size.
+// Elementwise kernels: persistent grid; warp w takes the contiguous range
+// [w T / W, (w+1) T / W) of the T groups of 32 consecutive elements.
 constexpr int kElemThreads = 256;
-constexpr int kElems = 4;
+
+template <typename F>
+__device__ __forceinline__ void for_my_groups(size_t G, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const long long W = warp_count(), w = warp_id();
+  const long long NG = (long long)((G + 31) >> 5);
+  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  for (long long gi = g0; gi < g1; ++gi) {
+    const size_t idx = (size_t)gi * 32 + lane;
+    if (idx < G) f(idx);
+  }
+}
+
+// Up to kUnroll groups of this warp's range are loaded before any of them is
+// used, so their memory latencies overlap.
+constexpr int kUnroll = 4;
 
 // Lanczos iteration j, second half: U_{j+1} = z - alpha_j sigma_j U_j; beta_j = ||U_{j+1}||.
 __global__ void __launch_bounds__(kElemThreads)
@@ -247,21 +287,32 @@ __global__ void __launch_bounds__(kElemThreads)
                      double2 *__restrict__ unext, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kElemThreads / 32 + 1];
   const double c = -ls->alpha[j] * ls->sigma[j];
-  double acc = 0.0;
-  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
+  double acc0 = 0.0, acc1 = 0.0;
+  const int lane = threadIdx.x & 31;
+  const long long W = warp_count(), w = warp_id();
+  const long long NG = (long long)((G + 31) >> 5);
+  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  for (long long gb = g0; gb < g1; gb += kUnroll) {
+    double2 zz[kUnroll], uu[kUnroll];
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    const size_t idx = base + (size_t)e * kElemThreads;
-    if (idx < G) {
-      const double2 zz = z[idx], uu = u[idx];
-      const double2 o = make_double2(__fma_rn(c, uu.x, zz.x), __fma_rn(c, uu.y, zz.y));
-      unext[idx] = o;
-      acc = __fma_rn(o.x, o.x, acc);
-      acc = __fma_rn(o.y, o.y, acc);
+    for (int r = 0; r < kUnroll; ++r) {
+      const size_t idx = (size_t)(gb + r) * 32 + lane;
+      const bool ok = (gb + r < g1) && idx < G;
+      zz[r] = ok ? z[idx] : make_double2(0.0, 0.0);
+      uu[r] = ok ? u[idx] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+      const size_t idx = (size_t)(gb + r) * 32 + lane;
+      if ((gb + r < g1) && idx < G) {
+        const double2 o = make_double2(__fma_rn(c, uu[r].x, zz[r].x), __fma_rn(c, uu[r].y, zz[r].y));
+        unext[idx] = o;
+        acc0 = __fma_rn(o.x, o.x, acc0);
+        acc1 = __fma_rn(o.y, o.y, acc1);
+      }
     }
   }
-  const double b = block_sum(acc, sh);
-  if (publish_partial(b, red, gridDim.x)) {
+  if (publish_block_partial(acc0 + acc1, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
       const double beta = sqrt(s);
@@ -277,19 +328,25 @@ __global__ void __launch_bounds__(kElemThreads)
     norm_kernel(size_t G, const double2 *__restrict__ x, Reduction *red, LanczosScalars *ls,
                 int *status) {
   __shared__ double sh[kElemThreads / 32 + 1];
-  double acc = 0.0;
-  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
+  double acc0 = 0.0, acc1 = 0.0;
+  const int lane = threadIdx.x & 31;
+  const long long W = warp_count(), w = warp_id();
+  const long long NG = (long long)((G + 31) >> 5);
+  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  for (long long gb = g0; gb < g1; gb += kUnroll) {
+    double2 v[kUnroll];
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    const size_t idx = base + (size_t)e * kElemThreads;
-    if (idx < G) {
-      const double2 v = x[idx];
-      acc = __fma_rn(v.x, v.x, acc);
-      acc = __fma_rn(v.y, v.y, acc);
+    for (int r = 0; r < kUnroll; ++r) {
+      const size_t idx = (size_t)(gb + r) * 32 + lane;
+      v[r] = ((gb + r < g1) && idx < G) ? x[idx] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+      acc0 = __fma_rn(v[r].x, v[r].x, acc0);
+      acc1 = __fma_rn(v[r].y, v[r].y, acc1);
     }
   }
-  const double b = block_sum(acc, sh);
-  if (publish_partial(b, red, gridDim.x)) {
+  if (publish_block_partial(acc0 + acc1, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
       red->normsq = s;
@@ -315,35 +372,29 @@ __global__ void __launch_bounds__(kElemThreads)
   __syncthreads();
   const int k = s_k;
   double acc = 0.0;
-  const size_t base = (size_t)blockIdx.x * kElemThreads * kElems + threadIdx.x;
-#pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    const size_t idx = base + (size_t)e * kElemThreads;
-    if (idx < G) {
-      const double2 u0 = psi[idx];
-      double ox = __fma_rn(coef[0].x, u0.x, __dmul_rn(-coef[0].y, u0.y));
-      double oy = __fma_rn(coef[0].x, u0.y, __dmul_rn(coef[0].y, u0.x));
-      for (int jj = 1; jj < k; ++jj) {
-        const double2 u = work[(size_t)(jj - 1) * stride + idx];
-        const double2 c = coef[jj];
-        ox = __fma_rn(c.x, u.x, ox);
-        ox = __fma_rn(-c.y, u.y, ox);
-        oy = __fma_rn(c.x, u.y, oy);
-        oy = __fma_rn(c.y, u.x, oy);
-      }
-      const int jr = (int)(idx % (size_t)N);
-      if (jr >= mask_start) {
-        const double mv = mask[jr];
-        ox = __dmul_rn(mv, ox);
-        oy = __dmul_rn(mv, oy);
-      }
-      psi[idx] = make_double2(ox, oy);
-      acc = __fma_rn(ox, ox, acc);
-      acc = __fma_rn(oy, oy, acc);
+  for_my_groups(G, [&](size_t idx) {
+    const double2 u0 = psi[idx];
+    double ox = __fma_rn(coef[0].x, u0.x, __dmul_rn(-coef[0].y, u0.y));
+    double oy = __fma_rn(coef[0].x, u0.y, __dmul_rn(coef[0].y, u0.x));
+    for (int jj = 1; jj < k; ++jj) {
+      const double2 u = work[(size_t)(jj - 1) * stride + idx];
+      const double2 c = coef[jj];
+      ox = __fma_rn(c.x, u.x, ox);
+      ox = __fma_rn(-c.y, u.y, ox);
+      oy = __fma_rn(c.x, u.y, oy);
+      oy = __fma_rn(c.y, u.x, oy);
     }
-  }
-  const double b = block_sum(acc, sh);
-  if (publish_partial(b, red, gridDim.x)) {
+    const int jr = (int)(idx % (size_t)N);
+    if (jr >= mask_start) {
+      const double mv = mask[jr];
+      ox = __dmul_rn(mv, ox);
+      oy = __dmul_rn(mv, oy);
+    }
+    psi[idx] = make_double2(ox, oy);
+    acc = __fma_rn(ox, ox, acc);
+    acc = __fma_rn(oy, oy, acc);
+  });
+  if (publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
       red->normsq = s;
@@ -451,10 +502,9 @@ StencilIn make_in(const Geometry &g, const OperatorView &op, double E, const dou
   return in;
 }
 
-inline unsigned elem_blocks(size_t G) {
-  const size_t per = (size_t)kElemThreads * kElems;
-  return (unsigned)((G + per - 1) / per);
-}
+// Persistent grids: a few blocks per SM (all resident at once).
+inline unsigned stencil_blocks(const Geometry &g) { return (unsigned)(g.sms * kStencilBlocksPerSM); }
+inline unsigned elem_blocks(const Geometry &g) { return (unsigned)(g.sms * kElemBlocksPerSM); }
 
 }  // namespace
 
@@ -462,7 +512,7 @@ inline unsigned elem_blocks(size_t G) {
 cudaError_t launch_apply_h(const Geometry &g, const OperatorView &op, double E,
                            const double2 *x, double2 *y, cudaStream_t s) {
   const StencilIn in = make_in(g, op, E, x);
-  const dim3 grid = stencil_grid(g.N, g.L);
+  const unsigned grid = stencil_blocks(g);
   if (g.stencil == 5)
     apply_h_kernel<5><<<grid, kBlockJ, 0, s>>>(in, y);
   else
@@ -474,7 +524,7 @@ cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, doubl
                                 const double2 *v_in, const double2 *psi, double2 *v_out,
                                 bool final_stage, cudaStream_t st) {
   const StencilIn in = make_in(g, op, E, v_in);
-  const dim3 grid = stencil_grid(g.N, g.L);
+  const unsigned grid = stencil_blocks(g);
   if (g.stencil == 5)
     taylor_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, op.mask_start,
                                                      final_stage ? 1 : 0);
@@ -492,7 +542,7 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
   static const double a_next[4] = {0.5, 0.5, 1.0, 0.0};
   static const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const StencilIn in = make_in(g, op, E, gin);
-  const dim3 grid = stencil_grid(g.N, g.L);
+  const unsigned grid = stencil_blocks(g);
   const double ca = dt * a_next[stage - 1], cb = dt * b[stage - 1];
   if (g.stencil == 5)
     rk_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next,
@@ -506,7 +556,7 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
 cudaError_t launch_norm(const Geometry &g, const double2 *x, Reduction *red,
                         LanczosScalars *ls, int *status, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  norm_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(G, x, red, ls, status);
+  norm_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, x, red, ls, status);
   return cudaGetLastError();
 }
 
@@ -514,7 +564,7 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
                              const double2 *u, const double2 *uprev, double2 *z,
                              Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const StencilIn in = make_in(g, op, E, u);
-  const dim3 grid = stencil_grid(g.N, g.L);
+  const unsigned grid = stencil_blocks(g);
   if (g.stencil == 5)
     lanczos_a_kernel<5><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
   else
@@ -525,7 +575,7 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
 cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
                              double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  lanczos_b_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(G, j, z, u, unext, red, ls);
+  lanczos_b_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, unext, red, ls);
   return cudaGetLastError();
 }
 
@@ -535,7 +585,7 @@ cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, in
                                    cudaStream_t st) {
   (void)m;
   const size_t G = (size_t)g.N * (g.L + 1);
-  lanczos_combine_kernel<<<elem_blocks(G), kElemThreads, 0, st>>>(
+  lanczos_combine_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(
       G, g.N, psi, work, stride, op.mask, op.mask_start, red, ls, status);
   return cudaGetLastError();
 }

@@ -31,27 +31,43 @@ constexpr int kEx = 256;
 constexpr int KP = kMaxKrylov;
 constexpr int kJacobiSweeps = 12;
 constexpr int kRefineIters = 3;
+// FP32 Jacobi stops once the off-diagonal mass is below this fraction of the
+// total (off-diagonal norm ~3e-6 relative): the FP64 refinement converges
+// quadratically from there (3e-6 -> 1e-11 -> 1e-22).
+constexpr float kJacobiTol = 1e-11f;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ double block_sum_d(double v, double *sh) {
+// FP32 block sum (used only for thresholds: 4-cycle adds instead of 64-cycle FP64).
+__device__ float block_sum_f(float v, float *sh) {
   const int tid = threadIdx.x;
-  v = warp_sum_d(v);
+  v = warp_sum_f(v);
   if ((tid & 31) == 0) sh[tid >> 5] = v;
   __syncthreads();
   if (tid < 32) {
-    double s = (tid < kEx / 32) ? sh[tid] : 0.0;
-    s = warp_sum_d(s);
+    float s = (tid < kEx / 32) ? sh[tid] : 0.f;
+    s = warp_sum_f(s);
     if (tid == 0) sh[kEx / 32] = s;
   }
   __syncthreads();
-  const double r = sh[kEx / 32];
+  const float r = sh[kEx / 32];
   __syncthreads();
   return r;
+}
+
+// a / b for FP64 without the long-latency division: FP32 reciprocal refined by
+// two Newton steps (relative error ~1e-16) when b is inside FP32 range.
+__device__ __forceinline__ double fast_div(double a, double b) {
+  const double ab = fabs(b);
+  if (!(ab > 1e-30 && ab < 1e30)) return a / b;
+  double y = (double)__frcp_rn((float)b);
+  y = y * fma(-b, y, 2.0);
+  y = y * fma(-b, y, 2.0);
+  return a * y;
 }
 
 // Round-robin ("circle") pairing: in round r of an even count n, pair t is
@@ -77,7 +93,7 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
   __shared__ int rp[KP / 2], rq[KP / 2];
   __shared__ double X[KP][KP + 1], W[KP][KP + 1], R[KP][KP + 1], S[KP][KP + 1];
   __shared__ double lam[KP];
-  __shared__ double sh[kEx / 32 + 1];
+  __shared__ float shf[kEx / 32 + 1];
   __shared__ int s_k, s_done;
   const int tid = threadIdx.x;
 
@@ -116,16 +132,16 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
   __syncthreads();
   for (int sweep = 0; sweep < kJacobiSweeps && k > 1; ++sweep) {
     // convergence test on the off-diagonal mass
-    double off = 0.0, tot = 0.0;
+    float off = 0.f, tot = 0.f;
     for (int w = tid; w < k * k; w += kEx) {
       const int i = w / k, j = w % k;
-      const double v = (double)Af[i][j];
+      const float v = Af[i][j];
       tot += v * v;
       if (i != j) off += v * v;
     }
-    off = block_sum_d(off, sh);
-    tot = block_sum_d(tot, sh);
-    if (tid == 0) s_done = (off <= 1e-14 * tot) ? 1 : 0;
+    off = block_sum_f(off, shf);
+    tot = block_sum_f(tot, shf);
+    if (tid == 0) s_done = (off <= kJacobiTol * tot) ? 1 : 0;
     __syncthreads();
     if (s_done) break;
     for (int r = 0; r < n - 1; ++r) {
@@ -183,12 +199,12 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
     const int i = w / k, j = w % k;
     X[i][j] = (double)Vf[i][j];
   }
-  double tnorm2 = 0.0;
+  float tnorm2 = 0.f;
   for (int i = tid; i < k; i += kEx) {
-    tnorm2 += al[i] * al[i];
-    if (i + 1 < k) tnorm2 += 2.0 * be[i] * be[i];
+    tnorm2 += (float)al[i] * (float)al[i];
+    if (i + 1 < k) tnorm2 += 2.f * (float)be[i] * (float)be[i];
   }
-  const double tnorm = sqrt(block_sum_d(tnorm2, sh));   // ||T||_F (also syncs X)
+  const double tnorm = (double)sqrtf(block_sum_f(tnorm2, shf));   // ||T||_F (also syncs X)
   for (int it = 0; it < kRefineIters; ++it) {
     // W = T X
     for (int w = tid; w < k * k; w += kEx) {
@@ -199,44 +215,59 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
       W[i][e] = v;
     }
     __syncthreads();
-    // R = I - X^T X,  S = X^T T X
+    // R = I - X^T X,  S = X^T T X  (two independent FMA chains each, for ILP)
     for (int w = tid; w < k * k; w += kEx) {
       const int a = w / k, b = w % k;
-      double r = 0.0, s = 0.0;
-      for (int i = 0; i < k; ++i) {
-        r = fma(X[i][a], X[i][b], r);
-        s = fma(X[i][a], W[i][b], s);
+      double r0 = 0.0, r1 = 0.0, s0 = 0.0, s1 = 0.0;
+      int i = 0;
+      for (; i + 1 < k; i += 2) {
+        r0 = fma(X[i][a], X[i][b], r0);
+        s0 = fma(X[i][a], W[i][b], s0);
+        r1 = fma(X[i + 1][a], X[i + 1][b], r1);
+        s1 = fma(X[i + 1][a], W[i + 1][b], s1);
       }
-      R[a][b] = ((a == b) ? 1.0 : 0.0) - r;
-      S[a][b] = s;
+      if (i < k) {
+        r0 = fma(X[i][a], X[i][b], r0);
+        s0 = fma(X[i][a], W[i][b], s0);
+      }
+      R[a][b] = ((a == b) ? 1.0 : 0.0) - (r0 + r1);
+      S[a][b] = s0 + s1;
     }
     __syncthreads();
-    if (tid < k) lam[tid] = S[tid][tid] / (1.0 - R[tid][tid]);
+    if (tid < k) lam[tid] = fast_div(S[tid][tid], 1.0 - R[tid][tid]);
     __syncthreads();
-    double sd2 = 0.0, r2 = 0.0;
+    float sd2 = 0.f, r2 = 0.f;
     for (int w = tid; w < k * k; w += kEx) {
       const int a = w / k, b = w % k;
-      const double d = S[a][b] - ((a == b) ? lam[a] : 0.0);
+      const float d = (float)(S[a][b] - ((a == b) ? lam[a] : 0.0));
+      const float rr = (float)R[a][b];
       sd2 += d * d;
-      r2 += R[a][b] * R[a][b];
+      r2 += rr * rr;
     }
-    const double delta = 2.0 * (sqrt(block_sum_d(sd2, sh)) + tnorm * sqrt(block_sum_d(r2, sh)));
+    const float sdn = sqrtf(block_sum_f(sd2, shf));
+    const float rn = sqrtf(block_sum_f(r2, shf));
+    const double delta = 2.0 * ((double)sdn + tnorm * (double)rn);
     // E (stored in W)
     for (int w = tid; w < k * k; w += kEx) {
       const int a = w / k, b = w % k;
       double e;
       const double gap = lam[b] - lam[a];
       if (a == b || fabs(gap) <= delta) e = 0.5 * R[a][b];
-      else e = (S[a][b] + lam[b] * R[a][b]) / gap;
+      else e = fast_div(S[a][b] + lam[b] * R[a][b], gap);
       W[a][b] = e;
     }
     __syncthreads();
     // X <- X + X E   (new X into S, then copy)
     for (int w = tid; w < k * k; w += kEx) {
       const int i = w / k, b = w % k;
-      double v = X[i][b];
-      for (int a = 0; a < k; ++a) v = fma(X[i][a], W[a][b], v);
-      S[i][b] = v;
+      double v0 = X[i][b], v1 = 0.0;
+      int a = 0;
+      for (; a + 1 < k; a += 2) {
+        v0 = fma(X[i][a], W[a][b], v0);
+        v1 = fma(X[i][a + 1], W[a + 1][b], v1);
+      }
+      if (a < k) v0 = fma(X[i][a], W[a][b], v0);
+      S[i][b] = v0 + v1;
     }
     __syncthreads();
     for (int w = tid; w < k * k; w += kEx) {
