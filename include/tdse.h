@@ -58,6 +58,7 @@ typedef enum {
 enum { TDSE_STENCIL_3 = 3, TDSE_STENCIL_5 = 5 };
 enum { TDSE_TAYLOR = 0, TDSE_RK4 = 1, TDSE_LANCZOS = 2 };
 enum { TDSE_GHOST_ZERO = 0, TDSE_GHOST_ODD = 1 };
+enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
 /* largest Krylov dimension tdse_propagate accepts for TDSE_LANCZOS */
 #define TDSE_MAX_KRYLOV 32
 
@@ -67,6 +68,7 @@ typedef struct {
   int absorber;         /* 1: multiply by the cos^(1/8) mask after every step    */
   double absorber_r;    /* mask is 1 for r <= absorber_r and falls to r_N        */
   double r_b;           /* yield radius: yield = 1 - sum_{r_j <= r_b} |f|^2 dr   */
+  int precision;        /* TDSE_FP64 (default) or TDSE_MIXED (see tdse_propagate) */
 } tdse_opts;
 
 /*
@@ -135,6 +137,12 @@ int tdse_set_reference(tdse_t *h, const double *f0_host);
  *                  methods"), field at mid-step; the Krylov space is cut when
  *                  beta_j <= 1e-13 max(1, max|alpha|).
  * The absorber, if on, multiplies the state by the mask after every step.
+ * Precision (tdse_opts.precision): TDSE_FP64 computes everything in FP64.
+ * TDSE_MIXED keeps the state, every update of it, the Lanczos dot products,
+ * norms and the tridiagonal exponential in FP64, and applies H in FP32 to the
+ * FP32 hi/lo split of the state plus complex64 work vectors (Krylov vectors,
+ * Taylor corrections, RK slopes; RK stage sums are compensated two-float
+ * sums), with the radial Laplacian formed from differences.
  * Errors: TDSE_ERR_ARG (dt <= 0, nsteps < 0, order < 1 for Taylor/Lanczos,
  * order > TDSE_MAX_KRYLOV for Lanczos), TDSE_ERR_OOM, TDSE_ERR_CUDA.
  */
@@ -157,7 +165,8 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
 /*
  * y = H(E) x on caller-owned DEVICE buffers (asynchronous on the handle's
  * stream); x and y hold (lmax+1)*N interleaved complex doubles, 16-byte
- * aligned, and must not overlap.  This is the bare operator of Eq. (h_matrix).
+ * aligned, and must not overlap.  This is the bare operator of Eq. (h_matrix),
+ * in FP64, or in the mixed arithmetic when tdse_opts.precision is TDSE_MIXED.
  */
 int tdse_apply_h(tdse_t *h, double E, const void *x_dev, void *y_dev);
 

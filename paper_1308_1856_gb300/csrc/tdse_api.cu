@@ -31,6 +31,16 @@ struct tdse {
   LanczosScalars *ls = nullptr;
   int *status = nullptr;
   double *obs_partials = nullptr, *obs_out = nullptr;
+  // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
+  // a final stage reads one pair with halos while writing the other) and
+  // complex64 work vectors
+  float *diagf = nullptr, *rjf = nullptr, *kappaf = nullptr;
+  float2 *split = nullptr;         // 4 vectors: hi[0], lo[0], hi[1], lo[1]
+  int split_cur = 0;
+  bool split_valid = false;        // split[split_cur] holds the split of psi
+  bool mixed_norm_valid = false;   // sigma_0 / psinorm hold ||psi|| (mixed Lanczos)
+  float2 *mwork = nullptr;
+  size_t mwork_vecs = 0;
   // bookkeeping
   std::string err;
   bool poisoned = false;
@@ -114,6 +124,14 @@ OperatorView view(const tdse *h) {
   return op;
 }
 
+MixedView mview(const tdse *h) {
+  MixedView mv;
+  mv.diag = h->diagf;
+  mv.rj = h->rjf;
+  mv.kappa = h->kappaf;
+  return mv;
+}
+
 // Grid r_j = j*dr + offset (j = 1..N) and the tables of the operator.
 int build_tables(tdse *h) {
   const Geometry &g = h->g;
@@ -148,7 +166,15 @@ int build_tables(tdse *h) {
     }
   }
   h->mask_start = mstart;
+  // FP32 tables of the mixed path: the diagonal without c0 (difference-form Laplacian)
+  std::vector<float> df(d.size()), rf(N), kf(L + 2);
+  for (size_t q = 0; q < d.size(); ++q) df[q] = (float)(d[q] - g.c0);
+  for (int j = 0; j < N; ++j) rf[j] = (float)r[j];
+  for (int l = 0; l <= L + 1; ++l) kf[l] = (float)kap[l];
   cudaStream_t s = h->stream;
+  TDSE_CUDA(h, cudaMemcpyAsync(h->diagf, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice, s), "copy diagf");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->rjf, rf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s), "copy rf");
+  TDSE_CUDA(h, cudaMemcpyAsync(h->kappaf, kf.data(), sizeof(float) * (L + 2), cudaMemcpyHostToDevice, s), "copy kf");
   TDSE_CUDA(h, cudaMemcpyAsync(h->rj, r.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy r");
   TDSE_CUDA(h, cudaMemcpyAsync(h->diag, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice, s), "copy diag");
   TDSE_CUDA(h, cudaMemcpyAsync(h->kappa, kap.data(), sizeof(double) * (L + 2), cudaMemcpyHostToDevice, s), "copy kappa");
@@ -170,6 +196,11 @@ void free_all(tdse *h) {
   cudaFree(h->status);
   cudaFree(h->obs_partials);
   cudaFree(h->obs_out);
+  cudaFree(h->diagf);
+  cudaFree(h->rjf);
+  cudaFree(h->kappaf);
+  cudaFree(h->split);
+  cudaFree(h->mwork);
   for (auto &m : h->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -211,6 +242,140 @@ int check_status_word(tdse *h) {
     TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync status");
     return fail(h, TDSE_ERR_NONFINITE, "state holds Inf/NaN (unstable step size?)");
   }
+  return TDSE_OK;
+}
+
+int ensure_mixed(tdse *h, size_t nvec) {
+  const size_t G = npts(h);
+  if (!h->split) {
+    cudaError_t e = cudaMalloc(&h->split, sizeof(float2) * G * 4);
+    if (e != cudaSuccess) {
+      h->split = nullptr;
+      cudaGetLastError();
+      return fail(h, TDSE_ERR_OOM, "split buffers: " + std::string(cudaGetErrorString(e)));
+    }
+    h->split_valid = false;
+    h->mixed_norm_valid = false;
+  }
+  if (h->mwork_vecs >= nvec) return TDSE_OK;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before realloc");
+  cudaFree(h->mwork);
+  h->mwork = nullptr;
+  h->mwork_vecs = 0;
+  cudaError_t e = cudaMalloc(&h->mwork, sizeof(float2) * G * nvec);
+  if (e != cudaSuccess) {
+    h->mwork = nullptr;
+    cudaGetLastError();
+    return fail(h, TDSE_ERR_OOM, "mixed work vectors: " + std::string(cudaGetErrorString(e)));
+  }
+  h->mwork_vecs = nvec;
+  return TDSE_OK;
+}
+
+float2 *split_hi(tdse *h, int which) { return h->split + (size_t)(2 * which) * npts(h); }
+float2 *split_lo(tdse *h, int which) { return h->split + (size_t)(2 * which + 1) * npts(h); }
+
+// Make split[split_cur] hold psi and, when need_norm, sigma_0 = 1/||psi||.
+int refresh_split(tdse *h, bool need_norm) {
+  if (h->split_valid && (!need_norm || h->mixed_norm_valid)) return TDSE_OK;
+  TDSE_LAUNCH(h, TDSE_K_NORM,
+              launch_mx_split(h->g, h->psi, split_hi(h, h->split_cur), split_lo(h, h->split_cur),
+                              h->red, h->ls, h->status, h->stream),
+              "mixed split");
+  h->split_valid = true;
+  h->mixed_norm_valid = true;
+  return TDSE_OK;
+}
+
+int mx_taylor_steps(tdse *h, int P, double dt, long nsteps) {
+  int rc = ensure_mixed(h, 2);
+  if (rc) return rc;
+  rc = refresh_split(h, false);
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const MixedView mv = mview(h);
+  const size_t G = npts(h);
+  float2 *wb[2] = {h->mwork, h->mwork + G};
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const int cur = h->split_cur, nxt = 1 - cur;
+    const float2 *w_in = nullptr;
+    for (int k = P; k >= 1; --k) {
+      const bool last = (k == 1);
+      float2 *w_out = last ? nullptr : wb[(P - k) & 1];
+      TDSE_LAUNCH(h, TDSE_K_TAYLOR_STAGE,
+                  launch_mx_taylor_stage(h->g, mv, op, E, dt / (double)k, split_hi(h, cur), split_lo(h, cur),
+                                         w_in, w_out, last, h->psi, split_hi(h, nxt), split_lo(h, nxt),
+                                         h->stream),
+                  "mixed taylor stage");
+      w_in = w_out;
+    }
+    h->split_cur = nxt;
+  }
+  // the final stage re-splits psi but does not recompute ||psi||
+  h->mixed_norm_valid = false;
+  return TDSE_OK;
+}
+
+int mx_rk4_steps(tdse *h, double dt, long nsteps) {
+  int rc = ensure_mixed(h, 4);
+  if (rc) return rc;
+  rc = refresh_split(h, false);
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const MixedView mv = mview(h);
+  const size_t G = npts(h);
+  float2 *ka = h->mwork, *kb = h->mwork + G, *ahi = h->mwork + 2 * G, *alo = h->mwork + 3 * G;
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double tn = t0 + (double)n * dt;
+    const double E1 = field_at(h, tn), E2 = field_at(h, tn + 0.5 * dt), E4 = field_at(h, tn + dt);
+    const int cur = h->split_cur, nxt = 1 - cur;
+    float2 *hi = split_hi(h, cur), *lo = split_lo(h, cur);
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E1, 1, dt, hi, lo, nullptr, ka, ahi, alo, h->psi, nullptr, nullptr, h->stream), "mixed rk 1");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E2, 2, dt, hi, lo, ka, kb, ahi, alo, h->psi, nullptr, nullptr, h->stream), "mixed rk 2");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E2, 3, dt, hi, lo, kb, ka, ahi, alo, h->psi, nullptr, nullptr, h->stream), "mixed rk 3");
+    TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E4, 4, dt, hi, lo, ka, nullptr, ahi, alo, h->psi, split_hi(h, nxt), split_lo(h, nxt), h->stream), "mixed rk 4");
+    h->split_cur = nxt;
+  }
+  h->mixed_norm_valid = false;
+  return TDSE_OK;
+}
+
+int mx_lanczos_steps(tdse *h, int m, double dt, long nsteps) {
+  // mixed work: slot 0 z, slots 1..m-1 U_1..U_{m-1} (complex64); U_0 is psi (hi/lo)
+  int rc = ensure_mixed(h, (size_t)(m > 1 ? m : 1));
+  if (rc) return rc;
+  rc = refresh_split(h, true);
+  if (rc) return rc;
+  const OperatorView op = view(h);
+  const MixedView mv = mview(h);
+  const size_t G = npts(h);
+  float2 *z = h->mwork;
+  auto U = [&](int j) -> float2 * { return h->mwork + (size_t)j * G; };   // j >= 1
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    float2 *hi = split_hi(h, h->split_cur), *lo = split_lo(h, h->split_cur);
+    for (int j = 0; j < m; ++j) {
+      TDSE_LAUNCH(h, TDSE_K_LANCZOS_A,
+                  launch_mx_lanczos_a(h->g, mv, E, j, hi, lo, j > 0 ? U(j) : nullptr,
+                                      j > 1 ? U(j - 1) : nullptr, z, h->red, h->ls, h->stream),
+                  "mixed lanczos a");
+      if (j + 1 < m)
+        TDSE_LAUNCH(h, TDSE_K_LANCZOS_B,
+                    launch_mx_lanczos_b(h->g, j, z, j > 0 ? U(j) : nullptr, hi, lo, U(j + 1), h->red, h->ls,
+                                        h->stream),
+                    "mixed lanczos b");
+    }
+    TDSE_LAUNCH(h, TDSE_K_LANCZOS_EXPM, launch_lanczos_expm(m, dt, h->ls, h->stream), "lanczos expm");
+    TDSE_LAUNCH(h, TDSE_K_LANCZOS_COMBINE,
+                launch_mx_lanczos_combine(h->g, op, h->psi, hi, lo, h->mwork + G, G, h->red, h->ls,
+                                          h->status, h->stream),
+                "mixed lanczos combine");
+  }
+  h->mixed_norm_valid = true;   // the combine leaves psi split and sigma_0 current
   return TDSE_OK;
 }
 
@@ -314,10 +479,10 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
     cudaGetLastError();
     return TDSE_ERR_CUDA;
   }
-  // one partial per block of the persistent grids; the final pass reads at most
-  // 16 per thread (128 threads)
-  if ((size_t)sms * kStencilBlocksPerSM > (size_t)16 * 128 ||
-      (size_t)sms * kElemBlocksPerSM > (size_t)16 * 128)
+  // one partial per block of the persistent grids; the final pass of a block
+  // reads at most 16 per thread
+  if ((size_t)sms * kStencilBlocksPerSM > (size_t)16 * kBlockJ ||
+      (size_t)sms * kElemBlocksPerSM > (size_t)16 * kElemThreads)
     return TDSE_ERR_CUDA;
   tdse *h = new (std::nothrow) tdse();
   if (!h) return TDSE_ERR_OOM;
@@ -361,7 +526,10 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
             cudaMalloc(&h->ls, sizeof(LanczosScalars)) == cudaSuccess &&
             cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->obs_partials, sizeof(double) * obs_n) == cudaSuccess &&
-            cudaMalloc(&h->obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess;
+            cudaMalloc(&h->obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess &&
+            cudaMalloc(&h->diagf, sizeof(float) * G) == cudaSuccess &&
+            cudaMalloc(&h->rjf, sizeof(float) * N) == cudaSuccess &&
+            cudaMalloc(&h->kappaf, sizeof(float) * (lmax + 2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(h);
@@ -411,6 +579,8 @@ int tdse_set_options(tdse_t *h, const tdse_opts *o) {
   int rc = check_usable(h);
   if (rc) return rc;
   h->lanczos_norm_valid = false;
+  h->split_valid = false;
+  h->mixed_norm_valid = false;
   if (!o) return fail(h, TDSE_ERR_ARG, "null options");
   if (o->ghost != TDSE_GHOST_ZERO && o->ghost != TDSE_GHOST_ODD)
     return fail(h, TDSE_ERR_ARG, "ghost must be 0 or 1");
@@ -419,6 +589,8 @@ int tdse_set_options(tdse_t *h, const tdse_opts *o) {
   if (o->absorber && !(o->absorber_r >= 0.0 && o->absorber_r < rlast))
     return fail(h, TDSE_ERR_ARG, "absorber radius outside the box");
   if (!std::isfinite(o->r_b)) return fail(h, TDSE_ERR_ARG, "r_b must be finite");
+  if (o->precision != TDSE_FP64 && o->precision != TDSE_MIXED)
+    return fail(h, TDSE_ERR_ARG, "precision must be TDSE_FP64 or TDSE_MIXED");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   h->opts = *o;
   return build_tables(h);
@@ -462,6 +634,8 @@ int tdse_set_state(tdse_t *h, const double *F) {
   int rc = check_usable(h);
   if (rc) return rc;
   h->lanczos_norm_valid = false;
+  h->split_valid = false;
+  h->mixed_norm_valid = false;
   if (!F) return fail(h, TDSE_ERR_ARG, "null state");
   TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyHostToDevice, h->stream), "set state");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync set state");
@@ -481,6 +655,8 @@ int tdse_set_state_device(tdse_t *h, const void *F) {
   int rc = check_usable(h);
   if (rc) return rc;
   h->lanczos_norm_valid = false;
+  h->split_valid = false;
+  h->mixed_norm_valid = false;
   if (!F || ((uintptr_t)F & 15)) return fail(h, TDSE_ERR_ARG, "device state must be 16-byte aligned");
   TDSE_CUDA(h, cudaMemcpyAsync(h->psi, F, sizeof(double2) * npts(h), cudaMemcpyDeviceToDevice, h->stream), "set state");
   return TDSE_OK;
@@ -506,8 +682,37 @@ int tdse_set_reference(tdse_t *h, const double *f0) {
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
   int rc = check_usable(h);
   if (rc) return rc;
-  if (nsteps > 0 && method != TDSE_LANCZOS) h->lanczos_norm_valid = false;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  const bool mixed = h->opts.precision == TDSE_MIXED;
+  if (nsteps > 0) {
+    // each path keeps its own cached norm / split; work in the other one invalidates it
+    if (mixed || method != TDSE_LANCZOS) h->lanczos_norm_valid = false;
+    if (!mixed) {
+      h->split_valid = false;
+      h->mixed_norm_valid = false;
+    }
+  }
+  if (mixed) {
+    switch (method) {
+      case TDSE_TAYLOR:
+        if (order < 1) return fail(h, TDSE_ERR_ARG, "Taylor order must be >= 1");
+        rc = mx_taylor_steps(h, order, dt, nsteps);
+        break;
+      case TDSE_RK4:
+        rc = mx_rk4_steps(h, dt, nsteps);
+        break;
+      case TDSE_LANCZOS:
+        if (order < 1 || order > TDSE_MAX_KRYLOV)
+          return fail(h, TDSE_ERR_ARG, "Krylov dimension must be in 1..TDSE_MAX_KRYLOV");
+        rc = mx_lanczos_steps(h, order, dt, nsteps);
+        break;
+      default:
+        return fail(h, TDSE_ERR_ARG, "unknown method");
+    }
+    if (rc) return rc;
+    h->t += (double)nsteps * dt;
+    return TDSE_OK;
+  }
   switch (method) {
     case TDSE_TAYLOR:
       if (order < 1) return fail(h, TDSE_ERR_ARG, "Taylor order must be >= 1");
@@ -562,6 +767,15 @@ int tdse_apply_h(tdse_t *h, double E, const void *x, void *y) {
   const char *xa = (const char *)x, *ya = (const char *)y;
   if (xa < ya + bytes && ya < xa + bytes) return fail(h, TDSE_ERR_ARG, "x and y overlap");
   if (!std::isfinite(E)) return fail(h, TDSE_ERR_ARG, "non-finite field");
+  if (h->opts.precision == TDSE_MIXED) {
+    rc = ensure_mixed(h, 2);
+    if (rc) return rc;
+    TDSE_LAUNCH(h, TDSE_K_APPLY_H,
+                launch_mx_apply_h(h->g, mview(h), E, (const double2 *)x, h->mwork, h->mwork + npts(h),
+                                  (double2 *)y, h->stream),
+                "mixed apply_h");
+    return TDSE_OK;
+  }
   TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), E, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
   return TDSE_OK;
 }

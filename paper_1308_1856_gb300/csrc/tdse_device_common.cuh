@@ -1,0 +1,88 @@
+// Device helpers shared by the FP64 and mixed-precision kernels: the
+// persistent-grid work split and the deterministic grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tdse_internal.cuh"
+
+namespace tdse_dev {
+namespace common {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed shuffle tree + fixed warp order); the result
+// is valid in every thread.  `sh` needs blockDim/32 + 1 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  v = warp_sum(v);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double s = (tid < (nthreads >> 5)) ? sh[tid] : 0.0;
+    s = warp_sum(s);
+    if (tid == 0) sh[nthreads >> 5] = s;
+  }
+  __syncthreads();
+  const double r = sh[nthreads >> 5];
+  __syncthreads();
+  return r;
+}
+
+// Called by every thread of the last block: fixed-order sum of all partials.
+// Each thread first issues all its loads (independent, so their latencies
+// overlap) and then adds them in index order.
+constexpr int kMaxPartialsPerThread = 16;
+__device__ __forceinline__ double reduce_partials(Reduction *red, unsigned nparts, double *sh) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  __threadfence();
+  double v[kMaxPartialsPerThread];
+#pragma unroll
+  for (int r = 0; r < kMaxPartialsPerThread; ++r) {
+    const unsigned k = tid + (unsigned)r * nthreads;
+    v[r] = (k < nparts) ? __ldcg(&red->partial[k]) : 0.0;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int r = 0; r < kMaxPartialsPerThread; ++r) s += v[r];
+  s = block_sum(s, sh);
+  if (tid == 0) red->ticket = 0u;
+  return s;
+}
+
+// Global warp index and warp count of a 1-D persistent launch.
+__device__ __forceinline__ int warp_id() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+__device__ __forceinline__ int warp_count() { return gridDim.x * (blockDim.x >> 5); }
+
+// Range [s0, s1) of `total` work items owned by warp w of W (balanced to one item).
+__device__ __forceinline__ void warp_range(long long total, long long &s0, long long &s1) {
+  const long long W = warp_count(), w = warp_id();
+  s0 = total * w / W;
+  s1 = total * (w + 1) / W;
+}
+
+// Sum v over the block (fixed shuffle tree and warp order), store it as this
+// block's partial and report whether this block is the last to finish.  The
+// last block then adds all block partials in block order, so the result does
+// not depend on timing.
+__device__ __forceinline__ bool publish_block_partial(double v, Reduction *red, double *sh) {
+  __shared__ unsigned s_last;
+  const double b = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    red->partial[blockIdx.x] = b;
+    __threadfence();
+    const unsigned t = atomicAdd(&red->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+}  // namespace common
+}  // namespace tdse_dev

@@ -20,9 +20,13 @@
 namespace tdse_dev {
 
 constexpr int kMaxKrylov = TDSE_MAX_KRYLOV;
-constexpr int kBlockJ = 128;            // threads per block of the stencil kernels
-constexpr int kStencilBlocksPerSM = 8;  // persistent stencil grid: 8 x 4 warps per SM
-constexpr int kElemBlocksPerSM = 4;     // persistent elementwise grid: 4 x 8 warps per SM
+// Persistent grids use few, large blocks (2 x 16 warps per SM): every block
+// ends with one same-address atomic for the grid reduction, and those
+// serialise in L2, so the block count sets the length of the reduction tail.
+constexpr int kBlockJ = 512;            // threads per block of the stencil kernels
+constexpr int kStencilBlocksPerSM = 2;
+constexpr int kElemThreads = 512;       // threads per block of the elementwise kernels
+constexpr int kElemBlocksPerSM = 2;
 constexpr int kMaxPartials = 16384;     // block partial slots of one grid reduction
 
 // Scalars of one Lanczos step, resident in device memory.
@@ -30,6 +34,8 @@ struct LanczosScalars {
   double alpha[kMaxKrylov];      // alpha_j = <q_j, H q_j>
   double beta[kMaxKrylov];       // beta_j = ||w_j|| (beta[j] links q_j and q_{j+1})
   double sigma[kMaxKrylov + 1];  // sigma_j = 1 / ||U_j||  (U_0 = psi, U_j unnormalised)
+  double ratio[kMaxKrylov + 1];  // ratio_j = sigma_{j-1} / sigma_j  (= beta_{j-1} sigma_{j-1})
+  double acoef[kMaxKrylov];      // -alpha_j sigma_j (coefficient of U_j in U_{j+1})
   double psinorm;                // ||psi|| at the start of the step
   double2 coef[kMaxKrylov];      // psi_new = sum_j coef_j U_j
   int kdim;                      // Krylov dimension kept
@@ -81,6 +87,36 @@ cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, in
                                    double2 *psi, const double2 *work, size_t stride,
                                    Reduction *red, LanczosScalars *ls, int *status,
                                    cudaStream_t st);
+// ---- mixed precision (tdse_kernels_mixed.cu) ------------------------------
+struct MixedView {
+  const float *diag;   // l(l+1)/(2 r^2) + V(r) (+ odd-ghost fold), without c0
+  const float *rj, *kappa;
+};
+
+cudaError_t launch_mx_split(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo,
+                            Reduction *red, LanczosScalars *ls, int *status, cudaStream_t st);
+cudaError_t launch_mx_apply_h(const Geometry &g, const MixedView &mv, double E, const double2 *x,
+                              float2 *tmp_hi, float2 *tmp_lo, double2 *y, cudaStream_t st);
+cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E, int j,
+                                const float2 *hi, const float2 *lo, const float2 *u,
+                                const float2 *uprev, float2 *z, Reduction *red,
+                                LanczosScalars *ls, cudaStream_t st);
+cudaError_t launch_mx_lanczos_b(const Geometry &g, int j, const float2 *z, const float2 *u,
+                                const float2 *hi, const float2 *lo, float2 *unext,
+                                Reduction *red, LanczosScalars *ls, cudaStream_t st);
+cudaError_t launch_mx_lanczos_combine(const Geometry &g, const OperatorView &op, double2 *psi,
+                                      float2 *hi, float2 *lo, const float2 *u1, size_t stride,
+                                      Reduction *red, LanczosScalars *ls, int *status,
+                                      cudaStream_t st);
+cudaError_t launch_mx_taylor_stage(const Geometry &g, const MixedView &mv, const OperatorView &op,
+                                   double E, double s, const float2 *hi, const float2 *lo,
+                                   const float2 *w_in, float2 *w_out, bool final_stage,
+                                   double2 *psi, float2 *hi_out, float2 *lo_out, cudaStream_t st);
+cudaError_t launch_mx_rk_stage(const Geometry &g, const MixedView &mv, const OperatorView &op,
+                               double E, int stage, double dt, const float2 *hi, const float2 *lo,
+                               const float2 *k_in, float2 *k_out, float2 *acc_hi, float2 *acc_lo,
+                               double2 *psi, float2 *hi_out, float2 *lo_out, cudaStream_t st);
+
 cudaError_t launch_observables(const Geometry &g, const OperatorView &op, const double2 *psi,
                                const double2 *ref0, double r_b, double *partials, int nq,
                                double *out, cudaStream_t st);

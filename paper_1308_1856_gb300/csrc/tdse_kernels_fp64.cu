@@ -24,60 +24,16 @@
 // instructions (5-point Taylor stage: 17).
 #include <cuda_runtime.h>
 
+#include "tdse_device_common.cuh"
 #include "tdse_internal.cuh"
 
 namespace tdse_dev {
 
 namespace {
 
+using namespace common;
+
 __device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic block sum (fixed shuffle tree + fixed warp order); the result
-// is valid in every thread.  `sh` needs blockDim/32 + 1 doubles.
-__device__ double block_sum(double v, double *sh) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthreads = blockDim.x * blockDim.y;
-  v = warp_sum(v);
-  if ((tid & 31) == 0) sh[tid >> 5] = v;
-  __syncthreads();
-  if (tid < 32) {
-    double s = (tid < (nthreads >> 5)) ? sh[tid] : 0.0;
-    s = warp_sum(s);
-    if (tid == 0) sh[nthreads >> 5] = s;
-  }
-  __syncthreads();
-  const double r = sh[nthreads >> 5];
-  __syncthreads();
-  return r;
-}
-
-// Called by every thread of the last block: fixed-order sum of all partials.
-// Each thread first issues all its loads (independent, so their latencies
-// overlap) and then adds them in index order.
-constexpr int kMaxPartialsPerThread = 16;
-__device__ double reduce_partials(Reduction *red, unsigned nparts, double *sh) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthreads = blockDim.x * blockDim.y;
-  __threadfence();
-  double v[kMaxPartialsPerThread];
-#pragma unroll
-  for (int r = 0; r < kMaxPartialsPerThread; ++r) {
-    const unsigned k = tid + (unsigned)r * nthreads;
-    v[r] = (k < nparts) ? __ldcg(&red->partial[k]) : 0.0;
-  }
-  double s = 0.0;
-#pragma unroll
-  for (int r = 0; r < kMaxPartialsPerThread; ++r) s += v[r];
-  s = block_sum(s, sh);
-  if (tid == 0) red->ticket = 0u;
-  return s;
-}
 
 struct StencilIn {
   const double2 *__restrict__ x;
@@ -135,10 +91,6 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
   }
 }
 
-// Global warp index and warp count of a 1-D persistent launch.
-__device__ __forceinline__ int warp_id() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
-__device__ __forceinline__ int warp_count() { return gridDim.x * (blockDim.x >> 5); }
-
 // Visit this warp's share of the 32-point row segments (see the file header).
 template <int ST, typename F>
 __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
@@ -160,27 +112,10 @@ __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
   }
 }
 
-// Sum v over the block (fixed shuffle tree and warp order), store it as this
-// block's partial and report whether this block is the last to finish.  The
-// last block then adds all block partials in block order, so the result does
-// not depend on timing.
-__device__ bool publish_block_partial(double v, Reduction *red, double *sh) {
-  __shared__ unsigned s_last;
-  const double b = block_sum(v, sh);
-  if (threadIdx.x == 0) {
-    red->partial[blockIdx.x] = b;
-    __threadfence();
-    const unsigned t = atomicAdd(&red->ticket, 1u);
-    s_last = (t == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
 // ---------------------------------------------------------------------------
 // y = H(E) x
 template <int ST>
-__global__ void __launch_bounds__(kBlockJ) apply_h_kernel(StencilIn in, double2 *__restrict__ y) {
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) apply_h_kernel(StencilIn in, double2 *__restrict__ y) {
   for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
 }
 
@@ -188,7 +123,7 @@ __global__ void __launch_bounds__(kBlockJ) apply_h_kernel(StencilIn in, double2 
 //   v_out = psi + (-i s) H v_in,  s = dt / k.
 // The last stage (k = 1) writes psi itself and applies the absorber mask.
 template <int ST>
-__global__ void __launch_bounds__(kBlockJ)
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
                         int mask_start, int final_stage) {
@@ -208,7 +143,7 @@ __global__ void __launch_bounds__(kBlockJ)
 //   stages 1-3: g_next = psi + (dt a) k,  acc_out = acc_in + (dt b) k  (acc_in = psi at stage 1)
 //   stage 4:    psi    = acc_in + (dt b) k, then the absorber mask.
 template <int ST>
-__global__ void __launch_bounds__(kBlockJ)
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     rk_stage_kernel(StencilIn in, int stage, double ca, double cb,
                     const double2 *__restrict__ psi, const double2 *__restrict__ acc_in,
                     double2 *__restrict__ acc_out, double2 *__restrict__ g_next,
@@ -234,12 +169,12 @@ __global__ void __launch_bounds__(kBlockJ)
 //   beta_{j-1} q_{j-1} = (sigma_{j-1} / sigma_j) U_{j-1},
 //   alpha_j = Re <q_j, z> = sigma_j Re <U_j, z>  (grid reduction; last block stores it).
 template <int ST>
-__global__ void __launch_bounds__(kBlockJ)
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     lanczos_a_kernel(StencilIn in, int j, const double2 *__restrict__ uprev,
                      double2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kBlockJ / 32 + 1];
   const double sig = ls->sigma[j];
-  const double cprev = (j > 0) ? ls->sigma[j - 1] / sig : 0.0;
+  const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
   double acc = 0.0;
   for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2 u) {
     double2 o;
@@ -257,13 +192,15 @@ __global__ void __launch_bounds__(kBlockJ)
   });
   if (publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
-    if (threadIdx.x == 0) ls->alpha[j] = s * sig;
+    if (threadIdx.x == 0) {
+      ls->alpha[j] = s * sig;
+      ls->acoef[j] = -(s * sig) * sig;
+    }
   }
 }
 
 // Elementwise kernels: persistent grid; warp w takes the contiguous range
 // [w T / W, (w+1) T / W) of the T groups of 32 consecutive elements.
-constexpr int kElemThreads = 256;
 
 template <typename F>
 __device__ __forceinline__ void for_my_groups(size_t G, F &&f) {
@@ -282,11 +219,11 @@ __device__ __forceinline__ void for_my_groups(size_t G, F &&f) {
 constexpr int kUnroll = 4;
 
 // Lanczos iteration j, second half: U_{j+1} = z - alpha_j sigma_j U_j; beta_j = ||U_{j+1}||.
-__global__ void __launch_bounds__(kElemThreads)
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     lanczos_b_kernel(size_t G, int j, const double2 *__restrict__ z, const double2 *__restrict__ u,
                      double2 *__restrict__ unext, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kElemThreads / 32 + 1];
-  const double c = -ls->alpha[j] * ls->sigma[j];
+  const double c = ls->acoef[j];
   double acc0 = 0.0, acc1 = 0.0;
   const int lane = threadIdx.x & 31;
   const long long W = warp_count(), w = warp_id();
@@ -317,14 +254,16 @@ __global__ void __launch_bounds__(kElemThreads)
     if (threadIdx.x == 0) {
       const double beta = sqrt(s);
       ls->beta[j] = beta;
-      ls->sigma[j + 1] = (beta > 0.0) ? 1.0 / beta : 0.0;
+      const double sn = (beta > 0.0) ? 1.0 / beta : 0.0;
+      ls->sigma[j + 1] = sn;
+      ls->ratio[j + 1] = (sn > 0.0) ? ls->sigma[j] * beta : 0.0;
     }
   }
 }
 
 // ||x||^2 -> Lanczos start scalars (sigma_0 = 1/||psi||, psinorm) and the
 // non-finite status bit.
-__global__ void __launch_bounds__(kElemThreads)
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     norm_kernel(size_t G, const double2 *__restrict__ x, Reduction *red, LanczosScalars *ls,
                 int *status) {
   __shared__ double sh[kElemThreads / 32 + 1];
@@ -360,7 +299,7 @@ __global__ void __launch_bounds__(kElemThreads)
 
 // psi_new = sum_{j<k} coef_j U_j  (U_0 = psi, read and written in place by
 // the same thread), then the absorber mask and ||psi_new||^2 for the next step.
-__global__ void __launch_bounds__(kElemThreads)
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     lanczos_combine_kernel(size_t G, int N, double2 *psi, const double2 *__restrict__ work,
                            size_t stride, const double *__restrict__ mask, int mask_start,
                            Reduction *red, LanczosScalars *ls, int *status) {
