@@ -46,6 +46,8 @@ ALL_METHODS = [(m, o, dt, p) for p in ("fp64", "mixed")
 METHODS = list(ALL_METHODS)
 HBM_PEAK_GBS = 6783.1       # measured copy bandwidth of this GB300 pool (MEASURED_PEAKS.json)
 METRIC = "grid-point*steps/s"
+BATCH_DT = 0.02            # the batched configuration states no step; that of the at-scale one
+BATCH_ABSORBER = 50.0      # nor an absorber; the same cos^(1/8) mask over the last 50 a.u.
 FP64_FMA_PER_CLK_PER_SM = 2          # measured on GB300 (FP64 FMA throughput probe)
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -168,6 +170,83 @@ def make_handle(stream_ptr: int, precision: str = "fp64"):
     return t
 
 
+class HandleRow:
+    """One single-instance propagator on the at-scale grid."""
+    kind = "single"
+
+    def __init__(self, method, order, dt, prec, stream_ptr, psi0):
+        self.method, self.order, self.dt, self.prec = method, order, dt, prec
+        self.name = f"{method}-{order}/{prec}"
+        self.h = make_handle(stream_ptr, prec)
+        self.h.set_state(psi0)
+        self.h.time = 0.3 * CFG.duration
+        self.gp = CFG.G
+        self.e2e_bytes = (CFG.G * 16, CFG.G * 16 + 8 * (CFG.lmax + 5))
+
+    def step(self):
+        self.h.propagate(self.method, self.order, self.dt, 1)
+
+    # algorithmic grid points processed by each launch of a kernel kind, per step
+    def kernel_points(self, kind):
+        if kind in ("lanczos_a",):
+            return self.order * self.gp
+        if kind == "lanczos_b":
+            return (self.order - 1) * self.gp
+        if kind in ("taylor_stage",):
+            return self.order * self.gp
+        if kind == "rk_stage":
+            return 4 * self.gp
+        return self.gp
+
+    def e2e_step(self, pin_in, pin_out):
+        self.h.set_state_ptr(pin_in[0].data_ptr())
+        self.step()
+        self.h.get_state_ptr(pin_out[0].data_ptr())
+        return self.h.observables()
+
+
+class BatchRow:
+    """The batched configuration: 256 uneven instances (seed 1308), one Lanczos
+    step of every instance per benchmark step."""
+    kind = "batched"
+
+    def __init__(self, prec, stream_ptr, count=256):
+        from paper_1308_1856_gb300 import Batch
+        self.specs = W.batched_specs(count, 1308)
+        self.prec = prec
+        self.name = f"batched-{count}/{prec}"
+        d = [dict(N=x.N, dr=x.dr, lmax=x.lmax, krylov=x.krylov, dt=BATCH_DT, E0=x.E0, omega=x.omega,
+                  ncycles=x.ncycles, absorber_r=x.N * x.dr - BATCH_ABSORBER) for x in self.specs]
+        self.b = Batch(d, stencil=5, precision=prec)
+        self.b.set_stream(stream_ptr)
+        self.gp = self.b.points
+        self.G = [x.N * (x.lmax + 1) for x in self.specs]
+        self.e2e_bytes = (self.gp * 16, self.gp * 16)
+
+    def step(self):
+        self.b.propagate(1)
+
+    def kernel_points(self, kind):
+        m = [x.krylov for x in self.specs]
+        if kind == "lanczos_a":
+            return sum(g * mi for g, mi in zip(self.G, m))
+        if kind == "lanczos_b":
+            return sum(g * (mi - 1) for g, mi in zip(self.G, m))
+        return self.gp
+
+    @property
+    def h(self):
+        return self.b
+
+    def e2e_step(self, pin_in, pin_out):
+        for i in range(len(self.specs)):
+            self.b.set_state_ptr(i, pin_in[i].data_ptr())
+        self.step()
+        for i in range(len(self.specs)):
+            self.b.get_state_ptr(i, pin_out[i].data_ptr())
+        return self.b.observables(0)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -175,21 +254,20 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(dev)              # a real stream (not the legacy default stream)
     torch.cuda.set_stream(stream)
     psi0 = start_state()
-    handles = {}
-    for name, order, dt, prec in METHODS:
-        t = make_handle(stream.cuda_stream, prec)
-        t.set_state(psi0)
-        t.time = 0.3 * CFG.duration
-        handles[(name, prec)] = t
+    rows = []
+    if args.rows in ("all", "single"):
+        rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
+    if args.rows in ("all", "batched"):
+        rows += [BatchRow(p, stream.cuda_stream) for p in ("fp64", "mixed")
+                 if args.precision in ("all", p) and args.method in ("all", "lanczos")]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    G = CFG.G
 
     def one_step(events=None):
-        for idx, (name, order, dt, prec) in enumerate(METHODS):
+        for idx, row in enumerate(rows):
             flush.fill_(float(idx))
             if events is not None:
                 events[idx][0].record(stream)
-            handles[(name, prec)].propagate(name, order, dt, 1)
+            row.step()
             if events is not None:
                 events[idx][1].record(stream)
 
@@ -201,109 +279,116 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
-    launches0 = sum(h.launches for h in handles.values())
+    launches0 = sum(r.h.launches for r in rows)
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-            for _ in METHODS] for _ in range(args.steps)]
+            for _ in rows] for _ in range(args.steps)]
     wall0 = time.perf_counter()
     for k in range(args.steps):
         one_step(evs[k])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    launches = sum(h.launches for h in handles.values()) - launches0
-    per_method_ms = {f"{name}-{order}/{prec}": sum(evs[k][i][0].elapsed_time(evs[k][i][1])
-                                                    for k in range(args.steps))
-                     for i, (name, order, _, prec) in enumerate(METHODS)}
-    total_ms = sum(per_method_ms.values())
+    launches = sum(r.h.launches for r in rows) - launches0
+    row_ms = {r.name: sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps))
+              for i, r in enumerate(rows)}
+    total_ms = sum(row_ms.values())
     if ws > 1:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
         torch.distributed.barrier()
-    for h in handles.values():
-        h.sync()                          # raises on Inf/NaN
+    for r in rows:
+        r.h.sync() if hasattr(r.h, "sync") else r.b.observables(0)   # raises on Inf/NaN
     # ---- per-kernel durations (a separate profiled pass over the same steps) ----
-    for h in handles.values():
-        h.profile(True)
-    for _ in range(max(2, min(args.steps, 5))):
+    for r in rows:
+        r.h.profile(True)
+    prof_steps = 2
+    for _ in range(prof_steps):
         one_step()
-    prof = {}
-    for (mname, prec), h in handles.items():
-        for kname, (ms, n) in h.profile_read().items():
+    prof = {}          # (row kind, precision, kernel) -> [ms, launches, algorithmic points]
+    for r in rows:
+        for kname, (ms, n) in r.h.profile_read().items():
             if n:
-                a, b = prof.get((prec, kname), (0.0, 0))
-                prof[(prec, kname)] = (a + ms, b + n)
-        h.profile(False)
-    kernel_share = {f"{k}/{p}": ms for (p, k), (ms, n) in prof.items()}
-    fp64_kernels = {k: v for k, v in prof.items() if k[0] == "fp64"}
-    roofline = None
-    if fp64_kernels:
-        top = max(fp64_kernels, key=lambda k: fp64_kernels[k][0])
-        top_ms, top_n = prof[top]
-        avg_ms = top_ms / top_n
-        flops = KERNEL_FLOPS_PER_GP.get(top[1], H5_FLOPS) * G
-        achieved = flops / (avg_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": f"{top[1]} (fp64)", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": MEASURED_TRAFFIC.get(top[1]), "flops_per_launch": flops,
-                    "avg_launch_ms": avg_ms,
-                    "peak_source": "FP64: 152 SMs x 2 FMA/clk/SM x 2 flop x 2070 MHz (derived)"}
-    mixed_kernels = {k: v for k, v in prof.items() if k[0] == "mixed" and k[1] in MIXED_BYTES_PER_GP}
-    roofline_mixed = None
-    if mixed_kernels:
-        topm = max(mixed_kernels, key=lambda k: mixed_kernels[k][0])
-        mms, mn = prof[topm]
-        mavg = mms / mn
-        mbytes = MIXED_BYTES_PER_GP[topm[1]] * G
-        mach = mbytes / (mavg * 1e-3) / 1e9
-        roofline_mixed = {"bound": "hbm", "kernel": f"{topm[1]} (mixed)", "achieved": mach,
-                          "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": mach / HBM_PEAK_GBS,
-                          "traffic": None, "bytes_per_launch": mbytes, "avg_launch_ms": mavg,
-                          "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json) of measured"}
+                a = prof.setdefault((r.kind, r.prec, kname), [0.0, 0, 0])
+                a[0] += ms
+                a[1] += n
+                a[2] += prof_steps * r.kernel_points(kname)
+        r.h.profile(False)
+    kernel_share = {f"{k}/{p}/{kind}": v[0] for (kind, p, k), v in prof.items()}
+    tot_k = sum(kernel_share.values())
+
+    def roof_fp64(key):
+        ms, n, pts = prof[key]
+        flops = KERNEL_FLOPS_PER_GP.get(key[2], H5_FLOPS) * pts
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": f"{key[2]} ({key[0]}, fp64)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": MEASURED_TRAFFIC.get(key[2]) if key[0] == "single" else None,
+                "flops_per_launch": flops / n, "avg_launch_ms": ms / n,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk/SM x 2 flop x 2070 MHz (derived)"}
+
+    def roof_mixed(key):
+        ms, n, pts = prof[key]
+        nbytes = MIXED_BYTES_PER_GP[key[2]] * pts
+        achieved = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": f"{key[2]} ({key[0]}, mixed)", "achieved": achieved,
+                "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                "bytes_per_launch": nbytes / n, "avg_launch_ms": ms / n,
+                "peak_source": "HBM copy bandwidth of measured (MEASURED_PEAKS.json)"}
+
+    f64 = [k for k in prof if k[1] == "fp64" and k[2] in KERNEL_FLOPS_PER_GP]
+    mix = [k for k in prof if k[1] == "mixed" and k[2] in MIXED_BYTES_PER_GP]
+    top_all = max(prof, key=lambda k: prof[k][0])
+    roofline = roof_fp64(top_all) if top_all in f64 else (roof_mixed(top_all) if top_all in mix else None)
+    roofline_fp64 = roof_fp64(max(f64, key=lambda k: prof[k][0])) if f64 else None
+    roofline_mixed = roof_mixed(max(mix, key=lambda k: prof[k][0])) if mix else None
     # ---- end-to-end through the C ABI with host buffers ----
-    pinned_in = torch.from_numpy(psi0.view(np.float64).copy()).pin_memory()
-    pinned_out = [torch.empty_like(pinned_in).pin_memory() for _ in METHODS]
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else 2
+    pins = []
+    for r in rows:
+        if r.kind == "single":
+            pin_in = [torch.from_numpy(psi0.view(np.float64).copy()).pin_memory()]
+            pin_out = [torch.empty_like(pin_in[0]).pin_memory()]
+        else:
+            pin_in = [torch.from_numpy(r.b.get_state(i).view(np.float64).copy()).pin_memory()
+                      for i in range(len(r.specs))] if e2e_steps else []
+            pin_out = [torch.empty_like(p).pin_memory() for p in pin_in]
+        pins.append((pin_in, pin_out))
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     obs = None
     for _ in range(e2e_steps):
-        for i, (name, order, dt, prec) in enumerate(METHODS):
-            h = handles[(name, prec)]
-            h.set_state_ptr(pinned_in.data_ptr())
-            h.propagate(name, order, dt, 1)
-            h.get_state_ptr(pinned_out[i].data_ptr())
-            obs = h.observables()
+        for r, (pin_in, pin_out) in zip(rows, pins):
+            obs = r.e2e_step(pin_in, pin_out)
     e2e_s = time.perf_counter() - e0
-    nm = len(METHODS)
-    h2d = nm * G * 16
-    d2h = nm * (G * 16 + 8 * (CFG.lmax + 5))
-    gp_steps = nm * G * args.steps * ws
-    value = gp_steps / (total_ms * 1e-3)
-    e2e_value = nm * G * e2e_steps * ws / e2e_s if e2e_steps else None
+    gp_step = sum(r.gp for r in rows)
+    value = gp_step * args.steps * ws / (total_ms * 1e-3)
+    e2e_value = gp_step * e2e_steps * ws / e2e_s if e2e_steps else None
     result = {
         "metric": METRIC, "value": value, "unit": "grid-point*steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "+".join(sorted({"f64" if p == "fp64" else "f32+f64" for _, _, _, p in METHODS})),
+        "dtype": "+".join(sorted({"f64" if r.prec == "fp64" else "f32+f64" for r in rows})),
         "data": "synthetic",
-        "config": {"workload": "scale: hydrogen N=8000 dr=0.05 lmax=63 5-point, cos^(1/8) mask; "
-                               "one step each of Taylor-12 and RK4 (dt=4e-6) and Lanczos-12 (dt=0.02), "
-                               "in FP64 and in mixed precision",
-                   "grid_points": G, "methods": [f"{m}-{o}/{p}" for m, o, _, p in METHODS],
-                   "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before every timed propagator step"},
-        "methods_ms_per_step": {k: v / args.steps for k, v in per_method_ms.items()},
-        "methods_gp_steps_per_s": {k: G * args.steps / (v * 1e-3) for k, v in per_method_ms.items()},
-        "roofline": roofline if roofline is not None else roofline_mixed,
-        "roofline_mixed": roofline_mixed,
-        "kernel_ms_share": {k: round(ms / sum(kernel_share.values()), 4) for k, ms in kernel_share.items()},
-        "e2e": {"value": e2e_value, "unit": "grid-point*steps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "config": {"workload": "scale (hydrogen N=8000 dr=0.05 lmax=63 5-point, cos^(1/8) mask): one step each of "
+                               "Taylor-12 and RK4 (dt=4e-6) and Lanczos-12 (dt=0.02) in FP64 and mixed; "
+                               "batched: 256 instances (seed 1308, N 2000-16000, dr 0.1, lmax 15-127, "
+                               "Krylov 8-16, dt 0.02), one Lanczos step each, FP64 and mixed",
+                   "grid_points_per_step": gp_step, "rows": [r.name for r in rows],
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "flushed (256 MB write) before every timed row"},
+        "rows_ms_per_step": {k: v / args.steps for k, v in row_ms.items()},
+        "rows_gp_steps_per_s": {r.name: r.gp * args.steps / (row_ms[r.name] * 1e-3) for r in rows},
+        "roofline": roofline, "roofline_fp64": roofline_fp64, "roofline_mixed": roofline_mixed,
+        "kernel_ms_share": {k: round(v / tot_k, 4) for k, v in kernel_share.items()},
+        "e2e": {"value": e2e_value, "unit": "grid-point*steps/s",
+                "h2d_bytes_per_step": sum(r.e2e_bytes[0] for r in rows),
+                "d2h_bytes_per_step": sum(r.e2e_bytes[1] for r in rows), "steps": e2e_steps},
         "gpu_launches": launches, "wall_s": wall, "clocks": clocks,
-        "final_norm_lanczos": obs["norm"] if obs else None,
     }
-    for h in handles.values():
-        h.close()
+    for r in rows:
+        if hasattr(r.h, "close"):
+            r.h.close()
     return result
 
 
@@ -333,7 +418,7 @@ def cpu_oracle_sample(budget_s: float = 12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -342,6 +427,8 @@ def main():
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
                     help="restrict to one precision (profiling runs)")
+    ap.add_argument("--rows", default="all", choices=["all", "single", "batched"],
+                    help="restrict to the single-instance or the batched rows (profiling runs)")
     args = ap.parse_args()
     METHODS[:] = [m for m in ALL_METHODS if (args.method in ("all", m[0]))
                   and (args.precision in ("all", m[3]))]

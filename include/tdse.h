@@ -225,6 +225,68 @@ int tdse_observables_noalloc(int N, double dr, int lmax, double offset, double r
                              const void *psi_dev, const void *ref0_dev, double *out_dev,
                              void *cuda_stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched Lanczos propagation of many independent instances.               */
+/* ------------------------------------------------------------------------ */
+/*
+ * One instance of a batch: its own grid, potential, pulse, absorber, Krylov
+ * dimension and step.  Units and conventions as for a single handle; the
+ * stencil (3 or 5) must be the same for every instance of a batch.
+ */
+typedef struct {
+  int N;                /* radial points                                          */
+  double dr;            /* grid spacing                                           */
+  int lmax;             /* partial waves 0..lmax                                   */
+  double Z;             /* nuclear charge of V(r) = -Z/r                           */
+  double E0, omega, ncycles, cep;   /* sin^2 pulse as in tdse_set_pulse            */
+  int krylov;           /* Lanczos dimension, 1..TDSE_MAX_KRYLOV                   */
+  double dt;            /* step                                                   */
+  double absorber_r;    /* cos^(1/8) mask for r > absorber_r; >= r_N switches it off */
+  double r_b;           /* yield radius                                           */
+} tdse_instance_spec;
+
+typedef struct tdse_batch tdse_batch_t;
+
+/*
+ * Create a batch of `count` instances advanced together by the Lanczos
+ * propagator (Appendix "Lanczos methods"), in FP64 or mixed precision
+ * (TDSE_FP64 / TDSE_MIXED, as for tdse_opts.precision).  Every instance starts
+ * in the normalised 1s state of its grid at t = 0.  Each kernel launch covers
+ * the Lanczos phase of all instances; every reduction is split into fixed
+ * per-instance chunks, so an instance's results do not depend on which other
+ * instances share the batch (bitwise).  All device memory is owned by the
+ * batch.  Errors: TDSE_ERR_ARG (count < 1, an invalid spec, mixed stencils),
+ * TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_batch_create(const tdse_instance_spec *specs, int count, int stencil, int precision,
+                      tdse_batch_t **out);
+int tdse_batch_destroy(tdse_batch_t *b);
+const char *tdse_batch_last_error(const tdse_batch_t *b);
+int tdse_batch_set_stream(tdse_batch_t *b, void *cuda_stream);
+
+/* Per-instance state in / out of HOST memory ((lmax_i+1)*N_i interleaved complex). */
+int tdse_batch_set_state(tdse_batch_t *b, int i, const double *F_host);
+int tdse_batch_get_state(tdse_batch_t *b, int i, double *F_host);
+double tdse_batch_get_time(const tdse_batch_t *b, int i);
+
+/*
+ * Advance every instance by nsteps Lanczos steps of its own dt (asynchronous).
+ * Errors: TDSE_ERR_ARG (nsteps < 0), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_batch_propagate(tdse_batch_t *b, long nsteps);
+
+/* Observables of instance i, as tdse_observables (synchronises the stream). */
+int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
+                           double *yield, double *p_ground);
+
+/* Total grid points of the batch and kernel launches issued (accounting). */
+long long tdse_batch_points(const tdse_batch_t *b);
+long long tdse_batch_launch_count(const tdse_batch_t *b);
+
+/* Per-kernel timing of a batch, as tdse_profile / tdse_profile_read (TDSE_K_* kinds). */
+int tdse_batch_profile(tdse_batch_t *b, int enable);
+int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

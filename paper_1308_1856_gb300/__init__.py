@@ -148,3 +148,97 @@ class TDSE:
             self._check(C.tdse_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
             out[name] = (ms.value, n.value)
         return out
+
+
+class Batch:
+    """Many instances advanced together by the batched Lanczos launches.
+
+    specs: iterable of dicts with keys N, dr, lmax, Z, E0, omega, ncycles, cep,
+    krylov, dt, absorber_r, r_b (see tdse_instance_spec in include/tdse.h)."""
+
+    def __init__(self, specs, stencil: int = 5, precision: str = "fp64"):
+        specs = list(specs)
+        arr = (C.tdse_instance_spec * len(specs))()
+        for k, s in enumerate(specs):
+            arr[k] = C.tdse_instance_spec(int(s["N"]), float(s["dr"]), int(s["lmax"]), float(s.get("Z", 1.0)),
+                                          float(s.get("E0", 0.0)), float(s.get("omega", 0.057)),
+                                          float(s.get("ncycles", 2.0)), float(s.get("cep", 0.0)),
+                                          int(s["krylov"]), float(s["dt"]),
+                                          float(s.get("absorber_r", 1e300)), float(s.get("r_b", 10.0)))
+        self.specs = specs
+        prec = {"fp64": C.TDSE_FP64, "mixed": C.TDSE_MIXED}[precision]
+        h = ctypes.c_void_p()
+        rc = C.tdse_batch_create(arr, len(specs), int(stencil), prec, ctypes.byref(h))
+        if rc != 0:
+            raise TDSEError(rc, "tdse_batch_create failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TDSEError(rc, C.tdse_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            C.tdse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, i):
+        return (int(self.specs[i]["lmax"]) + 1, int(self.specs[i]["N"]))
+
+    def set_stream(self, stream_ptr: int):
+        self._check(C.tdse_batch_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)))
+
+    def set_state(self, i, F):
+        a = np.ascontiguousarray(F, dtype=np.complex128)
+        self._check(C.tdse_batch_set_state(self.h, int(i), ctypes.c_void_p(a.ctypes.data)))
+
+    def get_state(self, i):
+        out = np.empty(self.shape(i), dtype=np.complex128)
+        self._check(C.tdse_batch_get_state(self.h, int(i), ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_state_ptr(self, i, host_ptr: int):
+        self._check(C.tdse_batch_set_state(self.h, int(i), ctypes.c_void_p(host_ptr)))
+
+    def get_state_ptr(self, i, host_ptr: int):
+        self._check(C.tdse_batch_get_state(self.h, int(i), ctypes.c_void_p(host_ptr)))
+
+    def time(self, i):
+        return C.tdse_batch_get_time(self.h, int(i))
+
+    def propagate(self, nsteps: int):
+        self._check(C.tdse_batch_propagate(self.h, int(nsteps)))
+
+    def observables(self, i) -> dict:
+        norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
+        lp = np.zeros(self.shape(i)[0])
+        self._check(C.tdse_batch_observables(self.h, int(i), ctypes.byref(norm), ctypes.c_void_p(lp.ctypes.data),
+                                             ctypes.byref(dip), ctypes.byref(yld), ctypes.byref(pg)))
+        return {"norm": norm.value, "dipole": dip.value, "yield": yld.value, "p_ground": pg.value,
+                "l_pop": lp}
+
+    @property
+    def points(self) -> int:
+        return C.tdse_batch_points(self.h)
+
+    def profile(self, enable: bool):
+        self._check(C.tdse_batch_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(C.KERNEL_KINDS):
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            self._check(C.tdse_batch_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    @property
+    def launches(self) -> int:
+        return C.tdse_batch_launch_count(self.h)

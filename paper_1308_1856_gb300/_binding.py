@@ -34,6 +34,13 @@ class tdse_opts(ctypes.Structure):
                 ("precision", ctypes.c_int)]
 
 
+class tdse_instance_spec(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("dr", ctypes.c_double), ("lmax", ctypes.c_int),
+                ("Z", ctypes.c_double), ("E0", ctypes.c_double), ("omega", ctypes.c_double),
+                ("ncycles", ctypes.c_double), ("cep", ctypes.c_double), ("krylov", ctypes.c_int),
+                ("dt", ctypes.c_double), ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double)]
+
+
 SIGNATURES = {
     "tdse_create": (_c_int, [_c_int, _c_double, _c_int, _c_int, _c_double, _dp,
                              ctypes.POINTER(_vp)]),
@@ -59,6 +66,20 @@ SIGNATURES = {
     "tdse_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "tdse_observables_noalloc": (_c_int, [_c_int, _c_double, _c_int, _c_double, _c_double,
                                           _vp, _vp, _vp, _vp]),
+    "tdse_batch_create": (_c_int, [ctypes.POINTER(tdse_instance_spec), _c_int, _c_int, _c_int,
+                                   ctypes.POINTER(_vp)]),
+    "tdse_batch_destroy": (_c_int, [_vp]),
+    "tdse_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "tdse_batch_set_stream": (_c_int, [_vp, _vp]),
+    "tdse_batch_set_state": (_c_int, [_vp, _c_int, _vp]),
+    "tdse_batch_get_state": (_c_int, [_vp, _c_int, _vp]),
+    "tdse_batch_get_time": (_c_double, [_vp, _c_int]),
+    "tdse_batch_propagate": (_c_int, [_vp, _c_long]),
+    "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
+    "tdse_batch_points": (ctypes.c_longlong, [_vp]),
+    "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
+    "tdse_batch_profile": (_c_int, [_vp, _c_int]),
+    "tdse_batch_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _LIB = None
@@ -119,6 +140,19 @@ tdse_profile = _fn("tdse_profile")
 tdse_profile_read = _fn("tdse_profile_read")
 tdse_observables_noalloc = _fn("tdse_observables_noalloc")
 TDSE_NOALLOC_MAX_LMAX = 255
+tdse_batch_create = _fn("tdse_batch_create")
+tdse_batch_destroy = _fn("tdse_batch_destroy")
+tdse_batch_last_error = _fn("tdse_batch_last_error")
+tdse_batch_set_stream = _fn("tdse_batch_set_stream")
+tdse_batch_set_state = _fn("tdse_batch_set_state")
+tdse_batch_get_state = _fn("tdse_batch_get_state")
+tdse_batch_get_time = _fn("tdse_batch_get_time")
+tdse_batch_propagate = _fn("tdse_batch_propagate")
+tdse_batch_observables = _fn("tdse_batch_observables")
+tdse_batch_points = _fn("tdse_batch_points")
+tdse_batch_launch_count = _fn("tdse_batch_launch_count")
+tdse_batch_profile = _fn("tdse_batch_profile")
+tdse_batch_profile_read = _fn("tdse_batch_profile_read")
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
                 "lanczos_expm", "lanczos_combine", "observables"]

@@ -740,8 +740,10 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
   int rc = check_usable(h);
   if (rc) return rc;
   const int L = h->g.L;
-  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES, launch_observables(h->g, view(h), h->psi, h->ref0, h->opts.r_b, h->obs_partials, 5,
-                                    h->obs_out, h->stream),
+  unsigned *ticket = reinterpret_cast<unsigned *>(h->obs_partials + (size_t)5 * observables_blocks(h->g) * (L + 1));
+  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+              launch_observables(h->g, view(h), h->psi, h->ref0, h->opts.r_b, h->obs_partials, ticket,
+                                 h->obs_out, h->stream),
               "observables");
   std::vector<double> out(L + 5);
   TDSE_CUDA(h, cudaMemcpyAsync(out.data(), h->obs_out, sizeof(double) * (L + 5), cudaMemcpyDeviceToHost, h->stream),

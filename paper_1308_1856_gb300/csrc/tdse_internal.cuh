@@ -83,6 +83,8 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
 cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
                              double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st);
+cudaError_t launch_lanczos_expm_batched(int count, const int *m, const double *dt,
+                                        LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,
                                    double2 *psi, const double2 *work, size_t stride,
                                    Reduction *red, LanczosScalars *ls, int *status,
@@ -117,9 +119,11 @@ cudaError_t launch_mx_rk_stage(const Geometry &g, const MixedView &mv, const Ope
                                const float2 *k_in, float2 *k_out, float2 *acc_hi, float2 *acc_lo,
                                double2 *psi, float2 *hi_out, float2 *lo_out, cudaStream_t st);
 
+// partials: 5 * observables_blocks(g) * (L+1) doubles; ticket: a zeroed
+// counter at a fixed address of the caller (left zeroed on return).
 cudaError_t launch_observables(const Geometry &g, const OperatorView &op, const double2 *psi,
-                               const double2 *ref0, double r_b, double *partials, int nq,
-                               double *out, cudaStream_t st);
+                               const double2 *ref0, double r_b, double *partials,
+                               unsigned *ticket, double *out, cudaStream_t st);
 int observables_blocks(const Geometry &g);
 
 }  // namespace tdse_dev

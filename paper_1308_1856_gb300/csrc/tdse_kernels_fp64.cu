@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "tdse_device_common.cuh"
+#include "tdse_stencil.cuh"
 #include "tdse_internal.cuh"
 
 namespace tdse_dev {
@@ -32,64 +33,7 @@ namespace tdse_dev {
 namespace {
 
 using namespace common;
-
-__device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
-
-struct StencilIn {
-  const double2 *__restrict__ x;
-  const double *__restrict__ diag;
-  const double *__restrict__ rj;
-  const double *__restrict__ kappa;
-  int N, L;
-  double c1, c2, E;
-};
-
-// (H x) at (l, i) from the register window; 15 FP64 instructions (5-point).
-template <int ST>
-__device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *row, int i,
-                                           double d, double2 prev, double2 cur, double2 next,
-                                           double a_cur, double a_next) {
-  const double2 z = make_double2(0.0, 0.0);
-  const double2 m1 = (i >= 1) ? ldg2(row + i - 1) : z;
-  const double2 p1 = (i + 1 < in.N) ? ldg2(row + i + 1) : z;
-  double tx = __dmul_rn(d, cur.x);
-  double ty = __dmul_rn(d, cur.y);
-  tx = __fma_rn(in.c1, __dadd_rn(m1.x, p1.x), tx);
-  ty = __fma_rn(in.c1, __dadd_rn(m1.y, p1.y), ty);
-  if (ST == 5) {
-    const double2 m2 = (i >= 2) ? ldg2(row + i - 2) : z;
-    const double2 p2 = (i + 2 < in.N) ? ldg2(row + i + 2) : z;
-    tx = __fma_rn(in.c2, __dadd_rn(m2.x, p2.x), tx);
-    ty = __fma_rn(in.c2, __dadd_rn(m2.y, p2.y), ty);
-  }
-  tx = __fma_rn(a_cur, prev.x, tx);
-  ty = __fma_rn(a_cur, prev.y, ty);
-  tx = __fma_rn(a_next, next.x, tx);
-  ty = __fma_rn(a_next, next.y, ty);
-  return make_double2(tx, ty);
-}
-
-// Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).
-template <int ST, typename F>
-__device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
-  const int N = in.N, L = in.L;
-  const double2 z = make_double2(0.0, 0.0);
-  const double Er = __dmul_rn(in.E, in.rj[i]);
-  double2 prev = (l0 > 0) ? ldg2(in.x + (size_t)(l0 - 1) * N + i) : z;
-  double2 cur = ldg2(in.x + (size_t)l0 * N + i);
-  double a_cur = __dmul_rn(in.kappa[l0], Er);
-  for (int l = l0; l < l1; ++l) {
-    const size_t idx = (size_t)l * N + i;
-    const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
-    const double a_next = __dmul_rn(in.kappa[l + 1], Er);
-    const double d = __ldg(in.diag + idx);
-    const double2 t = h_point<ST>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
-    f(i, idx, t, cur);
-    prev = cur;
-    cur = next;
-    a_cur = a_next;
-  }
-}
+using namespace stencil;
 
 // Visit this warp's share of the 32-point row segments (see the file header).
 template <int ST, typename F>
@@ -535,13 +479,10 @@ int observables_blocks(const Geometry &g) {
 }
 
 cudaError_t launch_observables(const Geometry &g, const OperatorView &op, const double2 *psi,
-                               const double2 *ref0, double r_b, double *partials, int nq,
-                               double *out, cudaStream_t st) {
-  (void)nq;
+                               const double2 *ref0, double r_b, double *partials,
+                               unsigned *ticket, double *out, cudaStream_t st) {
   const int nbx = observables_blocks(g);
   const dim3 grid(nbx, g.L + 1);
-  // partials: kObsQ * nbx * (L+1) doubles followed by one unsigned ticket
-  unsigned *ticket = reinterpret_cast<unsigned *>(partials + (size_t)kObsQ * nbx * (g.L + 1));
   observables_kernel<<<grid, kObsThreads, 0, st>>>(psi, ref0, op.rj, op.kappa, g.N, g.L, g.dr,
                                                    r_b, partials, ticket, out);
   return cudaGetLastError();

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "tdse_device_common.cuh"
+#include "tdse_stencil.cuh"
 #include "tdse_internal.cuh"
 
 namespace tdse_dev {
@@ -29,82 +30,13 @@ namespace tdse_dev {
 namespace {
 
 using namespace common;
-
-struct MixedIn {
-  const float2 *__restrict__ hi;   // split of psi (may be null)
-  const float2 *__restrict__ lo;
-  const float2 *__restrict__ w;    // FP32 work vector (may be null)
-  float ws;                        // scale of w in the operand
-  const float *__restrict__ diag;  // l(l+1)/(2 r^2) + V(r) (+ odd-ghost fold), no c0
-  const float *__restrict__ rj;
-  const float *__restrict__ kappa;
-  int N, L;
-  float c1, c2, E;
-};
-
-// Parts of the operand at one index.
-template <bool S, bool Wp>
-struct Parts {
-  float2 h, l, w;
-};
-
-template <bool S, bool Wp>
-__device__ __forceinline__ Parts<S, Wp> load_parts(const MixedIn &in, size_t idx, bool ok) {
-  Parts<S, Wp> p;
-  const float2 z = make_float2(0.f, 0.f);
-  p.h = z;
-  p.l = z;
-  p.w = z;
-  if (ok) {
-    if (S) {
-      p.h = __ldg(in.hi + idx);
-      p.l = __ldg(in.lo + idx);
-    }
-    if (Wp) p.w = __ldg(in.w + idx);
-  }
-  return p;
-}
-
-template <bool S, bool Wp>
-__device__ __forceinline__ float2 value(const Parts<S, Wp> &p, float ws) {
-  float2 v = make_float2(0.f, 0.f);
-  if (S) {
-    v.x = p.l.x;
-    v.y = p.l.y;
-  }
-  if (Wp) {
-    v.x = fmaf(ws, p.w.x, v.x);
-    v.y = fmaf(ws, p.w.y, v.y);
-  }
-  if (S) {
-    v.x += p.h.x;
-    v.y += p.h.y;
-  }
-  return v;
-}
-
-// a - c, part by part.
-template <bool S, bool Wp>
-__device__ __forceinline__ float2 diff(const Parts<S, Wp> &a, const Parts<S, Wp> &c, float ws) {
-  float2 d = make_float2(0.f, 0.f);
-  if (Wp) {
-    d.x = ws * (a.w.x - c.w.x);
-    d.y = ws * (a.w.y - c.w.y);
-  }
-  if (S) {
-    d.x += (a.l.x - c.l.x);
-    d.y += (a.l.y - c.l.y);
-    d.x += (a.h.x - c.h.x);
-    d.y += (a.h.y - c.h.y);
-  }
-  return d;
-}
+using namespace stencil;
 
 // Walk this warp's row segments; f(i, idx, Hx, x_center) per point.
 template <int ST, bool S, bool Wp, typename F>
 __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
   const int lane = threadIdx.x & 31;
-  const int N = in.N, L = in.L, Lp1 = L + 1;
+  const int N = in.N, Lp1 = in.L + 1;
   const long long NJ = (N + 31) >> 5;
   long long s, s_end;
   warp_range(NJ * Lp1, s, s_end);
@@ -114,49 +46,9 @@ __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
     const int i = jg * 32 + lane;
-    if (i < N) {
-      const float Er = in.E * in.rj[i];
-      Parts<S, Wp> prev = load_parts<S, Wp>(in, (size_t)(l0 - 1) * N + i, l0 > 0);
-      Parts<S, Wp> cur = load_parts<S, Wp>(in, (size_t)l0 * N + i, true);
-      float a_cur = in.kappa[l0] * Er;
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * N + i;
-        const Parts<S, Wp> next = load_parts<S, Wp>(in, idx + N, l < L);
-        const float a_next = in.kappa[l + 1] * Er;
-        const Parts<S, Wp> m1 = load_parts<S, Wp>(in, idx - 1, i >= 1);
-        const Parts<S, Wp> p1 = load_parts<S, Wp>(in, idx + 1, i + 1 < N);
-        const float2 d1m = diff(m1, cur, in.ws), d1p = diff(p1, cur, in.ws);
-        const float2 vc = value(cur, in.ws), vp = value(prev, in.ws), vn = value(next, in.ws);
-        const float dg = __ldg(in.diag + idx);
-        float tx = in.c1 * (d1m.x + d1p.x);
-        float ty = in.c1 * (d1m.y + d1p.y);
-        if (ST == 5) {
-          const Parts<S, Wp> m2 = load_parts<S, Wp>(in, idx - 2, i >= 2);
-          const Parts<S, Wp> p2 = load_parts<S, Wp>(in, idx + 2, i + 2 < N);
-          const float2 d2m = diff(m2, cur, in.ws), d2p = diff(p2, cur, in.ws);
-          tx = fmaf(in.c2, d2m.x + d2p.x, tx);
-          ty = fmaf(in.c2, d2m.y + d2p.y, ty);
-        }
-        tx = fmaf(dg, vc.x, tx);
-        ty = fmaf(dg, vc.y, ty);
-        tx = fmaf(a_cur, vp.x, tx);
-        ty = fmaf(a_cur, vp.y, ty);
-        tx = fmaf(a_next, vn.x, tx);
-        ty = fmaf(a_next, vn.y, ty);
-        f(i, idx, make_float2(tx, ty), vc);
-        prev = cur;
-        cur = next;
-        a_cur = a_next;
-      }
-    }
+    if (i < N) mixed_walk_rows<ST, S, Wp>(in, i, l0, l1, f);
     s += l1 - l0;
   }
-}
-
-// Split an FP64 value into hi + lo (two FP32 parts).
-__device__ __forceinline__ void split2(double2 v, float2 &h, float2 &lo) {
-  h = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-  lo = make_float2(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y));
 }
 
 // ---------------------------------------------------------------------------

@@ -78,7 +78,7 @@ __device__ __forceinline__ void pair_of(int r, int t, int n, int &p, int &q) {
 
 // Thread mappings below use a row stride of 32 (w >> 5, w & 31) so that no
 // loop needs a runtime integer division.
-__global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, LanczosScalars *ls) {
+__device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls) {
   __shared__ double al[KP], be[KP];
   __shared__ float Af[KP][KP + 1];
   __shared__ float Vf[KP][KP + 1];
@@ -351,8 +351,25 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
   }
 }
 
+__global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, LanczosScalars *ls) {
+  expm_body(m, dt, ls);
+}
+
+// One block per instance of a batch.
+__global__ void __launch_bounds__(kEx)
+    lanczos_expm_batched_kernel(const int *__restrict__ m, const double *__restrict__ dt,
+                                LanczosScalars *ls) {
+  expm_body(m[blockIdx.x], dt[blockIdx.x], ls + blockIdx.x);
+}
+
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st) {
   lanczos_expm_kernel<<<1, kEx, 0, st>>>(m, dt, ls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_expm_batched(int count, const int *m, const double *dt,
+                                        LanczosScalars *ls, cudaStream_t st) {
+  lanczos_expm_batched_kernel<<<count, kEx, 0, st>>>(m, dt, ls);
   return cudaGetLastError();
 }
 
