@@ -473,6 +473,8 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
   if (N < 1 || lmax < 0 || !(dr > 0.0) || (stencil != 3 && stencil != 5) || !std::isfinite(Z))
     return TDSE_ERR_ARG;
   const size_t G = (size_t)N * (lmax + 1);
+  // work splits and point indices use 32-bit arithmetic in the kernels
+  if (G >= ((size_t)1 << 31)) return TDSE_ERR_ARG;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {

@@ -125,7 +125,7 @@ __device__ __forceinline__ void chunk_columns(const BatchInst &I, int ci, F &&f)
   }
 }
 
-// Warp w of W takes global chunks [T w / W, T (w+1) / W) of the list.
+// Each warp takes a balanced, contiguous range of the list's chunks (warp_range).
 template <typename F>
 __device__ __forceinline__ void for_my_chunks(const ChunkList &cl, F &&f) {
   long long c0, c1;

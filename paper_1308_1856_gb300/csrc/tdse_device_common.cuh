@@ -60,11 +60,16 @@ __device__ __forceinline__ double reduce_partials(Reduction *red, unsigned npart
 __device__ __forceinline__ int warp_id() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
 __device__ __forceinline__ int warp_count() { return gridDim.x * (blockDim.x >> 5); }
 
-// Range [s0, s1) of `total` work items owned by warp w of W (balanced to one item).
+// Range [s0, s1) of `total` (< 2^32) work items owned by warp w of the W warps:
+// q = total / W items each, one more for the first total - q W warps.  Only a
+// 32-bit division: a 64-bit integer division compiles to FP64 arithmetic,
+// which issues at 1/64 of the FP32 rate on this part.
 __device__ __forceinline__ void warp_range(long long total, long long &s0, long long &s1) {
-  const long long W = warp_count(), w = warp_id();
-  s0 = total * w / W;
-  s1 = total * (w + 1) / W;
+  const unsigned W = (unsigned)warp_count(), w = (unsigned)warp_id();
+  const unsigned T = (unsigned)total;
+  const unsigned q = T / W, r = T - q * W;
+  s0 = (long long)w * q + (w < r ? w : r);
+  s1 = s0 + q + (w < r ? 1u : 0u);
 }
 
 // Sum v over the block (fixed shuffle tree and warp order), store it as this

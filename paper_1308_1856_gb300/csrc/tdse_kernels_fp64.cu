@@ -9,8 +9,8 @@
 //
 // Work decomposition: the grid is persistent (a few blocks per SM) and the
 // (L+1) x N points are cut into segments of 32 consecutive radial points of
-// one partial wave, ordered radial-group-major.  Warp w takes the contiguous
-// range [w T / W, (w+1) T / W) of the T segments, so every warp gets the same
+// one partial wave, ordered radial-group-major.  Warp w takes a contiguous,
+// balanced range of the T segments (warp_range), so every warp gets the same
 // amount of work to within one segment and the assignment (hence every
 // reduction order) is fixed.  Inside a range a lane owns one radial index j
 // and walks l upwards keeping x_{l-1,j}, x_{l,j}, x_{l+1,j} in registers, so
@@ -39,14 +39,12 @@ using namespace stencil;
 template <int ST, typename F>
 __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
   const int lane = threadIdx.x & 31;
-  const long long W = warp_count(), w = warp_id();
   const int Lp1 = in.L + 1;
   const long long NJ = (in.N + 31) >> 5;
-  const long long total = NJ * Lp1;
-  long long s = total * w / W;
-  const long long s_end = total * (w + 1) / W;
+  long long s, s_end;
+  warp_range(NJ * Lp1, s, s_end);
   while (s < s_end) {
-    const int jg = (int)(s / Lp1);
+    const int jg = (int)((unsigned)s / (unsigned)Lp1);
     const int l0 = (int)(s - (long long)jg * Lp1);
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
@@ -143,15 +141,14 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   }
 }
 
-// Elementwise kernels: persistent grid; warp w takes the contiguous range
-// [w T / W, (w+1) T / W) of the T groups of 32 consecutive elements.
+// Elementwise kernels: persistent grid; each warp takes a contiguous, balanced
+// range of the groups of 32 consecutive elements (warp_range).
 
 template <typename F>
 __device__ __forceinline__ void for_my_groups(size_t G, F &&f) {
   const int lane = threadIdx.x & 31;
-  const long long W = warp_count(), w = warp_id();
-  const long long NG = (long long)((G + 31) >> 5);
-  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  long long g0, g1;
+  warp_range((long long)((G + 31) >> 5), g0, g1);
   for (long long gi = g0; gi < g1; ++gi) {
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) f(idx);
@@ -170,9 +167,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   const double c = ls->acoef[j];
   double acc0 = 0.0, acc1 = 0.0;
   const int lane = threadIdx.x & 31;
-  const long long W = warp_count(), w = warp_id();
-  const long long NG = (long long)((G + 31) >> 5);
-  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  long long g0, g1;
+  warp_range((long long)((G + 31) >> 5), g0, g1);
   for (long long gb = g0; gb < g1; gb += kUnroll) {
     double2 zz[kUnroll], uu[kUnroll];
 #pragma unroll
@@ -213,9 +209,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   __shared__ double sh[kElemThreads / 32 + 1];
   double acc0 = 0.0, acc1 = 0.0;
   const int lane = threadIdx.x & 31;
-  const long long W = warp_count(), w = warp_id();
-  const long long NG = (long long)((G + 31) >> 5);
-  const long long g0 = NG * w / W, g1 = NG * (w + 1) / W;
+  long long g0, g1;
+  warp_range((long long)((G + 31) >> 5), g0, g1);
   for (long long gb = g0; gb < g1; gb += kUnroll) {
     double2 v[kUnroll];
 #pragma unroll
@@ -267,7 +262,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       oy = __fma_rn(c.x, u.y, oy);
       oy = __fma_rn(c.y, u.x, oy);
     }
-    const int jr = (int)(idx % (size_t)N);
+    const int jr = (int)((unsigned)idx % (unsigned)N);
     if (jr >= mask_start) {
       const double mv = mask[jr];
       ox = __dmul_rn(mv, ox);

@@ -41,7 +41,7 @@ __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
   long long s, s_end;
   warp_range(NJ * Lp1, s, s_end);
   while (s < s_end) {
-    const int jg = (int)(s / Lp1);
+    const int jg = (int)((unsigned)s / (unsigned)Lp1);
     const int l0 = (int)(s - (long long)jg * Lp1);
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       const double2 p = psi[idx];
       double ox = fma(c0.x, p.x, fma(-c0.y, p.y, (double)cx));
       double oy = fma(c0.x, p.y, fma(c0.y, p.x, (double)cy));
-      const int jr = (int)(idx % (size_t)N);
+      const int jr = (int)((unsigned)idx % (unsigned)N);
       if (jr >= mask_start) {
         const double mv = mask[jr];
         ox *= mv;
