@@ -247,6 +247,74 @@ class BatchRow:
         return self.b.observables(0)
 
 
+def batched_request_spec(x, dt=BATCH_DT):
+    return dict(N=x.N, dr=x.dr, lmax=x.lmax, krylov=x.krylov, dt=dt, E0=x.E0, omega=x.omega,
+                ncycles=x.ncycles, absorber_r=x.N * x.dr - BATCH_ABSORBER)
+
+
+def serve_trace(stream_ptr, precision, rate, count, horizon, kbatch, budget, seed):
+    """Continuous batching of a finite Poisson trace through the server: each
+    request is one instance of the batched configuration (seeded draws) run for
+    `horizon` Lanczos steps from t = 0; the loop admits what has arrived and
+    fits, runs one step batch of `kbatch` steps over every running request,
+    waits for it, and retires what finished.  Time-to-completion = the end of
+    the step batch in which a request took its last step minus its arrival."""
+    from paper_1308_1856_gb300 import Server
+    specs = [batched_request_spec(x) for x in W.batched_specs(count, seed)]
+    arrivals = W.poisson_arrivals(count, rate, seed + 1)
+    srv = Server(budget, max_resident=count, stencil=5, precision=precision)
+    srv.set_stream(stream_ptr)
+    st0 = srv.stats()
+    arrived, lat, resident_peak, batches = {}, [], 0, 0
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(lat) < count:
+        now = time.perf_counter() - t0
+        while nxt < count and arrivals[nxt] <= now:
+            arrived[srv.submit(specs[nxt], horizon)] = arrivals[nxt]
+            nxt += 1
+        st = srv.stats()
+        if st["running"] == 0 and st["queued"] == 0:
+            time.sleep(max(0.0, arrivals[nxt] - now))
+            continue
+        srv.step(kbatch)
+        srv.sync()
+        batches += 1
+        done = time.perf_counter() - t0
+        resident_peak = max(resident_peak, srv.stats()["resident"])
+        for rid in srv.poll():
+            lat.append(done - arrived.pop(rid))
+            srv.observables(rid)                 # the result a client reads (raises on Inf/NaN)
+            srv.release(rid)
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"rate_req_per_s": rate, "requests": count, "horizon_steps": horizon, "step_batch": kbatch,
+            "precision": precision, "hbm_budget_bytes": budget,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": makespan,
+            "gp_steps_per_s": (st["gp_steps"] - st0["gp_steps"]) / makespan,
+            "resident_peak": resident_peak, "step_batches": batches,
+            "gpu_launches": st["launches"] - st0["launches"]}
+
+
+def run_served(args, stream_ptr):
+    """Config 'served': an overloaded trace (mean 50 req/s) and one at a rate
+    the GPU sustains, both through the same server."""
+    budget = int(args.serve_budget_gb * (1 << 30))
+    out = {"workload": "served: Poisson arrivals, specs drawn as in the batched configuration "
+                       f"(seed {args.serve_seed}), each request {args.serve_horizon} Lanczos steps "
+                       f"(dt {BATCH_DT}) from t = 0, step batches of {args.serve_batch}, HBM budget "
+                       f"{args.serve_budget_gb:g} GB, FIFO admission"}
+    for name, rate, count in (("overload", args.serve_rate, args.serve_requests),
+                              ("sustained", args.serve_sustained_rate, args.serve_sustained_requests)):
+        if count > 0:
+            out[name] = serve_trace(stream_ptr, args.serve_precision, rate, count, args.serve_horizon,
+                                    args.serve_batch, budget, args.serve_seed)
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -255,6 +323,8 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_stream(stream)
     psi0 = start_state()
     rows = []
+    if args.rows == "served":
+        return {"metric": METRIC, "served": run_served(args, stream.cuda_stream)}
     if args.rows in ("all", "single"):
         rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
     if args.rows in ("all", "batched"):
@@ -389,6 +459,8 @@ def run_ours(args, ws, rank, local):
     for r in rows:
         if hasattr(r.h, "close"):
             r.h.close()
+    if args.rows == "all" and not args.no_serve:
+        result["served"] = run_served(args, stream.cuda_stream)
     return result
 
 
@@ -427,8 +499,18 @@ def main():
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
                     help="restrict to one precision (profiling runs)")
-    ap.add_argument("--rows", default="all", choices=["all", "single", "batched"],
-                    help="restrict to the single-instance or the batched rows (profiling runs)")
+    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served"],
+                    help="restrict to the single-instance, batched or served rows")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served traces")
+    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="overloaded trace: mean req/s")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-sustained-rate", type=float, default=2.0)
+    ap.add_argument("--serve-sustained-requests", type=int, default=32)
+    ap.add_argument("--serve-horizon", type=int, default=500, help="Lanczos steps per request")
+    ap.add_argument("--serve-batch", type=int, default=100, help="steps per step batch")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-seed", type=int, default=1309)
     args = ap.parse_args()
     METHODS[:] = [m for m in ALL_METHODS if (args.method in ("all", m[0]))
                   and (args.precision in ("all", m[3]))]

@@ -287,6 +287,79 @@ long long tdse_batch_launch_count(const tdse_batch_t *b);
 int tdse_batch_profile(tdse_batch_t *b, int enable);
 int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches);
 
+/* ------------------------------------------------------------------------ */
+/* Served instances: continuous batching under a device-memory budget.       */
+/* ------------------------------------------------------------------------ */
+/*
+ * A request is one tdse_instance_spec plus a number of Lanczos steps from
+ * t = 0 (the normalised 1s state of its grid), propagated as in the batch.
+ * The paper has no serving layer; the server schedules many such requests
+ * on one GPU:
+ *   - tdse_server_create takes the whole budget at once (one device
+ *     allocation of hbm_budget bytes, the arena) and at most max_resident
+ *     requests resident (admitted and not yet released) at a time;
+ *   - submitted requests wait in a FIFO queue; tdse_server_step first admits
+ *     the head of the queue while a slot is free and the arena has a
+ *     contiguous range for it (nothing overtakes the head), then advances
+ *     every running request by min(k, steps left) steps, one launch per
+ *     Lanczos phase over all of them (asynchronous on the server's stream);
+ *   - a finished request keeps its state resident for readout until
+ *     tdse_server_release, which also cancels a queued or running request.
+ * A request's results are bitwise the same whatever else runs beside it and
+ * however its steps are split into step batches.
+ * Errors: TDSE_ERR_ARG (bad arguments, an invalid spec, a spec larger than the
+ * budget, an unknown or non-resident id), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+typedef struct tdse_server tdse_server_t;
+
+/* Device bytes one request of this spec occupies in the arena (0 if invalid). */
+unsigned long long tdse_server_instance_bytes(const tdse_instance_spec *spec, int precision);
+
+int tdse_server_create(unsigned long long hbm_budget, int max_resident, int stencil, int precision,
+                       tdse_server_t **out);
+int tdse_server_destroy(tdse_server_t *s);
+const char *tdse_server_last_error(const tdse_server_t *s);
+int tdse_server_set_stream(tdse_server_t *s, void *cuda_stream);
+
+/* Queue a request of nsteps >= 1 steps; *id receives its id (> 0). */
+int tdse_server_submit(tdse_server_t *s, const tdse_instance_spec *spec, long nsteps, long long *id);
+
+/* Admit what fits, then advance all running requests by up to k >= 1 steps
+ * (asynchronous); *finished (may be NULL) = requests that took their last
+ * step in this call. */
+int tdse_server_step(tdse_server_t *s, long k, int *finished);
+
+/* Wait for every step enqueued so far. */
+int tdse_server_sync(tdse_server_t *s);
+
+/* Ids of finished requests not reported before, oldest first: at most cap of
+ * them into ids[], their number into *n; the rest are reported next time. */
+int tdse_server_poll(tdse_server_t *s, long long *ids, int cap, int *n);
+
+/* State of a request: 0 queued, 1 running, 2 finished; steps enqueued / asked. */
+int tdse_server_status(const tdse_server_t *s, long long id, int *state, long *steps_done,
+                       long *steps_total);
+
+/* Observables / state of a resident request, as tdse_batch_* (synchronise). */
+int tdse_server_observables(tdse_server_t *s, long long id, double *norm, double *l_pop,
+                            double *dipole, double *yield, double *p_ground);
+int tdse_server_get_state(tdse_server_t *s, long long id, double *F_host);
+
+/* Drop a request (queued, running or finished) and free its slot and memory. */
+int tdse_server_release(tdse_server_t *s, long long id);
+
+typedef struct {
+  long long queued, running, resident, finished_total;
+  unsigned long long bytes_budget, bytes_in_use, largest_free;
+  long long gp_steps;   /* grid-point steps enqueued since creation */
+  long long launches;   /* kernel launches issued since creation */
+} tdse_server_stats_t;
+int tdse_server_stats(const tdse_server_t *s, tdse_server_stats_t *st);
+
+/* Per-kernel timing, as tdse_profile / tdse_profile_read. */
+int tdse_server_profile(tdse_server_t *s, int enable);
+int tdse_server_profile_read(tdse_server_t *s, int kind, double *total_ms, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -150,6 +150,14 @@ class TDSE:
         return out
 
 
+def _spec_struct(s) -> "C.tdse_instance_spec":
+    return C.tdse_instance_spec(int(s["N"]), float(s["dr"]), int(s["lmax"]), float(s.get("Z", 1.0)),
+                                float(s.get("E0", 0.0)), float(s.get("omega", 0.057)),
+                                float(s.get("ncycles", 2.0)), float(s.get("cep", 0.0)),
+                                int(s["krylov"]), float(s["dt"]),
+                                float(s.get("absorber_r", 1e300)), float(s.get("r_b", 10.0)))
+
+
 class Batch:
     """Many instances advanced together by the batched Lanczos launches.
 
@@ -160,11 +168,7 @@ class Batch:
         specs = list(specs)
         arr = (C.tdse_instance_spec * len(specs))()
         for k, s in enumerate(specs):
-            arr[k] = C.tdse_instance_spec(int(s["N"]), float(s["dr"]), int(s["lmax"]), float(s.get("Z", 1.0)),
-                                          float(s.get("E0", 0.0)), float(s.get("omega", 0.057)),
-                                          float(s.get("ncycles", 2.0)), float(s.get("cep", 0.0)),
-                                          int(s["krylov"]), float(s["dt"]),
-                                          float(s.get("absorber_r", 1e300)), float(s.get("r_b", 10.0)))
+            arr[k] = _spec_struct(s)
         self.specs = specs
         prec = {"fp64": C.TDSE_FP64, "mixed": C.TDSE_MIXED}[precision]
         h = ctypes.c_void_p()
@@ -242,3 +246,108 @@ class Batch:
     @property
     def launches(self) -> int:
         return C.tdse_batch_launch_count(self.h)
+
+
+class Server:
+    """Continuous batching of Lanczos requests under a device-memory budget
+    (tdse_server_* in include/tdse.h): submit(spec, nsteps) queues a request,
+    step(k) admits what fits and advances every running request by up to k
+    steps, poll() lists finished requests, release(id) frees one."""
+
+    QUEUED, RUNNING, FINISHED = 0, 1, 2
+
+    def __init__(self, hbm_budget: int, max_resident: int = 1024, stencil: int = 5,
+                 precision: str = "fp64"):
+        self.precision = precision
+        self.max_resident = int(max_resident)
+        self._prec = {"fp64": C.TDSE_FP64, "mixed": C.TDSE_MIXED}[precision]
+        h = ctypes.c_void_p()
+        rc = C.tdse_server_create(int(hbm_budget), int(max_resident), int(stencil), self._prec,
+                                  ctypes.byref(h))
+        if rc != 0:
+            raise TDSEError(rc, "tdse_server_create failed")
+        self.h = h
+        self._shape = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TDSEError(rc, C.tdse_server_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            C.tdse_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def instance_bytes(self, spec) -> int:
+        return int(C.tdse_server_instance_bytes(ctypes.byref(_spec_struct(spec)), self._prec))
+
+    def set_stream(self, stream_ptr: int):
+        self._check(C.tdse_server_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)))
+
+    def submit(self, spec, nsteps: int) -> int:
+        rid = ctypes.c_longlong()
+        self._check(C.tdse_server_submit(self.h, ctypes.byref(_spec_struct(spec)), int(nsteps),
+                                         ctypes.byref(rid)))
+        self._shape[rid.value] = (int(spec["lmax"]) + 1, int(spec["N"]))
+        return rid.value
+
+    def step(self, k: int) -> int:
+        fin = ctypes.c_int()
+        self._check(C.tdse_server_step(self.h, int(k), ctypes.byref(fin)))
+        return fin.value
+
+    def sync(self):
+        self._check(C.tdse_server_sync(self.h))
+
+    def poll(self, cap: int = 4096) -> list:
+        ids = (ctypes.c_longlong * cap)()
+        n = ctypes.c_int()
+        self._check(C.tdse_server_poll(self.h, ids, cap, ctypes.byref(n)))
+        return [ids[i] for i in range(n.value)]
+
+    def status(self, rid: int):
+        st, done, total = ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
+        self._check(C.tdse_server_status(self.h, int(rid), ctypes.byref(st), ctypes.byref(done),
+                                         ctypes.byref(total)))
+        return st.value, done.value, total.value
+
+    def observables(self, rid: int) -> dict:
+        norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
+        lp = np.zeros(self._shape[rid][0])
+        self._check(C.tdse_server_observables(self.h, int(rid), ctypes.byref(norm),
+                                              ctypes.c_void_p(lp.ctypes.data), ctypes.byref(dip),
+                                              ctypes.byref(yld), ctypes.byref(pg)))
+        return {"norm": norm.value, "dipole": dip.value, "yield": yld.value, "p_ground": pg.value,
+                "l_pop": lp}
+
+    def get_state(self, rid: int):
+        out = np.empty(self._shape[rid], dtype=np.complex128)
+        self._check(C.tdse_server_get_state(self.h, int(rid), ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def release(self, rid: int):
+        self._check(C.tdse_server_release(self.h, int(rid)))
+        self._shape.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = C.tdse_server_stats_t()
+        self._check(C.tdse_server_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def profile(self, enable: bool):
+        self._check(C.tdse_server_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(C.KERNEL_KINDS):
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            self._check(C.tdse_server_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out

@@ -41,6 +41,18 @@ class tdse_instance_spec(ctypes.Structure):
                 ("dt", ctypes.c_double), ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double)]
 
 
+class tdse_server_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_longlong), ("running", ctypes.c_longlong),
+                ("resident", ctypes.c_longlong), ("finished_total", ctypes.c_longlong),
+                ("bytes_budget", ctypes.c_ulonglong), ("bytes_in_use", ctypes.c_ulonglong),
+                ("largest_free", ctypes.c_ulonglong), ("gp_steps", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong)]
+
+
+_llp = ctypes.POINTER(ctypes.c_longlong)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_long)
+
 SIGNATURES = {
     "tdse_create": (_c_int, [_c_int, _c_double, _c_int, _c_int, _c_double, _dp,
                              ctypes.POINTER(_vp)]),
@@ -80,6 +92,22 @@ SIGNATURES = {
     "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_batch_profile": (_c_int, [_vp, _c_int]),
     "tdse_batch_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "tdse_server_instance_bytes": (ctypes.c_ulonglong, [ctypes.POINTER(tdse_instance_spec), _c_int]),
+    "tdse_server_create": (_c_int, [ctypes.c_ulonglong, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)]),
+    "tdse_server_destroy": (_c_int, [_vp]),
+    "tdse_server_last_error": (ctypes.c_char_p, [_vp]),
+    "tdse_server_set_stream": (_c_int, [_vp, _vp]),
+    "tdse_server_submit": (_c_int, [_vp, ctypes.POINTER(tdse_instance_spec), _c_long, _llp]),
+    "tdse_server_step": (_c_int, [_vp, _c_long, _ip]),
+    "tdse_server_sync": (_c_int, [_vp]),
+    "tdse_server_poll": (_c_int, [_vp, _llp, _c_int, _ip]),
+    "tdse_server_status": (_c_int, [_vp, ctypes.c_longlong, _ip, _lp, _lp]),
+    "tdse_server_observables": (_c_int, [_vp, ctypes.c_longlong, _dp, _vp, _dp, _dp, _dp]),
+    "tdse_server_get_state": (_c_int, [_vp, ctypes.c_longlong, _vp]),
+    "tdse_server_release": (_c_int, [_vp, ctypes.c_longlong]),
+    "tdse_server_stats": (_c_int, [_vp, ctypes.POINTER(tdse_server_stats_t)]),
+    "tdse_server_profile": (_c_int, [_vp, _c_int]),
+    "tdse_server_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _LIB = None
@@ -153,6 +181,22 @@ tdse_batch_points = _fn("tdse_batch_points")
 tdse_batch_launch_count = _fn("tdse_batch_launch_count")
 tdse_batch_profile = _fn("tdse_batch_profile")
 tdse_batch_profile_read = _fn("tdse_batch_profile_read")
+tdse_server_instance_bytes = _fn("tdse_server_instance_bytes")
+tdse_server_create = _fn("tdse_server_create")
+tdse_server_destroy = _fn("tdse_server_destroy")
+tdse_server_last_error = _fn("tdse_server_last_error")
+tdse_server_set_stream = _fn("tdse_server_set_stream")
+tdse_server_submit = _fn("tdse_server_submit")
+tdse_server_step = _fn("tdse_server_step")
+tdse_server_sync = _fn("tdse_server_sync")
+tdse_server_poll = _fn("tdse_server_poll")
+tdse_server_status = _fn("tdse_server_status")
+tdse_server_observables = _fn("tdse_server_observables")
+tdse_server_get_state = _fn("tdse_server_get_state")
+tdse_server_release = _fn("tdse_server_release")
+tdse_server_stats = _fn("tdse_server_stats")
+tdse_server_profile = _fn("tdse_server_profile")
+tdse_server_profile_read = _fn("tdse_server_profile_read")
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
                 "lanczos_expm", "lanczos_combine", "observables"]

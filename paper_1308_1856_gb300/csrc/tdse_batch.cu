@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "tdse_device_common.cuh"
+#include "tdse_engine.h"
 #include "tdse_internal.cuh"
 #include "tdse_stencil.cuh"
 
@@ -39,37 +40,17 @@ using namespace stencil;
 
 constexpr int kChunkSegs = 64;   // 32-point row segments per reduction chunk
 
-struct BatchInst {
-  int N, L, m;
-  int mask_start;        // first radial index with mask != 1 (N if none)
-  long long off;         // first point of the instance in psi / diag / split / z
-  long long woff;        // first point of its Krylov area (slot j at woff + j*G)
-  int roff;              // first entry in the per-r tables (rj, mask)
-  int koff;              // first entry in the kappa table
-  int nseg;              // 32-point row segments
-  int nchunk;            // reduction chunks
-  int cbase;             // first chunk partial slot
-  int pad;
-  double c1, c2;         // stencil coefficients (c0 is folded into diag)
-};
-
+// Per-launch view of the engine's device state.
 struct BatchDev {
   const BatchInst *inst;
-  const double *diag, *rj, *kappa, *mask;
-  const float *diagf, *rjf, *kappaf;
-  double2 *psi;
-  double2 *work;         // FP64 Krylov area: slot 0 = z, slots 1..m-1 = U_j
-  float2 *hi, *lo;       // mixed: split of psi
-  float2 *mwork;         // mixed Krylov area
   LanczosScalars *ls;
-  double *partial;       // chunk partial slots
-  unsigned *ticket;      // per-instance arrival counters
+  unsigned *ticket;      // per-slot arrival counters (zero between launches)
   int *status;
-  const double *E;       // field of every instance at this step's mid-point
+  const double *E;       // field of every slot at this step's mid-point
 };
 
 struct ChunkList {
-  const int *act;        // active instances (ids)
+  const int *act;        // active slots
   const int *cpre;       // prefix sums of their chunk counts (nact + 1)
   int nact, total;
 };
@@ -93,7 +74,7 @@ __device__ __forceinline__ bool chunk_done(const BatchDev &B, const BatchInst &I
   v = warp_sum(v);
   unsigned last = 0;
   if ((threadIdx.x & 31) == 0) {
-    B.partial[I.cbase + ci] = v;
+    I.partial[ci] = v;
     __threadfence();
     last = (atomicAdd(&B.ticket[inst], 1u) == (unsigned)(I.nchunk - 1)) ? 1u : 0u;
   }
@@ -101,7 +82,7 @@ __device__ __forceinline__ bool chunk_done(const BatchDev &B, const BatchInst &I
   if (!last) return false;
   __threadfence();
   double s = 0.0;
-  for (int c = threadIdx.x & 31; c < I.nchunk; c += 32) s += __ldcg(&B.partial[I.cbase + c]);
+  for (int c = threadIdx.x & 31; c < I.nchunk; c += 32) s += __ldcg(&I.partial[c]);
   total = warp_sum(s);
   if ((threadIdx.x & 31) == 0) B.ticket[inst] = 0u;
   return true;
@@ -143,9 +124,9 @@ __device__ __forceinline__ StencilIn fp64_in(const BatchDev &B, const BatchInst 
                                              const double2 *x) {
   StencilIn in;
   in.x = x;
-  in.diag = B.diag + I.off;
-  in.rj = B.rj + I.roff;
-  in.kappa = B.kappa + I.koff;
+  in.diag = I.diag;
+  in.rj = I.rj;
+  in.kappa = I.kappa;
   in.N = I.N;
   in.L = I.L;
   in.c1 = I.c1;
@@ -161,9 +142,9 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    const double2 *u = (j == 0) ? B.psi + I.off : B.work + I.woff + (long long)j * G;
-    const double2 *up = (j <= 1) ? B.psi + I.off : B.work + I.woff + (long long)(j - 1) * G;
-    double2 *z = B.work + I.woff;
+    const double2 *u = (j == 0) ? I.psi : I.work + (long long)j * G;
+    const double2 *up = (j <= 1) ? I.psi : I.work + (long long)(j - 1) * G;
+    double2 *z = I.work;
     const double sig = ls->sigma[j];
     const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
     const StencilIn in = fp64_in(B, I, inst, u);
@@ -199,9 +180,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    const double2 *u = (j == 0) ? B.psi + I.off : B.work + I.woff + (long long)j * G;
-    const double2 *z = B.work + I.woff;
-    double2 *un = B.work + I.woff + (long long)(j + 1) * G;
+    const double2 *u = (j == 0) ? I.psi : I.work + (long long)j * G;
+    const double2 *z = I.work;
+    double2 *un = I.work + (long long)(j + 1) * G;
     const double c = ls->acoef[j];
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
@@ -230,7 +211,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_norm_fp64(BatchDev B, ChunkList cl) {
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
-    const double2 *x = B.psi + I.off;
+    const double2 *x = I.psi;
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
       for (int l = l0; l < l1; ++l) {
@@ -257,9 +238,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    double2 *psi = B.psi + I.off;
-    const double2 *U1 = B.work + I.woff + G;
-    const double *mask = B.mask + I.roff;
+    double2 *psi = I.psi;
+    const double2 *U1 = I.work + G;
+    const double *mask = I.mask;
     const int k = ls->kdim;
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
@@ -305,9 +286,9 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   in.lo = lo;
   in.w = w;
   in.ws = 1.f;
-  in.diag = B.diagf + I.off;
-  in.rj = B.rjf + I.roff;
-  in.kappa = B.kappaf + I.koff;
+  in.diag = I.diagf;
+  in.rj = I.rjf;
+  in.kappa = I.kappaf;
   in.N = I.N;
   in.L = I.L;
   in.c1 = (float)I.c1;
@@ -323,9 +304,9 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    const float2 *hi = B.hi + I.off, *lo = B.lo + I.off;
-    float2 *z = B.mwork + I.woff;
-    const float2 *uprev = (j >= 2) ? B.mwork + I.woff + (long long)(j - 1) * G : nullptr;
+    const float2 *hi = I.hi, *lo = I.lo;
+    float2 *z = I.mwork;
+    const float2 *uprev = (j >= 2) ? I.mwork + (long long)(j - 1) * G : nullptr;
     const double sigd = ls->sigma[j];
     const float sig = (float)sigd;
     const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
@@ -357,7 +338,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       const MixedIn in = mixed_in(B, I, inst, hi, lo, nullptr);
       chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false>(in, i, l0, l1, epi); });
     } else {
-      const MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, B.mwork + I.woff + (long long)j * G);
+      const MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
       chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true>(in, i, l0, l1, epi); });
     }
     accd += (double)acc;
@@ -375,10 +356,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    const float2 *u = (j == 0) ? nullptr : B.mwork + I.woff + (long long)j * G;
-    const float2 *hi = B.hi + I.off, *lo = B.lo + I.off;
-    const float2 *z = B.mwork + I.woff;
-    float2 *un = B.mwork + I.woff + (long long)(j + 1) * G;
+    const float2 *u = (j == 0) ? nullptr : I.mwork + (long long)j * G;
+    const float2 *hi = I.hi, *lo = I.lo;
+    const float2 *z = I.mwork;
+    float2 *un = I.mwork + (long long)(j + 1) * G;
     const float c = (float)ls->acoef[j];
     float acc = 0.f;
     double accd = 0.0;
@@ -421,8 +402,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_split_mixed(BatchDev B, ChunkList cl) {
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
-    const double2 *x = B.psi + I.off;
-    float2 *hi = B.hi + I.off, *lo = B.lo + I.off;
+    const double2 *x = I.psi;
+    float2 *hi = I.hi, *lo = I.lo;
     float acc = 0.f;
     double accd = 0.0;
     int cnt = 0;
@@ -461,10 +442,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    double2 *psi = B.psi + I.off;
-    float2 *hi = B.hi + I.off, *lo = B.lo + I.off;
-    const float2 *U1 = B.mwork + I.woff + G;
-    const double *mask = B.mask + I.roff;
+    double2 *psi = I.psi;
+    float2 *hi = I.hi, *lo = I.lo;
+    const float2 *U1 = I.mwork + G;
+    const double *mask = I.mask;
     const int k = ls->kdim;
     const double2 c0 = ls->coef[0];
     float acc = 0.f;
@@ -519,97 +500,50 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 }  // namespace
 }  // namespace tdse_dev
 
-// ===========================================================================
-// Host side
-// ===========================================================================
-using namespace tdse_dev;
 
-struct tdse_batch {
-  int count = 0, stencil = 5, precision = TDSE_FP64;
-  std::vector<tdse_instance_spec> spec;
-  std::vector<BatchInst> hinst;
-  std::vector<double> t;             // time of every instance
-  long long npts = 0, nwork = 0;
-  int nchunks = 0, max_m = 0, sms = 0;
-  cudaStream_t own_stream = nullptr, stream = nullptr;
-  // device
-  BatchInst *inst = nullptr;
-  double *diag = nullptr, *rj = nullptr, *kappa = nullptr, *mask = nullptr;
-  float *diagf = nullptr, *rjf = nullptr, *kappaf = nullptr;
-  double2 *psi = nullptr, *work = nullptr;
-  float2 *split = nullptr, *mwork = nullptr;
-  LanczosScalars *ls = nullptr;
-  double *partial = nullptr;
-  unsigned *ticket = nullptr;
-  int *status = nullptr;
-  int *act = nullptr, *cpre = nullptr;   // active lists of every phase, flattened
-  int *m_dev = nullptr;
-  double *dt_dev = nullptr, *E_dev = nullptr;
-  long long E_cap = 0;
-  std::vector<int> act_off, act_n, act_total;   // per phase j (0..max_m)
-  double *obs_partials = nullptr, *obs_out = nullptr, *obs_rj = nullptr, *obs_kappa = nullptr;
-  double2 *ref0 = nullptr;
-  bool norm_valid = false;
-  long long launches = 0;
-  std::string err;
-  bool poisoned = false;
-  // per-kernel timing (tdse_batch_profile)
-  bool profiling = false;
-  struct Mark { int kind; cudaEvent_t a, b; };
-  std::vector<Mark> marks;
-  size_t nmarks = 0;
-  double prof_ms[TDSE_K_COUNT] = {0};
-  long long prof_n[TDSE_K_COUNT] = {0};
-};
-
+// ===========================================================================
+// Host side: the engine
+// ===========================================================================
+namespace tdse_dev {
 namespace {
 
-int bfail(tdse_batch *b, int code, const std::string &msg) {
-  if (b) {
-    b->err = msg;
-    if (code == TDSE_ERR_CUDA) b->poisoned = true;
-  }
-  return code;
-}
+constexpr size_t kAlign = 256;
 
-#define BT_CUDA(b, call, what)                                                        \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) return bfail(b, TDSE_ERR_CUDA, std::string(what) + ": " + \
-                                                              cudaGetErrorString(e_)); \
-  } while (0)
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// Start event of a profiled launch; returns the stop event to record after it.
-cudaEvent_t bprof_begin(tdse_batch *b, int kind) {
-  if (!b->profiling) return nullptr;
-  if (b->nmarks == b->marks.size()) {
-    tdse_batch::Mark m;
-    if (cudaEventCreate(&m.a) != cudaSuccess || cudaEventCreate(&m.b) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    b->marks.push_back(m);
-  }
-  tdse_batch::Mark &m = b->marks[b->nmarks++];
-  m.kind = kind;
-  cudaEventRecord(m.a, b->stream);
-  return m.b;
-}
+struct Layout {
+  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, ref0, total;
+};
 
-void bprof_end(tdse_batch *b, cudaEvent_t e) {
-  if (e) cudaEventRecord(e, b->stream);
-}
-
-int bprof_collect(tdse_batch *b) {
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync profile");
-  for (size_t i = 0; i < b->nmarks; ++i) {
-    float ms = 0.f;
-    BT_CUDA(b, cudaEventElapsedTime(&ms, b->marks[i].a, b->marks[i].b), "event time");
-    b->prof_ms[b->marks[i].kind] += ms;
-    b->prof_n[b->marks[i].kind] += 1;
-  }
-  b->nmarks = 0;
-  return TDSE_OK;
+Layout layout_of(const tdse_instance_spec &s, int precision) {
+  const size_t N = (size_t)s.N, Lp1 = (size_t)s.lmax + 1, G = N * Lp1, m = (size_t)s.krylov;
+  const size_t nseg = ((N + 31) / 32) * Lp1;
+  const size_t nchunk = (nseg + kChunkSegs - 1) / kChunkSegs;
+  const bool mixed = precision == TDSE_MIXED;
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += align_up(bytes);
+    return at;
+  };
+  const size_t none = ~(size_t)0;
+  L.psi = take(16 * G);
+  L.diag = mixed ? none : take(8 * G);
+  L.work = mixed ? none : take(16 * G * m);
+  L.diagf = mixed ? take(4 * G) : none;
+  L.hi = mixed ? take(8 * G) : none;
+  L.lo = mixed ? take(8 * G) : none;
+  L.mwork = mixed ? take(8 * G * m) : none;
+  L.rj = take(8 * N);
+  L.mask = take(8 * N);
+  L.kappa = take(8 * (Lp1 + 1));
+  L.rjf = mixed ? take(4 * N) : none;
+  L.kappaf = mixed ? take(4 * (Lp1 + 1)) : none;
+  L.partial = take(8 * nchunk);
+  L.ref0 = take(16 * N);
+  L.total = off;
+  return L;
 }
 
 double pulse_at(const tdse_instance_spec &s, double t) {
@@ -620,81 +554,544 @@ double pulse_at(const tdse_instance_spec &s, double t) {
   return s.E0 * env * env * std::sin(s.omega * t + s.cep);
 }
 
-void bfree(tdse_batch *b) {
-  cudaFree(b->inst);
-  cudaFree(b->diag);
-  cudaFree(b->rj);
-  cudaFree(b->kappa);
-  cudaFree(b->mask);
-  cudaFree(b->diagf);
-  cudaFree(b->rjf);
-  cudaFree(b->kappaf);
-  cudaFree(b->psi);
-  cudaFree(b->work);
-  cudaFree(b->split);
-  cudaFree(b->mwork);
-  cudaFree(b->ls);
-  cudaFree(b->partial);
-  cudaFree(b->ticket);
-  cudaFree(b->status);
-  cudaFree(b->act);
-  cudaFree(b->cpre);
-  cudaFree(b->m_dev);
-  cudaFree(b->dt_dev);
-  cudaFree(b->E_dev);
-  cudaFree(b->obs_partials);
-  cudaFree(b->obs_out);
-  cudaFree(b->ref0);
-  for (auto &m : b->marks) {
-    cudaEventDestroy(m.a);
-    cudaEventDestroy(m.b);
-  }
-  if (b->own_stream) cudaStreamDestroy(b->own_stream);
-}
-
-BatchDev dev_view(const tdse_batch *b) {
-  BatchDev B;
-  B.inst = b->inst;
-  B.diag = b->diag;
-  B.rj = b->rj;
-  B.kappa = b->kappa;
-  B.mask = b->mask;
-  B.diagf = b->diagf;
-  B.rjf = b->rjf;
-  B.kappaf = b->kappaf;
-  B.psi = b->psi;
-  B.work = b->work;
-  B.hi = b->split;
-  B.lo = b->split ? b->split + b->npts : nullptr;
-  B.mwork = b->mwork;
-  B.ls = b->ls;
-  B.partial = b->partial;
-  B.ticket = b->ticket;
-  B.status = b->status;
-  B.E = b->E_dev;
-  return B;
-}
-
-ChunkList chunk_list(const tdse_batch *b, int j) {
+ChunkList list_at(const int *base, int off, int nact, int total) {
   ChunkList cl;
-  cl.act = b->act + b->act_off[j];
-  cl.cpre = b->cpre + b->act_off[j] + j;   // prefix arrays have nact + 1 entries
-  cl.nact = b->act_n[j];
-  cl.total = b->act_total[j];
+  cl.act = base + off;
+  cl.cpre = base + off + nact;
+  cl.nact = nact;
+  cl.total = total;
   return cl;
 }
 
+}  // namespace
+
+#define EN_CUDA(call, what)                                                             \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(TDSE_ERR_CUDA, std::string(what) + ": " +        \
+                                                         cudaGetErrorString(e_));       \
+  } while (0)
+
 bool valid_spec(const tdse_instance_spec &s) {
-  if (s.N < 1 || s.lmax < 0 || !(s.dr > 0.0) || !(s.dt > 0.0) || !std::isfinite(s.Z)) return false;
+  if (s.N < 1 || s.lmax < 0 || !(s.dr > 0.0) || !(s.dt > 0.0) || !std::isfinite(s.dt) ||
+      !std::isfinite(s.dr) || !std::isfinite(s.Z))
+    return false;
   if (s.krylov < 1 || s.krylov > TDSE_MAX_KRYLOV) return false;
   if (!std::isfinite(s.E0) || !std::isfinite(s.omega) || !std::isfinite(s.ncycles) ||
       !std::isfinite(s.cep) || !std::isfinite(s.absorber_r) || !std::isfinite(s.r_b))
     return false;
   if (s.E0 != 0.0 && (!(s.omega > 0.0) || !(s.ncycles > 0.0))) return false;
+  // segment and chunk indices are 32-bit in the kernels
+  const long long nseg = (long long)((s.N + 31) / 32) * (s.lmax + 1);
+  if (nseg > (1LL << 30) || (long long)s.N * (s.lmax + 1) >= (1LL << 31)) return false;
   return true;
 }
 
-}  // namespace
+size_t instance_bytes(const tdse_instance_spec &s, int precision) {
+  return layout_of(s, precision).total;
+}
+
+Engine::~Engine() {
+  if (stream) cudaStreamSynchronize(stream);
+  cudaFree(inst);
+  cudaFree(ls);
+  cudaFree(ticket);
+  cudaFree(status);
+  cudaFree(m_dev);
+  cudaFree(dt_dev);
+  cudaFree(E_dev);
+  cudaFree(lists);
+  cudaFree(obs_partials);   // obs_out points into this block
+  cudaFree(obs_ticket);
+  for (auto &mk : marks) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+int Engine::fail(int code, const std::string &msg) {
+  err = msg;
+  if (code == TDSE_ERR_CUDA) poisoned = true;
+  return code;
+}
+
+int Engine::init(int cap, int st, int prec) {
+  capacity = cap;
+  stencil = st;
+  precision = prec;
+  int dev = 0;
+  EN_CUDA(cudaGetDevice(&dev), "device");
+  EN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attributes");
+  EN_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking), "stream");
+  stream = own_stream;
+  hinst.assign(cap, BatchInst{});
+  spec.assign(cap, tdse_instance_spec{});
+  nstep.assign(cap, 0);
+  placed.assign(cap, 0);
+  norm_valid.assign(cap, 0);
+  const bool ok = cudaMalloc(&inst, sizeof(BatchInst) * cap) == cudaSuccess &&
+                  cudaMalloc(&ls, sizeof(LanczosScalars) * cap) == cudaSuccess &&
+                  cudaMalloc(&ticket, sizeof(unsigned) * cap) == cudaSuccess &&
+                  cudaMalloc(&status, sizeof(int)) == cudaSuccess &&
+                  cudaMalloc(&m_dev, sizeof(int) * cap) == cudaSuccess &&
+                  cudaMalloc(&dt_dev, sizeof(double) * cap) == cudaSuccess &&
+                  cudaMalloc(&obs_ticket, sizeof(unsigned)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return fail(TDSE_ERR_OOM, "engine descriptors");
+  }
+  EN_CUDA(cudaMemsetAsync(ls, 0, sizeof(LanczosScalars) * cap, stream), "clear");
+  EN_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * cap, stream), "clear");
+  EN_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream), "clear");
+  EN_CUDA(cudaMemsetAsync(m_dev, 0, sizeof(int) * cap, stream), "clear");
+  EN_CUDA(cudaMemsetAsync(dt_dev, 0, sizeof(double) * cap, stream), "clear");
+  EN_CUDA(cudaMemsetAsync(obs_ticket, 0, sizeof(unsigned), stream), "clear");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  return TDSE_OK;
+}
+
+int Engine::ensure(void **p, size_t &cap, size_t bytes, const char *what) {
+  if (bytes <= cap) return TDSE_OK;
+  EN_CUDA(cudaStreamSynchronize(stream), "sync before growing a buffer");
+  cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TDSE_ERR_OOM, what);
+  }
+  cap = bytes;
+  return TDSE_OK;
+}
+
+int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !mem || ((uintptr_t)mem & (kAlign - 1)))
+    return fail(TDSE_ERR_ARG, "bad slot or unaligned instance memory");
+  if (!valid_spec(s)) return fail(TDSE_ERR_ARG, "invalid instance spec");
+  const bool mixed = precision == TDSE_MIXED;
+  const Layout Lo = layout_of(s, precision);
+  char *base = static_cast<char *>(mem);
+  const int N = s.N, L = s.lmax;
+  const size_t G = (size_t)N * (L + 1);
+  BatchInst I{};
+  I.N = N;
+  I.L = L;
+  I.m = s.krylov;
+  I.nseg = (int)((size_t)((N + 31) / 32) * (L + 1));
+  I.nchunk = (I.nseg + kChunkSegs - 1) / kChunkSegs;
+  const double h2 = s.dr * s.dr;
+  double c0;
+  if (stencil == 5) {
+    c0 = 30.0 / (24.0 * h2);
+    I.c1 = -16.0 / (24.0 * h2);
+    I.c2 = 1.0 / (24.0 * h2);
+  } else {
+    c0 = 1.0 / h2;
+    I.c1 = -0.5 / h2;
+    I.c2 = 0.0;
+  }
+  I.psi = reinterpret_cast<double2 *>(base + Lo.psi);
+  I.rj = reinterpret_cast<double *>(base + Lo.rj);
+  I.mask = reinterpret_cast<double *>(base + Lo.mask);
+  I.kappa = reinterpret_cast<double *>(base + Lo.kappa);
+  I.partial = reinterpret_cast<double *>(base + Lo.partial);
+  I.ref0 = reinterpret_cast<double2 *>(base + Lo.ref0);
+  if (mixed) {
+    I.diagf = reinterpret_cast<float *>(base + Lo.diagf);
+    I.hi = reinterpret_cast<float2 *>(base + Lo.hi);
+    I.lo = reinterpret_cast<float2 *>(base + Lo.lo);
+    I.mwork = reinterpret_cast<float2 *>(base + Lo.mwork);
+    I.rjf = reinterpret_cast<float *>(base + Lo.rjf);
+    I.kappaf = reinterpret_cast<float *>(base + Lo.kappaf);
+  } else {
+    I.diag = reinterpret_cast<double *>(base + Lo.diag);
+    I.work = reinterpret_cast<double2 *>(base + Lo.work);
+  }
+  // tables (host), r_j = j dr, j = 1..N
+  std::vector<double> rj(N), kap(L + 2), msk(N, 1.0);
+  for (int j = 0; j < N; ++j) rj[j] = (double)(j + 1) * s.dr;
+  kap[0] = 0.0;
+  for (int l = 1; l <= L; ++l) {
+    const double ll = (double)l * (double)l;
+    kap[l] = std::sqrt(ll / (4.0 * ll - 1.0));
+  }
+  kap[L + 1] = 0.0;
+  I.mask_start = N;
+  const double R = rj[N - 1], ra = s.absorber_r;
+  if (ra < R) {
+    for (int j = 0; j < N; ++j) {
+      const double r = rj[j];
+      if (r > ra) {
+        if (I.mask_start == N) I.mask_start = j;
+        msk[j] = std::pow(std::cos(0.5 * M_PI * (r - ra) / (R - ra)), 0.125);
+      }
+    }
+  }
+  // normalised 1s state in l = 0 (also the p_ground reference)
+  std::vector<double> ref(2 * (size_t)N, 0.0);
+  double nrm = 0.0;
+  for (int j = 0; j < N; ++j) {
+    const double p = 2.0 * rj[j] * std::exp(-rj[j]);
+    ref[2 * j] = p;
+    nrm += p * p;
+  }
+  const double sc = 1.0 / std::sqrt(s.dr * nrm);
+  for (int j = 0; j < N; ++j) ref[2 * j] *= sc;
+  cudaStream_t st = stream;
+  EN_CUDA(cudaMemsetAsync(I.psi, 0, sizeof(double2) * G, st), "clear state");
+  EN_CUDA(cudaMemcpyAsync(I.psi, ref.data(), sizeof(double) * ref.size(), cudaMemcpyHostToDevice, st), "state");
+  EN_CUDA(cudaMemcpyAsync(I.ref0, ref.data(), sizeof(double) * ref.size(), cudaMemcpyHostToDevice, st), "reference");
+  EN_CUDA(cudaMemcpyAsync((void *)I.rj, rj.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "r table");
+  EN_CUDA(cudaMemcpyAsync((void *)I.mask, msk.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "mask");
+  EN_CUDA(cudaMemcpyAsync((void *)I.kappa, kap.data(), sizeof(double) * (L + 2), cudaMemcpyHostToDevice, st), "kappa");
+  if (mixed) {
+    std::vector<float> df(G), rf(N), kf(L + 2);
+    for (int l = 0; l <= L; ++l) {
+      const double cent = 0.5 * (double)l * (double)(l + 1);
+      for (int j = 0; j < N; ++j) {
+        const double r = rj[j];
+        df[(size_t)l * N + j] = (float)((c0 + cent / (r * r) - s.Z / r) - c0);
+      }
+    }
+    for (int j = 0; j < N; ++j) rf[j] = (float)rj[j];
+    for (int l = 0; l < L + 2; ++l) kf[l] = (float)kap[l];
+    EN_CUDA(cudaMemcpyAsync((void *)I.diagf, df.data(), sizeof(float) * G, cudaMemcpyHostToDevice, st), "diag");
+    EN_CUDA(cudaMemcpyAsync((void *)I.rjf, rf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st), "r table");
+    EN_CUDA(cudaMemcpyAsync((void *)I.kappaf, kf.data(), sizeof(float) * (L + 2), cudaMemcpyHostToDevice, st), "kappa");
+    EN_CUDA(cudaStreamSynchronize(st), "sync tables");
+  } else {
+    std::vector<double> diag(G);
+    for (int l = 0; l <= L; ++l) {
+      const double cent = 0.5 * (double)l * (double)(l + 1);
+      for (int j = 0; j < N; ++j) {
+        const double r = rj[j];
+        diag[(size_t)l * N + j] = c0 + cent / (r * r) - s.Z / r;
+      }
+    }
+    EN_CUDA(cudaMemcpyAsync((void *)I.diag, diag.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st), "diag");
+    EN_CUDA(cudaStreamSynchronize(st), "sync tables");
+  }
+  const int m = s.krylov;
+  const double dt = s.dt;
+  EN_CUDA(cudaMemcpyAsync(inst + slot, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, st), "descriptor");
+  EN_CUDA(cudaMemcpyAsync(m_dev + slot, &m, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor");
+  EN_CUDA(cudaMemcpyAsync(dt_dev + slot, &dt, sizeof(double), cudaMemcpyHostToDevice, st), "descriptor");
+  EN_CUDA(cudaStreamSynchronize(st), "sync descriptor");
+  hinst[slot] = I;
+  spec[slot] = s;
+  nstep[slot] = 0;
+  placed[slot] = 1;
+  norm_valid[slot] = 0;
+  return TDSE_OK;
+}
+
+void Engine::clear(int slot) {
+  if (slot < 0 || slot >= capacity) return;
+  placed[slot] = 0;
+  norm_valid[slot] = 0;
+  hinst[slot] = BatchInst{};
+}
+
+double Engine::time_of(int slot) const {
+  return (slot >= 0 && slot < capacity) ? (double)nstep[slot] * spec[slot].dt : 0.0;
+}
+
+long long Engine::steps_of(int slot) const { return (slot >= 0 && slot < capacity) ? nstep[slot] : 0; }
+
+cudaEvent_t Engine::prof_begin(int kind) {
+  if (!profiling) return nullptr;
+  if (nmarks == marks.size()) {
+    Mark mk;
+    if (cudaEventCreate(&mk.a) != cudaSuccess || cudaEventCreate(&mk.b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    marks.push_back(mk);
+  }
+  Mark &mk = marks[nmarks++];
+  mk.kind = kind;
+  cudaEventRecord(mk.a, stream);
+  return mk.b;
+}
+
+void Engine::prof_end(cudaEvent_t e) {
+  if (e) cudaEventRecord(e, stream);
+}
+
+int Engine::prof_collect() {
+  EN_CUDA(cudaStreamSynchronize(stream), "sync profile");
+  for (size_t i = 0; i < nmarks; ++i) {
+    float ms = 0.f;
+    EN_CUDA(cudaEventElapsedTime(&ms, marks[i].a, marks[i].b), "event time");
+    prof_ms[marks[i].kind] += ms;
+    prof_n[marks[i].kind] += 1;
+  }
+  nmarks = 0;
+  return TDSE_OK;
+}
+
+int Engine::profile(int enable) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (profiling) {
+    const int rc = prof_collect();
+    if (rc) return rc;
+  }
+  if (enable)
+    for (int k = 0; k < TDSE_K_COUNT; ++k) {
+      prof_ms[k] = 0.0;
+      prof_n[k] = 0;
+    }
+  profiling = enable != 0;
+  return TDSE_OK;
+}
+
+int Engine::profile_read(int kind, double *total_ms, long long *n) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (kind < 0 || kind >= TDSE_K_COUNT) return fail(TDSE_ERR_ARG, "unknown kernel kind");
+  if (profiling) {
+    const int rc = prof_collect();
+    if (rc) return rc;
+  }
+  if (total_ms) *total_ms = prof_ms[kind];
+  if (n) *n = prof_n[kind];
+  return TDSE_OK;
+}
+
+int Engine::sync() {
+  if (poisoned) return TDSE_ERR_STATE;
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  return TDSE_OK;
+}
+
+int Engine::set_stream(void *cuda_stream) {
+  if (poisoned) return TDSE_ERR_STATE;
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  stream = cuda_stream ? (cudaStream_t)cuda_stream : own_stream;
+  return TDSE_OK;
+}
+
+int Engine::set_state(int slot, const double *F) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot] || !F) return fail(TDSE_ERR_ARG, "bad instance or null state");
+  const BatchInst &I = hinst[slot];
+  const size_t G = (size_t)I.N * (I.L + 1);
+  EN_CUDA(cudaMemcpyAsync(I.psi, F, sizeof(double2) * G, cudaMemcpyHostToDevice, stream), "set state");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  norm_valid[slot] = 0;
+  return TDSE_OK;
+}
+
+int Engine::get_state(int slot, double *F) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot] || !F) return fail(TDSE_ERR_ARG, "bad instance or null state");
+  const BatchInst &I = hinst[slot];
+  const size_t G = (size_t)I.N * (I.L + 1);
+  EN_CUDA(cudaMemcpyAsync(F, I.psi, sizeof(double2) * G, cudaMemcpyDeviceToHost, stream), "get state");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  return TDSE_OK;
+}
+
+// Append the chunk list of `ids` to the host staging; list_off receives its offset.
+int Engine::launch_lists(const std::vector<int> &ids, int &list_off) {
+  list_off = (int)hlists.size();
+  hlists.insert(hlists.end(), ids.begin(), ids.end());
+  int tot = 0;
+  hlists.push_back(0);
+  for (int id : ids) {
+    tot += hinst[id].nchunk;
+    hlists.push_back(tot);
+  }
+  return tot;
+}
+
+int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slots.size() != steps.size()) return fail(TDSE_ERR_ARG, "slots and steps differ in length");
+  long kmax = 0;
+  std::vector<char> seen(capacity, 0);
+  for (size_t q = 0; q < slots.size(); ++q) {
+    const int s = slots[q];
+    if (s < 0 || s >= capacity || !placed[s] || steps[q] < 0 || seen[s])
+      return fail(TDSE_ERR_ARG, "bad slot or step count");
+    seen[s] = 1;
+    kmax = std::max(kmax, steps[q]);
+  }
+  if (kmax == 0) return TDSE_OK;
+  // launch errors are read with cudaGetLastError: drop an earlier, unrelated
+  // non-sticky error of this thread first (a sticky one fails the launches too)
+  cudaGetLastError();
+  const bool mixed = precision == TDSE_MIXED;
+  // segments of the run: the active set changes only where a slot finishes
+  std::vector<long> ends;
+  for (long k : steps)
+    if (k > 0) ends.push_back(k);
+  std::sort(ends.begin(), ends.end());
+  ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+  struct Seg { long n0, n1; int maxm; std::vector<int> off, nact, total; };
+  std::vector<Seg> segs;
+  hlists.clear();
+  std::vector<int> need_norm;
+  for (size_t q = 0; q < slots.size(); ++q)
+    if (steps[q] > 0 && !norm_valid[slots[q]]) need_norm.push_back(slots[q]);
+  std::sort(need_norm.begin(), need_norm.end());
+  int norm_off = 0, norm_total = 0;
+  if (!need_norm.empty()) norm_total = launch_lists(need_norm, norm_off);
+  long n0 = 0;
+  for (long e : ends) {
+    Seg sg;
+    sg.n0 = n0;
+    sg.n1 = e;
+    std::vector<int> act;
+    for (size_t q = 0; q < slots.size(); ++q)
+      if (steps[q] >= e) act.push_back(slots[q]);
+    std::sort(act.begin(), act.end());
+    sg.maxm = 0;
+    for (int s : act) sg.maxm = std::max(sg.maxm, spec[s].krylov);
+    for (int j = 0; j <= sg.maxm; ++j) {
+      std::vector<int> ph;
+      for (int s : act)
+        if (j == 0 || spec[s].krylov > j) ph.push_back(s);
+      int off = 0;
+      const int tot = launch_lists(ph, off);
+      sg.off.push_back(off);
+      sg.nact.push_back((int)ph.size());
+      sg.total.push_back(tot);
+    }
+    segs.push_back(std::move(sg));
+    n0 = e;
+  }
+  // field at the mid-point of every step: E[n * capacity + slot]
+  const size_t nE = (size_t)kmax * capacity;
+  int rc = ensure(reinterpret_cast<void **>(&E_dev), E_cap, sizeof(double) * nE, "field table");
+  if (rc) return rc;
+  rc = ensure(reinterpret_cast<void **>(&lists), lists_cap, sizeof(int) * std::max<size_t>(1, hlists.size()), "chunk lists");
+  if (rc) return rc;
+  hE.assign(nE, 0.0);
+  for (size_t q = 0; q < slots.size(); ++q) {
+    const int s = slots[q];
+    const tdse_instance_spec &sp = spec[s];
+    for (long n = 0; n < steps[q]; ++n) {
+      const double tn = (double)(nstep[s] + n) * sp.dt;
+      hE[(size_t)n * capacity + s] = pulse_at(sp, tn + 0.5 * sp.dt);
+    }
+  }
+  cudaStream_t st = stream;
+  EN_CUDA(cudaMemcpyAsync(E_dev, hE.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, st), "field upload");
+  EN_CUDA(cudaMemcpyAsync(lists, hlists.data(), sizeof(int) * hlists.size(), cudaMemcpyHostToDevice, st), "list upload");
+  const unsigned sgrid = (unsigned)(sms * kStencilBlocksPerSM);
+  const unsigned egrid = (unsigned)(sms * kElemBlocksPerSM);
+  BatchDev B;
+  B.inst = inst;
+  B.ls = ls;
+  B.ticket = ticket;
+  B.status = status;
+  B.E = E_dev;
+  if (!need_norm.empty()) {
+    const ChunkList cl = list_at(lists, norm_off, (int)need_norm.size(), norm_total);
+    cudaEvent_t pe = prof_begin(TDSE_K_NORM);
+    if (mixed) bt_split_mixed<<<egrid, kElemThreads, 0, st>>>(B, cl);
+    else bt_norm_fp64<<<egrid, kElemThreads, 0, st>>>(B, cl);
+    prof_end(pe);
+    ++launches;
+    EN_CUDA(cudaGetLastError(), "batch norm");
+    for (int s : need_norm) norm_valid[s] = 1;
+  }
+  for (const Seg &sg : segs) {
+    const ChunkList all = list_at(lists, sg.off[0], sg.nact[0], sg.total[0]);
+    for (long n = sg.n0; n < sg.n1; ++n) {
+      B.E = E_dev + (size_t)n * capacity;
+      for (int j = 0; j < sg.maxm; ++j) {
+        const ChunkList cl = list_at(lists, sg.off[j], sg.nact[j], sg.total[j]);
+        if (cl.total == 0) break;
+        cudaEvent_t pa = prof_begin(TDSE_K_LANCZOS_A);
+        if (mixed) {
+          if (stencil == 5) bt_lanczos_a_mixed<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
+          else bt_lanczos_a_mixed<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
+        } else {
+          if (stencil == 5) bt_lanczos_a_fp64<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
+          else bt_lanczos_a_fp64<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
+        }
+        prof_end(pa);
+        ++launches;
+        EN_CUDA(cudaGetLastError(), "batch lanczos a");
+        // U_{j+1} only for the instances that go on to iteration j + 1
+        if (j + 1 < sg.maxm && sg.total[j + 1] > 0) {
+          const ChunkList cn = list_at(lists, sg.off[j + 1], sg.nact[j + 1], sg.total[j + 1]);
+          cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
+          if (mixed) bt_lanczos_b_mixed<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+          else bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+          prof_end(pb);
+          ++launches;
+          EN_CUDA(cudaGetLastError(), "batch lanczos b");
+        }
+      }
+      cudaEvent_t px = prof_begin(TDSE_K_LANCZOS_EXPM);
+      EN_CUDA(launch_lanczos_expm_batched(all.nact, all.act, m_dev, dt_dev, ls, st), "batch expm");
+      prof_end(px);
+      ++launches;
+      cudaEvent_t pc = prof_begin(TDSE_K_LANCZOS_COMBINE);
+      if (mixed) bt_combine_mixed<<<egrid, kElemThreads, 0, st>>>(B, all);
+      else bt_combine_fp64<<<egrid, kElemThreads, 0, st>>>(B, all);
+      prof_end(pc);
+      ++launches;
+      EN_CUDA(cudaGetLastError(), "batch combine");
+    }
+  }
+  for (size_t q = 0; q < slots.size(); ++q) nstep[slots[q]] += steps[q];
+  return TDSE_OK;
+}
+
+int Engine::observables(int slot, std::vector<double> &out) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+  const tdse_instance_spec &s = spec[slot];
+  const BatchInst &I = hinst[slot];
+  Geometry g;
+  g.N = I.N;
+  g.L = I.L;
+  g.stencil = stencil;
+  g.sms = sms;
+  g.dr = s.dr;
+  g.c0 = g.c1 = g.c2 = 0.0;
+  OperatorView op;
+  op.diag = I.diag;
+  op.rj = I.rj;
+  op.kappa = I.kappa;
+  op.mask = I.mask;
+  op.mask_start = I.mask_start;
+  const size_t np = (size_t)5 * observables_blocks(g) * (I.L + 1);
+  int rc = ensure(reinterpret_cast<void **>(&obs_partials), obs_cap, sizeof(double) * (np + I.L + 6), "observables");
+  if (rc) return rc;
+  obs_out = obs_partials + np;
+  EN_CUDA(launch_observables(g, op, I.psi, I.ref0, s.r_b, obs_partials, obs_ticket, obs_out, stream), "observables");
+  ++launches;
+  out.assign(I.L + 5, 0.0);
+  EN_CUDA(cudaMemcpyAsync(out.data(), obs_out, sizeof(double) * (I.L + 5), cudaMemcpyDeviceToHost, stream), "read");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  if (!std::isfinite(out[0])) return fail(TDSE_ERR_NONFINITE, "the instance holds Inf/NaN");
+  return TDSE_OK;
+}
+
+}  // namespace tdse_dev
+
+// ===========================================================================
+// C ABI: a fixed batch
+// ===========================================================================
+using namespace tdse_dev;
+
+struct tdse_batch {
+  Engine eng;
+  int count = 0;
+  void *mem = nullptr;
+  long long npts = 0;
+  ~tdse_batch() {
+    if (eng.stream) cudaStreamSynchronize(eng.stream);
+    cudaFree(mem);
+  }
+};
 
 extern "C" {
 
@@ -707,431 +1104,91 @@ int tdse_batch_create(const tdse_instance_spec *specs, int count, int stencil, i
     return TDSE_ERR_ARG;
   for (int i = 0; i < count; ++i)
     if (!valid_spec(specs[i])) return TDSE_ERR_ARG;
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return TDSE_ERR_CUDA;
-  }
   tdse_batch *b = new (std::nothrow) tdse_batch();
   if (!b) return TDSE_ERR_OOM;
-  b->count = count;
-  b->stencil = stencil;
-  b->precision = precision;
-  b->sms = sms;
-  b->spec.assign(specs, specs + count);
-  b->t.assign(count, 0.0);
-  // layout
-  long long off = 0, woff = 0;
-  int roff = 0, koff = 0, cbase = 0, maxm = 0;
-  b->hinst.resize(count);
-  for (int i = 0; i < count; ++i) {
-    const tdse_instance_spec &s = specs[i];
-    BatchInst &I = b->hinst[i];
-    const long long G = (long long)s.N * (s.lmax + 1);
-    I.N = s.N;
-    I.L = s.lmax;
-    I.m = s.krylov;
-    I.off = off;
-    I.woff = woff;
-    I.roff = roff;
-    I.koff = koff;
-    const long long nseg = (long long)((s.N + 31) / 32) * (s.lmax + 1);
-    if (nseg > (1LL << 30) || off + G > (1LL << 40)) {
-      delete b;
-      return TDSE_ERR_ARG;
-    }
-    I.nseg = (int)nseg;
-    I.nchunk = (int)((nseg + kChunkSegs - 1) / kChunkSegs);
-    I.cbase = cbase;
-    I.pad = 0;
-    const double h2 = s.dr * s.dr;
-    if (stencil == 5) {
-      I.c1 = -16.0 / (24.0 * h2);
-      I.c2 = 1.0 / (24.0 * h2);
-    } else {
-      I.c1 = -0.5 / h2;
-      I.c2 = 0.0;
-    }
-    off += G;
-    woff += G * s.krylov;
-    roff += s.N;
-    koff += s.lmax + 2;
-    cbase += I.nchunk;
-    maxm = std::max(maxm, s.krylov);
-  }
-  b->npts = off;
-  b->nwork = woff;
-  b->nchunks = cbase;
-  b->max_m = maxm;
-  // host tables
-  std::vector<double> diag(off), rj(roff), kap(koff), msk(roff, 1.0);
-  std::vector<double> psi0(2 * off, 0.0);
-  for (int i = 0; i < count; ++i) {
-    const tdse_instance_spec &s = specs[i];
-    BatchInst &I = b->hinst[i];
-    const double c0 = (stencil == 5) ? 30.0 / (24.0 * s.dr * s.dr) : 1.0 / (s.dr * s.dr);
-    for (int j = 0; j < s.N; ++j) rj[I.roff + j] = (double)(j + 1) * s.dr;
-    for (int l = 0; l <= s.lmax; ++l) {
-      const double cent = 0.5 * (double)l * (double)(l + 1);
-      for (int j = 0; j < s.N; ++j) {
-        const double r = rj[I.roff + j];
-        diag[I.off + (long long)l * s.N + j] = c0 + cent / (r * r) - s.Z / r;
-      }
-    }
-    kap[I.koff] = 0.0;
-    for (int l = 1; l <= s.lmax; ++l) {
-      const double ll = (double)l * (double)l;
-      kap[I.koff + l] = std::sqrt(ll / (4.0 * ll - 1.0));
-    }
-    kap[I.koff + s.lmax + 1] = 0.0;
-    I.mask_start = s.N;
-    const double R = rj[I.roff + s.N - 1], ra = s.absorber_r;
-    if (ra < R) {
-      for (int j = 0; j < s.N; ++j) {
-        const double r = rj[I.roff + j];
-        if (r > ra) {
-          if (I.mask_start == s.N) I.mask_start = j;
-          msk[I.roff + j] = std::pow(std::cos(0.5 * M_PI * (r - ra) / (R - ra)), 0.125);
-        }
-      }
-    }
-    // normalised 1s state in l = 0
-    double nrm = 0.0;
-    for (int j = 0; j < s.N; ++j) {
-      const double r = rj[I.roff + j];
-      const double p = 2.0 * r * std::exp(-r);
-      psi0[2 * (I.off + j)] = p;
-      nrm += p * p;
-    }
-    const double sc = 1.0 / std::sqrt(s.dr * nrm);
-    for (int j = 0; j < s.N; ++j) psi0[2 * (I.off + j)] *= sc;
-  }
-  // active lists: phase j holds the instances with krylov > j
-  std::vector<int> act, cpre;
-  b->act_off.resize(maxm + 1);
-  b->act_n.resize(maxm + 1);
-  b->act_total.resize(maxm + 1);
-  for (int j = 0; j <= maxm; ++j) {
-    b->act_off[j] = (int)act.size();
-    int n = 0, tot = 0;
-    std::vector<int> pre;
-    pre.push_back(0);
-    for (int i = 0; i < count; ++i) {
-      if (specs[i].krylov > j || j == 0) {
-        act.push_back(i);
-        tot += b->hinst[i].nchunk;
-        pre.push_back(tot);
-        ++n;
-      }
-    }
-    // cpre is stored with one extra entry per phase: offset act_off[j] + j
-    while ((int)cpre.size() < b->act_off[j] + j) cpre.push_back(0);
-    cpre.insert(cpre.end(), pre.begin(), pre.end());
-    b->act_n[j] = n;
-    b->act_total[j] = tot;
-  }
-  std::vector<int> mh(count);
-  std::vector<double> dth(count);
-  for (int i = 0; i < count; ++i) {
-    mh[i] = specs[i].krylov;
-    dth[i] = specs[i].dt;
-  }
-  // device allocation
-  if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    b->own_stream = nullptr;
+  int rc = b->eng.init(count, stencil, precision);
+  if (rc) {
     delete b;
-    return TDSE_ERR_CUDA;
+    return rc;
   }
-  b->stream = b->own_stream;
-  int maxL = 0, maxN = 0;
+  b->count = count;
+  std::vector<size_t> at(count);
+  size_t total = 0;
   for (int i = 0; i < count; ++i) {
-    maxL = std::max(maxL, specs[i].lmax);
-    maxN = std::max(maxN, specs[i].N);
+    at[i] = total;
+    total += instance_bytes(specs[i], precision);
+    b->npts += (long long)specs[i].N * (specs[i].lmax + 1);
   }
-  const bool mixed = precision == TDSE_MIXED;
-  bool ok = cudaMalloc(&b->inst, sizeof(BatchInst) * count) == cudaSuccess &&
-            cudaMalloc(&b->diag, sizeof(double) * off) == cudaSuccess &&
-            cudaMalloc(&b->rj, sizeof(double) * roff) == cudaSuccess &&
-            cudaMalloc(&b->kappa, sizeof(double) * koff) == cudaSuccess &&
-            cudaMalloc(&b->mask, sizeof(double) * roff) == cudaSuccess &&
-            cudaMalloc(&b->psi, sizeof(double2) * off) == cudaSuccess &&
-            cudaMalloc(&b->ls, sizeof(LanczosScalars) * count) == cudaSuccess &&
-            cudaMalloc(&b->partial, sizeof(double) * std::max(1, cbase)) == cudaSuccess &&
-            cudaMalloc(&b->ticket, sizeof(unsigned) * count) == cudaSuccess &&
-            cudaMalloc(&b->status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&b->act, sizeof(int) * std::max<size_t>(1, act.size())) == cudaSuccess &&
-            cudaMalloc(&b->cpre, sizeof(int) * std::max<size_t>(1, cpre.size())) == cudaSuccess &&
-            cudaMalloc(&b->m_dev, sizeof(int) * count) == cudaSuccess &&
-            cudaMalloc(&b->dt_dev, sizeof(double) * count) == cudaSuccess &&
-            cudaMalloc(&b->obs_partials, sizeof(double) * ((size_t)5 * 8 * (maxL + 1) + 2)) == cudaSuccess &&
-            cudaMalloc(&b->obs_out, sizeof(double) * (maxL + 6)) == cudaSuccess &&
-            cudaMalloc(&b->ref0, sizeof(double2) * maxN) == cudaSuccess;
-  if (ok && !mixed) ok = cudaMalloc(&b->work, sizeof(double2) * woff) == cudaSuccess;
-  if (ok && mixed)
-    ok = cudaMalloc(&b->diagf, sizeof(float) * off) == cudaSuccess &&
-         cudaMalloc(&b->rjf, sizeof(float) * roff) == cudaSuccess &&
-         cudaMalloc(&b->kappaf, sizeof(float) * koff) == cudaSuccess &&
-         cudaMalloc(&b->split, sizeof(float2) * off * 2) == cudaSuccess &&
-         cudaMalloc(&b->mwork, sizeof(float2) * woff) == cudaSuccess;
-  if (!ok) {
+  if (cudaMalloc(&b->mem, total) != cudaSuccess) {
     cudaGetLastError();
-    bfree(b);
+    b->mem = nullptr;
     delete b;
     return TDSE_ERR_OOM;
   }
-  cudaStream_t s = b->stream;
-  bool cp = cudaMemcpyAsync(b->inst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->diag, diag.data(), sizeof(double) * off, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->rj, rj.data(), sizeof(double) * roff, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->kappa, kap.data(), sizeof(double) * koff, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->mask, msk.data(), sizeof(double) * roff, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->psi, psi0.data(), sizeof(double) * 2 * off, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemsetAsync(b->ls, 0, sizeof(LanczosScalars) * count, s) == cudaSuccess &&
-            cudaMemsetAsync(b->ticket, 0, sizeof(unsigned) * count, s) == cudaSuccess &&
-            cudaMemsetAsync(b->status, 0, sizeof(int), s) == cudaSuccess &&
-            cudaMemcpyAsync(b->act, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->cpre, cpre.data(), sizeof(int) * cpre.size(), cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->m_dev, mh.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(b->dt_dev, dth.data(), sizeof(double) * count, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemsetAsync(b->obs_partials, 0, sizeof(double) * ((size_t)5 * 8 * (maxL + 1) + 2), s) == cudaSuccess;
-  if (cp && mixed) {
-    std::vector<float> df(off), rf(roff), kf(koff);
-    for (int i = 0; i < count; ++i) {
-      const tdse_instance_spec &sp = specs[i];
-      const BatchInst &I = b->hinst[i];
-      const double c0 = (stencil == 5) ? 30.0 / (24.0 * sp.dr * sp.dr) : 1.0 / (sp.dr * sp.dr);
-      const long long G = (long long)sp.N * (sp.lmax + 1);
-      for (long long q = 0; q < G; ++q) df[I.off + q] = (float)(diag[I.off + q] - c0);
+  for (int i = 0; i < count; ++i) {
+    rc = b->eng.place(i, specs[i], static_cast<char *>(b->mem) + at[i]);
+    if (rc) {
+      delete b;
+      return rc;
     }
-    for (int q = 0; q < roff; ++q) rf[q] = (float)rj[q];
-    for (int q = 0; q < koff; ++q) kf[q] = (float)kap[q];
-    cp = cudaMemcpyAsync(b->diagf, df.data(), sizeof(float) * off, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-         cudaMemcpyAsync(b->rjf, rf.data(), sizeof(float) * roff, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-         cudaMemcpyAsync(b->kappaf, kf.data(), sizeof(float) * koff, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-         cudaStreamSynchronize(s) == cudaSuccess;
-  }
-  if (!cp || cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    bfree(b);
-    delete b;
-    return TDSE_ERR_CUDA;
   }
   *out = b;
   return TDSE_OK;
 }
 
 int tdse_batch_destroy(tdse_batch_t *b) {
-  if (!b) return TDSE_OK;
-  if (b->stream) cudaStreamSynchronize(b->stream);
-  bfree(b);
   delete b;
   return TDSE_OK;
 }
 
-const char *tdse_batch_last_error(const tdse_batch_t *b) { return b ? b->err.c_str() : "null batch"; }
+const char *tdse_batch_last_error(const tdse_batch_t *b) { return b ? b->eng.err.c_str() : "null batch"; }
 
 int tdse_batch_set_stream(tdse_batch_t *b, void *cuda_stream) {
-  if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync");
-  b->stream = cuda_stream ? (cudaStream_t)cuda_stream : b->own_stream;
-  return TDSE_OK;
+  return b ? b->eng.set_stream(cuda_stream) : TDSE_ERR_ARG;
 }
 
 int tdse_batch_set_state(tdse_batch_t *b, int i, const double *F) {
-  if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (i < 0 || i >= b->count || !F) return bfail(b, TDSE_ERR_ARG, "bad instance or null state");
-  const BatchInst &I = b->hinst[i];
-  const size_t G = (size_t)I.N * (I.L + 1);
-  BT_CUDA(b, cudaMemcpyAsync(b->psi + I.off, F, sizeof(double2) * G, cudaMemcpyHostToDevice, b->stream), "set state");
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync");
-  b->norm_valid = false;
-  return TDSE_OK;
+  return b ? b->eng.set_state(i, F) : TDSE_ERR_ARG;
 }
 
 int tdse_batch_get_state(tdse_batch_t *b, int i, double *F) {
-  if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (i < 0 || i >= b->count || !F) return bfail(b, TDSE_ERR_ARG, "bad instance or null state");
-  const BatchInst &I = b->hinst[i];
-  const size_t G = (size_t)I.N * (I.L + 1);
-  BT_CUDA(b, cudaMemcpyAsync(F, b->psi + I.off, sizeof(double2) * G, cudaMemcpyDeviceToHost, b->stream), "get state");
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync");
-  return TDSE_OK;
+  return b ? b->eng.get_state(i, F) : TDSE_ERR_ARG;
 }
 
 double tdse_batch_get_time(const tdse_batch_t *b, int i) {
-  return (b && i >= 0 && i < b->count) ? b->t[i] : 0.0;
+  return (b && i >= 0 && i < b->count) ? b->eng.time_of(i) : 0.0;
 }
 
 int tdse_batch_propagate(tdse_batch_t *b, long nsteps) {
   if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (nsteps < 0) return bfail(b, TDSE_ERR_ARG, "nsteps < 0");
-  if (nsteps == 0) return TDSE_OK;
-  const int C = b->count;
-  // field of every instance at the mid-point of every step of this call
-  const long long nE = (long long)nsteps * C;
-  if (nE > b->E_cap) {
-    BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync");
-    cudaFree(b->E_dev);
-    b->E_dev = nullptr;
-    b->E_cap = 0;
-    if (cudaMalloc(&b->E_dev, sizeof(double) * nE) != cudaSuccess) {
-      cudaGetLastError();
-      return bfail(b, TDSE_ERR_OOM, "field table");
-    }
-    b->E_cap = nE;
-  }
-  std::vector<double> Eh(nE);
-  for (long n = 0; n < nsteps; ++n)
-    for (int i = 0; i < C; ++i)
-      Eh[(size_t)n * C + i] = pulse_at(b->spec[i], b->t[i] + (double)n * b->spec[i].dt + 0.5 * b->spec[i].dt);
-  BT_CUDA(b, cudaMemcpyAsync(b->E_dev, Eh.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, b->stream), "field upload");
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync field upload");
-  const bool mixed = b->precision == TDSE_MIXED;
-  const unsigned sgrid = (unsigned)(b->sms * kStencilBlocksPerSM);
-  const unsigned egrid = (unsigned)(b->sms * kElemBlocksPerSM);
-  cudaStream_t st = b->stream;
-  BatchDev B = dev_view(b);
-  const ChunkList all = chunk_list(b, 0);
-  if (!b->norm_valid) {
-    cudaEvent_t pe = bprof_begin(b, TDSE_K_NORM);
-    if (mixed) bt_split_mixed<<<egrid, kElemThreads, 0, st>>>(B, all);
-    else bt_norm_fp64<<<egrid, kElemThreads, 0, st>>>(B, all);
-    bprof_end(b, pe);
-    ++b->launches;
-    BT_CUDA(b, cudaGetLastError(), "batch norm");
-  }
-  for (long n = 0; n < nsteps; ++n) {
-    B.E = b->E_dev + (size_t)n * C;
-    for (int j = 0; j < b->max_m; ++j) {
-      const ChunkList cl = chunk_list(b, j);
-      if (cl.total == 0) break;
-      cudaEvent_t pa = bprof_begin(b, TDSE_K_LANCZOS_A);
-      if (mixed) {
-        if (b->stencil == 5) bt_lanczos_a_mixed<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-        else bt_lanczos_a_mixed<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-      } else {
-        if (b->stencil == 5) bt_lanczos_a_fp64<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-        else bt_lanczos_a_fp64<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-      }
-      bprof_end(b, pa);
-      ++b->launches;
-      BT_CUDA(b, cudaGetLastError(), "batch lanczos a");
-      // U_{j+1} only for the instances that go on to iteration j + 1
-      const ChunkList cn = chunk_list(b, j + 1);
-      if (j + 1 < b->max_m && cn.total > 0) {
-        cudaEvent_t pb = bprof_begin(b, TDSE_K_LANCZOS_B);
-        if (mixed) bt_lanczos_b_mixed<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-        else bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-        bprof_end(b, pb);
-        ++b->launches;
-        BT_CUDA(b, cudaGetLastError(), "batch lanczos b");
-      }
-    }
-    cudaEvent_t px = bprof_begin(b, TDSE_K_LANCZOS_EXPM);
-    BT_CUDA(b, launch_lanczos_expm_batched(C, b->m_dev, b->dt_dev, b->ls, st), "batch expm");
-    bprof_end(b, px);
-    ++b->launches;
-    cudaEvent_t pc = bprof_begin(b, TDSE_K_LANCZOS_COMBINE);
-    if (mixed) bt_combine_mixed<<<egrid, kElemThreads, 0, st>>>(B, all);
-    else bt_combine_fp64<<<egrid, kElemThreads, 0, st>>>(B, all);
-    bprof_end(b, pc);
-    ++b->launches;
-    BT_CUDA(b, cudaGetLastError(), "batch combine");
-  }
-  for (int i = 0; i < C; ++i) b->t[i] += (double)nsteps * b->spec[i].dt;
-  b->norm_valid = true;
-  return TDSE_OK;
+  if (b->eng.poisoned) return TDSE_ERR_STATE;
+  if (nsteps < 0) return b->eng.fail(TDSE_ERR_ARG, "nsteps < 0");
+  std::vector<int> slots(b->count);
+  for (int i = 0; i < b->count; ++i) slots[i] = i;
+  return b->eng.run(slots, std::vector<long>(b->count, nsteps));
 }
 
 int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
                            double *yield, double *p_ground) {
   if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (i < 0 || i >= b->count) return bfail(b, TDSE_ERR_ARG, "bad instance");
-  const tdse_instance_spec &s = b->spec[i];
-  const BatchInst &I = b->hinst[i];
-  Geometry g;
-  g.N = I.N;
-  g.L = I.L;
-  g.stencil = b->stencil;
-  g.sms = b->sms;
-  g.dr = s.dr;
-  g.c0 = g.c1 = g.c2 = 0.0;
-  OperatorView op;
-  op.diag = b->diag + I.off;
-  op.rj = b->rj + I.roff;
-  op.kappa = b->kappa + I.koff;
-  op.mask = b->mask + I.roff;
-  op.mask_start = I.mask_start;
-  // reference of p_ground: the 1s state of the instance's grid
-  std::vector<double> ref(2 * (size_t)I.N, 0.0);
-  double nrm = 0.0;
-  for (int j = 0; j < I.N; ++j) {
-    const double r = (double)(j + 1) * s.dr;
-    ref[2 * j] = 2.0 * r * std::exp(-r);
-    nrm += ref[2 * j] * ref[2 * j];
-  }
-  for (int j = 0; j < I.N; ++j) ref[2 * j] /= std::sqrt(s.dr * nrm);
-  BT_CUDA(b, cudaMemcpyAsync(b->ref0, ref.data(), sizeof(double) * ref.size(), cudaMemcpyHostToDevice, b->stream), "ref");
-  // the counter sits after the largest partial block, at the same address for every instance
-  int maxL = 0;
-  for (const auto &sp : b->spec) maxL = std::max(maxL, sp.lmax);
-  unsigned *ticket = reinterpret_cast<unsigned *>(b->obs_partials + (size_t)5 * 8 * (maxL + 1));
-  BT_CUDA(b, launch_observables(g, op, b->psi + I.off, b->ref0, s.r_b, b->obs_partials, ticket, b->obs_out,
-                                b->stream),
-          "observables");
-  ++b->launches;
-  std::vector<double> out(I.L + 5);
-  BT_CUDA(b, cudaMemcpyAsync(out.data(), b->obs_out, sizeof(double) * (I.L + 5), cudaMemcpyDeviceToHost, b->stream), "read");
-  BT_CUDA(b, cudaStreamSynchronize(b->stream), "sync");
-  int st = 0;
-  BT_CUDA(b, cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+  std::vector<double> out;
+  const int rc = b->eng.observables(i, out);
+  if (rc && rc != TDSE_ERR_NONFINITE) return rc;
   if (norm) *norm = out[0];
   if (dipole) *dipole = out[1];
   if (yield) *yield = out[2];
   if (p_ground) *p_ground = out[3];
-  if (l_pop) std::memcpy(l_pop, out.data() + 4, sizeof(double) * (I.L + 1));
-  if ((st & kStatusNonFinite) || !std::isfinite(out[0]))
-    return bfail(b, TDSE_ERR_NONFINITE, "an instance holds Inf/NaN");
-  return TDSE_OK;
+  if (l_pop) std::memcpy(l_pop, out.data() + 4, sizeof(double) * (out.size() - 4));
+  return rc;
 }
 
 long long tdse_batch_points(const tdse_batch_t *b) { return b ? b->npts : 0; }
-long long tdse_batch_launch_count(const tdse_batch_t *b) { return b ? b->launches : 0; }
+long long tdse_batch_launch_count(const tdse_batch_t *b) { return b ? b->eng.launches : 0; }
 
-int tdse_batch_profile(tdse_batch_t *b, int enable) {
-  if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (b->profiling) {
-    const int rc = bprof_collect(b);
-    if (rc) return rc;
-  }
-  if (enable)
-    for (int k = 0; k < TDSE_K_COUNT; ++k) {
-      b->prof_ms[k] = 0.0;
-      b->prof_n[k] = 0;
-    }
-  b->profiling = enable != 0;
-  return TDSE_OK;
-}
+int tdse_batch_profile(tdse_batch_t *b, int enable) { return b ? b->eng.profile(enable) : TDSE_ERR_ARG; }
 
 int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches) {
-  if (!b) return TDSE_ERR_ARG;
-  if (b->poisoned) return TDSE_ERR_STATE;
-  if (kind < 0 || kind >= TDSE_K_COUNT) return bfail(b, TDSE_ERR_ARG, "unknown kernel kind");
-  if (b->profiling) {
-    const int rc = bprof_collect(b);
-    if (rc) return rc;
-  }
-  if (total_ms) *total_ms = b->prof_ms[kind];
-  if (launches) *launches = b->prof_n[kind];
-  return TDSE_OK;
+  return b ? b->eng.profile_read(kind, total_ms, launches) : TDSE_ERR_ARG;
 }
 
 }  // extern "C"

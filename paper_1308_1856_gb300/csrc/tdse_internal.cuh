@@ -83,7 +83,9 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
 cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
                              double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st);
-cudaError_t launch_lanczos_expm_batched(int count, const int *m, const double *dt,
+// One block per listed instance: ids[0..count) index m, dt and ls (ids NULL:
+// instances 0..count-1).
+cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt,
                                         LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,
                                    double2 *psi, const double2 *work, size_t stride,

@@ -355,11 +355,12 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
   expm_body(m, dt, ls);
 }
 
-// One block per instance of a batch.
+// One block per listed instance of a batch (ids[b], or b when ids is null).
 __global__ void __launch_bounds__(kEx)
-    lanczos_expm_batched_kernel(const int *__restrict__ m, const double *__restrict__ dt,
-                                LanczosScalars *ls) {
-  expm_body(m[blockIdx.x], dt[blockIdx.x], ls + blockIdx.x);
+    lanczos_expm_batched_kernel(const int *__restrict__ ids, const int *__restrict__ m,
+                                const double *__restrict__ dt, LanczosScalars *ls) {
+  const int i = ids ? ids[blockIdx.x] : (int)blockIdx.x;
+  expm_body(m[i], dt[i], ls + i);
 }
 
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st) {
@@ -367,9 +368,10 @@ cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_expm_batched(int count, const int *m, const double *dt,
+cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt,
                                         LanczosScalars *ls, cudaStream_t st) {
-  lanczos_expm_batched_kernel<<<count, kEx, 0, st>>>(m, dt, ls);
+  if (count < 1) return cudaSuccess;
+  lanczos_expm_batched_kernel<<<count, kEx, 0, st>>>(ids, m, dt, ls);
   return cudaGetLastError();
 }
 

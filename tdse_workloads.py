@@ -152,3 +152,12 @@ def batched_specs(count: int = 256, seed: int = 1308) -> List[InstanceSpec]:
         m = int(rng.integers(8, 17))
         out.append(InstanceSpec(N, 0.1, lmax, I, lam, nc, m))
     return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of `count` requests of a Poisson process of the given
+    mean rate (req/s): exponential gaps, the first request at t = 0."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, count)
+    gaps[0] = 0.0
+    return np.cumsum(gaps)

@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 def _declared():
     txt = open(HEADER).read()
-    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|long long|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
+    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|unsigned long long|long long|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
                           txt, re.M))
 
 
@@ -52,3 +52,42 @@ def test_library_is_sm103a_build():
     assert os.path.exists(B.library_path())
     from paper_1308_1856_gb300 import build as bld
     assert "arch=compute_103a,code=sm_103a" in " ".join(bld.ARCH)
+
+
+def test_server_arguments_rejected_without_touching_the_device(lib):
+    h = ctypes.c_void_p()
+    for args in [(0, 16, 5, 0), (1 << 20, 0, 5, 0), (1 << 20, 16, 4, 0), (1 << 20, 16, 5, 2)]:
+        assert B.tdse_server_create(*args, ctypes.byref(h)) == B.TDSE_ERR_ARG, args
+        assert not h.value
+    assert B.tdse_server_destroy(None) == 0
+    assert B.tdse_server_last_error(None) == b"null server"
+    assert B.tdse_server_step(None, 10, None) == B.TDSE_ERR_ARG
+    assert B.tdse_server_release(None, 1) == B.TDSE_ERR_ARG
+    assert B.tdse_server_sync(None) == B.TDSE_ERR_ARG
+
+
+def _spec(**kw):
+    d = dict(N=1000, dr=0.1, lmax=15, Z=1.0, E0=0.05, omega=0.057, ncycles=2.0, cep=0.0, krylov=12,
+             dt=0.02, absorber_r=50.0, r_b=10.0)
+    d.update(kw)
+    return B.tdse_instance_spec(*[d[f] for f, _ in B.tdse_instance_spec._fields_])
+
+
+def test_server_instance_bytes(lib):
+    """Device bytes of one request: every array of the instance, each rounded
+    up to 256 bytes (counted here from the list of arrays, not the code)."""
+    def up(x):
+        return (x + 255) // 256 * 256
+
+    for N, L, m in [(1000, 15, 12), (2000, 127, 16), (33, 0, 1), (16000, 63, 8)]:
+        G = N * (L + 1)
+        nchunk = -(-((N + 31) // 32) * (L + 1) // 64)
+        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(16 * N)
+        fp64 = common + up(8 * G) + up(16 * G * m)
+        mixed = common + up(4 * G) + 2 * up(8 * G) + up(8 * G * m) + up(4 * N) + up(4 * (L + 2))
+        s = _spec(N=N, lmax=L, krylov=m)
+        assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == fp64
+        assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_MIXED) == mixed
+    bad = _spec(krylov=0)
+    assert B.tdse_server_instance_bytes(ctypes.byref(bad), B.TDSE_FP64) == 0
+    assert B.tdse_server_instance_bytes(ctypes.byref(_spec(dt=-1.0)), B.TDSE_FP64) == 0
