@@ -247,6 +247,20 @@ class BatchRow:
         return self.b.observables(0)
 
 
+def combine_over_ranks(total_ms: float, units: float, ws: int, device="cpu"):
+    """Slowest rank's timed milliseconds and the units all ranks processed
+    (replicas: no data exchange, only these two scalars)."""
+    if ws == 1:
+        return total_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def batched_request_spec(x, dt=BATCH_DT):
     return dict(N=x.N, dr=x.dr, lmax=x.lmax, krylov=x.krylov, dt=dt, E0=x.E0, omega=x.omega,
                 ncycles=x.ncycles, absorber_r=x.N * x.dr - BATCH_ABSORBER)
@@ -328,7 +342,7 @@ def run_ours(args, ws, rank, local):
     if args.rows in ("all", "single"):
         rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
     if args.rows in ("all", "batched"):
-        rows += [BatchRow(p, stream.cuda_stream) for p in ("fp64", "mixed")
+        rows += [BatchRow(p, stream.cuda_stream, count=args.batch_count) for p in ("fp64", "mixed")
                  if args.precision in ("all", p) and args.method in ("all", "lanczos")]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -362,10 +376,9 @@ def run_ours(args, ws, rank, local):
     row_ms = {r.name: sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps))
               for i, r in enumerate(rows)}
     total_ms = sum(row_ms.values())
+    gp_step = sum(r.gp for r in rows)
+    total_ms, units_all = combine_over_ranks(total_ms, gp_step * args.steps, ws, dev)
     if ws > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
         torch.distributed.barrier()
     for r in rows:
         r.h.sync() if hasattr(r.h, "sync") else r.b.observables(0)   # raises on Inf/NaN
@@ -431,9 +444,9 @@ def run_ours(args, ws, rank, local):
         for r, (pin_in, pin_out) in zip(rows, pins):
             obs = r.e2e_step(pin_in, pin_out)
     e2e_s = time.perf_counter() - e0
-    gp_step = sum(r.gp for r in rows)
-    value = gp_step * args.steps * ws / (total_ms * 1e-3)
-    e2e_value = gp_step * e2e_steps * ws / e2e_s if e2e_steps else None
+    e2e_s_max, e2e_units = combine_over_ranks(e2e_s, gp_step * e2e_steps, ws, dev)
+    value = units_all / (total_ms * 1e-3)
+    e2e_value = e2e_units / e2e_s_max if e2e_steps else None
     result = {
         "metric": METRIC, "value": value, "unit": "grid-point*steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -501,6 +514,8 @@ def main():
                     help="restrict to one precision (profiling runs)")
     ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served"],
                     help="restrict to the single-instance, batched or served rows")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="instances of the batched rows (smaller only for profiling captures)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served traces")
     ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--serve-rate", type=float, default=50.0, help="overloaded trace: mean req/s")

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double c = ls->acoef[j];
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const size_t idx = (size_t)l * I.N + i;
         const double2 zz = z[idx], uu = u[idx];
@@ -214,6 +215,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double2 *x = I.psi;
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const double2 v = x[(size_t)l * I.N + i];
         acc = __fma_rn(v.x, v.x, acc);
@@ -234,6 +236,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 // psi_new = sum_{j<k} coef_j U_j, mask, ||psi_new|| (FP64).
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_combine_fp64(BatchDev B, ChunkList cl) {
+  // the chunk's coefficients, one copy per warp
+  __shared__ double2 wcoef[kElemThreads / 32][kMaxKrylov];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
@@ -242,17 +247,21 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double2 *U1 = I.work + G;
     const double *mask = I.mask;
     const int k = ls->kdim;
+    __syncwarp();
+    if (lane < k) wcoef[wib][lane] = ls->coef[lane];
+    __syncwarp();
+    const double2 c0 = wcoef[wib][0];
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const size_t idx = (size_t)l * I.N + i;
         const double2 u0 = psi[idx];
-        const double2 c0 = ls->coef[0];
         double ox = __fma_rn(c0.x, u0.x, __dmul_rn(-c0.y, u0.y));
         double oy = __fma_rn(c0.x, u0.y, __dmul_rn(c0.y, u0.x));
         for (int jj = 1; jj < k; ++jj) {
           const double2 u = U1[(size_t)(jj - 1) * G + idx];
-          const double2 c = ls->coef[jj];
+          const double2 c = wcoef[wib][jj];
           ox = __fma_rn(c.x, u.x, ox);
           ox = __fma_rn(-c.y, u.y, ox);
           oy = __fma_rn(c.x, u.y, oy);
@@ -289,6 +298,8 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   in.diag = I.diagf;
   in.rj = I.rjf;
   in.kappa = I.kappaf;
+  in.pf0 = nullptr;
+  in.pf1 = nullptr;
   in.N = I.N;
   in.L = I.L;
   in.c1 = (float)I.c1;
@@ -310,9 +321,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const double sigd = ls->sigma[j];
     const float sig = (float)sigd;
     const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
-    float acc = 0.f;
-    double accd = 0.0;
-    int cnt = 0;
+    PairSum acc;
     auto epi = [&](int, size_t idx, float2 t, float2 u) {
       float2 o = make_float2(sig * t.x, sig * t.y);
       if (j > 0) {
@@ -327,21 +336,22 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
         o.y = fmaf(-cprev, up.y, o.y);
       }
       z[idx] = o;
-      acc = fmaf(u.x, o.x, fmaf(u.y, o.y, acc));
-      if (++cnt == 8) {
-        accd += (double)acc;
-        acc = 0.f;
-        cnt = 0;
-      }
+      acc.add(fmaf(u.x, o.x, u.y * o.y));
     };
     if (j == 0) {
       const MixedIn in = mixed_in(B, I, inst, hi, lo, nullptr);
       chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false>(in, i, l0, l1, epi); });
     } else {
-      const MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
+      MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
+      if (uprev) {
+        in.pf0 = uprev;
+      } else {
+        in.pf0 = hi;
+        in.pf1 = lo;
+      }
       chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true>(in, i, l0, l1, epi); });
     }
-    accd += (double)acc;
+    const double accd = acc.value();
     double s;
     if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
       ls->alpha[j] = s * sigd;
@@ -361,10 +371,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const float2 *z = I.mwork;
     float2 *un = I.mwork + (long long)(j + 1) * G;
     const float c = (float)ls->acoef[j];
-    float acc = 0.f;
-    double accd = 0.0;
-    int cnt = 0;
+    PairSum acc;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const size_t idx = (size_t)l * I.N + i;
         float2 uu;
@@ -377,15 +386,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
         const float2 zz = z[idx];
         const float2 o = make_float2(fmaf(c, uu.x, zz.x), fmaf(c, uu.y, zz.y));
         un[idx] = o;
-        acc = fmaf(o.x, o.x, fmaf(o.y, o.y, acc));
-        if (++cnt == 8) {
-          accd += (double)acc;
-          acc = 0.f;
-          cnt = 0;
-        }
+        acc.add(fmaf(o.x, o.x, o.y * o.y));
       }
     });
-    accd += (double)acc;
+    const double accd = acc.value();
     double s;
     if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
       const double beta = sqrt(s);
@@ -397,32 +401,26 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   });
 }
 
-// psi -> (hi, lo) and ||psi|| (FP32 products, FP64 sums).
+// psi -> (hi, lo) and ||psi|| (FP32 products summed in FP32 pairs, then FP64).
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_split_mixed(BatchDev B, ChunkList cl) {
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
     const double2 *x = I.psi;
     float2 *hi = I.hi, *lo = I.lo;
-    float acc = 0.f;
-    double accd = 0.0;
-    int cnt = 0;
+    PairSum acc;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const size_t idx = (size_t)l * I.N + i;
         float2 h, lw;
         split2(x[idx], h, lw);
         hi[idx] = h;
         lo[idx] = lw;
-        acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
-        if (++cnt == 8) {
-          accd += (double)acc;
-          acc = 0.f;
-          cnt = 0;
-        }
+        acc.add(fmaf(h.x, h.x, h.y * h.y));
       }
     });
-    accd += (double)acc;
+    const double accd = acc.value();
     double s;
     if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
       LanczosScalars *ls = B.ls + inst;
@@ -438,6 +436,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 // mask, split, ||psi_new||.
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_combine_mixed(BatchDev B, ChunkList cl) {
+  // the chunk's FP32 coefficients, converted once and kept per warp
+  __shared__ float2 wcoef[kElemThreads / 32][kMaxKrylov];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
@@ -448,17 +449,21 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double *mask = I.mask;
     const int k = ls->kdim;
     const double2 c0 = ls->coef[0];
-    float acc = 0.f;
-    double accd = 0.0;
-    int cnt = 0;
+    __syncwarp();
+    if (lane < k) {
+      const double2 cd = ls->coef[lane];
+      wcoef[wib][lane] = make_float2((float)cd.x, (float)cd.y);
+    }
+    __syncwarp();
+    PairSum acc;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
+#pragma unroll 4
       for (int l = l0; l < l1; ++l) {
         const size_t idx = (size_t)l * I.N + i;
         float cx = 0.f, cy = 0.f;
         for (int jj = 1; jj < k; ++jj) {
           const float2 u = U1[(size_t)(jj - 1) * G + idx];
-          const double2 cd = ls->coef[jj];
-          const float2 c = make_float2((float)cd.x, (float)cd.y);
+          const float2 c = wcoef[wib][jj];
           cx = fmaf(c.x, u.x, cx);
           cx = fmaf(-c.y, u.y, cx);
           cy = fmaf(c.x, u.y, cy);
@@ -478,15 +483,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
         split2(o, h, lw);
         hi[idx] = h;
         lo[idx] = lw;
-        acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
-        if (++cnt == 8) {
-          accd += (double)acc;
-          acc = 0.f;
-          cnt = 0;
-        }
+        acc.add(fmaf(h.x, h.x, h.y * h.y));
       }
     });
-    accd += (double)acc;
+    const double accd = acc.value();
     double s;
     if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
       const double nrm = sqrt(s);

@@ -57,6 +57,22 @@ __device__ __forceinline__ double reduce_partials(Reduction *red, unsigned npart
 }
 
 // Global warp index and warp count of a 1-D persistent launch.
+// Running sum of FP32 terms held as an unevaluated pair s + c: every addition
+// is error-free (Knuth's TwoSum), so the pair keeps about twice the FP32
+// precision and a long run of terms needs no FP64 arithmetic until value().
+// (FP64 instructions, conversions included, issue at a small fraction of the
+// FP32 rate on this part.)
+struct PairSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __device__ __forceinline__ int warp_id() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
 __device__ __forceinline__ int warp_count() { return gridDim.x * (blockDim.x >> 5); }
 

@@ -17,8 +17,9 @@
 //
 // Work decomposition and reductions are those of the FP64 kernels (persistent
 // grid, balanced 32-point row segments per warp, fixed-order block partials).
-// Per-thread partial sums are FP32 over the thread's few points; the grid
-// reduction of alpha, beta and the norm is FP64.
+// Each thread sums its FP32 products in an error-free FP32 pair (about twice
+// the FP32 precision, no FP64 instruction per point); the block and grid
+// reductions of alpha, beta and the norm are FP64.
 #include <cuda_runtime.h>
 
 #include "tdse_device_common.cuh"
@@ -53,7 +54,7 @@ __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
 
 // ---------------------------------------------------------------------------
 // psi -> (hi, lo) and the Lanczos start scalars (||psi|| from FP32 products
-// accumulated in FP64).
+// summed per thread in an FP32 pair, then across threads in FP64).
 
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     mx_split_kernel(size_t G, const double2 *__restrict__ psi, float2 *__restrict__ hi,
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   const int lane = threadIdx.x & 31;
   long long g0, g1;
   warp_range((long long)((G + 31) >> 5), g0, g1);
-  float acc = 0.f;
-  double accd = 0.0;
+  PairSum acc;
+#pragma unroll 4
   for (long long gi = g0; gi < g1; ++gi) {
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) {
@@ -71,14 +72,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       split2(psi[idx], h, l);
       hi[idx] = h;
       lo[idx] = l;
-      acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
-    }
-    if (((gi - g0) & 7) == 7) {   // flush the FP32 partial every 8 groups
-      accd += (double)acc;
-      acc = 0.f;
+      acc.add(fmaf(h.x, h.x, h.y * h.y));
     }
   }
-  accd += (double)acc;
+  const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -98,6 +95,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   const int lane = threadIdx.x & 31;
   long long g0, g1;
   warp_range((long long)((G + 31) >> 5), g0, g1);
+#pragma unroll 4
   for (long long gi = g0; gi < g1; ++gi) {
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) {
@@ -129,9 +127,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   const double sigd = ls->sigma[j];
   const float sig = (float)sigd;
   const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
-  float acc = 0.f;
-  double accd = 0.0;
-  int cnt = 0;
+  PairSum acc;
   mixed_segments<ST, FIRST, !FIRST>(in, [&](int, size_t idx, float2 t, float2 u) {
     float2 o = make_float2(sig * t.x, sig * t.y);
     if (!FIRST) {
@@ -146,14 +142,9 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       o.y = fmaf(-cprev, up.y, o.y);
     }
     z[idx] = o;
-    acc = fmaf(u.x, o.x, fmaf(u.y, o.y, acc));
-    if (++cnt == 8) {
-      accd += (double)acc;
-      acc = 0.f;
-      cnt = 0;
-    }
+    acc.add(fmaf(u.x, o.x, u.y * o.y));
   });
-  accd += (double)acc;
+  const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -164,7 +155,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 }
 
 // Lanczos iteration j, second half (mixed): U_{j+1} = z - alpha_j sigma_j U_j;
-// beta_j = ||U_{j+1}|| (FP32 products, FP64 reduction).
+// beta_j = ||U_{j+1}|| (FP32 products, FP32-pair sums, FP64 reduction).
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     mx_lanczos_b_kernel(size_t G, int j, const float2 *__restrict__ z, const float2 *__restrict__ u,
                         const float2 *__restrict__ u_hi, const float2 *__restrict__ u_lo,
@@ -174,8 +165,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   const int lane = threadIdx.x & 31;
   long long g0, g1;
   warp_range((long long)((G + 31) >> 5), g0, g1);
-  float acc = 0.f;
-  double accd = 0.0;
+  PairSum acc;
+#pragma unroll 4
   for (long long gi = g0; gi < g1; ++gi) {
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) {
@@ -189,14 +180,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       const float2 zz = z[idx];
       const float2 o = make_float2(fmaf(c, uu.x, zz.x), fmaf(c, uu.y, zz.y));
       unext[idx] = o;
-      acc = fmaf(o.x, o.x, fmaf(o.y, o.y, acc));
-    }
-    if (((gi - g0) & 7) == 7) {
-      accd += (double)acc;
-      acc = 0.f;
+      acc.add(fmaf(o.x, o.x, o.y * o.y));
     }
   }
-  accd += (double)acc;
+  const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -235,8 +222,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   const int lane = threadIdx.x & 31;
   long long g0, g1;
   warp_range((long long)((G + 31) >> 5), g0, g1);
-  float acc = 0.f;
-  double accd = 0.0;
+  PairSum acc;
+#pragma unroll 4
   for (long long gi = g0; gi < g1; ++gi) {
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) {
@@ -264,14 +251,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       split2(o, h, l);
       hi[idx] = h;
       lo[idx] = l;
-      acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
-    }
-    if (((gi - g0) & 7) == 7) {
-      accd += (double)acc;
-      acc = 0.f;
+      acc.add(fmaf(h.x, h.x, h.y * h.y));
     }
   }
-  accd += (double)acc;
+  const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -371,6 +354,8 @@ MixedIn make_mixed(const Geometry &g, const MixedView &mv, float E, const float2
   in.diag = mv.diag;
   in.rj = mv.rj;
   in.kappa = mv.kappa;
+  in.pf0 = nullptr;
+  in.pf1 = nullptr;
   in.N = g.N;
   in.L = g.L;
   in.c1 = (float)g.c1;
@@ -418,7 +403,13 @@ cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E
     else
       mx_lanczos_a_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, j, nullptr, nullptr, nullptr, z, red, ls);
   } else {
-    const MixedIn in = make_mixed(g, mv, (float)E, nullptr, nullptr, u, 1.f);
+    MixedIn in = make_mixed(g, mv, (float)E, nullptr, nullptr, u, 1.f);
+    if (uprev) {
+      in.pf0 = uprev;
+    } else {
+      in.pf0 = hi;
+      in.pf1 = lo;
+    }
     if (g.stencil == 5)
       mx_lanczos_a_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, j, uprev, hi, lo, z, red, ls);
     else

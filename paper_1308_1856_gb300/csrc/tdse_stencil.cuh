@@ -52,9 +52,33 @@ struct MixedIn {
   const float *__restrict__ diag;  // l(l+1)/(2 r^2) + V(r) (+ odd-ghost fold), no c0
   const float *__restrict__ rj;
   const float *__restrict__ kappa;
+  const float2 *pf0, *pf1;         // rows the caller's epilogue reads at the same index (may be null)
   int N, L;
   float c1, c2, E;
 };
+
+// Rows ahead of the current one whose lines the mixed walker asks L2 for.
+// The walk visits one row per iteration with little arithmetic, so a load
+// issued one row ahead does not cover DRAM latency at the occupancy these
+// kernels run at; prefetches (no destination register) go further ahead.
+constexpr int kPrefetchRows = 6;
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of every array the walker and its epilogue read at row offset idx.
+template <bool S, bool Wp>
+__device__ __forceinline__ void prefetch_row(const MixedIn &in, size_t idx) {
+  if (S) {
+    prefetch_l2(in.hi + idx);
+    prefetch_l2(in.lo + idx);
+  }
+  if (Wp) prefetch_l2(in.w + idx);
+  prefetch_l2(in.diag + idx);
+  if (in.pf0) prefetch_l2(in.pf0 + idx);
+  if (in.pf1) prefetch_l2(in.pf1 + idx);
+}
 
 // Parts of the operand at one index.
 template <bool S, bool Wp>
@@ -150,8 +174,10 @@ __device__ __forceinline__ void mixed_walk_rows(const MixedIn &in, int i, int l0
   Parts<S, Wp> prev = load_parts<S, Wp>(in, (size_t)(l0 - 1) * N + i, l0 > 0);
   Parts<S, Wp> cur = load_parts<S, Wp>(in, (size_t)l0 * N + i, true);
   float a_cur = in.kappa[l0] * Er;
+  for (int q = 1; q < kPrefetchRows && l0 + q < l1; ++q) prefetch_row<S, Wp>(in, (size_t)(l0 + q) * N + i);
   for (int l = l0; l < l1; ++l) {
     const size_t idx = (size_t)l * N + i;
+    if (l + kPrefetchRows < l1) prefetch_row<S, Wp>(in, idx + (size_t)kPrefetchRows * N);
     const Parts<S, Wp> next = load_parts<S, Wp>(in, idx + N, l < L);
     const float a_next = in.kappa[l + 1] * Er;
     const Parts<S, Wp> m1 = load_parts<S, Wp>(in, idx - 1, i >= 1);
