@@ -38,7 +38,8 @@ namespace {
 using namespace common;
 using namespace stencil;
 
-constexpr int kChunkSegs = 64;   // 32-point row segments per reduction chunk
+constexpr int kChunkSegs = 64;   // 32-point row segments per reduction chunk (stencil kernels)
+constexpr int kChunkPts = kChunkSegs * 32;   // consecutive points per chunk (elementwise kernels)
 
 // Per-launch view of the engine's device state.
 struct BatchDev {
@@ -70,19 +71,19 @@ __device__ __forceinline__ int find_owner(const ChunkList &cl, int gc) {
 // chunk, reduce the instance's chunk partials in order; returns true in every
 // lane of the warp that must finish the instance (with the sum in `total`).
 __device__ __forceinline__ bool chunk_done(const BatchDev &B, const BatchInst &I, int inst, int ci,
-                                           double v, double &total) {
+                                           int nchunk, double v, double &total) {
   v = warp_sum(v);
   unsigned last = 0;
   if ((threadIdx.x & 31) == 0) {
     I.partial[ci] = v;
     __threadfence();
-    last = (atomicAdd(&B.ticket[inst], 1u) == (unsigned)(I.nchunk - 1)) ? 1u : 0u;
+    last = (atomicAdd(&B.ticket[inst], 1u) == (unsigned)(nchunk - 1)) ? 1u : 0u;
   }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return false;
   __threadfence();
   double s = 0.0;
-  for (int c = threadIdx.x & 31; c < I.nchunk; c += 32) s += __ldcg(&I.partial[c]);
+  for (int c = threadIdx.x & 31; c < nchunk; c += 32) s += __ldcg(&I.partial[c]);
   total = warp_sum(s);
   if ((threadIdx.x & 31) == 0) B.ticket[inst] = 0u;
   return true;
@@ -103,6 +104,24 @@ __device__ __forceinline__ void chunk_columns(const BatchInst &I, int ci, F &&f)
     const int i = jg * 32 + lane;
     if (i < I.N) f(i, l0, l1);
     s += l1 - l0;
+  }
+}
+
+// Visit chunk ci of an instance in the elementwise layout: the kChunkPts
+// consecutive points [ci*C, min((ci+1)*C, G)) of the l-major array, lane-strided
+// so that every load is coalesced; f(idx, i) with i = idx mod N, the radial index.
+template <typename F>
+__device__ __forceinline__ void chunk_points(const BatchInst &I, int ci, F &&f) {
+  const unsigned N = (unsigned)I.N;
+  const unsigned G = N * (unsigned)(I.L + 1);
+  const unsigned base = (unsigned)ci * kChunkPts + (threadIdx.x & 31);
+  const unsigned end = min(G, (unsigned)(ci + 1) * kChunkPts);
+  unsigned i = base % N;
+#pragma unroll 4
+  for (unsigned idx = base; idx < end; idx += 32) {
+    f((size_t)idx, (int)i);
+    i += 32;
+    while (i >= N) i -= N;
   }
 }
 
@@ -166,7 +185,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       });
     });
     double s;
-    if (chunk_done(B, I, inst, ci, acc, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk, acc, s) && (threadIdx.x & 31) == 0) {
       ls->alpha[j] = s * sig;
       ls->acoef[j] = -(s * sig) * sig;
     }
@@ -185,19 +204,15 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     double2 *un = I.work + (long long)(j + 1) * G;
     const double c = ls->acoef[j];
     double acc = 0.0;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * I.N + i;
-        const double2 zz = z[idx], uu = u[idx];
-        const double2 o = make_double2(__fma_rn(c, uu.x, zz.x), __fma_rn(c, uu.y, zz.y));
-        un[idx] = o;
-        acc = __fma_rn(o.x, o.x, acc);
-        acc = __fma_rn(o.y, o.y, acc);
-      }
+    chunk_points(I, ci, [&](size_t idx, int) {
+      const double2 zz = z[idx], uu = u[idx];
+      const double2 o = make_double2(__fma_rn(c, uu.x, zz.x), __fma_rn(c, uu.y, zz.y));
+      un[idx] = o;
+      acc = __fma_rn(o.x, o.x, acc);
+      acc = __fma_rn(o.y, o.y, acc);
     });
     double s;
-    if (chunk_done(B, I, inst, ci, acc, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
       const double beta = sqrt(s);
       ls->beta[j] = beta;
       const double sn = (beta > 0.0) ? 1.0 / beta : 0.0;
@@ -214,16 +229,13 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     const double2 *x = I.psi;
     double acc = 0.0;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const double2 v = x[(size_t)l * I.N + i];
-        acc = __fma_rn(v.x, v.x, acc);
-        acc = __fma_rn(v.y, v.y, acc);
-      }
+    chunk_points(I, ci, [&](size_t idx, int) {
+      const double2 v = x[idx];
+      acc = __fma_rn(v.x, v.x, acc);
+      acc = __fma_rn(v.y, v.y, acc);
     });
     double s;
-    if (chunk_done(B, I, inst, ci, acc, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
       LanczosScalars *ls = B.ls + inst;
       const double nrm = sqrt(s);
       ls->psinorm = nrm;
@@ -252,33 +264,29 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     __syncwarp();
     const double2 c0 = wcoef[wib][0];
     double acc = 0.0;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * I.N + i;
-        const double2 u0 = psi[idx];
-        double ox = __fma_rn(c0.x, u0.x, __dmul_rn(-c0.y, u0.y));
-        double oy = __fma_rn(c0.x, u0.y, __dmul_rn(c0.y, u0.x));
-        for (int jj = 1; jj < k; ++jj) {
-          const double2 u = U1[(size_t)(jj - 1) * G + idx];
-          const double2 c = wcoef[wib][jj];
-          ox = __fma_rn(c.x, u.x, ox);
-          ox = __fma_rn(-c.y, u.y, ox);
-          oy = __fma_rn(c.x, u.y, oy);
-          oy = __fma_rn(c.y, u.x, oy);
-        }
-        if (i >= I.mask_start) {
-          const double mv = mask[i];
-          ox = __dmul_rn(mv, ox);
-          oy = __dmul_rn(mv, oy);
-        }
-        psi[idx] = make_double2(ox, oy);
-        acc = __fma_rn(ox, ox, acc);
-        acc = __fma_rn(oy, oy, acc);
+    chunk_points(I, ci, [&](size_t idx, int i) {
+      const double2 u0 = psi[idx];
+      double ox = __fma_rn(c0.x, u0.x, __dmul_rn(-c0.y, u0.y));
+      double oy = __fma_rn(c0.x, u0.y, __dmul_rn(c0.y, u0.x));
+      for (int jj = 1; jj < k; ++jj) {
+        const double2 u = U1[(size_t)(jj - 1) * G + idx];
+        const double2 c = wcoef[wib][jj];
+        ox = __fma_rn(c.x, u.x, ox);
+        ox = __fma_rn(-c.y, u.y, ox);
+        oy = __fma_rn(c.x, u.y, oy);
+        oy = __fma_rn(c.y, u.x, oy);
       }
+      if (i >= I.mask_start) {
+        const double mv = mask[i];
+        ox = __dmul_rn(mv, ox);
+        oy = __dmul_rn(mv, oy);
+      }
+      psi[idx] = make_double2(ox, oy);
+      acc = __fma_rn(ox, ox, acc);
+      acc = __fma_rn(oy, oy, acc);
     });
     double s;
-    if (chunk_done(B, I, inst, ci, acc, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
       const double nrm = sqrt(s);
       ls->psinorm = nrm;
       ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     }
     const double accd = acc.value();
     double s;
-    if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
       ls->alpha[j] = s * sigd;
       ls->acoef[j] = -(s * sigd) * sigd;
     }
@@ -372,26 +380,22 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     float2 *un = I.mwork + (long long)(j + 1) * G;
     const float c = (float)ls->acoef[j];
     PairSum acc;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * I.N + i;
-        float2 uu;
-        if (u) {
-          uu = u[idx];
-        } else {
-          const float2 h = hi[idx], lw = lo[idx];
-          uu = make_float2(h.x + lw.x, h.y + lw.y);
-        }
-        const float2 zz = z[idx];
-        const float2 o = make_float2(fmaf(c, uu.x, zz.x), fmaf(c, uu.y, zz.y));
-        un[idx] = o;
-        acc.add(fmaf(o.x, o.x, o.y * o.y));
+    chunk_points(I, ci, [&](size_t idx, int) {
+      float2 uu;
+      if (u) {
+        uu = u[idx];
+      } else {
+        const float2 h = hi[idx], lw = lo[idx];
+        uu = make_float2(h.x + lw.x, h.y + lw.y);
       }
+      const float2 zz = z[idx];
+      const float2 o = make_float2(fmaf(c, uu.x, zz.x), fmaf(c, uu.y, zz.y));
+      un[idx] = o;
+      acc.add(fmaf(o.x, o.x, o.y * o.y));
     });
     const double accd = acc.value();
     double s;
-    if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, accd, s) && (threadIdx.x & 31) == 0) {
       const double beta = sqrt(s);
       ls->beta[j] = beta;
       const double sn = (beta > 0.0) ? 1.0 / beta : 0.0;
@@ -409,20 +413,16 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double2 *x = I.psi;
     float2 *hi = I.hi, *lo = I.lo;
     PairSum acc;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * I.N + i;
-        float2 h, lw;
-        split2(x[idx], h, lw);
-        hi[idx] = h;
-        lo[idx] = lw;
-        acc.add(fmaf(h.x, h.x, h.y * h.y));
-      }
+    chunk_points(I, ci, [&](size_t idx, int) {
+      float2 h, lw;
+      split2(x[idx], h, lw);
+      hi[idx] = h;
+      lo[idx] = lw;
+      acc.add(fmaf(h.x, h.x, h.y * h.y));
     });
     const double accd = acc.value();
     double s;
-    if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, accd, s) && (threadIdx.x & 31) == 0) {
       LanczosScalars *ls = B.ls + inst;
       const double nrm = sqrt(s);
       ls->psinorm = nrm;
@@ -456,39 +456,35 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     }
     __syncwarp();
     PairSum acc;
-    chunk_columns(I, ci, [&](int i, int l0, int l1) {
-#pragma unroll 4
-      for (int l = l0; l < l1; ++l) {
-        const size_t idx = (size_t)l * I.N + i;
-        float cx = 0.f, cy = 0.f;
-        for (int jj = 1; jj < k; ++jj) {
-          const float2 u = U1[(size_t)(jj - 1) * G + idx];
-          const float2 c = wcoef[wib][jj];
-          cx = fmaf(c.x, u.x, cx);
-          cx = fmaf(-c.y, u.y, cx);
-          cy = fmaf(c.x, u.y, cy);
-          cy = fmaf(c.y, u.x, cy);
-        }
-        const double2 p = psi[idx];
-        double ox = fma(c0.x, p.x, fma(-c0.y, p.y, (double)cx));
-        double oy = fma(c0.x, p.y, fma(c0.y, p.x, (double)cy));
-        if (i >= I.mask_start) {
-          const double mv = mask[i];
-          ox *= mv;
-          oy *= mv;
-        }
-        const double2 o = make_double2(ox, oy);
-        psi[idx] = o;
-        float2 h, lw;
-        split2(o, h, lw);
-        hi[idx] = h;
-        lo[idx] = lw;
-        acc.add(fmaf(h.x, h.x, h.y * h.y));
+    chunk_points(I, ci, [&](size_t idx, int i) {
+      float cx = 0.f, cy = 0.f;
+      for (int jj = 1; jj < k; ++jj) {
+        const float2 u = U1[(size_t)(jj - 1) * G + idx];
+        const float2 c = wcoef[wib][jj];
+        cx = fmaf(c.x, u.x, cx);
+        cx = fmaf(-c.y, u.y, cx);
+        cy = fmaf(c.x, u.y, cy);
+        cy = fmaf(c.y, u.x, cy);
       }
+      const double2 p = psi[idx];
+      double ox = fma(c0.x, p.x, fma(-c0.y, p.y, (double)cx));
+      double oy = fma(c0.x, p.y, fma(c0.y, p.x, (double)cy));
+      if (i >= I.mask_start) {
+        const double mv = mask[i];
+        ox *= mv;
+        oy *= mv;
+      }
+      const double2 o = make_double2(ox, oy);
+      psi[idx] = o;
+      float2 h, lw;
+      split2(o, h, lw);
+      hi[idx] = h;
+      lo[idx] = lw;
+      acc.add(fmaf(h.x, h.x, h.y * h.y));
     });
     const double accd = acc.value();
     double s;
-    if (chunk_done(B, I, inst, ci, accd, s) && (threadIdx.x & 31) == 0) {
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, accd, s) && (threadIdx.x & 31) == 0) {
       const double nrm = sqrt(s);
       ls->psinorm = nrm;
       ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
@@ -518,7 +514,7 @@ struct Layout {
 Layout layout_of(const tdse_instance_spec &s, int precision) {
   const size_t N = (size_t)s.N, Lp1 = (size_t)s.lmax + 1, G = N * Lp1, m = (size_t)s.krylov;
   const size_t nseg = ((N + 31) / 32) * Lp1;
-  const size_t nchunk = (nseg + kChunkSegs - 1) / kChunkSegs;
+  const size_t nchunk = std::max((nseg + kChunkSegs - 1) / kChunkSegs, (G + kChunkPts - 1) / kChunkPts);
   const bool mixed = precision == TDSE_MIXED;
   Layout L;
   size_t off = 0;
@@ -682,6 +678,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.m = s.krylov;
   I.nseg = (int)((size_t)((N + 31) / 32) * (L + 1));
   I.nchunk = (I.nseg + kChunkSegs - 1) / kChunkSegs;
+  I.nchunk_e = (int)((G + kChunkPts - 1) / kChunkPts);
   const double h2 = s.dr * s.dr;
   double c0;
   if (stencil == 5) {
@@ -894,14 +891,15 @@ int Engine::get_state(int slot, double *F) {
   return TDSE_OK;
 }
 
-// Append the chunk list of `ids` to the host staging; list_off receives its offset.
-int Engine::launch_lists(const std::vector<int> &ids, int &list_off) {
+// Append the chunk list of `ids` (stencil or elementwise chunks) to the host
+// staging; list_off receives its offset, the return value its chunk count.
+int Engine::launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off) {
   list_off = (int)hlists.size();
   hlists.insert(hlists.end(), ids.begin(), ids.end());
   int tot = 0;
   hlists.push_back(0);
   for (int id : ids) {
-    tot += hinst[id].nchunk;
+    tot += elementwise ? hinst[id].nchunk_e : hinst[id].nchunk;
     hlists.push_back(tot);
   }
   return tot;
@@ -930,7 +928,9 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     if (k > 0) ends.push_back(k);
   std::sort(ends.begin(), ends.end());
   ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
-  struct Seg { long n0, n1; int maxm; std::vector<int> off, nact, total; };
+  // per phase j: the stencil-chunk list (lanczos_a) and the elementwise one
+  // (lanczos_b, combine) of the slots still active in that phase
+  struct Seg { long n0, n1; int maxm; std::vector<int> off, nact, total, eoff, etotal; };
   std::vector<Seg> segs;
   hlists.clear();
   std::vector<int> need_norm;
@@ -938,7 +938,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     if (steps[q] > 0 && !norm_valid[slots[q]]) need_norm.push_back(slots[q]);
   std::sort(need_norm.begin(), need_norm.end());
   int norm_off = 0, norm_total = 0;
-  if (!need_norm.empty()) norm_total = launch_lists(need_norm, norm_off);
+  if (!need_norm.empty()) norm_total = launch_lists(need_norm, true, norm_off);
   long n0 = 0;
   for (long e : ends) {
     Seg sg;
@@ -954,11 +954,14 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
       std::vector<int> ph;
       for (int s : act)
         if (j == 0 || spec[s].krylov > j) ph.push_back(s);
-      int off = 0;
-      const int tot = launch_lists(ph, off);
+      int off = 0, eoff = 0;
+      const int tot = launch_lists(ph, false, off);
+      const int etot = launch_lists(ph, true, eoff);
       sg.off.push_back(off);
       sg.nact.push_back((int)ph.size());
       sg.total.push_back(tot);
+      sg.eoff.push_back(eoff);
+      sg.etotal.push_back(etot);
     }
     segs.push_back(std::move(sg));
     n0 = e;
@@ -1000,7 +1003,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     for (int s : need_norm) norm_valid[s] = 1;
   }
   for (const Seg &sg : segs) {
-    const ChunkList all = list_at(lists, sg.off[0], sg.nact[0], sg.total[0]);
+    const ChunkList all = list_at(lists, sg.eoff[0], sg.nact[0], sg.etotal[0]);
     for (long n = sg.n0; n < sg.n1; ++n) {
       B.E = E_dev + (size_t)n * capacity;
       for (int j = 0; j < sg.maxm; ++j) {
@@ -1018,8 +1021,8 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
         ++launches;
         EN_CUDA(cudaGetLastError(), "batch lanczos a");
         // U_{j+1} only for the instances that go on to iteration j + 1
-        if (j + 1 < sg.maxm && sg.total[j + 1] > 0) {
-          const ChunkList cn = list_at(lists, sg.off[j + 1], sg.nact[j + 1], sg.total[j + 1]);
+        if (j + 1 < sg.maxm && sg.etotal[j + 1] > 0) {
+          const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.nact[j + 1], sg.etotal[j + 1]);
           cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
           if (mixed) bt_lanczos_b_mixed<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
           else bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);

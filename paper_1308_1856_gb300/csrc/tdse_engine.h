@@ -25,7 +25,9 @@ struct BatchInst {
   int N, L, m;
   int mask_start;        // first radial index with mask != 1 (N if none)
   int nseg;              // 32-point row segments
-  int nchunk;            // reduction chunks
+  int nchunk;            // reduction chunks of the stencil kernels (row segments)
+  int nchunk_e;          // reduction chunks of the elementwise kernels (consecutive points)
+  int pad;
   double c1, c2;         // stencil coefficients (c0 is folded into diag)
   double2 *psi;          // (L+1) x N state, l-major
   const double *diag;    // FP64: c0 + l(l+1)/(2 r^2) - Z/r
@@ -35,7 +37,7 @@ struct BatchInst {
   float2 *hi, *lo;       // mixed: split of psi
   double2 *work;         // FP64 Krylov area: slot 0 = z, slots 1..m-1 = U_j
   float2 *mwork;         // mixed Krylov area, same slots
-  double *partial;       // nchunk chunk partial sums
+  double *partial;       // max(nchunk, nchunk_e) chunk partial sums
   double2 *ref0;         // N values: the p_ground reference (1s state of the grid)
 };
 
@@ -85,7 +87,7 @@ class Engine {
 
  private:
   int ensure(void **p, size_t &cap, size_t bytes, const char *what);
-  int launch_lists(const std::vector<int> &ids, int &list_off);
+  int launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off);
   cudaEvent_t prof_begin(int kind);
   void prof_end(cudaEvent_t e);
   int prof_collect();
