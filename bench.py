@@ -155,9 +155,19 @@ def start_state(seed: int = 31):
     return W.smooth_state(CFG.N, CFG.dr, CFG.lmax, seed=seed, lmax_populated=20)
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu captures
-# summarised under profiles/ (null once a kernel changes after its capture)
-MEASURED_TRAFFIC = {"lanczos_a": 19.9e6, "taylor_stage": 12.4e6, "rk_stage": 12.4e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# grid point of one launch, from the ncu captures summarised under profiles/:
+# the batched kernels on the first 16 instances of the batched configuration
+# (phases where all 16 are active, 10.66M points per launch), scaled here to a
+# full launch by its points; the single-instance kernels on the at-scale grid
+# (512000 points).  An entry is removed when its kernel changes after capture.
+MEASURED_TRAFFIC_PER_POINT = {
+    ("batched", "fp64", "lanczos_a"): (531.5e6 + 169.3e6) / 10664737,
+    ("batched", "fp64", "lanczos_b"): (341.8e6 + 142.0e6) / 10664737,
+    ("batched", "mixed", "lanczos_a"): (313.2e6 + 78.1e6) / 10664737,
+    ("batched", "mixed", "lanczos_b"): (171.2e6 + 56.2e6) / 10664737,
+    ("single", "fp64", "taylor_stage"): 20.6e6 / 512000,
+}
 
 
 def make_handle(stream_ptr: int, precision: str = "fp64"):
@@ -400,13 +410,17 @@ def run_ours(args, ws, rank, local):
     kernel_share = {f"{k}/{p}/{kind}": v[0] for (kind, p, k), v in prof.items()}
     tot_k = sum(kernel_share.values())
 
+    def traffic_of(key, points_per_launch):
+        per = MEASURED_TRAFFIC_PER_POINT.get((key[0], key[1], key[2]))
+        return None if per is None else per * points_per_launch
+
     def roof_fp64(key):
         ms, n, pts = prof[key]
         flops = KERNEL_FLOPS_PER_GP.get(key[2], H5_FLOPS) * pts
         achieved = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": f"{key[2]} ({key[0]}, fp64)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": MEASURED_TRAFFIC.get(key[2]) if key[0] == "single" else None,
+                "traffic": traffic_of(key, pts / n),
                 "flops_per_launch": flops / n, "avg_launch_ms": ms / n,
                 "peak_source": "FP64: 152 SMs x 2 FMA/clk/SM x 2 flop x 2070 MHz (derived)"}
 
@@ -415,7 +429,8 @@ def run_ours(args, ws, rank, local):
         nbytes = MIXED_BYTES_PER_GP[key[2]] * pts
         achieved = nbytes / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "kernel": f"{key[2]} ({key[0]}, mixed)", "achieved": achieved,
-                "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS,
+                "traffic": traffic_of(key, pts / n),
                 "bytes_per_launch": nbytes / n, "avg_launch_ms": ms / n,
                 "peak_source": "HBM copy bandwidth of measured (MEASURED_PEAKS.json)"}
 

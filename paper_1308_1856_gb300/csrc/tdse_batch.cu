@@ -368,13 +368,15 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   });
 }
 
+// SPLIT: U_j is U_0 = psi, read as its split (j = 0).
+template <bool SPLIT>
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_lanczos_b_mixed(BatchDev B, ChunkList cl, int j) {
   for_my_chunks(cl, [&](int inst, int ci) {
     const BatchInst I = B.inst[inst];
     LanczosScalars *ls = B.ls + inst;
     const long long G = (long long)I.N * (I.L + 1);
-    const float2 *u = (j == 0) ? nullptr : I.mwork + (long long)j * G;
+    const float2 *u = I.mwork + (long long)j * G;
     const float2 *hi = I.hi, *lo = I.lo;
     const float2 *z = I.mwork;
     float2 *un = I.mwork + (long long)(j + 1) * G;
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     PairSum acc;
     chunk_points(I, ci, [&](size_t idx, int) {
       float2 uu;
-      if (u) {
+      if (!SPLIT) {
         uu = u[idx];
       } else {
         const float2 h = hi[idx], lw = lo[idx];
@@ -1024,8 +1026,12 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
         if (j + 1 < sg.maxm && sg.etotal[j + 1] > 0) {
           const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.nact[j + 1], sg.etotal[j + 1]);
           cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
-          if (mixed) bt_lanczos_b_mixed<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-          else bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+          if (mixed) {
+            if (j == 0) bt_lanczos_b_mixed<true><<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+            else bt_lanczos_b_mixed<false><<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+          } else {
+            bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
+          }
           prof_end(pb);
           ++launches;
           EN_CUDA(cudaGetLastError(), "batch lanczos b");

@@ -156,6 +156,8 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 
 // Lanczos iteration j, second half (mixed): U_{j+1} = z - alpha_j sigma_j U_j;
 // beta_j = ||U_{j+1}|| (FP32 products, FP32-pair sums, FP64 reduction).
+// SPLIT: U_j is U_0 = psi, read as its split (j = 0).
+template <bool SPLIT>
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     mx_lanczos_b_kernel(size_t G, int j, const float2 *__restrict__ z, const float2 *__restrict__ u,
                         const float2 *__restrict__ u_hi, const float2 *__restrict__ u_lo,
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const size_t idx = (size_t)gi * 32 + lane;
     if (idx < G) {
       float2 uu;
-      if (u) {
+      if (!SPLIT) {
         uu = u[idx];
       } else {
         const float2 h = u_hi[idx], l = u_lo[idx];
@@ -422,7 +424,10 @@ cudaError_t launch_mx_lanczos_b(const Geometry &g, int j, const float2 *z, const
                                 const float2 *hi, const float2 *lo, float2 *unext,
                                 Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  mx_lanczos_b_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, hi, lo, unext, red, ls);
+  if (u)
+    mx_lanczos_b_kernel<false><<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, hi, lo, unext, red, ls);
+  else
+    mx_lanczos_b_kernel<true><<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, hi, lo, unext, red, ls);
   return cudaGetLastError();
 }
 
