@@ -229,6 +229,7 @@ class BatchRow:
                   ncycles=x.ncycles, absorber_r=x.N * x.dr - BATCH_ABSORBER) for x in self.specs]
         self.b = Batch(d, stencil=5, precision=prec)
         self.b.set_stream(stream_ptr)
+        self.schedule = self.b.autotune()     # before the warm-up; not timed
         self.gp = self.b.points
         self.G = [x.N * (x.lmax + 1) for x in self.specs]
         self.e2e_bytes = (self.gp * 16, self.gp * 16)
@@ -479,6 +480,7 @@ def run_ours(args, ws, rank, local):
         "rows_gp_steps_per_s": {r.name: r.gp * args.steps / (row_ms[r.name] * 1e-3) for r in rows},
         "roofline": roofline, "roofline_fp64": roofline_fp64, "roofline_mixed": roofline_mixed,
         "kernel_ms_share": {k: round(v / tot_k, 4) for k, v in kernel_share.items()},
+        "batched_schedules": {r.name: r.schedule for r in rows if r.kind == "batched"},
         "e2e": {"value": e2e_value, "unit": "grid-point*steps/s",
                 "h2d_bytes_per_step": sum(r.e2e_bytes[0] for r in rows),
                 "d2h_bytes_per_step": sum(r.e2e_bytes[1] for r in rows), "steps": e2e_steps},

@@ -287,6 +287,30 @@ long long tdse_batch_launch_count(const tdse_batch_t *b);
 int tdse_batch_profile(tdse_batch_t *b, int enable);
 int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches);
 
+/*
+ * Launch schedule of the batched kernels: the rows the stencil kernels
+ * prefetch ahead into L2 (0, 3, 6 or 10), and the blocks per SM of the
+ * stencil and of the elementwise kernels (1 or 2, of 512 threads).  Results
+ * do not depend on the schedule (bitwise): every reduction is split into
+ * fixed per-instance chunks whatever the grid.  Segments of three or more
+ * steps with an unchanged set of instances run as one captured CUDA graph of
+ * a step, replayed once per step.
+ *
+ * tdse_batch_autotune times every schedule on Lanczos phase 0 of the batch's
+ * instances (launches whose outputs the next step recomputes, so the state is
+ * untouched), keeps the fastest and returns it in *chosen (may be NULL);
+ * synchronous.  tdse_batch_set_schedule installs one (TDSE_ERR_ARG outside
+ * the choices above); tdse_batch_get_schedule reads the current one.
+ */
+typedef struct {
+  int prefetch_rows;
+  int stencil_blocks_per_sm;
+  int elem_blocks_per_sm;
+} tdse_schedule;
+int tdse_batch_autotune(tdse_batch_t *b, tdse_schedule *chosen);
+int tdse_batch_set_schedule(tdse_batch_t *b, const tdse_schedule *s);
+int tdse_batch_get_schedule(const tdse_batch_t *b, tdse_schedule *s);
+
 /* ------------------------------------------------------------------------ */
 /* Served instances: continuous batching under a device-memory budget.       */
 /* ------------------------------------------------------------------------ */
@@ -355,6 +379,11 @@ typedef struct {
   long long launches;   /* kernel launches issued since creation */
 } tdse_server_stats_t;
 int tdse_server_stats(const tdse_server_t *s, tdse_server_stats_t *st);
+
+/* Schedule of the server's launches, as tdse_batch_*_schedule; autotune times
+ * the schedules on the requests running now (none running: nothing changes). */
+int tdse_server_autotune(tdse_server_t *s, tdse_schedule *chosen);
+int tdse_server_set_schedule(tdse_server_t *s, const tdse_schedule *sch);
 
 /* Per-kernel timing, as tdse_profile / tdse_profile_read. */
 int tdse_server_profile(tdse_server_t *s, int enable);

@@ -247,6 +247,21 @@ class Batch:
     def launches(self) -> int:
         return C.tdse_batch_launch_count(self.h)
 
+    def autotune(self) -> dict:
+        """Time every launch schedule on this batch and keep the fastest."""
+        sch = C.tdse_schedule()
+        self._check(C.tdse_batch_autotune(self.h, ctypes.byref(sch)))
+        return {k: getattr(sch, k) for k, _ in sch._fields_}
+
+    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int):
+        sch = C.tdse_schedule(int(prefetch_rows), int(stencil_blocks_per_sm), int(elem_blocks_per_sm))
+        self._check(C.tdse_batch_set_schedule(self.h, ctypes.byref(sch)))
+
+    def schedule(self) -> dict:
+        sch = C.tdse_schedule()
+        self._check(C.tdse_batch_get_schedule(self.h, ctypes.byref(sch)))
+        return {k: getattr(sch, k) for k, _ in sch._fields_}
+
 
 class Server:
     """Continuous batching of Lanczos requests under a device-memory budget
@@ -339,6 +354,16 @@ class Server:
         st = C.tdse_server_stats_t()
         self._check(C.tdse_server_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def autotune(self) -> dict:
+        """Time every launch schedule on the running requests and keep the fastest."""
+        sch = C.tdse_schedule()
+        self._check(C.tdse_server_autotune(self.h, ctypes.byref(sch)))
+        return {k: getattr(sch, k) for k, _ in sch._fields_}
+
+    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int):
+        sch = C.tdse_schedule(int(prefetch_rows), int(stencil_blocks_per_sm), int(elem_blocks_per_sm))
+        self._check(C.tdse_server_set_schedule(self.h, ctypes.byref(sch)))
 
     def profile(self, enable: bool):
         self._check(C.tdse_server_profile(self.h, 1 if enable else 0))

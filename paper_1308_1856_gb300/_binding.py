@@ -41,6 +41,11 @@ class tdse_instance_spec(ctypes.Structure):
                 ("dt", ctypes.c_double), ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double)]
 
 
+class tdse_schedule(ctypes.Structure):
+    _fields_ = [("prefetch_rows", ctypes.c_int), ("stencil_blocks_per_sm", ctypes.c_int),
+                ("elem_blocks_per_sm", ctypes.c_int)]
+
+
 class tdse_server_stats_t(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_longlong), ("running", ctypes.c_longlong),
                 ("resident", ctypes.c_longlong), ("finished_total", ctypes.c_longlong),
@@ -92,6 +97,11 @@ SIGNATURES = {
     "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_batch_profile": (_c_int, [_vp, _c_int]),
     "tdse_batch_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "tdse_batch_autotune": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
+    "tdse_batch_set_schedule": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
+    "tdse_batch_get_schedule": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
+    "tdse_server_autotune": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
+    "tdse_server_set_schedule": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
     "tdse_server_instance_bytes": (ctypes.c_ulonglong, [ctypes.POINTER(tdse_instance_spec), _c_int]),
     "tdse_server_create": (_c_int, [ctypes.c_ulonglong, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "tdse_server_destroy": (_c_int, [_vp]),
@@ -181,6 +191,11 @@ tdse_batch_points = _fn("tdse_batch_points")
 tdse_batch_launch_count = _fn("tdse_batch_launch_count")
 tdse_batch_profile = _fn("tdse_batch_profile")
 tdse_batch_profile_read = _fn("tdse_batch_profile_read")
+tdse_batch_autotune = _fn("tdse_batch_autotune")
+tdse_batch_set_schedule = _fn("tdse_batch_set_schedule")
+tdse_batch_get_schedule = _fn("tdse_batch_get_schedule")
+tdse_server_autotune = _fn("tdse_server_autotune")
+tdse_server_set_schedule = _fn("tdse_server_set_schedule")
 tdse_server_instance_bytes = _fn("tdse_server_instance_bytes")
 tdse_server_create = _fn("tdse_server_create")
 tdse_server_destroy = _fn("tdse_server_destroy")

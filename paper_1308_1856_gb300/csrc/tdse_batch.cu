@@ -41,20 +41,12 @@ using namespace stencil;
 constexpr int kChunkSegs = 64;   // 32-point row segments per reduction chunk (stencil kernels)
 constexpr int kChunkPts = kChunkSegs * 32;   // consecutive points per chunk (elementwise kernels)
 
-// Per-launch view of the engine's device state.
-struct BatchDev {
-  const BatchInst *inst;
-  LanczosScalars *ls;
-  unsigned *ticket;      // per-slot arrival counters (zero between launches)
-  int *status;
-  const double *E;       // field of every slot at this step's mid-point
-};
+__device__ __forceinline__ double field_of(const BatchDev &B, int inst) {
+  return B.E[(size_t)(*B.step) * (size_t)B.cap + inst];
+}
 
-struct ChunkList {
-  const int *act;        // active slots
-  const int *cpre;       // prefix sums of their chunk counts (nact + 1)
-  int nact, total;
-};
+// Advance the run's step counter (one thread, after every step's last launch).
+__global__ void bt_next_step(int *step) { *step += 1; }
 
 // Index in the active list of the instance that owns global chunk gc.
 __device__ __forceinline__ int find_owner(const ChunkList &cl, int gc) {
@@ -150,11 +142,11 @@ __device__ __forceinline__ StencilIn fp64_in(const BatchDev &B, const BatchInst 
   in.L = I.L;
   in.c1 = I.c1;
   in.c2 = I.c2;
-  in.E = B.E[inst];
+  in.E = field_of(B, inst);
   return in;
 }
 
-template <int ST>
+template <int ST, int PF>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     bt_lanczos_a_fp64(BatchDev B, ChunkList cl, int j) {
   for_my_chunks(cl, [&](int inst, int ci) {
@@ -169,7 +161,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const StencilIn in = fp64_in(B, I, inst, u);
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
-      walk_rows<ST>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
+      walk_rows<ST, PF>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
         double2 o;
         if (j > 0) {
           const double2 pv = up[idx];
@@ -312,11 +304,11 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   in.L = I.L;
   in.c1 = (float)I.c1;
   in.c2 = (float)I.c2;
-  in.E = (float)B.E[inst];
+  in.E = (float)field_of(B, inst);
   return in;
 }
 
-template <int ST>
+template <int ST, int PF>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     bt_lanczos_a_mixed(BatchDev B, ChunkList cl, int j) {
   for_my_chunks(cl, [&](int inst, int ci) {
@@ -348,7 +340,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     };
     if (j == 0) {
       const MixedIn in = mixed_in(B, I, inst, hi, lo, nullptr);
-      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false>(in, i, l0, l1, epi); });
+      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false, PF>(in, i, l0, l1, epi); });
     } else {
       MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
       if (uprev) {
@@ -357,7 +349,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
         in.pf0 = hi;
         in.pf1 = lo;
       }
-      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true>(in, i, l0, l1, epi); });
+      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true, PF>(in, i, l0, l1, epi); });
     }
     const double accd = acc.value();
     double s;
@@ -591,6 +583,7 @@ size_t instance_bytes(const tdse_instance_spec &s, int precision) {
 
 Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
+  for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
   cudaFree(inst);
   cudaFree(ls);
   cudaFree(ticket);
@@ -598,6 +591,7 @@ Engine::~Engine() {
   cudaFree(m_dev);
   cudaFree(dt_dev);
   cudaFree(E_dev);
+  cudaFree(step_dev);
   cudaFree(lists);
   cudaFree(obs_partials);   // obs_out points into this block
   cudaFree(obs_ticket);
@@ -907,6 +901,160 @@ int Engine::launch_lists(const std::vector<int> &ids, bool elementwise, int &lis
   return tot;
 }
 
+namespace {
+
+constexpr long kGraphMinSteps = 3;   // segments this long replay one captured step graph
+
+template <int ST, int PF>
+void launch_a_pf(bool mixed, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  if (mixed) bt_lanczos_a_mixed<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
+  else bt_lanczos_a_fp64<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
+}
+
+template <int ST>
+void launch_a_st(bool mixed, int pf, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl,
+                 int j) {
+  switch (pf) {
+    case 0: launch_a_pf<ST, 0>(mixed, grid, st, B, cl, j); break;
+    case 3: launch_a_pf<ST, 3>(mixed, grid, st, B, cl, j); break;
+    case 10: launch_a_pf<ST, 10>(mixed, grid, st, B, cl, j); break;
+    default: launch_a_pf<ST, 6>(mixed, grid, st, B, cl, j); break;
+  }
+}
+
+}  // namespace
+
+void Engine::drop_graphs() {
+  if (graphs.empty()) return;
+  cudaStreamSynchronize(stream);
+  for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
+  graphs.clear();
+}
+
+BatchDev Engine::device_view() const {
+  BatchDev B;
+  B.inst = inst;
+  B.ls = ls;
+  B.ticket = ticket;
+  B.status = status;
+  B.E = E_dev;
+  B.step = step_dev;
+  B.cap = capacity;
+  return B;
+}
+
+void Engine::build_segment(Segment &sg, const std::vector<int> &act) {
+  sg.maxm = 0;
+  for (int s : act) sg.maxm = std::max(sg.maxm, spec[s].krylov);
+  for (int j = 0; j <= sg.maxm; ++j) {
+    std::vector<int> ph;
+    for (int s : act)
+      if (j == 0 || spec[s].krylov > j) ph.push_back(s);
+    int off = 0, eoff = 0;
+    const int tot = launch_lists(ph, false, off);
+    const int etot = launch_lists(ph, true, eoff);
+    sg.off.push_back(off);
+    sg.nact.push_back((int)ph.size());
+    sg.total.push_back(tot);
+    sg.eoff.push_back(eoff);
+    sg.etotal.push_back(etot);
+  }
+}
+
+// Upload the staged field table (nE entries) and chunk lists; zero the step counter.
+int Engine::upload_run(size_t nE) {
+  int rc = ensure(reinterpret_cast<void **>(&E_dev), E_cap, sizeof(double) * std::max<size_t>(1, nE),
+                  "field table");
+  if (rc) return rc;
+  rc = ensure(reinterpret_cast<void **>(&lists), lists_cap, sizeof(int) * std::max<size_t>(1, hlists.size()),
+              "chunk lists");
+  if (rc) return rc;
+  if (!step_dev && cudaMalloc(&step_dev, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    step_dev = nullptr;
+    return fail(TDSE_ERR_OOM, "step counter");
+  }
+  cudaStream_t st = stream;
+  if (nE) EN_CUDA(cudaMemcpyAsync(E_dev, hE.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, st), "field upload");
+  if (!hlists.empty())
+    EN_CUDA(cudaMemcpyAsync(lists, hlists.data(), sizeof(int) * hlists.size(), cudaMemcpyHostToDevice, st),
+            "list upload");
+  EN_CUDA(cudaMemsetAsync(step_dev, 0, sizeof(int), st), "step counter");
+  return TDSE_OK;
+}
+
+int Engine::norm_pass(const BatchDev &B, const std::vector<int> &ids, int off, int total) {
+  const ChunkList cl = list_at(lists, off, (int)ids.size(), total);
+  const unsigned egrid = (unsigned)(sms * sched.eblocks);
+  cudaEvent_t pe = prof_begin(TDSE_K_NORM);
+  if (precision == TDSE_MIXED) bt_split_mixed<<<egrid, kElemThreads, 0, stream>>>(B, cl);
+  else bt_norm_fp64<<<egrid, kElemThreads, 0, stream>>>(B, cl);
+  prof_end(pe);
+  ++launches;
+  EN_CUDA(cudaGetLastError(), "batch norm");
+  for (int s : ids) norm_valid[s] = 1;
+  return TDSE_OK;
+}
+
+int Engine::launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s) {
+  const unsigned grid = (unsigned)(sms * s.sblocks);
+  const bool mixed = precision == TDSE_MIXED;
+  if (stencil == 5) launch_a_st<5>(mixed, s.pf, grid, stream, B, cl, j);
+  else launch_a_st<3>(mixed, s.pf, grid, stream, B, cl, j);
+  EN_CUDA(cudaGetLastError(), "batch lanczos a");
+  return TDSE_OK;
+}
+
+int Engine::launch_b(const BatchDev &B, const ChunkList &cn, int j, const Schedule &s) {
+  const unsigned grid = (unsigned)(sms * s.eblocks);
+  if (precision == TDSE_MIXED) {
+    if (j == 0) bt_lanczos_b_mixed<true><<<grid, kElemThreads, 0, stream>>>(B, cn, j);
+    else bt_lanczos_b_mixed<false><<<grid, kElemThreads, 0, stream>>>(B, cn, j);
+  } else {
+    bt_lanczos_b_fp64<<<grid, kElemThreads, 0, stream>>>(B, cn, j);
+  }
+  EN_CUDA(cudaGetLastError(), "batch lanczos b");
+  return TDSE_OK;
+}
+
+// Every launch of one step of a segment; count receives the number of kernels.
+int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
+  count = 0;
+  int rc;
+  const ChunkList all = list_at(lists, sg.eoff[0], sg.nact[0], sg.etotal[0]);
+  for (int j = 0; j < sg.maxm; ++j) {
+    const ChunkList cl = list_at(lists, sg.off[j], sg.nact[j], sg.total[j]);
+    if (cl.total == 0) break;
+    cudaEvent_t pa = prof_begin(TDSE_K_LANCZOS_A);
+    if ((rc = launch_a(B, cl, j, sched))) return rc;
+    prof_end(pa);
+    ++count;
+    // U_{j+1} only for the instances that go on to iteration j + 1
+    if (j + 1 < sg.maxm && sg.etotal[j + 1] > 0) {
+      const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.nact[j + 1], sg.etotal[j + 1]);
+      cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
+      if ((rc = launch_b(B, cn, j, sched))) return rc;
+      prof_end(pb);
+      ++count;
+    }
+  }
+  cudaEvent_t px = prof_begin(TDSE_K_LANCZOS_EXPM);
+  EN_CUDA(launch_lanczos_expm_batched(all.nact, all.act, m_dev, dt_dev, ls, stream), "batch expm");
+  prof_end(px);
+  ++count;
+  const unsigned egrid = (unsigned)(sms * sched.eblocks);
+  cudaEvent_t pc = prof_begin(TDSE_K_LANCZOS_COMBINE);
+  if (precision == TDSE_MIXED) bt_combine_mixed<<<egrid, kElemThreads, 0, stream>>>(B, all);
+  else bt_combine_fp64<<<egrid, kElemThreads, 0, stream>>>(B, all);
+  prof_end(pc);
+  ++count;
+  EN_CUDA(cudaGetLastError(), "batch combine");
+  bt_next_step<<<1, 1, 0, stream>>>(step_dev);
+  ++count;
+  EN_CUDA(cudaGetLastError(), "batch step counter");
+  return TDSE_OK;
+}
+
 int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   if (poisoned) return TDSE_ERR_STATE;
   if (slots.size() != steps.size()) return fail(TDSE_ERR_ARG, "slots and steps differ in length");
@@ -920,20 +1068,17 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     kmax = std::max(kmax, steps[q]);
   }
   if (kmax == 0) return TDSE_OK;
+  drop_graphs();
   // launch errors are read with cudaGetLastError: drop an earlier, unrelated
   // non-sticky error of this thread first (a sticky one fails the launches too)
   cudaGetLastError();
-  const bool mixed = precision == TDSE_MIXED;
   // segments of the run: the active set changes only where a slot finishes
   std::vector<long> ends;
   for (long k : steps)
     if (k > 0) ends.push_back(k);
   std::sort(ends.begin(), ends.end());
   ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
-  // per phase j: the stencil-chunk list (lanczos_a) and the elementwise one
-  // (lanczos_b, combine) of the slots still active in that phase
-  struct Seg { long n0, n1; int maxm; std::vector<int> off, nact, total, eoff, etotal; };
-  std::vector<Seg> segs;
+  std::vector<Segment> segs;
   hlists.clear();
   std::vector<int> need_norm;
   for (size_t q = 0; q < slots.size(); ++q)
@@ -943,37 +1088,19 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   if (!need_norm.empty()) norm_total = launch_lists(need_norm, true, norm_off);
   long n0 = 0;
   for (long e : ends) {
-    Seg sg;
+    Segment sg;
     sg.n0 = n0;
     sg.n1 = e;
     std::vector<int> act;
     for (size_t q = 0; q < slots.size(); ++q)
       if (steps[q] >= e) act.push_back(slots[q]);
     std::sort(act.begin(), act.end());
-    sg.maxm = 0;
-    for (int s : act) sg.maxm = std::max(sg.maxm, spec[s].krylov);
-    for (int j = 0; j <= sg.maxm; ++j) {
-      std::vector<int> ph;
-      for (int s : act)
-        if (j == 0 || spec[s].krylov > j) ph.push_back(s);
-      int off = 0, eoff = 0;
-      const int tot = launch_lists(ph, false, off);
-      const int etot = launch_lists(ph, true, eoff);
-      sg.off.push_back(off);
-      sg.nact.push_back((int)ph.size());
-      sg.total.push_back(tot);
-      sg.eoff.push_back(eoff);
-      sg.etotal.push_back(etot);
-    }
+    build_segment(sg, act);
     segs.push_back(std::move(sg));
     n0 = e;
   }
   // field at the mid-point of every step: E[n * capacity + slot]
   const size_t nE = (size_t)kmax * capacity;
-  int rc = ensure(reinterpret_cast<void **>(&E_dev), E_cap, sizeof(double) * nE, "field table");
-  if (rc) return rc;
-  rc = ensure(reinterpret_cast<void **>(&lists), lists_cap, sizeof(int) * std::max<size_t>(1, hlists.size()), "chunk lists");
-  if (rc) return rc;
   hE.assign(nE, 0.0);
   for (size_t q = 0; q < slots.size(); ++q) {
     const int s = slots[q];
@@ -983,73 +1110,144 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
       hE[(size_t)n * capacity + s] = pulse_at(sp, tn + 0.5 * sp.dt);
     }
   }
-  cudaStream_t st = stream;
-  EN_CUDA(cudaMemcpyAsync(E_dev, hE.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, st), "field upload");
-  EN_CUDA(cudaMemcpyAsync(lists, hlists.data(), sizeof(int) * hlists.size(), cudaMemcpyHostToDevice, st), "list upload");
-  const unsigned sgrid = (unsigned)(sms * kStencilBlocksPerSM);
-  const unsigned egrid = (unsigned)(sms * kElemBlocksPerSM);
-  BatchDev B;
-  B.inst = inst;
-  B.ls = ls;
-  B.ticket = ticket;
-  B.status = status;
-  B.E = E_dev;
-  if (!need_norm.empty()) {
-    const ChunkList cl = list_at(lists, norm_off, (int)need_norm.size(), norm_total);
-    cudaEvent_t pe = prof_begin(TDSE_K_NORM);
-    if (mixed) bt_split_mixed<<<egrid, kElemThreads, 0, st>>>(B, cl);
-    else bt_norm_fp64<<<egrid, kElemThreads, 0, st>>>(B, cl);
-    prof_end(pe);
-    ++launches;
-    EN_CUDA(cudaGetLastError(), "batch norm");
-    for (int s : need_norm) norm_valid[s] = 1;
-  }
-  for (const Seg &sg : segs) {
-    const ChunkList all = list_at(lists, sg.eoff[0], sg.nact[0], sg.etotal[0]);
-    for (long n = sg.n0; n < sg.n1; ++n) {
-      B.E = E_dev + (size_t)n * capacity;
-      for (int j = 0; j < sg.maxm; ++j) {
-        const ChunkList cl = list_at(lists, sg.off[j], sg.nact[j], sg.total[j]);
-        if (cl.total == 0) break;
-        cudaEvent_t pa = prof_begin(TDSE_K_LANCZOS_A);
-        if (mixed) {
-          if (stencil == 5) bt_lanczos_a_mixed<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-          else bt_lanczos_a_mixed<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-        } else {
-          if (stencil == 5) bt_lanczos_a_fp64<5><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-          else bt_lanczos_a_fp64<3><<<sgrid, kBlockJ, 0, st>>>(B, cl, j);
-        }
-        prof_end(pa);
-        ++launches;
-        EN_CUDA(cudaGetLastError(), "batch lanczos a");
-        // U_{j+1} only for the instances that go on to iteration j + 1
-        if (j + 1 < sg.maxm && sg.etotal[j + 1] > 0) {
-          const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.nact[j + 1], sg.etotal[j + 1]);
-          cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
-          if (mixed) {
-            if (j == 0) bt_lanczos_b_mixed<true><<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-            else bt_lanczos_b_mixed<false><<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-          } else {
-            bt_lanczos_b_fp64<<<egrid, kElemThreads, 0, st>>>(B, cn, j);
-          }
-          prof_end(pb);
-          ++launches;
-          EN_CUDA(cudaGetLastError(), "batch lanczos b");
-        }
+  int rc = upload_run(nE);
+  if (rc) return rc;
+  const BatchDev B = device_view();
+  if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) return rc;
+  for (const Segment &sg : segs) {
+    const long nst = sg.n1 - sg.n0;
+    int count = 0;
+    if (!profiling && nst >= kGraphMinSteps) {
+      // capture one step and replay it: the step counter on the device selects
+      // each step's field
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      EN_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      rc = enqueue_step(B, sg, count);
+      const cudaError_t ec = cudaStreamEndCapture(stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
       }
-      cudaEvent_t px = prof_begin(TDSE_K_LANCZOS_EXPM);
-      EN_CUDA(launch_lanczos_expm_batched(all.nact, all.act, m_dev, dt_dev, ls, st), "batch expm");
-      prof_end(px);
-      ++launches;
-      cudaEvent_t pc = prof_begin(TDSE_K_LANCZOS_COMBINE);
-      if (mixed) bt_combine_mixed<<<egrid, kElemThreads, 0, st>>>(B, all);
-      else bt_combine_fp64<<<egrid, kElemThreads, 0, st>>>(B, all);
-      prof_end(pc);
-      ++launches;
-      EN_CUDA(cudaGetLastError(), "batch combine");
+      EN_CUDA(ec, "end capture");
+      const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      EN_CUDA(ei, "instantiate step graph");
+      graphs.push_back(ge);
+      for (long n = 0; n < nst; ++n) EN_CUDA(cudaGraphLaunch(ge, stream), "step graph launch");
+      launches += (long long)count * nst;
+    } else {
+      for (long n = 0; n < nst; ++n) {
+        if ((rc = enqueue_step(B, sg, count))) return rc;
+        launches += count;
+      }
     }
   }
   for (size_t q = 0; q < slots.size(); ++q) nstep[slots[q]] += steps[q];
+  return TDSE_OK;
+}
+
+int Engine::set_schedule(const Schedule &s) {
+  bool pf_ok = false;
+  for (int p : kPfChoices) pf_ok = pf_ok || p == s.pf;
+  if (!pf_ok || s.sblocks < 1 || s.sblocks > kStencilBlocksPerSM || s.eblocks < 1 || s.eblocks > kElemBlocksPerSM)
+    return fail(TDSE_ERR_ARG, "schedule outside the tuned choices");
+  sched = s;
+  return TDSE_OK;
+}
+
+int Engine::autotune(const std::vector<int> &slots) {
+  if (poisoned) return TDSE_ERR_STATE;
+  std::vector<int> act;
+  for (int s : slots) {
+    if (s < 0 || s >= capacity || !placed[s]) return fail(TDSE_ERR_ARG, "bad slot");
+    act.push_back(s);
+  }
+  if (act.empty()) return TDSE_OK;
+  std::sort(act.begin(), act.end());
+  drop_graphs();
+  cudaGetLastError();
+  hlists.clear();
+  std::vector<int> need_norm;
+  for (int s : act)
+    if (!norm_valid[s]) need_norm.push_back(s);
+  int norm_off = 0, norm_total = 0;
+  if (!need_norm.empty()) norm_total = launch_lists(need_norm, true, norm_off);
+  Segment sg;
+  sg.n0 = 0;
+  sg.n1 = 1;
+  build_segment(sg, act);
+  hE.assign((size_t)capacity, 0.0);
+  for (int s : act) hE[s] = pulse_at(spec[s], (double)nstep[s] * spec[s].dt + 0.5 * spec[s].dt);
+  int rc = upload_run((size_t)capacity);
+  if (rc) return rc;
+  const BatchDev B = device_view();
+  const bool was_profiling = profiling;
+  profiling = false;
+  if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) {
+    profiling = was_profiling;
+    return rc;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    profiling = was_profiling;
+    if (e0) cudaEventDestroy(e0);
+    return fail(TDSE_ERR_CUDA, "autotune events");
+  }
+  // phase 0 launches rewrite only what the next step recomputes (z, U_1 and
+  // their scalars), so timing them leaves the state untouched
+  const ChunkList a0 = list_at(lists, sg.off[0], sg.nact[0], sg.total[0]);
+  const bool have_b = sg.maxm > 1 && sg.etotal[1] > 0;
+  const ChunkList b0 = have_b ? list_at(lists, sg.eoff[1], sg.nact[1], sg.etotal[1]) : a0;
+  auto time_it = [&](auto &&launch, float &best) -> int {
+    best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, stream);
+      const int r = launch();
+      if (r) return r;
+      cudaEventRecord(e1, stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return fail(TDSE_ERR_CUDA, "autotune sync");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return TDSE_OK;
+  };
+  Schedule bestS = sched;
+  float bestA = 1e30f, bestB = 1e30f;
+  for (int sb = 1; sb <= kStencilBlocksPerSM && !rc; ++sb)
+    for (int pf : kPfChoices) {
+      Schedule c = sched;
+      c.pf = pf;
+      c.sblocks = sb;
+      float t = 0.f;
+      rc = time_it([&]() { return launch_a(B, a0, 0, c); }, t);
+      if (rc) break;
+      if (t < bestA) {
+        bestA = t;
+        bestS.pf = pf;
+        bestS.sblocks = sb;
+      }
+    }
+  if (!rc && have_b) {
+    // lanczos_b at phase 0 reads z from the last A launch above
+    for (int eb = 1; eb <= kElemBlocksPerSM && !rc; ++eb) {
+      Schedule c = sched;
+      c.eblocks = eb;
+      float t = 0.f;
+      rc = time_it([&]() { return launch_b(B, b0, 0, c); }, t);
+      if (!rc && t < bestB) {
+        bestB = t;
+        bestS.eblocks = eb;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  profiling = was_profiling;
+  if (rc) return rc;
+  sched = bestS;
   return TDSE_OK;
 }
 
@@ -1195,6 +1393,34 @@ long long tdse_batch_points(const tdse_batch_t *b) { return b ? b->npts : 0; }
 long long tdse_batch_launch_count(const tdse_batch_t *b) { return b ? b->eng.launches : 0; }
 
 int tdse_batch_profile(tdse_batch_t *b, int enable) { return b ? b->eng.profile(enable) : TDSE_ERR_ARG; }
+
+int tdse_batch_autotune(tdse_batch_t *b, tdse_schedule *chosen) {
+  if (!b) return TDSE_ERR_ARG;
+  std::vector<int> slots(b->count);
+  for (int i = 0; i < b->count; ++i) slots[i] = i;
+  const int rc = b->eng.autotune(slots);
+  if (rc) return rc;
+  return tdse_batch_get_schedule(b, chosen);
+}
+
+int tdse_batch_set_schedule(tdse_batch_t *b, const tdse_schedule *s) {
+  if (!b || !s) return TDSE_ERR_ARG;
+  Schedule c;
+  c.pf = s->prefetch_rows;
+  c.sblocks = s->stencil_blocks_per_sm;
+  c.eblocks = s->elem_blocks_per_sm;
+  return b->eng.set_schedule(c);
+}
+
+int tdse_batch_get_schedule(const tdse_batch_t *b, tdse_schedule *s) {
+  if (!b) return TDSE_ERR_ARG;
+  if (s) {
+    s->prefetch_rows = b->eng.sched.pf;
+    s->stencil_blocks_per_sm = b->eng.sched.sblocks;
+    s->elem_blocks_per_sm = b->eng.sched.eblocks;
+  }
+  return TDSE_OK;
+}
 
 int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches) {
   return b ? b->eng.profile_read(kind, total_ms, launches) : TDSE_ERR_ARG;

@@ -41,6 +41,36 @@ struct BatchInst {
   double2 *ref0;         // N values: the p_ground reference (1s state of the grid)
 };
 
+// List of the chunks one launch visits: the active slots and the prefix sums
+// of their chunk counts (nact + 1 entries).
+struct ChunkList {
+  const int *act;
+  const int *cpre;
+  int nact, total;
+};
+
+// Per-launch view of the engine's device state.
+struct BatchDev {
+  const BatchInst *inst;
+  LanczosScalars *ls;
+  unsigned *ticket;      // per-slot arrival counters (zero between launches)
+  int *status;
+  const double *E;       // field table of the run: E[n * cap + slot] at step n's mid-point
+  const int *step;       // step of the run being computed (device counter, so one
+                         // captured step graph serves every step of a segment)
+  int cap;
+};
+
+// Launch schedule of the batched kernels.  Results do not depend on it
+// (chunks and their reduction order are fixed per instance); the autotuner
+// picks the fastest for the resident instances.
+struct Schedule {
+  int pf = 6;                        // rows the stencil kernels prefetch ahead (kPfChoices)
+  int sblocks = kStencilBlocksPerSM; // blocks per SM of the stencil kernels (1 or 2)
+  int eblocks = kElemBlocksPerSM;    // blocks per SM of the elementwise kernels (1 or 2)
+};
+constexpr int kPfChoices[] = {0, 3, 6, 10};
+
 // Bytes of device memory one instance needs (every array 256-byte aligned).
 size_t instance_bytes(const tdse_instance_spec &s, int precision);
 // Whether a spec is usable (finite, positive sizes, 1 <= krylov <= max, ...).
@@ -71,11 +101,17 @@ class Engine {
   int set_stream(void *cuda_stream);
   int profile(int enable);
   int profile_read(int kind, double *total_ms, long long *launches);
+  // Time every schedule on phase 0 of the given slots (side-effect free:
+  // the next step recomputes everything those launches write) and keep the
+  // fastest.  Synchronous.
+  int autotune(const std::vector<int> &slots);
+  int set_schedule(const Schedule &s);
   double time_of(int slot) const;
   long long steps_of(int slot) const;
   int fail(int code, const std::string &msg);
 
   int capacity = 0, stencil = 5, precision = TDSE_FP64, sms = 0;
+  Schedule sched;
   std::vector<BatchInst> hinst;
   std::vector<tdse_instance_spec> spec;
   std::vector<long long> nstep;   // steps taken by each slot (t = nstep * dt)
@@ -88,6 +124,21 @@ class Engine {
  private:
   int ensure(void **p, size_t &cap, size_t bytes, const char *what);
   int launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off);
+  // per phase j of a segment: the stencil-chunk list (lanczos_a) and the
+  // elementwise one (lanczos_b, combine) of the slots still active in it
+  struct Segment {
+    long n0, n1;
+    int maxm;
+    std::vector<int> off, nact, total, eoff, etotal;
+  };
+  void build_segment(Segment &sg, const std::vector<int> &act);
+  BatchDev device_view() const;
+  int upload_run(size_t nE);
+  int norm_pass(const BatchDev &B, const std::vector<int> &ids, int off, int total);
+  int launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
+  int launch_b(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
+  int enqueue_step(const BatchDev &B, const Segment &sg, int &count);
+  void drop_graphs();
   cudaEvent_t prof_begin(int kind);
   void prof_end(cudaEvent_t e);
   int prof_collect();
@@ -101,6 +152,8 @@ class Engine {
   double *dt_dev = nullptr;
   double *E_dev = nullptr;
   size_t E_cap = 0;
+  int *step_dev = nullptr;       // step counter of the run (BatchDev::step)
+  std::vector<cudaGraphExec_t> graphs;   // step graphs of the last run (freed after a sync)
   int *lists = nullptr;          // chunk lists of the launches of one run
   size_t lists_cap = 0;
   double *obs_partials = nullptr, *obs_out = nullptr;

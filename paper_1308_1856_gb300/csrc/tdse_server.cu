@@ -232,6 +232,33 @@ int tdse_server_stats(const tdse_server_t *s, tdse_server_stats_t *st) {
   return TDSE_OK;
 }
 
+int tdse_server_autotune(tdse_server_t *s, tdse_schedule *chosen) {
+  int rc = usable(s);
+  if (rc) return rc;
+  std::vector<int> slots;
+  std::vector<long> steps;
+  std::vector<long long> ids;
+  s->sched->plan(1, slots, steps, ids);
+  if ((rc = s->eng.autotune(slots))) return rc;
+  if (chosen) {
+    chosen->prefetch_rows = s->eng.sched.pf;
+    chosen->stencil_blocks_per_sm = s->eng.sched.sblocks;
+    chosen->elem_blocks_per_sm = s->eng.sched.eblocks;
+  }
+  return TDSE_OK;
+}
+
+int tdse_server_set_schedule(tdse_server_t *s, const tdse_schedule *sch) {
+  const int rc = usable(s);
+  if (rc) return rc;
+  if (!sch) return s->eng.fail(TDSE_ERR_ARG, "null schedule");
+  Schedule c;
+  c.pf = sch->prefetch_rows;
+  c.sblocks = sch->stencil_blocks_per_sm;
+  c.eblocks = sch->elem_blocks_per_sm;
+  return s->eng.set_schedule(c);
+}
+
 int tdse_server_profile(tdse_server_t *s, int enable) {
   const int rc = usable(s);
   return rc ? rc : s->eng.profile(enable);

@@ -10,6 +10,17 @@ namespace stencil {
 
 __device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
 
+// Rows ahead of the current one whose lines the mixed walker asks L2 for.
+// The walk visits one row per iteration with little arithmetic, so a load
+// issued one row ahead does not cover DRAM latency at the occupancy these
+// kernels run at; prefetches (no destination register) go further ahead.
+constexpr int kPrefetchRows = 6;
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+
 struct StencilIn {
   const double2 *__restrict__ x;
   const double *__restrict__ diag;
@@ -56,16 +67,6 @@ struct MixedIn {
   int N, L;
   float c1, c2, E;
 };
-
-// Rows ahead of the current one whose lines the mixed walker asks L2 for.
-// The walk visits one row per iteration with little arithmetic, so a load
-// issued one row ahead does not cover DRAM latency at the occupancy these
-// kernels run at; prefetches (no destination register) go further ahead.
-constexpr int kPrefetchRows = 6;
-
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // L2 prefetch of every array the walker and its epilogue read at row offset idx.
 template <bool S, bool Wp>
@@ -144,8 +145,9 @@ __device__ __forceinline__ void split2(double2 v, float2 &h, float2 &lo) {
   lo = make_float2(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y));
 }
 
-// Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).
-template <int ST, typename F>
+// Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).  PF > 0
+// asks L2 for the operand and diagonal rows PF rows ahead.
+template <int ST, int PF = 0, typename F>
 __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const double2 z = make_double2(0.0, 0.0);
@@ -153,8 +155,17 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
   double2 prev = (l0 > 0) ? ldg2(in.x + (size_t)(l0 - 1) * N + i) : z;
   double2 cur = ldg2(in.x + (size_t)l0 * N + i);
   double a_cur = __dmul_rn(in.kappa[l0], Er);
+  if (PF > 0)
+    for (int q = 1; q < PF && l0 + q < l1; ++q) {
+      prefetch_l2(in.x + (size_t)(l0 + q) * N + i);
+      prefetch_l2(in.diag + (size_t)(l0 + q) * N + i);
+    }
   for (int l = l0; l < l1; ++l) {
     const size_t idx = (size_t)l * N + i;
+    if (PF > 0 && l + PF < l1) {
+      prefetch_l2(in.x + idx + (size_t)PF * N);
+      prefetch_l2(in.diag + idx + (size_t)PF * N);
+    }
     const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
     const double a_next = __dmul_rn(in.kappa[l + 1], Er);
     const double d = __ldg(in.diag + idx);
@@ -167,17 +178,19 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
 }
 
 // Walk rows [l0, l1) of column i of the mixed operand; f(i, idx, Hx, x_center).
-template <int ST, bool S, bool Wp, typename F>
+// PF > 0 asks L2 for every operand row PF rows ahead (prefetch_row).
+template <int ST, bool S, bool Wp, int PF = kPrefetchRows, typename F>
 __device__ __forceinline__ void mixed_walk_rows(const MixedIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const float Er = in.E * in.rj[i];
   Parts<S, Wp> prev = load_parts<S, Wp>(in, (size_t)(l0 - 1) * N + i, l0 > 0);
   Parts<S, Wp> cur = load_parts<S, Wp>(in, (size_t)l0 * N + i, true);
   float a_cur = in.kappa[l0] * Er;
-  for (int q = 1; q < kPrefetchRows && l0 + q < l1; ++q) prefetch_row<S, Wp>(in, (size_t)(l0 + q) * N + i);
+  if (PF > 0)
+    for (int q = 1; q < PF && l0 + q < l1; ++q) prefetch_row<S, Wp>(in, (size_t)(l0 + q) * N + i);
   for (int l = l0; l < l1; ++l) {
     const size_t idx = (size_t)l * N + i;
-    if (l + kPrefetchRows < l1) prefetch_row<S, Wp>(in, idx + (size_t)kPrefetchRows * N);
+    if (PF > 0 && l + PF < l1) prefetch_row<S, Wp>(in, idx + (size_t)PF * N);
     const Parts<S, Wp> next = load_parts<S, Wp>(in, idx + N, l < L);
     const float a_next = in.kappa[l + 1] * Er;
     const Parts<S, Wp> m1 = load_parts<S, Wp>(in, idx - 1, i >= 1);

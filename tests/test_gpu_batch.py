@@ -82,3 +82,48 @@ def test_batch_set_state_and_invalid_specs():
     for bad in (dict(s, krylov=0), dict(s, krylov=33), dict(s, N=0), dict(s, dt=-1.0)):
         with pytest.raises(TDSEError):
             Batch([s, bad])
+
+
+SCHEDULES = [(6, 2, 2), (0, 2, 2), (3, 1, 2), (10, 2, 1), (0, 1, 1)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_schedule_and_graph_replay_do_not_change_results(precision):
+    """Every launch schedule (prefetch distance, blocks per SM) and the
+    captured-graph replay of multi-step segments give bitwise the same states
+    as step-by-step launches with the default schedule."""
+    from paper_1308_1856_gb300 import Batch
+    ref = Batch(SPECS, precision=precision)
+    for _ in range(7):
+        ref.propagate(1)                    # one-step runs: no graph
+    want = [ref.get_state(i) for i in range(len(SPECS))]
+    ref.close()
+    for sch in SCHEDULES:
+        b = Batch(SPECS, precision=precision)
+        b.set_schedule(*sch)
+        b.propagate(7)                      # one run of 7 steps: a replayed step graph
+        for i in range(len(SPECS)):
+            assert np.array_equal(b.get_state(i), want[i]), (sch, i)
+        b.close()
+
+
+def test_batch_autotune_leaves_the_state_untouched():
+    from paper_1308_1856_gb300 import Batch, TDSEError
+    a = Batch(SPECS, precision="mixed")
+    a.propagate(3)
+    chosen = a.autotune()
+    assert chosen["prefetch_rows"] in (0, 3, 6, 10)
+    assert chosen["stencil_blocks_per_sm"] in (1, 2) and chosen["elem_blocks_per_sm"] in (1, 2)
+    assert a.schedule() == chosen
+    a.propagate(4)
+    b = Batch(SPECS, precision="mixed")
+    b.propagate(3)
+    b.propagate(4)
+    for i in range(len(SPECS)):
+        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+    with pytest.raises(TDSEError):
+        a.set_schedule(5, 2, 2)
+    with pytest.raises(TDSEError):
+        a.set_schedule(6, 3, 2)
+    a.close()
+    b.close()

@@ -147,3 +147,27 @@ def test_server_errors():
     with pytest.raises(TDSEError):
         srv.release(12345)
     srv.close()
+
+
+def test_server_autotune_and_graph_segments():
+    """Autotuning on the running requests and step batches long enough to be
+    replayed as graphs leave every request's result unchanged (bitwise)."""
+    from paper_1308_1856_gb300 import Server
+    ref = Server(64 << 20, max_resident=16)
+    ids = [ref.submit(s, 9 + 4 * i) for i, s in enumerate(SPECS)]
+    for _ in range(40):
+        if ref.stats()["running"] == 0 and ref.stats()["queued"] == 0:
+            break
+        ref.step(1)                          # one-step runs: no graphs
+    want = {i: ref.get_state(r) for i, r in enumerate(ids)}
+    ref.close()
+    srv = Server(64 << 20, max_resident=16)
+    ids = [srv.submit(s, 9 + 4 * i) for i, s in enumerate(SPECS)]
+    srv.step(2)
+    chosen = srv.autotune()
+    assert chosen["prefetch_rows"] in (0, 3, 6, 10)
+    srv.step(100)                            # segments of several steps
+    srv.sync()
+    for i, r in enumerate(ids):
+        assert np.array_equal(srv.get_state(r), want[i]), i
+    srv.close()
