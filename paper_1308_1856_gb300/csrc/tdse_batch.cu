@@ -38,8 +38,16 @@ namespace {
 using namespace common;
 using namespace stencil;
 
-constexpr int kChunkSegs = 64;   // 32-point row segments per reduction chunk (stencil kernels)
-constexpr int kChunkPts = kChunkSegs * 32;   // consecutive points per chunk (elementwise kernels)
+#ifndef TDSE_CHUNK_SEGS
+#define TDSE_CHUNK_SEGS 64
+#endif
+#ifndef TDSE_CHUNK_PTS
+#define TDSE_CHUNK_PTS 2048
+#endif
+// Reduction chunks.  Their sizes fix each instance's summation order, so they
+// are compile-time constants (the launch schedule never changes them).
+constexpr int kChunkSegs = TDSE_CHUNK_SEGS;  // 32-point row segments per chunk (stencil kernels)
+constexpr int kChunkPts = TDSE_CHUNK_PTS;    // consecutive points per chunk (elementwise kernels)
 
 __device__ __forceinline__ double field_of(const BatchDev &B, int inst) {
   return B.E[(size_t)(*B.step) * (size_t)B.cap + inst];
