@@ -289,8 +289,11 @@ int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long lo
 
 /*
  * Launch schedule of the batched kernels: the rows the stencil kernels
- * prefetch ahead into L2 (0, 3, 6 or 10), and the blocks per SM of the
- * stencil and of the elementwise kernels (1 or 2, of 512 threads).  Results
+ * prefetch ahead into L2 (0, 3, 6 or 10); for the mixed-precision stencil
+ * kernel, the rows staged ahead through a per-warp ring of shared memory by
+ * asynchronous copies (0 = off, 3 or 5; the prefetch distance is then
+ * unused); and the blocks per SM of the stencil and of the elementwise
+ * kernels (1 or 2, of 512 threads).  Results
  * do not depend on the schedule (bitwise): every reduction is split into
  * fixed per-instance chunks whatever the grid.  Segments of three or more
  * steps with an unchanged set of instances run as one captured CUDA graph of
@@ -304,6 +307,7 @@ int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long lo
  */
 typedef struct {
   int prefetch_rows;
+  int ring_rows;              /* mixed precision: 0, or 3 or 5 rows staged in shared memory */
   int stencil_blocks_per_sm;
   int elem_blocks_per_sm;
 } tdse_schedule;

@@ -253,8 +253,10 @@ class Batch:
         self._check(C.tdse_batch_autotune(self.h, ctypes.byref(sch)))
         return {k: getattr(sch, k) for k, _ in sch._fields_}
 
-    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int):
-        sch = C.tdse_schedule(int(prefetch_rows), int(stencil_blocks_per_sm), int(elem_blocks_per_sm))
+    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int,
+                     ring_rows: int = 0):
+        sch = C.tdse_schedule(int(prefetch_rows), int(ring_rows), int(stencil_blocks_per_sm),
+                              int(elem_blocks_per_sm))
         self._check(C.tdse_batch_set_schedule(self.h, ctypes.byref(sch)))
 
     def schedule(self) -> dict:
@@ -361,8 +363,10 @@ class Server:
         self._check(C.tdse_server_autotune(self.h, ctypes.byref(sch)))
         return {k: getattr(sch, k) for k, _ in sch._fields_}
 
-    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int):
-        sch = C.tdse_schedule(int(prefetch_rows), int(stencil_blocks_per_sm), int(elem_blocks_per_sm))
+    def set_schedule(self, prefetch_rows: int, stencil_blocks_per_sm: int, elem_blocks_per_sm: int,
+                     ring_rows: int = 0):
+        sch = C.tdse_schedule(int(prefetch_rows), int(ring_rows), int(stencil_blocks_per_sm),
+                              int(elem_blocks_per_sm))
         self._check(C.tdse_server_set_schedule(self.h, ctypes.byref(sch)))
 
     def profile(self, enable: bool):

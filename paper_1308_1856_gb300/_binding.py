@@ -42,8 +42,8 @@ class tdse_instance_spec(ctypes.Structure):
 
 
 class tdse_schedule(ctypes.Structure):
-    _fields_ = [("prefetch_rows", ctypes.c_int), ("stencil_blocks_per_sm", ctypes.c_int),
-                ("elem_blocks_per_sm", ctypes.c_int)]
+    _fields_ = [("prefetch_rows", ctypes.c_int), ("ring_rows", ctypes.c_int),
+                ("stencil_blocks_per_sm", ctypes.c_int), ("elem_blocks_per_sm", ctypes.c_int)]
 
 
 class tdse_server_stats_t(ctypes.Structure):

@@ -107,6 +107,22 @@ __device__ __forceinline__ void chunk_columns(const BatchInst &I, int ci, F &&f)
   }
 }
 
+// The same segments as chunk_columns, for warp-collective walkers: every lane
+// gets f(jg, l0, l1) (its column jg*32 + lane may be >= N).
+template <typename F>
+__device__ __forceinline__ void chunk_groups(const BatchInst &I, int ci, F &&f) {
+  const int Lp1 = I.L + 1;
+  int s = ci * kChunkSegs;
+  const int s_end = min(s + kChunkSegs, I.nseg);
+  while (s < s_end) {
+    const int jg = s / Lp1;
+    const int l0 = s - jg * Lp1;
+    const int l1 = min(Lp1, l0 + (s_end - s));
+    f(jg, l0, l1);
+    s += l1 - l0;
+  }
+}
+
 // Visit chunk ci of an instance in the elementwise layout: the kChunkPts
 // consecutive points [ci*C, min((ci+1)*C, G)) of the l-major array, lane-strided
 // so that every load is coalesced; f(idx, i) with i = idx mod N, the radial index.
@@ -359,6 +375,54 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       }
       chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true, PF>(in, i, l0, l1, epi); });
     }
+    const double accd = acc.value();
+    double s;
+    if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
+      ls->alpha[j] = s * sigd;
+      ls->acoef[j] = -(s * sigd) * sigd;
+    }
+  });
+}
+
+// Lanczos A (mixed) with the operand rows staged through a per-warp ring of
+// shared memory (staged_walk_rows, depth D); the same arithmetic as
+// bt_lanczos_a_mixed.  MODE 0: j = 0, the operand is the split of psi;
+// MODE 1: j = 1, U_0 (for the ratio term) is the split of psi; MODE 2: j >= 2.
+template <int ST, int D, int MODE>
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
+    bt_lanczos_a_mixed_staged(BatchDev B, ChunkList cl, int j) {
+  extern __shared__ float2 ring_smem[];
+  constexpr bool S = MODE == 0;
+  constexpr int NE = MODE == 0 ? 0 : (MODE == 1 ? 2 : 1);
+  float2 *ring = ring_smem + (threadIdx.x >> 5) * (D + 1) * RingLayout<S, !S, NE>::kSlot;
+  for_my_chunks(cl, [&](int inst, int ci) {
+    const BatchInst I = B.inst[inst];
+    LanczosScalars *ls = B.ls + inst;
+    const long long G = (long long)I.N * (I.L + 1);
+    float2 *z = I.mwork;
+    const double sigd = ls->sigma[j];
+    const float sig = (float)sigd;
+    const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
+    PairSum acc;
+    auto epi = [&](int, size_t idx, float2 t, float2 u, float2 e0, float2 e1) {
+      float2 o = make_float2(sig * t.x, sig * t.y);
+      if (MODE > 0) {
+        const float2 up = (MODE == 1) ? make_float2(e0.x + e1.x, e0.y + e1.y) : e0;
+        o.x = fmaf(-cprev, up.x, o.x);
+        o.y = fmaf(-cprev, up.y, o.y);
+      }
+      z[idx] = o;
+      acc.add(fmaf(u.x, o.x, u.y * o.y));
+    };
+    MixedIn in = S ? mixed_in(B, I, inst, I.hi, I.lo, nullptr)
+                   : mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
+    if (MODE == 1) {
+      in.pf0 = I.hi;
+      in.pf1 = I.lo;
+    } else if (MODE == 2) {
+      in.pf0 = I.mwork + (long long)(j - 1) * G;
+    }
+    chunk_groups(I, ci, [&](int jg, int l0, int l1) { staged_walk_rows<ST, S, !S, NE, D>(in, ring, jg, l0, l1, epi); });
     const double accd = acc.value();
     double s;
     if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
@@ -919,6 +983,31 @@ void launch_a_pf(bool mixed, unsigned grid, cudaStream_t st, const BatchDev &B, 
   else bt_lanczos_a_fp64<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
 }
 
+// Staged variant: dynamic shared memory of 16 warps' rings, raised above the
+// 48 KB default once per instantiation.
+template <int ST, int D, int MODE>
+cudaError_t launch_staged_mode(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  constexpr bool S = MODE == 0;
+  constexpr int NE = MODE == 0 ? 0 : (MODE == 1 ? 2 : 1);
+  constexpr int bytes = (kBlockJ / 32) * ring_bytes<S, !S, NE, D>();
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(bt_lanczos_a_mixed_staged<ST, D, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  bt_lanczos_a_mixed_staged<ST, D, MODE><<<grid, kBlockJ, bytes, st>>>(B, cl, j);
+  return cudaGetLastError();
+}
+
+template <int ST, int D>
+cudaError_t launch_staged(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  if (j == 0) return launch_staged_mode<ST, D, 0>(grid, st, B, cl, j);
+  if (j == 1) return launch_staged_mode<ST, D, 1>(grid, st, B, cl, j);
+  return launch_staged_mode<ST, D, 2>(grid, st, B, cl, j);
+}
+
 template <int ST>
 void launch_a_st(bool mixed, int pf, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl,
                  int j) {
@@ -1007,6 +1096,13 @@ int Engine::norm_pass(const BatchDev &B, const std::vector<int> &ids, int off, i
 int Engine::launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s) {
   const unsigned grid = (unsigned)(sms * s.sblocks);
   const bool mixed = precision == TDSE_MIXED;
+  if (mixed && s.ring > 0) {
+    cudaError_t e;
+    if (stencil == 5) e = (s.ring == 3) ? launch_staged<5, 3>(grid, stream, B, cl, j) : launch_staged<5, 5>(grid, stream, B, cl, j);
+    else e = (s.ring == 3) ? launch_staged<3, 3>(grid, stream, B, cl, j) : launch_staged<3, 5>(grid, stream, B, cl, j);
+    EN_CUDA(e, "batch lanczos a (staged)");
+    return TDSE_OK;
+  }
   if (stencil == 5) launch_a_st<5>(mixed, s.pf, grid, stream, B, cl, j);
   else launch_a_st<3>(mixed, s.pf, grid, stream, B, cl, j);
   EN_CUDA(cudaGetLastError(), "batch lanczos a");
@@ -1156,9 +1252,11 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
 }
 
 int Engine::set_schedule(const Schedule &s) {
-  bool pf_ok = false;
+  bool pf_ok = false, ring_ok = false;
   for (int p : kPfChoices) pf_ok = pf_ok || p == s.pf;
-  if (!pf_ok || s.sblocks < 1 || s.sblocks > kStencilBlocksPerSM || s.eblocks < 1 || s.eblocks > kElemBlocksPerSM)
+  for (int r : kRingChoices) ring_ok = ring_ok || r == s.ring;
+  if (!pf_ok || !ring_ok || s.sblocks < 1 || s.sblocks > kStencilBlocksPerSM || s.eblocks < 1 ||
+      s.eblocks > kElemBlocksPerSM)
     return fail(TDSE_ERR_ARG, "schedule outside the tuned choices");
   sched = s;
   return TDSE_OK;
@@ -1224,20 +1322,27 @@ int Engine::autotune(const std::vector<int> &slots) {
   };
   Schedule bestS = sched;
   float bestA = 1e30f, bestB = 1e30f;
+  // the staged ring exists for the mixed stencil kernel only
+  const int nring = precision == TDSE_MIXED ? (int)(sizeof(kRingChoices) / sizeof(int)) : 1;
   for (int sb = 1; sb <= kStencilBlocksPerSM && !rc; ++sb)
-    for (int pf : kPfChoices) {
-      Schedule c = sched;
-      c.pf = pf;
-      c.sblocks = sb;
-      float t = 0.f;
-      rc = time_it([&]() { return launch_a(B, a0, 0, c); }, t);
-      if (rc) break;
-      if (t < bestA) {
-        bestA = t;
-        bestS.pf = pf;
-        bestS.sblocks = sb;
+    for (int ri = 0; ri < nring && !rc; ++ri)
+      for (int pf : kPfChoices) {
+        const int ring = kRingChoices[ri];
+        if (ring > 0 && pf != kPfChoices[0]) continue;   // the ring does not use the prefetch distance
+        Schedule c = sched;
+        c.pf = pf;
+        c.ring = ring;
+        c.sblocks = sb;
+        float t = 0.f;
+        rc = time_it([&]() { return launch_a(B, a0, 0, c); }, t);
+        if (rc) break;
+        if (t < bestA) {
+          bestA = t;
+          bestS.pf = pf;
+          bestS.ring = ring;
+          bestS.sblocks = sb;
+        }
       }
-    }
   if (!rc && have_b) {
     // lanczos_b at phase 0 reads z from the last A launch above
     for (int eb = 1; eb <= kElemBlocksPerSM && !rc; ++eb) {
@@ -1415,6 +1520,7 @@ int tdse_batch_set_schedule(tdse_batch_t *b, const tdse_schedule *s) {
   if (!b || !s) return TDSE_ERR_ARG;
   Schedule c;
   c.pf = s->prefetch_rows;
+  c.ring = s->ring_rows;
   c.sblocks = s->stencil_blocks_per_sm;
   c.eblocks = s->elem_blocks_per_sm;
   return b->eng.set_schedule(c);
@@ -1424,6 +1530,7 @@ int tdse_batch_get_schedule(const tdse_batch_t *b, tdse_schedule *s) {
   if (!b) return TDSE_ERR_ARG;
   if (s) {
     s->prefetch_rows = b->eng.sched.pf;
+    s->ring_rows = b->eng.sched.ring;
     s->stencil_blocks_per_sm = b->eng.sched.sblocks;
     s->elem_blocks_per_sm = b->eng.sched.eblocks;
   }

@@ -66,10 +66,12 @@ struct BatchDev {
 // picks the fastest for the resident instances.
 struct Schedule {
   int pf = 6;                        // rows the stencil kernels prefetch ahead (kPfChoices)
+  int ring = 0;                      // mixed stencil kernel: rows staged ahead in shared memory (0: off)
   int sblocks = kStencilBlocksPerSM; // blocks per SM of the stencil kernels (1 or 2)
   int eblocks = kElemBlocksPerSM;    // blocks per SM of the elementwise kernels (1 or 2)
 };
 constexpr int kPfChoices[] = {0, 3, 6, 10};
+constexpr int kRingChoices[] = {0, 3, 5};
 
 // Bytes of device memory one instance needs (every array 256-byte aligned).
 size_t instance_bytes(const tdse_instance_spec &s, int precision);

@@ -242,6 +242,7 @@ int tdse_server_autotune(tdse_server_t *s, tdse_schedule *chosen) {
   if ((rc = s->eng.autotune(slots))) return rc;
   if (chosen) {
     chosen->prefetch_rows = s->eng.sched.pf;
+    chosen->ring_rows = s->eng.sched.ring;
     chosen->stencil_blocks_per_sm = s->eng.sched.sblocks;
     chosen->elem_blocks_per_sm = s->eng.sched.eblocks;
   }
@@ -254,6 +255,7 @@ int tdse_server_set_schedule(tdse_server_t *s, const tdse_schedule *sch) {
   if (!sch) return s->eng.fail(TDSE_ERR_ARG, "null schedule");
   Schedule c;
   c.pf = sch->prefetch_rows;
+  c.ring = sch->ring_rows;
   c.sblocks = sch->stencil_blocks_per_sm;
   c.eblocks = sch->elem_blocks_per_sm;
   return s->eng.set_schedule(c);
