@@ -48,6 +48,7 @@ using namespace stencil;
 // are compile-time constants (the launch schedule never changes them).
 constexpr int kChunkSegs = TDSE_CHUNK_SEGS;  // 32-point row segments per chunk (stencil kernels)
 constexpr int kChunkPts = TDSE_CHUNK_PTS;    // consecutive points per chunk (elementwise kernels)
+constexpr int kCombinePts = 2;               // points per lane whose Krylov loads the combines overlap
 
 __device__ __forceinline__ double field_of(const BatchDev &B, int inst) {
   return B.E[(size_t)(*B.step) * (size_t)B.cap + inst];
@@ -141,6 +142,59 @@ __device__ __forceinline__ void chunk_points(const BatchInst &I, int ci, F &&f) 
   }
 }
 
+// As chunk_points, four lane-strided points at a time: the loads of all four
+// (load(idx) -> V) are issued before the first op(idx, i, V), whose stores
+// the compiler could not otherwise move loads across (the arrays may alias as
+// far as it knows).  The points reach op in the same order as in chunk_points.
+template <typename Ld, typename Op>
+__device__ __forceinline__ void chunk_points_x4(const BatchInst &I, int ci, Ld &&load, Op &&op) {
+  const unsigned N = (unsigned)I.N;
+  const unsigned G = N * (unsigned)(I.L + 1);
+  const unsigned base = (unsigned)ci * kChunkPts + (threadIdx.x & 31);
+  const unsigned end = min(G, (unsigned)(ci + 1) * kChunkPts);
+  unsigned i = base % N;
+  using V = decltype(load((size_t)0));
+  for (unsigned idx = base; idx < end; idx += 128) {
+    V v[4];
+    int iq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      iq[q] = (int)i;
+      if (idx + 32 * q < end) v[q] = load((size_t)(idx + 32 * q));
+      i += 32;
+      while (i >= N) i -= N;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (idx + 32 * q < end) op((size_t)(idx + 32 * q), iq[q], v[q]);
+  }
+}
+
+// The points of chunk_points in groups of Q consecutive lane-strided points:
+// f(idx[Q], i[Q], nq) with the first nq entries valid.
+template <int Q, typename F>
+__device__ __forceinline__ void chunk_groups_of(const BatchInst &I, int ci, F &&f) {
+  const unsigned N = (unsigned)I.N;
+  const unsigned G = N * (unsigned)(I.L + 1);
+  const unsigned base = (unsigned)ci * kChunkPts + (threadIdx.x & 31);
+  const unsigned end = min(G, (unsigned)(ci + 1) * kChunkPts);
+  unsigned i = base % N;
+  for (unsigned idx = base; idx < end; idx += 32 * Q) {
+    size_t ix[Q];
+    int iq[Q];
+    int nq = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      ix[q] = (size_t)(idx + 32 * q);
+      iq[q] = (int)i;
+      if (idx + 32 * q < end) nq = q + 1;
+      i += 32;
+      while (i >= N) i -= N;
+    }
+    f(ix, iq, nq);
+  }
+}
+
 // Each warp takes a balanced, contiguous range of the list's chunks (warp_range).
 template <typename F>
 __device__ __forceinline__ void for_my_chunks(const ChunkList &cl, F &&f) {
@@ -220,9 +274,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     double2 *un = I.work + (long long)(j + 1) * G;
     const double c = ls->acoef[j];
     double acc = 0.0;
-    chunk_points(I, ci, [&](size_t idx, int) {
-      const double2 zz = z[idx], uu = u[idx];
-      const double2 o = make_double2(__fma_rn(c, uu.x, zz.x), __fma_rn(c, uu.y, zz.y));
+    struct ZU { double2 z, u; };
+    chunk_points_x4(I, ci, [&](size_t idx) { return ZU{z[idx], u[idx]}; },
+                    [&](size_t idx, int, const ZU &v) {
+      const double2 o = make_double2(__fma_rn(c, v.u.x, v.z.x), __fma_rn(c, v.u.y, v.z.y));
       un[idx] = o;
       acc = __fma_rn(o.x, o.x, acc);
       acc = __fma_rn(o.y, o.y, acc);
@@ -245,8 +300,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const BatchInst I = B.inst[inst];
     const double2 *x = I.psi;
     double acc = 0.0;
-    chunk_points(I, ci, [&](size_t idx, int) {
-      const double2 v = x[idx];
+    chunk_points_x4(I, ci, [&](size_t idx) { return x[idx]; }, [&](size_t, int, const double2 &v) {
       acc = __fma_rn(v.x, v.x, acc);
       acc = __fma_rn(v.y, v.y, acc);
     });
@@ -280,26 +334,46 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     __syncwarp();
     const double2 c0 = wcoef[wib][0];
     double acc = 0.0;
-    chunk_points(I, ci, [&](size_t idx, int i) {
-      const double2 u0 = psi[idx];
-      double ox = __fma_rn(c0.x, u0.x, __dmul_rn(-c0.y, u0.y));
-      double oy = __fma_rn(c0.x, u0.y, __dmul_rn(c0.y, u0.x));
+    // kCombinePts points at a time, Krylov vector by Krylov vector
+    chunk_groups_of<kCombinePts>(I, ci, [&](const size_t (&ix)[kCombinePts], const int (&iq)[kCombinePts], int nq) {
+      double ox[kCombinePts], oy[kCombinePts];
+#pragma unroll
+      for (int q = 0; q < kCombinePts; ++q) {
+        if (q < nq) {
+          const double2 u0 = psi[ix[q]];
+          ox[q] = __fma_rn(c0.x, u0.x, __dmul_rn(-c0.y, u0.y));
+          oy[q] = __fma_rn(c0.x, u0.y, __dmul_rn(c0.y, u0.x));
+        }
+      }
       for (int jj = 1; jj < k; ++jj) {
-        const double2 u = U1[(size_t)(jj - 1) * G + idx];
+        double2 u[kCombinePts];
+#pragma unroll
+        for (int q = 0; q < kCombinePts; ++q)
+          if (q < nq) u[q] = U1[(size_t)(jj - 1) * G + ix[q]];
         const double2 c = wcoef[wib][jj];
-        ox = __fma_rn(c.x, u.x, ox);
-        ox = __fma_rn(-c.y, u.y, ox);
-        oy = __fma_rn(c.x, u.y, oy);
-        oy = __fma_rn(c.y, u.x, oy);
+#pragma unroll
+        for (int q = 0; q < kCombinePts; ++q) {
+          if (q < nq) {
+            ox[q] = __fma_rn(c.x, u[q].x, ox[q]);
+            ox[q] = __fma_rn(-c.y, u[q].y, ox[q]);
+            oy[q] = __fma_rn(c.x, u[q].y, oy[q]);
+            oy[q] = __fma_rn(c.y, u[q].x, oy[q]);
+          }
+        }
       }
-      if (i >= I.mask_start) {
-        const double mv = mask[i];
-        ox = __dmul_rn(mv, ox);
-        oy = __dmul_rn(mv, oy);
+#pragma unroll
+      for (int q = 0; q < kCombinePts; ++q) {
+        if (q < nq) {
+          if (iq[q] >= I.mask_start) {
+            const double mv = mask[iq[q]];
+            ox[q] = __dmul_rn(mv, ox[q]);
+            oy[q] = __dmul_rn(mv, oy[q]);
+          }
+          psi[ix[q]] = make_double2(ox[q], oy[q]);
+          acc = __fma_rn(ox[q], ox[q], acc);
+          acc = __fma_rn(oy[q], oy[q], acc);
+        }
       }
-      psi[idx] = make_double2(ox, oy);
-      acc = __fma_rn(ox, ox, acc);
-      acc = __fma_rn(oy, oy, acc);
     });
     double s;
     if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
@@ -446,7 +520,8 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     float2 *un = I.mwork + (long long)(j + 1) * G;
     const float c = (float)ls->acoef[j];
     PairSum acc;
-    chunk_points(I, ci, [&](size_t idx, int) {
+    struct ZU { float2 z, u; };
+    chunk_points_x4(I, ci, [&](size_t idx) {
       float2 uu;
       if (!SPLIT) {
         uu = u[idx];
@@ -454,8 +529,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
         const float2 h = hi[idx], lw = lo[idx];
         uu = make_float2(h.x + lw.x, h.y + lw.y);
       }
-      const float2 zz = z[idx];
-      const float2 o = make_float2(fmaf(c, uu.x, zz.x), fmaf(c, uu.y, zz.y));
+      return ZU{z[idx], uu};
+    }, [&](size_t idx, int, const ZU &v) {
+      const float2 o = make_float2(fmaf(c, v.u.x, v.z.x), fmaf(c, v.u.y, v.z.y));
       un[idx] = o;
       acc.add(fmaf(o.x, o.x, o.y * o.y));
     });
@@ -479,9 +555,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double2 *x = I.psi;
     float2 *hi = I.hi, *lo = I.lo;
     PairSum acc;
-    chunk_points(I, ci, [&](size_t idx, int) {
+    chunk_points_x4(I, ci, [&](size_t idx) { return x[idx]; }, [&](size_t idx, int, const double2 &v) {
       float2 h, lw;
-      split2(x[idx], h, lw);
+      split2(v, h, lw);
       hi[idx] = h;
       lo[idx] = lw;
       acc.add(fmaf(h.x, h.x, h.y * h.y));
@@ -522,31 +598,50 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     }
     __syncwarp();
     PairSum acc;
-    chunk_points(I, ci, [&](size_t idx, int i) {
-      float cx = 0.f, cy = 0.f;
+    // kCombinePts points at a time, Krylov vector by Krylov vector
+    chunk_groups_of<kCombinePts>(I, ci, [&](const size_t (&ix)[kCombinePts], const int (&iq)[kCombinePts], int nq) {
+      float cx[kCombinePts], cy[kCombinePts];
+#pragma unroll
+      for (int q = 0; q < kCombinePts; ++q) cx[q] = cy[q] = 0.f;
+      double2 p[kCombinePts];
+#pragma unroll
+      for (int q = 0; q < kCombinePts; ++q)
+        if (q < nq) p[q] = psi[ix[q]];
       for (int jj = 1; jj < k; ++jj) {
-        const float2 u = U1[(size_t)(jj - 1) * G + idx];
+        float2 u[kCombinePts];
+#pragma unroll
+        for (int q = 0; q < kCombinePts; ++q)
+          if (q < nq) u[q] = U1[(size_t)(jj - 1) * G + ix[q]];
         const float2 c = wcoef[wib][jj];
-        cx = fmaf(c.x, u.x, cx);
-        cx = fmaf(-c.y, u.y, cx);
-        cy = fmaf(c.x, u.y, cy);
-        cy = fmaf(c.y, u.x, cy);
+#pragma unroll
+        for (int q = 0; q < kCombinePts; ++q) {
+          if (q < nq) {
+            cx[q] = fmaf(c.x, u[q].x, cx[q]);
+            cx[q] = fmaf(-c.y, u[q].y, cx[q]);
+            cy[q] = fmaf(c.x, u[q].y, cy[q]);
+            cy[q] = fmaf(c.y, u[q].x, cy[q]);
+          }
+        }
       }
-      const double2 p = psi[idx];
-      double ox = fma(c0.x, p.x, fma(-c0.y, p.y, (double)cx));
-      double oy = fma(c0.x, p.y, fma(c0.y, p.x, (double)cy));
-      if (i >= I.mask_start) {
-        const double mv = mask[i];
-        ox *= mv;
-        oy *= mv;
+#pragma unroll
+      for (int q = 0; q < kCombinePts; ++q) {
+        if (q < nq) {
+          double ox = fma(c0.x, p[q].x, fma(-c0.y, p[q].y, (double)cx[q]));
+          double oy = fma(c0.x, p[q].y, fma(c0.y, p[q].x, (double)cy[q]));
+          if (iq[q] >= I.mask_start) {
+            const double mv = mask[iq[q]];
+            ox *= mv;
+            oy *= mv;
+          }
+          const double2 o = make_double2(ox, oy);
+          psi[ix[q]] = o;
+          float2 h, lw;
+          split2(o, h, lw);
+          hi[ix[q]] = h;
+          lo[ix[q]] = lw;
+          acc.add(fmaf(h.x, h.x, h.y * h.y));
+        }
       }
-      const double2 o = make_double2(ox, oy);
-      psi[idx] = o;
-      float2 h, lw;
-      split2(o, h, lw);
-      hi[idx] = h;
-      lo[idx] = lw;
-      acc.add(fmaf(h.x, h.x, h.y * h.y));
     });
     const double accd = acc.value();
     double s;
