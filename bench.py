@@ -332,11 +332,14 @@ def run_served(args, stream_ptr):
                        f"(seed {args.serve_seed}), each request {args.serve_horizon} Lanczos steps "
                        f"(dt {BATCH_DT}) from t = 0, step batches of {args.serve_batch}, HBM budget "
                        f"{args.serve_budget_gb:g} GB, FIFO admission"}
-    for name, rate, count in (("overload", args.serve_rate, args.serve_requests),
-                              ("sustained", args.serve_sustained_rate, args.serve_sustained_requests)):
-        if count > 0:
-            out[name] = serve_trace(stream_ptr, args.serve_precision, rate, count, args.serve_horizon,
-                                    args.serve_batch, budget, args.serve_seed)
+    precs = ["fp64", "mixed"] if args.serve_precision == "both" else [args.serve_precision]
+    for prec in precs:
+        for name, rate, count in (("overload", args.serve_rate, args.serve_requests),
+                                  ("sustained", args.serve_sustained_rate, args.serve_sustained_requests)):
+            if count > 0:
+                key = name if len(precs) == 1 else f"{name}_{prec}"
+                out[key] = serve_trace(stream_ptr, prec, rate, count, args.serve_horizon, args.serve_batch,
+                                       budget, args.serve_seed)
     return out
 
 
@@ -563,7 +566,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched rows (smaller only for profiling captures)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served traces")
-    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--serve-precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--serve-rate", type=float, default=50.0, help="overloaded trace: mean req/s")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-sustained-rate", type=float, default=2.0)

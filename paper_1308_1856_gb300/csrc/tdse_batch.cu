@@ -221,6 +221,7 @@ __device__ __forceinline__ StencilIn fp64_in(const BatchDev &B, const BatchInst 
   in.c1 = I.c1;
   in.c2 = I.c2;
   in.E = field_of(B, inst);
+  in.dscale = 1.0;
   return in;
 }
 
@@ -236,18 +237,18 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     double2 *z = I.work;
     const double sig = ls->sigma[j];
     const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
-    const StencilIn in = fp64_in(B, I, inst, u);
+    // t = sigma_j H U_j directly (the operator scaled by sigma_j)
+    const StencilIn in = scaled(fp64_in(B, I, inst, u), sig);
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
-      walk_rows<ST, PF>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
+      walk_rows<ST, PF, true>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
         double2 o;
         if (j > 0) {
           const double2 pv = up[idx];
-          o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, pv.x));
-          o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, pv.y));
+          o.x = __fma_rn(-cprev, pv.x, t.x);
+          o.y = __fma_rn(-cprev, pv.y, t.y);
         } else {
-          o.x = __dmul_rn(sig, t.x);
-          o.y = __dmul_rn(sig, t.y);
+          o = t;
         }
         z[idx] = o;
         acc = __fma_rn(uc.x, o.x, acc);

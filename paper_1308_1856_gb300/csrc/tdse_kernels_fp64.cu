@@ -36,7 +36,7 @@ using namespace common;
 using namespace stencil;
 
 // Visit this warp's share of the 32-point row segments (see the file header).
-template <int ST, typename F>
+template <int ST, bool SCALED = false, typename F>
 __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
   const int lane = threadIdx.x & 31;
   const int Lp1 = in.L + 1;
@@ -49,7 +49,7 @@ __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
     const int i = jg * 32 + lane;
-    if (i < in.N) walk_rows<ST>(in, i, l0, l1, f);
+    if (i < in.N) walk_rows<ST, 0, SCALED>(in, i, l0, l1, f);
     s += l1 - l0;
   }
 }
@@ -118,15 +118,15 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   const double sig = ls->sigma[j];
   const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
   double acc = 0.0;
-  for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2 u) {
+  // t = sigma_j H U_j directly (the operator scaled by sigma_j)
+  for_my_segments<ST, true>(scaled(in, sig), [&](int, size_t idx, double2 t, double2 u) {
     double2 o;
     if (j > 0) {
       const double2 up = uprev[idx];
-      o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, up.x));
-      o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, up.y));
+      o.x = __fma_rn(-cprev, up.x, t.x);
+      o.y = __fma_rn(-cprev, up.y, t.y);
     } else {
-      o.x = __dmul_rn(sig, t.x);
-      o.y = __dmul_rn(sig, t.y);
+      o = t;
     }
     z[idx] = o;
     acc = __fma_rn(u.x, o.x, acc);
@@ -377,6 +377,7 @@ StencilIn make_in(const Geometry &g, const OperatorView &op, double E, const dou
   in.c1 = g.c1;
   in.c2 = g.c2;
   in.E = E;
+  in.dscale = 1.0;
   return in;
 }
 

@@ -28,7 +28,20 @@ struct StencilIn {
   const double *__restrict__ kappa;
   int N, L;
   double c1, c2, E;
+  double dscale;   // walkers with SCALED multiply the diagonal by it (the other terms
+                   // are scaled through c1, c2 and E by the caller)
 };
+
+// The operator scaled by s: every coefficient that multiplies the operand is
+// multiplied by s once (c1, c2, E here, the diagonal point by point by the
+// SCALED walker), so s H x costs one FP64 multiply per point instead of two.
+__device__ __forceinline__ StencilIn scaled(StencilIn in, double s) {
+  in.c1 = __dmul_rn(s, in.c1);
+  in.c2 = __dmul_rn(s, in.c2);
+  in.E = __dmul_rn(s, in.E);
+  in.dscale = s;
+  return in;
+}
 
 // (H x) at (l, i) from the register window; 15 FP64 instructions (5-point).
 template <int ST>
@@ -147,7 +160,7 @@ __device__ __forceinline__ void split2(double2 v, float2 &h, float2 &lo) {
 
 // Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).  PF > 0
 // asks L2 for the operand and diagonal rows PF rows ahead.
-template <int ST, int PF = 0, typename F>
+template <int ST, int PF = 0, bool SCALED = false, typename F>
 __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const double2 z = make_double2(0.0, 0.0);
@@ -168,7 +181,7 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
     }
     const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
     const double a_next = __dmul_rn(in.kappa[l + 1], Er);
-    const double d = __ldg(in.diag + idx);
+    const double d = SCALED ? __dmul_rn(in.dscale, __ldg(in.diag + idx)) : __ldg(in.diag + idx);
     const double2 t = h_point<ST>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
     f(i, idx, t, cur);
     prev = cur;
