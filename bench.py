@@ -162,10 +162,10 @@ def start_state(seed: int = 31):
 # full launch by its points; the single-instance kernels on the at-scale grid
 # (512000 points).  An entry is removed when its kernel changes after capture.
 MEASURED_TRAFFIC_PER_POINT = {
-    ("batched", "fp64", "lanczos_a"): (531.5e6 + 169.3e6) / 10664737,
-    ("batched", "fp64", "lanczos_b"): (341.8e6 + 142.0e6) / 10664737,
-    ("batched", "mixed", "lanczos_a"): (313.2e6 + 78.1e6) / 10664737,
-    ("batched", "mixed", "lanczos_b"): (171.2e6 + 56.2e6) / 10664737,
+    ("batched", "fp64", "lanczos_a"): (537.7e6 + 169.0e6) / 10664737,
+    ("batched", "fp64", "lanczos_b"): (343.0e6 + 141.3e6) / 10664737,
+    ("batched", "mixed", "lanczos_a"): (297.0e6 + 70.0e6) / 10664737,
+    ("batched", "mixed", "lanczos_b"): (171.2e6 + 55.2e6) / 10664737,
     ("single", "fp64", "taylor_stage"): 20.6e6 / 512000,
 }
 
@@ -220,7 +220,7 @@ class BatchRow:
     step of every instance per benchmark step."""
     kind = "batched"
 
-    def __init__(self, prec, stream_ptr, count=256):
+    def __init__(self, prec, stream_ptr, count=256, schedule=None):
         from paper_1308_1856_gb300 import Batch
         self.specs = W.batched_specs(count, 1308)
         self.prec = prec
@@ -229,7 +229,12 @@ class BatchRow:
                   ncycles=x.ncycles, absorber_r=x.N * x.dr - BATCH_ABSORBER) for x in self.specs]
         self.b = Batch(d, stencil=5, precision=prec)
         self.b.set_stream(stream_ptr)
-        self.schedule = self.b.autotune()     # before the warm-up; not timed
+        if schedule is None:
+            self.schedule = self.b.autotune()     # before the warm-up; not timed
+        else:                                     # a fixed schedule (profiling runs)
+            pf, ring, sb, eb = schedule
+            self.b.set_schedule(pf, sb, eb, ring_rows=ring)
+            self.schedule = self.b.schedule()
         self.gp = self.b.points
         self.G = [x.N * (x.lmax + 1) for x in self.specs]
         self.e2e_bytes = (self.gp * 16, self.gp * 16)
@@ -356,7 +361,8 @@ def run_ours(args, ws, rank, local):
     if args.rows in ("all", "single"):
         rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
     if args.rows in ("all", "batched"):
-        rows += [BatchRow(p, stream.cuda_stream, count=args.batch_count) for p in ("fp64", "mixed")
+        rows += [BatchRow(p, stream.cuda_stream, count=args.batch_count, schedule=args.schedule.get(p))
+                 for p in ("fp64", "mixed")
                  if args.precision in ("all", p) and args.method in ("all", "lanczos")]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -565,6 +571,9 @@ def main():
                     help="restrict to the single-instance, batched or served rows")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched rows (smaller only for profiling captures)")
+    ap.add_argument("--schedule", action="append", default=[], metavar="PREC=PF,RING,SB,EB",
+                    help="fixed launch schedule of a batched row instead of autotuning (profiling runs): "
+                         "prefetch rows, ring rows, stencil and elementwise blocks per SM")
     ap.add_argument("--no-serve", action="store_true", help="skip the served traces")
     ap.add_argument("--serve-precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--serve-rate", type=float, default=50.0, help="overloaded trace: mean req/s")
@@ -576,6 +585,11 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-seed", type=int, default=1309)
     args = ap.parse_args()
+    sched = {}
+    for item in args.schedule:
+        prec, vals = item.split("=")
+        sched[prec] = tuple(int(v) for v in vals.split(","))
+    args.schedule = sched
     METHODS[:] = [m for m in ALL_METHODS if (args.method in ("all", m[0]))
                   and (args.precision in ("all", m[3]))]
     ws, rank, local = dist_env()
