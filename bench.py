@@ -255,11 +255,9 @@ class BatchRow:
         return self.b
 
     def e2e_step(self, pin_in, pin_out):
-        for i in range(len(self.specs)):
-            self.b.set_state_ptr(i, pin_in[i].data_ptr())
+        self.b.set_states_ptr(pin_in[0].data_ptr())
         self.step()
-        for i in range(len(self.specs)):
-            self.b.get_state_ptr(i, pin_out[i].data_ptr())
+        self.b.get_states_ptr(pin_out[0].data_ptr())
         return self.b.observables(0)
 
 
@@ -458,8 +456,7 @@ def run_ours(args, ws, rank, local):
             pin_in = [torch.from_numpy(psi0.view(np.float64).copy()).pin_memory()]
             pin_out = [torch.empty_like(pin_in[0]).pin_memory()]
         else:
-            pin_in = [torch.from_numpy(r.b.get_state(i).view(np.float64).copy()).pin_memory()
-                      for i in range(len(r.specs))] if e2e_steps else []
+            pin_in = [torch.from_numpy(r.b.get_states().view(np.float64)).pin_memory()] if e2e_steps else []
             pin_out = [torch.empty_like(p).pin_memory() for p in pin_in]
         pins.append((pin_in, pin_out))
     torch.cuda.synchronize()

@@ -269,6 +269,14 @@ int tdse_batch_set_state(tdse_batch_t *b, int i, const double *F_host);
 int tdse_batch_get_state(tdse_batch_t *b, int i, double *F_host);
 double tdse_batch_get_time(const tdse_batch_t *b, int i);
 
+/* Every instance's state in / out of ONE host buffer: instance i's
+ * (lmax_i+1)*N_i interleaved complex values follow instance i-1's, in
+ * instance order (tdse_batch_points complex values in all).  The copies are
+ * enqueued back to back and waited for once; pinned memory makes them
+ * asynchronous DMA. */
+int tdse_batch_set_states(tdse_batch_t *b, const double *F_all_host);
+int tdse_batch_get_states(tdse_batch_t *b, double *F_all_host);
+
 /*
  * Advance every instance by nsteps Lanczos steps of its own dt (asynchronous).
  * Errors: TDSE_ERR_ARG (nsteps < 0), TDSE_ERR_OOM, TDSE_ERR_CUDA.

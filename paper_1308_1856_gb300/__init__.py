@@ -216,6 +216,19 @@ class Batch:
     def time(self, i):
         return C.tdse_batch_get_time(self.h, int(i))
 
+    def set_states_ptr(self, host_ptr: int):
+        """All states from one host buffer (instance order, back to back)."""
+        self._check(C.tdse_batch_set_states(self.h, ctypes.c_void_p(host_ptr)))
+
+    def get_states_ptr(self, host_ptr: int):
+        self._check(C.tdse_batch_get_states(self.h, ctypes.c_void_p(host_ptr)))
+
+    def get_states(self):
+        """All states as one complex array (instance order, back to back)."""
+        out = np.empty(self.points, dtype=np.complex128)
+        self._check(C.tdse_batch_get_states(self.h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def propagate(self, nsteps: int):
         self._check(C.tdse_batch_propagate(self.h, int(nsteps)))
 

@@ -91,6 +91,8 @@ SIGNATURES = {
     "tdse_batch_set_state": (_c_int, [_vp, _c_int, _vp]),
     "tdse_batch_get_state": (_c_int, [_vp, _c_int, _vp]),
     "tdse_batch_get_time": (_c_double, [_vp, _c_int]),
+    "tdse_batch_set_states": (_c_int, [_vp, _vp]),
+    "tdse_batch_get_states": (_c_int, [_vp, _vp]),
     "tdse_batch_propagate": (_c_int, [_vp, _c_long]),
     "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
     "tdse_batch_points": (ctypes.c_longlong, [_vp]),
@@ -185,6 +187,8 @@ tdse_batch_set_stream = _fn("tdse_batch_set_stream")
 tdse_batch_set_state = _fn("tdse_batch_set_state")
 tdse_batch_get_state = _fn("tdse_batch_get_state")
 tdse_batch_get_time = _fn("tdse_batch_get_time")
+tdse_batch_set_states = _fn("tdse_batch_set_states")
+tdse_batch_get_states = _fn("tdse_batch_get_states")
 tdse_batch_propagate = _fn("tdse_batch_propagate")
 tdse_batch_observables = _fn("tdse_batch_observables")
 tdse_batch_points = _fn("tdse_batch_points")

@@ -1055,6 +1055,26 @@ int Engine::get_state(int slot, double *F) {
   return TDSE_OK;
 }
 
+int Engine::copy_states(const std::vector<int> &slots, double *F, bool to_device) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (!F) return fail(TDSE_ERR_ARG, "null state buffer");
+  size_t off = 0;
+  for (int slot : slots) {
+    if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+    const BatchInst &I = hinst[slot];
+    const size_t G = (size_t)I.N * (I.L + 1);
+    if (to_device) {
+      EN_CUDA(cudaMemcpyAsync(I.psi, F + off, sizeof(double2) * G, cudaMemcpyHostToDevice, stream), "set states");
+      norm_valid[slot] = 0;
+    } else {
+      EN_CUDA(cudaMemcpyAsync(F + off, I.psi, sizeof(double2) * G, cudaMemcpyDeviceToHost, stream), "get states");
+    }
+    off += 2 * G;
+  }
+  EN_CUDA(cudaStreamSynchronize(stream), "sync states");
+  return TDSE_OK;
+}
+
 // Append the chunk list of `ids` (stencil or elementwise chunks) to the host
 // staging; list_off receives its offset, the return value its chunk count.
 int Engine::launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off) {
@@ -1569,6 +1589,20 @@ int tdse_batch_set_state(tdse_batch_t *b, int i, const double *F) {
 
 int tdse_batch_get_state(tdse_batch_t *b, int i, double *F) {
   return b ? b->eng.get_state(i, F) : TDSE_ERR_ARG;
+}
+
+int tdse_batch_set_states(tdse_batch_t *b, const double *F_all) {
+  if (!b) return TDSE_ERR_ARG;
+  std::vector<int> slots(b->count);
+  for (int i = 0; i < b->count; ++i) slots[i] = i;
+  return b->eng.copy_states(slots, const_cast<double *>(F_all), true);
+}
+
+int tdse_batch_get_states(tdse_batch_t *b, double *F_all) {
+  if (!b) return TDSE_ERR_ARG;
+  std::vector<int> slots(b->count);
+  for (int i = 0; i < b->count; ++i) slots[i] = i;
+  return b->eng.copy_states(slots, F_all, false);
 }
 
 double tdse_batch_get_time(const tdse_batch_t *b, int i) {

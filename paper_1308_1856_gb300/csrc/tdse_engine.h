@@ -99,6 +99,9 @@ class Engine {
   int observables(int slot, std::vector<double> &out);
   int set_state(int slot, const double *F_host);
   int get_state(int slot, double *F_host);
+  // The states of `slots`, back to back in one host buffer (slot order), in or
+  // out with one wait at the end.
+  int copy_states(const std::vector<int> &slots, double *F_host, bool to_device);
   int sync();
   int set_stream(void *cuda_stream);
   int profile(int enable);

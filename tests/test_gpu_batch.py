@@ -130,3 +130,23 @@ def test_batch_autotune_leaves_the_state_untouched():
         a.set_schedule(0, 2, 2, ring_rows=4)
     a.close()
     b.close()
+
+
+def test_batch_all_states_in_one_buffer():
+    """tdse_batch_get_states / set_states move every instance's state through
+    one host buffer in instance order, the same values as per-instance calls."""
+    from paper_1308_1856_gb300 import Batch
+    b = Batch(SPECS)
+    b.propagate(3)
+    flat = b.get_states()
+    parts = [b.get_state(i).ravel() for i in range(len(SPECS))]
+    assert np.array_equal(flat, np.concatenate(parts))
+    rng = np.random.default_rng(5)
+    new = rng.normal(size=flat.shape) + 1j * rng.normal(size=flat.shape)
+    b.set_states_ptr(new.ctypes.data)
+    off = 0
+    for i, s in enumerate(SPECS):
+        G = s["N"] * (s["lmax"] + 1)
+        assert np.array_equal(b.get_state(i).ravel(), new[off:off + G])
+        off += G
+    b.close()
