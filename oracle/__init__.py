@@ -115,6 +115,8 @@ def _lib(precision: str = "f64"):
                                       ctypes.POINTER(_Mask), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_long, dp,
                                       ctypes.POINTER(ctypes.c_int)]
+        lib.orc_propagate_imag.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_long, dp, dp]
         lib.orc_lanczos_coefficients.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double,
                                                  ctypes.c_int, dp, dp, dp]
         lib.orc_observables.argtypes = [ctypes.POINTER(_Grid), dp, dp, ctypes.c_double, dp]
@@ -165,6 +167,19 @@ def propagate(grid: Grid, psi: np.ndarray, method: str, order: int, dt: float, n
                                        ctypes.byref(kmin))
     _check(rc, "propagate")
     return ps, kmin.value
+
+
+def propagate_imag(grid: Grid, psi: np.ndarray, method: str, order: int, dtau: float, nsteps: int,
+                   precision: str = "f64"):
+    """Imaginary-time steps (Sec. 3) with renormalisation after each; returns
+    (psi_new, energy estimate of the last step)."""
+    ps = _state(psi, grid)
+    g, keep = grid._c()
+    e = ctypes.c_double(0.0)
+    rc = _lib(precision).orc_propagate_imag(ctypes.byref(g), METHODS[method], int(order), float(dtau),
+                                            int(nsteps), _dptr(ps.view(np.float64)), ctypes.byref(e))
+    _check(rc, "propagate_imag")
+    return ps, e.value
 
 
 def lanczos_coefficients(grid: Grid, E: float, m: int, psi: np.ndarray, precision: str = "f64"):

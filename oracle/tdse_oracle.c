@@ -58,12 +58,16 @@ typedef long double REAL;
 #define RFABS fabsl
 #define RCOS cosl
 #define RSIN sinl
+#define REXP expl
+#define RLOG logl
 #else
 typedef double REAL;
 #define RSQRT sqrt
 #define RFABS fabs
 #define RCOS cos
 #define RSIN sin
+#define REXP exp
+#define RLOG log
 #endif
 
 /* ------------------------------------------------------------------------ */
@@ -219,15 +223,16 @@ static void store_state(const cplx *in, double *out, size_t n) {
 /*   F_{n+1} = sum_{p=0}^{P} F^{(p)},  F^{(0)} = F_n,                        */
 /*   F^{(p)} = (-i dt / p) H F^{(p-1)}     (factor read as 1/p, see header)  */
 /* ------------------------------------------------------------------------ */
+/* imag != 0: imaginary time (Sec. 3), F^{(p)} = (-dt / p) H F^{(p-1)}.      */
 static void taylor_step(const orc_grid *g, REAL E, int P, REAL dt, cplx *psi,
-                        cplx *term, cplx *tmp) {
+                        cplx *term, cplx *tmp, int imag) {
   const size_t n = dim(g);
   memcpy(term, psi, n * sizeof(cplx));
   for (int p = 1; p <= P; ++p) {
     apply_H(g, E, term, tmp);
     const REAL s = dt / (REAL)p;
     for (size_t i = 0; i < n; ++i) {
-      term[i] = c_scale(s, c_mul_minus_i(tmp[i]));
+      term[i] = imag ? c_scale(-s, tmp[i]) : c_scale(s, c_mul_minus_i(tmp[i]));
       psi[i] = c_add(psi[i], term[i]);
     }
   }
@@ -237,8 +242,9 @@ static void taylor_step(const orc_grid *g, REAL E, int P, REAL dt, cplx *psi,
 /* Classic RK4, Eq. (RKDeriv) with dF/dt = -i H(t) F (Eq. (tdse_matrix)):    */
 /* c = (0, 1/2, 1/2, 1), a_{21} = a_{32} = 1/2, a_{43} = 1, b = (1,2,2,1)/6. */
 /* ------------------------------------------------------------------------ */
+/* imag != 0: imaginary time, dF/dt = -H F.                                  */
 static void rk4_step(const orc_grid *g, const REAL Ec[4], REAL dt, cplx *psi,
-                     cplx *k, cplx *g_arg, cplx *acc) {
+                     cplx *k, cplx *g_arg, cplx *acc, int imag) {
   static const REAL a_prev[4] = {0, 0.5, 0.5, 1.0};   /* a_{i,i-1}          */
   static const REAL b[4] = {1, 2, 2, 1};              /* times 1/6          */
   const size_t n = dim(g);
@@ -249,7 +255,8 @@ static void rk4_step(const orc_grid *g, const REAL Ec[4], REAL dt, cplx *psi,
       g_arg[i] = (s == 0) ? psi[i] : c_add(psi[i], c_scale(dt * a_prev[s], k[i]));
     apply_H(g, Ec[s], g_arg, k);
     for (size_t i = 0; i < n; ++i) {
-      k[i] = c_mul_minus_i(k[i]);          /* k_s = -i H(t_n + c_s dt) g */
+      k[i] = imag ? c_scale(-1, k[i])      /* k_s = -H g (imaginary time) */
+                  : c_mul_minus_i(k[i]);   /* k_s = -i H(t_n + c_s dt) g */
       acc[i] = c_add(acc[i], c_scale(b[s], k[i]));
     }
   }
@@ -307,8 +314,9 @@ static void jacobi_eig(int n, REAL *A, REAL *w, REAL *V) {
 /*   F_{n+1} = ||F|| Q exp(-i T dt) e_1,  T = tridiag(beta, alpha, beta).    */
 /* Returns the Krylov dimension actually used.                               */
 /* ------------------------------------------------------------------------ */
+/* imag != 0: F_{n+1} = ||F|| Q exp(-T dt) e_1 (imaginary time).             */
 static int lanczos_step(const orc_grid *g, REAL E, int m, REAL dt, cplx *psi,
-                        cplx *Q /* (m+1) * n */, cplx *w, REAL *alpha, REAL *beta) {
+                        cplx *Q /* (m+1) * n */, cplx *w, REAL *alpha, REAL *beta, int imag) {
   const size_t n = dim(g);
   const REAL nrm = vec_norm(psi, n);
   if (nrm == 0) return 0;
@@ -349,8 +357,9 @@ static int lanczos_step(const orc_grid *g, REAL E, int m, REAL dt, cplx *psi,
   for (int i = 0; i < k; ++i) {
     cplx s = c_make(0, 0);
     for (int e = 0; e < k; ++e) {
-      const REAL ph = -lam[e] * dt;            /* exp(-i lambda dt) */
-      s = c_add(s, c_scale(V[i * k + e] * V[0 * k + e], c_make(RCOS(ph), RSIN(ph))));
+      const REAL ph = -lam[e] * dt;            /* exp(-i lambda dt), or exp(-lambda dt) */
+      const cplx f = imag ? c_make(REXP(ph), 0) : c_make(RCOS(ph), RSIN(ph));
+      s = c_add(s, c_scale(V[i * k + e] * V[0 * k + e], f));
     }
     c[i] = s;
   }
@@ -426,20 +435,60 @@ int orc_propagate(const orc_grid *g, const orc_pulse *pulse, const orc_mask *mas
   for (long s = 0; s < nsteps; ++s) {
     const double tn = t0 + (double)s * dt;
     if (method == ORC_TAYLOR) {
-      taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt, psi, w1, w2);
+      taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt, psi, w1, w2, 0);
     } else if (method == ORC_RK4) {
       const REAL Ec[4] = {(REAL)orc_field(pulse, tn), (REAL)orc_field(pulse, tn + 0.5 * dt),
                           (REAL)orc_field(pulse, tn + 0.5 * dt), (REAL)orc_field(pulse, tn + dt)};
-      rk4_step(g, Ec, (REAL)dt, psi, w1, w2, w3);
+      rk4_step(g, Ec, (REAL)dt, psi, w1, w2, w3, 0);
     } else {
       const int k = lanczos_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt,
-                                 psi, w2 /* Q: order+1 vectors */, w1, alpha, beta);
+                                 psi, w2 /* Q: order+1 vectors */, w1, alpha, beta, 0);
       if (k < kmin) kmin = k;
     }
     apply_mask(g, mask, psi);
   }
   store_state(psi, psi_io, n);
   if (min_krylov) *min_krylov = kmin;
+  free(buf);
+  return ORC_OK;
+}
+
+/*
+ * Imaginary-time propagation (Sec. 3, "Imaginary time"): the same propagators
+ * with -i replaced by -1 (no field, no mask).  Each step:
+ *   n0 = dr sum |F|^2;  F <- P(-H dt) F;  n1 = dr sum |F|^2;
+ *   E = -ln(n1 / n0) / (2 dt);  F <- F / sqrt(n1).
+ * For an eigenstate of eigenvalue lambda, E is lambda (Lanczos, exactly up to
+ * rounding) or -ln(T_P(-lambda dt)^2) / (2 dt) (Taylor-P; RK4 = Taylor-4).
+ * energy (may be NULL) receives the last step's E.
+ */
+int orc_propagate_imag(const orc_grid *g, int method, int order, double dt, long nsteps,
+                       double *psi_io, double *energy) {
+  if (!check_grid(g) || nsteps < 0 || !(dt > 0)) return ORC_ERR_ARG;
+  if (method < 0 || method > 2) return ORC_ERR_ARG;
+  if (method != ORC_RK4 && order < 1) return ORC_ERR_ARG;
+  if (method == ORC_LANCZOS && order > ORC_MAX_KRYLOV) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  const int nvec = (method == ORC_LANCZOS) ? order + 3 : 4;
+  cplx *buf = (cplx *)malloc((size_t)nvec * n * sizeof(cplx));
+  if (!buf) return ORC_ERR_OOM;
+  cplx *psi = buf, *w1 = buf + n, *w2 = buf + 2 * n, *w3 = buf + 3 * n;
+  REAL alpha[ORC_MAX_KRYLOV], beta[ORC_MAX_KRYLOV];
+  const REAL zero4[4] = {0, 0, 0, 0};
+  load_state(psi_io, psi, n);
+  REAL e = 0;
+  for (long s = 0; s < nsteps; ++s) {
+    const REAL n0 = (REAL)g->h * vec_norm(psi, n) * vec_norm(psi, n);
+    if (method == ORC_TAYLOR) taylor_step(g, 0, order, (REAL)dt, psi, w1, w2, 1);
+    else if (method == ORC_RK4) rk4_step(g, zero4, (REAL)dt, psi, w1, w2, w3, 1);
+    else lanczos_step(g, 0, order, (REAL)dt, psi, w2, w1, alpha, beta, 1);
+    const REAL n1 = (REAL)g->h * vec_norm(psi, n) * vec_norm(psi, n);
+    e = -RLOG(n1 / n0) / (2 * (REAL)dt);
+    const REAL sc = 1 / RSQRT(n1);
+    for (size_t i = 0; i < n; ++i) psi[i] = c_scale(sc, psi[i]);
+  }
+  store_state(psi, psi_io, n);
+  if (energy) *energy = (double)e;
   free(buf);
   return ORC_OK;
 }
@@ -457,7 +506,7 @@ int orc_lanczos_coefficients(const orc_grid *g, double E, int m, const double *p
   REAL alpha[ORC_MAX_KRYLOV], beta[ORC_MAX_KRYLOV];
   cplx *psi = buf, *w = buf + n, *Q = buf + 2 * n;
   load_state(psi_in, psi, n);
-  const int k = lanczos_step(g, (REAL)E, m, (REAL)1e-300, psi, Q, w, alpha, beta);
+  const int k = lanczos_step(g, (REAL)E, m, (REAL)1e-300, psi, Q, w, alpha, beta, 0);
   for (int i = 0; i < k; ++i) alpha_out[i] = (double)alpha[i];
   for (int i = 0; i + 1 < k; ++i) beta_out[i] = (double)beta[i];
   free(buf);

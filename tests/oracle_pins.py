@@ -24,7 +24,11 @@ Pins used (arXiv 1308.1856 passages in brackets):
     [Eq. (Dipole)]; populations sum to the norm; p_g of the reference is 1;
   * the sin^2 pulse vanishes at its end points, has zero area, is odd about
     T/2 and peaks at E0 [Sec. 3]; the cos^(1/8) mask is 1 inside and near 0
-    at the box edge [Sec. 2.1].
+    at the box edge [Sec. 2.1];
+  * imaginary time [Sec. 3]: on a grid eigenstate the energy estimate is the
+    eigenvalue (Lanczos) or the closed form of the Taylor/RK4 polynomial, and
+    from the 1s state it converges to the lowest eigenvalue and the paper's
+    printed ground-state energies [Sec. 6, Example 1].
 """
 from __future__ import annotations
 
@@ -313,7 +317,49 @@ def check_mask(prec="f64"):
     assert oracle.mask_value(off, R, R, prec) == 1.0
 
 
+def check_imaginary_time_eigenstate(prec="f64"):
+    """Imaginary time (Sec. 3) on a grid eigenstate phi with eigenvalue lam:
+    Lanczos (which stops at dimension 1) returns phi itself, normalised, and
+    the energy estimate lam; Taylor-P returns phi with the estimate
+    -ln(T_P(-lam dt)^2) / (2 dt), T_P the degree-P Taylor polynomial of exp;
+    RK4 the same with P = 4 (closed forms, not the oracle)."""
+    g = Grid(N=40, h=0.25, L=2, stencil=5, Z=1.0)
+    H = oracle.dense_H(g, 0.0, prec)
+    lam, V = np.linalg.eigh(H)
+    dt, P = 0.02, 8
+    for idx in (0, 7, 41):
+        phi = 1.7 * V[:, idx].reshape(3, 40).astype(complex) * np.exp(0.3j)
+        unit = phi / math.sqrt(g.h * float(np.sum(np.abs(phi) ** 2)))
+        for method, order, deg in (("lanczos", 6, None), ("taylor", P, P), ("rk4", 4, 4)):
+            out, e = oracle.propagate_imag(g, phi, method, order, dt, 2, precision=prec)
+            if deg is None:
+                want = lam[idx]
+            else:
+                tp = sum((-lam[idx] * dt) ** p / math.factorial(p) for p in range(deg + 1))
+                want = -math.log(tp * tp) / (2 * dt)
+            assert abs(e - want) <= 1e-10 * max(1.0, abs(want)), (method, idx, e, want)
+            assert np.abs(out - unit).max() <= 1e-10, (method, idx)
+
+
+def check_imaginary_time_ground_state(prec="f64"):
+    """From the 1s start state, imaginary-time Lanczos converges to the
+    lowest eigenvalue of the l = 0 block (banded eigensolver) and reaches
+    the paper's printed ground-state energies (near -0.47 without, near -0.5
+    with the -0.02 offset) [Sec. 6, Example 1]."""
+    pv = paper_values()
+    for key in ("ground_state_no_offset", "ground_state_offset"):
+        e = pv[key]
+        g = Grid(N=500, h=e["dr"], L=0, stencil=e["stencil"], offset=e["offset"], Z=1.0)
+        r = g.r()
+        psi = (2 * r * np.exp(-r)).astype(complex).reshape(1, -1)
+        _, E = oracle.propagate_imag(g, psi, "lanczos", 12, 0.5, 100, precision=prec)
+        low = _lowest(g, 0, prec)[0]
+        assert abs(E - low) <= 1e-11, (key, E, low)
+        assert abs(E - e["energy"]) <= e["tolerance"], (key, E)
+
+
 ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_hydrogen_paper_values, check_hydrogen_convergence,
               check_field_free_eigenstate, check_dense_expm, check_time_order,
-              check_norm_and_yield, check_observables, check_pulse, check_mask]
+              check_norm_and_yield, check_observables, check_pulse, check_mask,
+              check_imaginary_time_eigenstate, check_imaginary_time_ground_state]

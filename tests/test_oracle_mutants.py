@@ -50,6 +50,12 @@ MUTANTS = [
      P.check_norm_and_yield),
     ("mask_exponent", "pow(cos(x), 0.125)", "pow(cos(x), 0.25)", P.check_mask),
     ("envelope_period", "sin(M_PI * t / T);", "sin(2.0 * M_PI * t / T);", P.check_pulse),
+    ("imag_energy_printed_factor", "e = -RLOG(n1 / n0) / (2 * (REAL)dt);", "e = -RLOG(n1 / n0) / ((REAL)dt);",
+     P.check_imaginary_time_eigenstate),
+    ("imag_lanczos_exponent_sign", "c_make(REXP(ph), 0)", "c_make(REXP(-ph), 0)",
+     P.check_imaginary_time_ground_state),
+    ("imag_taylor_sign", "term[i] = imag ? c_scale(-s, tmp[i])", "term[i] = imag ? c_scale(s, tmp[i])",
+     P.check_imaginary_time_eigenstate),
 ]
 
 
