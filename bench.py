@@ -346,6 +346,34 @@ def run_served(args, stream_ptr):
     return out
 
 
+def mixed_error(stream_ptr, psi0, nsteps=10):
+    """The mixed-precision path's error against the FP64 path on the at-scale
+    grid: Lanczos-12 from the benchmark's start state, at a step where the
+    propagator converges (dt = 5e-6) and at the stated dt = 0.02, where
+    rounding is amplified (compare with the FP64 floor: tests/test_gpu_floor.py).
+    The FP64 path itself matches the oracle to 1e-12 per step (tests)."""
+    out = {}
+    for dt in (5e-6, CFG.dt):
+        res = {}
+        for prec in ("fp64", "mixed"):
+            h = make_handle(stream_ptr, prec)
+            h.set_state(psi0)
+            h.time = 0.3 * CFG.duration
+            h.propagate("lanczos", 12, dt, nsteps)
+            res[prec] = (h.get_state(), h.observables())
+            h.close()
+        (a, oa), (b, ob) = res["fp64"], res["mixed"]
+        big = oa["l_pop"] >= 1e-8
+        out[f"dt={dt:g}"] = {
+            "steps": nsteps,
+            "state_rel_l2": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+            "l_pop_max_rel_err": float(np.max(np.abs(ob["l_pop"][big] - oa["l_pop"][big]) / oa["l_pop"][big])),
+            "norm_abs_err": abs(ob["norm"] - oa["norm"]),
+            "dipole_abs_err": abs(ob["dipole"] - oa["dipole"]),
+        }
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -495,6 +523,8 @@ def run_ours(args, ws, rank, local):
     for r in rows:
         if hasattr(r.h, "close"):
             r.h.close()
+    if args.rows == "all":
+        result["mixed_error"] = mixed_error(stream.cuda_stream, psi0)
     if args.rows == "all" and not args.no_serve:
         result["served"] = run_served(args, stream.cuda_stream)
     return result

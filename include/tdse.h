@@ -149,6 +149,20 @@ int tdse_set_reference(tdse_t *h, const double *f0_host);
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps);
 
 /*
+ * Imaginary-time propagation (Sec. 3, "Imaginary time"): nsteps steps of the
+ * chosen propagator applied to exp(-H dtau) instead of exp(-i H dt), with no
+ * field and no absorber; after every step the state is renormalised
+ * (dr sum |f|^2 = 1) and the energy estimate
+ *   E = -ln(||psi_new||^2 / ||psi||^2) / (2 dtau)
+ * is formed (the paper prints -ln <psi|psi> / dt; the factor 1/2 makes an
+ * eigenstate's estimate its eigenvalue).  *energy (may be NULL) receives the
+ * last step's estimate; synchronises the stream.  The time t does not change.
+ * FP64 only: TDSE_ERR_ARG with TDSE_MIXED, dtau <= 0, nsteps < 0 or a bad
+ * method/order.
+ */
+int tdse_propagate_imag(tdse_t *h, int method, int order, double dtau, long nsteps, double *energy);
+
+/*
  * Observables of the current state (synchronises the stream), Sec. 4, each
  * integral taken as dr * sum over grid points:
  *   norm     = dr sum_l sum_j |f_lj|^2

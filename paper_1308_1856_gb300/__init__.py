@@ -118,6 +118,13 @@ class TDSE:
     def propagate(self, method: str, order: int, dt: float, nsteps: int):
         self._check(C.tdse_propagate(self.h, METHODS[method], int(order), float(dt), int(nsteps)))
 
+    def propagate_imag(self, method: str, order: int, dtau: float, nsteps: int) -> float:
+        """Imaginary-time steps with renormalisation; returns the last energy estimate."""
+        e = ctypes.c_double()
+        self._check(C.tdse_propagate_imag(self.h, METHODS[method], int(order), float(dtau), int(nsteps),
+                                          ctypes.byref(e)))
+        return e.value
+
     def observables(self) -> dict:
         norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
         lp = np.zeros(self.lmax + 1)

@@ -75,6 +75,7 @@ SIGNATURES = {
     "tdse_get_state_device": (_c_int, [_vp, _vp]),
     "tdse_set_reference": (_c_int, [_vp, _vp]),
     "tdse_propagate": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long]),
+    "tdse_propagate_imag": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long, _dp]),
     "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
     "tdse_sync": (_c_int, [_vp]),
@@ -172,6 +173,7 @@ tdse_set_state_device = _fn("tdse_set_state_device")
 tdse_get_state_device = _fn("tdse_get_state_device")
 tdse_set_reference = _fn("tdse_set_reference")
 tdse_propagate = _fn("tdse_propagate")
+tdse_propagate_imag = _fn("tdse_propagate_imag")
 tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")
 tdse_sync = _fn("tdse_sync")

@@ -31,6 +31,7 @@ struct tdse {
   LanczosScalars *ls = nullptr;
   int *status = nullptr;
   double *obs_partials = nullptr, *obs_out = nullptr;
+  double *imag = nullptr;          // imaginary time: {squared norm before the step, energy}
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
   // a final stage reads one pair with halos while writing the other) and
   // complex64 work vectors
@@ -196,6 +197,7 @@ void free_all(tdse *h) {
   cudaFree(h->status);
   cudaFree(h->obs_partials);
   cudaFree(h->obs_out);
+  cudaFree(h->imag);
   cudaFree(h->diagf);
   cudaFree(h->rjf);
   cudaFree(h->kappaf);
@@ -446,6 +448,69 @@ int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
                 "lanczos combine");
   }
   return TDSE_OK;
+}
+
+// Imaginary-time propagation (Sec. 3, "Imaginary time"): every step applies
+// the propagator of exp(-H dt) (field 0, no absorber), then
+//   E = -ln(||psi_new||^2 / ||psi||^2) / (2 dt),  psi <- psi_new / ||psi_new||
+// (norms dr-weighted).  energy receives the last step's estimate.
+int imag_steps(tdse *h, int method, int order, double dt, long nsteps, double *energy) {
+  if (!h->imag && cudaMalloc(&h->imag, 2 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->imag = nullptr;
+    return fail(h, TDSE_ERR_OOM, "imaginary-time scalars");
+  }
+  const size_t G = npts(h);
+  OperatorView op = view(h);
+  op.mask_start = h->g.N;   // no absorber in imaginary time
+  int rc = ensure_work(h, method == TDSE_LANCZOS ? (size_t)(order > 1 ? order : 1) : (method == TDSE_RK4 ? 3 : 2));
+  if (rc) return rc;
+  for (long n = 0; n < nsteps; ++n) {
+    TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
+    TDSE_CUDA(h, launch_imag_begin(h->red, h->g.dr, h->imag, h->stream), "imaginary-time norm");
+    if (method == TDSE_TAYLOR) {
+      double2 *buf[2] = {h->work, h->work + G};
+      const double2 *in = h->psi;
+      for (int k = order; k >= 1; --k) {
+        const bool last = (k == 1);
+        double2 *out = last ? ((order == 1) ? buf[0] : h->psi) : buf[(order - k) & 1];
+        TDSE_LAUNCH(h, TDSE_K_TAYLOR_STAGE,
+                    launch_taylor_stage(h->g, op, 0.0, dt / (double)k, in, h->psi, out, last, h->stream, true),
+                    "taylor stage");
+        in = out;
+      }
+      if (order == 1)
+        TDSE_CUDA(h, cudaMemcpyAsync(h->psi, buf[0], sizeof(double2) * G, cudaMemcpyDeviceToDevice, h->stream),
+                  "taylor copy");
+    } else if (method == TDSE_RK4) {
+      double2 *ga = h->work, *gb = h->work + G, *acc = h->work + 2 * G;
+      TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, 0.0, 1, dt, h->psi, h->psi, h->psi, acc, ga, nullptr, h->stream, true), "rk stage 1");
+      TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, 0.0, 2, dt, ga, h->psi, acc, acc, gb, nullptr, h->stream, true), "rk stage 2");
+      TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, 0.0, 3, dt, gb, h->psi, acc, acc, ga, nullptr, h->stream, true), "rk stage 3");
+      TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, 0.0, 4, dt, ga, h->psi, acc, nullptr, nullptr, h->psi, h->stream, true), "rk stage 4");
+    } else {
+      const int m = order;
+      double2 *z = h->work;
+      auto U = [&](int j) -> double2 * { return j == 0 ? h->psi : h->work + (size_t)j * G; };
+      for (int j = 0; j < m; ++j) {
+        TDSE_LAUNCH(h, TDSE_K_LANCZOS_A, launch_lanczos_a(h->g, op, 0.0, j, U(j), j > 0 ? U(j - 1) : nullptr, z, h->red, h->ls, h->stream),
+                    "lanczos a");
+        if (j + 1 < m)
+          TDSE_LAUNCH(h, TDSE_K_LANCZOS_B, launch_lanczos_b(h->g, j, z, U(j), U(j + 1), h->red, h->ls, h->stream), "lanczos b");
+      }
+      TDSE_LAUNCH(h, TDSE_K_LANCZOS_EXPM, launch_lanczos_expm(m, dt, h->ls, h->stream, true), "lanczos expm");
+      TDSE_LAUNCH(h, TDSE_K_LANCZOS_COMBINE, launch_lanczos_combine(h->g, op, m, h->psi, h->work + G, G, h->red, h->ls, h->status, h->stream),
+                  "lanczos combine");
+    }
+    TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
+    TDSE_CUDA(h, launch_imag_normalize(h->g, h->psi, h->red, dt, h->imag, h->stream), "imaginary-time normalise");
+  }
+  double out[2] = {0.0, 0.0};
+  if (nsteps > 0)
+    TDSE_CUDA(h, cudaMemcpyAsync(out, h->imag, sizeof(out), cudaMemcpyDeviceToHost, h->stream), "read energy");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync imaginary time");
+  if (energy) *energy = out[1];
+  return check_status_word(h);
 }
 
 void initial_state(const tdse *h, std::vector<double> &F) {
@@ -735,6 +800,24 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
   if (rc) return rc;
   h->t += (double)nsteps * dt;
   return TDSE_OK;
+}
+
+int tdse_propagate_imag(tdse_t *h, int method, int order, double dtau, long nsteps, double *energy) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!(dtau > 0.0) || !std::isfinite(dtau) || nsteps < 0)
+    return fail(h, TDSE_ERR_ARG, "need dtau > 0 and nsteps >= 0");
+  if (h->opts.precision != TDSE_FP64) return fail(h, TDSE_ERR_ARG, "imaginary time runs in FP64 only");
+  if (method == TDSE_TAYLOR && order < 1) return fail(h, TDSE_ERR_ARG, "Taylor order must be >= 1");
+  if (method == TDSE_LANCZOS && (order < 1 || order > TDSE_MAX_KRYLOV))
+    return fail(h, TDSE_ERR_ARG, "Krylov dimension must be in 1..TDSE_MAX_KRYLOV");
+  if (method != TDSE_TAYLOR && method != TDSE_RK4 && method != TDSE_LANCZOS)
+    return fail(h, TDSE_ERR_ARG, "unknown method");
+  // the real-time paths' cached norms and splits do not survive
+  h->lanczos_norm_valid = false;
+  h->split_valid = false;
+  h->mixed_norm_valid = false;
+  return imag_steps(h, method, order, dtau, nsteps, energy);
 }
 
 int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, double *yield,

@@ -68,13 +68,20 @@ struct OperatorView {
 
 cudaError_t launch_apply_h(const Geometry &g, const OperatorView &op, double E,
                            const double2 *x, double2 *y, cudaStream_t s);
+// imag: the stage of exp(-H dt) (imaginary time: -H instead of -i H, no mask).
 cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, double E, double s,
                                 const double2 *v_in, const double2 *psi, double2 *v_out,
-                                bool final_stage, cudaStream_t st);
+                                bool final_stage, cudaStream_t st, bool imag = false);
 cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E, int stage,
                             double dt, const double2 *gin, const double2 *psi,
                             const double2 *acc_in, double2 *acc_out, double2 *g_next,
-                            double2 *psi_out, cudaStream_t st);
+                            double2 *psi_out, cudaStream_t st, bool imag = false);
+// Imaginary time: prev[0] = dr * red->normsq (the squared norm before a step);
+// after the step (red->normsq of the new state): energy[0] =
+// -ln(dr normsq / prev) / (2 dt) and psi /= sqrt(dr normsq).
+cudaError_t launch_imag_begin(const Reduction *red, double dr, double *imag_dev, cudaStream_t st);
+cudaError_t launch_imag_normalize(const Geometry &g, double2 *psi, const Reduction *red, double dt,
+                                  double *imag_dev, cudaStream_t st);
 cudaError_t launch_norm(const Geometry &g, const double2 *x, Reduction *red,
                         LanczosScalars *ls, int *status, cudaStream_t st);
 cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E, int j,
@@ -82,7 +89,8 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
                              Reduction *red, LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
                              double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st);
-cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st);
+// imag: c = exp(-T dt) e_1 (imaginary-time propagation) instead of exp(-i T dt) e_1.
+cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag = false);
 // One block per listed instance: ids[0..count) index m, dt and ls (ids NULL:
 // instances 0..count-1).
 cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt,

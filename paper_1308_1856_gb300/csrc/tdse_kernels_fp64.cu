@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) apply_h_kernel(S
 }
 
 // Horner stage of the Taylor polynomial (Eq. (Taylor)):
-//   v_out = psi + (-i s) H v_in,  s = dt / k.
+//   v_out = psi + (-i s) H v_in,  s = dt / k   (IMAG: psi - s H v_in, Sec. 3's
+//   imaginary-time propagation).
 // The last stage (k = 1) writes psi itself and applies the absorber mask.
-template <int ST>
+template <int ST, bool IMAG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
@@ -74,8 +75,13 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const bool masked = i >= mstart;
     const double2 p = psi[idx];
     double2 o;
-    o.x = __fma_rn(s, t.y, p.x);     // (-i s)(tx + i ty) = s ty - i s tx
-    o.y = __fma_rn(-s, t.x, p.y);
+    if (IMAG) {
+      o.x = __fma_rn(-s, t.x, p.x);
+      o.y = __fma_rn(-s, t.y, p.y);
+    } else {
+      o.x = __fma_rn(s, t.y, p.x);     // (-i s)(tx + i ty) = s ty - i s tx
+      o.y = __fma_rn(-s, t.x, p.y);
+    }
     if (masked) { const double mv = mask[i]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
     out[idx] = o;
   });
@@ -84,7 +90,8 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 // Stage `stage` (1..4) of classic RK4 (Eq. (RKDeriv)) with k = -i H(t_n + c dt) g:
 //   stages 1-3: g_next = psi + (dt a) k,  acc_out = acc_in + (dt b) k  (acc_in = psi at stage 1)
 //   stage 4:    psi    = acc_in + (dt b) k, then the absorber mask.
-template <int ST>
+// IMAG: k = -H g (imaginary time) instead of -i H g.
+template <int ST, bool IMAG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     rk_stage_kernel(StencilIn in, int stage, double ca, double cb,
                     const double2 *__restrict__ psi, const double2 *__restrict__ acc_in,
@@ -94,12 +101,17 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   const int mstart = (stage == 4) ? mask_start : in.N;
   for_my_segments<ST>(in, [&](int i, size_t idx, double2 t, double2) {
     const double2 a = acc_in[idx];
+    // c k with k = -i t:  (c t.y, -c t.x);  with k = -t:  (-c t.x, -c t.y)
+    auto add = [&](double c, double2 base) {
+      return IMAG ? make_double2(__fma_rn(-c, t.x, base.x), __fma_rn(-c, t.y, base.y))
+                  : make_double2(__fma_rn(c, t.y, base.x), __fma_rn(-c, t.x, base.y));
+    };
     if (stage < 4) {
       const double2 p = psi[idx];
-      g_next[idx] = make_double2(__fma_rn(ca, t.y, p.x), __fma_rn(-ca, t.x, p.y));
-      acc_out[idx] = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
+      g_next[idx] = add(ca, p);
+      acc_out[idx] = add(cb, a);
     } else {
-      double2 o = make_double2(__fma_rn(cb, t.y, a.x), __fma_rn(-cb, t.x, a.y));
+      double2 o = add(cb, a);
       if (i >= mstart) { const double mv = mask[i]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
       psi_out[idx] = o;
     }
@@ -234,6 +246,24 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       if (!isfinite(s)) atomicOr(status, kStatusNonFinite);
     }
   }
+}
+
+// Imaginary time (Sec. 3): the squared norm before a step, then after it the
+// energy estimate and the renormalisation of psi.
+__global__ void imag_begin_kernel(const Reduction *red, double dr, double *imag) {
+  imag[0] = dr * red->normsq;
+}
+
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
+    imag_normalize_kernel(size_t G, double2 *psi, const Reduction *red, double dr, double dt,
+                          double *imag) {
+  const double n2 = dr * red->normsq;
+  const double sc = (n2 > 0.0) ? 1.0 / sqrt(n2) : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) imag[1] = -log(n2 / imag[0]) / (2.0 * dt);
+  for_my_groups(G, [&](size_t idx) {
+    const double2 v = psi[idx];
+    psi[idx] = make_double2(__dmul_rn(sc, v.x), __dmul_rn(sc, v.y));
+  });
 }
 
 // psi_new = sum_{j<k} coef_j U_j  (U_0 = psi, read and written in place by
@@ -401,34 +431,55 @@ cudaError_t launch_apply_h(const Geometry &g, const OperatorView &op, double E,
 
 cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, double E, double s,
                                 const double2 *v_in, const double2 *psi, double2 *v_out,
-                                bool final_stage, cudaStream_t st) {
+                                bool final_stage, cudaStream_t st, bool imag) {
   const StencilIn in = make_in(g, op, E, v_in);
   const unsigned grid = stencil_blocks(g);
-  if (g.stencil == 5)
-    taylor_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, op.mask_start,
-                                                     final_stage ? 1 : 0);
-  else
-    taylor_stage_kernel<3><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, op.mask_start,
-                                                     final_stage ? 1 : 0);
+  const int fin = final_stage ? 1 : 0;
+  const int mstart = imag ? g.N : op.mask_start;   // imaginary time: no absorber
+  if (g.stencil == 5) {
+    if (imag) taylor_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+    else taylor_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+  } else {
+    if (imag) taylor_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+    else taylor_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E, int stage,
                             double dt, const double2 *gin, const double2 *psi,
                             const double2 *acc_in, double2 *acc_out, double2 *g_next,
-                            double2 *psi_out, cudaStream_t st) {
+                            double2 *psi_out, cudaStream_t st, bool imag) {
   // classic tableau: a_{s+1,s} = (1/2, 1/2, 1), b = (1, 2, 2, 1) / 6
   static const double a_next[4] = {0.5, 0.5, 1.0, 0.0};
   static const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const StencilIn in = make_in(g, op, E, gin);
   const unsigned grid = stencil_blocks(g);
   const double ca = dt * a_next[stage - 1], cb = dt * b[stage - 1];
-  if (g.stencil == 5)
-    rk_stage_kernel<5><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next,
-                                                 psi_out, op.mask, op.mask_start);
-  else
-    rk_stage_kernel<3><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next,
-                                                 psi_out, op.mask, op.mask_start);
+  const int mstart = imag ? g.N : op.mask_start;
+  if (g.stencil == 5) {
+    if (imag)
+      rk_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+    else
+      rk_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+  } else {
+    if (imag)
+      rk_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+    else
+      rk_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_imag_begin(const Reduction *red, double dr, double *imag_dev, cudaStream_t st) {
+  imag_begin_kernel<<<1, 1, 0, st>>>(red, dr, imag_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_imag_normalize(const Geometry &g, double2 *psi, const Reduction *red, double dt,
+                                  double *imag_dev, cudaStream_t st) {
+  const size_t G = (size_t)g.N * (g.L + 1);
+  imag_normalize_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, psi, red, g.dr, dt, imag_dev);
   return cudaGetLastError();
 }
 

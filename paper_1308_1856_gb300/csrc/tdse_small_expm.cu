@@ -78,7 +78,8 @@ __device__ __forceinline__ void pair_of(int r, int t, int n, int &p, int &q) {
 
 // Thread mappings below use a row stride of 32 (w >> 5, w & 31) so that no
 // loop needs a runtime integer division.
-__device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls) {
+// imag: c = exp(-T dt) e_1 (imaginary time) instead of exp(-i T dt) e_1.
+__device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, bool imag = false) {
   __shared__ double al[KP], be[KP];
   __shared__ float Af[KP][KP + 1];
   __shared__ float Vf[KP][KP + 1];
@@ -313,12 +314,17 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls) 
     __syncthreads();
   }
 
-  // ---- c_i = sum_e X_ie X_0e exp(-i lambda_e dt) --------------------------
+  // ---- c_i = sum_e X_ie X_0e exp(-i lambda_e dt)  (exp(-lambda_e dt) if imag)
   if (tid < k) {
-    double sn, cs;
-    sincos(lam[tid] * dt, &sn, &cs);
-    W[0][tid] = X[0][tid] * cs;    // Re
-    W[1][tid] = -X[0][tid] * sn;   // Im
+    if (imag) {
+      W[0][tid] = X[0][tid] * exp(-lam[tid] * dt);
+      W[1][tid] = 0.0;
+    } else {
+      double sn, cs;
+      sincos(lam[tid] * dt, &sn, &cs);
+      W[0][tid] = X[0][tid] * cs;    // Re
+      W[1][tid] = -X[0][tid] * sn;   // Im
+    }
   }
   __syncthreads();
   if (tid < KP) {
@@ -351,8 +357,8 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls) 
   }
 }
 
-__global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, LanczosScalars *ls) {
-  expm_body(m, dt, ls);
+__global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, LanczosScalars *ls, int imag) {
+  expm_body(m, dt, ls, imag != 0);
 }
 
 // One block per listed instance of a batch (ids[b], or b when ids is null).
@@ -363,8 +369,8 @@ __global__ void __launch_bounds__(kEx)
   expm_body(m[i], dt[i], ls + i);
 }
 
-cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st) {
-  lanczos_expm_kernel<<<1, kEx, 0, st>>>(m, dt, ls);
+cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag) {
+  lanczos_expm_kernel<<<1, kEx, 0, st>>>(m, dt, ls, imag ? 1 : 0);
   return cudaGetLastError();
 }
 

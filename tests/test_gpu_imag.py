@@ -1,0 +1,61 @@
+"""Imaginary-time propagation (Sec. 3) on the GPU against the oracle: the
+state and the energy estimate after each method's steps, convergence to the
+grid ground state, and argument errors."""
+import numpy as np
+import pytest
+
+import oracle
+import tdse_workloads as W
+from gpu_helpers import grid_of, make, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+# Lanczos-12 at a step where the imaginary-time Krylov propagator converges on
+# every grid here (at dtau = 0.2 the 3-point dr = 0.1 grid has rho(H) dtau ~ 600
+# and the oracle itself drifts 3.5e-5 from its long-double build in 5 steps)
+@pytest.mark.parametrize("method,order,dtau", [("taylor", 8, 0.01), ("rk4", 4, 0.01), ("lanczos", 12, 0.005),
+                                               ("taylor", 1, 0.001), ("lanczos", 1, 0.05)])
+@pytest.mark.parametrize("geom", [(300, 0.2, 4, 5), (517, 0.1, 7, 3), (13, 0.25, 0, 5)])
+def test_imag_steps_match_oracle(method, order, dtau, geom):
+    N, dr, L, st = geom
+    psi = W.smooth_state(N, dr, L, seed=9)
+    t = make(N, dr, L, st, absorber_r=0.5 * N * dr)   # the absorber must be ignored in imaginary time
+    t.set_state(psi)
+    e_gpu = t.propagate_imag(method, order, dtau, 5)
+    got = t.get_state()
+    t.close()
+    want, e_orc = oracle.propagate_imag(grid_of(N, dr, L, st), psi, method, order, dtau, 5)
+    assert rel_l2(got, want) <= 1e-12, rel_l2(got, want)
+    assert abs(e_gpu - e_orc) <= 1e-11 * max(1.0, abs(e_orc)), (e_gpu, e_orc)
+
+
+def test_imag_ground_state_energy():
+    """From the 1s state at dr = 0.2 (5-point, zero ghost), imaginary-time
+    Lanczos converges to the grid's ground state, the paper's ~ -0.47 a.u.;
+    the result equals the oracle's and the state is normalised."""
+    N, dr = 500, 0.2
+    t = make(N, dr, 0, 5)
+    e = t.propagate_imag("lanczos", 12, 0.5, 100)
+    ob = t.observables()
+    state = t.get_state()
+    t.close()
+    g = grid_of(N, dr, 0, 5)
+    want, e_orc = oracle.propagate_imag(g, W.hydrogen_1s(N, dr, 0), "lanczos", 12, 0.5, 100)
+    assert abs(e - e_orc) <= 1e-12
+    assert abs(e - (-0.4714542026506671)) <= 1e-10
+    assert abs(ob["norm"] - 1.0) <= 1e-13
+    assert rel_l2(state, want) <= 1e-10
+
+
+def test_imag_arguments():
+    from paper_1308_1856_gb300 import TDSEError
+    t = make(50, 0.2, 1, 5)
+    with pytest.raises(TDSEError):
+        t.propagate_imag("lanczos", 12, -0.1, 3)
+    with pytest.raises(TDSEError):
+        t.propagate_imag("lanczos", 0, 0.1, 3)
+    t.set_options(precision="mixed")
+    with pytest.raises(TDSEError):
+        t.propagate_imag("taylor", 4, 0.1, 3)
+    t.close()
