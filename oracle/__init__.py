@@ -28,7 +28,8 @@ METHODS = {"taylor": TAYLOR, "rk4": RK4, "lanczos": LANCZOS}
 class _Grid(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_int), ("stencil", ctypes.c_int),
                 ("ghost", ctypes.c_int), ("h", ctypes.c_double), ("offset", ctypes.c_double),
-                ("Z", ctypes.c_double), ("vtable", ctypes.POINTER(ctypes.c_double))]
+                ("Z", ctypes.c_double), ("vtable", ctypes.POINTER(ctypes.c_double)),
+                ("gauge", ctypes.c_int)]
 
 
 class _Pulse(ctypes.Structure):
@@ -51,12 +52,13 @@ class Grid:
     offset: float = 0.0
     Z: float = 1.0
     vtable: Optional[np.ndarray] = None
+    gauge: int = 0          # 0: length gauge (r E coupling); 1: velocity gauge (A coupling)
 
     def r(self) -> np.ndarray:
         return np.arange(1, self.N + 1, dtype=np.float64) * self.h + self.offset
 
     def _c(self):
-        g = _Grid(self.N, self.L, self.stencil, self.ghost, self.h, self.offset, self.Z, None)
+        g = _Grid(self.N, self.L, self.stencil, self.ghost, self.h, self.offset, self.Z, None, self.gauge)
         keep = None
         if self.vtable is not None:
             keep = np.ascontiguousarray(self.vtable, dtype=np.float64)
@@ -122,6 +124,8 @@ def _lib(precision: str = "f64"):
         lib.orc_observables.argtypes = [ctypes.POINTER(_Grid), dp, dp, ctypes.c_double, dp]
         lib.orc_field.argtypes = [ctypes.POINTER(_Pulse), ctypes.c_double]
         lib.orc_field.restype = ctypes.c_double
+        lib.orc_vecpot.argtypes = [ctypes.POINTER(_Pulse), ctypes.c_double]
+        lib.orc_vecpot.restype = ctypes.c_double
         lib.orc_mask_value.argtypes = [ctypes.POINTER(_Mask), ctypes.c_double, ctypes.c_double]
         lib.orc_mask_value.restype = ctypes.c_double
         _LIBS[precision] = lib
@@ -214,6 +218,12 @@ def field(pulse: Pulse, t: float, precision: str = "f64") -> float:
     return _lib(precision).orc_field(ctypes.byref(pulse._c()), float(t))
 
 
+def vecpot(pulse: Pulse, t: float, precision: str = "f64") -> float:
+    """A(t) = -c int_0^t E (composite 5-point Gauss, Sec. 3)."""
+    p = pulse._c()
+    return _lib(precision).orc_vecpot(ctypes.byref(p), float(t))
+
+
 def mask_value(mask: Mask, r: float, R: float, precision: str = "f64") -> float:
     return _lib(precision).orc_mask_value(ctypes.byref(mask._c()), float(r), float(R))
 
@@ -237,14 +247,16 @@ def band_H(grid: Grid, E: float = 0.0, l: int = 0, precision: str = "f64") -> np
 
 
 def dense_H(grid: Grid, E: float, precision: str = "f64") -> np.ndarray:
-    """Dense matrix of H(E), assembled column by column from apply_H (tiny grids only)."""
+    """Dense matrix of H(E) (H(A) in the velocity gauge, complex), assembled
+    column by column from apply_H (tiny grids only)."""
     n = (grid.L + 1) * grid.N
     if n > 4096:
         raise ValueError("dense_H is for tiny grids")
-    H = np.empty((n, n))
+    H = np.empty((n, n), dtype=np.complex128 if grid.gauge else np.float64)
     e = np.zeros(n, dtype=np.complex128)
     for k in range(n):
         e[:] = 0
         e[k] = 1
-        H[:, k] = apply_H(grid, E, e.reshape(grid.L + 1, grid.N), precision).reshape(n).real
+        col = apply_H(grid, E, e.reshape(grid.L + 1, grid.N), precision).reshape(n)
+        H[:, k] = col if grid.gauge else col.real
     return H

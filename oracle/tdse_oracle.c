@@ -97,6 +97,7 @@ typedef struct {
   double offset;       /* constant shift of every grid point                  */
   double Z;            /* nuclear charge for V(r) = -Z/r                      */
   const double *vtable;/* optional V(r_j), length N; NULL selects -Z/r        */
+  int gauge;           /* 0 = length gauge (field E), 1 = velocity gauge (A)  */
 } orc_grid;
 
 typedef struct {
@@ -141,6 +142,25 @@ static cplx f_at(const orc_grid *g, const cplx *F, int l, int j) {
   return c_make(0, 0);
 }
 
+/* First derivative at index j: the 4th-order formula of Sec. 2 (printed as
+ * 1/(12 h^2)[...] with a garbled f_{j-1} term; read as the standard
+ * [-f_{j+2} + 8 f_{j+1} - 8 f_{j-1} + f_{j-2}] / (12 h)) for the 5-point
+ * stencil, [f_{j+1} - f_{j-1}] / (2 h) for the 3-point one.                 */
+static cplx d1_at(const orc_grid *g, const cplx *x, int l, int j) {
+  const REAL h = (REAL)g->h;
+  if (g->stencil == 5) {
+    cplx s = c_scale(-1, f_at(g, x, l, j + 2));
+    s = c_add(s, c_scale(8, f_at(g, x, l, j + 1)));
+    s = c_add(s, c_scale(-8, f_at(g, x, l, j - 1)));
+    s = c_add(s, f_at(g, x, l, j - 2));
+    return c_scale(1 / (12 * h), s);
+  }
+  return c_scale(1 / (2 * h), c_sub(f_at(g, x, l, j + 1), f_at(g, x, l, j - 1)));
+}
+
+/* Speed of light in atomic units. */
+#define ORC_C_AU 137.035999084
+
 /*
  * y = H(E) x for the length-gauge Hamiltonian of Eq. (h_matrix):
  *   diagonal blocks h_l = -1/2 d^2/dr^2 + l(l+1)/(2 r^2) + V(r)
@@ -174,8 +194,24 @@ static void apply_H(const orc_grid *g, REAL E, const cplx *x, cplx *y) {
       const REAL centrifugal = (REAL)l * (REAL)(l + 1) / (2 * r * r);
       cplx v = c_scale(-0.5, d2);
       v = c_add(v, c_scale(centrifugal + potential(g, j), f_at(g, x, l, j)));
-      if (l >= 1) v = c_add(v, c_scale(r * E * kappa(l), f_at(g, x, l - 1, j)));
-      if (l < L) v = c_add(v, c_scale(r * E * kappa(l + 1), f_at(g, x, l + 1, j)));
+      if (g->gauge == 0) {
+        if (l >= 1) v = c_add(v, c_scale(r * E * kappa(l), f_at(g, x, l - 1, j)));
+        if (l < L) v = c_add(v, c_scale(r * E * kappa(l + 1), f_at(g, x, l + 1, j)));
+      } else {
+        /* velocity gauge (Sec. 2, E holds A(t)): (A/c) p_z with p_z = -i d/dz in the
+         * partial-wave basis of psi = sum_l f_l(r)/r Y_l0,
+         *   -i (A/c) [ (d/dr - l/r) kappa_l f_{l-1} + (d/dr + (l+1)/r) kappa_{l+1} f_{l+1} ].
+         * Reading: the paper prints the l/r terms with the opposite signs; those
+         * fail p_z = i[H_0, z] and gauge invariance (see the design notes). */
+        cplx w = c_make(0, 0);
+        if (l >= 1)
+          w = c_add(w, c_scale(kappa(l), c_sub(d1_at(g, x, l - 1, j),
+                                               c_scale((REAL)l / r, f_at(g, x, l - 1, j)))));
+        if (l < L)
+          w = c_add(w, c_scale(kappa(l + 1), c_add(d1_at(g, x, l + 1, j),
+                                                   c_scale((REAL)(l + 1) / r, f_at(g, x, l + 1, j)))));
+        v = c_add(v, c_mul_minus_i(c_scale(E / (REAL)ORC_C_AU, w)));
+      }
       y[(size_t)l * N + (j - 1)] = v;
     }
   }
@@ -190,6 +226,37 @@ double orc_field(const orc_pulse *p, double t) {
   if (t < 0.0 || t > T) return 0.0;
   const double env = sin(M_PI * t / T);
   return p->E0 * env * env * sin(p->omega * t + p->cep);
+}
+
+/*
+ * Vector potential of the pulse, A(t) = -c int_0^t E(t') dt' (Sec. 3: A is
+ * obtained from E by 5-point Gauss quadrature).  Reading: the integral runs
+ * over fixed panels of [0, T] (the smallest number of equal panels no wider
+ * than 0.25 a.u.), each by 5-point Gauss-Legendre, plus the part of the
+ * panel that holds t; A(t) = A(T) for t > T and 0 for t < 0.
+ */
+static double gauss5(const orc_pulse *p, double a, double b) {
+  static const double x[5] = {-0.9061798459386640, -0.5384693101056831, 0.0,
+                              0.5384693101056831, 0.9061798459386640};
+  static const double w[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889,
+                              0.4786286704993665, 0.2369268850561891};
+  const double m = 0.5 * (a + b), hw = 0.5 * (b - a);
+  double s = 0.0;
+  for (int k = 0; k < 5; ++k) s += w[k] * orc_field(p, m + hw * x[k]);
+  return hw * s;
+}
+
+double orc_vecpot(const orc_pulse *p, double t) {
+  if (p->E0 == 0.0 || p->omega <= 0.0 || t <= 0.0) return 0.0;
+  const double T = 2.0 * M_PI * p->ncycles / p->omega;
+  const double tt = t < T ? t : T;
+  const long panels = (long)ceil(T / 0.25);
+  const double w = T / (double)panels;
+  const long full = (long)floor(tt / w);
+  double s = 0.0;
+  for (long k = 0; k < full && k < panels; ++k) s += gauss5(p, (double)k * w, (double)(k + 1) * w);
+  if (full < panels && tt > (double)full * w) s += gauss5(p, (double)full * w, tt);
+  return -ORC_C_AU * s;
 }
 
 /* Absorbing mask value at radius r (Sec. 2.1, applied as a mask). */
@@ -389,6 +456,7 @@ static int check_grid(const orc_grid *g) {
   if (!g || g->N < 1 || g->L < 0 || g->h <= 0) return 0;
   if (g->stencil != 3 && g->stencil != 5) return 0;
   if (g->ghost != 0 && g->ghost != 1) return 0;
+  if (g->gauge != 0 && g->gauge != 1) return 0;
   return 1;
 }
 
@@ -432,16 +500,18 @@ int orc_propagate(const orc_grid *g, const orc_pulse *pulse, const orc_mask *mas
   if (method == ORC_LANCZOS && order > ORC_MAX_KRYLOV) { free(buf); return ORC_ERR_ARG; }
   load_state(psi_io, psi, n);
   int kmin = order;
+  /* the coupling's time-dependent factor: E(t) in the length gauge, A(t) in the velocity gauge */
+  double (*coupling)(const orc_pulse *, double) = g->gauge ? orc_vecpot : orc_field;
   for (long s = 0; s < nsteps; ++s) {
     const double tn = t0 + (double)s * dt;
     if (method == ORC_TAYLOR) {
-      taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt, psi, w1, w2, 0);
+      taylor_step(g, (REAL)coupling(pulse, tn + 0.5 * dt), order, (REAL)dt, psi, w1, w2, 0);
     } else if (method == ORC_RK4) {
-      const REAL Ec[4] = {(REAL)orc_field(pulse, tn), (REAL)orc_field(pulse, tn + 0.5 * dt),
-                          (REAL)orc_field(pulse, tn + 0.5 * dt), (REAL)orc_field(pulse, tn + dt)};
+      const REAL Ec[4] = {(REAL)coupling(pulse, tn), (REAL)coupling(pulse, tn + 0.5 * dt),
+                          (REAL)coupling(pulse, tn + 0.5 * dt), (REAL)coupling(pulse, tn + dt)};
       rk4_step(g, Ec, (REAL)dt, psi, w1, w2, w3, 0);
     } else {
-      const int k = lanczos_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt), order, (REAL)dt,
+      const int k = lanczos_step(g, (REAL)coupling(pulse, tn + 0.5 * dt), order, (REAL)dt,
                                  psi, w2 /* Q: order+1 vectors */, w1, alpha, beta, 0);
       if (k < kmin) kmin = k;
     }

@@ -358,8 +358,81 @@ def check_imaginary_time_ground_state(prec="f64"):
         assert abs(E - e["energy"]) <= e["tolerance"], (key, E)
 
 
+C_AU = 137.035999084   # speed of light, atomic units (CODATA 2018)
+
+
+def check_velocity_gauge_operator(prec="f64"):
+    """Velocity gauge (Sec. 2): H(A) is Hermitian and equals the length-gauge
+    H0 at A = 0; its coupling is (A/c) p_z with p_z = i[H0, z] -- the
+    commutator of the field-free operator with the length-gauge coupling z
+    (H(E=1) - H(0)) -- which holds exactly for these difference formulas
+    away from r = 0 (the second-derivative weights times (r_k - r_j) are
+    twice the first-derivative weights)."""
+    for st in (3, 5):
+        g = Grid(N=30, h=0.3, L=3, stencil=st, gauge=1)
+        H = oracle.dense_H(g, 17.0, prec)
+        assert np.abs(H - H.conj().T).max() <= 1e-13 * np.abs(H).max(), "velocity H not Hermitian"
+        g0 = Grid(N=30, h=0.3, L=3, stencil=st)
+        assert np.array_equal(oracle.dense_H(g, 0.0, prec).real, oracle.dense_H(g0, 0.0, prec))
+        N, L = 400, 4
+        gl = Grid(N=N, h=0.05, L=L, stencil=st)
+        gv = Grid(N=N, h=0.05, L=L, stencil=st, gauge=1)
+        r = gl.r()
+        psi = np.zeros((L + 1, N), complex)
+        psi[0] = 2 * r * np.exp(-r)
+        psi[1] = (0.3 + 0.2j) * r * r * np.exp(-r / 2)
+        psi[3] = 0.1j * r ** 4 * np.exp(-r / 3)
+        h0 = lambda x: oracle.apply_H(gl, 0.0, x, prec)
+        z = lambda x: oracle.apply_H(gl, 1.0, x, prec) - h0(x)
+        pz = oracle.apply_H(gv, C_AU, psi, prec) - oracle.apply_H(gv, 0.0, psi, prec)
+        comm = 1j * (h0(z(psi)) - z(h0(psi)))
+        inner = slice(3, N - 3)
+        err = np.abs(comm - pz)[:, inner].max() / np.abs(pz).max()
+        assert err <= 1e-10, (st, err)
+
+
+def check_vector_potential(prec="f64"):
+    """A(t) = -c int_0^t E (Sec. 3): dA/dt = -c E (central differences), A = 0
+    before the pulse, and A(T) = 0 for the sin^2 pulse (zero area)."""
+    p = Pulse(E0=0.07, omega=0.11, ncycles=3, cep=0.4)
+    T = p.duration()
+    a_max = 0.0
+    for t in np.linspace(0.03 * T, 0.97 * T, 23):
+        hh = 1e-3
+        dA = (oracle.vecpot(p, t + hh, prec) - oracle.vecpot(p, t - hh, prec)) / (2 * hh)
+        E = oracle.field(p, t, prec)
+        assert abs(dA + C_AU * E) <= 1e-5 * C_AU * p.E0, (t, dA, E)
+        a_max = max(a_max, abs(oracle.vecpot(p, t, prec)))
+    assert oracle.vecpot(p, -1.0, prec) == 0.0
+    assert abs(oracle.vecpot(p, T, prec)) <= 1e-12 * a_max
+    assert oracle.vecpot(p, T + 5.0, prec) == oracle.vecpot(p, T, prec)
+
+
+def check_gauge_invariance(prec="f64"):
+    """Length and velocity gauge give the same physics once A = 0 again:
+    after the whole pulse the ground-state population and the partial-wave
+    populations agree between the gauges to the time-step error (the paper's
+    0.27145 vs 0.27144 comparison, Sec. 6, on a small grid)."""
+    pulse = Pulse(E0=0.05, omega=0.25, ncycles=1)
+    dt = 0.005
+    n = int(np.ceil(pulse.duration() / dt))
+    res = {}
+    for gauge in (0, 1):
+        g = Grid(N=300, h=0.1, L=6, stencil=5, gauge=gauge)
+        r = g.r()
+        psi0 = np.zeros((7, 300), complex)
+        psi0[0] = 2 * r * np.exp(-r)
+        psi0, _ = oracle.propagate_imag(g, psi0, "lanczos", 12, 0.5, 40, precision=prec)
+        out, _ = oracle.propagate(g, psi0, "lanczos", 10, dt, n, pulse=pulse, precision=prec)
+        res[gauge] = oracle.observables(g, out, psi0[0], r_b=10.0, precision=prec)
+    assert abs(res[0]["p_ground"] - res[1]["p_ground"]) <= 1e-4, res
+    assert np.abs(res[0]["l_pop"] - res[1]["l_pop"]).max() <= 1e-4
+    assert 1 - res[0]["p_ground"] >= 1e-3, "the pulse must change the state"
+
+
 ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_hydrogen_paper_values, check_hydrogen_convergence,
               check_field_free_eigenstate, check_dense_expm, check_time_order,
               check_norm_and_yield, check_observables, check_pulse, check_mask,
-              check_imaginary_time_eigenstate, check_imaginary_time_ground_state]
+              check_imaginary_time_eigenstate, check_imaginary_time_ground_state,
+              check_velocity_gauge_operator, check_vector_potential, check_gauge_invariance]

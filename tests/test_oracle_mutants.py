@@ -30,10 +30,10 @@ MUTANTS = [
      "const REAL s = dt / (REAL)(p > 1 ? p - 1 : 1);", P.check_field_free_eigenstate),
     ("rk4_weights", "static const REAL b[4] = {1, 2, 2, 1};",
      "static const REAL b[4] = {2, 1, 2, 1};", P.check_field_free_eigenstate),
-    ("rk4_stage_time", "(REAL)orc_field(pulse, tn + dt)};", "(REAL)orc_field(pulse, tn + 0.5 * dt)};",
+    ("rk4_stage_time", "(REAL)coupling(pulse, tn + dt)};", "(REAL)coupling(pulse, tn + 0.5 * dt)};",
      P.check_time_order),
-    ("taylor_field_time", "taylor_step(g, (REAL)orc_field(pulse, tn + 0.5 * dt)",
-     "taylor_step(g, (REAL)orc_field(pulse, tn)", P.check_time_order),
+    ("taylor_field_time", "taylor_step(g, (REAL)coupling(pulse, tn + 0.5 * dt)",
+     "taylor_step(g, (REAL)coupling(pulse, tn)", P.check_time_order),
     ("lanczos_drop_beta", "w[i] = c_sub(w[i], c_scale(beta[j - 1], qprev[i]));",
      "w[i] = w[i];", P.check_dense_expm),
     ("lanczos_alpha_sign", "a += qj[i].re * w[i].re + qj[i].im * w[i].im;",
@@ -56,6 +56,12 @@ MUTANTS = [
      P.check_imaginary_time_ground_state),
     ("imag_taylor_sign", "term[i] = imag ? c_scale(-s, tmp[i])", "term[i] = imag ? c_scale(s, tmp[i])",
      P.check_imaginary_time_eigenstate),
+    ("velocity_printed_signs", "w = c_add(w, c_scale(kappa(l), c_sub(d1_at(g, x, l - 1, j),",
+     "w = c_add(w, c_scale(kappa(l), c_add(d1_at(g, x, l - 1, j),", P.check_velocity_gauge_operator),
+    ("velocity_missing_c", "c_scale(E / (REAL)ORC_C_AU, w)", "c_scale(E, w)", P.check_velocity_gauge_operator),
+    ("vecpot_sign", "return -ORC_C_AU * s;", "return ORC_C_AU * s;", P.check_vector_potential),
+    ("first_derivative_weight", "s = c_add(s, c_scale(8, f_at(g, x, l, j + 1)));",
+     "s = c_add(s, c_scale(7, f_at(g, x, l, j + 1)));", P.check_velocity_gauge_operator),
 ]
 
 
