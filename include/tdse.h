@@ -59,6 +59,17 @@ enum { TDSE_STENCIL_3 = 3, TDSE_STENCIL_5 = 5 };
 enum { TDSE_TAYLOR = 0, TDSE_RK4 = 1, TDSE_LANCZOS = 2 };
 enum { TDSE_GHOST_ZERO = 0, TDSE_GHOST_ODD = 1 };
 enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
+/*
+ * Gauge of the laser coupling (Sec. 2).  Length: r E(t) kappa couplings.
+ * Velocity: (A(t)/c) p_z, p_z = -i [(d/dr - l/r) kappa_l f_{l-1} +
+ * (d/dr + (l+1)/r) kappa_{l+1} f_{l+1}] with the first derivative of the
+ * chosen stencil (4th-order 5-point, or 3-point central); A(t) = -c int_0^t E
+ * by composite 5-point Gauss quadrature on panels of at most 0.25 a.u. (the
+ * paper prints the l/r terms with the opposite signs, which breaks
+ * p_z = i[H_0, z] and gauge invariance).  The velocity gauge runs in FP64 with
+ * the zero ghost (TDSE_ERR_ARG otherwise); observables are the same formulas.
+ */
+enum { TDSE_GAUGE_LENGTH = 0, TDSE_GAUGE_VELOCITY = 1 };
 /* largest Krylov dimension tdse_propagate accepts for TDSE_LANCZOS */
 #define TDSE_MAX_KRYLOV 32
 
@@ -69,6 +80,7 @@ typedef struct {
   double absorber_r;    /* mask is 1 for r <= absorber_r and falls to r_N        */
   double r_b;           /* yield radius: yield = 1 - sum_{r_j <= r_b} |f|^2 dr   */
   int precision;        /* TDSE_FP64 (default) or TDSE_MIXED (see tdse_propagate) */
+  int gauge;            /* TDSE_GAUGE_LENGTH (default) or TDSE_GAUGE_VELOCITY     */
 } tdse_opts;
 
 /*
@@ -181,6 +193,7 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
  * stream); x and y hold (lmax+1)*N interleaved complex doubles, 16-byte
  * aligned, and must not overlap.  This is the bare operator of Eq. (h_matrix),
  * in FP64, or in the mixed arithmetic when tdse_opts.precision is TDSE_MIXED.
+ * In the velocity gauge E is the vector potential A.
  */
 int tdse_apply_h(tdse_t *h, double E, const void *x_dev, void *y_dev);
 

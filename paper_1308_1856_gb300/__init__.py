@@ -63,10 +63,11 @@ class TDSE:
 
     # -- C calls -------------------------------------------------------------------
     def set_options(self, ghost=0, offset=0.0, absorber=False, absorber_r=0.0, r_b=10.0,
-                    precision="fp64"):
+                    precision="fp64", gauge="length"):
         prec = {"fp64": C.TDSE_FP64, "mixed": C.TDSE_MIXED}[precision]
+        gg = {"length": C.TDSE_GAUGE_LENGTH, "velocity": C.TDSE_GAUGE_VELOCITY}[gauge]
         o = C.tdse_opts(int(ghost), float(offset), 1 if absorber else 0, float(absorber_r), float(r_b),
-                        prec)
+                        prec, gg)
         self._check(C.tdse_set_options(self.h, ctypes.byref(o)))
 
     def set_stream(self, stream_ptr: int):

@@ -21,6 +21,7 @@ TDSE_STENCIL_3, TDSE_STENCIL_5 = 3, 5
 TDSE_TAYLOR, TDSE_RK4, TDSE_LANCZOS = 0, 1, 2
 TDSE_GHOST_ZERO, TDSE_GHOST_ODD = 0, 1
 TDSE_FP64, TDSE_MIXED = 0, 1
+TDSE_GAUGE_LENGTH, TDSE_GAUGE_VELOCITY = 0, 1
 TDSE_MAX_KRYLOV = 32
 
 # Every symbol include/tdse.h declares: name -> (restype, argtypes)
@@ -31,7 +32,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class tdse_opts(ctypes.Structure):
     _fields_ = [("ghost", ctypes.c_int), ("offset", ctypes.c_double), ("absorber", ctypes.c_int),
                 ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("gauge", ctypes.c_int)]
 
 
 class tdse_instance_spec(ctypes.Structure):

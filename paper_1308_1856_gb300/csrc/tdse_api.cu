@@ -26,6 +26,7 @@ struct tdse {
   double2 *psi = nullptr, *ref0 = nullptr, *work = nullptr;
   size_t work_vecs = 0;
   double *diag = nullptr, *rj = nullptr, *kappa = nullptr, *mask = nullptr;
+  double *rinv = nullptr;          // 1 / r_j (velocity gauge)
   int mask_start = 0;
   Reduction *red = nullptr;
   LanczosScalars *ls = nullptr;
@@ -121,6 +122,7 @@ OperatorView view(const tdse *h) {
   op.rj = h->rj;
   op.kappa = h->kappa;
   op.mask = h->mask;
+  op.rinv = h->rinv;
   op.mask_start = (h->opts.absorber) ? h->mask_start : h->g.N;
   return op;
 }
@@ -177,6 +179,9 @@ int build_tables(tdse *h) {
   TDSE_CUDA(h, cudaMemcpyAsync(h->rjf, rf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s), "copy rf");
   TDSE_CUDA(h, cudaMemcpyAsync(h->kappaf, kf.data(), sizeof(float) * (L + 2), cudaMemcpyHostToDevice, s), "copy kf");
   TDSE_CUDA(h, cudaMemcpyAsync(h->rj, r.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy r");
+  std::vector<double> ri(N);
+  for (int j = 0; j < N; ++j) ri[j] = 1.0 / r[j];
+  TDSE_CUDA(h, cudaMemcpyAsync(h->rinv, ri.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy 1/r");
   TDSE_CUDA(h, cudaMemcpyAsync(h->diag, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice, s), "copy diag");
   TDSE_CUDA(h, cudaMemcpyAsync(h->kappa, kap.data(), sizeof(double) * (L + 2), cudaMemcpyHostToDevice, s), "copy kappa");
   TDSE_CUDA(h, cudaMemcpyAsync(h->mask, msk.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy mask");
@@ -190,6 +195,7 @@ void free_all(tdse *h) {
   cudaFree(h->work);
   cudaFree(h->diag);
   cudaFree(h->rj);
+  cudaFree(h->rinv);
   cudaFree(h->kappa);
   cudaFree(h->mask);
   cudaFree(h->red);
@@ -232,6 +238,41 @@ double field_at(const tdse *h, double t) {
   if (t < 0.0 || t > T) return 0.0;
   const double env = std::sin(M_PI * t / T);
   return h->E0 * env * env * std::sin(h->omega * t + h->cep);
+}
+
+constexpr double kLightAU = 137.035999084;   // speed of light, atomic units
+
+// int_a^b E by 5-point Gauss-Legendre.
+double field_integral(const tdse *h, double a, double b) {
+  static const double node[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                                 0.9061798459386640};
+  static const double weight[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889,
+                                   0.4786286704993665, 0.2369268850561891};
+  const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+  double acc = 0.0;
+  for (int k = 0; k < 5; ++k) acc += weight[k] * field_at(h, mid + half * node[k]);
+  return half * acc;
+}
+
+// A(t) = -c int_0^t E (Sec. 3): equal panels of [0, T], as few as keep them
+// at most 0.25 a.u. wide, each by 5-point Gauss, and the part of the panel
+// holding t; constant after the pulse.
+double vecpot_at(const tdse *h, double t) {
+  if (h->E0 == 0.0 || h->omega <= 0.0 || t <= 0.0) return 0.0;
+  const double T = 2.0 * M_PI * h->ncycles / h->omega;
+  const double tt = std::min(t, T);
+  const long panels = (long)std::ceil(T / 0.25);
+  const double w = T / (double)panels;
+  const long full = (long)std::floor(tt / w);
+  double acc = 0.0;
+  for (long k = 0; k < full && k < panels; ++k) acc += field_integral(h, (double)k * w, (double)(k + 1) * w);
+  if (full < panels && tt > (double)full * w) acc += field_integral(h, (double)full * w, tt);
+  return -kLightAU * acc;
+}
+
+// The coupling's time factor handed to the kernels: E(t), or A(t)/c in the velocity gauge.
+double coupling_at(const tdse *h, double t) {
+  return h->opts.gauge == TDSE_GAUGE_VELOCITY ? vecpot_at(h, t) / kLightAU : field_at(h, t);
 }
 
 int check_status_word(tdse *h) {
@@ -300,7 +341,7 @@ int mx_taylor_steps(tdse *h, int P, double dt, long nsteps) {
   float2 *wb[2] = {h->mwork, h->mwork + G};
   const double t0 = h->t;
   for (long n = 0; n < nsteps; ++n) {
-    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const double E = coupling_at(h, t0 + (double)n * dt + 0.5 * dt);
     const int cur = h->split_cur, nxt = 1 - cur;
     const float2 *w_in = nullptr;
     for (int k = P; k >= 1; --k) {
@@ -332,7 +373,7 @@ int mx_rk4_steps(tdse *h, double dt, long nsteps) {
   const double t0 = h->t;
   for (long n = 0; n < nsteps; ++n) {
     const double tn = t0 + (double)n * dt;
-    const double E1 = field_at(h, tn), E2 = field_at(h, tn + 0.5 * dt), E4 = field_at(h, tn + dt);
+    const double E1 = coupling_at(h, tn), E2 = coupling_at(h, tn + 0.5 * dt), E4 = coupling_at(h, tn + dt);
     const int cur = h->split_cur, nxt = 1 - cur;
     float2 *hi = split_hi(h, cur), *lo = split_lo(h, cur);
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E1, 1, dt, hi, lo, nullptr, ka, ahi, alo, h->psi, nullptr, nullptr, h->stream), "mixed rk 1");
@@ -358,7 +399,7 @@ int mx_lanczos_steps(tdse *h, int m, double dt, long nsteps) {
   auto U = [&](int j) -> float2 * { return h->mwork + (size_t)j * G; };   // j >= 1
   const double t0 = h->t;
   for (long n = 0; n < nsteps; ++n) {
-    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const double E = coupling_at(h, t0 + (double)n * dt + 0.5 * dt);
     float2 *hi = split_hi(h, h->split_cur), *lo = split_lo(h, h->split_cur);
     for (int j = 0; j < m; ++j) {
       TDSE_LAUNCH(h, TDSE_K_LANCZOS_A,
@@ -390,7 +431,7 @@ int taylor_steps(tdse *h, int P, double dt, long nsteps) {
   double2 *buf[2] = {h->work, h->work + G};
   const double t0 = h->t;
   for (long n = 0; n < nsteps; ++n) {
-    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const double E = coupling_at(h, t0 + (double)n * dt + 0.5 * dt);
     const double2 *in = h->psi;
     for (int k = P; k >= 1; --k) {
       const bool last = (k == 1);
@@ -415,7 +456,7 @@ int rk4_steps(tdse *h, double dt, long nsteps) {
   const double t0 = h->t;
   for (long n = 0; n < nsteps; ++n) {
     const double tn = t0 + (double)n * dt;
-    const double E1 = field_at(h, tn), E2 = field_at(h, tn + 0.5 * dt), E4 = field_at(h, tn + dt);
+    const double E1 = coupling_at(h, tn), E2 = coupling_at(h, tn + 0.5 * dt), E4 = coupling_at(h, tn + dt);
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E1, 1, dt, h->psi, h->psi, h->psi, acc, ga, nullptr, h->stream), "rk stage 1");
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 2, dt, ga, h->psi, acc, acc, gb, nullptr, h->stream), "rk stage 2");
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 3, dt, gb, h->psi, acc, acc, ga, nullptr, h->stream), "rk stage 3");
@@ -436,7 +477,7 @@ int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
   if (nsteps > 0 && !h->lanczos_norm_valid)
     TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
   for (long n = 0; n < nsteps; ++n) {
-    const double E = field_at(h, t0 + (double)n * dt + 0.5 * dt);
+    const double E = coupling_at(h, t0 + (double)n * dt + 0.5 * dt);
     for (int j = 0; j < m; ++j) {
       TDSE_LAUNCH(h, TDSE_K_LANCZOS_A, launch_lanczos_a(h->g, op, E, j, U(j), j > 0 ? U(j - 1) : nullptr, z, h->red, h->ls, h->stream),
                   "lanczos a");
@@ -587,6 +628,7 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
             cudaMalloc(&h->ref0, sizeof(double2) * N) == cudaSuccess &&
             cudaMalloc(&h->diag, sizeof(double) * G) == cudaSuccess &&
             cudaMalloc(&h->rj, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&h->rinv, sizeof(double) * N) == cudaSuccess &&
             cudaMalloc(&h->kappa, sizeof(double) * (lmax + 2)) == cudaSuccess &&
             cudaMalloc(&h->mask, sizeof(double) * N) == cudaSuccess &&
             cudaMalloc(&h->red, sizeof(Reduction)) == cudaSuccess &&
@@ -658,8 +700,13 @@ int tdse_set_options(tdse_t *h, const tdse_opts *o) {
   if (!std::isfinite(o->r_b)) return fail(h, TDSE_ERR_ARG, "r_b must be finite");
   if (o->precision != TDSE_FP64 && o->precision != TDSE_MIXED)
     return fail(h, TDSE_ERR_ARG, "precision must be TDSE_FP64 or TDSE_MIXED");
+  if (o->gauge != TDSE_GAUGE_LENGTH && o->gauge != TDSE_GAUGE_VELOCITY)
+    return fail(h, TDSE_ERR_ARG, "gauge must be TDSE_GAUGE_LENGTH or TDSE_GAUGE_VELOCITY");
+  if (o->gauge == TDSE_GAUGE_VELOCITY && (o->precision != TDSE_FP64 || o->ghost != TDSE_GHOST_ZERO))
+    return fail(h, TDSE_ERR_ARG, "the velocity gauge runs in FP64 with the zero ghost");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   h->opts = *o;
+  h->g.gauge = o->gauge;
   return build_tables(h);
 }
 
@@ -863,7 +910,9 @@ int tdse_apply_h(tdse_t *h, double E, const void *x, void *y) {
                 "mixed apply_h");
     return TDSE_OK;
   }
-  TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), E, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
+  // the velocity-gauge kernels take A/c
+  const double e = (h->opts.gauge == TDSE_GAUGE_VELOCITY) ? E / kLightAU : E;
+  TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), e, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
   return TDSE_OK;
 }
 

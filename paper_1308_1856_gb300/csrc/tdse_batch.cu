@@ -222,6 +222,8 @@ __device__ __forceinline__ StencilIn fp64_in(const BatchDev &B, const BatchInst 
   in.c2 = I.c2;
   in.E = field_of(B, inst);
   in.dscale = 1.0;
+  in.rinv = nullptr;   // the batch runs the length gauge
+  in.d1c = 0.0;
   return in;
 }
 

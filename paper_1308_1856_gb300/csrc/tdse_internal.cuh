@@ -55,6 +55,7 @@ enum : int { kStatusNonFinite = 1 };
 
 struct Geometry {
   int N, L, stencil;
+  int gauge = 0;                  // 0 length gauge (r E coupling), 1 velocity gauge (A p_z / c)
   int sms;                        // multiprocessors of the device (persistent grids)
   double dr;
   double c0, c1, c2;              // -1/2 d2/dr2 coefficients (c2 = 0 for 3 points)
@@ -63,6 +64,7 @@ struct Geometry {
 // ---- launchers (tdse_kernels_fp64.cu) -------------------------------------
 struct OperatorView {
   const double *diag, *rj, *kappa, *mask;
+  const double *rinv = nullptr;   // 1 / r_j (velocity gauge)
   int mask_start;                 // first j index (0-based) with mask != 1; N if none
 };
 

@@ -24,6 +24,8 @@
 // instructions (5-point Taylor stage: 17).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "tdse_device_common.cuh"
 #include "tdse_stencil.cuh"
 #include "tdse_internal.cuh"
@@ -36,7 +38,7 @@ using namespace common;
 using namespace stencil;
 
 // Visit this warp's share of the 32-point row segments (see the file header).
-template <int ST, bool SCALED = false, typename F>
+template <int ST, bool SCALED = false, bool VG = false, typename F>
 __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
   const int lane = threadIdx.x & 31;
   const int Lp1 = in.L + 1;
@@ -49,29 +51,29 @@ __device__ __forceinline__ void for_my_segments(const StencilIn &in, F &&f) {
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
     const int i = jg * 32 + lane;
-    if (i < in.N) walk_rows<ST, 0, SCALED>(in, i, l0, l1, f);
+    if (i < in.N) walk_rows<ST, 0, SCALED, VG>(in, i, l0, l1, f);
     s += l1 - l0;
   }
 }
 
 // ---------------------------------------------------------------------------
 // y = H(E) x
-template <int ST>
+template <int ST, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) apply_h_kernel(StencilIn in, double2 *__restrict__ y) {
-  for_my_segments<ST>(in, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
+  for_my_segments<ST, false, VG>(in, [&](int, size_t idx, double2 t, double2) { y[idx] = t; });
 }
 
 // Horner stage of the Taylor polynomial (Eq. (Taylor)):
 //   v_out = psi + (-i s) H v_in,  s = dt / k   (IMAG: psi - s H v_in, Sec. 3's
 //   imaginary-time propagation).
 // The last stage (k = 1) writes psi itself and applies the absorber mask.
-template <int ST, bool IMAG>
+template <int ST, bool IMAG, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
                         int mask_start, int final_stage) {
   const int mstart = final_stage ? mask_start : in.N;
-  for_my_segments<ST>(in, [&](int i, size_t idx, double2 t, double2) {
+  for_my_segments<ST, false, VG>(in, [&](int i, size_t idx, double2 t, double2) {
     const bool masked = i >= mstart;
     const double2 p = psi[idx];
     double2 o;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 //   stages 1-3: g_next = psi + (dt a) k,  acc_out = acc_in + (dt b) k  (acc_in = psi at stage 1)
 //   stage 4:    psi    = acc_in + (dt b) k, then the absorber mask.
 // IMAG: k = -H g (imaginary time) instead of -i H g.
-template <int ST, bool IMAG>
+template <int ST, bool IMAG, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     rk_stage_kernel(StencilIn in, int stage, double ca, double cb,
                     const double2 *__restrict__ psi, const double2 *__restrict__ acc_in,
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
                     double2 *__restrict__ psi_out, const double *__restrict__ mask,
                     int mask_start) {
   const int mstart = (stage == 4) ? mask_start : in.N;
-  for_my_segments<ST>(in, [&](int i, size_t idx, double2 t, double2) {
+  for_my_segments<ST, false, VG>(in, [&](int i, size_t idx, double2 t, double2) {
     const double2 a = acc_in[idx];
     // c k with k = -i t:  (c t.y, -c t.x);  with k = -t:  (-c t.x, -c t.y)
     auto add = [&](double c, double2 base) {
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 //   z = H q_j - beta_{j-1} q_{j-1},   q_j = sigma_j U_j,
 //   beta_{j-1} q_{j-1} = (sigma_{j-1} / sigma_j) U_{j-1},
 //   alpha_j = Re <q_j, z> = sigma_j Re <U_j, z>  (grid reduction; last block stores it).
-template <int ST>
+template <int ST, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     lanczos_a_kernel(StencilIn in, int j, const double2 *__restrict__ uprev,
                      double2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
   double acc = 0.0;
   // t = sigma_j H U_j directly (the operator scaled by sigma_j)
-  for_my_segments<ST, true>(scaled(in, sig), [&](int, size_t idx, double2 t, double2 u) {
+  for_my_segments<ST, true, VG>(scaled(in, sig), [&](int, size_t idx, double2 t, double2 u) {
     double2 o;
     if (j > 0) {
       const double2 up = uprev[idx];
@@ -408,7 +410,26 @@ StencilIn make_in(const Geometry &g, const OperatorView &op, double E, const dou
   in.c2 = g.c2;
   in.E = E;
   in.dscale = 1.0;
+  in.rinv = op.rinv;
+  in.d1c = (g.stencil == 5) ? 1.0 / (12.0 * g.dr) : 1.0 / (2.0 * g.dr);
   return in;
+}
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+template <bool V>
+using BC = std::integral_constant<bool, V>;
+
+// f(stencil, velocity gauge) with both as compile-time constants.
+template <typename F>
+void dispatch(const Geometry &g, bool vg, F &&f) {
+  if (g.stencil == 5) {
+    if (vg) f(IC<5>{}, BC<true>{});
+    else f(IC<5>{}, BC<false>{});
+  } else {
+    if (vg) f(IC<3>{}, BC<true>{});
+    else f(IC<3>{}, BC<false>{});
+  }
 }
 
 // Persistent grids: a few blocks per SM (all resident at once).
@@ -422,10 +443,9 @@ cudaError_t launch_apply_h(const Geometry &g, const OperatorView &op, double E,
                            const double2 *x, double2 *y, cudaStream_t s) {
   const StencilIn in = make_in(g, op, E, x);
   const unsigned grid = stencil_blocks(g);
-  if (g.stencil == 5)
-    apply_h_kernel<5><<<grid, kBlockJ, 0, s>>>(in, y);
-  else
-    apply_h_kernel<3><<<grid, kBlockJ, 0, s>>>(in, y);
+  dispatch(g, g.gauge == 1, [&](auto st, auto vg) {
+    apply_h_kernel<decltype(st)::value, decltype(vg)::value><<<grid, kBlockJ, 0, s>>>(in, y);
+  });
   return cudaGetLastError();
 }
 
@@ -435,14 +455,13 @@ cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, doubl
   const StencilIn in = make_in(g, op, E, v_in);
   const unsigned grid = stencil_blocks(g);
   const int fin = final_stage ? 1 : 0;
-  const int mstart = imag ? g.N : op.mask_start;   // imaginary time: no absorber
-  if (g.stencil == 5) {
-    if (imag) taylor_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
-    else taylor_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
-  } else {
-    if (imag) taylor_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
-    else taylor_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
-  }
+  const int mstart = imag ? g.N : op.mask_start;   // imaginary time: no absorber, no field
+  dispatch(g, !imag && g.gauge == 1, [&](auto stc, auto vg) {
+    constexpr int ST = decltype(stc)::value;
+    constexpr bool VG = decltype(vg)::value;
+    if (imag) taylor_stage_kernel<ST, true, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+    else taylor_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+  });
   return cudaGetLastError();
 }
 
@@ -457,17 +476,14 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
   const unsigned grid = stencil_blocks(g);
   const double ca = dt * a_next[stage - 1], cb = dt * b[stage - 1];
   const int mstart = imag ? g.N : op.mask_start;
-  if (g.stencil == 5) {
+  dispatch(g, !imag && g.gauge == 1, [&](auto stc, auto vg) {
+    constexpr int ST = decltype(stc)::value;
+    constexpr bool VG = decltype(vg)::value;
     if (imag)
-      rk_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+      rk_stage_kernel<ST, true, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
     else
-      rk_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
-  } else {
-    if (imag)
-      rk_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
-    else
-      rk_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
-  }
+      rk_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+  });
   return cudaGetLastError();
 }
 
@@ -495,10 +511,9 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
                              Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const StencilIn in = make_in(g, op, E, u);
   const unsigned grid = stencil_blocks(g);
-  if (g.stencil == 5)
-    lanczos_a_kernel<5><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
-  else
-    lanczos_a_kernel<3><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
+  dispatch(g, g.gauge == 1, [&](auto stc, auto vg) {
+    lanczos_a_kernel<decltype(stc)::value, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
+  });
   return cudaGetLastError();
 }
 

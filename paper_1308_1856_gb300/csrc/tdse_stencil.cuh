@@ -27,10 +27,30 @@ struct StencilIn {
   const double *__restrict__ rj;
   const double *__restrict__ kappa;
   int N, L;
-  double c1, c2, E;
+  double c1, c2, E;  // E: the field (length gauge) or A/c (velocity gauge)
   double dscale;   // walkers with SCALED multiply the diagonal by it (the other terms
                    // are scaled through c1, c2 and E by the caller)
+  const double *__restrict__ rinv;   // velocity gauge: 1 / r_j
+  double d1c;                        // velocity gauge: 1/(12 dr) (5-point) or 1/(2 dr) (3-point)
 };
+
+// First derivative of a row at column i (zero beyond the box): Sec. 2's
+// 4th-order formula [-f_{j+2} + 8 f_{j+1} - 8 f_{j-1} + f_{j-2}] / (12 dr), or
+// [f_{j+1} - f_{j-1}] / (2 dr) with the 3-point stencil.
+template <int ST>
+__device__ __forceinline__ double2 d1_point(const StencilIn &in, const double2 *row, int i) {
+  const double2 z = make_double2(0.0, 0.0);
+  const double2 m1 = (i >= 1) ? ldg2(row + i - 1) : z;
+  const double2 p1 = (i + 1 < in.N) ? ldg2(row + i + 1) : z;
+  if (ST == 5) {
+    const double2 m2 = (i >= 2) ? ldg2(row + i - 2) : z;
+    const double2 p2 = (i + 2 < in.N) ? ldg2(row + i + 2) : z;
+    return make_double2(
+        __dmul_rn(in.d1c, __fma_rn(8.0, __dsub_rn(p1.x, m1.x), __dsub_rn(m2.x, p2.x))),
+        __dmul_rn(in.d1c, __fma_rn(8.0, __dsub_rn(p1.y, m1.y), __dsub_rn(m2.y, p2.y))));
+  }
+  return make_double2(__dmul_rn(in.d1c, __dsub_rn(p1.x, m1.x)), __dmul_rn(in.d1c, __dsub_rn(p1.y, m1.y)));
+}
 
 // The operator scaled by s: every coefficient that multiplies the operand is
 // multiplied by s once (c1, c2, E here, the diagonal point by point by the
@@ -44,7 +64,8 @@ __device__ __forceinline__ StencilIn scaled(StencilIn in, double s) {
 }
 
 // (H x) at (l, i) from the register window; 15 FP64 instructions (5-point).
-template <int ST>
+// LG = false leaves out the length-gauge coupling (the velocity gauge adds its own).
+template <int ST, bool LG = true>
 __device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *row, int i,
                                            double d, double2 prev, double2 cur, double2 next,
                                            double a_cur, double a_next) {
@@ -61,10 +82,12 @@ __device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *r
     tx = __fma_rn(in.c2, __dadd_rn(m2.x, p2.x), tx);
     ty = __fma_rn(in.c2, __dadd_rn(m2.y, p2.y), ty);
   }
-  tx = __fma_rn(a_cur, prev.x, tx);
-  ty = __fma_rn(a_cur, prev.y, ty);
-  tx = __fma_rn(a_next, next.x, tx);
-  ty = __fma_rn(a_next, next.y, ty);
+  if (LG) {
+    tx = __fma_rn(a_cur, prev.x, tx);
+    ty = __fma_rn(a_cur, prev.y, ty);
+    tx = __fma_rn(a_next, next.x, tx);
+    ty = __fma_rn(a_next, next.y, ty);
+  }
   return make_double2(tx, ty);
 }
 
@@ -160,7 +183,10 @@ __device__ __forceinline__ void split2(double2 v, float2 &h, float2 &lo) {
 
 // Walk rows [l0, l1) of column i and call f(i, idx, Hx, x_center).  PF > 0
 // asks L2 for the operand and diagonal rows PF rows ahead.
-template <int ST, int PF = 0, bool SCALED = false, typename F>
+// VG: velocity gauge, (A/c) p_z with p_z = -i [ (d/dr - l/r) kappa_l f_{l-1}
+// + (d/dr + (l+1)/r) kappa_{l+1} f_{l+1} ] (the partial-wave form of -i d/dz;
+// the paper prints the l/r terms with the opposite signs) in place of r E kappa.
+template <int ST, int PF = 0, bool SCALED = false, bool VG = false, typename F>
 __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const double2 z = make_double2(0.0, 0.0);
@@ -182,7 +208,26 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
     const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
     const double a_next = __dmul_rn(in.kappa[l + 1], Er);
     const double d = SCALED ? __dmul_rn(in.dscale, __ldg(in.diag + idx)) : __ldg(in.diag + idx);
-    const double2 t = h_point<ST>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
+    double2 t = h_point<ST, !VG>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
+    if (VG) {
+      const double ri = __ldg(in.rinv + i);
+      double wx = 0.0, wy = 0.0;
+      if (l > 0) {
+        const double2 dp = d1_point<ST>(in, in.x + (size_t)(l - 1) * N, i);
+        const double k = in.kappa[l], lr = __dmul_rn((double)l, ri);
+        wx = __dmul_rn(k, __fma_rn(-lr, prev.x, dp.x));
+        wy = __dmul_rn(k, __fma_rn(-lr, prev.y, dp.y));
+      }
+      if (l < L) {
+        const double2 dn = d1_point<ST>(in, in.x + (size_t)(l + 1) * N, i);
+        const double k = in.kappa[l + 1], lr = __dmul_rn((double)(l + 1), ri);
+        wx = __fma_rn(k, __fma_rn(lr, next.x, dn.x), wx);
+        wy = __fma_rn(k, __fma_rn(lr, next.y, dn.y), wy);
+      }
+      // -i (A/c) w
+      t.x = __fma_rn(in.E, wy, t.x);
+      t.y = __fma_rn(-in.E, wx, t.y);
+    }
     f(i, idx, t, cur);
     prev = cur;
     cur = next;

@@ -12,19 +12,19 @@ def rel_l2(a, b) -> float:
 
 
 def make(N, dr, L, stencil, *, ghost=0, offset=0.0, Z=1.0, vtable=None, pulse=None,
-         absorber_r=None, r_b=10.0):
+         absorber_r=None, r_b=10.0, gauge="length"):
     from paper_1308_1856_gb300 import TDSE
     t = TDSE(N, dr, L, stencil=stencil, Z=Z, v_table=vtable)
     t.set_options(ghost=ghost, offset=offset, absorber=absorber_r is not None,
-                  absorber_r=absorber_r or 0.0, r_b=r_b)
+                  absorber_r=absorber_r or 0.0, r_b=r_b, gauge=gauge)
     if pulse is not None:
         t.set_pulse(pulse.E0, pulse.omega, pulse.ncycles, pulse.cep)
     return t
 
 
-def grid_of(N, dr, L, stencil, *, ghost=0, offset=0.0, Z=1.0, vtable=None):
+def grid_of(N, dr, L, stencil, *, ghost=0, offset=0.0, Z=1.0, vtable=None, gauge=0):
     return oracle.Grid(N=N, h=dr, L=L, stencil=stencil, ghost=ghost, offset=offset, Z=Z,
-                       vtable=vtable)
+                       vtable=vtable, gauge=gauge)
 
 
 def apply_h_gpu(t, E, x: np.ndarray) -> np.ndarray:

@@ -1,0 +1,86 @@
+"""The velocity gauge (Sec. 2) on the GPU against the oracle: the operator,
+single steps of every method, a whole pulse, gauge invariance against the
+GPU's own length gauge, and the argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+import tdse_workloads as W
+from gpu_helpers import apply_h_gpu, grid_of, make, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("N,dr,L,st", [(7, 0.3, 2, 3), (33, 0.2, 5, 5), (257, 0.1, 6, 5),
+                                       (1000, 0.05, 9, 5), (517, 0.2, 13, 3)])
+def test_velocity_apply_h(N, dr, L, st):
+    g = grid_of(N, dr, L, st, gauge=1)
+    t = make(N, dr, L, st, gauge="velocity")
+    # Both sides round each term once but in different orders (the GPU's
+    # diagonal c0 + l(l+1)/(2r^2) + V is one table entry), so the difference is
+    # a few unit roundoffs of the largest terms: |c0| |x| ~ 1.25/dr^2 |x|
+    # against |Hx|.  Random states have no cancellation (|Hx| ~ |c0| |x|);
+    # smooth ones cancel down to |Hx| ~ |x|, i.e. up to ~1e3 at dr = 0.05.
+    for x, tol in ((W.smooth_state(N, dr, L, seed=3), 1e-12), (W.random_state(N, L, seed=4), 1e-13)):
+        for A in (0.0, 1.7, -31.0):
+            got = apply_h_gpu(t, A, x)
+            want = oracle.apply_H(g, A, x)
+            assert rel_l2(got, want) <= tol, (A, tol, rel_l2(got, want))
+    t.close()
+
+
+@pytest.mark.parametrize("method,order,dt", [("taylor", 8, 0.01), ("rk4", 4, 0.005), ("lanczos", 12, 0.05),
+                                             ("lanczos", 1, 0.01)])
+@pytest.mark.parametrize("geom", [(500, 0.2, 4, 3), (1000, 0.05, 9, 5)])
+def test_velocity_one_step(method, order, dt, geom):
+    N, dr, L, st = geom
+    if method != "lanczos":
+        dt = min(dt, 2.5 / (2.7 / dr ** 2 + L * (L + 1) / (2 * dr ** 2)))   # stable explicit step
+    pulse = oracle.Pulse(E0=0.0534, omega=0.057, ncycles=2)
+    psi = W.smooth_state(N, dr, L, seed=5)
+    t = make(N, dr, L, st, pulse=pulse, gauge="velocity")
+    t.set_state(psi)
+    t.time = 70.0
+    t.propagate(method, order, dt, 1)
+    got = t.get_state()
+    t.close()
+    want, _ = oracle.propagate(grid_of(N, dr, L, st, gauge=1), psi, method, order, dt, 1, t0=70.0, pulse=pulse)
+    assert rel_l2(got, want) <= 1e-12, rel_l2(got, want)
+
+
+def test_velocity_full_pulse_and_gauge_invariance():
+    """A one-cycle pulse on a small grid from the imaginary-time ground state:
+    the velocity-gauge run matches the oracle over all steps, and after the
+    pulse its populations match the GPU's length-gauge run to the step error."""
+    N, dr, L = 300, 0.1, 6
+    pulse = oracle.Pulse(E0=0.05, omega=0.25, ncycles=1)
+    dt = 0.005
+    n = int(np.ceil(pulse.duration() / dt))
+    # the start state comes from the oracle (no oracle input comes from the GPU)
+    psi0, _ = oracle.propagate_imag(grid_of(N, dr, L, 5), W.hydrogen_1s(N, dr, L), "lanczos", 12, 0.5, 40)
+    out = {}
+    for gauge in ("length", "velocity"):
+        t = make(N, dr, L, 5, pulse=pulse, gauge=gauge)
+        t.set_state(psi0)
+        t.set_reference(psi0[0])
+        t.propagate("lanczos", 10, dt, n)
+        out[gauge] = (t.get_state(), t.observables())
+        t.close()
+    got, ob = out["velocity"]
+    want, _ = oracle.propagate(grid_of(N, dr, L, 5, gauge=1), psi0, "lanczos", 10, dt, n, pulse=pulse)
+    assert rel_l2(got, want) <= 1e-10, rel_l2(got, want)
+    ol = out["length"][1]
+    assert abs(ob["p_ground"] - ol["p_ground"]) <= 1e-4, (ob["p_ground"], ol["p_ground"])
+    assert np.abs(ob["l_pop"] - ol["l_pop"]).max() <= 1e-4
+    assert 1 - ol["p_ground"] >= 1e-3
+
+
+def test_velocity_arguments():
+    from paper_1308_1856_gb300 import TDSEError
+    t = make(50, 0.2, 2, 5)
+    with pytest.raises(TDSEError):
+        t.set_options(gauge="velocity", precision="mixed")
+    with pytest.raises(TDSEError):
+        t.set_options(gauge="velocity", ghost=1)
+    t.set_options(gauge="velocity")
+    t.close()
