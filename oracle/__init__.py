@@ -117,6 +117,9 @@ def _lib(precision: str = "f64"):
                                       ctypes.POINTER(_Mask), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_long, dp,
                                       ctypes.POINTER(ctypes.c_int)]
+        lib.orc_propagate_rk.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Pulse),
+                                         ctypes.POINTER(_Mask), ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_long, dp, dp]
         lib.orc_propagate_imag.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_long, dp, dp]
         lib.orc_lanczos_coefficients.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double,
@@ -171,6 +174,25 @@ def propagate(grid: Grid, psi: np.ndarray, method: str, order: int, dt: float, n
                                        ctypes.byref(kmin))
     _check(rc, "propagate")
     return ps, kmin.value
+
+
+RK_TABLEAUS = {"euler": 0, "classic": 1, "fehlberg": 2, "cash_karp": 3, "dormand_prince": 4, "merson": 5}
+
+
+def propagate_rk(grid: Grid, psi: np.ndarray, tableau: str, dt: float, nsteps: int, t0: float = 0.0,
+                 pulse: Optional[Pulse] = None, mask: Optional[Mask] = None, precision: str = "f64"):
+    """Explicit RK steps with the named tableau (Sec. "Runge-Kutta"); returns
+    (psi_new, sigma = sum over the steps of sqrt(|Delta|^2 / S))."""
+    ps = _state(psi, grid)
+    g, keep = grid._c()
+    p = (pulse or Pulse())._c()
+    m = (mask or Mask(0.0, on=False))._c()
+    sig = ctypes.c_double(0.0)
+    rc = _lib(precision).orc_propagate_rk(ctypes.byref(g), ctypes.byref(p), ctypes.byref(m),
+                                          RK_TABLEAUS[tableau], float(dt), float(t0), int(nsteps),
+                                          _dptr(ps.view(np.float64)), ctypes.byref(sig))
+    _check(rc, "propagate_rk")
+    return ps, sig.value
 
 
 def propagate_imag(grid: Grid, psi: np.ndarray, method: str, order: int, dtau: float, nsteps: int,

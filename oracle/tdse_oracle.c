@@ -25,6 +25,11 @@
  *   Runge-Kutta (classic RK4) .............. Sec. 5 "RungeKutta.c", Eq. (RKDeriv)
  *   Lanczos propagator ..................... Sec. 5 "Lanczos.c", Appendix
  *                                            "Lanczos methods"
+ *   explicit RK and embedded pairs ......... Sec. "Runge-Kutta" (method list
+ *                                            and the error estimate sigma)
+ *   imaginary-time propagation ............. Sec. 3 (dt -> -i dtau)
+ *   velocity gauge ......................... Sec. 2, Eq. (tdse-potential) (G = V)
+ *                                            and Sec. 3, Eq. (VectorStep)
  *   observables ............................ Sec. 4, Eqs. (p_g), (p_b),
  *                                            (yield_1), (Norm), (Dipole)
  *
@@ -46,7 +51,10 @@
  *     eigendecomposition of the real symmetric tridiagonal T;
  *   - the absorber is the mask M(r) = cos^{1/8}(pi/2 (r - r_a)/(R - r_a)) for
  *     r > r_a (R = r_N), applied once after every full step;
- *   - integrals are h * sum over grid points; p_g is |<psi_0|psi>|^2.
+ *   - integrals are h * sum over grid points; p_g is |<psi_0|psi>|^2;
+ *   - an embedded RK pair propagates its higher-order solution, and the S of
+ *     sigma_n = sqrt(|Delta|^2 / S) counts complex entries of psi; Euler and
+ *     classic RK4 have no embedded pair (sigma = 0).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -559,6 +567,122 @@ int orc_propagate_imag(const orc_grid *g, int method, int order, double dt, long
   }
   store_state(psi, psi_io, n);
   if (energy) *energy = (double)e;
+  free(buf);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Explicit Runge-Kutta methods of Sec. "Runge-Kutta" (Euler, classic RK4,   */
+/* and the embedded pairs RKF 4(5), Cash-Karp, Dormand-Prince, Merson):      */
+/*   k_i = f(t_n + c_i h, F_n + h sum_{j<i} a_ij k_j),  f = -i H(t) F,       */
+/*   F^(2) = F_n + h sum b2_i k_i (higher order), F^(1) with b1 (lower),     */
+/*   Delta = F^(2) - F^(1),  sigma_n = sqrt(|Delta|^2 / S),  sigma = sum.     */
+/* Reading: the step keeps the higher-order solution F^(2); S is the number  */
+/* of complex components of F.  Coefficients: the published tableaus         */
+/* (Fehlberg 1969; Cash & Karp 1990; Dormand & Prince 1980; Merson 1957).    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int s;                      /* stages */
+  double c[7];
+  double a[7][7];             /* a[i][j], j < i */
+  double b2[7], b1[7];        /* higher and lower order weights */
+} orc_tableau;
+
+static const orc_tableau ORC_TABLEAUS[6] = {
+  /* 0: Euler (no embedded pair) */
+  {1, {0}, {{0}}, {1}, {1}},
+  /* 1: classic RK4 (no embedded pair) */
+  {4, {0, 0.5, 0.5, 1},
+   {{0}, {0.5}, {0, 0.5}, {0, 0, 1}},
+   {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}},
+  /* 2: Runge-Kutta-Fehlberg 4(5) */
+  {6, {0, 1.0 / 4, 3.0 / 8, 12.0 / 13, 1, 1.0 / 2},
+   {{0},
+    {1.0 / 4},
+    {3.0 / 32, 9.0 / 32},
+    {1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197},
+    {439.0 / 216, -8, 3680.0 / 513, -845.0 / 4104},
+    {-8.0 / 27, 2, -3544.0 / 2565, 1859.0 / 4104, -11.0 / 40}},
+   {16.0 / 135, 0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50, 2.0 / 55},
+   {25.0 / 216, 0, 1408.0 / 2565, 2197.0 / 4104, -1.0 / 5, 0}},
+  /* 3: Cash-Karp 4(5) */
+  {6, {0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1, 7.0 / 8},
+   {{0},
+    {1.0 / 5},
+    {3.0 / 40, 9.0 / 40},
+    {3.0 / 10, -9.0 / 10, 6.0 / 5},
+    {-11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27},
+    {1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592, 253.0 / 4096}},
+   {37.0 / 378, 0, 250.0 / 621, 125.0 / 594, 0, 512.0 / 1771},
+   {2825.0 / 27648, 0, 18575.0 / 48384, 13525.0 / 55296, 277.0 / 14336, 1.0 / 4}},
+  /* 4: Dormand-Prince 5(4) */
+  {7, {0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1, 1},
+   {{0},
+    {1.0 / 5},
+    {3.0 / 40, 9.0 / 40},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
+   {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0},
+   {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40}},
+  /* 5: Merson 4("5"): fourth-order solution, third-order companion */
+  {5, {0, 1.0 / 3, 1.0 / 3, 1.0 / 2, 1},
+   {{0},
+    {1.0 / 3},
+    {1.0 / 6, 1.0 / 6},
+    {1.0 / 8, 0, 3.0 / 8},
+    {1.0 / 2, 0, -3.0 / 2, 2}},
+   {1.0 / 6, 0, 0, 2.0 / 3, 1.0 / 6},
+   {1.0 / 10, 0, 3.0 / 10, 2.0 / 5, 1.0 / 5}},
+};
+
+/*
+ * Advance psi by nsteps steps of the explicit RK method `tableau` (0..5 as
+ * above); the mask (if on) after every step.  sigma (may be NULL) receives
+ * sum_n sigma_n over these steps.
+ */
+int orc_propagate_rk(const orc_grid *g, const orc_pulse *pulse, const orc_mask *mask, int tableau,
+                     double dt, double t0, long nsteps, double *psi_io, double *sigma) {
+  if (!check_grid(g) || !pulse || nsteps < 0 || !(dt > 0)) return ORC_ERR_ARG;
+  if (tableau < 0 || tableau > 5) return ORC_ERR_ARG;
+  const orc_tableau *tb = &ORC_TABLEAUS[tableau];
+  const size_t n = dim(g);
+  cplx *buf = (cplx *)malloc((size_t)(tb->s + 2) * n * sizeof(cplx));
+  if (!buf) return ORC_ERR_OOM;
+  cplx *psi = buf, *arg = buf + n, *k = buf + 2 * n;   /* k_i at k + i n */
+  double (*coupling)(const orc_pulse *, double) = g->gauge ? orc_vecpot : orc_field;
+  load_state(psi_io, psi, n);
+  REAL sig = 0;
+  for (long st = 0; st < nsteps; ++st) {
+    const double tn = t0 + (double)st * dt;
+    for (int i = 0; i < tb->s; ++i) {
+      for (size_t q = 0; q < n; ++q) {
+        cplx v = psi[q];
+        for (int j = 0; j < i; ++j)
+          v = c_add(v, c_scale((REAL)dt * (REAL)tb->a[i][j], k[(size_t)j * n + q]));
+        arg[q] = v;
+      }
+      cplx *ki = k + (size_t)i * n;
+      apply_H(g, (REAL)coupling(pulse, tn + tb->c[i] * dt), arg, ki);
+      for (size_t q = 0; q < n; ++q) ki[q] = c_mul_minus_i(ki[q]);   /* k_i = -i H g */
+    }
+    REAL d2 = 0;
+    for (size_t q = 0; q < n; ++q) {
+      cplx hi = psi[q], delta = c_make(0, 0);
+      for (int i = 0; i < tb->s; ++i) {
+        const cplx ki = k[(size_t)i * n + q];
+        hi = c_add(hi, c_scale((REAL)dt * (REAL)tb->b2[i], ki));
+        delta = c_add(delta, c_scale((REAL)dt * ((REAL)tb->b2[i] - (REAL)tb->b1[i]), ki));
+      }
+      psi[q] = hi;
+      d2 += delta.re * delta.re + delta.im * delta.im;
+    }
+    sig += RSQRT(d2 / (REAL)n);
+    apply_mask(g, mask, psi);
+  }
+  store_state(psi, psi_io, n);
+  if (sigma) *sigma = (double)sig;
   free(buf);
   return ORC_OK;
 }

@@ -28,7 +28,14 @@ Pins used (arXiv 1308.1856 passages in brackets):
   * imaginary time [Sec. 3]: on a grid eigenstate the energy estimate is the
     eigenvalue (Lanczos) or the closed form of the Taylor/RK4 polynomial, and
     from the 1s state it converges to the lowest eigenvalue and the paper's
-    printed ground-state energies [Sec. 6, Example 1].
+    printed ground-state energies [Sec. 6, Example 1];
+  * explicit Runge-Kutta methods [Sec. "Runge-Kutta"]: the propagated
+    solution converges at the method's order (1 Euler, 4 classic and Merson,
+    5 for Fehlberg, Cash-Karp and Dormand-Prince) against scipy's DOP853 with
+    a time-dependent field; the error estimate sigma is zero without an
+    embedded pair and of the lower solution's order otherwise; one
+    Dormand-Prince step and its error estimate equal scipy's RK45 step (same
+    pair) to rounding; an Euler step is psi - i dt H(t_n) psi.
 """
 from __future__ import annotations
 
@@ -430,9 +437,101 @@ def check_gauge_invariance(prec="f64"):
     assert 1 - res[0]["p_ground"] >= 1e-3, "the pulse must change the state"
 
 
+def _rk_problem(prec):
+    g = Grid(N=12, h=0.4, L=2, stencil=5, Z=1.0)
+    pulse = Pulse(E0=2.0, omega=3.0, ncycles=2)
+    H0 = oracle.dense_H(g, 0.0, prec)
+    D = oracle.dense_H(g, 1.0, prec) - H0
+    psi = _rand_state(2, 12, 3)
+    psi /= np.linalg.norm(psi)
+
+    def rhs(t, y):
+        return -1j * ((H0 + oracle.field(pulse, t, prec) * D) @ y)
+    return g, pulse, psi, rhs
+
+
+# (tableau, order of the propagated solution, steps over [1, 2] for the order test)
+RK_ORDERS = (("euler", 1, (800, 1600, 3200)), ("classic", 4, (40, 80, 160)),
+             ("fehlberg", 5, (40, 80, 160)), ("cash_karp", 5, (40, 80, 160)),
+             ("dormand_prince", 5, (40, 80, 160)), ("merson", 4, (40, 80, 160)))
+RK_PAIRS = ("fehlberg", "cash_karp", "dormand_prince", "merson")
+
+
+def check_rk_orders(prec="f64"):
+    """Global error under dt-halving against DOP853 (time-dependent field, so
+    the stage times c_i count too): ratio 2^p for the propagated solution;
+    the summed estimate sigma = sum_n sigma_n falls as h^4 for every pair
+    (sigma_n is the local error of the order-4 (Merson: order-3, which is
+    order 4 on this linear problem at leading order) companion, h^5), and is
+    exactly zero for Euler and classic RK4, which carry no embedded pair."""
+    g, pulse, psi, rhs = _rk_problem(prec)
+    t0, t1 = 1.0, 2.0
+    ref = si.solve_ivp(rhs, (t0, t1), psi.reshape(-1), method="DOP853", rtol=1e-13,
+                       atol=1e-13).y[:, -1]
+    for name, p, counts in RK_ORDERS:
+        err, sig = [], []
+        for n in counts:
+            out, s = oracle.propagate_rk(g, psi, name, (t1 - t0) / n, n, t0=t0, pulse=pulse,
+                                         precision=prec)
+            err.append(np.linalg.norm(out.reshape(-1) - ref))
+            sig.append(s)
+        rat = np.array(err[:-1]) / np.array(err[1:])
+        want = 2.0 ** p
+        assert np.all((rat > 0.75 * want) & (rat < 1.4 * want)), f"{name} dt-halving ratios {rat}"
+        if name in RK_PAIRS:
+            srat = np.array(sig[:-1]) / np.array(sig[1:])
+            assert np.all((srat > 12.0) & (srat < 22.0)), f"{name} sigma ratios {srat}"
+        else:
+            assert all(s == 0.0 for s in sig), f"{name} has no embedded pair: sigma {sig}"
+
+
+def check_rk_dormand_prince_step(prec="f64"):
+    """scipy's RK45 is the Dormand-Prince 5(4) pair, propagating the fifth-order
+    solution: one of its steps (rtol and atol so large the step of size dt is
+    accepted) gives the same state as one oracle step, and its error vector
+    dt K^T E gives sigma = |error| / sqrt(S), S the complex entries of psi."""
+    g, pulse, psi, rhs = _rk_problem(prec)
+    t0, dt = 1.0, 0.03
+    sol = si.RK45(rhs, t0, psi.reshape(-1).copy(), t_bound=t0 + 10, first_step=dt, max_step=dt,
+                  rtol=1e6, atol=1e6)
+    sol.step()
+    assert abs(sol.t - (t0 + dt)) <= 1e-14
+    err_vec = dt * (sol.K.T @ sol.E)
+    out, s = oracle.propagate_rk(g, psi, "dormand_prince", dt, 1, t0=t0, pulse=pulse, precision=prec)
+    assert np.abs(out.reshape(-1) - sol.y).max() <= 1e-14 * np.abs(sol.y).max(), "DP step"
+    want = np.linalg.norm(err_vec) / math.sqrt(psi.size)
+    assert abs(s - want) <= 1e-9 * want, (s, want)
+
+
+def check_rk_error_estimate(prec="f64"):
+    """One step: sigma_n falls as h^5 for every pair; for the 4(5) pairs the
+    propagated (fifth-order) state is closer to the exact one than the
+    estimate sqrt(S) sigma_n; an Euler step is psi - i dt H(t_n) psi."""
+    g, pulse, psi, rhs = _rk_problem(prec)
+    t0 = 1.0
+    for name in RK_PAIRS:
+        sig = []
+        for dt in (0.02, 0.01, 0.005):
+            out, s = oracle.propagate_rk(g, psi, name, dt, 1, t0=t0, pulse=pulse, precision=prec)
+            sig.append(s)
+            if name != "merson" and dt <= 0.01:
+                ex = si.solve_ivp(rhs, (t0, t0 + dt), psi.reshape(-1), method="DOP853", rtol=1e-13,
+                                  atol=1e-15).y[:, -1]
+                assert np.linalg.norm(out.reshape(-1) - ex) <= math.sqrt(psi.size) * s, name
+        rat = np.array(sig[:-1]) / np.array(sig[1:])
+        assert np.all((rat > 26.0) & (rat < 38.0)), f"{name} one-step sigma ratios {rat}"
+    dt = 0.01
+    out, s = oracle.propagate_rk(g, psi, "euler", dt, 1, t0=t0, pulse=pulse, precision=prec)
+    H = oracle.dense_H(g, oracle.field(pulse, t0, prec), prec)
+    want = psi.reshape(-1) - 1j * dt * (H @ psi.reshape(-1))
+    assert np.abs(out.reshape(-1) - want).max() <= 1e-15 * np.abs(want).max() * 10, "Euler step"
+    assert s == 0.0
+
+
 ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_hydrogen_paper_values, check_hydrogen_convergence,
               check_field_free_eigenstate, check_dense_expm, check_time_order,
               check_norm_and_yield, check_observables, check_pulse, check_mask,
               check_imaginary_time_eigenstate, check_imaginary_time_ground_state,
-              check_velocity_gauge_operator, check_vector_potential, check_gauge_invariance]
+              check_velocity_gauge_operator, check_vector_potential, check_gauge_invariance,
+              check_rk_orders, check_rk_dormand_prince_step, check_rk_error_estimate]

@@ -62,6 +62,21 @@ MUTANTS = [
     ("vecpot_sign", "return -ORC_C_AU * s;", "return ORC_C_AU * s;", P.check_vector_potential),
     ("first_derivative_weight", "s = c_add(s, c_scale(8, f_at(g, x, l, j + 1)));",
      "s = c_add(s, c_scale(7, f_at(g, x, l, j + 1)));", P.check_velocity_gauge_operator),
+    ("rkf_stage_coefficient", "{1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197}",
+     "{1932.0 / 2197, -7200.0 / 2197, 7269.0 / 2197}", P.check_rk_orders),
+    ("cash_karp_node", "{0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1, 7.0 / 8}",
+     "{0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1, 5.0 / 8}", P.check_rk_orders),
+    ("cash_karp_lower_weight", "277.0 / 14336, 1.0 / 4}", "277.0 / 14336, 1.0 / 2}", P.check_rk_orders),
+    ("dormand_prince_lower_weight", "-92097.0 / 339200, 187.0 / 2100, 1.0 / 40}",
+     "-92097.0 / 339200, 187.0 / 2100, 1.0 / 4}", P.check_rk_dormand_prince_step),
+    ("merson_weights", "{1.0 / 6, 0, 0, 2.0 / 3, 1.0 / 6}", "{1.0 / 6, 0, 2.0 / 3, 0, 1.0 / 6}",
+     P.check_rk_orders),
+    ("rk_stage_time", "coupling(pulse, tn + tb->c[i] * dt)", "coupling(pulse, tn)", P.check_rk_orders),
+    ("rk_keeps_lower_solution", "hi = c_add(hi, c_scale((REAL)dt * (REAL)tb->b2[i], ki));",
+     "hi = c_add(hi, c_scale((REAL)dt * (REAL)tb->b1[i], ki));", P.check_rk_orders),
+    ("sigma_counts_reals", "sig += RSQRT(d2 / (REAL)n);", "sig += RSQRT(d2 / (REAL)(2 * n));",
+     P.check_rk_dormand_prince_step),
+    ("sigma_no_sqrt", "sig += RSQRT(d2 / (REAL)n);", "sig += d2 / (REAL)n;", P.check_rk_orders),
 ]
 
 
