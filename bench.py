@@ -346,6 +346,67 @@ def run_served(args, stream_ptr):
     return out
 
 
+# Stage counts of the explicit Runge-Kutta tableaus (appendix "Runge-Kutta").
+RK_STAGES = {"euler": 1, "classic": 4, "fehlberg": 6, "cash_karp": 6, "dormand_prince": 7, "merson": 5}
+
+
+def rk_step_flops_per_gp(s: int) -> int:
+    """Algorithmic FP64 flops per grid point of one step of an s-stage explicit
+    RK method through the general stage kernel (5-point stencil, FMA = 2):
+    stage i < s-1 applies H and forms g_{i+1} from psi and i+1 slopes
+    (4 (i+1)); the last applies H, forms psi and Delta from s slopes each
+    (8 s) and adds |Delta|^2 (4)."""
+    return s * H5_FLOPS + sum(4 * (i + 1) for i in range(s - 1)) + 8 * s + 4
+
+
+def run_rk_pairs(stream_ptr, psi0, steps=5, warmup=3, tableaus=("dormand_prince", "fehlberg")):
+    """Embedded RK pairs on the at-scale grid (FP64, dt = the explicit
+    propagators' stable step): per-step time by CUDA events on the library's
+    stream with L2 flushed (256 MB write) before every step (the flush outside
+    the events), and the general stage kernel against the FP64 ALU peak from a
+    separate profiled pass."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": "scale grid (N=8000 dr=0.05 lmax=63 5-point, mask), FP64, "
+                       f"dt={CFG.dt_stable:g}, L2 flushed before every step"}
+    for tb in tableaus:
+        s = RK_STAGES[tb]
+        h = make_handle(stream_ptr, "fp64")
+        h.set_state(psi0)
+        h.time = 0.3 * CFG.duration
+        for _ in range(warmup):
+            h.propagate_rk(tb, CFG.dt_stable, 1)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sigma = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            sigma += h.propagate_rk(tb, CFG.dt_stable, 1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        h.profile(True)
+        for k in range(steps):
+            flush.fill_(float(k))
+            h.propagate_rk(tb, CFG.dt_stable, 1)
+        kms, n = h.profile_read().get("rk_stage", (0.0, 0))
+        h.profile(False)
+        h.close()
+        flops = rk_step_flops_per_gp(s) * CFG.G * steps
+        achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
+        out[tb] = {
+            "stages": s, "ms_per_step": ms, "gp_steps_per_s": CFG.G / (ms * 1e-3),
+            "sigma_per_step": sigma / steps,
+            "roofline": {"bound": "alu", "kernel": "rk_general_stage (single, fp64)", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": None if achieved is None else achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "flops_per_launch": flops / max(n, 1),
+                         "avg_launch_ms": kms / max(n, 1), "launches": n},
+        }
+    return out
+
+
 def mixed_error(stream_ptr, psi0, nsteps=10):
     """The mixed-precision path's error against the FP64 path on the at-scale
     grid: Lanczos-12 from the benchmark's start state, at a step where the
@@ -525,6 +586,7 @@ def run_ours(args, ws, rank, local):
             r.h.close()
     if args.rows == "all":
         result["mixed_error"] = mixed_error(stream.cuda_stream, psi0)
+        result["rk_pairs"] = run_rk_pairs(stream.cuda_stream, psi0)
     if args.rows == "all" and not args.no_serve:
         result["served"] = run_served(args, stream.cuda_stream)
     return result

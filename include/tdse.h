@@ -160,6 +160,37 @@ int tdse_set_reference(tdse_t *h, const double *f0_host);
  */
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps);
 
+/* Explicit Runge-Kutta methods of the appendix "Runge-Kutta". */
+enum {
+  TDSE_RK_EULER = 0,          /* forward Euler, no embedded pair */
+  TDSE_RK_CLASSIC = 1,        /* classic RK4, no embedded pair */
+  TDSE_RK_FEHLBERG = 2,       /* Runge-Kutta-Fehlberg 4(5), 6 stages */
+  TDSE_RK_CASH_KARP = 3,      /* Cash-Karp 4(5), 6 stages */
+  TDSE_RK_DORMAND_PRINCE = 4, /* Dormand-Prince 5(4), 7 stages */
+  TDSE_RK_MERSON = 5          /* Merson 4("5"), 5 stages */
+};
+
+/*
+ * nsteps steps of the explicit Runge-Kutta method `tableau` (TDSE_RK_*) with
+ * the published Butcher tableau (appendix "Runge-Kutta"):
+ *   k_i = -i H(t_n + c_i dt) (F_n + dt sum_{j<i} a_ij k_j),
+ *   F_{n+1} = F_n + dt sum_i b_i k_i          (the higher-order solution),
+ *   Delta = dt sum_i (b_i - bhat_i) k_i       (bhat: the embedded companion),
+ *   sigma_n = sqrt(sum |Delta|^2 / S),  S = (L+1) N complex entries,
+ * with the field (length gauge) or A/c (velocity gauge) at the stage times,
+ * and the absorber mask, if on, after every step (sigma_n is taken before
+ * the mask).  dt is fixed: the paper accumulates sigma = sum_n sigma_n as an
+ * error measure and does not adapt the step.  *sigma (may be NULL) receives
+ * the sum over these steps; synchronises the stream; advances t by
+ * nsteps dt.  Methods without an embedded pair give sigma = 0.
+ * One stage is one launch; slopes of earlier stages are stored, so the handle
+ * keeps max(2, s + 1) state-sized work vectors (s stages).
+ * FP64 only: TDSE_ERR_ARG with TDSE_MIXED, dt <= 0, nsteps < 0 or an
+ * unknown tableau; TDSE_ERR_OOM; TDSE_ERR_CUDA; TDSE_ERR_NONFINITE if the
+ * state became non-finite.
+ */
+int tdse_propagate_rk(tdse_t *h, int tableau, double dt, long nsteps, double *sigma);
+
 /*
  * Imaginary-time propagation (Sec. 3, "Imaginary time"): nsteps steps of the
  * chosen propagator applied to exp(-H dtau) instead of exp(-i H dt), with no

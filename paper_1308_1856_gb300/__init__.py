@@ -17,6 +17,9 @@ from ._binding import (TDSE_LANCZOS, TDSE_RK4, TDSE_TAYLOR, TDSE_GHOST_ODD, TDSE
                        TDSE_MAX_KRYLOV)
 
 METHODS = {"taylor": TDSE_TAYLOR, "rk4": TDSE_RK4, "lanczos": TDSE_LANCZOS}
+RK_TABLEAUS = {"euler": C.TDSE_RK_EULER, "classic": C.TDSE_RK_CLASSIC, "fehlberg": C.TDSE_RK_FEHLBERG,
+               "cash_karp": C.TDSE_RK_CASH_KARP, "dormand_prince": C.TDSE_RK_DORMAND_PRINCE,
+               "merson": C.TDSE_RK_MERSON}
 
 
 class TDSEError(RuntimeError):
@@ -118,6 +121,14 @@ class TDSE:
 
     def propagate(self, method: str, order: int, dt: float, nsteps: int):
         self._check(C.tdse_propagate(self.h, METHODS[method], int(order), float(dt), int(nsteps)))
+
+    def propagate_rk(self, tableau: str, dt: float, nsteps: int) -> float:
+        """Explicit Runge-Kutta steps with a named tableau (RK_TABLEAUS); returns
+        the summed error estimate sigma of the embedded pair (0 without one)."""
+        sig = ctypes.c_double()
+        self._check(C.tdse_propagate_rk(self.h, RK_TABLEAUS[tableau], float(dt), int(nsteps),
+                                        ctypes.byref(sig)))
+        return sig.value
 
     def propagate_imag(self, method: str, order: int, dtau: float, nsteps: int) -> float:
         """Imaginary-time steps with renormalisation; returns the last energy estimate."""

@@ -21,6 +21,8 @@ TDSE_STENCIL_3, TDSE_STENCIL_5 = 3, 5
 TDSE_TAYLOR, TDSE_RK4, TDSE_LANCZOS = 0, 1, 2
 TDSE_GHOST_ZERO, TDSE_GHOST_ODD = 0, 1
 TDSE_FP64, TDSE_MIXED = 0, 1
+(TDSE_RK_EULER, TDSE_RK_CLASSIC, TDSE_RK_FEHLBERG, TDSE_RK_CASH_KARP, TDSE_RK_DORMAND_PRINCE,
+ TDSE_RK_MERSON) = range(6)
 TDSE_GAUGE_LENGTH, TDSE_GAUGE_VELOCITY = 0, 1
 TDSE_MAX_KRYLOV = 32
 
@@ -77,6 +79,7 @@ SIGNATURES = {
     "tdse_set_reference": (_c_int, [_vp, _vp]),
     "tdse_propagate": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long]),
     "tdse_propagate_imag": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long, _dp]),
+    "tdse_propagate_rk": (_c_int, [_vp, _c_int, _c_double, _c_long, _dp]),
     "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
     "tdse_sync": (_c_int, [_vp]),
@@ -175,6 +178,7 @@ tdse_get_state_device = _fn("tdse_get_state_device")
 tdse_set_reference = _fn("tdse_set_reference")
 tdse_propagate = _fn("tdse_propagate")
 tdse_propagate_imag = _fn("tdse_propagate_imag")
+tdse_propagate_rk = _fn("tdse_propagate_rk")
 tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")
 tdse_sync = _fn("tdse_sync")

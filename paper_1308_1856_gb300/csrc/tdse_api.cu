@@ -33,6 +33,7 @@ struct tdse {
   int *status = nullptr;
   double *obs_partials = nullptr, *obs_out = nullptr;
   double *imag = nullptr;          // imaginary time: {squared norm before the step, energy}
+  double *rk_sigma = nullptr;      // explicit RK: sum of the steps' error estimates
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
   // a final stage reads one pair with halos while writing the other) and
   // complex64 work vectors
@@ -204,6 +205,7 @@ void free_all(tdse *h) {
   cudaFree(h->obs_partials);
   cudaFree(h->obs_out);
   cudaFree(h->imag);
+  cudaFree(h->rk_sigma);
   cudaFree(h->diagf);
   cudaFree(h->rjf);
   cudaFree(h->kappaf);
@@ -489,6 +491,124 @@ int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
                 "lanczos combine");
   }
   return TDSE_OK;
+}
+
+// Butcher tableaus of the explicit methods of the appendix "Runge-Kutta", as
+// published (Euler; classic RK4; Fehlberg's 4(5) pair, 1969; Cash and Karp's
+// 4(5) pair, 1990; Dormand and Prince's 5(4) pair, 1980; Merson's 4("5")
+// pair, 1957).  b is the propagated solution, bhat the embedded companion
+// (equal to b where the method has none, so sigma = 0).
+struct RkTableau {
+  int s;
+  double c[kRkMaxStages];
+  double a[kRkMaxStages][kRkMaxStages];
+  double b[kRkMaxStages], bhat[kRkMaxStages];
+};
+
+const RkTableau &rk_tableau(int id) {
+  static const RkTableau euler = {1, {0.0}, {{0.0}}, {1.0}, {1.0}};
+  static const RkTableau classic = {
+      4, {0.0, 0.5, 0.5, 1.0}, {{0.0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}},
+      {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}};
+  static const RkTableau fehlberg = {
+      6, {0.0, 1.0 / 4, 3.0 / 8, 12.0 / 13, 1.0, 1.0 / 2},
+      {{0.0},
+       {1.0 / 4},
+       {3.0 / 32, 9.0 / 32},
+       {1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197},
+       {439.0 / 216, -8.0, 3680.0 / 513, -845.0 / 4104},
+       {-8.0 / 27, 2.0, -3544.0 / 2565, 1859.0 / 4104, -11.0 / 40}},
+      {16.0 / 135, 0.0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50, 2.0 / 55},
+      {25.0 / 216, 0.0, 1408.0 / 2565, 2197.0 / 4104, -1.0 / 5, 0.0}};
+  static const RkTableau cash_karp = {
+      6, {0.0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1.0, 7.0 / 8},
+      {{0.0},
+       {1.0 / 5},
+       {3.0 / 40, 9.0 / 40},
+       {3.0 / 10, -9.0 / 10, 6.0 / 5},
+       {-11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27},
+       {1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592, 253.0 / 4096}},
+      {37.0 / 378, 0.0, 250.0 / 621, 125.0 / 594, 0.0, 512.0 / 1771},
+      {2825.0 / 27648, 0.0, 18575.0 / 48384, 13525.0 / 55296, 277.0 / 14336, 1.0 / 4}};
+  static const RkTableau dormand_prince = {
+      7, {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0},
+      {{0.0},
+       {1.0 / 5},
+       {3.0 / 40, 9.0 / 40},
+       {44.0 / 45, -56.0 / 15, 32.0 / 9},
+       {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+       {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+       {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
+      {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0},
+      {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40}};
+  static const RkTableau merson = {
+      5, {0.0, 1.0 / 3, 1.0 / 3, 1.0 / 2, 1.0},
+      {{0.0}, {1.0 / 3}, {1.0 / 6, 1.0 / 6}, {1.0 / 8, 0.0, 3.0 / 8}, {1.0 / 2, 0.0, -3.0 / 2, 2.0}},
+      {1.0 / 6, 0.0, 0.0, 2.0 / 3, 1.0 / 6},
+      {1.0 / 10, 0.0, 3.0 / 10, 2.0 / 5, 1.0 / 5}};
+  static const RkTableau *const all[] = {&euler, &classic, &fehlberg, &cash_karp, &dormand_prince, &merson};
+  return *all[id];
+}
+
+// nsteps steps of the explicit method `id`: s stage launches per step (the
+// last one forms the new state, the mask and the step's error estimate).
+// Work: g ping-pong in slots 0-1, slopes k_0..k_{s-2} in slots 2.., so
+// max(2, s + 1) vectors.  *sigma (may be NULL) receives sum_n sigma_n.
+int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
+  const RkTableau &tb = rk_tableau(id);
+  const int s = tb.s;
+  int rc = ensure_work(h, (size_t)(s + 1 > 2 ? s + 1 : 2));
+  if (rc) return rc;
+  if (!h->rk_sigma && cudaMalloc(&h->rk_sigma, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->rk_sigma = nullptr;
+    return fail(h, TDSE_ERR_OOM, "RK error-estimate scalar");
+  }
+  TDSE_CUDA(h, cudaMemsetAsync(h->rk_sigma, 0, sizeof(double), h->stream), "clear sigma");
+  const OperatorView op = view(h);
+  const size_t G = npts(h);
+  double2 *gbuf[2] = {h->work, h->work + G};
+  auto kbuf = [&](int j) { return h->work + (size_t)(2 + j) * G; };
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double tn = t0 + (double)n * dt;
+    for (int i = 0; i < s; ++i) {
+      RkStageArgs a{};
+      a.stage = i;
+      a.last = (i == s - 1) ? 1 : 0;
+      a.sigma = h->rk_sigma;
+      a.status = h->status;
+      for (int j = 0; j < i; ++j) a.k[j] = kbuf(j);
+      for (int j = 0; j <= i; ++j) {
+        if (a.last) {
+          a.coef[j] = dt * tb.b[j];
+          a.dcoef[j] = dt * (tb.b[j] - tb.bhat[j]);
+        } else {
+          a.coef[j] = dt * tb.a[i + 1][j];
+        }
+      }
+      const double2 *gin = (i == 0) ? h->psi : gbuf[(i - 1) & 1];
+      if (!a.last) {
+        a.k_out = kbuf(i);
+        a.g_out = gbuf[i & 1];
+      } else {
+        // the stencil reads gin's neighbours: with one stage gin is psi, so the
+        // new state goes to a work slot first
+        a.psi_out = (i == 0) ? gbuf[0] : h->psi;
+      }
+      const double E = coupling_at(h, tn + tb.c[i] * dt);
+      TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_general_stage(h->g, op, E, gin, h->psi, a, h->red, h->stream),
+                  "rk stage");
+    }
+    if (s == 1)
+      TDSE_CUDA(h, cudaMemcpyAsync(h->psi, gbuf[0], sizeof(double2) * G, cudaMemcpyDeviceToDevice, h->stream),
+                "rk copy");
+  }
+  double out = 0.0;
+  TDSE_CUDA(h, cudaMemcpyAsync(&out, h->rk_sigma, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read sigma");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync rk");
+  if (sigma) *sigma = out;
+  return check_status_word(h);
 }
 
 // Imaginary-time propagation (Sec. 3, "Imaginary time"): every step applies
@@ -844,6 +964,23 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
     default:
       return fail(h, TDSE_ERR_ARG, "unknown method");
   }
+  if (rc) return rc;
+  h->t += (double)nsteps * dt;
+  return TDSE_OK;
+}
+
+int tdse_propagate_rk(tdse_t *h, int tableau, double dt, long nsteps, double *sigma) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  if (tableau < TDSE_RK_EULER || tableau > TDSE_RK_MERSON) return fail(h, TDSE_ERR_ARG, "unknown Runge-Kutta tableau");
+  if (h->opts.precision != TDSE_FP64) return fail(h, TDSE_ERR_ARG, "the Runge-Kutta pairs run in FP64 only");
+  if (nsteps > 0) {
+    h->lanczos_norm_valid = false;
+    h->split_valid = false;
+    h->mixed_norm_valid = false;
+  }
+  rc = rk_general_steps(h, tableau, dt, nsteps, sigma);
   if (rc) return rc;
   h->t += (double)nsteps * dt;
   return TDSE_OK;

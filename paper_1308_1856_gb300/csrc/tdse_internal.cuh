@@ -78,6 +78,31 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
                             double dt, const double2 *gin, const double2 *psi,
                             const double2 *acc_in, double2 *acc_out, double2 *g_next,
                             double2 *psi_out, cudaStream_t st, bool imag = false);
+// One stage of an explicit Runge-Kutta method with up to kRkMaxStages stages
+// (appendix "Runge-Kutta"): stage i computes k_i = -i H(E) g_i at every point
+// (g_i = gin; g_0 is psi itself) and then, pointwise,
+//   i < s-1: k_out = k_i,  g_out = psi + sum_{j<=i} coef[j] k_j  (coef = dt a_{i+1,j});
+//   i = s-1: psi_out = mask * (psi + sum_j coef[j] k_j)           (coef = dt b_j, the
+//            propagated weights), Delta = sum_j dcoef[j] k_j       (dcoef = dt (b_j - b^_j)),
+//            *sigma += sqrt(sum |Delta|^2 / S) with S = (L+1) N (a grid reduction
+//            in a fixed order; the last block adds it), and the status word
+//            gets kStatusNonFinite when that sum is not finite (0 * Inf and
+//            every sum with a NaN slope are NaN, so this also holds for the
+//            methods whose b - bhat is zero).
+// k[j] (j < i) are the stored slopes of the earlier stages; psi_out may be
+// psi (each point is read before it is written by the same thread) but not gin.
+constexpr int kRkMaxStages = 7;
+struct RkStageArgs {
+  const double2 *k[kRkMaxStages];
+  double2 *k_out, *g_out, *psi_out;
+  double coef[kRkMaxStages], dcoef[kRkMaxStages];
+  double *sigma;
+  int *status;
+  int stage, last;
+};
+cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
+                                    const double2 *gin, const double2 *psi, const RkStageArgs &a,
+                                    Reduction *red, cudaStream_t st);
 // Imaginary time: prev[0] = dr * red->normsq (the squared norm before a step);
 // after the step (red->normsq of the new state): energy[0] =
 // -ln(dr normsq / prev) / (2 dt) and psi /= sqrt(dr normsq).

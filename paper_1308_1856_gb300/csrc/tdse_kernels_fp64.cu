@@ -120,6 +120,58 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   });
 }
 
+// Stage a.stage of a general explicit Runge-Kutta method (appendix
+// "Runge-Kutta"); see RkStageArgs.  The slopes of the earlier stages are read
+// pointwise and combined in stage order, the new slope k_i = -i H g_i last,
+// so the sums round in the same order as the oracle's.
+template <int ST, bool VG>
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
+    rk_general_stage_kernel(StencilIn in, RkStageArgs a, const double2 *__restrict__ psi,
+                            const double *__restrict__ mask, int mask_start, Reduction *red,
+                            double S) {
+  __shared__ double sh[kBlockJ / 32 + 1];
+  const int i = a.stage;
+  const bool last = a.last != 0;
+  double acc = 0.0;
+  for_my_segments<ST, false, VG>(in, [&](int r, size_t idx, double2 t, double2) {
+    const double2 ki = make_double2(t.y, -t.x);   // -i (tx + i ty)
+    double2 o = psi[idx];
+    double2 d = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < kRkMaxStages - 1; ++j) {
+      if (j < i) {
+        const double2 kj = a.k[j][idx];
+        o.x = __fma_rn(a.coef[j], kj.x, o.x);
+        o.y = __fma_rn(a.coef[j], kj.y, o.y);
+        if (last) {
+          d.x = __fma_rn(a.dcoef[j], kj.x, d.x);
+          d.y = __fma_rn(a.dcoef[j], kj.y, d.y);
+        }
+      }
+    }
+    o.x = __fma_rn(a.coef[i], ki.x, o.x);
+    o.y = __fma_rn(a.coef[i], ki.y, o.y);
+    if (!last) {
+      a.k_out[idx] = ki;
+      a.g_out[idx] = o;
+    } else {
+      d.x = __fma_rn(a.dcoef[i], ki.x, d.x);
+      d.y = __fma_rn(a.dcoef[i], ki.y, d.y);
+      acc = __fma_rn(d.x, d.x, acc);
+      acc = __fma_rn(d.y, d.y, acc);
+      if (r >= mask_start) { const double mv = mask[r]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
+      a.psi_out[idx] = o;
+    }
+  });
+  if (last && publish_block_partial(acc, red, sh)) {
+    const double s = reduce_partials(red, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *a.sigma += sqrt(s / S);
+      if (!isfinite(s)) atomicOr(a.status, kStatusNonFinite);
+    }
+  }
+}
+
 // Lanczos iteration j, first half (Appendix "Lanczos methods"):
 //   z = H q_j - beta_{j-1} q_{j-1},   q_j = sigma_j U_j,
 //   beta_{j-1} q_{j-1} = (sigma_{j-1} / sigma_j) U_{j-1},
@@ -483,6 +535,20 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
       rk_stage_kernel<ST, true, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
     else
       rk_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
+                                    const double2 *gin, const double2 *psi, const RkStageArgs &a,
+                                    Reduction *red, cudaStream_t st) {
+  if (a.stage < 0 || a.stage >= kRkMaxStages) return cudaErrorInvalidValue;
+  const StencilIn in = make_in(g, op, E, gin);
+  const unsigned grid = stencil_blocks(g);
+  const double S = (double)g.N * (double)(g.L + 1);
+  dispatch(g, g.gauge == 1, [&](auto stc, auto vg) {
+    rk_general_stage_kernel<decltype(stc)::value, decltype(vg)::value>
+        <<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
   });
   return cudaGetLastError();
 }
