@@ -346,17 +346,19 @@ def run_served(args, stream_ptr):
     return out
 
 
-# Stage counts of the explicit Runge-Kutta tableaus (appendix "Runge-Kutta").
+# Stage counts of the explicit Runge-Kutta tableaus (appendix "Runge-Kutta"),
+# and the first-same-as-last one (its last stage's argument is the new state).
 RK_STAGES = {"euler": 1, "classic": 4, "fehlberg": 6, "cash_karp": 6, "dormand_prince": 7, "merson": 5}
+RK_FSAL = ("dormand_prince",)
 
 
-def rk_step_flops_per_gp(s: int) -> int:
+def rk_step_flops_per_gp(s: int, fsal: bool = False) -> int:
     """Algorithmic FP64 flops per grid point of one step of an s-stage explicit
     RK method through the general stage kernel (5-point stencil, FMA = 2):
     stage i < s-1 applies H and forms g_{i+1} from psi and i+1 slopes
-    (4 (i+1)); the last applies H, forms psi and Delta from s slopes each
-    (8 s) and adds |Delta|^2 (4)."""
-    return s * H5_FLOPS + sum(4 * (i + 1) for i in range(s - 1)) + 8 * s + 4
+    (4 (i+1)); the last applies H, forms psi (unless first-same-as-last) and
+    Delta from s slopes (4 s each) and adds |Delta|^2 (4)."""
+    return s * H5_FLOPS + sum(4 * (i + 1) for i in range(s - 1)) + (4 if fsal else 8) * s + 4
 
 
 def run_rk_pairs(stream_ptr, psi0, steps=5, warmup=3, tableaus=("dormand_prince", "fehlberg")):
@@ -393,7 +395,7 @@ def run_rk_pairs(stream_ptr, psi0, steps=5, warmup=3, tableaus=("dormand_prince"
         kms, n = h.profile_read().get("rk_stage", (0.0, 0))
         h.profile(False)
         h.close()
-        flops = rk_step_flops_per_gp(s) * CFG.G * steps
+        flops = rk_step_flops_per_gp(s, tb in RK_FSAL) * CFG.G * steps
         achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
         out[tb] = {
             "stages": s, "ms_per_step": ms, "gp_steps_per_s": CFG.G / (ms * 1e-3),
@@ -445,6 +447,9 @@ def run_ours(args, ws, rank, local):
     rows = []
     if args.rows == "served":
         return {"metric": METRIC, "served": run_served(args, stream.cuda_stream)}
+    if args.rows == "rk":
+        return {"metric": METRIC, "rk_pairs": run_rk_pairs(stream.cuda_stream, psi0, steps=args.steps,
+                                                           warmup=args.warmup)}
     if args.rows in ("all", "single"):
         rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
     if args.rows in ("all", "batched"):
@@ -656,8 +661,8 @@ def main():
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
                     help="restrict to one precision (profiling runs)")
-    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served"],
-                    help="restrict to the single-instance, batched or served rows")
+    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served", "rk"],
+                    help="restrict to the single-instance, batched, served or embedded-RK rows")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched rows (smaller only for profiling captures)")
     ap.add_argument("--schedule", action="append", default=[], metavar="PREC=PF,RING,SB,EB",

@@ -557,6 +557,9 @@ const RkTableau &rk_tableau(int id) {
 int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
   const RkTableau &tb = rk_tableau(id);
   const int s = tb.s;
+  // first same as last: the last stage's argument is the new state
+  bool fsal = s > 1 && tb.b[s - 1] == 0.0;
+  for (int j = 0; j + 1 < s; ++j) fsal = fsal && tb.a[s - 1][j] == tb.b[j];
   int rc = ensure_work(h, (size_t)(s + 1 > 2 ? s + 1 : 2));
   if (rc) return rc;
   if (!h->rk_sigma && cudaMalloc(&h->rk_sigma, sizeof(double)) != cudaSuccess) {
@@ -576,6 +579,7 @@ int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
       RkStageArgs a{};
       a.stage = i;
       a.last = (i == s - 1) ? 1 : 0;
+      a.fsal = (a.last && fsal) ? 1 : 0;
       a.sigma = h->rk_sigma;
       a.status = h->status;
       for (int j = 0; j < i; ++j) a.k[j] = kbuf(j);

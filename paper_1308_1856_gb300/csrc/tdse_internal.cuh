@@ -91,6 +91,8 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
 //            methods whose b - bhat is zero).
 // k[j] (j < i) are the stored slopes of the earlier stages; psi_out may be
 // psi (each point is read before it is written by the same thread) but not gin.
+// fsal (last stage only): the tableau is first-same-as-last (b_{s-1} = 0 and
+// a_{s-1,j} = b_j), so psi + sum_j coef[j] k_j is gin itself and is not re-summed.
 constexpr int kRkMaxStages = 7;
 struct RkStageArgs {
   const double2 *k[kRkMaxStages];
@@ -98,7 +100,7 @@ struct RkStageArgs {
   double coef[kRkMaxStages], dcoef[kRkMaxStages];
   double *sigma;
   int *status;
-  int stage, last;
+  int stage, last, fsal;
 };
 cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
                                     const double2 *gin, const double2 *psi, const RkStageArgs &a,

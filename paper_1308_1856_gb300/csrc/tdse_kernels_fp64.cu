@@ -121,49 +121,62 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 }
 
 // Stage a.stage of a general explicit Runge-Kutta method (appendix
-// "Runge-Kutta"); see RkStageArgs.  The slopes of the earlier stages are read
-// pointwise and combined in stage order, the new slope k_i = -i H g_i last,
-// so the sums round in the same order as the oracle's.
-template <int ST, bool VG>
+// "Runge-Kutta"); see RkStageArgs.  NK = a.stage + 1 terms and MODE are
+// compile-time, so no FP64 instruction is issued for absent terms (a
+// predicated-off FP64 instruction still takes its FP64 issue slot):
+//   MODE 0: an inner stage (k_i and g_{i+1} out);
+//   MODE 1: the last stage (psi, Delta and the sigma partial);
+//   MODE 2: the last stage of a first-same-as-last tableau (b_{s-1} = 0 and
+//           a_{s-1,j} = b_j): psi_new is the stage's own input g_{s-1}, which
+//           the previous stage summed in the same order with the same
+//           coefficients, so only Delta is formed.
+// The slopes of the earlier stages are read pointwise and combined in stage
+// order, the new slope k_i = -i H g_i last, so the sums round in the same
+// order as the oracle's.
+template <int ST, bool VG, int NK, int MODE>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     rk_general_stage_kernel(StencilIn in, RkStageArgs a, const double2 *__restrict__ psi,
                             const double *__restrict__ mask, int mask_start, Reduction *red,
                             double S) {
+  constexpr bool LAST = MODE != 0;
+  constexpr bool FSAL = MODE == 2;
   __shared__ double sh[kBlockJ / 32 + 1];
-  const int i = a.stage;
-  const bool last = a.last != 0;
   double acc = 0.0;
-  for_my_segments<ST, false, VG>(in, [&](int r, size_t idx, double2 t, double2) {
+  for_my_segments<ST, false, VG>(in, [&](int r, size_t idx, double2 t, double2 u) {
     const double2 ki = make_double2(t.y, -t.x);   // -i (tx + i ty)
-    double2 o = psi[idx];
+    double2 kj[NK > 1 ? NK - 1 : 1];
+#pragma unroll
+    for (int j = 0; j < NK - 1; ++j) kj[j] = a.k[j][idx];
+    double2 o = FSAL ? u : psi[idx];
     double2 d = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int j = 0; j < kRkMaxStages - 1; ++j) {
-      if (j < i) {
-        const double2 kj = a.k[j][idx];
-        o.x = __fma_rn(a.coef[j], kj.x, o.x);
-        o.y = __fma_rn(a.coef[j], kj.y, o.y);
-        if (last) {
-          d.x = __fma_rn(a.dcoef[j], kj.x, d.x);
-          d.y = __fma_rn(a.dcoef[j], kj.y, d.y);
-        }
+    for (int j = 0; j < NK - 1; ++j) {
+      if (!FSAL) {
+        o.x = __fma_rn(a.coef[j], kj[j].x, o.x);
+        o.y = __fma_rn(a.coef[j], kj[j].y, o.y);
+      }
+      if (LAST) {
+        d.x = __fma_rn(a.dcoef[j], kj[j].x, d.x);
+        d.y = __fma_rn(a.dcoef[j], kj[j].y, d.y);
       }
     }
-    o.x = __fma_rn(a.coef[i], ki.x, o.x);
-    o.y = __fma_rn(a.coef[i], ki.y, o.y);
-    if (!last) {
+    if (!FSAL) {
+      o.x = __fma_rn(a.coef[NK - 1], ki.x, o.x);
+      o.y = __fma_rn(a.coef[NK - 1], ki.y, o.y);
+    }
+    if (!LAST) {
       a.k_out[idx] = ki;
       a.g_out[idx] = o;
     } else {
-      d.x = __fma_rn(a.dcoef[i], ki.x, d.x);
-      d.y = __fma_rn(a.dcoef[i], ki.y, d.y);
+      d.x = __fma_rn(a.dcoef[NK - 1], ki.x, d.x);
+      d.y = __fma_rn(a.dcoef[NK - 1], ki.y, d.y);
       acc = __fma_rn(d.x, d.x, acc);
       acc = __fma_rn(d.y, d.y, acc);
       if (r >= mask_start) { const double mv = mask[r]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
       a.psi_out[idx] = o;
     }
   });
-  if (last && publish_block_partial(acc, red, sh)) {
+  if (LAST && publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
       *a.sigma += sqrt(s / S);
@@ -546,9 +559,32 @@ cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, d
   const StencilIn in = make_in(g, op, E, gin);
   const unsigned grid = stencil_blocks(g);
   const double S = (double)g.N * (double)(g.L + 1);
+  const int mode = a.last ? (a.fsal ? 2 : 1) : 0;
+  if (!a.last && a.stage == kRkMaxStages - 1) return cudaErrorInvalidValue;   // no stage after the last
+  if (a.fsal && (!a.last || a.stage == 0)) return cudaErrorInvalidValue;
   dispatch(g, g.gauge == 1, [&](auto stc, auto vg) {
-    rk_general_stage_kernel<decltype(stc)::value, decltype(vg)::value>
-        <<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+    constexpr int ST = decltype(stc)::value;
+    constexpr bool VG = decltype(vg)::value;
+    auto go = [&](auto nk) {
+      constexpr int NK = decltype(nk)::value;
+      if (mode == 1)
+        rk_general_stage_kernel<ST, VG, NK, 1><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+      else if constexpr (NK > 1)
+        if (mode == 2)
+          rk_general_stage_kernel<ST, VG, NK, 2><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+      if constexpr (NK < kRkMaxStages)
+        if (mode == 0)
+          rk_general_stage_kernel<ST, VG, NK, 0><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+    };
+    switch (a.stage + 1) {
+      case 1: go(IC<1>{}); break;
+      case 2: go(IC<2>{}); break;
+      case 3: go(IC<3>{}); break;
+      case 4: go(IC<4>{}); break;
+      case 5: go(IC<5>{}); break;
+      case 6: go(IC<6>{}); break;
+      default: go(IC<7>{}); break;
+    }
   });
   return cudaGetLastError();
 }
