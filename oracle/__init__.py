@@ -117,6 +117,10 @@ def _lib(precision: str = "f64"):
                                       ctypes.POINTER(_Mask), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_long, dp,
                                       ctypes.POINTER(ctypes.c_int)]
+        lib.orc_dipole_moments.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Pulse), ctypes.c_double,
+                                           dp, dp]
+        lib.orc_flux.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Pulse), ctypes.c_double, dp,
+                                 ctypes.c_double, ctypes.c_int, dp, dp, dp]
         lib.orc_propagate_rk.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Pulse),
                                          ctypes.POINTER(_Mask), ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_long, dp, dp]
@@ -234,6 +238,34 @@ def observables(grid: Grid, psi: np.ndarray, ref0: Optional[np.ndarray] = None,
                                            float(r_b), _dptr(out)), "observables")
     return {"norm": out[0], "dipole": out[1], "yield": out[2], "p_ground": out[3],
             "l_pop": out[4:].copy()}
+
+
+def dipole_moments(grid: Grid, psi: np.ndarray, t: float = 0.0, pulse: Optional[Pulse] = None,
+                   precision: str = "f64") -> np.ndarray:
+    """[<z>, d<z>/dt, d^2<z>/dt^2] of psi at time t (Sec. 4)."""
+    ps = _state(psi, grid)
+    g, keep = grid._c()
+    p = (pulse or Pulse())._c()
+    out = np.zeros(3)
+    _check(_lib(precision).orc_dipole_moments(ctypes.byref(g), ctypes.byref(p), float(t),
+                                              _dptr(ps.view(np.float64)), _dptr(out)), "dipole_moments")
+    return out
+
+
+def flux(grid: Grid, psi: np.ndarray, r_b: float, cos_theta=None, t: float = 0.0,
+         pulse: Optional[Pulse] = None, precision: str = "f64"):
+    """(total, per_angle): r_b^2 times the radial current through the sphere
+    r = r_b, integrated over the angles and at each cos(theta) (Sec. 4)."""
+    ps = _state(psi, grid)
+    g, keep = grid._c()
+    p = (pulse or Pulse())._c()
+    ct = np.ascontiguousarray(np.zeros(0) if cos_theta is None else cos_theta, dtype=np.float64)
+    per = np.zeros(max(len(ct), 1))
+    tot = np.zeros(1)
+    _check(_lib(precision).orc_flux(ctypes.byref(g), ctypes.byref(p), float(t), _dptr(ps.view(np.float64)),
+                                    float(r_b), len(ct), _dptr(ct) if len(ct) else None, _dptr(tot),
+                                    _dptr(per) if len(ct) else None), "flux")
+    return float(tot[0]), per[:len(ct)]
 
 
 def field(pulse: Pulse, t: float, precision: str = "f64") -> float:

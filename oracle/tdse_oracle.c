@@ -32,6 +32,9 @@
  *                                            and Sec. 3, Eq. (VectorStep)
  *   observables ............................ Sec. 4, Eqs. (p_g), (p_b),
  *                                            (yield_1), (Norm), (Dipole)
+ *   dipole velocity and acceleration ....... Sec. 4, Eqs. (DipoleVelocity),
+ *                                            (DipoleAccel)
+ *   radial flux, PAD and flux yield ........ Sec. 4, Eqs. (flux), (pad), (yield)
  *
  * Readings where the paper is silent or garbled (each is also listed in the
  * design notes):
@@ -759,6 +762,117 @@ int orc_observables(const orc_grid *g, const double *psi_in, const double *ref0,
   out[1] = (double)dip;
   out[2] = (double)(1 - h * inside);
   out[3] = (double)pg;
+  free(F);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dipole moment, velocity and acceleration (Sec. 4, Eqs. (Dipole),          */
+/* (DipoleVelocity), (DipoleAccel)) of psi at time t, m = 0:                 */
+/*   <z>    = 2 sum_l kappa_{l+1} h sum_j r_j Re(f_l^* f_{l+1})              */
+/*   <zdot> = 2 sum_l kappa_{l+1} h sum_j Im(f_{l+1}^* (D1 f_l - (l+1)/r f_l))*/
+/*            [+ (A(t)/c) norm in the velocity gauge]                         */
+/*   <zddot> = -E(t) norm - 2 Z sum_l kappa_{l+1} h sum_j Re(f_l^* f_{l+1})/r^2 */
+/* D1 is the first-derivative formula of the velocity gauge (d1_at).          */
+/* Readings: Eq. (DipoleVelocity) is printed without the factor 2 that        */
+/* Eq. (Dipole) carries; d<z>/dt = <zdot> (Ehrenfest) needs it.  <zdot> is    */
+/* the kinetic momentum, so the velocity gauge adds (A/c) norm; the paper's   */
+/* -E(t) is -E(t) norm (the two agree for a normalised state).  The           */
+/* acceleration form needs dV/dr: with a tabulated potential out[2] is NaN.   */
+/* ------------------------------------------------------------------------ */
+int orc_dipole_moments(const orc_grid *g, const orc_pulse *pulse, double t, const double *psi_in,
+                       double *out) {
+  if (!check_grid(g) || !pulse || !psi_in || !out) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  cplx *F = (cplx *)malloc(n * sizeof(cplx));
+  if (!F) return ORC_ERR_OOM;
+  load_state(psi_in, F, n);
+  const REAL h = (REAL)g->h;
+  const int N = g->N, L = g->L;
+  REAL norm = 0, z = 0, pz = 0, fz = 0;
+  for (int l = 0; l <= L; ++l)
+    for (int j = 1; j <= N; ++j) {
+      const cplx a = F[(size_t)l * N + (j - 1)];
+      norm += a.re * a.re + a.im * a.im;
+    }
+  for (int l = 0; l < L; ++l) {
+    REAL sz = 0, sp = 0, sf = 0;
+    for (int j = 1; j <= N; ++j) {
+      const REAL r = grid_r(g, j);
+      const cplx a = F[(size_t)l * N + (j - 1)], b = F[(size_t)(l + 1) * N + (j - 1)];
+      const REAL re = a.re * b.re + a.im * b.im;                 /* Re(conj(a) b) */
+      const cplx w = c_sub(d1_at(g, F, l, j), c_scale((REAL)(l + 1) / r, a));
+      sz += r * re;
+      sp += b.re * w.im - b.im * w.re;                           /* Im(conj(b) w) */
+      sf += re / (r * r);
+    }
+    z += 2 * kappa(l + 1) * h * sz;
+    pz += 2 * kappa(l + 1) * h * sp;
+    fz += 2 * kappa(l + 1) * h * sf;
+  }
+  norm *= h;
+  out[0] = (double)z;
+  out[1] = (double)(pz + (g->gauge ? (REAL)orc_vecpot(pulse, t) / (REAL)ORC_C_AU * norm : 0));
+  out[2] = g->vtable ? NAN : (double)(-(REAL)orc_field(pulse, t) * norm - (REAL)g->Z * fz);
+  free(F);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Flux through the sphere r = r_b (Sec. 4, Eqs. (flux), (pad), (yield)),     */
+/* m = 0, psi = sum_l f_l(r)/r Y_l0:                                          */
+/*   total:  r_b^2 int dOmega j_r = sum_l Im(f_l^* D1 f_l)                    */
+/*                                  [+ 2 (A/c) sum_l kappa_{l+1} Re(f_l^* f_{l+1})] */
+/*   angle:  r_b^2 j_r(theta) = Im(S^* P) [+ (A/c) cos(theta) |S|^2],         */
+/*           S = sum_l f_l Y_l0(theta),  P = sum_l (D1 f_l) Y_l0(theta),      */
+/*           Y_l0 = sqrt((2l+1)/(4 pi)) P_l(cos theta)                        */
+/* at the grid point nearest r_b (the A terms in the velocity gauge only).    */
+/* Readings: Eq. (flux) prints -Im; the continuity equation (outward flux     */
+/* empties the inside) and Eq. (yield) need +Im.  The A term of Eq. (yield)   */
+/* is complex as printed; the flux is its real part.                          */
+/* ------------------------------------------------------------------------ */
+static int nearest_index(const orc_grid *g, double r_b) {
+  int best = 1;
+  for (int j = 2; j <= g->N; ++j)
+    if (RFABS(grid_r(g, j) - (REAL)r_b) < RFABS(grid_r(g, best) - (REAL)r_b)) best = j;
+  return best;
+}
+
+int orc_flux(const orc_grid *g, const orc_pulse *pulse, double t, const double *psi_in, double r_b,
+             int ntheta, const double *cos_theta, double *total, double *per_angle) {
+  if (!check_grid(g) || !pulse || !psi_in || !total || ntheta < 0) return ORC_ERR_ARG;
+  if (ntheta > 0 && (!cos_theta || !per_angle)) return ORC_ERR_ARG;
+  const size_t n = dim(g);
+  const int N = g->N, L = g->L;
+  cplx *F = (cplx *)malloc((n + 2 * (size_t)(L + 1)) * sizeof(cplx));
+  if (!F) return ORC_ERR_OOM;
+  load_state(psi_in, F, n);
+  cplx *fb = F + n, *db = fb + (L + 1);     /* f_l(r_b) and (D1 f_l)(r_b) */
+  const int jb = nearest_index(g, r_b);
+  for (int l = 0; l <= L; ++l) {
+    fb[l] = F[(size_t)l * N + (jb - 1)];
+    db[l] = d1_at(g, F, l, jb);
+  }
+  const REAL ac = g->gauge ? (REAL)orc_vecpot(pulse, t) / (REAL)ORC_C_AU : 0;
+  REAL tot = 0;
+  for (int l = 0; l <= L; ++l) tot += fb[l].re * db[l].im - fb[l].im * db[l].re;
+  for (int l = 0; l < L; ++l)
+    tot += 2 * ac * kappa(l + 1) * (fb[l].re * fb[l + 1].re + fb[l].im * fb[l + 1].im);
+  *total = (double)tot;
+  for (int k = 0; k < ntheta; ++k) {
+    const REAL x = (REAL)cos_theta[k];
+    cplx S = c_make(0, 0), P = c_make(0, 0);
+    REAL pm = 0, pl = 1;                      /* P_{l-1}(x), P_l(x) */
+    for (int l = 0; l <= L; ++l) {
+      const REAL y = RSQRT((REAL)(2 * l + 1) / (4 * (REAL)M_PI)) * pl;
+      S = c_add(S, c_scale(y, fb[l]));
+      P = c_add(P, c_scale(y, db[l]));
+      const REAL next = ((REAL)(2 * l + 1) * x * pl - (REAL)l * pm) / (REAL)(l + 1);   /* Bonnet */
+      pm = pl;
+      pl = next;
+    }
+    per_angle[k] = (double)(S.re * P.im - S.im * P.re + ac * x * (S.re * S.re + S.im * S.im));
+  }
   free(F);
   return ORC_OK;
 }

@@ -35,7 +35,17 @@ Pins used (arXiv 1308.1856 passages in brackets):
     a time-dependent field; the error estimate sigma is zero without an
     embedded pair and of the lower solution's order otherwise; one
     Dormand-Prince step and its error estimate equal scipy's RK45 step (same
-    pair) to rounding; an Euler step is psi - i dt H(t_n) psi.
+    pair) to rounding; an Euler step is psi - i dt H(t_n) psi;
+  * dipole velocity and acceleration [Sec. 4]: d<z>/dt = <zdot> (Ehrenfest)
+    to the time-difference error in the length gauge, where the discrete
+    identity is exact, and converging at the stencil's order in the velocity
+    gauge; d<zdot>/dt = <zddot> converging at the stencil's order in both;
+  * flux at r_b [Sec. 4]: on plane waves f_l = c_l e^{ikr} the flux is the
+    stencil's derivative symbol times sum |c_l|^2, and the angular density
+    that times |sum c_l Y_l0|^2 (scipy's spherical harmonics); Gauss-Legendre
+    quadrature of the angular density gives the total in both gauges;
+    continuity: d/dt of the population inside r_b is minus the flux, and the
+    time-integrated flux is the population that crossed r_b.
 """
 from __future__ import annotations
 
@@ -528,10 +538,135 @@ def check_rk_error_estimate(prec="f64"):
     assert s == 0.0
 
 
+def _packet(N, h, L, lmax_populated, r0=12.0, w=1.5, k=0.7, seed=1):
+    """Normalised outgoing Gaussian packet exp(-(r-r0)^2/(2w^2) + ikr) in the
+    partial waves l <= lmax_populated (random complex weights)."""
+    r = h * np.arange(1, N + 1)
+    rng = np.random.default_rng(seed)
+    c = rng.normal(size=L + 1) + 1j * rng.normal(size=L + 1)
+    c[lmax_populated + 1:] = 0
+    psi = c[:, None] * np.exp(-(r - r0) ** 2 / (2 * w * w) + 1j * k * r)[None, :]
+    return psi / math.sqrt(h * np.vdot(psi, psi).real)
+
+
+def _moments_along(g, psi, t0, dt, pulse, prec):
+    """Dipole moments at t0, t0 + dt, t0 + 2 dt along a Lanczos-16 propagation."""
+    a1, _ = oracle.propagate(g, psi, "lanczos", 16, dt, 1, t0=t0, pulse=pulse, precision=prec)
+    a2, _ = oracle.propagate(g, a1, "lanczos", 16, dt, 1, t0=t0 + dt, pulse=pulse, precision=prec)
+    return [oracle.dipole_moments(g, x, t0 + i * dt, pulse, prec) for i, x in enumerate((psi, a1, a2))]
+
+
+def check_dipole_ehrenfest(prec="f64"):
+    """Second-order one-sided time differences (dt = 1e-4, error ~1e-8) of
+    <z> and <zdot> against <zdot> and <zddot>.  The packet leaves the top two
+    partial waves empty, so the truncation at lmax does not enter [z, p_z]."""
+    pulse = Pulse(E0=0.05, omega=0.25, ncycles=2)
+    t0, dt = 7.0, 1e-4
+    for gauge in (0, 1):
+        for st, order in ((5, 4), (3, 2)):
+            errs = []
+            for h in (0.2, 0.1):
+                N, L = int(30 / h), 6
+                g = Grid(N=N, h=h, L=L, stencil=st, gauge=gauge)
+                z = _moments_along(g, _packet(N, h, L, 4), t0, dt, pulse, prec)
+                v = (-3 * z[0][0] + 4 * z[1][0] - z[2][0]) / (2 * dt)
+                a = (-3 * z[0][1] + 4 * z[1][1] - z[2][1]) / (2 * dt)
+                errs.append((abs(v - z[0][1]) / abs(z[0][1]), abs(a - z[0][2]) / abs(z[0][2])))
+            (v0, a0), (v1, a1) = errs
+            if gauge == 0:
+                assert v0 <= 1e-7 and v1 <= 1e-7, f"length-gauge Ehrenfest d<z>/dt: {errs}"
+            else:
+                assert v0 <= 0.1 and v0 / v1 >= 0.6 * 2 ** order, f"velocity-gauge d<z>/dt: {errs}"
+            assert a0 <= 0.1 and a0 / a1 >= 0.6 * 2 ** order, f"d<zdot>/dt, stencil {st}: {errs}"
+
+
+def check_flux_closed_form(prec="f64"):
+    """Plane waves f_l = c_l e^{ikr}: D1 e^{ikr} = i s(k) e^{ikr} with
+    s = sin(kh)/h (3-point) or (8 sin kh - sin 2kh)/(6h) (5-point), so the
+    flux is s sum |c_l|^2 and the angular density s |sum_l c_l Y_l0|^2."""
+    h, N, L, k = 0.1, 300, 3, 0.9
+    r = h * np.arange(1, N + 1)
+    c = np.array([1.0, 0.5j, -0.3, 0.2 + 0.1j])
+    psi = c[:, None] * np.exp(1j * k * r)[None, :]
+    x = np.linspace(-1.0, 1.0, 7)
+    theta = np.arccos(x)
+    if hasattr(sp, "sph_harm_y"):
+        Y = np.array([sp.sph_harm_y(l, 0, theta, 0.0).real for l in range(L + 1)])
+    else:
+        Y = np.array([sp.sph_harm(0, l, 0.0, theta).real for l in range(L + 1)])
+    S = (c[:, None] * Y).sum(axis=0)
+    for st in (3, 5):
+        s = np.sin(k * h) / h if st == 3 else (8 * np.sin(k * h) - np.sin(2 * k * h)) / (6 * h)
+        tot, per = oracle.flux(Grid(N=N, h=h, L=L, stencil=st), psi, 15.0, x, precision=prec)
+        assert abs(tot - s * np.sum(np.abs(c) ** 2)) <= 1e-13, (st, tot)
+        assert np.abs(per - s * np.abs(S) ** 2).max() <= 1e-13, st
+
+
+def check_flux_angular_integral(prec="f64"):
+    """2 pi int d(cos theta) of the angular density = the total flux, exactly
+    for Gauss-Legendre with L + 3 nodes (the density is a polynomial of
+    degree 2L + 1 in cos theta), in both gauges (the A term of the velocity
+    gauge carries the cos(theta) couplings)."""
+    pulse = Pulse(E0=0.05, omega=0.25, ncycles=2)
+    x, w = np.polynomial.legendre.leggauss(9)
+    for gauge in (0, 1):
+        g = Grid(N=300, h=0.1, L=6, stencil=5, gauge=gauge)
+        psi = _packet(300, 0.1, 6, 6)
+        tot, per = oracle.flux(g, psi, 12.3, x, t=9.0, pulse=pulse, precision=prec)
+        assert abs(tot - 2 * np.pi * np.sum(w * per)) <= 1e-13 * max(1.0, abs(tot)), gauge
+        assert abs(tot) >= 0.1
+
+
+def check_flux_continuity(prec="f64"):
+    """Length gauge, an outgoing packet at r_b: d/dt P_inside = -flux, with
+    P_inside = h (sum_{r_j < r_b} |f|^2 + |f(r_b)|^2 / 2); converging at order
+    2 for the 5-point stencil (the half-weight surface), to the time-difference
+    error for the 3-point one.  The flux integrated over a run (trapezoid in
+    time) is the population that crossed r_b."""
+    rb = 12.0
+    for st in (5, 3):
+        errs = []
+        for h in (0.2, 0.1):
+            N, L = int(40 / h), 3
+            g = Grid(N=N, h=h, L=L, stencil=st)
+            psi = _packet(N, h, L, 3, r0=10.0, k=1.0)
+            jb = int(round(rb / h))
+
+            def inside(p):
+                a = np.abs(p) ** 2
+                return h * (a[:, :jb - 1].sum() + 0.5 * a[:, jb - 1].sum())
+            dt = 1e-3
+            a1, _ = oracle.propagate(g, psi, "lanczos", 16, dt, 1, precision=prec)
+            a2, _ = oracle.propagate(g, a1, "lanczos", 16, dt, 1, t0=dt, precision=prec)
+            d = (-3 * inside(psi) + 4 * inside(a1) - inside(a2)) / (2 * dt)
+            F, _ = oracle.flux(g, psi, rb, precision=prec)
+            errs.append(abs(d + F) / abs(F))
+        if st == 5:
+            assert errs[0] <= 2e-2 and errs[0] / errs[1] >= 3.0, errs
+        else:
+            assert max(errs) <= 1e-5, errs
+    h, N, L, dt, n = 0.1, 400, 3, 0.02, 150
+    g = Grid(N=N, h=h, L=L, stencil=3)
+    psi = _packet(N, h, L, 3, r0=10.0, k=1.0)
+    jb = int(round(rb / h))
+    before = h * (np.abs(psi[:, jb:]) ** 2).sum() + 0.5 * h * (np.abs(psi[:, jb - 1]) ** 2).sum()
+    fl, _ = oracle.flux(g, psi, rb, precision=prec)
+    integral = 0.0
+    for i in range(n):
+        psi, _ = oracle.propagate(g, psi, "lanczos", 16, dt, 1, t0=i * dt, precision=prec)
+        f1, _ = oracle.flux(g, psi, rb, precision=prec)
+        integral += 0.5 * dt * (fl + f1)
+        fl = f1
+    after = h * (np.abs(psi[:, jb:]) ** 2).sum() + 0.5 * h * (np.abs(psi[:, jb - 1]) ** 2).sum()
+    assert integral >= 0.2 and abs(integral - (after - before)) <= 1e-3 * integral, (integral, after - before)
+
+
 ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_hydrogen_paper_values, check_hydrogen_convergence,
               check_field_free_eigenstate, check_dense_expm, check_time_order,
               check_norm_and_yield, check_observables, check_pulse, check_mask,
               check_imaginary_time_eigenstate, check_imaginary_time_ground_state,
               check_velocity_gauge_operator, check_vector_potential, check_gauge_invariance,
-              check_rk_orders, check_rk_dormand_prince_step, check_rk_error_estimate]
+              check_rk_orders, check_rk_dormand_prince_step, check_rk_error_estimate,
+              check_dipole_ehrenfest, check_flux_closed_form, check_flux_angular_integral,
+              check_flux_continuity]

@@ -77,6 +77,24 @@ MUTANTS = [
     ("sigma_counts_reals", "sig += RSQRT(d2 / (REAL)n);", "sig += RSQRT(d2 / (REAL)(2 * n));",
      P.check_rk_dormand_prince_step),
     ("sigma_no_sqrt", "sig += RSQRT(d2 / (REAL)n);", "sig += d2 / (REAL)n;", P.check_rk_orders),
+    ("dipole_velocity_printed_factor", "pz += 2 * kappa(l + 1) * h * sp;", "pz += kappa(l + 1) * h * sp;",
+     P.check_dipole_ehrenfest),
+    ("dipole_velocity_centrifugal", "c_scale((REAL)(l + 1) / r, a));", "c_scale((REAL)l / r, a));",
+     P.check_dipole_ehrenfest),
+    ("dipole_velocity_gauge_term", "(REAL)orc_vecpot(pulse, t) / (REAL)ORC_C_AU * norm",
+     "-(REAL)orc_vecpot(pulse, t) / (REAL)ORC_C_AU * norm", P.check_dipole_ehrenfest),
+    ("dipole_accel_field_sign", "(double)(-(REAL)orc_field(pulse, t) * norm", "(double)((REAL)orc_field(pulse, t) * norm",
+     P.check_dipole_ehrenfest),
+    ("dipole_accel_power", "sf += re / (r * r);", "sf += re / r;", P.check_dipole_ehrenfest),
+    ("flux_printed_sign", "tot += fb[l].re * db[l].im - fb[l].im * db[l].re;",
+     "tot -= fb[l].re * db[l].im - fb[l].im * db[l].re;", P.check_flux_continuity),
+    ("flux_gauge_term_factor", "tot += 2 * ac * kappa(l + 1)", "tot += ac * kappa(l + 1)",
+     P.check_flux_angular_integral),
+    ("harmonic_normalisation", "RSQRT((REAL)(2 * l + 1) / (4 * (REAL)M_PI))", "RSQRT((REAL)(2 * l + 1) / (2 * (REAL)M_PI))",
+     P.check_flux_closed_form),
+    ("legendre_recurrence", "((REAL)(2 * l + 1) * x * pl - (REAL)l * pm)", "((REAL)(2 * l + 1) * x * pl - (REAL)(l + 1) * pm)",
+     P.check_flux_closed_form),
+    ("flux_radius_off_by_one", "return best;", "return best + 1;", P.check_flux_continuity),
 ]
 
 
