@@ -160,6 +160,60 @@ int tdse_set_reference(tdse_t *h, const double *f0_host);
  */
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps);
 
+/*
+ * Dipole moment, velocity and acceleration of the current state at the
+ * handle's time t (Sec. 4, Eqs. (Dipole), (DipoleVelocity), (DipoleAccel)),
+ * m = 0, dr-weighted sums over the grid:
+ *   <z>     = 2 sum_l kappa_{l+1} sum_j r_j Re(f_l^* f_{l+1}) dr
+ *   <zdot>  = 2 sum_l kappa_{l+1} sum_j Im(f_{l+1}^* (D1 f_l - (l+1)/r_j f_l)) dr
+ *             [+ (A(t)/c) ||psi||^2 in the velocity gauge]
+ *   <zddot> = -E(t) ||psi||^2 - 2 Z sum_l kappa_{l+1} sum_j Re(f_l^* f_{l+1}) / r_j^2 dr
+ * D1 is the first-derivative formula of the velocity gauge (5- or 3-point,
+ * with the grid's ghost).  <zdot> carries the factor 2 that Ehrenfest's
+ * theorem d<z>/dt = <zdot> needs (the printed Eq. (DipoleVelocity) omits it)
+ * and is the kinetic momentum.  The acceleration form needs dV/dr, so with a
+ * tabulated potential *zddot is NaN.  Any output pointer may be NULL.
+ * Synchronises the stream.  Errors: TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_dipole_moments(tdse_t *h, double *z, double *zdot, double *zddot);
+
+/*
+ * Record <z>, <zdot> and <zddot> (as tdse_dipole_moments) after every
+ * real-time step of tdse_propagate / tdse_propagate_rk into a device buffer
+ * of `capacity` entries (one extra launch per step; recording stops when the
+ * buffer is full).  capacity 0 turns recording off; every call discards what
+ * was recorded.  TDSE_ERR_ARG for capacity < 0; TDSE_ERR_OOM.
+ */
+int tdse_dipole_series(tdse_t *h, long capacity);
+/* Copy up to max_entries recorded entries to out as {t, <z>, <zdot>, <zddot>}
+ * (4 doubles each, in step order); *count (may be NULL) receives the number
+ * recorded so far.  out may be NULL to query the count.  Synchronises. */
+int tdse_dipole_series_read(tdse_t *h, double *out, long max_entries, long *count);
+
+/*
+ * Flux through the sphere r = r_b (Sec. 4, Eqs. (flux), (pad), (yield)),
+ * evaluated at the grid point nearest r_b (a tie goes to the inner point):
+ *   flux       = sum_l Im(f_l^* D1 f_l) [+ 2 (A/c) sum_l kappa_{l+1} Re(f_l^* f_{l+1})]
+ *              = r_b^2 times the radial current integrated over the sphere,
+ *   density_k  = Im(S_k^* P_k) [+ (A/c) cos(theta_k) |S_k|^2]
+ *              = r_b^2 j_r(r_b, theta_k),  S_k = sum_l Y_l0(theta_k) f_l,
+ *                P_k = sum_l Y_l0(theta_k) D1 f_l,  Y_l0 = sqrt((2l+1)/(4 pi)) P_l,
+ * outward positive (the paper prints -Im in Eq. (flux); the continuity
+ * equation and Eq. (yield) fix the sign), the A terms in the velocity gauge
+ * only.  After every real-time step the time integrals are advanced by the
+ * trapezoid rule over the step: yield = int flux dt (Eq. (yield)), pad_k =
+ * int density_k dt (Eq. (pad), dP/dOmega).  Setup evaluates the current state
+ * and zeroes the integrals; r_b <= 0 turns the flux off.  cos_theta: ntheta
+ * values in [-1, 1] (host, copied).  One extra single-block launch per step.
+ * Errors: TDSE_ERR_ARG (r_b outside the box, bad angles, lmax > 1535),
+ * TDSE_ERR_OOM, TDSE_ERR_CUDA.  Synchronises.
+ */
+int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta);
+/* The current flux and density (at the last step's end, or at setup) and their
+ * time integrals; any pointer may be NULL (density and pad hold ntheta
+ * values).  TDSE_ERR_ARG if the flux is not set up.  Synchronises. */
+int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, double *pad);
+
 /* Explicit Runge-Kutta methods of the appendix "Runge-Kutta". */
 enum {
   TDSE_RK_EULER = 0,          /* forward Euler, no embedded pair */

@@ -137,6 +137,40 @@ class TDSE:
                                           ctypes.byref(e)))
         return e.value
 
+    def dipole_moments(self) -> np.ndarray:
+        """[<z>, d<z>/dt, d^2<z>/dt^2] of the current state (Sec. 4)."""
+        z, v, a = (ctypes.c_double() for _ in range(3))
+        self._check(C.tdse_dipole_moments(self.h, ctypes.byref(z), ctypes.byref(v), ctypes.byref(a)))
+        return np.array([z.value, v.value, a.value])
+
+    def record_dipole(self, capacity: int):
+        """Record the dipole moments after every real-time step (0: off)."""
+        self._check(C.tdse_dipole_series(self.h, int(capacity)))
+
+    def dipole_series(self) -> np.ndarray:
+        """(n, 4) array of {t, <z>, <zdot>, <zddot>} recorded so far."""
+        n = ctypes.c_long()
+        self._check(C.tdse_dipole_series_read(self.h, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 4))
+        if n.value:
+            self._check(C.tdse_dipole_series_read(self.h, out.ctypes.data_as(C._dp), n.value, ctypes.byref(n)))
+        return out
+
+    def flux_setup(self, r_b: float, cos_theta=None):
+        """Accumulate the flux through r = r_b and its angular density (Sec. 4)."""
+        ct = np.ascontiguousarray(np.zeros(0) if cos_theta is None else cos_theta, dtype=np.float64)
+        self._flux_nt = len(ct)
+        self._check(C.tdse_flux_setup(self.h, float(r_b), len(ct), ct.ctypes.data_as(C._dp) if len(ct) else None))
+
+    def flux(self) -> dict:
+        """{flux, yield, density[ntheta], pad[ntheta]}: the flux now and its time integrals."""
+        nt = getattr(self, "_flux_nt", 0)
+        f, y = ctypes.c_double(), ctypes.c_double()
+        dens, pad = np.zeros(max(nt, 1)), np.zeros(max(nt, 1))
+        self._check(C.tdse_flux_read(self.h, ctypes.byref(f), ctypes.byref(y), dens.ctypes.data_as(C._dp),
+                                     pad.ctypes.data_as(C._dp)))
+        return {"flux": f.value, "yield": y.value, "density": dens[:nt], "pad": pad[:nt]}
+
     def observables(self) -> dict:
         norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
         lp = np.zeros(self.lmax + 1)

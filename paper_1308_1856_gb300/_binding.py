@@ -80,6 +80,11 @@ SIGNATURES = {
     "tdse_propagate": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long]),
     "tdse_propagate_imag": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_long, _dp]),
     "tdse_propagate_rk": (_c_int, [_vp, _c_int, _c_double, _c_long, _dp]),
+    "tdse_dipole_moments": (_c_int, [_vp, _dp, _dp, _dp]),
+    "tdse_dipole_series": (_c_int, [_vp, _c_long]),
+    "tdse_dipole_series_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
+    "tdse_flux_setup": (_c_int, [_vp, _c_double, _c_int, _dp]),
+    "tdse_flux_read": (_c_int, [_vp, _dp, _dp, _dp, _dp]),
     "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
     "tdse_sync": (_c_int, [_vp]),
@@ -179,6 +184,11 @@ tdse_set_reference = _fn("tdse_set_reference")
 tdse_propagate = _fn("tdse_propagate")
 tdse_propagate_imag = _fn("tdse_propagate_imag")
 tdse_propagate_rk = _fn("tdse_propagate_rk")
+tdse_dipole_moments = _fn("tdse_dipole_moments")
+tdse_dipole_series = _fn("tdse_dipole_series")
+tdse_dipole_series_read = _fn("tdse_dipole_series_read")
+tdse_flux_setup = _fn("tdse_flux_setup")
+tdse_flux_read = _fn("tdse_flux_read")
 tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")
 tdse_sync = _fn("tdse_sync")

@@ -34,6 +34,15 @@ struct tdse {
   double *obs_partials = nullptr, *obs_out = nullptr;
   double *imag = nullptr;          // imaginary time: {squared norm before the step, energy}
   double *rk_sigma = nullptr;      // explicit RK: sum of the steps' error estimates
+  // Sec. 4 observables recorded after every real-time step (the step hooks)
+  double *dip_out = nullptr;       // one-shot dipole moments (3 doubles)
+  double *series = nullptr;        // 3 doubles per recorded step: <z>, <zdot>, <zddot>
+  long series_cap = 0;
+  std::vector<double> series_t;    // the recorded steps' times
+  double *flux_state = nullptr;    // see launch_flux; 2 + 2 ntheta doubles
+  double *flux_y = nullptr;        // Y_l0(theta_k), (L+1) x ntheta
+  double *flux_ct = nullptr;       // cos(theta_k)
+  int flux_ntheta = 0, flux_ib = -1;
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
   // a final stage reads one pair with halos while writing the other) and
   // complex64 work vectors
@@ -206,6 +215,11 @@ void free_all(tdse *h) {
   cudaFree(h->obs_out);
   cudaFree(h->imag);
   cudaFree(h->rk_sigma);
+  cudaFree(h->dip_out);
+  cudaFree(h->series);
+  cudaFree(h->flux_state);
+  cudaFree(h->flux_y);
+  cudaFree(h->flux_ct);
   cudaFree(h->diagf);
   cudaFree(h->rjf);
   cudaFree(h->kappaf);
@@ -332,6 +346,48 @@ int refresh_split(tdse *h, bool need_norm) {
   return TDSE_OK;
 }
 
+// ---- Sec. 4 observables after every real-time step --------------------------
+bool hooks_on(const tdse *h) { return h->series_cap > 0 || h->flux_ib >= 0; }
+
+// A/c of the velocity gauge at t (0 in the length gauge).
+double ac_at(const tdse *h, double t) { return h->g.gauge == 1 ? coupling_at(h, t) : 0.0; }
+
+unsigned *obs_ticket(tdse *h) {
+  return reinterpret_cast<unsigned *>(h->obs_partials + (size_t)5 * observables_blocks(h->g) * (h->g.L + 1));
+}
+
+int launch_dipole(tdse *h, double t, double *out) {
+  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+              launch_dipole_moments(h->g, view(h), h->psi, h->opts.ghost, field_at(h, t), ac_at(h, t), h->Z,
+                                    h->vtab.empty(), h->obs_partials, obs_ticket(h), out, h->stream),
+              "dipole moments");
+  return TDSE_OK;
+}
+
+// After a step that ended at t_new: record the dipole moments (if a series is
+// open and not full) and advance the flux integrals (if set up).
+int step_hook(tdse *h, double t_new, double dt) {
+  if (h->series_cap > 0 && (long)h->series_t.size() < h->series_cap) {
+    int rc = launch_dipole(h, t_new, h->series + 3 * h->series_t.size());
+    if (rc) return rc;
+    h->series_t.push_back(t_new);
+  }
+  if (h->flux_ib >= 0)
+    TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+                launch_flux(h->g, view(h), h->psi, h->opts.ghost, h->flux_ib, ac_at(h, t_new), h->flux_y,
+                            h->flux_ct, h->flux_ntheta, dt, false, h->flux_state, h->stream),
+                "flux");
+  return TDSE_OK;
+}
+
+#define TDSE_HOOK(h, t_new, dt)                  \
+  do {                                           \
+    if (hooks_on(h)) {                           \
+      int hr_ = step_hook(h, t_new, dt);         \
+      if (hr_) return hr_;                       \
+    }                                            \
+  } while (0)
+
 int mx_taylor_steps(tdse *h, int P, double dt, long nsteps) {
   int rc = ensure_mixed(h, 2);
   if (rc) return rc;
@@ -357,6 +413,7 @@ int mx_taylor_steps(tdse *h, int P, double dt, long nsteps) {
       w_in = w_out;
     }
     h->split_cur = nxt;
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   // the final stage re-splits psi but does not recompute ||psi||
   h->mixed_norm_valid = false;
@@ -383,6 +440,7 @@ int mx_rk4_steps(tdse *h, double dt, long nsteps) {
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E2, 3, dt, hi, lo, kb, ka, ahi, alo, h->psi, nullptr, nullptr, h->stream), "mixed rk 3");
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_mx_rk_stage(h->g, mv, op, E4, 4, dt, hi, lo, ka, nullptr, ahi, alo, h->psi, split_hi(h, nxt), split_lo(h, nxt), h->stream), "mixed rk 4");
     h->split_cur = nxt;
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   h->mixed_norm_valid = false;
   return TDSE_OK;
@@ -419,6 +477,7 @@ int mx_lanczos_steps(tdse *h, int m, double dt, long nsteps) {
                 launch_mx_lanczos_combine(h->g, op, h->psi, hi, lo, h->mwork + G, G, h->red, h->ls,
                                           h->status, h->stream),
                 "mixed lanczos combine");
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   h->mixed_norm_valid = true;   // the combine leaves psi split and sigma_0 current
   return TDSE_OK;
@@ -445,6 +504,7 @@ int taylor_steps(tdse *h, int P, double dt, long nsteps) {
     if (P == 1)
       TDSE_CUDA(h, cudaMemcpyAsync(h->psi, buf[0], sizeof(double2) * G, cudaMemcpyDeviceToDevice, h->stream),
                 "taylor copy");
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   return TDSE_OK;
 }
@@ -463,6 +523,7 @@ int rk4_steps(tdse *h, double dt, long nsteps) {
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 2, dt, ga, h->psi, acc, acc, gb, nullptr, h->stream), "rk stage 2");
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E2, 3, dt, gb, h->psi, acc, acc, ga, nullptr, h->stream), "rk stage 3");
     TDSE_LAUNCH(h, TDSE_K_RK_STAGE, launch_rk_stage(h->g, op, E4, 4, dt, ga, h->psi, acc, nullptr, nullptr, h->psi, h->stream), "rk stage 4");
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   return TDSE_OK;
 }
@@ -489,6 +550,7 @@ int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
     TDSE_LAUNCH(h, TDSE_K_LANCZOS_EXPM, launch_lanczos_expm(m, dt, h->ls, h->stream), "lanczos expm");
     TDSE_LAUNCH(h, TDSE_K_LANCZOS_COMBINE, launch_lanczos_combine(h->g, op, m, h->psi, h->work + G, G, h->red, h->ls, h->status, h->stream),
                 "lanczos combine");
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   return TDSE_OK;
 }
@@ -607,6 +669,7 @@ int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
     if (s == 1)
       TDSE_CUDA(h, cudaMemcpyAsync(h->psi, gbuf[0], sizeof(double2) * G, cudaMemcpyDeviceToDevice, h->stream),
                 "rk copy");
+    TDSE_HOOK(h, t0 + (double)(n + 1) * dt, dt);
   }
   double out = 0.0;
   TDSE_CUDA(h, cudaMemcpyAsync(&out, h->rk_sigma, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read sigma");
@@ -1030,6 +1093,148 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
   if (p_ground) *p_ground = out[3];
   if (l_pop) std::memcpy(l_pop, out.data() + 4, sizeof(double) * (L + 1));
   if (!std::isfinite(out[0])) return fail(h, TDSE_ERR_NONFINITE, "state holds Inf/NaN (unstable step size?)");
+  return TDSE_OK;
+}
+
+int tdse_dipole_moments(tdse_t *h, double *z, double *zdot, double *zddot) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!h->dip_out && cudaMalloc(&h->dip_out, 3 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->dip_out = nullptr;
+    return fail(h, TDSE_ERR_OOM, "dipole output");
+  }
+  rc = launch_dipole(h, h->t, h->dip_out);
+  if (rc) return rc;
+  double out[3];
+  TDSE_CUDA(h, cudaMemcpyAsync(out, h->dip_out, sizeof(out), cudaMemcpyDeviceToHost, h->stream), "read dipole");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync dipole");
+  if (z) *z = out[0];
+  if (zdot) *zdot = out[1];
+  if (zddot) *zddot = out[2];
+  return TDSE_OK;
+}
+
+int tdse_dipole_series(tdse_t *h, long capacity) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (capacity < 0) return fail(h, TDSE_ERR_ARG, "capacity must be >= 0");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before series");
+  cudaFree(h->series);
+  h->series = nullptr;
+  h->series_cap = 0;
+  h->series_t.clear();
+  if (capacity == 0) return TDSE_OK;
+  if (cudaMalloc(&h->series, sizeof(double) * 3 * (size_t)capacity) != cudaSuccess) {
+    cudaGetLastError();
+    h->series = nullptr;
+    return fail(h, TDSE_ERR_OOM, "dipole series");
+  }
+  h->series_t.reserve((size_t)capacity);
+  h->series_cap = capacity;
+  return TDSE_OK;
+}
+
+int tdse_dipole_series_read(tdse_t *h, double *out, long max_entries, long *count) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  const long n = (long)h->series_t.size();
+  if (count) *count = n;
+  if (!out || max_entries <= 0 || n == 0) return TDSE_OK;
+  const long k = n < max_entries ? n : max_entries;
+  std::vector<double> v((size_t)3 * k);
+  TDSE_CUDA(h, cudaMemcpyAsync(v.data(), h->series, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->stream),
+            "read series");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync series");
+  for (long i = 0; i < k; ++i) {
+    out[4 * i] = h->series_t[(size_t)i];
+    out[4 * i + 1] = v[(size_t)3 * i];
+    out[4 * i + 2] = v[(size_t)3 * i + 1];
+    out[4 * i + 3] = v[(size_t)3 * i + 2];
+  }
+  return TDSE_OK;
+}
+
+int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before flux setup");
+  cudaFree(h->flux_state);
+  cudaFree(h->flux_y);
+  cudaFree(h->flux_ct);
+  h->flux_state = h->flux_y = h->flux_ct = nullptr;
+  h->flux_ib = -1;
+  h->flux_ntheta = 0;
+  if (!(r_b > 0.0)) return TDSE_OK;   // off
+  const int N = h->g.N, L = h->g.L;
+  if (!std::isfinite(r_b) || ntheta < 0 || (ntheta > 0 && !cos_theta))
+    return fail(h, TDSE_ERR_ARG, "need a finite r_b > 0, ntheta >= 0 and cos_theta for ntheta > 0");
+  if (flux_shared_bytes(h->g) > 48 * 1024) return fail(h, TDSE_ERR_ARG, "flux: lmax too large (at most 1535)");
+  // the grid point nearest r_b (r_j = (j + 1) dr + offset, j 0-based), inside the box
+  const double x = (r_b - h->opts.offset) / h->g.dr - 1.0;
+  if (!(x > -0.5 && x < (double)N - 0.5)) return fail(h, TDSE_ERR_ARG, "r_b lies outside the box");
+  int ib = (int)std::ceil(x - 0.5);   // nearest; a tie goes to the inner point
+  if (ib < 0) ib = 0;
+  if (ib > N - 1) ib = N - 1;
+  std::vector<double> ct(ntheta), y((size_t)(L + 1) * (ntheta > 0 ? ntheta : 1));
+  for (int k = 0; k < ntheta; ++k) {
+    const double c = cos_theta[k];
+    if (!(c >= -1.0 && c <= 1.0)) return fail(h, TDSE_ERR_ARG, "cos_theta values must lie in [-1, 1]");
+    ct[k] = c;
+    // Y_l0 = sqrt((2l+1)/(4 pi)) P_l(c), P_l by the three-term recurrence
+    double p0 = 1.0, p1 = c;
+    for (int l = 0; l <= L; ++l) {
+      const double pl = (l == 0) ? 1.0 : (l == 1 ? c : 0.0);
+      double P = pl;
+      if (l >= 2) {
+        P = ((2.0 * l - 1.0) * c * p1 - (l - 1.0) * p0) / (double)l;
+        p0 = p1;
+        p1 = P;
+      }
+      y[(size_t)l * ntheta + k] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * P;
+    }
+  }
+  const size_t nstate = 2 + 2 * (size_t)ntheta;
+  if (cudaMalloc(&h->flux_state, sizeof(double) * nstate) != cudaSuccess ||
+      (ntheta > 0 && (cudaMalloc(&h->flux_y, sizeof(double) * y.size()) != cudaSuccess ||
+                      cudaMalloc(&h->flux_ct, sizeof(double) * ct.size()) != cudaSuccess))) {
+    cudaGetLastError();
+    cudaFree(h->flux_state);
+    cudaFree(h->flux_y);
+    cudaFree(h->flux_ct);
+    h->flux_state = h->flux_y = h->flux_ct = nullptr;
+    return fail(h, TDSE_ERR_OOM, "flux buffers");
+  }
+  if (ntheta > 0) {
+    TDSE_CUDA(h, cudaMemcpyAsync(h->flux_y, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, h->stream),
+              "flux table");
+    TDSE_CUDA(h, cudaMemcpyAsync(h->flux_ct, ct.data(), sizeof(double) * ct.size(), cudaMemcpyHostToDevice, h->stream),
+              "flux angles");
+  }
+  h->flux_ib = ib;
+  h->flux_ntheta = ntheta;
+  // the current state opens the integrals (at zero)
+  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+              launch_flux(h->g, view(h), h->psi, h->opts.ghost, ib, ac_at(h, h->t), h->flux_y, h->flux_ct, ntheta,
+                          0.0, true, h->flux_state, h->stream),
+              "flux");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync flux setup");
+  return TDSE_OK;
+}
+
+int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, double *pad) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (h->flux_ib < 0) return fail(h, TDSE_ERR_ARG, "flux is not set up");
+  const int nt = h->flux_ntheta;
+  std::vector<double> v(2 + 2 * (size_t)nt);
+  TDSE_CUDA(h, cudaMemcpyAsync(v.data(), h->flux_state, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->stream),
+            "read flux");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync flux");
+  if (flux) *flux = v[0];
+  if (yield) *yield = v[1];
+  if (density && nt) std::memcpy(density, v.data() + 2, sizeof(double) * nt);
+  if (pad && nt) std::memcpy(pad, v.data() + 2 + nt, sizeof(double) * nt);
   return TDSE_OK;
 }
 

@@ -105,6 +105,22 @@ struct RkStageArgs {
 cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
                                     const double2 *gin, const double2 *psi, const RkStageArgs &a,
                                     Reduction *red, cudaStream_t st);
+// ---- Sec. 4 dipole moments and flux (tdse_kernels_flux.cu) -------------------
+// out[0..2] = <z>, d<z>/dt, d^2<z>/dt^2 of psi (E the field, ac = A/c in the
+// velocity gauge else 0; the acceleration is NaN unless coulomb).  partials:
+// 4 * dipole_blocks(g) * (L+1) doubles; ticket: zeroed, left zeroed.
+int dipole_blocks(const Geometry &g);
+cudaError_t launch_dipole_moments(const Geometry &g, const OperatorView &op, const double2 *psi,
+                                  int ghost, double E, double ac, double Z, bool coulomb,
+                                  double *partials, unsigned *ticket, double *out, cudaStream_t st);
+// Flux through r = r_(ib+1) and its angular density at ntheta angles
+// (ytab: Y_l0(theta_k), l-major); state = {flux now, its integral, density now
+// [ntheta], density integral [ntheta]}.  init: set "now" and zero the
+// integrals; else integral += dt/2 (previous now + new now) first.
+size_t flux_shared_bytes(const Geometry &g);
+cudaError_t launch_flux(const Geometry &g, const OperatorView &op, const double2 *psi, int ghost,
+                        int ib, double ac, const double *ytab, const double *cos_theta, int ntheta,
+                        double dt, bool init, double *state, cudaStream_t st);
 // Imaginary time: prev[0] = dr * red->normsq (the squared norm before a step);
 // after the step (red->normsq of the new state): energy[0] =
 // -ln(dr normsq / prev) / (2 dt) and psi /= sqrt(dr normsq).

@@ -46,6 +46,13 @@ def test_null_handle_calls(lib):
     assert B.tdse_propagate(None, 0, 4, 0.1, 1) == B.TDSE_ERR_ARG
     assert B.tdse_sync(None) == B.TDSE_ERR_ARG
     assert B.tdse_launch_count(None) == 0
+    assert B.tdse_propagate_rk(None, B.TDSE_RK_DORMAND_PRINCE, 0.1, 1, None) == B.TDSE_ERR_ARG
+    assert B.tdse_propagate_imag(None, 2, 12, 0.1, 1, None) == B.TDSE_ERR_ARG
+    assert B.tdse_dipole_moments(None, None, None, None) == B.TDSE_ERR_ARG
+    assert B.tdse_dipole_series(None, 10) == B.TDSE_ERR_ARG
+    assert B.tdse_dipole_series_read(None, None, 0, None) == B.TDSE_ERR_ARG
+    assert B.tdse_flux_setup(None, 10.0, 0, None) == B.TDSE_ERR_ARG
+    assert B.tdse_flux_read(None, None, None, None, None) == B.TDSE_ERR_ARG
 
 
 def test_library_is_sm103a_build():
