@@ -65,6 +65,10 @@ KERNEL_FLOPS_PER_GP = {
     "lanczos_b": 8,                          # z - a u, + |.|^2
     "lanczos_combine": 8 * 12 + 4,           # sum of 12 complex products + norm
 }
+# Dipole moments kernel, per grid point: |f|^2 (4), w Re(f_l^* f_{l+1}) (5),
+# the unscaled first derivative (8), w Im(f_{l+1}^* D1 f_l) (5) and
+# w (l+1) Im(f_{l+1}^* f_l) (5).
+DIPOLE_FLOPS_PER_GP = 27
 # Algorithmic HBM bytes per grid point of the mixed kernels (complex64 work
 # vectors 8 B, split of psi 16 B, FP32 diagonal table 4 B; one read of every
 # operand and one write of every output).
@@ -409,6 +413,59 @@ def run_rk_pairs(stream_ptr, psi0, steps=5, warmup=3, tableaus=("dormand_prince"
     return out
 
 
+def run_step_observables(stream_ptr, psi0, steps=5, warmup=3, ntheta=180, r_b=10.0):
+    """Sec. 4 observables recorded after every step on the at-scale grid
+    (FP64 Lanczos-12, dt = 0.02): the dipole series (<z>, <zdot>, <zddot>)
+    and the flux through r_b with its density at ntheta angles and their time
+    integrals.  Per-step time with and without them (CUDA events, L2 flushed
+    before every step), and the dipole kernel against the FP64 peak (it reads
+    the state once, 16 B per grid point, and is FP64-instruction bound)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ct = np.cos((np.arange(ntheta) + 0.5) * np.pi / ntheta)
+    out = {"workload": f"scale grid, FP64 Lanczos-12 dt={CFG.dt:g}; dipole series + flux at r_b={r_b:g} with "
+                       f"{ntheta} angles after every step; L2 flushed before every step"}
+    for label, hooks in (("without", False), ("with", True)):
+        h = make_handle(stream_ptr, "fp64")
+        h.set_state(psi0)
+        h.time = 0.3 * CFG.duration
+        if hooks:
+            h.record_dipole(steps + warmup + 8)
+            h.flux_setup(r_b, ct)
+        for _ in range(warmup):
+            h.propagate("lanczos", 12, CFG.dt, 1)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            h.propagate("lanczos", 12, CFG.dt, 1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        out[f"ms_per_step_{label}"] = sum(a.elapsed_time(b) for a, b in evs) / steps
+        if hooks:
+            h.profile(True)
+            for k in range(3):
+                flush.fill_(float(k))
+                h.propagate("lanczos", 12, CFG.dt, 1)
+            prof = h.profile_read()
+            h.profile(False)
+            dms, dn = prof.get("dipole", (0.0, 0))
+            fms, fn = prof.get("flux", (0.0, 0))
+            flops = DIPOLE_FLOPS_PER_GP * CFG.G
+            ach = flops / (dms / dn * 1e-3) / 1e12 if dn else None
+            out["dipole_kernel"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": None if ach is None else ach / FP64_PEAK_TFLOPS,
+                                    "flops_per_launch": flops, "bytes_per_launch": 16.0 * CFG.G,
+                                    "avg_launch_ms": dms / max(dn, 1), "launches": dn}
+            out["flux_kernel_avg_ms"] = fms / max(fn, 1)
+            f = h.flux()
+            out["flux_now"], out["flux_yield"] = f["flux"], f["yield"]
+        h.close()
+    out["overhead_frac"] = out["ms_per_step_with"] / out["ms_per_step_without"] - 1.0
+    return out
+
+
 def mixed_error(stream_ptr, psi0, nsteps=10):
     """The mixed-precision path's error against the FP64 path on the at-scale
     grid: Lanczos-12 from the benchmark's start state, at a step where the
@@ -450,6 +507,9 @@ def run_ours(args, ws, rank, local):
     if args.rows == "rk":
         return {"metric": METRIC, "rk_pairs": run_rk_pairs(stream.cuda_stream, psi0, steps=args.steps,
                                                            warmup=args.warmup)}
+    if args.rows == "obs":
+        return {"metric": METRIC, "step_observables": run_step_observables(stream.cuda_stream, psi0,
+                                                                           steps=args.steps, warmup=args.warmup)}
     if args.rows in ("all", "single"):
         rows += [HandleRow(m, o, dt, p, stream.cuda_stream, psi0) for m, o, dt, p in METHODS]
     if args.rows in ("all", "batched"):
@@ -592,6 +652,7 @@ def run_ours(args, ws, rank, local):
     if args.rows == "all":
         result["mixed_error"] = mixed_error(stream.cuda_stream, psi0)
         result["rk_pairs"] = run_rk_pairs(stream.cuda_stream, psi0)
+        result["step_observables"] = run_step_observables(stream.cuda_stream, psi0)
     if args.rows == "all" and not args.no_serve:
         result["served"] = run_served(args, stream.cuda_stream)
     return result
@@ -661,8 +722,8 @@ def main():
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
                     help="restrict to one precision (profiling runs)")
-    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served", "rk"],
-                    help="restrict to the single-instance, batched, served or embedded-RK rows")
+    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served", "rk", "obs"],
+                    help="restrict to the single-instance, batched, served, embedded-RK or step-observable rows")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched rows (smaller only for profiling captures)")
     ap.add_argument("--schedule", action="append", default=[], metavar="PREC=PF,RING,SB,EB",

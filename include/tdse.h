@@ -3,8 +3,8 @@
  *
  * The library advances the partial-wave radial wavefunction of a one-electron
  * (hydrogen / single-active-electron) atom in a linearly polarised laser field,
- * in the length gauge, with hand-written sm_103a CUDA kernels.  It follows
- * arXiv 1308.1856 (CLTDSE):
+ * in the length or the velocity gauge, with hand-written sm_103a CUDA kernels.
+ * It follows arXiv 1308.1856 (CLTDSE):
  *
  *   state vector F, l-major  ............ Sec. 2, the vector F of Eq. (h_matrix)
  *   Hamiltonian H(t) ..................... Sec. 2, Eqs. (tdse-radial-field),
@@ -12,10 +12,14 @@
  *   dF/dt = -i H(t) F .................... Eq. (tdse_matrix)
  *   Taylor / Runge-Kutta / Lanczos ....... Sec. 5 "TDSE": Eq. (Taylor),
  *                                          Eq. (RKDeriv), Appendix "Lanczos methods"
- *   pulse ................................ Sec. 3, Eq. (EField)
+ *   embedded Runge-Kutta pairs ........... Appendix "Runge-Kutta"
+ *   imaginary time ....................... Sec. 3
+ *   pulse, vector potential .............. Sec. 3, Eqs. (EField), (VectorStep)
  *   absorber ............................. Sec. 2.1 (applied as a mask)
  *   observables .......................... Sec. 4: Eqs. (p_g), (p_b), (yield_1),
  *                                          (Norm), (Dipole)
+ *   dipole velocity / acceleration ....... Sec. 4: Eqs. (DipoleVelocity), (DipoleAccel)
+ *   radial flux, PAD, flux yield ......... Sec. 4: Eqs. (flux), (pad), (yield)
  *
  * Conventions
  *   - Atomic units.  Grid r_j = j*dr + offset, j = 1..N; partial waves
@@ -292,7 +296,7 @@ long long tdse_launch_count(const tdse_t *h);
 enum {
   TDSE_K_APPLY_H = 0, TDSE_K_TAYLOR_STAGE, TDSE_K_RK_STAGE, TDSE_K_NORM, TDSE_K_LANCZOS_A,
   TDSE_K_LANCZOS_B, TDSE_K_LANCZOS_EXPM, TDSE_K_LANCZOS_COMBINE, TDSE_K_OBSERVABLES,
-  TDSE_K_COUNT
+  TDSE_K_DIPOLE, TDSE_K_FLUX, TDSE_K_COUNT
 };
 
 /*

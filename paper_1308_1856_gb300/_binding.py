@@ -235,4 +235,4 @@ tdse_server_profile = _fn("tdse_server_profile")
 tdse_server_profile_read = _fn("tdse_server_profile_read")
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
-                "lanczos_expm", "lanczos_combine", "observables"]
+                "lanczos_expm", "lanczos_combine", "observables", "dipole", "flux"]

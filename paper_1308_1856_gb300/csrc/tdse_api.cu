@@ -36,11 +36,12 @@ struct tdse {
   double *rk_sigma = nullptr;      // explicit RK: sum of the steps' error estimates
   // Sec. 4 observables recorded after every real-time step (the step hooks)
   double *dip_out = nullptr;       // one-shot dipole moments (3 doubles)
+  double *dip_partials = nullptr;  // 4 * dipole_blocks doubles, then the arrival ticket
   double *series = nullptr;        // 3 doubles per recorded step: <z>, <zdot>, <zddot>
   long series_cap = 0;
   std::vector<double> series_t;    // the recorded steps' times
   double *flux_state = nullptr;    // see launch_flux; 2 + 2 ntheta doubles
-  double *flux_y = nullptr;        // Y_l0(theta_k), (L+1) x ntheta
+  double *flux_y = nullptr;        // Y_l0(theta_k), angle-major: [k (L+1) + l]
   double *flux_ct = nullptr;       // cos(theta_k)
   int flux_ntheta = 0, flux_ib = -1;
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
@@ -216,6 +217,7 @@ void free_all(tdse *h) {
   cudaFree(h->imag);
   cudaFree(h->rk_sigma);
   cudaFree(h->dip_out);
+  cudaFree(h->dip_partials);
   cudaFree(h->series);
   cudaFree(h->flux_state);
   cudaFree(h->flux_y);
@@ -352,14 +354,20 @@ bool hooks_on(const tdse *h) { return h->series_cap > 0 || h->flux_ib >= 0; }
 // A/c of the velocity gauge at t (0 in the length gauge).
 double ac_at(const tdse *h, double t) { return h->g.gauge == 1 ? coupling_at(h, t) : 0.0; }
 
-unsigned *obs_ticket(tdse *h) {
-  return reinterpret_cast<unsigned *>(h->obs_partials + (size_t)5 * observables_blocks(h->g) * (h->g.L + 1));
-}
-
 int launch_dipole(tdse *h, double t, double *out) {
-  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+  const size_t np = (size_t)4 * dipole_blocks(h->g);
+  if (!h->dip_partials) {
+    if (cudaMalloc(&h->dip_partials, sizeof(double) * (np + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      h->dip_partials = nullptr;
+      return fail(h, TDSE_ERR_OOM, "dipole partials");
+    }
+    TDSE_CUDA(h, cudaMemsetAsync(h->dip_partials + np, 0, sizeof(double), h->stream), "clear dipole ticket");
+  }
+  unsigned *ticket = reinterpret_cast<unsigned *>(h->dip_partials + np);
+  TDSE_LAUNCH(h, TDSE_K_DIPOLE,
               launch_dipole_moments(h->g, view(h), h->psi, h->opts.ghost, field_at(h, t), ac_at(h, t), h->Z,
-                                    h->vtab.empty(), h->obs_partials, obs_ticket(h), out, h->stream),
+                                    h->vtab.empty(), h->dip_partials, ticket, out, h->stream),
               "dipole moments");
   return TDSE_OK;
 }
@@ -373,7 +381,7 @@ int step_hook(tdse *h, double t_new, double dt) {
     h->series_t.push_back(t_new);
   }
   if (h->flux_ib >= 0)
-    TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+    TDSE_LAUNCH(h, TDSE_K_FLUX,
                 launch_flux(h->g, view(h), h->psi, h->opts.ghost, h->flux_ib, ac_at(h, t_new), h->flux_y,
                             h->flux_ct, h->flux_ntheta, dt, false, h->flux_state, h->stream),
                 "flux");
@@ -1191,7 +1199,7 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta) 
         p0 = p1;
         p1 = P;
       }
-      y[(size_t)l * ntheta + k] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * P;
+      y[(size_t)k * (L + 1) + l] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * P;
     }
   }
   const size_t nstate = 2 + 2 * (size_t)ntheta;
@@ -1214,7 +1222,7 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta) 
   h->flux_ib = ib;
   h->flux_ntheta = ntheta;
   // the current state opens the integrals (at zero)
-  TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+  TDSE_LAUNCH(h, TDSE_K_FLUX,
               launch_flux(h->g, view(h), h->psi, h->opts.ghost, ib, ac_at(h, h->t), h->flux_y, h->flux_ct, ntheta,
                           0.0, true, h->flux_state, h->stream),
               "flux");

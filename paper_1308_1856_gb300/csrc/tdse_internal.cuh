@@ -108,13 +108,13 @@ cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, d
 // ---- Sec. 4 dipole moments and flux (tdse_kernels_flux.cu) -------------------
 // out[0..2] = <z>, d<z>/dt, d^2<z>/dt^2 of psi (E the field, ac = A/c in the
 // velocity gauge else 0; the acceleration is NaN unless coulomb).  partials:
-// 4 * dipole_blocks(g) * (L+1) doubles; ticket: zeroed, left zeroed.
+// 4 * dipole_blocks(g) doubles; ticket: zeroed, left zeroed.
 int dipole_blocks(const Geometry &g);
 cudaError_t launch_dipole_moments(const Geometry &g, const OperatorView &op, const double2 *psi,
                                   int ghost, double E, double ac, double Z, bool coulomb,
                                   double *partials, unsigned *ticket, double *out, cudaStream_t st);
 // Flux through r = r_(ib+1) and its angular density at ntheta angles
-// (ytab: Y_l0(theta_k), l-major); state = {flux now, its integral, density now
+// (ytab: Y_l0(theta_k), angle-major: ytab[k (L+1) + l]); state = {flux now, its integral, density now
 // [ntheta], density integral [ntheta]}.  init: set "now" and zero the
 // integrals; else integral += dt/2 (previous now + new now) first.
 size_t flux_shared_bytes(const Geometry &g);
