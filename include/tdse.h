@@ -399,6 +399,23 @@ int tdse_batch_get_states(tdse_batch_t *b, double *F_all_host);
  */
 int tdse_batch_propagate(tdse_batch_t *b, long nsteps);
 
+/*
+ * Copy every state in, advance every instance by nsteps steps and copy every
+ * state out, with the copies overlapping the compute (synchronous).  The
+ * instances are cut into `groups` contiguous groups of about equal points;
+ * group g is propagated once its input copy is done, and its output copy runs
+ * while group g+1 computes, on two extra streams (one per copy direction).
+ * The input copies start once the work already queued on the batch's stream
+ * is done.  F_in / F_out: host buffers laid out as tdse_batch_set_states
+ * (page-locked for the copies to overlap); either may be NULL.  The
+ * result equals tdse_batch_set_states + tdse_batch_propagate +
+ * tdse_batch_get_states bitwise (an instance's arithmetic does not depend on
+ * which instances run with it).  Errors: TDSE_ERR_ARG (nsteps < 0,
+ * groups < 1), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in_host, double *F_out_host, long nsteps,
+                            int groups);
+
 /* Observables of instance i, as tdse_observables (synchronises the stream). */
 int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
                            double *yield, double *p_ground);

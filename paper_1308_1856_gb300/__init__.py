@@ -276,6 +276,13 @@ class Batch:
     def get_states_ptr(self, host_ptr: int):
         self._check(C.tdse_batch_get_states(self.h, ctypes.c_void_p(host_ptr)))
 
+    def propagate_io(self, in_ptr: Optional[int], out_ptr: Optional[int], nsteps: int, groups: int = 4):
+        """States in from / out to host addresses (page-locked for overlap; None
+        skips that direction) around nsteps steps, copies overlapping compute."""
+        self._check(C.tdse_batch_propagate_io(self.h, ctypes.c_void_p(in_ptr) if in_ptr else None,
+                                              ctypes.c_void_p(out_ptr) if out_ptr else None,
+                                              int(nsteps), int(groups)))
+
     def get_states(self):
         """All states as one complex array (instance order, back to back)."""
         out = np.empty(self.points, dtype=np.complex128)

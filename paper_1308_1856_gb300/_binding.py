@@ -104,6 +104,7 @@ SIGNATURES = {
     "tdse_batch_set_states": (_c_int, [_vp, _vp]),
     "tdse_batch_get_states": (_c_int, [_vp, _vp]),
     "tdse_batch_propagate": (_c_int, [_vp, _c_long]),
+    "tdse_batch_propagate_io": (_c_int, [_vp, _vp, _vp, _c_long, _c_int]),
     "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
     "tdse_batch_points": (ctypes.c_longlong, [_vp]),
     "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
@@ -207,6 +208,7 @@ tdse_batch_get_time = _fn("tdse_batch_get_time")
 tdse_batch_set_states = _fn("tdse_batch_set_states")
 tdse_batch_get_states = _fn("tdse_batch_get_states")
 tdse_batch_propagate = _fn("tdse_batch_propagate")
+tdse_batch_propagate_io = _fn("tdse_batch_propagate_io")
 tdse_batch_observables = _fn("tdse_batch_observables")
 tdse_batch_points = _fn("tdse_batch_points")
 tdse_batch_launch_count = _fn("tdse_batch_launch_count")

@@ -1525,11 +1525,47 @@ struct tdse_batch {
   int count = 0;
   void *mem = nullptr;
   long long npts = 0;
+  // pipelined host I/O (tdse_batch_propagate_io): one stream per copy direction
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  std::vector<cudaEvent_t> ev;
   ~tdse_batch() {
     if (eng.stream) cudaStreamSynchronize(eng.stream);
+    if (io_in) cudaStreamSynchronize(io_in);
+    if (io_out) cudaStreamSynchronize(io_out);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (io_in) cudaStreamDestroy(io_in);
+    if (io_out) cudaStreamDestroy(io_out);
     cudaFree(mem);
   }
 };
+
+namespace {
+
+// Streams and 2 * groups + 1 events of the pipelined I/O, created once.
+int io_ready(tdse_batch *b, int groups) {
+  Engine &e = b->eng;
+  if (!b->io_in && cudaStreamCreateWithFlags(&b->io_in, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->io_in = nullptr;
+    return e.fail(TDSE_ERR_CUDA, "I/O stream");
+  }
+  if (!b->io_out && cudaStreamCreateWithFlags(&b->io_out, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->io_out = nullptr;
+    return e.fail(TDSE_ERR_CUDA, "I/O stream");
+  }
+  while ((int)b->ev.size() < 2 * groups + 1) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return e.fail(TDSE_ERR_CUDA, "I/O events");
+    }
+    b->ev.push_back(ev);
+  }
+  return TDSE_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1618,6 +1654,64 @@ int tdse_batch_propagate(tdse_batch_t *b, long nsteps) {
   std::vector<int> slots(b->count);
   for (int i = 0; i < b->count; ++i) slots[i] = i;
   return b->eng.run(slots, std::vector<long>(b->count, nsteps));
+}
+
+int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, long nsteps, int groups) {
+  if (!b) return TDSE_ERR_ARG;
+  Engine &e = b->eng;
+  if (e.poisoned) return TDSE_ERR_STATE;
+  if (nsteps < 0 || groups < 1) return e.fail(TDSE_ERR_ARG, "need nsteps >= 0 and groups >= 1");
+  if (groups > b->count) groups = b->count;
+  int rc = io_ready(b, groups);
+  if (rc) return rc;
+  // contiguous groups of about equal points; each instance's offset in the host buffers
+  std::vector<size_t> off(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) off[i + 1] = off[i] + 2 * (size_t)e.hinst[i].N * (e.hinst[i].L + 1);
+  std::vector<int> first(groups + 1, b->count);
+  first[0] = 0;
+  for (int g = 1, i = 0; g < groups; ++g) {
+    const size_t target = off[b->count] / groups * g;
+    while (i < b->count && off[i] < target) ++i;
+    first[g] = std::max(i, first[g - 1] + 1 <= b->count ? first[g - 1] + 1 : b->count);
+  }
+  auto bytes = [&](int i) { return sizeof(double) * (off[i + 1] - off[i]); };
+  // every input copy first, in group order on the input stream, after the
+  // work already queued on the compute stream (it may still write the states)
+  if (F_in) {
+    if (cudaEventRecord(b->ev[2 * groups], e.stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->io_in, b->ev[2 * groups], 0) != cudaSuccess)
+      return e.fail(TDSE_ERR_CUDA, "order input copies");
+    for (int g = 0; g < groups; ++g) {
+      for (int i = first[g]; i < first[g + 1]; ++i) {
+        if (cudaMemcpyAsync(e.hinst[i].psi, F_in + off[i], bytes(i), cudaMemcpyHostToDevice, b->io_in) != cudaSuccess)
+          return e.fail(TDSE_ERR_CUDA, "input copy");
+        e.norm_valid[i] = 0;
+      }
+      if (cudaEventRecord(b->ev[2 * g], b->io_in) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "input event");
+    }
+  }
+  // group g computes once its input is in; its output copy waits for it and
+  // overlaps the next group's compute
+  for (int g = 0; g < groups; ++g) {
+    if (F_in && cudaStreamWaitEvent(e.stream, b->ev[2 * g], 0) != cudaSuccess)
+      return e.fail(TDSE_ERR_CUDA, "wait input");
+    std::vector<int> slots;
+    for (int i = first[g]; i < first[g + 1]; ++i) slots.push_back(i);
+    rc = e.run(slots, std::vector<long>(slots.size(), nsteps));
+    if (rc) return rc;
+    if (F_out) {
+      if (cudaEventRecord(b->ev[2 * g + 1], e.stream) != cudaSuccess ||
+          cudaStreamWaitEvent(b->io_out, b->ev[2 * g + 1], 0) != cudaSuccess)
+        return e.fail(TDSE_ERR_CUDA, "output event");
+      for (int i = first[g]; i < first[g + 1]; ++i)
+        if (cudaMemcpyAsync(F_out + off[i], e.hinst[i].psi, bytes(i), cudaMemcpyDeviceToHost, b->io_out) != cudaSuccess)
+          return e.fail(TDSE_ERR_CUDA, "output copy");
+    }
+  }
+  if (cudaStreamSynchronize(b->io_in) != cudaSuccess || cudaStreamSynchronize(e.stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->io_out) != cudaSuccess)
+    return e.fail(TDSE_ERR_CUDA, "sync I/O");
+  return TDSE_OK;
 }
 
 int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
