@@ -476,6 +476,40 @@ def run_step_observables(stream_ptr, psi0, steps=5, warmup=3, ntheta=180, r_b=10
     return out
 
 
+def run_small_config(stream_ptr, nsteps=200, reps=3):
+    """The small configuration (N=500, dr=0.2, lmax=4, 3-point; 2,500 grid
+    points), where a step is a few microseconds of arithmetic and the launch
+    and grid-reduction latency decide: us per step of each FP64 propagator,
+    nsteps steps per call (one call timed by CUDA events, best of reps, L2
+    flushed before each)."""
+    import torch
+    from paper_1308_1856_gb300 import TDSE
+    c = W.SMALL
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    psi0 = W.hydrogen_1s(c.N, c.dr, c.lmax)
+    out = {"workload": f"small configuration N={c.N} dr={c.dr} lmax={c.lmax} {c.stencil}-point, FP64, "
+                       f"{nsteps} steps per timed call, best of {reps}"}
+    for method, order, dt in (("taylor", 8, 0.01), ("rk4", 4, 0.01), ("lanczos", 12, 0.05)):
+        t = TDSE(c.N, c.dr, c.lmax, stencil=c.stencil)
+        t.set_pulse(c.E0, c.omega, c.ncycles)
+        t.set_stream(stream_ptr)
+        t.set_state(psi0)
+        t.propagate(method, order, dt, 20)
+        best = float("inf")
+        for k in range(reps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t.propagate(method, order, dt, nsteps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        t.close()
+        out[f"{method}-{order}"] = {"us_per_step": 1e3 * best / nsteps, "gp_steps_per_s": c.G * nsteps / (best * 1e-3)}
+    return out
+
+
 def mixed_error(stream_ptr, psi0, nsteps=10):
     """The mixed-precision path's error against the FP64 path on the at-scale
     grid: Lanczos-12 from the benchmark's start state, at a step where the
@@ -517,6 +551,8 @@ def run_ours(args, ws, rank, local):
     if args.rows == "rk":
         return {"metric": METRIC, "rk_pairs": run_rk_pairs(stream.cuda_stream, psi0, steps=args.steps,
                                                            warmup=args.warmup)}
+    if args.rows == "small":
+        return {"metric": METRIC, "small_config": run_small_config(stream.cuda_stream)}
     if args.rows == "obs":
         return {"metric": METRIC, "step_observables": run_step_observables(stream.cuda_stream, psi0,
                                                                            steps=args.steps, warmup=args.warmup)}
@@ -677,6 +713,7 @@ def run_ours(args, ws, rank, local):
         result["mixed_error"] = mixed_error(stream.cuda_stream, psi0)
         result["rk_pairs"] = run_rk_pairs(stream.cuda_stream, psi0)
         result["step_observables"] = run_step_observables(stream.cuda_stream, psi0)
+        result["small_config"] = run_small_config(stream.cuda_stream)
     if args.rows == "all" and not args.no_serve:
         result["served"] = run_served(args, stream.cuda_stream)
     return result
@@ -746,8 +783,9 @@ def main():
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
                     help="restrict to one precision (profiling runs)")
-    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served", "rk", "obs"],
-                    help="restrict to the single-instance, batched, served, embedded-RK or step-observable rows")
+    ap.add_argument("--rows", default="all", choices=["all", "single", "batched", "served", "rk", "obs", "small"],
+                    help="restrict to one group of rows (single-instance, batched, served, embedded RK, "
+                         "step observables, small configuration)")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched rows (smaller only for profiling captures)")
     ap.add_argument("--schedule", action="append", default=[], metavar="PREC=PF,RING,SB,EB",

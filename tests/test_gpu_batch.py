@@ -193,3 +193,51 @@ def test_batch_propagate_io_equals_the_separate_calls(precision, groups, nsteps)
     with pytest.raises(Exception):
         b.propagate_io(None, None, 1, 0)
     b.close()
+
+
+def _full_batched_specs():
+    """The batched configuration as the benchmark runs it: 256 instances of
+    batched_specs(256, 1308), dt = 0.02, the cos^(1/8) mask over the last 50 a.u."""
+    return [dict(N=x.N, dr=x.dr, lmax=x.lmax, krylov=x.krylov, dt=0.02, E0=x.E0, omega=x.omega,
+                 ncycles=x.ncycles, absorber_r=x.N * x.dr - 50.0) for x in W.batched_specs(256, 1308)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_batched_configuration_sampled(precision):
+    """The full batched configuration (256 instances, 1.65e8 grid points) in the
+    benchmark's launch configuration (autotuned schedule, one step per call):
+    four sampled instances (the smallest, the largest and two others) start
+    from smooth random states, the rest from the 1s state, and every instance
+    takes one step.  Each sampled instance matches the oracle: FP64 within
+    1e-12 of the FP64 oracle, or, where the step amplifies rounding beyond
+    that, within 10 x the oracle's own f64-vs-long-double floor of the
+    long-double oracle; mixed within 1e-6 of the FP64 oracle (one mixed step
+    on the at-scale grid stays below 1e-7)."""
+    from paper_1308_1856_gb300 import Batch
+    d = _full_batched_specs()
+    G = [s["N"] * (s["lmax"] + 1) for s in d]
+    sample = sorted({int(np.argmin(G)), int(np.argmax(G)), 17, 200})
+    b = Batch(d, stencil=5, precision=precision)
+    b.autotune()
+    start = {}
+    for i in sample:
+        s = d[i]
+        start[i] = W.smooth_state(s["N"], s["dr"], s["lmax"], seed=i, lmax_populated=20)
+        b.set_state(i, start[i])
+    b.propagate(1)
+    got = {i: b.get_state(i) for i in sample}
+    b.close()
+    for i in sample:
+        s = d[i]
+        g = oracle.Grid(N=s["N"], h=s["dr"], L=s["lmax"], stencil=5)
+        pulse = oracle.Pulse(E0=s["E0"], omega=s["omega"], ncycles=s["ncycles"])
+        mask = oracle.Mask(s["absorber_r"])
+        f64, _ = oracle.propagate(g, start[i], "lanczos", s["krylov"], s["dt"], 1, pulse=pulse, mask=mask)
+        err = rel_l2(got[i], f64)
+        if precision == "mixed":
+            assert err <= 1e-6, (i, err)
+        elif err > 1e-12:
+            fld, _ = oracle.propagate(g, start[i], "lanczos", s["krylov"], s["dt"], 1, pulse=pulse, mask=mask,
+                                      precision="fld")
+            floor = rel_l2(f64, fld)
+            assert rel_l2(got[i], fld) <= 10 * max(floor, 1e-15), (i, err, rel_l2(got[i], fld), floor)
