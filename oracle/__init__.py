@@ -34,7 +34,7 @@ class _Grid(ctypes.Structure):
 
 class _Pulse(ctypes.Structure):
     _fields_ = [("E0", ctypes.c_double), ("omega", ctypes.c_double),
-                ("ncycles", ctypes.c_double), ("cep", ctypes.c_double)]
+                ("ncycles", ctypes.c_double), ("cep", ctypes.c_double), ("shape", ctypes.c_int)]
 
 
 class _Mask(ctypes.Structure):
@@ -69,17 +69,19 @@ class Grid:
 
 @dataclass
 class Pulse:
-    """E(t) = E0 sin^2(pi t / T) sin(omega t + cep), T = 2 pi ncycles / omega."""
+    """shape 0: E(t) = E0 sin^2(pi t / T) sin(omega t + cep), T = 2 pi ncycles / omega;
+    shape 1 ("SineA"): A(t) = -(c E0 / omega) sin^2(pi t / T) sin(omega t + cep), E = -(1/c) dA/dt."""
     E0: float = 0.0
     omega: float = 0.057
     ncycles: float = 2.0
     cep: float = 0.0
+    shape: int = 0
 
     def duration(self) -> float:
         return 2.0 * math.pi * self.ncycles / self.omega
 
     def _c(self):
-        return _Pulse(self.E0, self.omega, self.ncycles, self.cep)
+        return _Pulse(self.E0, self.omega, self.ncycles, self.cep, self.shape)
 
 
 @dataclass

@@ -20,7 +20,7 @@
  *                                            difference formulas, (h_matrix)
  *   box boundary (zero beyond the box) ..... Sec. 2.1 first paragraph
  *   absorber (applied as a per-step mask) .. Sec. 2.1
- *   sin^2 pulse ............................ Sec. 3, Eq. (EField)
+ *   sin^2 pulse (on E, or on A "SineA") .... Sec. 3, Eqs. (EField), (VecSinSinCosE)
  *   Taylor propagator ...................... Sec. 5 "Taylor.c", Eq. (Taylor)
  *   Runge-Kutta (classic RK4) .............. Sec. 5 "RungeKutta.c", Eq. (RKDeriv)
  *   Lanczos propagator ..................... Sec. 5 "Lanczos.c", Appendix
@@ -116,6 +116,7 @@ typedef struct {
   double omega;        /* carrier frequency (a.u.)                            */
   double ncycles;      /* number of carrier cycles under the envelope         */
   double cep;          /* carrier phase                                       */
+  int shape;           /* 0: sin^2 envelope on E; 1: sin^2 envelope on A      */
 } orc_pulse;
 
 typedef struct {
@@ -229,13 +230,25 @@ static void apply_H(const orc_grid *g, REAL E, const cplx *x, cplx *y) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Pulse, Sec. 3 Eq. (EField) with the Hann (sin^2) envelope.                */
+/* Pulse, Sec. 3.  Shape 0: Eq. (EField) with the Hann (sin^2) envelope on E. */
+/* Shape 1 ("SineA"): the Hann envelope on A, Eq. (VecSinSinCosE):            */
+/*   A(t) = -(c E0 / omega) sin^2(W t) sin(omega t + cep),  W = omega/(2 n_c), */
+/*   E(t) = -(1/c) dA/dt                                                      */
+/*        = (E0/omega) sin(W t) [omega sin(W t) cos(omega t + cep)            */
+/*                               + 2 W cos(W t) sin(omega t + cep)].          */
+/* Reading: E0 is the peak field in both shapes (the printed Eq.              */
+/* (VecSinSinCosE) multiplies the bracket by E0, which makes omega E0 the     */
+/* peak); A then follows from A = -c int E, the convention of Eq. (VectorStep).*/
 /* ------------------------------------------------------------------------ */
 double orc_field(const orc_pulse *p, double t) {
   if (p->E0 == 0.0 || p->omega <= 0.0) return 0.0;
   const double T = 2.0 * M_PI * p->ncycles / p->omega;
   if (t < 0.0 || t > T) return 0.0;
   const double env = sin(M_PI * t / T);
+  if (p->shape == 1) {
+    const double W = M_PI / T, ph = p->omega * t + p->cep;
+    return p->E0 / p->omega * env * (p->omega * env * cos(ph) + 2.0 * W * cos(M_PI * t / T) * sin(ph));
+  }
   return p->E0 * env * env * sin(p->omega * t + p->cep);
 }
 

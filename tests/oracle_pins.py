@@ -45,7 +45,12 @@ Pins used (arXiv 1308.1856 passages in brackets):
     that times |sum c_l Y_l0|^2 (scipy's spherical harmonics); Gauss-Legendre
     quadrature of the angular density gives the total in both gauges;
     continuity: d/dt of the population inside r_b is minus the flux, and the
-    time-integrated flux is the population that crossed r_b.
+    time-integrated flux is the population that crossed r_b;
+  * the "SineA" pulse [Sec. 3, Eq. (VecSinSinCosE)]: the 5-point Gauss
+    quadrature of E reproduces the closed-form A(t) = -(c E0/omega)
+    sin^2(pi t/T) sin(omega t + cep) (the comparison of the paper's
+    vector-potential figure), E vanishes at both ends, and the peak field is
+    E0 for a many-cycle pulse.
 """
 from __future__ import annotations
 
@@ -661,6 +666,24 @@ def check_flux_continuity(prec="f64"):
     assert integral >= 0.2 and abs(integral - (after - before)) <= 1e-3 * integral, (integral, after - before)
 
 
+def check_sinea_pulse(prec="f64"):
+    c = 137.035999084
+    for ncyc, cep in ((10, 0.0), (3, 0.7)):
+        p = Pulse(E0=0.1688, omega=0.5512, ncycles=ncyc, cep=cep, shape=1)
+        T = p.duration()
+        ts = np.linspace(0.0, 1.05 * T, 701)
+        A = np.array([oracle.vecpot(p, t, prec) for t in ts])
+        tt = np.minimum(ts, T)
+        exact = -(c * p.E0 / p.omega) * np.sin(np.pi * tt / T) ** 2 * np.sin(p.omega * tt + p.cep)
+        assert np.abs(A - exact).max() <= 1e-12 * np.abs(exact).max(), np.abs(A - exact).max()
+        assert oracle.field(p, 0.0, prec) == 0.0 and abs(oracle.field(p, T, prec)) <= 1e-12
+        assert oracle.field(p, -1.0, prec) == 0.0 and oracle.field(p, T + 1.0, prec) == 0.0
+    p = Pulse(E0=0.1688, omega=0.5512, ncycles=10, shape=1)
+    ts = np.linspace(0.0, p.duration(), 20001)
+    peak = max(abs(oracle.field(p, t, prec)) for t in ts)
+    assert abs(peak - p.E0) <= 0.01 * p.E0, peak
+
+
 ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_hydrogen_paper_values, check_hydrogen_convergence,
               check_field_free_eigenstate, check_dense_expm, check_time_order,
@@ -669,4 +692,4 @@ ALL_CHECKS = [check_symmetric, check_coupling_blocks, check_stencil_polynomials,
               check_velocity_gauge_operator, check_vector_potential, check_gauge_invariance,
               check_rk_orders, check_rk_dormand_prince_step, check_rk_error_estimate,
               check_dipole_ehrenfest, check_flux_closed_form, check_flux_angular_integral,
-              check_flux_continuity]
+              check_flux_continuity, check_sinea_pulse]

@@ -95,6 +95,10 @@ MUTANTS = [
     ("legendre_recurrence", "((REAL)(2 * l + 1) * x * pl - (REAL)l * pm)", "((REAL)(2 * l + 1) * x * pl - (REAL)(l + 1) * pm)",
      P.check_flux_closed_form),
     ("flux_radius_off_by_one", "return best;", "return best + 1;", P.check_flux_continuity),
+    ("sinea_missing_envelope_term", "+ 2.0 * W * cos(M_PI * t / T) * sin(ph)", "+ 0.0 * W * cos(M_PI * t / T) * sin(ph)",
+     P.check_sinea_pulse),
+    ("sinea_envelope_frequency", "const double W = M_PI / T,", "const double W = 2.0 * M_PI / T,",
+     P.check_sinea_pulse),
 ]
 
 
