@@ -125,8 +125,25 @@ int tdse_set_stream(tdse_t *h, void *cuda_stream);
  */
 int tdse_set_pulse(tdse_t *h, double E0, double omega, double ncycles, double cep);
 
+/*
+ * Envelope of the pulse (Sec. 3).  TDSE_PULSE_SIN2_E (default): the sin^2
+ * envelope on E as above.  TDSE_PULSE_SIN2_A ("SineA", Eq. (VecSinSinCosE)):
+ * the sin^2 envelope on the vector potential,
+ *   A(t) = -(c E0/omega) sin^2(pi t/T) sin(omega t + cep),
+ *   E(t) = -(1/c) dA/dt = (E0/omega) sin(W t) [omega sin(W t) cos(omega t + cep)
+ *                                              + 2 W cos(W t) sin(omega t + cep)],
+ * W = pi/T = omega/(2 ncycles), 0 <= t <= T, zero elsewhere; E0 is the peak
+ * field of a many-cycle pulse in both shapes.  Errors: TDSE_ERR_ARG (unknown
+ * shape).
+ */
+enum { TDSE_PULSE_SIN2_E = 0, TDSE_PULSE_SIN2_A = 1 };
+int tdse_set_pulse_shape(tdse_t *h, int shape);
+
 /* Evaluate the pulse set by tdse_set_pulse at time t (host arithmetic). */
 double tdse_field(const tdse_t *h, double t);
+/* A(t) = -c int_0^t E, by 5-point Gauss quadrature on equal panels of [0, T]
+ * no wider than 0.25 a.u. (Sec. 3, Eq. (VectorStep)); constant after T. */
+double tdse_vector_potential(const tdse_t *h, double t);
 
 /* Current time of the state; tdse_propagate advances it by nsteps * dt. */
 int tdse_set_time(tdse_t *h, double t);

@@ -76,11 +76,16 @@ class TDSE:
     def set_stream(self, stream_ptr: int):
         self._check(C.tdse_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)))
 
-    def set_pulse(self, E0, omega, ncycles, cep=0.0):
+    def set_pulse(self, E0, omega, ncycles, cep=0.0, shape: str = "sin2_e"):
+        """sin^2 envelope on E ("sin2_e") or on the vector potential ("sin2_a", the paper's SineA)."""
         self._check(C.tdse_set_pulse(self.h, float(E0), float(omega), float(ncycles), float(cep)))
+        self._check(C.tdse_set_pulse_shape(self.h, {"sin2_e": C.TDSE_PULSE_SIN2_E, "sin2_a": C.TDSE_PULSE_SIN2_A}[shape]))
 
     def field(self, t: float) -> float:
         return C.tdse_field(self.h, float(t))
+
+    def vector_potential(self, t: float) -> float:
+        return C.tdse_vector_potential(self.h, float(t))
 
     @property
     def time(self) -> float:

@@ -24,6 +24,7 @@ TDSE_FP64, TDSE_MIXED = 0, 1
 (TDSE_RK_EULER, TDSE_RK_CLASSIC, TDSE_RK_FEHLBERG, TDSE_RK_CASH_KARP, TDSE_RK_DORMAND_PRINCE,
  TDSE_RK_MERSON) = range(6)
 TDSE_GAUGE_LENGTH, TDSE_GAUGE_VELOCITY = 0, 1
+TDSE_PULSE_SIN2_E, TDSE_PULSE_SIN2_A = 0, 1
 TDSE_MAX_KRYLOV = 32
 
 # Every symbol include/tdse.h declares: name -> (restype, argtypes)
@@ -70,6 +71,8 @@ SIGNATURES = {
     "tdse_set_stream": (_c_int, [_vp, _vp]),
     "tdse_set_pulse": (_c_int, [_vp, _c_double, _c_double, _c_double, _c_double]),
     "tdse_field": (_c_double, [_vp, _c_double]),
+    "tdse_vector_potential": (_c_double, [_vp, _c_double]),
+    "tdse_set_pulse_shape": (_c_int, [_vp, _c_int]),
     "tdse_set_time": (_c_int, [_vp, _c_double]),
     "tdse_get_time": (_c_double, [_vp]),
     "tdse_set_state": (_c_int, [_vp, _vp]),
@@ -175,6 +178,8 @@ tdse_set_options = _fn("tdse_set_options")
 tdse_set_stream = _fn("tdse_set_stream")
 tdse_set_pulse = _fn("tdse_set_pulse")
 tdse_field = _fn("tdse_field")
+tdse_vector_potential = _fn("tdse_vector_potential")
+tdse_set_pulse_shape = _fn("tdse_set_pulse_shape")
 tdse_set_time = _fn("tdse_set_time")
 tdse_get_time = _fn("tdse_get_time")
 tdse_set_state = _fn("tdse_set_state")

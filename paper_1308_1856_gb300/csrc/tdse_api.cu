@@ -20,6 +20,7 @@ struct tdse {
   std::vector<double> vtab;   // empty: -Z/r
   tdse_opts opts;
   double E0 = 0.0, omega = 0.0, ncycles = 0.0, cep = 0.0;
+  int pulse_shape = TDSE_PULSE_SIN2_E;
   double t = 0.0;
   cudaStream_t own_stream = nullptr, stream = nullptr;
   // device memory
@@ -255,6 +256,11 @@ double field_at(const tdse *h, double t) {
   const double T = 2.0 * M_PI * h->ncycles / h->omega;
   if (t < 0.0 || t > T) return 0.0;
   const double env = std::sin(M_PI * t / T);
+  if (h->pulse_shape == TDSE_PULSE_SIN2_A) {
+    // A = -(c E0/omega) sin^2(W t) sin(omega t + cep), W = pi/T; E = -(1/c) dA/dt
+    const double W = M_PI / T, ph = h->omega * t + h->cep;
+    return h->E0 / h->omega * env * (h->omega * env * std::cos(ph) + 2.0 * W * std::cos(W * t) * std::sin(ph));
+  }
   return h->E0 * env * env * std::sin(h->omega * t + h->cep);
 }
 
@@ -927,7 +933,17 @@ int tdse_set_pulse(tdse_t *h, double E0, double omega, double ncycles, double ce
   return TDSE_OK;
 }
 
+int tdse_set_pulse_shape(tdse_t *h, int shape) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (shape != TDSE_PULSE_SIN2_E && shape != TDSE_PULSE_SIN2_A) return fail(h, TDSE_ERR_ARG, "unknown pulse shape");
+  h->pulse_shape = shape;
+  return TDSE_OK;
+}
+
 double tdse_field(const tdse_t *h, double t) { return h ? field_at(h, t) : 0.0; }
+
+double tdse_vector_potential(const tdse_t *h, double t) { return h ? vecpot_at(h, t) : 0.0; }
 
 int tdse_set_time(tdse_t *h, double t) {
   int rc = check_usable(h);

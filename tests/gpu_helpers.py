@@ -18,7 +18,8 @@ def make(N, dr, L, stencil, *, ghost=0, offset=0.0, Z=1.0, vtable=None, pulse=No
     t.set_options(ghost=ghost, offset=offset, absorber=absorber_r is not None,
                   absorber_r=absorber_r or 0.0, r_b=r_b, gauge=gauge)
     if pulse is not None:
-        t.set_pulse(pulse.E0, pulse.omega, pulse.ncycles, pulse.cep)
+        t.set_pulse(pulse.E0, pulse.omega, pulse.ncycles, pulse.cep,
+                    shape="sin2_a" if getattr(pulse, "shape", 0) == 1 else "sin2_e")
     return t
 
 

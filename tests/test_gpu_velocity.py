@@ -84,3 +84,35 @@ def test_velocity_arguments():
         t.set_options(gauge="velocity", ghost=1)
     t.set_options(gauge="velocity")
     t.close()
+
+
+def test_sinea_pulse_field_and_vector_potential_match_the_oracle():
+    """The host's E(t) and A(t) of the sin^2-on-A pulse ("SineA", Eq.
+    (VecSinSinCosE)) equal the oracle's (independent code, both FP64 on the
+    host) to rounding over the whole pulse and after it."""
+    pulse = oracle.Pulse(E0=0.1688, omega=0.5512, ncycles=10, cep=0.3, shape=1)
+    t = make(20, 0.2, 1, 5, pulse=pulse)
+    T = pulse.duration()
+    for s in np.linspace(-1.0, T + 3.0, 257):
+        e, a = t.field(s), t.vector_potential(s)
+        assert abs(e - oracle.field(pulse, s)) <= 1e-15 * max(1.0, abs(e)), s
+        assert abs(a - oracle.vecpot(pulse, s)) <= 1e-12 * max(1.0, abs(a)), s
+    t.close()
+
+
+@pytest.mark.parametrize("gauge", ["length", "velocity"])
+@pytest.mark.parametrize("method,order,dt", [("lanczos", 12, 0.02), ("taylor", 8, 0.005), ("rk4", 4, 0.005)])
+def test_sinea_steps_vs_oracle(gauge, method, order, dt):
+    """Ten steps under the SineA pulse from mid-pulse on a ragged grid."""
+    N, dr, L = 517, 0.2, 7
+    pulse = oracle.Pulse(E0=0.1688, omega=0.5512, ncycles=4, shape=1)
+    psi = W.smooth_state(N, dr, L, seed=11)
+    t = make(N, dr, L, 5, pulse=pulse, gauge=gauge)
+    t.set_state(psi)
+    t.time = 0.4 * pulse.duration()
+    t.propagate(method, order, dt, 10)
+    got = t.get_state()
+    t.close()
+    g = grid_of(N, dr, L, 5, gauge=1 if gauge == "velocity" else 0)
+    want, _ = oracle.propagate(g, psi, method, order, dt, 10, t0=0.4 * pulse.duration(), pulse=pulse)
+    assert rel_l2(got, want) <= 1e-11, rel_l2(got, want)
