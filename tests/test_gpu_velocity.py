@@ -49,9 +49,14 @@ def test_velocity_one_step(method, order, dt, geom):
 
 
 def test_velocity_full_pulse_and_gauge_invariance():
-    """A one-cycle pulse on a small grid from the imaginary-time ground state:
-    the velocity-gauge run matches the oracle over all steps, and after the
-    pulse its populations match the GPU's length-gauge run to the step error."""
+    """A one-cycle pulse on a small grid from the imaginary-time ground state
+    (5027 Lanczos-10 steps): the velocity-gauge run matches the oracle, and
+    after the pulse its populations match the GPU's length-gauge run to the
+    step error.  Over this many steps an FP64 result depends on the order of
+    its sums at the 1e-10 level: the oracle's own distance to its long-double
+    build is 2e-11, and GPU builds that associate differently (the reduction
+    tree follows the SM count) have landed between 5e-11 and 2e-10 from it.
+    The state is held to 1e-9, the populations to 1e-10."""
     N, dr, L = 300, 0.1, 6
     pulse = oracle.Pulse(E0=0.05, omega=0.25, ncycles=1)
     dt = 0.005
@@ -67,8 +72,11 @@ def test_velocity_full_pulse_and_gauge_invariance():
         out[gauge] = (t.get_state(), t.observables())
         t.close()
     got, ob = out["velocity"]
-    want, _ = oracle.propagate(grid_of(N, dr, L, 5, gauge=1), psi0, "lanczos", 10, dt, n, pulse=pulse)
-    assert rel_l2(got, want) <= 1e-10, rel_l2(got, want)
+    g = grid_of(N, dr, L, 5, gauge=1)
+    want, _ = oracle.propagate(g, psi0, "lanczos", 10, dt, n, pulse=pulse)
+    assert rel_l2(got, want) <= 1e-9, rel_l2(got, want)
+    ow = oracle.observables(g, want, psi0[0], r_b=10.0)
+    assert abs(ob["p_ground"] - ow["p_ground"]) <= 1e-10 and np.abs(ob["l_pop"] - ow["l_pop"]).max() <= 1e-10
     ol = out["length"][1]
     assert abs(ob["p_ground"] - ol["p_ground"]) <= 1e-4, (ob["p_ground"], ol["p_ground"])
     assert np.abs(ob["l_pop"] - ol["l_pop"]).max() <= 1e-4
@@ -95,7 +103,8 @@ def test_sinea_pulse_field_and_vector_potential_match_the_oracle():
     T = pulse.duration()
     for s in np.linspace(-1.0, T + 3.0, 257):
         e, a = t.field(s), t.vector_potential(s)
-        assert abs(e - oracle.field(pulse, s)) <= 1e-15 * max(1.0, abs(e)), s
+        # the same formula in independent code: a few unit roundoffs of the carrier terms
+        assert abs(e - oracle.field(pulse, s)) <= 1e-14, s
         assert abs(a - oracle.vecpot(pulse, s)) <= 1e-12 * max(1.0, abs(a)), s
     t.close()
 
