@@ -44,6 +44,8 @@
 #ifndef TDSE_H
 #define TDSE_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -234,6 +236,22 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta);
  * time integrals; any pointer may be NULL (density and pad hold ntheta
  * values).  TDSE_ERR_ARG if the flux is not set up.  Synchronises. */
 int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, double *pad);
+
+/*
+ * Checkpoint and resume.  A checkpoint holds the state, the time, the cached
+ * norm the next Lanczos step starts from and, if the flux is set up, its
+ * current values and time integrals: loading it into a handle of the same
+ * grid, stencil, ghost, offset, gauge, precision and flux setup and
+ * propagating gives bitwise the states of the uninterrupted run.  (Loading
+ * into a handle of the other precision works but recomputes the norm.)
+ * tdse_checkpoint_bytes: size of the host buffer.  save: synchronous copy to
+ * host memory.  load: TDSE_ERR_ARG if the buffer is not a checkpoint, is too
+ * small, or was taken on another grid, ghost, offset, gauge or flux setup.
+ * The pulse, options and dipole series are the handle's, not the checkpoint's.
+ */
+size_t tdse_checkpoint_bytes(const tdse_t *h);
+int tdse_checkpoint_save(tdse_t *h, void *buf, size_t bytes);
+int tdse_checkpoint_load(tdse_t *h, const void *buf, size_t bytes);
 
 /* Explicit Runge-Kutta methods of the appendix "Runge-Kutta". */
 enum {

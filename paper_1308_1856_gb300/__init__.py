@@ -176,6 +176,17 @@ class TDSE:
                                      pad.ctypes.data_as(C._dp)))
         return {"flux": f.value, "yield": y.value, "density": dens[:nt], "pad": pad[:nt]}
 
+    def checkpoint(self) -> bytes:
+        """State, time, cached norm and flux integrals, for a bitwise resume."""
+        n = C.tdse_checkpoint_bytes(self.h)
+        buf = ctypes.create_string_buffer(n)
+        self._check(C.tdse_checkpoint_save(self.h, buf, n))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        self._check(C.tdse_checkpoint_load(self.h, buf, len(blob)))
+
     def observables(self) -> dict:
         norm, dip, yld, pg = (ctypes.c_double() for _ in range(4))
         lp = np.zeros(self.lmax + 1)

@@ -87,6 +87,9 @@ SIGNATURES = {
     "tdse_dipole_series": (_c_int, [_vp, _c_long]),
     "tdse_dipole_series_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
     "tdse_flux_setup": (_c_int, [_vp, _c_double, _c_int, _dp]),
+    "tdse_checkpoint_bytes": (ctypes.c_size_t, [_vp]),
+    "tdse_checkpoint_save": (_c_int, [_vp, _vp, ctypes.c_size_t]),
+    "tdse_checkpoint_load": (_c_int, [_vp, _vp, ctypes.c_size_t]),
     "tdse_flux_read": (_c_int, [_vp, _dp, _dp, _dp, _dp]),
     "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
@@ -194,6 +197,9 @@ tdse_dipole_moments = _fn("tdse_dipole_moments")
 tdse_dipole_series = _fn("tdse_dipole_series")
 tdse_dipole_series_read = _fn("tdse_dipole_series_read")
 tdse_flux_setup = _fn("tdse_flux_setup")
+tdse_checkpoint_bytes = _fn("tdse_checkpoint_bytes")
+tdse_checkpoint_save = _fn("tdse_checkpoint_save")
+tdse_checkpoint_load = _fn("tdse_checkpoint_load")
 tdse_flux_read = _fn("tdse_flux_read")
 tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")

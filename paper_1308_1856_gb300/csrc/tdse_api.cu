@@ -1005,6 +1005,7 @@ int tdse_set_reference(tdse_t *h, const double *f0) {
 }
 
 int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
+  TraceRange trace("tdse_propagate");
   int rc = check_usable(h);
   if (rc) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
@@ -1061,6 +1062,7 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
 }
 
 int tdse_propagate_rk(tdse_t *h, int tableau, double dt, long nsteps, double *sigma) {
+  TraceRange trace("tdse_propagate_rk");
   int rc = check_usable(h);
   if (rc) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
@@ -1078,6 +1080,7 @@ int tdse_propagate_rk(tdse_t *h, int tableau, double dt, long nsteps, double *si
 }
 
 int tdse_propagate_imag(tdse_t *h, int method, int order, double dtau, long nsteps, double *energy) {
+  TraceRange trace("tdse_propagate_imag");
   int rc = check_usable(h);
   if (rc) return rc;
   if (!(dtau > 0.0) || !std::isfinite(dtau) || nsteps < 0)
@@ -1259,6 +1262,117 @@ int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, doub
   if (yield) *yield = v[1];
   if (density && nt) std::memcpy(density, v.data() + 2, sizeof(double) * nt);
   if (pad && nt) std::memcpy(pad, v.data() + 2 + nt, sizeof(double) * nt);
+  return TDSE_OK;
+}
+
+// ---- checkpoint / resume -----------------------------------------------------
+namespace {
+
+struct CheckpointHeader {
+  char magic[8];               // "TDSECKP1"
+  int N, L, stencil, precision, gauge, ghost;
+  int flags;                   // bit 0: FP64 Lanczos norm cached; bit 1: mixed norm cached; bit 2: flux
+  int flux_ntheta, flux_ib, pad;
+  double t, offset, psinorm, sigma0;
+};
+constexpr char kCheckpointMagic[8] = {'T', 'D', 'S', 'E', 'C', 'K', 'P', '1'};
+
+size_t checkpoint_bytes(const tdse *h) {
+  size_t b = sizeof(CheckpointHeader) + sizeof(double2) * npts(h);
+  if (h->flux_ib >= 0) b += sizeof(double) * (2 + 2 * (size_t)h->flux_ntheta);
+  return b;
+}
+
+}  // namespace
+
+size_t tdse_checkpoint_bytes(const tdse_t *h) { return h ? checkpoint_bytes(h) : 0; }
+
+int tdse_checkpoint_save(tdse_t *h, void *buf, size_t bytes) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (!buf || bytes < checkpoint_bytes(h)) return fail(h, TDSE_ERR_ARG, "checkpoint buffer too small");
+  CheckpointHeader hd{};
+  std::memcpy(hd.magic, kCheckpointMagic, 8);
+  hd.N = h->g.N;
+  hd.L = h->g.L;
+  hd.stencil = h->g.stencil;
+  hd.precision = h->opts.precision;
+  hd.gauge = h->g.gauge;
+  hd.ghost = h->opts.ghost;
+  hd.t = h->t;
+  hd.offset = h->opts.offset;
+  const bool mixed = h->opts.precision == TDSE_MIXED;
+  hd.flags = (!mixed && h->lanczos_norm_valid ? 1 : 0) | (mixed && h->mixed_norm_valid && h->split_valid ? 2 : 0) |
+             (h->flux_ib >= 0 ? 4 : 0);
+  hd.flux_ntheta = h->flux_ntheta;
+  hd.flux_ib = h->flux_ib;
+  char *p = static_cast<char *>(buf);
+  TDSE_CUDA(h, cudaMemcpyAsync(p + sizeof(hd), h->psi, sizeof(double2) * npts(h), cudaMemcpyDeviceToHost, h->stream),
+            "checkpoint state");
+  double sc[2];
+  TDSE_CUDA(h, cudaMemcpyAsync(&sc[0], &h->ls->psinorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+            "checkpoint norm");
+  TDSE_CUDA(h, cudaMemcpyAsync(&sc[1], &h->ls->sigma[0], sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+            "checkpoint norm");
+  if (h->flux_ib >= 0)
+    TDSE_CUDA(h, cudaMemcpyAsync(p + sizeof(hd) + sizeof(double2) * npts(h), h->flux_state,
+                                 sizeof(double) * (2 + 2 * (size_t)h->flux_ntheta), cudaMemcpyDeviceToHost, h->stream),
+              "checkpoint flux");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync checkpoint");
+  hd.psinorm = sc[0];
+  hd.sigma0 = sc[1];
+  std::memcpy(p, &hd, sizeof(hd));
+  return TDSE_OK;
+}
+
+int tdse_checkpoint_load(tdse_t *h, const void *buf, size_t bytes) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  CheckpointHeader hd;
+  if (!buf || bytes < sizeof(hd)) return fail(h, TDSE_ERR_ARG, "checkpoint buffer too small");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kCheckpointMagic, 8) != 0) return fail(h, TDSE_ERR_ARG, "not a checkpoint");
+  if (hd.N != h->g.N || hd.L != h->g.L || hd.stencil != h->g.stencil || hd.ghost != h->opts.ghost ||
+      hd.offset != h->opts.offset || hd.gauge != h->g.gauge)
+    return fail(h, TDSE_ERR_ARG, "checkpoint of another grid, ghost, offset or gauge");
+  const bool has_flux = (hd.flags & 4) != 0;
+  if (has_flux != (h->flux_ib >= 0) || (has_flux && (hd.flux_ib != h->flux_ib || hd.flux_ntheta != h->flux_ntheta)))
+    return fail(h, TDSE_ERR_ARG, "checkpoint and handle differ in their flux setup");
+  const size_t need = sizeof(hd) + sizeof(double2) * npts(h) +
+                      (has_flux ? sizeof(double) * (2 + 2 * (size_t)hd.flux_ntheta) : 0);
+  if (bytes < need) return fail(h, TDSE_ERR_ARG, "checkpoint buffer too small");
+  const char *p = static_cast<const char *>(buf);
+  TDSE_CUDA(h, cudaMemcpyAsync(h->psi, p + sizeof(hd), sizeof(double2) * npts(h), cudaMemcpyHostToDevice, h->stream),
+            "restore state");
+  if (has_flux)
+    TDSE_CUDA(h, cudaMemcpyAsync(h->flux_state, p + sizeof(hd) + sizeof(double2) * npts(h),
+                                 sizeof(double) * (2 + 2 * (size_t)hd.flux_ntheta), cudaMemcpyHostToDevice, h->stream),
+              "restore flux");
+  const bool same_prec = hd.precision == h->opts.precision;
+  const bool mixed = h->opts.precision == TDSE_MIXED;
+  h->lanczos_norm_valid = false;
+  h->split_valid = false;
+  h->mixed_norm_valid = false;
+  if (same_prec && (hd.flags & 3)) {
+    // the cached norm of the saved run, so that the next Lanczos step starts from the same scalars
+    TDSE_CUDA(h, cudaMemcpyAsync(&h->ls->psinorm, &hd.psinorm, sizeof(double), cudaMemcpyHostToDevice, h->stream),
+              "restore norm");
+    TDSE_CUDA(h, cudaMemcpyAsync(&h->ls->sigma[0], &hd.sigma0, sizeof(double), cudaMemcpyHostToDevice, h->stream),
+              "restore norm");
+    if (!mixed) {
+      h->lanczos_norm_valid = (hd.flags & 1) != 0;
+    } else {
+      rc = ensure_mixed(h, 1);
+      if (rc) return rc;
+      TDSE_LAUNCH(h, TDSE_K_NORM,
+                  launch_mx_split_plain(h->g, h->psi, split_hi(h, h->split_cur), split_lo(h, h->split_cur), h->stream),
+                  "restore split");
+      h->split_valid = true;
+      h->mixed_norm_valid = (hd.flags & 2) != 0;
+    }
+  }
+  h->t = hd.t;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync restore");
   return TDSE_OK;
 }
 

@@ -1648,6 +1648,7 @@ double tdse_batch_get_time(const tdse_batch_t *b, int i) {
 }
 
 int tdse_batch_propagate(tdse_batch_t *b, long nsteps) {
+  TraceRange trace("tdse_batch_propagate");
   if (!b) return TDSE_ERR_ARG;
   if (b->eng.poisoned) return TDSE_ERR_STATE;
   if (nsteps < 0) return b->eng.fail(TDSE_ERR_ARG, "nsteps < 0");
@@ -1657,6 +1658,7 @@ int tdse_batch_propagate(tdse_batch_t *b, long nsteps) {
 }
 
 int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, long nsteps, int groups) {
+  TraceRange trace("tdse_batch_propagate_io");
   if (!b) return TDSE_ERR_ARG;
   Engine &e = b->eng;
   if (e.poisoned) return TDSE_ERR_STATE;

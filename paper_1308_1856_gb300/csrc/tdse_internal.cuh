@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -18,6 +19,14 @@
 #include "../../include/tdse.h"
 
 namespace tdse_dev {
+
+// NVTX range over one ABI call (visible in Nsight timelines; free without a tool).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr int kMaxKrylov = TDSE_MAX_KRYLOV;
 // Persistent grids use few, large blocks (2 x 16 warps per SM): every block
@@ -150,6 +159,8 @@ struct MixedView {
   const float *rj, *kappa;
 };
 
+// hi/lo split of psi without the norm (the same split as every other kernel's)
+cudaError_t launch_mx_split_plain(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo, cudaStream_t st);
 cudaError_t launch_mx_split(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo,
                             Reduction *red, LanczosScalars *ls, int *status, cudaStream_t st);
 cudaError_t launch_mx_apply_h(const Geometry &g, const MixedView &mv, double E, const double2 *x,

@@ -379,6 +379,12 @@ cudaError_t launch_mx_split(const Geometry &g, const double2 *psi, float2 *hi, f
   return cudaGetLastError();
 }
 
+cudaError_t launch_mx_split_plain(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo, cudaStream_t st) {
+  const size_t G = (size_t)g.N * (g.L + 1);
+  mx_split_plain_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, psi, hi, lo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mx_apply_h(const Geometry &g, const MixedView &mv, double E, const double2 *x,
                               float2 *tmp_hi, float2 *tmp_lo, double2 *y, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);

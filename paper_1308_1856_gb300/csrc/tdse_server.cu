@@ -119,6 +119,7 @@ int tdse_server_submit(tdse_server_t *s, const tdse_instance_spec *spec, long ns
 }
 
 int tdse_server_step(tdse_server_t *s, long k, int *finished) {
+  TraceRange trace("tdse_server_step");
   int rc = usable(s);
   if (rc) return rc;
   if (finished) *finished = 0;

@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 def _declared():
     txt = open(HEADER).read()
-    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|unsigned long long|long long|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
+    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|unsigned long long|long long|size_t|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
                           txt, re.M))
 
 
@@ -98,3 +98,19 @@ def test_server_instance_bytes(lib):
     bad = _spec(krylov=0)
     assert B.tdse_server_instance_bytes(ctypes.byref(bad), B.TDSE_FP64) == 0
     assert B.tdse_server_instance_bytes(ctypes.byref(_spec(dt=-1.0)), B.TDSE_FP64) == 0
+
+
+def test_header_is_plain_c99(tmp_path):
+    """include/tdse.h compiles on its own as C99 (no C++ or CUDA types leak
+    into the boundary) and every declared function links against the library."""
+    import subprocess
+    src = tmp_path / "use_header.c"
+    names = sorted(_declared())
+    body = "\n".join(f"  (void)&{n};" for n in names)
+    src.write_text(f'#include "tdse.h"\nint main(void) {{\n{body}\n  return 0;\n}}\n')
+    exe = tmp_path / "use_header"
+    lib = B.library_path()
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.dirname(HEADER), str(src), "-o", str(exe), lib,
+                        f"-Wl,-rpath,{os.path.dirname(lib)}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
