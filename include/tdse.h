@@ -214,6 +214,24 @@ int tdse_dipole_series(tdse_t *h, long capacity);
 int tdse_dipole_series_read(tdse_t *h, double *out, long max_entries, long *count);
 
 /*
+ * The per-step record (the paper's time-dependent output, Sec. 4): after every
+ * `every`-th real-time step, one row of tdse_record_width(h) = lmax + 11
+ * doubles is written on the device:
+ *   t, norm, dipole, yield, p_ground, l_pop[0..lmax],   (as tdse_observables)
+ *   <z>, <zdot>, <zddot>,                               (as tdse_dipole_moments)
+ *   flux, flux yield                                    (as tdse_flux_read; NaN without a flux setup)
+ * (p_e = (1 - yield) - p_ground.)  Two or three extra launches per recorded
+ * step; recording stops when `capacity` rows are full; every call discards
+ * what was recorded and restarts the step count.  capacity 0 turns it off.
+ * tdse_record_read copies up to max_rows rows (out may be NULL to query the
+ * count) and synchronises.  Errors: TDSE_ERR_ARG (every < 1, capacity < 0),
+ * TDSE_ERR_OOM.
+ */
+int tdse_record_setup(tdse_t *h, long every, long capacity);
+long tdse_record_width(const tdse_t *h);
+int tdse_record_read(tdse_t *h, double *out, long max_rows, long *count);
+
+/*
  * Flux through the sphere r = r_b (Sec. 4, Eqs. (flux), (pad), (yield)),
  * evaluated at the grid point nearest r_b (a tie goes to the inner point):
  *   flux       = sum_l Im(f_l^* D1 f_l) [+ 2 (A/c) sum_l kappa_{l+1} Re(f_l^* f_{l+1})]

@@ -176,6 +176,26 @@ class TDSE:
                                      pad.ctypes.data_as(C._dp)))
         return {"flux": f.value, "yield": y.value, "density": dens[:nt], "pad": pad[:nt]}
 
+    def record(self, every: int, capacity: int):
+        """Record the observables, dipole moments and flux every `every` steps (capacity 0: off)."""
+        self._check(C.tdse_record_setup(self.h, int(every), int(capacity)))
+
+    def records(self) -> dict:
+        """The recorded rows as arrays: t, norm, dipole, yield, p_ground, l_pop, z, zdot, zddot,
+        flux, flux_yield."""
+        w = C.tdse_record_width(self.h)
+        n = ctypes.c_long()
+        self._check(C.tdse_record_read(self.h, None, 0, ctypes.byref(n)))
+        a = np.zeros((n.value, w))
+        if n.value:
+            self._check(C.tdse_record_read(self.h, a.ctypes.data_as(C._dp), n.value, ctypes.byref(n)))
+        L = w - 11
+        cols = {"t": a[:, 0], "norm": a[:, 1], "dipole": a[:, 2], "yield": a[:, 3], "p_ground": a[:, 4],
+                "l_pop": a[:, 5:6 + L]}
+        for k, name in enumerate(("z", "zdot", "zddot", "flux", "flux_yield")):
+            cols[name] = a[:, 6 + L + k]
+        return cols
+
     def checkpoint(self) -> bytes:
         """State, time, cached norm and flux integrals, for a bitwise resume."""
         n = C.tdse_checkpoint_bytes(self.h)

@@ -87,6 +87,9 @@ SIGNATURES = {
     "tdse_dipole_series": (_c_int, [_vp, _c_long]),
     "tdse_dipole_series_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
     "tdse_flux_setup": (_c_int, [_vp, _c_double, _c_int, _dp]),
+    "tdse_record_setup": (_c_int, [_vp, _c_long, _c_long]),
+    "tdse_record_width": (_c_long, [_vp]),
+    "tdse_record_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
     "tdse_checkpoint_bytes": (ctypes.c_size_t, [_vp]),
     "tdse_checkpoint_save": (_c_int, [_vp, _vp, ctypes.c_size_t]),
     "tdse_checkpoint_load": (_c_int, [_vp, _vp, ctypes.c_size_t]),
@@ -197,6 +200,9 @@ tdse_dipole_moments = _fn("tdse_dipole_moments")
 tdse_dipole_series = _fn("tdse_dipole_series")
 tdse_dipole_series_read = _fn("tdse_dipole_series_read")
 tdse_flux_setup = _fn("tdse_flux_setup")
+tdse_record_setup = _fn("tdse_record_setup")
+tdse_record_width = _fn("tdse_record_width")
+tdse_record_read = _fn("tdse_record_read")
 tdse_checkpoint_bytes = _fn("tdse_checkpoint_bytes")
 tdse_checkpoint_save = _fn("tdse_checkpoint_save")
 tdse_checkpoint_load = _fn("tdse_checkpoint_load")

@@ -45,6 +45,11 @@ struct tdse {
   double *flux_y = nullptr;        // Y_l0(theta_k), angle-major: [k (L+1) + l]
   double *flux_ct = nullptr;       // cos(theta_k)
   int flux_ntheta = 0, flux_ib = -1;
+  // the per-step record (tdse_record_*): every rec_every-th step, one row of
+  // rec_width() doubles on the device, the times on the host
+  double *rec = nullptr;
+  long rec_cap = 0, rec_every = 1, rec_step = 0;
+  std::vector<double> rec_t;
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
   // a final stage reads one pair with halos while writing the other) and
   // complex64 work vectors
@@ -223,6 +228,7 @@ void free_all(tdse *h) {
   cudaFree(h->flux_state);
   cudaFree(h->flux_y);
   cudaFree(h->flux_ct);
+  cudaFree(h->rec);
   cudaFree(h->diagf);
   cudaFree(h->rjf);
   cudaFree(h->kappaf);
@@ -355,7 +361,10 @@ int refresh_split(tdse *h, bool need_norm) {
 }
 
 // ---- Sec. 4 observables after every real-time step --------------------------
-bool hooks_on(const tdse *h) { return h->series_cap > 0 || h->flux_ib >= 0; }
+bool hooks_on(const tdse *h) { return h->series_cap > 0 || h->flux_ib >= 0 || h->rec_cap > 0; }
+
+// Device row of the record: norm, dipole, yield, p_ground, l_pop[L+1], z, zdot, zddot, flux, flux yield.
+long rec_width(const tdse *h) { return (long)h->g.L + 10; }
 
 // A/c of the velocity gauge at t (0 in the length gauge).
 double ac_at(const tdse *h, double t) { return h->g.gauge == 1 ? coupling_at(h, t) : 0.0; }
@@ -391,6 +400,23 @@ int step_hook(tdse *h, double t_new, double dt) {
                 launch_flux(h->g, view(h), h->psi, h->opts.ghost, h->flux_ib, ac_at(h, t_new), h->flux_y,
                             h->flux_ct, h->flux_ntheta, dt, false, h->flux_state, h->stream),
                 "flux");
+  if (h->rec_cap > 0 && ++h->rec_step % h->rec_every == 0 && (long)h->rec_t.size() < h->rec_cap) {
+    const int L = h->g.L;
+    double *row = h->rec + (size_t)rec_width(h) * h->rec_t.size();
+    unsigned *ticket = reinterpret_cast<unsigned *>(h->obs_partials + (size_t)5 * observables_blocks(h->g) * (L + 1));
+    TDSE_LAUNCH(h, TDSE_K_OBSERVABLES,
+                launch_observables(h->g, view(h), h->psi, h->ref0, h->opts.r_b, h->obs_partials, ticket, row,
+                                   h->stream),
+                "record observables");
+    int rc = launch_dipole(h, t_new, row + L + 5);
+    if (rc) return rc;
+    if (h->flux_ib >= 0)
+      TDSE_CUDA(h, cudaMemcpyAsync(row + L + 8, h->flux_state, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   h->stream), "record flux");
+    else
+      TDSE_CUDA(h, cudaMemsetAsync(row + L + 8, 0xff, 2 * sizeof(double), h->stream), "record flux");   // NaN
+    h->rec_t.push_back(t_new);
+  }
   return TDSE_OK;
 }
 
@@ -1262,6 +1288,48 @@ int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, doub
   if (yield) *yield = v[1];
   if (density && nt) std::memcpy(density, v.data() + 2, sizeof(double) * nt);
   if (pad && nt) std::memcpy(pad, v.data() + 2 + nt, sizeof(double) * nt);
+  return TDSE_OK;
+}
+
+int tdse_record_setup(tdse_t *h, long every, long capacity) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (every < 1 || capacity < 0) return fail(h, TDSE_ERR_ARG, "need every >= 1 and capacity >= 0");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before record");
+  cudaFree(h->rec);
+  h->rec = nullptr;
+  h->rec_cap = 0;
+  h->rec_t.clear();
+  h->rec_every = every;
+  h->rec_step = 0;
+  if (capacity == 0) return TDSE_OK;
+  if (cudaMalloc(&h->rec, sizeof(double) * (size_t)rec_width(h) * (size_t)capacity) != cudaSuccess) {
+    cudaGetLastError();
+    h->rec = nullptr;
+    return fail(h, TDSE_ERR_OOM, "record");
+  }
+  h->rec_t.reserve((size_t)capacity);
+  h->rec_cap = capacity;
+  return TDSE_OK;
+}
+
+long tdse_record_width(const tdse_t *h) { return h ? rec_width(h) + 1 : 0; }
+
+int tdse_record_read(tdse_t *h, double *out, long max_rows, long *count) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  const long n = (long)h->rec_t.size();
+  if (count) *count = n;
+  if (!out || max_rows <= 0 || n == 0) return TDSE_OK;
+  const long k = n < max_rows ? n : max_rows, w = rec_width(h);
+  std::vector<double> v((size_t)w * k);
+  TDSE_CUDA(h, cudaMemcpyAsync(v.data(), h->rec, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->stream),
+            "read record");
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync record");
+  for (long i = 0; i < k; ++i) {
+    out[(size_t)(w + 1) * i] = h->rec_t[(size_t)i];
+    std::memcpy(out + (size_t)(w + 1) * i + 1, v.data() + (size_t)w * i, sizeof(double) * w);
+  }
   return TDSE_OK;
 }
 

@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 def _declared():
     txt = open(HEADER).read()
-    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|unsigned long long|long long|size_t|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
+    return set(re.findall(r"^\s*(?:const\s+)?(?:int|double|unsigned long long|long long|long|size_t|char|void)\s*\*?\s*(tdse_\w+)\s*\(",
                           txt, re.M))
 
 

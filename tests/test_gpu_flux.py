@@ -219,3 +219,53 @@ def test_flux_and_series_arguments():
     tt.propagate_imag("lanczos", 8, 0.1, 2)
     assert tt.dipole_series().shape == (0, 4)
     tt.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_record_rows_equal_the_separate_calls(prec):
+    """The per-step record (every 2nd step, capacity 4 of 5 recordable steps)
+    of one 10-step call: each row equals what tdse_observables,
+    tdse_dipole_moments and tdse_flux_read return after the same steps taken
+    two per call (the step times then accumulate differently, so the states
+    agree to rounding, 1e-12 relative, not bitwise)."""
+    N, dr, L = 400, 0.1, 6
+    psi = W.smooth_state(N, dr, L, seed=9)
+    ct = np.cos(np.linspace(0.0, np.pi, 5))
+
+    def fresh():
+        t = make(N, dr, L, 5, pulse=PULSE)
+        t.set_options(precision=prec, r_b=10.0)
+        t.set_state(psi)
+        t.time = 30.0
+        t.flux_setup(12.0, ct)
+        return t
+    a = fresh()
+    a.record(2, 4)
+    a.propagate("lanczos", 12, 0.01, 10)
+    rec = a.records()
+    a.close()
+    assert len(rec["t"]) == 4
+    b = fresh()
+
+    def close(x, y):
+        return abs(x - y) <= 1e-12 * max(1.0, abs(y))
+    for n in range(4):
+        b.propagate("lanczos", 12, 0.01, 2)
+        ob, dm, fl = b.observables(), b.dipole_moments(), b.flux()
+        assert abs(rec["t"][n] - (30.0 + 2 * (n + 1) * 0.01)) <= 1e-12
+        for key in ("norm", "dipole", "yield", "p_ground"):
+            assert close(rec[key][n], ob[key]), key
+        assert np.all(np.abs(rec["l_pop"][n] - ob["l_pop"]) <= 1e-12)
+        assert close(rec["z"][n], dm[0]) and close(rec["zdot"][n], dm[1]) and close(rec["zddot"][n], dm[2])
+        assert close(rec["flux"][n], fl["flux"]) and close(rec["flux_yield"][n], fl["yield"])
+    b.close()
+    # without a flux setup the flux columns are NaN; capacity 0 turns recording off
+    c = make(N, dr, L, 5, pulse=PULSE)
+    c.record(1, 3)
+    c.propagate("rk4", 4, 0.002, 2)
+    r = c.records()
+    assert len(r["t"]) == 2 and np.all(np.isnan(r["flux"]))
+    c.record(1, 0)
+    c.propagate("rk4", 4, 0.002, 2)
+    assert len(c.records()["t"]) == 0
+    c.close()
