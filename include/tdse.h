@@ -256,6 +256,17 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta);
 int tdse_flux_read(tdse_t *h, double *flux, double *yield, double *density, double *pad);
 
 /*
+ * Debug guard bands.  When the environment variable TDSE_GUARD_BYTES is a
+ * positive number at tdse_create, every device buffer the handle allocates
+ * sits between two bands of that many bytes (rounded up to 256) filled with
+ * 0xff.  tdse_check_guards synchronises and checks every band: TDSE_OK if
+ * all are intact (or guards are off), TDSE_ERR_STATE naming the buffer whose
+ * band a kernel overwrote.  (A stand-in for a device memory checker: out-of-
+ * bounds writes next to a buffer land in a band.)
+ */
+int tdse_check_guards(tdse_t *h);
+
+/*
  * Checkpoint and resume.  A checkpoint holds the state, the time, the cached
  * norm the next Lanczos step starts from and, if the flux is set up, its
  * current values and time integrals: loading it into a handle of the same

@@ -196,6 +196,10 @@ class TDSE:
             cols[name] = a[:, 6 + L + k]
         return cols
 
+    def check_guards(self):
+        """Raise if a debug guard band (TDSE_GUARD_BYTES) around a device buffer was overwritten."""
+        self._check(C.tdse_check_guards(self.h))
+
     def checkpoint(self) -> bytes:
         """State, time, cached norm and flux integrals, for a bitwise resume."""
         n = C.tdse_checkpoint_bytes(self.h)

@@ -87,6 +87,7 @@ SIGNATURES = {
     "tdse_dipole_series": (_c_int, [_vp, _c_long]),
     "tdse_dipole_series_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
     "tdse_flux_setup": (_c_int, [_vp, _c_double, _c_int, _dp]),
+    "tdse_check_guards": (_c_int, [_vp]),
     "tdse_record_setup": (_c_int, [_vp, _c_long, _c_long]),
     "tdse_record_width": (_c_long, [_vp]),
     "tdse_record_read": (_c_int, [_vp, _dp, _c_long, ctypes.POINTER(_c_long)]),
@@ -200,6 +201,7 @@ tdse_dipole_moments = _fn("tdse_dipole_moments")
 tdse_dipole_series = _fn("tdse_dipole_series")
 tdse_dipole_series_read = _fn("tdse_dipole_series_read")
 tdse_flux_setup = _fn("tdse_flux_setup")
+tdse_check_guards = _fn("tdse_check_guards")
 tdse_record_setup = _fn("tdse_record_setup")
 tdse_record_width = _fn("tdse_record_width")
 tdse_record_read = _fn("tdse_record_read")

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -60,6 +61,11 @@ struct tdse {
   bool mixed_norm_valid = false;   // sigma_0 / psinorm hold ||psi|| (mixed Lanczos)
   float2 *mwork = nullptr;
   size_t mwork_vecs = 0;
+  // debug guard bands (TDSE_GUARD_BYTES at create): every device buffer of the
+  // handle sits between two bands of 0xff bytes that tdse_check_guards verifies
+  size_t guard = 0;
+  struct Alloc { char *base; void *user; size_t bytes; const char *name; };
+  std::vector<Alloc> allocs;
   // bookkeeping
   std::string err;
   bool poisoned = false;
@@ -206,34 +212,72 @@ int build_tables(tdse *h) {
   return TDSE_OK;
 }
 
+// Device allocation of the handle: bytes between two guard bands of h->guard
+// bytes (0: none), registered so that dfree and the guard check find it.
+template <typename T>
+cudaError_t dmalloc(tdse *h, T **p, size_t bytes, const char *name) {
+  char *base = nullptr;
+  const size_t g = h->guard;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&base), bytes + 2 * g);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  if (g) {
+    e = cudaMemset(base, 0xff, g);
+    if (e == cudaSuccess) e = cudaMemset(base + g + bytes, 0xff, g);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      *p = nullptr;
+      return e;
+    }
+  }
+  *p = reinterpret_cast<T *>(base + g);
+  h->allocs.push_back({base, base + g, bytes, name});
+  return cudaSuccess;
+}
+#define DMALLOC(h, field, bytes) dmalloc(h, &(h)->field, bytes, #field)
+
+void dfree(tdse *h, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i].user == p) {
+      cudaFree(h->allocs[i].base);
+      h->allocs.erase(h->allocs.begin() + (long)i);
+      return;
+    }
+  cudaFree(p);
+}
+
 void free_all(tdse *h) {
-  cudaFree(h->psi);
-  cudaFree(h->ref0);
-  cudaFree(h->work);
-  cudaFree(h->diag);
-  cudaFree(h->rj);
-  cudaFree(h->rinv);
-  cudaFree(h->kappa);
-  cudaFree(h->mask);
-  cudaFree(h->red);
-  cudaFree(h->ls);
-  cudaFree(h->status);
-  cudaFree(h->obs_partials);
-  cudaFree(h->obs_out);
-  cudaFree(h->imag);
-  cudaFree(h->rk_sigma);
-  cudaFree(h->dip_out);
-  cudaFree(h->dip_partials);
-  cudaFree(h->series);
-  cudaFree(h->flux_state);
-  cudaFree(h->flux_y);
-  cudaFree(h->flux_ct);
-  cudaFree(h->rec);
-  cudaFree(h->diagf);
-  cudaFree(h->rjf);
-  cudaFree(h->kappaf);
-  cudaFree(h->split);
-  cudaFree(h->mwork);
+  dfree(h, h->psi);
+  dfree(h, h->ref0);
+  dfree(h, h->work);
+  dfree(h, h->diag);
+  dfree(h, h->rj);
+  dfree(h, h->rinv);
+  dfree(h, h->kappa);
+  dfree(h, h->mask);
+  dfree(h, h->red);
+  dfree(h, h->ls);
+  dfree(h, h->status);
+  dfree(h, h->obs_partials);
+  dfree(h, h->obs_out);
+  dfree(h, h->imag);
+  dfree(h, h->rk_sigma);
+  dfree(h, h->dip_out);
+  dfree(h, h->dip_partials);
+  dfree(h, h->series);
+  dfree(h, h->flux_state);
+  dfree(h, h->flux_y);
+  dfree(h, h->flux_ct);
+  dfree(h, h->rec);
+  dfree(h, h->diagf);
+  dfree(h, h->rjf);
+  dfree(h, h->kappaf);
+  dfree(h, h->split);
+  dfree(h, h->mwork);
   for (auto &m : h->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -244,10 +288,10 @@ void free_all(tdse *h) {
 int ensure_work(tdse *h, size_t nvec) {
   if (h->work_vecs >= nvec) return TDSE_OK;
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before realloc");
-  cudaFree(h->work);
+  dfree(h, h->work);
   h->work = nullptr;
   h->work_vecs = 0;
-  cudaError_t e = cudaMalloc(&h->work, sizeof(double2) * npts(h) * nvec);
+  cudaError_t e = DMALLOC(h, work, sizeof(double2) * npts(h) * nvec);
   if (e != cudaSuccess) {
     h->work = nullptr;
     cudaGetLastError();
@@ -321,7 +365,7 @@ int check_status_word(tdse *h) {
 int ensure_mixed(tdse *h, size_t nvec) {
   const size_t G = npts(h);
   if (!h->split) {
-    cudaError_t e = cudaMalloc(&h->split, sizeof(float2) * G * 4);
+    cudaError_t e = DMALLOC(h, split, sizeof(float2) * G * 4);
     if (e != cudaSuccess) {
       h->split = nullptr;
       cudaGetLastError();
@@ -332,10 +376,10 @@ int ensure_mixed(tdse *h, size_t nvec) {
   }
   if (h->mwork_vecs >= nvec) return TDSE_OK;
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before realloc");
-  cudaFree(h->mwork);
+  dfree(h, h->mwork);
   h->mwork = nullptr;
   h->mwork_vecs = 0;
-  cudaError_t e = cudaMalloc(&h->mwork, sizeof(float2) * G * nvec);
+  cudaError_t e = DMALLOC(h, mwork, sizeof(float2) * G * nvec);
   if (e != cudaSuccess) {
     h->mwork = nullptr;
     cudaGetLastError();
@@ -372,7 +416,7 @@ double ac_at(const tdse *h, double t) { return h->g.gauge == 1 ? coupling_at(h, 
 int launch_dipole(tdse *h, double t, double *out) {
   const size_t np = (size_t)4 * dipole_blocks(h->g);
   if (!h->dip_partials) {
-    if (cudaMalloc(&h->dip_partials, sizeof(double) * (np + 1)) != cudaSuccess) {
+    if (DMALLOC(h, dip_partials, sizeof(double) * (np + 1)) != cudaSuccess) {
       cudaGetLastError();
       h->dip_partials = nullptr;
       return fail(h, TDSE_ERR_OOM, "dipole partials");
@@ -664,7 +708,7 @@ int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
   for (int j = 0; j + 1 < s; ++j) fsal = fsal && tb.a[s - 1][j] == tb.b[j];
   int rc = ensure_work(h, (size_t)(s + 1 > 2 ? s + 1 : 2));
   if (rc) return rc;
-  if (!h->rk_sigma && cudaMalloc(&h->rk_sigma, sizeof(double)) != cudaSuccess) {
+  if (!h->rk_sigma && DMALLOC(h, rk_sigma, sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->rk_sigma = nullptr;
     return fail(h, TDSE_ERR_OOM, "RK error-estimate scalar");
@@ -723,7 +767,7 @@ int rk_general_steps(tdse *h, int id, double dt, long nsteps, double *sigma) {
 //   E = -ln(||psi_new||^2 / ||psi||^2) / (2 dt),  psi <- psi_new / ||psi_new||
 // (norms dr-weighted).  energy receives the last step's estimate.
 int imag_steps(tdse *h, int method, int order, double dt, long nsteps, double *energy) {
-  if (!h->imag && cudaMalloc(&h->imag, 2 * sizeof(double)) != cudaSuccess) {
+  if (!h->imag && DMALLOC(h, imag, 2 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->imag = nullptr;
     return fail(h, TDSE_ERR_OOM, "imaginary-time scalars");
@@ -849,23 +893,27 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
     return TDSE_ERR_CUDA;
   }
   h->stream = h->own_stream;
+  if (const char *gb = std::getenv("TDSE_GUARD_BYTES")) {
+    const long v = std::strtol(gb, nullptr, 10);
+    if (v > 0) h->guard = ((size_t)v + 255) / 256 * 256;   // keeps every buffer 256-byte aligned
+  }
   const int nbx = observables_blocks(h->g);
   const size_t obs_n = (size_t)5 * nbx * (lmax + 1) + 2;
-  bool ok = cudaMalloc(&h->psi, sizeof(double2) * G) == cudaSuccess &&
-            cudaMalloc(&h->ref0, sizeof(double2) * N) == cudaSuccess &&
-            cudaMalloc(&h->diag, sizeof(double) * G) == cudaSuccess &&
-            cudaMalloc(&h->rj, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&h->rinv, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&h->kappa, sizeof(double) * (lmax + 2)) == cudaSuccess &&
-            cudaMalloc(&h->mask, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&h->red, sizeof(Reduction)) == cudaSuccess &&
-            cudaMalloc(&h->ls, sizeof(LanczosScalars)) == cudaSuccess &&
-            cudaMalloc(&h->status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->obs_partials, sizeof(double) * obs_n) == cudaSuccess &&
-            cudaMalloc(&h->obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess &&
-            cudaMalloc(&h->diagf, sizeof(float) * G) == cudaSuccess &&
-            cudaMalloc(&h->rjf, sizeof(float) * N) == cudaSuccess &&
-            cudaMalloc(&h->kappaf, sizeof(float) * (lmax + 2)) == cudaSuccess;
+  bool ok = DMALLOC(h, psi, sizeof(double2) * G) == cudaSuccess &&
+            DMALLOC(h, ref0, sizeof(double2) * N) == cudaSuccess &&
+            DMALLOC(h, diag, sizeof(double) * G) == cudaSuccess &&
+            DMALLOC(h, rj, sizeof(double) * N) == cudaSuccess &&
+            DMALLOC(h, rinv, sizeof(double) * N) == cudaSuccess &&
+            DMALLOC(h, kappa, sizeof(double) * (lmax + 2)) == cudaSuccess &&
+            DMALLOC(h, mask, sizeof(double) * N) == cudaSuccess &&
+            DMALLOC(h, red, sizeof(Reduction)) == cudaSuccess &&
+            DMALLOC(h, ls, sizeof(LanczosScalars)) == cudaSuccess &&
+            DMALLOC(h, status, sizeof(int)) == cudaSuccess &&
+            DMALLOC(h, obs_partials, sizeof(double) * obs_n) == cudaSuccess &&
+            DMALLOC(h, obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess &&
+            DMALLOC(h, diagf, sizeof(float) * G) == cudaSuccess &&
+            DMALLOC(h, rjf, sizeof(float) * N) == cudaSuccess &&
+            DMALLOC(h, kappaf, sizeof(float) * (lmax + 2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(h);
@@ -1152,7 +1200,7 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
 int tdse_dipole_moments(tdse_t *h, double *z, double *zdot, double *zddot) {
   int rc = check_usable(h);
   if (rc) return rc;
-  if (!h->dip_out && cudaMalloc(&h->dip_out, 3 * sizeof(double)) != cudaSuccess) {
+  if (!h->dip_out && DMALLOC(h, dip_out, 3 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->dip_out = nullptr;
     return fail(h, TDSE_ERR_OOM, "dipole output");
@@ -1173,12 +1221,12 @@ int tdse_dipole_series(tdse_t *h, long capacity) {
   if (rc) return rc;
   if (capacity < 0) return fail(h, TDSE_ERR_ARG, "capacity must be >= 0");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before series");
-  cudaFree(h->series);
+  dfree(h, h->series);
   h->series = nullptr;
   h->series_cap = 0;
   h->series_t.clear();
   if (capacity == 0) return TDSE_OK;
-  if (cudaMalloc(&h->series, sizeof(double) * 3 * (size_t)capacity) != cudaSuccess) {
+  if (DMALLOC(h, series, sizeof(double) * 3 * (size_t)capacity) != cudaSuccess) {
     cudaGetLastError();
     h->series = nullptr;
     return fail(h, TDSE_ERR_OOM, "dipole series");
@@ -1212,9 +1260,9 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta) 
   int rc = check_usable(h);
   if (rc) return rc;
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before flux setup");
-  cudaFree(h->flux_state);
-  cudaFree(h->flux_y);
-  cudaFree(h->flux_ct);
+  dfree(h, h->flux_state);
+  dfree(h, h->flux_y);
+  dfree(h, h->flux_ct);
   h->flux_state = h->flux_y = h->flux_ct = nullptr;
   h->flux_ib = -1;
   h->flux_ntheta = 0;
@@ -1248,13 +1296,13 @@ int tdse_flux_setup(tdse_t *h, double r_b, int ntheta, const double *cos_theta) 
     }
   }
   const size_t nstate = 2 + 2 * (size_t)ntheta;
-  if (cudaMalloc(&h->flux_state, sizeof(double) * nstate) != cudaSuccess ||
-      (ntheta > 0 && (cudaMalloc(&h->flux_y, sizeof(double) * y.size()) != cudaSuccess ||
-                      cudaMalloc(&h->flux_ct, sizeof(double) * ct.size()) != cudaSuccess))) {
+  if (DMALLOC(h, flux_state, sizeof(double) * nstate) != cudaSuccess ||
+      (ntheta > 0 && (DMALLOC(h, flux_y, sizeof(double) * y.size()) != cudaSuccess ||
+                      DMALLOC(h, flux_ct, sizeof(double) * ct.size()) != cudaSuccess))) {
     cudaGetLastError();
-    cudaFree(h->flux_state);
-    cudaFree(h->flux_y);
-    cudaFree(h->flux_ct);
+    dfree(h, h->flux_state);
+    dfree(h, h->flux_y);
+    dfree(h, h->flux_ct);
     h->flux_state = h->flux_y = h->flux_ct = nullptr;
     return fail(h, TDSE_ERR_OOM, "flux buffers");
   }
@@ -1296,14 +1344,14 @@ int tdse_record_setup(tdse_t *h, long every, long capacity) {
   if (rc) return rc;
   if (every < 1 || capacity < 0) return fail(h, TDSE_ERR_ARG, "need every >= 1 and capacity >= 0");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync before record");
-  cudaFree(h->rec);
+  dfree(h, h->rec);
   h->rec = nullptr;
   h->rec_cap = 0;
   h->rec_t.clear();
   h->rec_every = every;
   h->rec_step = 0;
   if (capacity == 0) return TDSE_OK;
-  if (cudaMalloc(&h->rec, sizeof(double) * (size_t)rec_width(h) * (size_t)capacity) != cudaSuccess) {
+  if (DMALLOC(h, rec, sizeof(double) * (size_t)rec_width(h) * (size_t)capacity) != cudaSuccess) {
     cudaGetLastError();
     h->rec = nullptr;
     return fail(h, TDSE_ERR_OOM, "record");
@@ -1329,6 +1377,25 @@ int tdse_record_read(tdse_t *h, double *out, long max_rows, long *count) {
   for (long i = 0; i < k; ++i) {
     out[(size_t)(w + 1) * i] = h->rec_t[(size_t)i];
     std::memcpy(out + (size_t)(w + 1) * i + 1, v.data() + (size_t)w * i, sizeof(double) * w);
+  }
+  return TDSE_OK;
+}
+
+int tdse_check_guards(tdse_t *h) {
+  if (!h) return TDSE_ERR_ARG;
+  if (h->poisoned) return TDSE_ERR_STATE;
+  if (!h->guard) return TDSE_OK;
+  TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync guards");
+  std::vector<unsigned char> band(h->guard);
+  for (const tdse::Alloc &a : h->allocs) {
+    for (int side = 0; side < 2; ++side) {
+      const char *at = side ? static_cast<const char *>(a.user) + a.bytes : a.base;
+      TDSE_CUDA(h, cudaMemcpy(band.data(), at, h->guard, cudaMemcpyDeviceToHost), "read guard");
+      for (unsigned char c : band)
+        if (c != 0xff)
+          return fail(h, TDSE_ERR_STATE, std::string("guard band ") + (side ? "after " : "before ") + a.name +
+                                             " overwritten");
+    }
   }
   return TDSE_OK;
 }
