@@ -466,9 +466,11 @@ int tdse_batch_propagate(tdse_batch_t *b, long nsteps);
 /*
  * Copy every state in, advance every instance by nsteps steps and copy every
  * state out, with the copies overlapping the compute (synchronous).  The
- * instances are cut into `groups` contiguous groups of about equal points;
- * group g is propagated once its input copy is done, and its output copy runs
- * while group g+1 computes, on two extra streams (one per copy direction).
+ * instances are cut into `groups` contiguous groups (with three or more, the
+ * first and the last hold 1/(4 groups) of the points each, since only their
+ * copies are not hidden, and the others share the rest equally); group g is
+ * propagated once its input copy is done, and its output copy runs while
+ * group g+1 computes, on two extra streams (one per copy direction).
  * The input copies start once the work already queued on the batch's stream
  * is done.  F_in / F_out: host buffers laid out as tdse_batch_set_states
  * (page-locked for the copies to overlap); either may be NULL.  The

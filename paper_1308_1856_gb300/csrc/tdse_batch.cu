@@ -1666,14 +1666,22 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
   if (groups > b->count) groups = b->count;
   int rc = io_ready(b, groups);
   if (rc) return rc;
-  // contiguous groups of about equal points; each instance's offset in the host buffers
+  // contiguous groups; each instance's offset in the host buffers.  Only the
+  // first group's input copy and the last group's output copy are not hidden
+  // behind compute, so with three or more groups those two get 1/(4 groups)
+  // of the points each and the middle groups share the rest equally.
   std::vector<size_t> off(b->count + 1, 0);
   for (int i = 0; i < b->count; ++i) off[i + 1] = off[i] + 2 * (size_t)e.hinst[i].N * (e.hinst[i].L + 1);
+  const double total = (double)off[b->count];
+  std::vector<double> cut(groups + 1, 0.0);
+  const double edge = groups >= 3 ? 1.0 / (4.0 * groups) : 1.0 / groups;
+  for (int g = 1; g < groups; ++g)
+    cut[g] = (groups >= 3) ? edge + (1.0 - 2.0 * edge) * (double)(g - 1) / (double)(groups - 2) : (double)g / groups;
   std::vector<int> first(groups + 1, b->count);
   first[0] = 0;
   for (int g = 1, i = 0; g < groups; ++g) {
-    const size_t target = off[b->count] / groups * g;
-    while (i < b->count && off[i] < target) ++i;
+    const double target = cut[g] * total;
+    while (i < b->count && (double)off[i] < target) ++i;
     first[g] = std::max(i, first[g - 1] + 1 <= b->count ? first[g - 1] + 1 : b->count);
   }
   auto bytes = [&](int i) { return sizeof(double) * (off[i + 1] - off[i]); };
