@@ -248,14 +248,17 @@ def _spec_struct(s) -> "C.tdse_instance_spec":
                                 float(s.get("E0", 0.0)), float(s.get("omega", 0.057)),
                                 float(s.get("ncycles", 2.0)), float(s.get("cep", 0.0)),
                                 int(s["krylov"]), float(s["dt"]),
-                                float(s.get("absorber_r", 1e300)), float(s.get("r_b", 10.0)))
+                                float(s.get("absorber_r", 1e300)), float(s.get("r_b", 10.0)),
+                                {"length": C.TDSE_GAUGE_LENGTH, "velocity": C.TDSE_GAUGE_VELOCITY}[s.get("gauge", "length")],
+                                {"sin2_e": C.TDSE_PULSE_SIN2_E, "sin2_a": C.TDSE_PULSE_SIN2_A}[s.get("shape", "sin2_e")])
 
 
 class Batch:
     """Many instances advanced together by the batched Lanczos launches.
 
     specs: iterable of dicts with keys N, dr, lmax, Z, E0, omega, ncycles, cep,
-    krylov, dt, absorber_r, r_b (see tdse_instance_spec in include/tdse.h)."""
+    krylov, dt, absorber_r, r_b, gauge ("length" / "velocity"), shape ("sin2_e" /
+    "sin2_a") (see tdse_instance_spec in include/tdse.h)."""
 
     def __init__(self, specs, stencil: int = 5, precision: str = "fp64"):
         specs = list(specs)

@@ -42,7 +42,8 @@ class tdse_instance_spec(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dr", ctypes.c_double), ("lmax", ctypes.c_int),
                 ("Z", ctypes.c_double), ("E0", ctypes.c_double), ("omega", ctypes.c_double),
                 ("ncycles", ctypes.c_double), ("cep", ctypes.c_double), ("krylov", ctypes.c_int),
-                ("dt", ctypes.c_double), ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("absorber_r", ctypes.c_double), ("r_b", ctypes.c_double),
+                ("gauge", ctypes.c_int), ("pulse_shape", ctypes.c_int)]
 
 
 class tdse_schedule(ctypes.Structure):

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "tdse_internal.cuh"
+#include "tdse_pulse.h"
 
 using namespace tdse_dev;
 
@@ -301,48 +302,14 @@ int ensure_work(tdse *h, size_t nvec) {
   return TDSE_OK;
 }
 
-double field_at(const tdse *h, double t) {
-  if (h->E0 == 0.0 || h->omega <= 0.0) return 0.0;
-  const double T = 2.0 * M_PI * h->ncycles / h->omega;
-  if (t < 0.0 || t > T) return 0.0;
-  const double env = std::sin(M_PI * t / T);
-  if (h->pulse_shape == TDSE_PULSE_SIN2_A) {
-    // A = -(c E0/omega) sin^2(W t) sin(omega t + cep), W = pi/T; E = -(1/c) dA/dt
-    const double W = M_PI / T, ph = h->omega * t + h->cep;
-    return h->E0 / h->omega * env * (h->omega * env * std::cos(ph) + 2.0 * W * std::cos(W * t) * std::sin(ph));
-  }
-  return h->E0 * env * env * std::sin(h->omega * t + h->cep);
-}
+PulseParams pulse_of(const tdse *h) { return PulseParams{h->E0, h->omega, h->ncycles, h->cep, h->pulse_shape}; }
 
-constexpr double kLightAU = 137.035999084;   // speed of light, atomic units
-
-// int_a^b E by 5-point Gauss-Legendre.
-double field_integral(const tdse *h, double a, double b) {
-  static const double node[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
-                                 0.9061798459386640};
-  static const double weight[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889,
-                                   0.4786286704993665, 0.2369268850561891};
-  const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
-  double acc = 0.0;
-  for (int k = 0; k < 5; ++k) acc += weight[k] * field_at(h, mid + half * node[k]);
-  return half * acc;
-}
+double field_at(const tdse *h, double t) { return pulse_field(pulse_of(h), t); }
 
 // A(t) = -c int_0^t E (Sec. 3): equal panels of [0, T], as few as keep them
 // at most 0.25 a.u. wide, each by 5-point Gauss, and the part of the panel
 // holding t; constant after the pulse.
-double vecpot_at(const tdse *h, double t) {
-  if (h->E0 == 0.0 || h->omega <= 0.0 || t <= 0.0) return 0.0;
-  const double T = 2.0 * M_PI * h->ncycles / h->omega;
-  const double tt = std::min(t, T);
-  const long panels = (long)std::ceil(T / 0.25);
-  const double w = T / (double)panels;
-  const long full = (long)std::floor(tt / w);
-  double acc = 0.0;
-  for (long k = 0; k < full && k < panels; ++k) acc += field_integral(h, (double)k * w, (double)(k + 1) * w);
-  if (full < panels && tt > (double)full * w) acc += field_integral(h, (double)full * w, tt);
-  return -kLightAU * acc;
-}
+double vecpot_at(const tdse *h, double t) { return pulse_vecpot(pulse_of(h), t); }
 
 // The coupling's time factor handed to the kernels: E(t), or A(t)/c in the velocity gauge.
 double coupling_at(const tdse *h, double t) {

@@ -29,6 +29,7 @@
 
 #include "tdse_device_common.cuh"
 #include "tdse_engine.h"
+#include "tdse_pulse.h"
 #include "tdse_internal.cuh"
 #include "tdse_stencil.cuh"
 
@@ -220,14 +221,15 @@ __device__ __forceinline__ StencilIn fp64_in(const BatchDev &B, const BatchInst 
   in.L = I.L;
   in.c1 = I.c1;
   in.c2 = I.c2;
-  in.E = field_of(B, inst);
+  in.E = field_of(B, inst);   // A/c for a velocity-gauge instance
   in.dscale = 1.0;
-  in.rinv = nullptr;   // the batch runs the length gauge
-  in.d1c = 0.0;
+  in.rinv = I.rinv;
+  in.d1c = I.d1c;
   return in;
 }
 
-template <int ST, int PF>
+// VG: the chunk list holds velocity-gauge instances only (a separate launch).
+template <int ST, int PF, bool VG = false>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     bt_lanczos_a_fp64(BatchDev B, ChunkList cl, int j) {
   for_my_chunks(cl, [&](int inst, int ci) {
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     const StencilIn in = scaled(fp64_in(B, I, inst, u), sig);
     double acc = 0.0;
     chunk_columns(I, ci, [&](int i, int l0, int l1) {
-      walk_rows<ST, PF, true>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
+      walk_rows<ST, PF, true, VG>(in, i, l0, l1, [&](int, size_t idx, double2 t, double2 uc) {
         double2 o;
         if (j > 0) {
           const double2 pv = up[idx];
@@ -672,7 +674,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, ref0, total;
+  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, ref0, rinv, total;
 };
 
 Layout layout_of(const tdse_instance_spec &s, int precision) {
@@ -702,16 +704,15 @@ Layout layout_of(const tdse_instance_spec &s, int precision) {
   L.kappaf = mixed ? take(4 * (Lp1 + 1)) : none;
   L.partial = take(8 * nchunk);
   L.ref0 = take(16 * N);
+  L.rinv = (!mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? take(8 * N) : none;
   L.total = off;
   return L;
 }
 
+// The coupling's time factor of an instance at t: E(t), or A(t)/c in the velocity gauge.
 double pulse_at(const tdse_instance_spec &s, double t) {
-  if (s.E0 == 0.0 || s.omega <= 0.0) return 0.0;
-  const double T = 2.0 * M_PI * s.ncycles / s.omega;
-  if (t < 0.0 || t > T) return 0.0;
-  const double env = std::sin(M_PI * t / T);
-  return s.E0 * env * env * std::sin(s.omega * t + s.cep);
+  const PulseParams p{s.E0, s.omega, s.ncycles, s.cep, s.pulse_shape};
+  return s.gauge == TDSE_GAUGE_VELOCITY ? pulse_vecpot(p, t) / kLightAU : pulse_field(p, t);
 }
 
 ChunkList list_at(const int *base, int off, int nact, int total) {
@@ -741,6 +742,9 @@ bool valid_spec(const tdse_instance_spec &s) {
       !std::isfinite(s.cep) || !std::isfinite(s.absorber_r) || !std::isfinite(s.r_b))
     return false;
   if (s.E0 != 0.0 && (!(s.omega > 0.0) || !(s.ncycles > 0.0))) return false;
+  if ((s.gauge != TDSE_GAUGE_LENGTH && s.gauge != TDSE_GAUGE_VELOCITY) ||
+      (s.pulse_shape != TDSE_PULSE_SIN2_E && s.pulse_shape != TDSE_PULSE_SIN2_A))
+    return false;
   // segment and chunk indices are 32-bit in the kernels
   const long long nseg = (long long)((s.N + 31) / 32) * (s.lmax + 1);
   if (nseg > (1LL << 30) || (long long)s.N * (s.lmax + 1) >= (1LL << 31)) return false;
@@ -834,6 +838,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
     return fail(TDSE_ERR_ARG, "bad slot or unaligned instance memory");
   if (!valid_spec(s)) return fail(TDSE_ERR_ARG, "invalid instance spec");
   const bool mixed = precision == TDSE_MIXED;
+  if (mixed && s.gauge == TDSE_GAUGE_VELOCITY) return fail(TDSE_ERR_ARG, "the velocity gauge runs in FP64 batches only");
   const Layout Lo = layout_of(s, precision);
   char *base = static_cast<char *>(mem);
   const int N = s.N, L = s.lmax;
@@ -862,6 +867,9 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.kappa = reinterpret_cast<double *>(base + Lo.kappa);
   I.partial = reinterpret_cast<double *>(base + Lo.partial);
   I.ref0 = reinterpret_cast<double2 *>(base + Lo.ref0);
+  I.gauge = s.gauge;
+  I.d1c = (stencil == 5) ? 1.0 / (12.0 * s.dr) : 1.0 / (2.0 * s.dr);
+  I.rinv = (!mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? reinterpret_cast<double *>(base + Lo.rinv) : nullptr;
   if (mixed) {
     I.diagf = reinterpret_cast<float *>(base + Lo.diagf);
     I.hi = reinterpret_cast<float2 *>(base + Lo.hi);
@@ -910,6 +918,12 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   EN_CUDA(cudaMemcpyAsync((void *)I.rj, rj.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "r table");
   EN_CUDA(cudaMemcpyAsync((void *)I.mask, msk.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "mask");
   EN_CUDA(cudaMemcpyAsync((void *)I.kappa, kap.data(), sizeof(double) * (L + 2), cudaMemcpyHostToDevice, st), "kappa");
+  std::vector<double> ri;
+  if (I.rinv) {
+    ri.resize(N);
+    for (int j = 0; j < N; ++j) ri[j] = 1.0 / rj[j];
+    EN_CUDA(cudaMemcpyAsync((void *)I.rinv, ri.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "1/r table");
+  }
   if (mixed) {
     std::vector<float> df(G), rf(N), kf(L + 2);
     for (int l = 0; l <= L; ++l) {
@@ -1137,6 +1151,16 @@ void launch_a_st(bool mixed, int pf, unsigned grid, cudaStream_t st, const Batch
   }
 }
 
+template <int ST>
+void launch_a_vg_st(int pf, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  switch (pf) {
+    case 0: bt_lanczos_a_fp64<ST, 0, true><<<grid, kBlockJ, 0, st>>>(B, cl, j); break;
+    case 3: bt_lanczos_a_fp64<ST, 3, true><<<grid, kBlockJ, 0, st>>>(B, cl, j); break;
+    case 10: bt_lanczos_a_fp64<ST, 10, true><<<grid, kBlockJ, 0, st>>>(B, cl, j); break;
+    default: bt_lanczos_a_fp64<ST, 6, true><<<grid, kBlockJ, 0, st>>>(B, cl, j); break;
+  }
+}
+
 }  // namespace
 
 void Engine::drop_graphs() {
@@ -1162,16 +1186,25 @@ void Engine::build_segment(Segment &sg, const std::vector<int> &act) {
   sg.maxm = 0;
   for (int s : act) sg.maxm = std::max(sg.maxm, spec[s].krylov);
   for (int j = 0; j <= sg.maxm; ++j) {
-    std::vector<int> ph;
+    // the stencil kernel is launched once per gauge; the elementwise ones once
+    std::vector<int> ph, ph_len, ph_vel;
     for (int s : act)
-      if (j == 0 || spec[s].krylov > j) ph.push_back(s);
-    int off = 0, eoff = 0;
-    const int tot = launch_lists(ph, false, off);
+      if (j == 0 || spec[s].krylov > j) {
+        ph.push_back(s);
+        (spec[s].gauge == TDSE_GAUGE_VELOCITY ? ph_vel : ph_len).push_back(s);
+      }
+    int off = 0, voff = 0, eoff = 0;
+    const int tot = launch_lists(ph_len, false, off);
+    const int vtot = ph_vel.empty() ? 0 : launch_lists(ph_vel, false, voff);
     const int etot = launch_lists(ph, true, eoff);
     sg.off.push_back(off);
-    sg.nact.push_back((int)ph.size());
+    sg.nact.push_back((int)ph_len.size());
     sg.total.push_back(tot);
+    sg.voff.push_back(voff);
+    sg.vnact.push_back((int)ph_vel.size());
+    sg.vtotal.push_back(vtot);
     sg.eoff.push_back(eoff);
+    sg.enact.push_back((int)ph.size());
     sg.etotal.push_back(etot);
   }
 }
@@ -1227,6 +1260,15 @@ int Engine::launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedu
   return TDSE_OK;
 }
 
+// Velocity-gauge instances (FP64 only): the same kernel with the (A/c) p_z coupling.
+int Engine::launch_a_velocity(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s) {
+  const unsigned grid = (unsigned)(sms * s.sblocks);
+  if (stencil == 5) launch_a_vg_st<5>(s.pf, grid, stream, B, cl, j);
+  else launch_a_vg_st<3>(s.pf, grid, stream, B, cl, j);
+  EN_CUDA(cudaGetLastError(), "batch lanczos a (velocity gauge)");
+  return TDSE_OK;
+}
+
 int Engine::launch_b(const BatchDev &B, const ChunkList &cn, int j, const Schedule &s) {
   const unsigned grid = (unsigned)(sms * s.eblocks);
   if (precision == TDSE_MIXED) {
@@ -1243,17 +1285,26 @@ int Engine::launch_b(const BatchDev &B, const ChunkList &cn, int j, const Schedu
 int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
   count = 0;
   int rc;
-  const ChunkList all = list_at(lists, sg.eoff[0], sg.nact[0], sg.etotal[0]);
+  const ChunkList all = list_at(lists, sg.eoff[0], sg.enact[0], sg.etotal[0]);
   for (int j = 0; j < sg.maxm; ++j) {
     const ChunkList cl = list_at(lists, sg.off[j], sg.nact[j], sg.total[j]);
-    if (cl.total == 0) break;
-    cudaEvent_t pa = prof_begin(TDSE_K_LANCZOS_A);
-    if ((rc = launch_a(B, cl, j, sched))) return rc;
-    prof_end(pa);
-    ++count;
+    if (cl.total == 0 && sg.vtotal[j] == 0) break;
+    if (cl.total > 0) {
+      cudaEvent_t pa = prof_begin(TDSE_K_LANCZOS_A);
+      if ((rc = launch_a(B, cl, j, sched))) return rc;
+      prof_end(pa);
+      ++count;
+    }
+    if (sg.vtotal[j] > 0) {
+      const ChunkList vl = list_at(lists, sg.voff[j], sg.vnact[j], sg.vtotal[j]);
+      cudaEvent_t pv = prof_begin(TDSE_K_LANCZOS_A);
+      if ((rc = launch_a_velocity(B, vl, j, sched))) return rc;
+      prof_end(pv);
+      ++count;
+    }
     // U_{j+1} only for the instances that go on to iteration j + 1
     if (j + 1 < sg.maxm && sg.etotal[j + 1] > 0) {
-      const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.nact[j + 1], sg.etotal[j + 1]);
+      const ChunkList cn = list_at(lists, sg.eoff[j + 1], sg.enact[j + 1], sg.etotal[j + 1]);
       cudaEvent_t pb = prof_begin(TDSE_K_LANCZOS_B);
       if ((rc = launch_b(B, cn, j, sched))) return rc;
       prof_end(pb);
@@ -1423,7 +1474,7 @@ int Engine::autotune(const std::vector<int> &slots) {
   // their scalars), so timing them leaves the state untouched
   const ChunkList a0 = list_at(lists, sg.off[0], sg.nact[0], sg.total[0]);
   const bool have_b = sg.maxm > 1 && sg.etotal[1] > 0;
-  const ChunkList b0 = have_b ? list_at(lists, sg.eoff[1], sg.nact[1], sg.etotal[1]) : a0;
+  const ChunkList b0 = have_b ? list_at(lists, sg.eoff[1], sg.enact[1], sg.etotal[1]) : a0;
   auto time_it = [&](auto &&launch, float &best) -> int {
     best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -1461,6 +1512,11 @@ int Engine::autotune(const std::vector<int> &slots) {
           bestS.sblocks = sb;
         }
       }
+  if (!rc && sg.vtotal[0] > 0) {
+    // the velocity-gauge instances' phase-0 z, which lanczos_b below reads
+    const ChunkList v0 = list_at(lists, sg.voff[0], sg.vnact[0], sg.vtotal[0]);
+    rc = launch_a_velocity(B, v0, 0, sched);
+  }
   if (!rc && have_b) {
     // lanczos_b at phase 0 reads z from the last A launch above
     for (int eb = 1; eb <= kElemBlocksPerSM && !rc; ++eb) {

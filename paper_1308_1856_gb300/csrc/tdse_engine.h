@@ -27,8 +27,10 @@ struct BatchInst {
   int nseg;              // 32-point row segments
   int nchunk;            // reduction chunks of the stencil kernels (row segments)
   int nchunk_e;          // reduction chunks of the elementwise kernels (consecutive points)
-  int pad;
+  int gauge;             // TDSE_GAUGE_LENGTH or TDSE_GAUGE_VELOCITY (FP64 only)
   double c1, c2;         // stencil coefficients (c0 is folded into diag)
+  double d1c;            // first-derivative scale of the velocity gauge (1/(12 dr) or 1/(2 dr))
+  const double *rinv;    // 1/r_j (velocity gauge; null otherwise)
   double2 *psi;          // (L+1) x N state, l-major
   const double *diag;    // FP64: c0 + l(l+1)/(2 r^2) - Z/r
   const float *diagf;    // mixed: l(l+1)/(2 r^2) - Z/r (difference-form stencil)
@@ -55,7 +57,8 @@ struct BatchDev {
   LanczosScalars *ls;
   unsigned *ticket;      // per-slot arrival counters (zero between launches)
   int *status;
-  const double *E;       // field table of the run: E[n * cap + slot] at step n's mid-point
+  const double *E;       // coupling table of the run: E[n * cap + slot] at step n's mid-point
+                         // (the field, or A/c for a velocity-gauge instance)
   const int *step;       // step of the run being computed (device counter, so one
                          // captured step graph serves every step of a segment)
   int cap;
@@ -134,13 +137,16 @@ class Engine {
   struct Segment {
     long n0, n1;
     int maxm;
-    std::vector<int> off, nact, total, eoff, etotal;
+    std::vector<int> off, nact, total;      // stencil lists of the length-gauge instances
+    std::vector<int> voff, vnact, vtotal;   // stencil lists of the velocity-gauge instances
+    std::vector<int> eoff, enact, etotal;   // elementwise lists of every instance
   };
   void build_segment(Segment &sg, const std::vector<int> &act);
   BatchDev device_view() const;
   int upload_run(size_t nE);
   int norm_pass(const BatchDev &B, const std::vector<int> &ids, int off, int total);
   int launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
+  int launch_a_velocity(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
   int launch_b(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
   int enqueue_step(const BatchDev &B, const Segment &sg, int &count);
   void drop_graphs();

@@ -75,7 +75,7 @@ def test_server_arguments_rejected_without_touching_the_device(lib):
 
 def _spec(**kw):
     d = dict(N=1000, dr=0.1, lmax=15, Z=1.0, E0=0.05, omega=0.057, ncycles=2.0, cep=0.0, krylov=12,
-             dt=0.02, absorber_r=50.0, r_b=10.0)
+             dt=0.02, absorber_r=50.0, r_b=10.0, gauge=0, pulse_shape=0)
     d.update(kw)
     return B.tdse_instance_spec(*[d[f] for f, _ in B.tdse_instance_spec._fields_])
 
@@ -95,8 +95,17 @@ def test_server_instance_bytes(lib):
         s = _spec(N=N, lmax=L, krylov=m)
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == fp64
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_MIXED) == mixed
+    # a velocity-gauge instance also keeps 1/r (FP64)
+    for N, L, m in [(1000, 15, 12), (33, 0, 1)]:
+        G = N * (L + 1)
+        nchunk = max(-(-((N + 31) // 32) * (L + 1) // 64), -(-G // 2048))
+        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(16 * N)
+        s = _spec(N=N, lmax=L, krylov=m, gauge=1)
+        assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == common + up(8 * G) + up(16 * G * m) + up(8 * N)
     bad = _spec(krylov=0)
     assert B.tdse_server_instance_bytes(ctypes.byref(bad), B.TDSE_FP64) == 0
+    assert B.tdse_server_instance_bytes(ctypes.byref(_spec(gauge=2)), B.TDSE_FP64) == 0
+    assert B.tdse_server_instance_bytes(ctypes.byref(_spec(pulse_shape=5)), B.TDSE_FP64) == 0
     assert B.tdse_server_instance_bytes(ctypes.byref(_spec(dt=-1.0)), B.TDSE_FP64) == 0
 
 

@@ -241,3 +241,48 @@ def test_full_batched_configuration_sampled(precision):
                                       precision="fld")
             floor = rel_l2(f64, fld)
             assert rel_l2(got[i], fld) <= 10 * max(floor, 1e-15), (i, err, rel_l2(got[i], fld), floor)
+
+
+VELOCITY_SPECS = [
+    dict(N=500, dr=0.2, lmax=4, krylov=12, dt=0.02, E0=0.0534, omega=0.057, ncycles=2, gauge="velocity"),
+    dict(N=129, dr=0.25, lmax=2, krylov=5, dt=0.02, E0=0.08, omega=0.2, ncycles=2, cep=0.4, shape="sin2_a"),
+    dict(N=1000, dr=0.1, lmax=15, krylov=16, dt=4e-4, E0=0.05, omega=0.057, ncycles=4, absorber_r=80.0,
+         gauge="velocity", shape="sin2_a"),
+    dict(N=64, dr=0.2, lmax=3, krylov=3, dt=0.005, E0=0.1, omega=0.3, ncycles=2),
+]
+
+
+def _oracle_run_general(s, nsteps):
+    g = oracle.Grid(N=s["N"], h=s["dr"], L=s["lmax"], stencil=5, Z=s.get("Z", 1.0),
+                    gauge=1 if s.get("gauge") == "velocity" else 0)
+    psi0 = W.hydrogen_1s(s["N"], s["dr"], s["lmax"])
+    pulse = oracle.Pulse(E0=s.get("E0", 0.0), omega=s.get("omega", 0.057), ncycles=s.get("ncycles", 2.0),
+                         cep=s.get("cep", 0.0), shape=1 if s.get("shape") == "sin2_a" else 0)
+    mask = oracle.Mask(s["absorber_r"]) if "absorber_r" in s else None
+    out, _ = oracle.propagate(g, psi0, "lanczos", s["krylov"], s["dt"], nsteps, pulse=pulse, mask=mask)
+    return out
+
+
+def test_batch_velocity_gauge_and_sinea_instances():
+    """A batch mixing length- and velocity-gauge instances and both pulse
+    shapes (the velocity-gauge stencil kernel runs as its own launch over its
+    own chunk list): every instance matches the oracle over 25 steps, and a
+    velocity-gauge instance alone equals itself in the mix bitwise."""
+    from paper_1308_1856_gb300 import Batch
+    nsteps = 25
+    b = Batch(VELOCITY_SPECS, precision="fp64")
+    b.propagate(10)          # one graph-replayed segment
+    b.propagate(nsteps - 10)
+    for i, s in enumerate(VELOCITY_SPECS):
+        got = b.get_state(i)
+        want = _oracle_run_general(s, nsteps)
+        assert rel_l2(got, want) <= 1e-10, (i, rel_l2(got, want))
+    mix0 = b.get_state(0)
+    b.close()
+    alone = Batch([VELOCITY_SPECS[0]], precision="fp64")
+    alone.propagate(10)
+    alone.propagate(nsteps - 10)
+    assert np.array_equal(alone.get_state(0), mix0)
+    alone.close()
+    with pytest.raises(Exception):
+        Batch([VELOCITY_SPECS[0]], precision="mixed")       # the velocity gauge runs in FP64 batches only
