@@ -68,3 +68,15 @@ def test_reference_arm_prints_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["unit"] == d["e2e"]["unit"] == d["cpu_baseline"]["unit"]
+
+
+def test_rk_step_flop_count():
+    """Per-point FP64 flops of one step through the general RK stage kernel:
+    s applications of H (23 each), the inner stages' sums (4 per term), the
+    last stage's two sums (one when the tableau is first-same-as-last) and
+    |Delta|^2, counted here term by term."""
+    import bench
+    assert bench.rk_step_flops_per_gp(1) == 23 + 8 + 4
+    assert bench.rk_step_flops_per_gp(4) == 4 * 23 + (4 + 8 + 12) + 8 * 4 + 4
+    assert bench.rk_step_flops_per_gp(7, fsal=True) == 7 * 23 + (4 + 8 + 12 + 16 + 20 + 24) + 4 * 7 + 4
+    assert bench.RK_STAGES["dormand_prince"] == 7 and bench.RK_FSAL == ("dormand_prince",)

@@ -67,3 +67,23 @@ def test_lanczos_zero_state_and_single_point():
     z, _ = oracle.propagate(oracle.Grid(N=7, h=0.2, L=2), np.zeros((3, 7), complex),
                             "lanczos", 4, 0.1, 1)
     assert np.all(z == 0)
+
+
+def test_rk_and_observable_degenerate_inputs():
+    """Zero steps leave the state and sigma at zero; a state in l = 0 alone
+    has no dipole, no dipole velocity and only the field term -E ||psi||^2 in
+    its acceleration (every pair sum over (l, l+1) vanishes); without angles
+    the flux returns no density, and a real state carries no current."""
+    g = oracle.Grid(N=50, h=0.2, L=3, stencil=5)
+    psi = np.zeros((4, 50), complex)
+    psi[0] = W.hydrogen_1s(50, 0.2, 3)[0]
+    out, sig = oracle.propagate_rk(g, psi, "dormand_prince", 0.01, 0)
+    assert np.array_equal(out, psi) and sig == 0.0
+    pulse = oracle.Pulse(E0=0.05, omega=0.3, ncycles=2)
+    t = 3.0
+    z, zdot, zddot = oracle.dipole_moments(g, psi, t, pulse)
+    norm = 0.2 * float(np.sum(np.abs(psi) ** 2))
+    assert z == 0.0 and zdot == 0.0
+    assert abs(zddot + oracle.field(pulse, t) * norm) <= 1e-15
+    tot, per = oracle.flux(g, psi, 5.0)
+    assert per.shape == (0,) and tot == 0.0      # a real state carries no current
