@@ -779,6 +779,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--e2e-groups", type=int, default=None,
+                    help="instance groups of the batched rows' pipelined copies in the end-to-end leg")
     ap.add_argument("--method", default="all", choices=["all", "taylor", "rk4", "lanczos"],
                     help="restrict to one propagator (profiling runs)")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed"],
@@ -802,6 +804,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-seed", type=int, default=1309)
     args = ap.parse_args()
+    if args.e2e_groups is not None:
+        globals()["E2E_GROUPS"] = max(1, args.e2e_groups)
     sched = {}
     for item in args.schedule:
         prec, vals = item.split("=")

@@ -468,11 +468,18 @@ int tdse_batch_propagate(tdse_batch_t *b, long nsteps);
 /*
  * Copy every state in, advance every instance by nsteps steps and copy every
  * state out, with the copies overlapping the compute (synchronous).  The
- * instances are cut into `groups` contiguous groups (with three or more, the
- * first and the last hold 1/(4 groups) of the points each, since only their
- * copies are not hidden, and the others share the rest equally); group g is
- * propagated once its input copy is done, and its output copy runs while
- * group g+1 computes, on two extra streams (one per copy direction).
+ * instances are cut into `groups` contiguous groups; group g is propagated
+ * once its input copy is done, and its output copy runs while group g+1
+ * computes, on two extra streams (one per copy direction).  Only the first
+ * group's input copy and the last group's output copy are then exposed, so
+ * the group sizes grow from the first group to the middle and shrink to the
+ * last by a factor r, the compute time of the call over its input copy time
+ * (r = 4 on a batch's first call; later calls take r from the previous call,
+ * timed with events, times nsteps; r is kept within [1, 64]).  Where the
+ * batch holds a wave per group, every group but a middle one is cut to a
+ * whole number of waves of the stencil kernels' persistent grid (one chunk
+ * of 64 row segments per warp), so that its launches end without a partial
+ * last wave.
  * The input copies start once the work already queued on the batch's stream
  * is done.  F_in / F_out: host buffers laid out as tdse_batch_set_states
  * (page-locked for the copies to overlap); either may be NULL.  The

@@ -29,6 +29,7 @@
 
 #include "tdse_device_common.cuh"
 #include "tdse_engine.h"
+#include "tdse_sched.h"
 #include "tdse_pulse.h"
 #include "tdse_internal.cuh"
 #include "tdse_stencil.cuh"
@@ -1583,12 +1584,15 @@ struct tdse_batch {
   long long npts = 0;
   // pipelined host I/O (tdse_batch_propagate_io): one stream per copy direction
   cudaStream_t io_in = nullptr, io_out = nullptr;
-  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> ev;    // ordering events
+  std::vector<cudaEvent_t> tev;   // timing events: the input copies, each group's compute
+  double io_ratio = 0.0;          // compute time of a point-step over its copy time (0: not yet measured)
   ~tdse_batch() {
     if (eng.stream) cudaStreamSynchronize(eng.stream);
     if (io_in) cudaStreamSynchronize(io_in);
     if (io_out) cudaStreamSynchronize(io_out);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : tev) cudaEventDestroy(e);
     if (io_in) cudaStreamDestroy(io_in);
     if (io_out) cudaStreamDestroy(io_out);
     cudaFree(mem);
@@ -1597,7 +1601,8 @@ struct tdse_batch {
 
 namespace {
 
-// Streams and 2 * groups + 1 events of the pipelined I/O, created once.
+// Streams, 2 * groups + 1 ordering events and 2 * groups + 2 timing events of
+// the pipelined I/O, created once.
 int io_ready(tdse_batch *b, int groups) {
   Engine &e = b->eng;
   if (!b->io_in && cudaStreamCreateWithFlags(&b->io_in, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1618,8 +1623,21 @@ int io_ready(tdse_batch *b, int groups) {
     }
     b->ev.push_back(ev);
   }
+  while ((int)b->tev.size() < 2 * groups + 2) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      cudaGetLastError();
+      return e.fail(TDSE_ERR_CUDA, "I/O timing events");
+    }
+    b->tev.push_back(ev);
+  }
   return TDSE_OK;
 }
+
+// Taper ratio of the first pipelined call of a batch, before any measurement:
+// compute of a point-step over its one-way copy time, between the two
+// precisions' measured values on the benchmark's batch (about 2 mixed, 7 FP64).
+constexpr double kIoRatioFirst = 4.0;
 
 }  // namespace
 
@@ -1722,30 +1740,25 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
   if (groups > b->count) groups = b->count;
   int rc = io_ready(b, groups);
   if (rc) return rc;
-  // contiguous groups; each instance's offset in the host buffers.  Only the
-  // first group's input copy and the last group's output copy are not hidden
-  // behind compute, so with three or more groups those two get 1/(4 groups)
-  // of the points each and the middle groups share the rest equally.
-  std::vector<size_t> off(b->count + 1, 0);
-  for (int i = 0; i < b->count; ++i) off[i + 1] = off[i] + 2 * (size_t)e.hinst[i].N * (e.hinst[i].L + 1);
-  const double total = (double)off[b->count];
-  std::vector<double> cut(groups + 1, 0.0);
-  const double edge = groups >= 3 ? 1.0 / (4.0 * groups) : 1.0 / groups;
-  for (int g = 1; g < groups; ++g)
-    cut[g] = (groups >= 3) ? edge + (1.0 - 2.0 * edge) * (double)(g - 1) / (double)(groups - 2) : (double)g / groups;
-  std::vector<int> first(groups + 1, b->count);
-  first[0] = 0;
-  for (int g = 1, i = 0; g < groups; ++g) {
-    const double target = cut[g] * total;
-    while (i < b->count && (double)off[i] < target) ++i;
-    first[g] = std::max(i, first[g - 1] + 1 <= b->count ? first[g - 1] + 1 : b->count);
+  // each instance's offset in the host buffers (in doubles) and in stencil
+  // chunks; contiguous groups (tdse_sched::io_groups) tapered by the compute /
+  // copy time ratio that the previous call measured, in whole waves of the
+  // stencil grid's warps (one chunk per warp and wave) where the batch allows
+  std::vector<size_t> off(b->count + 1, 0), coff(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) {
+    off[i + 1] = off[i] + 2 * (size_t)e.hinst[i].N * (e.hinst[i].L + 1);
+    coff[i + 1] = coff[i] + (size_t)e.hinst[i].nchunk;
   }
+  const double ratio = (b->io_ratio > 0.0) ? b->io_ratio * (double)std::max(nsteps, 1L) : kIoRatioFirst;
+  const size_t wave = (size_t)e.sms * (size_t)e.sched.sblocks * (kBlockJ / 32);
+  const std::vector<int> first = tdse_sched::io_groups(coff, groups, ratio, wave);
   auto bytes = [&](int i) { return sizeof(double) * (off[i + 1] - off[i]); };
   // every input copy first, in group order on the input stream, after the
   // work already queued on the compute stream (it may still write the states)
   if (F_in) {
     if (cudaEventRecord(b->ev[2 * groups], e.stream) != cudaSuccess ||
-        cudaStreamWaitEvent(b->io_in, b->ev[2 * groups], 0) != cudaSuccess)
+        cudaStreamWaitEvent(b->io_in, b->ev[2 * groups], 0) != cudaSuccess ||
+        cudaEventRecord(b->tev[0], b->io_in) != cudaSuccess)
       return e.fail(TDSE_ERR_CUDA, "order input copies");
     for (int g = 0; g < groups; ++g) {
       for (int i = first[g]; i < first[g + 1]; ++i) {
@@ -1755,6 +1768,7 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
       }
       if (cudaEventRecord(b->ev[2 * g], b->io_in) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "input event");
     }
+    if (cudaEventRecord(b->tev[1], b->io_in) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "input event");
   }
   // group g computes once its input is in; its output copy waits for it and
   // overlaps the next group's compute
@@ -1763,8 +1777,10 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
       return e.fail(TDSE_ERR_CUDA, "wait input");
     std::vector<int> slots;
     for (int i = first[g]; i < first[g + 1]; ++i) slots.push_back(i);
+    if (cudaEventRecord(b->tev[2 + 2 * g], e.stream) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "timing event");
     rc = e.run(slots, std::vector<long>(slots.size(), nsteps));
     if (rc) return rc;
+    if (cudaEventRecord(b->tev[3 + 2 * g], e.stream) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "timing event");
     if (F_out) {
       if (cudaEventRecord(b->ev[2 * g + 1], e.stream) != cudaSuccess ||
           cudaStreamWaitEvent(b->io_out, b->ev[2 * g + 1], 0) != cudaSuccess)
@@ -1777,6 +1793,18 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
   if (cudaStreamSynchronize(b->io_in) != cudaSuccess || cudaStreamSynchronize(e.stream) != cudaSuccess ||
       cudaStreamSynchronize(b->io_out) != cudaSuccess)
     return e.fail(TDSE_ERR_CUDA, "sync I/O");
+  // the ratio for the next call: compute time of every group over the copy
+  // time of every input, per step
+  if (F_in && nsteps > 0) {
+    float t_in = 0.f, t_c = 0.f, t = 0.f;
+    bool ok = cudaEventElapsedTime(&t_in, b->tev[0], b->tev[1]) == cudaSuccess;
+    for (int g = 0; ok && g < groups; ++g) {
+      ok = cudaEventElapsedTime(&t, b->tev[2 + 2 * g], b->tev[3 + 2 * g]) == cudaSuccess;
+      t_c += t;
+    }
+    if (!ok) cudaGetLastError();
+    else if (t_in > 0.f && t_c > 0.f) b->io_ratio = (double)t_c / ((double)t_in * (double)nsteps);
+  }
   return TDSE_OK;
 }
 

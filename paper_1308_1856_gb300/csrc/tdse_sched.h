@@ -1,6 +1,8 @@
 // Host-only scheduling logic of the server: an arena allocator over one block
-// of device memory and the continuous-batching request scheduler.  Plain
-// C++17 with no CUDA dependency, so that it is exercised on a CPU as well.
+// of device memory and the continuous-batching request scheduler; and the
+// group cut of the batch engine's pipelined copy-in / propagate / copy-out.
+// Plain C++17 with no CUDA dependency, so that it is exercised on a CPU as
+// well.
 //
 // Request lifecycle: submitted -> queued (FIFO) -> admitted (a slot and an
 // arena range; its instance is placed on the device) -> running (advanced in
@@ -13,6 +15,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <deque>
@@ -250,5 +253,82 @@ class Scheduler {
   std::map<long long, Request> reqs_;
   long long finished_total_ = 0;
 };
+
+// Cut `count` instances into contiguous groups for a pipelined copy-in /
+// propagate / copy-out, in which group g+1's input copy runs while group g
+// computes and group g's output copy while group g+1 computes.  Only the
+// first group's input copy and the last group's output copy are then
+// exposed, and group g+1's input copy stays hidden while it is at most r
+// times group g's work, where r is the compute time of a unit of work over
+// its copy time (one direction).  The target sizes therefore grow by r from
+// the first group to the middle and shrink by r to the last:
+// w_g = r^min(g, G-1-g).  r is clamped to [1, 64] (a non-finite r counts as
+// 1); r = 1 gives equal groups.  off[i] is instance i's first unit
+// (off[count] = the total).  Returns first[0..G]: group g holds instances
+// [first[g], first[g+1]); G is `groups` clamped to [1, count], and every
+// group is non-empty.
+//
+// quantum = 0: each cut sits at the instance boundary nearest its target.
+// quantum = q > 0: a group's work runs in waves of q units (one unit per warp
+// of a persistent grid), so a group of k q + 1 units takes k + 1 waves.  When
+// the total holds at least one wave per group, the groups of the first half
+// are then cut to at most a whole number of waves each (the nearest whole
+// number to the target, at least one), walking forward from the first
+// instance, and those of the second half likewise walking back from the
+// last; the middle group (the one after cut G/2) takes the fraction.
+inline std::vector<int> io_groups(const std::vector<size_t> &off, int groups, double r, size_t quantum = 0) {
+  const int count = (int)off.size() - 1;
+  std::vector<int> first;
+  if (count < 1) return first;
+  const int G = std::max(1, std::min(groups, count));
+  if (!std::isfinite(r) || r < 1.0) r = 1.0;
+  if (r > 64.0) r = 64.0;
+  std::vector<double> w(G), target(G + 1, 0.0);
+  double wsum = 0.0;
+  for (int g = 0; g < G; ++g) {
+    w[g] = std::pow(r, (double)std::min(g, G - 1 - g));
+    wsum += w[g];
+  }
+  const double total = (double)off[count];
+  double acc = 0.0;
+  for (int g = 1; g < G; ++g) {
+    acc += w[g - 1];
+    target[g] = total * acc / wsum;
+  }
+  first.assign(G + 1, count);
+  first[0] = 0;
+  const double q = (double)quantum;
+  if (quantum == 0 || total < q * G) {
+    for (int g = 1; g < G; ++g) {
+      const int lo = first[g - 1] + 1, hi = count - (G - g);
+      int i = lo;
+      while (i < hi && (double)off[i + 1] <= target[g]) ++i;
+      // off[i] <= target < off[i + 1] unless clamped: take the nearer boundary
+      if (i < hi && target[g] - (double)off[i] > (double)off[i + 1] - target[g]) ++i;
+      first[g] = i;
+    }
+    return first;
+  }
+  const int h = G / 2;
+  for (int g = 1; g <= h; ++g) {   // forward: group g-1 gets at most k whole waves
+    const int lo = first[g - 1] + 1, hi = count - (G - g);
+    const double start = (double)off[first[g - 1]];
+    const double k = std::max(1.0, std::floor((target[g] - start) / q + 0.5));
+    const double t = start + k * q;
+    int i = lo;
+    while (i < hi && (double)off[i + 1] <= t) ++i;   // the last boundary <= t (lo if none)
+    first[g] = i;
+  }
+  for (int g = G - 1; g > h; --g) {   // backward: group g gets at most k whole waves
+    const int lo = first[h] + (g - h), hi = first[g + 1] - 1;
+    const double end = (double)off[first[g + 1]];
+    const double k = std::max(1.0, std::floor((end - target[g]) / q + 0.5));
+    const double t = end - k * q;
+    int i = hi;
+    while (i > lo && (double)off[i - 1] >= t) --i;   // the first boundary >= t (hi if none)
+    first[g] = i;
+  }
+  return first;
+}
 
 }  // namespace tdse_sched

@@ -158,7 +158,8 @@ def test_batch_propagate_io_equals_the_separate_calls(precision, groups, nsteps)
     """States in, nsteps steps and states out with the copies overlapping the
     compute give bitwise what set_states + propagate + get_states give, from
     page-locked and from ordinary host buffers; without an input buffer the
-    call continues from the device states."""
+    call continues from the device states; a later call, whose groups are
+    tapered by the compute / copy ratio the first call measured, too."""
     import torch
     from paper_1308_1856_gb300 import Batch
     ref = Batch(SPECS, precision=precision)
@@ -169,6 +170,9 @@ def test_batch_propagate_io_equals_the_separate_calls(precision, groups, nsteps)
     want = ref.get_states()
     ref.propagate(nsteps)
     want2 = ref.get_states()
+    ref.set_states_ptr(start.ctypes.data)
+    ref.propagate(nsteps)
+    want3 = ref.get_states()
     ref.close()
 
     def fresh():
@@ -185,6 +189,8 @@ def test_batch_propagate_io_equals_the_separate_calls(precision, groups, nsteps)
         assert np.array_equal(dst.numpy().view(np.complex128), want), pinned
         b.propagate_io(None, dst.data_ptr(), nsteps, groups)
         assert np.array_equal(dst.numpy().view(np.complex128), want2), pinned
+        b.propagate_io(src.data_ptr(), dst.data_ptr(), nsteps, groups)
+        assert np.array_equal(dst.numpy().view(np.complex128), want3), pinned
         b.close()
     # input only, then read back with the plain call
     b = fresh()

@@ -5,7 +5,9 @@ seeded random scenarios.  The allocator is compared with an independent
 first-fit model written from its definition (lowest-offset free range that
 fits; freed ranges merge with free neighbours); the scheduler is checked
 against its contract (FIFO admission, budget and slot limits, min(k, left)
-steps per batch, every request finishing, memory returned on release)."""
+steps per batch, every request finishing, memory returned on release).  The
+group cut of the batch engine's pipelined copy-in / propagate / copy-out
+(io_groups) is compared with a model written from its definition."""
 import os
 import shutil
 import subprocess
@@ -47,6 +49,10 @@ int main() {
     else if (cmd == "pollrel") { auto f = s.poll(); std::cout << f.size();
       for (auto x : f) { std::cout << " " << x; s.release(x); } std::cout << "\n"; }
     else if (cmd == "rel") { long long id; std::cin >> id; std::cout << s.release(id) << "\n"; }
+    else if (cmd == "cut") { int n, g; double r; size_t qu; std::cin >> n >> g >> r >> qu;
+      std::vector<size_t> off(n + 1); for (auto &x : off) std::cin >> x;
+      auto f = io_groups(off, g, r, qu); std::cout << f.size();
+      for (auto x : f) std::cout << " " << x; std::cout << "\n"; }
     else if (cmd == "q") { std::cout << s.queued() << " " << s.running() << " " << s.resident() << " "
       << s.arena().in_use() << " " << s.finished_total() << "\n"; }
   }
@@ -244,3 +250,87 @@ def test_scheduler_releases_and_head_of_line(driver):
     q = _parse_ints(out[16])
     assert q[:4] == [0, 0, 0, 0]
     assert out[17] == "-2"
+
+
+def _cut(driver, sizes, groups, r, quantum=0):
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    cmd = f"cut {len(sizes)} {groups} {r!r} {quantum} " + " ".join(map(str, off))
+    line = Session(driver, 1024, 256, 1).run([cmd])[0]
+    v = _parse_ints(line)
+    assert v[0] == len(v) - 1
+    return v[1:]
+
+
+def _cut_model(sizes, groups, r, quantum=0):
+    """The cut from its definition.  Weights r^min(g, G-1-g), r clamped to
+    [1, 64].  Without a quantum, each cut at the instance boundary nearest
+    its target point (the lower one on a tie) among those that leave every
+    group an instance.  With a quantum q (and at least q per group): the
+    first G//2 groups, forward, and the groups after the middle one,
+    backward, each get at most the whole number of waves nearest their
+    target (at least one), i.e. the farthest feasible boundary within it."""
+    n = len(sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(float)
+    G = max(1, min(groups, n))
+    r = min(max(r, 1.0), 64.0)
+    w = [r ** min(g, G - 1 - g) for g in range(G)]
+    target = [0.0] + [off[n] * sum(w[:g]) / sum(w) for g in range(1, G)]
+    first = [0] * G + [n]
+    if quantum == 0 or off[n] < quantum * G:
+        for g in range(1, G):
+            lo, hi = first[g - 1] + 1, n - (G - g)
+            first[g] = min(range(lo, hi + 1), key=lambda i: (abs(off[i] - target[g]), i))
+        return first
+    h = G // 2
+    for g in range(1, h + 1):
+        lo, hi = first[g - 1] + 1, n - (G - g)
+        start = off[first[g - 1]]
+        t = start + max(1.0, np.floor((target[g] - start) / quantum + 0.5)) * quantum
+        ok = [i for i in range(lo, hi + 1) if off[i] <= t]
+        first[g] = max(ok) if ok else lo
+    for g in range(G - 1, h, -1):
+        lo, hi = first[h] + (g - h), first[g + 1] - 1
+        end = off[first[g + 1]]
+        t = end - max(1.0, np.floor((end - target[g]) / quantum + 0.5)) * quantum
+        ok = [i for i in range(lo, hi + 1) if off[i] >= t]
+        first[g] = min(ok) if ok else hi
+    return first
+
+
+def test_io_groups_taper(driver):
+    """Equal groups at r = 1; the benchmark's FP64 taper (1, 7, 7, 1)/16 at
+    r = 7; r clamped to [1, 64]; more groups than instances, and fewer than one."""
+    assert _cut(driver, [5] * 12, 4, 1.0) == [0, 3, 6, 9, 12]
+    assert _cut(driver, [1] * 16, 4, 7.0) == [0, 1, 8, 15, 16]
+    assert _cut(driver, [1] * 130, 4, 1000.0) == [0, 1, 65, 129, 130]
+    assert _cut(driver, [1] * 12, 4, 0.5) == [0, 3, 6, 9, 12]
+    assert _cut(driver, [1] * 12, 4, -3.0) == [0, 3, 6, 9, 12]
+    assert _cut(driver, [4, 9, 2], 7, 3.0) == [0, 1, 2, 3]
+    assert _cut(driver, [4, 9, 2], 0, 3.0) == [0, 3]
+    assert _cut(driver, [1] * 6, 5, 2.0) == [0, 1, 2, 4, 5, 6]
+
+
+def test_io_groups_whole_waves(driver):
+    """With a wave of 10 units: the edge groups and the first middle group
+    get whole waves and the other middle group the fraction; a total below
+    one wave per group falls back to the nearest boundaries."""
+    assert _cut(driver, [1] * 100, 4, 7.0, 10) == [0, 10, 50, 90, 100]
+    assert _cut(driver, [1] * 105, 4, 7.0, 10) == [0, 10, 50, 95, 105]
+    assert _cut(driver, [3] * 35, 4, 7.0, 10) == [0, 3, 16, 32, 35]      # at most k waves each
+    assert _cut(driver, [1] * 30, 4, 7.0, 10) == _cut(driver, [1] * 30, 4, 7.0)
+    assert _cut(driver, [1] * 40, 2, 5.0, 10) == [0, 20, 40]            # two groups: halves
+    assert _cut(driver, [1] * 40, 3, 5.0, 10) == [0, 10, 30, 40]
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_io_groups_matches_model(driver, seed):
+    """Random instance sizes, group counts and ratios: contiguous non-empty
+    groups covering every instance, each cut where the model puts it."""
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        n = int(rng.integers(1, 40))
+        sizes = rng.integers(1, 100000, size=n).tolist()
+        groups = int(rng.integers(1, 10))
+        r = float(rng.uniform(0.5, 80.0))
+        quantum = int(rng.choice([0, 1000, 50000, 200000]))
+        got = _cut(driver, sizes, groups, r, quantum)
+        assert got == _cut_model(sizes, groups, r, quantum), (sizes, groups, r, quantum)
+        assert got[0] == 0 and got[-1] == n and all(a < b for a, b in zip(got, got[1:]))
