@@ -367,17 +367,25 @@ def check_imaginary_time_ground_state(prec="f64"):
     """From the 1s start state, imaginary-time Lanczos converges to the
     lowest eigenvalue of the l = 0 block (banded eigensolver) and reaches
     the paper's printed ground-state energies (near -0.47 without, near -0.5
-    with the -0.02 offset) [Sec. 6, Example 1]."""
+    with the -0.02 offset) [Sec. 6, Example 1].  Its radial density is a
+    poor match to the analytic 4 r^2 exp(-2 r) without the offset and a much
+    closer one with it [Sec. 6, Example 1 and its 1s radial-probability
+    figure]: here an L2 distance above 0.02, and at least 5 times smaller."""
     pv = paper_values()
+    dist = {}
     for key in ("ground_state_no_offset", "ground_state_offset"):
         e = pv[key]
         g = Grid(N=500, h=e["dr"], L=0, stencil=e["stencil"], offset=e["offset"], Z=1.0)
         r = g.r()
         psi = (2 * r * np.exp(-r)).astype(complex).reshape(1, -1)
-        _, E = oracle.propagate_imag(g, psi, "lanczos", 12, 0.5, 100, precision=prec)
+        st, E = oracle.propagate_imag(g, psi, "lanczos", 12, 0.5, 100, precision=prec)
         low = _lowest(g, 0, prec)[0]
         assert abs(E - low) <= 1e-11, (key, E, low)
         assert abs(E - e["energy"]) <= e["tolerance"], (key, E)
+        rho = np.abs(np.asarray(st, dtype=complex)[0]) ** 2
+        dist[key] = np.sqrt(g.h * np.sum((rho - 4 * r ** 2 * np.exp(-2 * r)) ** 2))
+    assert dist["ground_state_no_offset"] > 0.02, dist
+    assert dist["ground_state_offset"] * 5 < dist["ground_state_no_offset"], dist
 
 
 C_AU = 137.035999084   # speed of light, atomic units (CODATA 2018)
