@@ -48,6 +48,29 @@ def test_imag_ground_state_energy():
     assert rel_l2(state, want) <= 1e-10
 
 
+def test_imag_ground_state_with_offset():
+    """Diff2 of Sec. 6, Example 1: with the inner boundary moved by -0.02 a.u.
+    imaginary-time Lanczos from the 1s state reaches about -0.5 a.u.; the
+    energy and the state equal the oracle's, and the density is much closer
+    to the analytic 4 r^2 exp(-2 r) than without the offset."""
+    N, dr, off = 500, 0.2, -0.02
+    dist = []
+    for o in (0.0, off):
+        t = make(N, dr, 0, 5, offset=o)
+        psi0 = W.hydrogen_1s(N, dr, 0, o)
+        t.set_state(psi0)
+        e = t.propagate_imag("lanczos", 12, 0.5, 100)
+        state = t.get_state()
+        t.close()
+        want, e_orc = oracle.propagate_imag(grid_of(N, dr, 0, 5, offset=o), psi0, "lanczos", 12, 0.5, 100)
+        assert abs(e - e_orc) <= 1e-12, (o, e, e_orc)
+        assert rel_l2(state, want) <= 1e-10, o
+        r = np.arange(1, N + 1) * dr + o
+        dist.append(np.sqrt(dr * np.sum((np.abs(state[0]) ** 2 - 4 * r ** 2 * np.exp(-2 * r)) ** 2)))
+    assert abs(e - (-0.5)) <= 0.005, e             # the paper's "approximately -0.5 a.u."
+    assert dist[1] * 5 < dist[0], dist
+
+
 def test_imag_arguments():
     from paper_1308_1856_gb300 import TDSEError
     t = make(50, 0.2, 1, 5)
