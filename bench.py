@@ -167,10 +167,10 @@ def start_state(seed: int = 31):
 # full launch by its points; the single-instance kernels on the at-scale grid
 # (512000 points).  An entry is removed when its kernel changes after capture.
 MEASURED_TRAFFIC_PER_POINT = {
-    ("batched", "fp64", "lanczos_a"): (537.7e6 + 169.0e6) / 10664737,
-    ("batched", "fp64", "lanczos_b"): (343.0e6 + 141.3e6) / 10664737,
-    ("batched", "mixed", "lanczos_a"): (297.0e6 + 70.0e6) / 10664737,
-    ("batched", "mixed", "lanczos_b"): (171.2e6 + 55.2e6) / 10664737,
+    ("batched", "fp64", "lanczos_a"): (537.5e6 + 165.8e6) / 10664737,
+    ("batched", "fp64", "lanczos_b"): (343.0e6 + 138.5e6) / 10664737,
+    ("batched", "mixed", "lanczos_a"): (296.7e6 + 66.7e6) / 10664737,
+    ("batched", "mixed", "lanczos_b"): (171.2e6 + 52.7e6) / 10664737,
     ("single", "fp64", "taylor_stage"): 20.6e6 / 512000,
 }
 
