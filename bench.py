@@ -1,19 +1,25 @@
-"""Throughput benchmark of the FD-TDSE hot path on the at-scale configuration.
+"""Throughput benchmark of the FD-TDSE hot path.
 
-Workload ("scale"): hydrogen, N = 8000 radial points, dr = 0.05 a.u. (box 400),
-lmax = 63, 5-point stencil, complex128 state, sin^2 pulse (E0 = 0.0534,
-omega = 0.057, 4 cycles), cos^(1/8) mask over the last 50 a.u.  One benchmark
-step advances six resident states by one time step each: Taylor order 12,
-classic RK4 and Lanczos with Krylov dimension 12, each in FP64 and in mixed
-precision (FP32 stencil, FP64 state/dots/norms/expm).  Lanczos runs at
-dt = 0.02; the explicit Taylor/RK4 propagators are unstable at that dt on this
-grid (rho(H) dt ~ 1.6e4), so they run at their stable dt = 4e-6 -- the work
-per step does not depend on dt.  Metric: grid-point * steps per second summed
-over the propagators (6 * 512000 grid points per benchmark step).
+One benchmark step advances every row by one time step:
+- six at-scale single-instance rows: hydrogen, N = 8000 radial points,
+  dr = 0.05 a.u. (box 400), lmax = 63, 5-point stencil, complex128 state,
+  sin^2 pulse (E0 = 0.0534, omega = 0.057, 4 cycles), cos^(1/8) mask over the
+  last 50 a.u.; Taylor order 12, classic RK4 and Lanczos with Krylov
+  dimension 12, each in FP64 and in mixed precision (FP32 stencil, FP64
+  state/dots/norms/expm).  Lanczos runs at dt = 0.02; the explicit Taylor/RK4
+  propagators are unstable at that dt on this grid (rho(H) dt ~ 1.6e4), so
+  they run at their stable dt = 4e-6 -- the work per step does not depend on dt;
+- two batched rows: 256 seeded uneven instances (N 2000-16000, dr = 0.1,
+  lmax 15-127, Krylov dimension 8-16, dt = 0.02), one Lanczos step each, in
+  FP64 and in mixed precision, with an autotuned launch schedule.
+Metric: grid-point * steps per second summed over the rows (335.5 M grid
+points per benchmark step).  Further legs: end to end through the C ABI with
+host buffers, the served traces, the embedded RK pairs, the per-step
+observables, the small configuration and the serial oracle on the host cores.
 
-L2 (129 MB) is flushed before every timed propagator step by writing a 256 MB
-buffer; each propagator step is timed by CUDA events on the library's stream
-(the flush sits outside the events).
+L2 (129 MB) is flushed before every timed row by writing a 256 MB buffer;
+each row is timed by CUDA events on the library's stream (the flush sits
+outside the events).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): every rank runs an independent replica (the path has no
