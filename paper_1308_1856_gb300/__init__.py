@@ -1,9 +1,11 @@
 """GB300-native finite-difference TDSE propagation (arXiv 1308.1856 hot path).
 
 The compute path is the CUDA library ``libtdse.so`` (C ABI in include/tdse.h).
-``TDSE`` below is a thin convenience wrapper over the C calls: numpy/torch
-arrays in, status codes turned into exceptions.  PyTorch is used only for
-device memory and streams.
+``TDSE`` (one wavefunction), ``Batch`` (many uneven instances advanced
+together) and ``Server`` (continuous batching under a device-memory budget)
+below are thin convenience wrappers over the C calls: numpy/torch arrays in,
+status codes turned into exceptions.  PyTorch is used only for device memory
+and streams.  There is no CPU fallback: without the library, loading fails.
 """
 from __future__ import annotations
 
