@@ -72,8 +72,10 @@ enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
  * chosen stencil (4th-order 5-point, or 3-point central); A(t) = -c int_0^t E
  * by composite 5-point Gauss quadrature on panels of at most 0.25 a.u. (the
  * paper prints the l/r terms with the opposite signs, which breaks
- * p_z = i[H_0, z] and gauge invariance).  The velocity gauge runs in FP64 with
- * the zero ghost (TDSE_ERR_ARG otherwise); observables are the same formulas.
+ * p_z = i[H_0, z] and gauge invariance).  The velocity gauge runs with the
+ * zero ghost (TDSE_ERR_ARG otherwise), in FP64 or in mixed precision (the
+ * coupling's first derivatives then FP32, formed part by part like the
+ * Laplacian); observables are the same formulas.  In a batch it is FP64 only.
  */
 enum { TDSE_GAUGE_LENGTH = 0, TDSE_GAUGE_VELOCITY = 1 };
 /* largest Krylov dimension tdse_propagate accepts for TDSE_LANCZOS */

@@ -55,7 +55,7 @@ struct tdse {
   // mixed precision: FP32 tables, the hi/lo split of psi (two buffer pairs:
   // a final stage reads one pair with halos while writing the other) and
   // complex64 work vectors
-  float *diagf = nullptr, *rjf = nullptr, *kappaf = nullptr;
+  float *diagf = nullptr, *rjf = nullptr, *kappaf = nullptr, *rinvf = nullptr;
   float2 *split = nullptr;         // 4 vectors: hi[0], lo[0], hi[1], lo[1]
   int split_cur = 0;
   bool split_valid = false;        // split[split_cur] holds the split of psi
@@ -156,6 +156,7 @@ MixedView mview(const tdse *h) {
   mv.diag = h->diagf;
   mv.rj = h->rjf;
   mv.kappa = h->kappaf;
+  mv.rinv = h->rinvf;
   return mv;
 }
 
@@ -202,6 +203,9 @@ int build_tables(tdse *h) {
   TDSE_CUDA(h, cudaMemcpyAsync(h->diagf, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice, s), "copy diagf");
   TDSE_CUDA(h, cudaMemcpyAsync(h->rjf, rf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s), "copy rf");
   TDSE_CUDA(h, cudaMemcpyAsync(h->kappaf, kf.data(), sizeof(float) * (L + 2), cudaMemcpyHostToDevice, s), "copy kf");
+  std::vector<float> rif(N);
+  for (int j = 0; j < N; ++j) rif[j] = (float)(1.0 / r[j]);
+  TDSE_CUDA(h, cudaMemcpyAsync(h->rinvf, rif.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s), "copy 1/r (FP32)");
   TDSE_CUDA(h, cudaMemcpyAsync(h->rj, r.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s), "copy r");
   std::vector<double> ri(N);
   for (int j = 0; j < N; ++j) ri[j] = 1.0 / r[j];
@@ -277,6 +281,7 @@ void free_all(tdse *h) {
   dfree(h, h->diagf);
   dfree(h, h->rjf);
   dfree(h, h->kappaf);
+  dfree(h, h->rinvf);
   dfree(h, h->split);
   dfree(h, h->mwork);
   for (auto &m : h->marks) {
@@ -880,7 +885,8 @@ int tdse_create(int N, double dr, int lmax, int stencil, double Z, const double 
             DMALLOC(h, obs_out, sizeof(double) * (lmax + 6)) == cudaSuccess &&
             DMALLOC(h, diagf, sizeof(float) * G) == cudaSuccess &&
             DMALLOC(h, rjf, sizeof(float) * N) == cudaSuccess &&
-            DMALLOC(h, kappaf, sizeof(float) * (lmax + 2)) == cudaSuccess;
+            DMALLOC(h, kappaf, sizeof(float) * (lmax + 2)) == cudaSuccess &&
+            DMALLOC(h, rinvf, sizeof(float) * N) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(h);
@@ -944,8 +950,8 @@ int tdse_set_options(tdse_t *h, const tdse_opts *o) {
     return fail(h, TDSE_ERR_ARG, "precision must be TDSE_FP64 or TDSE_MIXED");
   if (o->gauge != TDSE_GAUGE_LENGTH && o->gauge != TDSE_GAUGE_VELOCITY)
     return fail(h, TDSE_ERR_ARG, "gauge must be TDSE_GAUGE_LENGTH or TDSE_GAUGE_VELOCITY");
-  if (o->gauge == TDSE_GAUGE_VELOCITY && (o->precision != TDSE_FP64 || o->ghost != TDSE_GHOST_ZERO))
-    return fail(h, TDSE_ERR_ARG, "the velocity gauge runs in FP64 with the zero ghost");
+  if (o->gauge == TDSE_GAUGE_VELOCITY && o->ghost != TDSE_GHOST_ZERO)
+    return fail(h, TDSE_ERR_ARG, "the velocity gauge runs with the zero ghost");
   TDSE_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   h->opts = *o;
   h->g.gauge = o->gauge;
@@ -1487,17 +1493,17 @@ int tdse_apply_h(tdse_t *h, double E, const void *x, void *y) {
   const char *xa = (const char *)x, *ya = (const char *)y;
   if (xa < ya + bytes && ya < xa + bytes) return fail(h, TDSE_ERR_ARG, "x and y overlap");
   if (!std::isfinite(E)) return fail(h, TDSE_ERR_ARG, "non-finite field");
+  // the velocity-gauge kernels take A/c
+  const double e = (h->opts.gauge == TDSE_GAUGE_VELOCITY) ? E / kLightAU : E;
   if (h->opts.precision == TDSE_MIXED) {
     rc = ensure_mixed(h, 2);
     if (rc) return rc;
     TDSE_LAUNCH(h, TDSE_K_APPLY_H,
-                launch_mx_apply_h(h->g, mview(h), E, (const double2 *)x, h->mwork, h->mwork + npts(h),
+                launch_mx_apply_h(h->g, mview(h), e, (const double2 *)x, h->mwork, h->mwork + npts(h),
                                   (double2 *)y, h->stream),
                 "mixed apply_h");
     return TDSE_OK;
   }
-  // the velocity-gauge kernels take A/c
-  const double e = (h->opts.gauge == TDSE_GAUGE_VELOCITY) ? E / kLightAU : E;
   TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), e, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
   return TDSE_OK;
 }

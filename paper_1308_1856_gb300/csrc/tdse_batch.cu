@@ -409,6 +409,8 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   in.c1 = (float)I.c1;
   in.c2 = (float)I.c2;
   in.E = (float)field_of(B, inst);
+  in.rinv = nullptr;   // the mixed batch runs the length gauge
+  in.d1c = 0.f;
   return in;
 }
 

@@ -157,6 +157,7 @@ cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, in
 struct MixedView {
   const float *diag;   // l(l+1)/(2 r^2) + V(r) (+ odd-ghost fold), without c0
   const float *rj, *kappa;
+  const float *rinv;   // 1 / r_j (velocity gauge)
 };
 
 // hi/lo split of psi without the norm (the same split as every other kernel's)

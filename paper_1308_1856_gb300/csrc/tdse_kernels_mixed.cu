@@ -15,12 +15,18 @@
 // so its error is relative to the difference, not to psi.  The diagonal table
 // then holds l(l+1)/(2 r^2) + V(r) without c0.
 //
+// In the velocity gauge (VG) the coupling is the (A/c) p_z of the FP64 walker,
+// with the first derivatives of rows l - 1 and l + 1 formed in FP32 from
+// part-by-part differences as well.
+//
 // Work decomposition and reductions are those of the FP64 kernels (persistent
 // grid, balanced 32-point row segments per warp, fixed-order block partials).
 // Each thread sums its FP32 products in an error-free FP32 pair (about twice
 // the FP32 precision, no FP64 instruction per point); the block and grid
 // reductions of alpha, beta and the norm are FP64.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "tdse_device_common.cuh"
 #include "tdse_stencil.cuh"
@@ -34,7 +40,8 @@ using namespace common;
 using namespace stencil;
 
 // Walk this warp's row segments; f(i, idx, Hx, x_center) per point.
-template <int ST, bool S, bool Wp, typename F>
+// VG: the velocity-gauge coupling.
+template <int ST, bool S, bool Wp, bool VG, typename F>
 __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
   const int lane = threadIdx.x & 31;
   const int N = in.N, Lp1 = in.L + 1;
@@ -47,7 +54,7 @@ __device__ __forceinline__ void mixed_segments(const MixedIn &in, F &&f) {
     const long long left = s_end - s;
     const int l1 = (left < (long long)(Lp1 - l0)) ? l0 + (int)left : Lp1;
     const int i = jg * 32 + lane;
-    if (i < N) mixed_walk_rows<ST, S, Wp>(in, i, l0, l1, f);
+    if (i < N) mixed_walk_rows<ST, S, Wp, kPrefetchRows, VG>(in, i, l0, l1, f);
     s += l1 - l0;
   }
 }
@@ -108,9 +115,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 }
 
 // y = H(E) x in the mixed arithmetic (FP32 stencil on the split of x).
-template <int ST>
+template <int ST, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) mx_apply_h_kernel(MixedIn in, double2 *__restrict__ y) {
-  mixed_segments<ST, true, false>(in, [&](int, size_t idx, float2 t, float2) {
+  mixed_segments<ST, true, false, VG>(in, [&](int, size_t idx, float2 t, float2) {
     y[idx] = make_double2((double)t.x, (double)t.y);
   });
 }
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) mx_apply_h_kerne
 // Lanczos iteration j, first half (mixed):
 //   z = sigma_j H U_j - (sigma_{j-1} / sigma_j) U_{j-1},  alpha_j = sigma_j Re<U_j, z>,
 // with U_0 = psi given as (hi, lo) and U_j (j >= 1) complex64.
-template <int ST, bool FIRST>
+template <int ST, bool FIRST, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     mx_lanczos_a_kernel(MixedIn in, int j, const float2 *__restrict__ uprev,
                         const float2 *__restrict__ prev_hi, const float2 *__restrict__ prev_lo,
@@ -128,7 +135,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   const float sig = (float)sigd;
   const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
   PairSum acc;
-  mixed_segments<ST, FIRST, !FIRST>(in, [&](int, size_t idx, float2 t, float2 u) {
+  mixed_segments<ST, FIRST, !FIRST, VG>(in, [&](int, size_t idx, float2 t, float2 u) {
     float2 o = make_float2(sig * t.x, sig * t.y);
     if (!FIRST) {
       float2 up;
@@ -272,12 +279,12 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 // Taylor stage k in correction form (Horner, Eq. (Taylor)):
 //   w_k = (-i dt/k) H (psi + w_{k+1}),  w_{P+1} = 0,  psi_new = psi + w_1.
 // The last stage adds w_1 to psi in FP64, applies the mask and re-splits psi.
-template <int ST, bool HAS_W>
+template <int ST, bool HAS_W, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     mx_taylor_stage_kernel(MixedIn in, float s, float2 *__restrict__ w_out, int final_stage,
                            double2 *psi, float2 *hi_out, float2 *lo_out,
                            const double *__restrict__ mask, int mask_start) {
-  mixed_segments<ST, true, HAS_W>(in, [&](int i, size_t idx, float2 t, float2) {
+  mixed_segments<ST, true, HAS_W, VG>(in, [&](int i, size_t idx, float2 t, float2) {
     const float2 w = make_float2(s * t.y, -s * t.x);   // (-i s)(tx + i ty)
     if (!final_stage) {
       w_out[idx] = w;
@@ -303,12 +310,12 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
 // stages 1-3 write k_s and add b_s k_s to the compensated FP32 accumulator
 // (acc_hi, acc_lo) by an error-free two-sum; stage 4 forms
 // psi_new = psi + dt (acc + b_4 k_4) in FP64, masks and re-splits psi.
-template <int ST, bool HAS_K>
+template <int ST, bool HAS_K, bool VG>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     mx_rk_stage_kernel(MixedIn in, int stage, float b, double dtd, float2 *__restrict__ k_out,
                        float2 *acc_hi, float2 *acc_lo, double2 *psi, float2 *hi_out,
                        float2 *lo_out, const double *__restrict__ mask, int mask_start) {
-  mixed_segments<ST, true, HAS_K>(in, [&](int i, size_t idx, float2 t, float2) {
+  mixed_segments<ST, true, HAS_K, VG>(in, [&](int i, size_t idx, float2 t, float2) {
     const float2 kv = make_float2(t.y, -t.x);          // -i H g
     const float2 x = make_float2(b * kv.x, b * kv.y);
     if (stage == 1) {
@@ -363,7 +370,25 @@ MixedIn make_mixed(const Geometry &g, const MixedView &mv, float E, const float2
   in.c1 = (float)g.c1;
   in.c2 = (float)g.c2;
   in.E = E;
+  in.rinv = mv.rinv;
+  in.d1c = (float)((g.stencil == 5) ? 1.0 / (12.0 * g.dr) : 1.0 / (2.0 * g.dr));
   return in;
+}
+
+template <bool V>
+using BC = std::integral_constant<bool, V>;
+
+// f(stencil, velocity gauge) with both as compile-time constants.
+template <typename F>
+void dispatch(const Geometry &g, F &&f) {
+  const bool vg = g.gauge == 1;
+  if (g.stencil == 5) {
+    if (vg) f(std::integral_constant<int, 5>{}, BC<true>{});
+    else f(std::integral_constant<int, 5>{}, BC<false>{});
+  } else {
+    if (vg) f(std::integral_constant<int, 3>{}, BC<true>{});
+    else f(std::integral_constant<int, 3>{}, BC<false>{});
+  }
 }
 
 inline unsigned stencil_blocks(const Geometry &g) { return (unsigned)(g.sms * kStencilBlocksPerSM); }
@@ -392,10 +417,9 @@ cudaError_t launch_mx_apply_h(const Geometry &g, const MixedView &mv, double E, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const MixedIn in = make_mixed(g, mv, (float)E, tmp_hi, tmp_lo, nullptr, 0.f);
-  if (g.stencil == 5)
-    mx_apply_h_kernel<5><<<stencil_blocks(g), kBlockJ, 0, st>>>(in, y);
-  else
-    mx_apply_h_kernel<3><<<stencil_blocks(g), kBlockJ, 0, st>>>(in, y);
+  dispatch(g, [&](auto stc, auto vg) {
+    mx_apply_h_kernel<decltype(stc)::value, decltype(vg)::value><<<stencil_blocks(g), kBlockJ, 0, st>>>(in, y);
+  });
   return cudaGetLastError();
 }
 
@@ -406,10 +430,10 @@ cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E
   const unsigned grid = stencil_blocks(g);
   if (j == 0) {
     const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, nullptr, 0.f);
-    if (g.stencil == 5)
-      mx_lanczos_a_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, j, nullptr, nullptr, nullptr, z, red, ls);
-    else
-      mx_lanczos_a_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, j, nullptr, nullptr, nullptr, z, red, ls);
+    dispatch(g, [&](auto stc, auto vg) {
+      mx_lanczos_a_kernel<decltype(stc)::value, true, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(
+          in, j, nullptr, nullptr, nullptr, z, red, ls);
+    });
   } else {
     MixedIn in = make_mixed(g, mv, (float)E, nullptr, nullptr, u, 1.f);
     if (uprev) {
@@ -418,10 +442,10 @@ cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E
       in.pf0 = hi;
       in.pf1 = lo;
     }
-    if (g.stencil == 5)
-      mx_lanczos_a_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, j, uprev, hi, lo, z, red, ls);
-    else
-      mx_lanczos_a_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, j, uprev, hi, lo, z, red, ls);
+    dispatch(g, [&](auto stc, auto vg) {
+      mx_lanczos_a_kernel<decltype(stc)::value, false, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(
+          in, j, uprev, hi, lo, z, red, ls);
+    });
   }
   return cudaGetLastError();
 }
@@ -455,17 +479,14 @@ cudaError_t launch_mx_taylor_stage(const Geometry &g, const MixedView &mv, const
   const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, w_in, 1.f);
   const int mstart = final_stage ? op.mask_start : g.N;
   const int fs = final_stage ? 1 : 0;
-  if (g.stencil == 5) {
+  dispatch(g, [&](auto stc, auto vg) {
+    constexpr int ST = decltype(stc)::value;
+    constexpr bool VG = decltype(vg)::value;
     if (w_in)
-      mx_taylor_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
+      mx_taylor_stage_kernel<ST, true, VG><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
     else
-      mx_taylor_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
-  } else {
-    if (w_in)
-      mx_taylor_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
-    else
-      mx_taylor_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
-  }
+      mx_taylor_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
+  });
   return cudaGetLastError();
 }
 
@@ -479,17 +500,14 @@ cudaError_t launch_mx_rk_stage(const Geometry &g, const MixedView &mv, const Ope
   const unsigned grid = stencil_blocks(g);
   const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, k_in, (float)(dt * a_in[stage - 1]));
   const int mstart = (stage == 4) ? op.mask_start : g.N;
-  if (g.stencil == 5) {
+  dispatch(g, [&](auto stc, auto vg) {
+    constexpr int ST = decltype(stc)::value;
+    constexpr bool VG = decltype(vg)::value;
     if (k_in)
-      mx_rk_stage_kernel<5, true><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
+      mx_rk_stage_kernel<ST, true, VG><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
     else
-      mx_rk_stage_kernel<5, false><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
-  } else {
-    if (k_in)
-      mx_rk_stage_kernel<3, true><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
-    else
-      mx_rk_stage_kernel<3, false><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
-  }
+      mx_rk_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
+  });
   return cudaGetLastError();
 }
 

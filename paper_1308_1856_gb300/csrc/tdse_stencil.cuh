@@ -101,7 +101,9 @@ struct MixedIn {
   const float *__restrict__ kappa;
   const float2 *pf0, *pf1;         // rows the caller's epilogue reads at the same index (may be null)
   int N, L;
-  float c1, c2, E;
+  float c1, c2, E;                 // E: the field (length gauge) or A/c (velocity gauge)
+  const float *__restrict__ rinv;  // velocity gauge: 1 / r_j (else unused)
+  float d1c;                       // velocity gauge: 1/(12 dr) (5-point) or 1/(2 dr) (3-point)
 };
 
 // L2 prefetch of every array the walker and its epilogue read at row offset idx.
@@ -235,9 +237,27 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
   }
 }
 
+// First derivative of the mixed operand's row starting at element `row`, at
+// column i (zero beyond the box): the formula of d1_point, with each
+// difference formed part by part (diff) as in the Laplacian.
+template <int ST, bool S, bool Wp>
+__device__ __forceinline__ float2 mixed_d1(const MixedIn &in, size_t row, int i) {
+  const Parts<S, Wp> m1 = load_parts<S, Wp>(in, row + i - 1, i >= 1);
+  const Parts<S, Wp> p1 = load_parts<S, Wp>(in, row + i + 1, i + 1 < in.N);
+  const float2 d1 = diff(p1, m1, in.ws);
+  if (ST == 5) {
+    const Parts<S, Wp> m2 = load_parts<S, Wp>(in, row + i - 2, i >= 2);
+    const Parts<S, Wp> p2 = load_parts<S, Wp>(in, row + i + 2, i + 2 < in.N);
+    const float2 d2 = diff(m2, p2, in.ws);
+    return make_float2(in.d1c * fmaf(8.f, d1.x, d2.x), in.d1c * fmaf(8.f, d1.y, d2.y));
+  }
+  return make_float2(in.d1c * d1.x, in.d1c * d1.y);
+}
+
 // Walk rows [l0, l1) of column i of the mixed operand; f(i, idx, Hx, x_center).
 // PF > 0 asks L2 for every operand row PF rows ahead (prefetch_row).
-template <int ST, bool S, bool Wp, int PF = kPrefetchRows, typename F>
+// VG: the velocity-gauge coupling (A/c) p_z of walk_rows in place of r E kappa.
+template <int ST, bool S, bool Wp, int PF = kPrefetchRows, bool VG = false, typename F>
 __device__ __forceinline__ void mixed_walk_rows(const MixedIn &in, int i, int l0, int l1, F &&f) {
   const int N = in.N, L = in.L;
   const float Er = in.E * in.rj[i];
@@ -267,10 +287,30 @@ __device__ __forceinline__ void mixed_walk_rows(const MixedIn &in, int i, int l0
     }
     tx = fmaf(dg, vc.x, tx);
     ty = fmaf(dg, vc.y, ty);
-    tx = fmaf(a_cur, vp.x, tx);
-    ty = fmaf(a_cur, vp.y, ty);
-    tx = fmaf(a_next, vn.x, tx);
-    ty = fmaf(a_next, vn.y, ty);
+    if (VG) {
+      const float ri = in.rinv[i];
+      float wx = 0.f, wy = 0.f;
+      if (l > 0) {
+        const float2 dp = mixed_d1<ST, S, Wp>(in, (size_t)(l - 1) * N, i);
+        const float k = in.kappa[l], lr = (float)l * ri;
+        wx = k * fmaf(-lr, vp.x, dp.x);
+        wy = k * fmaf(-lr, vp.y, dp.y);
+      }
+      if (l < L) {
+        const float2 dn = mixed_d1<ST, S, Wp>(in, (size_t)(l + 1) * N, i);
+        const float k = in.kappa[l + 1], lr = (float)(l + 1) * ri;
+        wx = fmaf(k, fmaf(lr, vn.x, dn.x), wx);
+        wy = fmaf(k, fmaf(lr, vn.y, dn.y), wy);
+      }
+      // -i (A/c) w
+      tx = fmaf(in.E, wy, tx);
+      ty = fmaf(-in.E, wx, ty);
+    } else {
+      tx = fmaf(a_cur, vp.x, tx);
+      ty = fmaf(a_cur, vp.y, ty);
+      tx = fmaf(a_next, vn.x, tx);
+      ty = fmaf(a_next, vn.y, ty);
+    }
     f(i, idx, make_float2(tx, ty), vc);
     prev = cur;
     cur = next;

@@ -87,11 +87,79 @@ def test_velocity_arguments():
     from paper_1308_1856_gb300 import TDSEError
     t = make(50, 0.2, 2, 5)
     with pytest.raises(TDSEError):
-        t.set_options(gauge="velocity", precision="mixed")
-    with pytest.raises(TDSEError):
         t.set_options(gauge="velocity", ghost=1)
+    with pytest.raises(TDSEError):
+        t.set_options(gauge="velocity", ghost=1, precision="mixed")
+    t.set_options(gauge="velocity", precision="mixed")
     t.set_options(gauge="velocity")
     t.close()
+
+
+def _mixed_velocity(N, dr, L, st, pulse=None):
+    t = make(N, dr, L, st, pulse=pulse, gauge="velocity")
+    t.set_options(gauge="velocity", precision="mixed")
+    return t
+
+
+@pytest.mark.parametrize("N,dr,L,st", [(7, 0.3, 2, 3), (33, 0.2, 5, 5), (257, 0.1, 6, 5), (517, 0.2, 13, 3)])
+def test_mixed_velocity_apply_h(N, dr, L, st):
+    """Mixed precision in the velocity gauge: the FP32 operator, whose
+    coupling takes the first derivatives of rows l -+ 1 from part-by-part
+    differences like the Laplacian, stays within a few FP32 roundings of the
+    FP64 oracle's (2e-6 relative, the bound of the length-gauge mixed operator)."""
+    g = grid_of(N, dr, L, st, gauge=1)
+    t = _mixed_velocity(N, dr, L, st)
+    for x in (W.smooth_state(N, dr, L, seed=3), W.random_state(N, L, seed=4)):
+        for A in (0.0, 1.7, -31.0):
+            got = apply_h_gpu(t, A, x)
+            want = oracle.apply_H(g, A, x)
+            assert rel_l2(got, want) <= 2e-6, (A, rel_l2(got, want))
+    t.close()
+
+
+@pytest.mark.parametrize("method,order,dt", [("taylor", 8, 0.01), ("rk4", 4, 0.005), ("lanczos", 12, 0.05),
+                                             ("lanczos", 1, 0.01)])
+def test_mixed_velocity_one_step(method, order, dt):
+    """One step of each method in mixed precision and the velocity gauge
+    against the FP64 oracle: ~dt |H psi| times the operator's FP32 error, held
+    to 1e-7 as in the length gauge."""
+    N, dr, L, st = 500, 0.2, 4, 3
+    if method != "lanczos":
+        dt = min(dt, 2.5 / (2.7 / dr ** 2 + L * (L + 1) / (2 * dr ** 2)))   # stable explicit step
+    pulse = oracle.Pulse(E0=0.0534, omega=0.057, ncycles=2)
+    psi = W.smooth_state(N, dr, L, seed=5)
+    t = _mixed_velocity(N, dr, L, st, pulse=pulse)
+    t.set_state(psi)
+    t.time = 70.0
+    t.propagate(method, order, dt, 1)
+    got = t.get_state()
+    t.close()
+    want, _ = oracle.propagate(grid_of(N, dr, L, st, gauge=1), psi, method, order, dt, 1, t0=70.0, pulse=pulse)
+    assert rel_l2(got, want) <= 1e-7, rel_l2(got, want)
+
+
+def test_mixed_velocity_many_steps_populations():
+    """100 Lanczos-12 steps of the small configuration's grid in the velocity
+    gauge: the l-populations above 1e-10 within 1e-6 relative of the FP64
+    oracle, the norm within 1e-6 (the target of the mixed path)."""
+    c = W.SMALL
+    pulse = oracle.Pulse(E0=c.E0, omega=c.omega, ncycles=c.ncycles)
+    psi0 = W.hydrogen_1s(c.N, c.dr, c.lmax)
+    t = _mixed_velocity(c.N, c.dr, c.lmax, c.stencil, pulse=pulse)
+    t.set_state(psi0)
+    t.time = 50.0
+    t.propagate("lanczos", 12, 0.05, 100)
+    got = t.get_state()
+    ob = t.observables()
+    t.close()
+    g = grid_of(c.N, c.dr, c.lmax, c.stencil, gauge=1)
+    want, _ = oracle.propagate(g, psi0, "lanczos", 12, 0.05, 100, t0=50.0, pulse=pulse)
+    ow = oracle.observables(g, want, psi0[0], r_b=10.0)
+    big = ow["l_pop"] > 1e-10
+    rel = np.abs(ob["l_pop"][big] - ow["l_pop"][big]) / ow["l_pop"][big]
+    assert rel.max() <= 1e-6, rel
+    assert abs(ob["norm"] - ow["norm"]) <= 1e-6
+    assert rel_l2(got, want) <= 1e-6, rel_l2(got, want)
 
 
 def test_sinea_pulse_field_and_vector_potential_match_the_oracle():
