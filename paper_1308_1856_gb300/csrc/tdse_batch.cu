@@ -1637,8 +1637,9 @@ int io_ready(tdse_batch *b, int groups) {
 }
 
 // Taper ratio of the first pipelined call of a batch, before any measurement:
-// compute of a point-step over its one-way copy time, between the two
-// precisions' measured values on the benchmark's batch (about 2 mixed, 7 FP64).
+// compute of a point-step over its one-way copy time.  It lies between the two
+// precisions' values on the 256-instance batched configuration, as estimated
+// from their step and copy times (about 2 mixed, 7 FP64).
 constexpr double kIoRatioFirst = 4.0;
 
 }  // namespace
