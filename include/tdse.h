@@ -352,8 +352,49 @@ int tdse_observables(tdse_t *h, double *norm, double *l_pop, double *dipole, dou
  */
 int tdse_apply_h(tdse_t *h, double E, const void *x_dev, void *y_dev);
 
+/*
+ * Small grids: a whole tdse_propagate call in one launch.  A grid of a few
+ * thousand points is microseconds of arithmetic per step, so a step of one
+ * launch per stage (Sec. 5: one kernel per Taylor term, per RK stage, per
+ * Lanczos phase) is bound by launch and grid-reduction latency.  On the
+ * small-grid path one thread-block cluster of at most 16 CTAs (one per SM)
+ * runs every step of the call: CTA r holds radial columns [r W, (r+1) W) of
+ * psi, of the diagonal table and of every work vector in its shared memory,
+ * reads the stencil's halo columns from its neighbours' shared memory,
+ * separates stages by cluster barriers and adds the Lanczos dot products and
+ * norms in a fixed order (every CTA holds the same sums, and forms the small
+ * exponential of each Lanczos step itself).  Taylor and RK4 give bitwise the
+ * states of the multi-launch path; Lanczos differs only in the association
+ * of its grid sums.  It applies to FP64 length-gauge propagation with no
+ * per-step observables set up (dipole series, flux, record), when the state
+ * and the method's work vectors (Taylor 3, RK4 4, Lanczos order + 1 vectors
+ * of the state's size, plus the diagonal table) fit in the cluster's shared
+ * memory (about 3 MB).
+ *   TDSE_SMALL_GRID_AUTO (default): that path for grids of at most 16384
+ *     points, the multi-launch path otherwise;
+ *   TDSE_SMALL_GRID_OFF: always the multi-launch path;
+ *   TDSE_SMALL_GRID_FORCE: that path whenever it applies, whatever the size.
+ * tdse_small_grid_path_used returns 1 if the last tdse_propagate call ran on
+ * it, else 0.  Errors: TDSE_ERR_ARG (unknown mode).
+ */
+enum { TDSE_SMALL_GRID_AUTO = 0, TDSE_SMALL_GRID_OFF = 1, TDSE_SMALL_GRID_FORCE = 2 };
+int tdse_set_small_grid_path(tdse_t *h, int mode);
+int tdse_small_grid_path_used(const tdse_t *h);
+
 /* Wait for the handle's stream; reports pending TDSE_ERR_NONFINITE. */
 int tdse_sync(tdse_t *h);
+
+/*
+ * Arithmetic-throughput probe (a measurement utility; the paper has no
+ * counterpart): the fused multiply-add rate, in flop/s (an FMA counts 2), that
+ * this GPU sustains on independent FP64 (fp64 = 1) or FP32 (fp64 = 0) chains:
+ * 8 blocks of 256 threads per SM, 8 chains per thread, best of three timed
+ * launches of about 20 ms after a warm-up, on cuda_stream (NULL: the legacy
+ * default stream), synchronous.  The FP64 kernels of this library are bound
+ * by this rate, so it measures the peak of their roofline.  Allocates
+ * nothing.  Errors: TDSE_ERR_ARG (NULL output), TDSE_ERR_CUDA.
+ */
+int tdse_fma_throughput(int fp64, double *flops_per_s, void *cuda_stream);
 
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long long tdse_launch_count(const tdse_t *h);
@@ -362,7 +403,7 @@ long long tdse_launch_count(const tdse_t *h);
 enum {
   TDSE_K_APPLY_H = 0, TDSE_K_TAYLOR_STAGE, TDSE_K_RK_STAGE, TDSE_K_NORM, TDSE_K_LANCZOS_A,
   TDSE_K_LANCZOS_B, TDSE_K_LANCZOS_EXPM, TDSE_K_LANCZOS_COMBINE, TDSE_K_OBSERVABLES,
-  TDSE_K_DIPOLE, TDSE_K_FLUX, TDSE_K_COUNT
+  TDSE_K_DIPOLE, TDSE_K_FLUX, TDSE_K_SMALL_GRID, TDSE_K_COUNT
 };
 
 /*
@@ -384,9 +425,14 @@ int tdse_profile_read(tdse_t *h, int kind, double *total_ms, long long *launches
  * or break the capture, or an embedding that forbids the library from owning
  * device memory) and so cannot create a handle.
  *
- * Same quantities as tdse_observables, for the grid r_j = j*dr + offset:
- * out_dev (device, lmax+5 doubles, 8-byte aligned) receives
- * {norm, dipole, yield, p_ground, l_pop[0..lmax]}.  psi_dev holds (lmax+1)*N
+ * Same quantities as tdse_observables, for the grid r_j = j*dr + offset
+ * (each r_j rounded as a product, then a sum, like the handle's table):
+ * out_dev (device, lmax+6 doubles, 8-byte aligned) receives
+ * {norm, dipole, yield, p_ground, l_pop[0..lmax], nonfinite}, where
+ * nonfinite is 1.0 when the state holds Inf or NaN (its norm sum is not
+ * finite; the handle path reports this as TDSE_ERR_NONFINITE) and 0.0
+ * otherwise: the call cannot return that status, since it does not wait for
+ * the kernel.  psi_dev holds (lmax+1)*N
  * interleaved complex doubles (device, 16-byte aligned); ref0_dev holds the N
  * complex values of the p_ground reference (device) or is NULL (p_ground = 0).
  * The work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy default
@@ -452,6 +498,10 @@ int tdse_batch_set_stream(tdse_batch_t *b, void *cuda_stream);
 int tdse_batch_set_state(tdse_batch_t *b, int i, const double *F_host);
 int tdse_batch_get_state(tdse_batch_t *b, int i, double *F_host);
 double tdse_batch_get_time(const tdse_batch_t *b, int i);
+/* Put instance i at time t (default 0): its next step starts at t, step n of
+ * the following calls at t + n dt (the pulse is evaluated there).
+ * Errors: TDSE_ERR_ARG (bad index, non-finite t). */
+int tdse_batch_set_time(tdse_batch_t *b, int i, double t);
 
 /* Every instance's state in / out of ONE host buffer: instance i's
  * (lmax_i+1)*N_i interleaved complex values follow instance i-1's, in
@@ -497,9 +547,12 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in_host, double *F_
 int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
                            double *yield, double *p_ground);
 
-/* Total grid points of the batch and kernel launches issued (accounting). */
+/* Total grid points of the batch and kernel launches issued (accounting).
+ * tdse_batch_graph_steps: steps (of all instances together) that ran as a
+ * replay of a captured step graph rather than as separate launches. */
 long long tdse_batch_points(const tdse_batch_t *b);
 long long tdse_batch_launch_count(const tdse_batch_t *b);
+long long tdse_batch_graph_steps(const tdse_batch_t *b);
 
 /* Per-kernel timing of a batch, as tdse_profile / tdse_profile_read (TDSE_K_* kinds). */
 int tdse_batch_profile(tdse_batch_t *b, int enable);
@@ -513,9 +566,12 @@ int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long lo
  * unused); and the blocks per SM of the stencil and of the elementwise
  * kernels (1 or 2, of 512 threads).  Results
  * do not depend on the schedule (bitwise): every reduction is split into
- * fixed per-instance chunks whatever the grid.  Segments of three or more
- * steps with an unchanged set of instances run as one captured CUDA graph of
- * a step, replayed once per step.
+ * fixed per-instance chunks whatever the grid.  A run is cut into segments
+ * where its set of active instances changes; a segment of three or more
+ * steps, or one that repeats the previous call's segment (a caller that
+ * advances one step per call), runs as a captured CUDA graph of one step,
+ * replayed once per step.  The batch keeps up to eight such graphs across
+ * calls and replays a cached one whenever a segment's launches are the same.
  *
  * tdse_batch_autotune times every schedule on Lanczos phase 0 of the batch's
  * instances (launches whose outputs the next step recomputes, so the state is

@@ -227,6 +227,15 @@ class TDSE:
     def sync(self):
         self._check(C.tdse_sync(self.h))
 
+    def set_small_grid_path(self, mode: str = "auto"):
+        """'auto' (default), 'off' or 'force': see tdse_set_small_grid_path."""
+        modes = {"auto": C.TDSE_SMALL_GRID_AUTO, "off": C.TDSE_SMALL_GRID_OFF, "force": C.TDSE_SMALL_GRID_FORCE}
+        self._check(C.tdse_set_small_grid_path(self.h, modes[mode]))
+
+    @property
+    def small_grid_path_used(self) -> bool:
+        return C.tdse_small_grid_path_used(self.h) == 1
+
     @property
     def launches(self) -> int:
         return C.tdse_launch_count(self.h)
@@ -243,6 +252,16 @@ class TDSE:
             self._check(C.tdse_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
             out[name] = (ms.value, n.value)
         return out
+
+
+def fma_throughput(fp64: bool = True, stream_ptr: int = 0) -> float:
+    """FP64 (or FP32) fused multiply-add rate of the current GPU in flop/s
+    (tdse_fma_throughput; synchronous)."""
+    out = ctypes.c_double()
+    rc = C.tdse_fma_throughput(1 if fp64 else 0, ctypes.byref(out), ctypes.c_void_p(stream_ptr or None))
+    if rc != 0:
+        raise TDSEError(rc, "tdse_fma_throughput failed")
+    return out.value
 
 
 def _spec_struct(s) -> "C.tdse_instance_spec":
@@ -314,6 +333,9 @@ class Batch:
     def time(self, i):
         return C.tdse_batch_get_time(self.h, int(i))
 
+    def set_time(self, i, t: float):
+        self._check(C.tdse_batch_set_time(self.h, int(i), float(t)))
+
     def set_states_ptr(self, host_ptr: int):
         """All states from one host buffer (instance order, back to back)."""
         self._check(C.tdse_batch_set_states(self.h, ctypes.c_void_p(host_ptr)))
@@ -364,6 +386,11 @@ class Batch:
     @property
     def launches(self) -> int:
         return C.tdse_batch_launch_count(self.h)
+
+    @property
+    def graph_steps(self) -> int:
+        """Steps replayed from captured step graphs since creation."""
+        return C.tdse_batch_graph_steps(self.h)
 
     def autotune(self) -> dict:
         """Time every launch schedule on this batch and keep the fastest."""

@@ -26,6 +26,7 @@ TDSE_FP64, TDSE_MIXED = 0, 1
 TDSE_GAUGE_LENGTH, TDSE_GAUGE_VELOCITY = 0, 1
 TDSE_PULSE_SIN2_E, TDSE_PULSE_SIN2_A = 0, 1
 TDSE_MAX_KRYLOV = 32
+TDSE_SMALL_GRID_AUTO, TDSE_SMALL_GRID_OFF, TDSE_SMALL_GRID_FORCE = 0, 1, 2
 
 # Every symbol include/tdse.h declares: name -> (restype, argtypes)
 _c_int, _c_double, _c_long, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p
@@ -99,6 +100,9 @@ SIGNATURES = {
     "tdse_observables": (_c_int, [_vp, _dp, _vp, _dp, _dp, _dp]),
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
     "tdse_sync": (_c_int, [_vp]),
+    "tdse_fma_throughput": (_c_int, [_c_int, _dp, _vp]),
+    "tdse_set_small_grid_path": (_c_int, [_vp, _c_int]),
+    "tdse_small_grid_path_used": (_c_int, [_vp]),
     "tdse_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_profile": (_c_int, [_vp, _c_int]),
     "tdse_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -112,6 +116,7 @@ SIGNATURES = {
     "tdse_batch_set_state": (_c_int, [_vp, _c_int, _vp]),
     "tdse_batch_get_state": (_c_int, [_vp, _c_int, _vp]),
     "tdse_batch_get_time": (_c_double, [_vp, _c_int]),
+    "tdse_batch_set_time": (_c_int, [_vp, _c_int, _c_double]),
     "tdse_batch_set_states": (_c_int, [_vp, _vp]),
     "tdse_batch_get_states": (_c_int, [_vp, _vp]),
     "tdse_batch_propagate": (_c_int, [_vp, _c_long]),
@@ -119,6 +124,7 @@ SIGNATURES = {
     "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
     "tdse_batch_points": (ctypes.c_longlong, [_vp]),
     "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
+    "tdse_batch_graph_steps": (ctypes.c_longlong, [_vp]),
     "tdse_batch_profile": (_c_int, [_vp, _c_int]),
     "tdse_batch_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "tdse_batch_autotune": (_c_int, [_vp, ctypes.POINTER(tdse_schedule)]),
@@ -213,6 +219,9 @@ tdse_flux_read = _fn("tdse_flux_read")
 tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")
 tdse_sync = _fn("tdse_sync")
+tdse_fma_throughput = _fn("tdse_fma_throughput")
+tdse_set_small_grid_path = _fn("tdse_set_small_grid_path")
+tdse_small_grid_path_used = _fn("tdse_small_grid_path_used")
 tdse_launch_count = _fn("tdse_launch_count")
 tdse_profile = _fn("tdse_profile")
 tdse_profile_read = _fn("tdse_profile_read")
@@ -225,6 +234,7 @@ tdse_batch_set_stream = _fn("tdse_batch_set_stream")
 tdse_batch_set_state = _fn("tdse_batch_set_state")
 tdse_batch_get_state = _fn("tdse_batch_get_state")
 tdse_batch_get_time = _fn("tdse_batch_get_time")
+tdse_batch_set_time = _fn("tdse_batch_set_time")
 tdse_batch_set_states = _fn("tdse_batch_set_states")
 tdse_batch_get_states = _fn("tdse_batch_get_states")
 tdse_batch_propagate = _fn("tdse_batch_propagate")
@@ -232,6 +242,7 @@ tdse_batch_propagate_io = _fn("tdse_batch_propagate_io")
 tdse_batch_observables = _fn("tdse_batch_observables")
 tdse_batch_points = _fn("tdse_batch_points")
 tdse_batch_launch_count = _fn("tdse_batch_launch_count")
+tdse_batch_graph_steps = _fn("tdse_batch_graph_steps")
 tdse_batch_profile = _fn("tdse_batch_profile")
 tdse_batch_profile_read = _fn("tdse_batch_profile_read")
 tdse_batch_autotune = _fn("tdse_batch_autotune")
@@ -257,4 +268,4 @@ tdse_server_profile = _fn("tdse_server_profile")
 tdse_server_profile_read = _fn("tdse_server_profile_read")
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
-                "lanczos_expm", "lanczos_combine", "observables", "dipole", "flux"]
+                "lanczos_expm", "lanczos_combine", "observables", "dipole", "flux", "small_grid"]

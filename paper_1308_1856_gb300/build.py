@@ -3,6 +3,9 @@
 Every ``csrc/*.cu`` file is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
 ``_build/libtdse.so``.  No fast-math: the FP64 path must round like IEEE FP64.
+Host code is compiled with ``-ffp-contract=off``: gcc on AArch64 would
+otherwise fuse a*b + c in the host-built tables (grid, diagonal, mask, pulse),
+which then round differently from an x86 build and from the oracle.
 """
 import concurrent.futures as cf
 import glob
@@ -18,6 +21,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtdse.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 

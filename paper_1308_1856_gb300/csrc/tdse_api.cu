@@ -74,6 +74,14 @@ struct tdse {
   // ||psi|| in the Lanczos scalars is current (the last work on psi was a
   // Lanczos step, whose combine kernel leaves it there)
   bool lanczos_norm_valid = false;
+  // small grids: a whole run in one cluster launch (tdse_cluster.cu)
+  int small_mode = TDSE_SMALL_GRID_AUTO;
+  int small_used = 0;              // the last tdse_propagate ran on that path
+  SmallPlan small_plan;            // cached for (small_method, small_order)
+  int small_method = -1, small_order = -1;
+  double *etab = nullptr;          // per-step fields of a cluster run
+  size_t etab_cap = 0;
+  std::vector<double> hetab;
   // per-kernel timing (tdse_profile)
   bool profiling = false;
   struct Mark { int kind; cudaEvent_t a, b; };
@@ -262,6 +270,7 @@ void free_all(tdse *h) {
   dfree(h, h->diag);
   dfree(h, h->rj);
   dfree(h, h->rinv);
+  dfree(h, h->etab);
   dfree(h, h->kappa);
   dfree(h, h->mask);
   dfree(h, h->red);
@@ -539,9 +548,69 @@ int mx_lanczos_steps(tdse *h, int m, double dt, long nsteps) {
   return TDSE_OK;
 }
 
+// ---- small grids: every step in one cluster launch ---------------------------
+// Grids of at most this many points take the cluster path by default (FP64,
+// length gauge, no per-step observables): below it a step is launch-latency
+// bound on the multi-launch path.
+constexpr size_t kSmallGridAutoPoints = 16384;
+
+// Run the steps on the cluster path if it applies; *done tells whether it did.
+int small_grid_steps(tdse *h, int method, int order, double dt, long nsteps, bool *done) {
+  *done = false;
+  if (h->small_mode == TDSE_SMALL_GRID_OFF || nsteps < 1 || nsteps > 0x7fffffffL || hooks_on(h) ||
+      h->opts.precision != TDSE_FP64 || h->g.gauge != 0)
+    return TDSE_OK;
+  if (h->small_mode == TDSE_SMALL_GRID_AUTO && npts(h) > kSmallGridAutoPoints) return TDSE_OK;
+  if (h->small_method != method || h->small_order != order) {
+    h->small_plan = plan_small_grid(h->g, method, order);
+    h->small_method = method;
+    h->small_order = order;
+  }
+  if (!h->small_plan.ok) return TDSE_OK;
+  const size_t per = (method == TDSE_RK4) ? 3 : 1;
+  const size_t nE = per * (size_t)nsteps;
+  if (h->etab_cap < nE) {
+    dfree(h, h->etab);
+    h->etab = nullptr;
+    h->etab_cap = 0;
+    cudaError_t e = DMALLOC(h, etab, sizeof(double) * nE);
+    if (e != cudaSuccess) {
+      h->etab = nullptr;
+      cudaGetLastError();
+      return fail(h, TDSE_ERR_OOM, "field table: " + std::string(cudaGetErrorString(e)));
+    }
+    h->etab_cap = nE;
+  }
+  h->hetab.resize(nE);
+  const double t0 = h->t;
+  for (long n = 0; n < nsteps; ++n) {
+    const double tn = t0 + (double)n * dt;
+    if (method == TDSE_RK4) {
+      h->hetab[3 * n] = coupling_at(h, tn);
+      h->hetab[3 * n + 1] = coupling_at(h, tn + 0.5 * dt);
+      h->hetab[3 * n + 2] = coupling_at(h, tn + dt);
+    } else {
+      h->hetab[n] = coupling_at(h, tn + 0.5 * dt);
+    }
+  }
+  // pageable source: the copy is staged before the call returns, so hetab may change afterwards
+  TDSE_CUDA(h, cudaMemcpyAsync(h->etab, h->hetab.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, h->stream),
+            "field table upload");
+  TDSE_LAUNCH(h, TDSE_K_SMALL_GRID,
+              launch_small_grid(h->small_plan, h->g, view(h), method, order, dt, nsteps, h->etab, h->psi, h->ls,
+                                h->red, h->status, h->stream),
+              "small-grid cluster run");
+  *done = true;
+  h->small_used = 1;
+  return TDSE_OK;
+}
+
 // ---- step plans ------------------------------------------------------------
 int taylor_steps(tdse *h, int P, double dt, long nsteps) {
-  int rc = ensure_work(h, 2);
+  bool done = false;
+  int rc = small_grid_steps(h, TDSE_TAYLOR, P, dt, nsteps, &done);
+  if (rc || done) return rc;
+  rc = ensure_work(h, 2);
   if (rc) return rc;
   const OperatorView op = view(h);
   const size_t G = npts(h);
@@ -566,7 +635,10 @@ int taylor_steps(tdse *h, int P, double dt, long nsteps) {
 }
 
 int rk4_steps(tdse *h, double dt, long nsteps) {
-  int rc = ensure_work(h, 3);
+  bool done = false;
+  int rc = small_grid_steps(h, TDSE_RK4, 4, dt, nsteps, &done);
+  if (rc || done) return rc;
+  rc = ensure_work(h, 3);
   if (rc) return rc;
   const OperatorView op = view(h);
   const size_t G = npts(h);
@@ -585,8 +657,11 @@ int rk4_steps(tdse *h, double dt, long nsteps) {
 }
 
 int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
+  bool done = false;
+  int rc = small_grid_steps(h, TDSE_LANCZOS, m, dt, nsteps, &done);
+  if (rc || done) return rc;
   // work slot 0: z; slots 1..m-1: U_1..U_{m-1} (U_0 is psi itself)
-  int rc = ensure_work(h, (size_t)(m > 1 ? m : 1));
+  rc = ensure_work(h, (size_t)(m > 1 ? m : 1));
   if (rc) return rc;
   const OperatorView op = view(h);
   const size_t G = npts(h);
@@ -1056,6 +1131,7 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
   int rc = check_usable(h);
   if (rc) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  h->small_used = 0;
   const bool mixed = h->opts.precision == TDSE_MIXED;
   if (nsteps > 0) {
     // each path keeps its own cached norm / split; work in the other one invalidates it
@@ -1507,6 +1583,17 @@ int tdse_apply_h(tdse_t *h, double E, const void *x, void *y) {
   TDSE_LAUNCH(h, TDSE_K_APPLY_H, launch_apply_h(h->g, view(h), e, (const double2 *)x, (double2 *)y, h->stream), "apply_h");
   return TDSE_OK;
 }
+
+int tdse_set_small_grid_path(tdse_t *h, int mode) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (mode != TDSE_SMALL_GRID_AUTO && mode != TDSE_SMALL_GRID_OFF && mode != TDSE_SMALL_GRID_FORCE)
+    return fail(h, TDSE_ERR_ARG, "small-grid path mode must be AUTO, OFF or FORCE");
+  h->small_mode = mode;
+  return TDSE_OK;
+}
+
+int tdse_small_grid_path_used(const tdse_t *h) { return h ? h->small_used : 0; }
 
 int tdse_sync(tdse_t *h) {
   int rc = check_usable(h);

@@ -760,7 +760,7 @@ size_t instance_bytes(const tdse_instance_spec &s, int precision) {
 
 Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
-  for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
+  for (CachedGraph &g : graphs) cudaGraphExecDestroy(g.exec);
   cudaFree(inst);
   cudaFree(ls);
   cudaFree(ticket);
@@ -797,6 +797,7 @@ int Engine::init(int cap, int st, int prec) {
   hinst.assign(cap, BatchInst{});
   spec.assign(cap, tdse_instance_spec{});
   nstep.assign(cap, 0);
+  tstart.assign(cap, 0.0);
   placed.assign(cap, 0);
   norm_valid.assign(cap, 0);
   const bool ok = cudaMalloc(&inst, sizeof(BatchInst) * cap) == cudaSuccess &&
@@ -963,6 +964,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   hinst[slot] = I;
   spec[slot] = s;
   nstep[slot] = 0;
+  tstart[slot] = 0.0;
   placed[slot] = 1;
   norm_valid[slot] = 0;
   return TDSE_OK;
@@ -976,7 +978,16 @@ void Engine::clear(int slot) {
 }
 
 double Engine::time_of(int slot) const {
-  return (slot >= 0 && slot < capacity) ? (double)nstep[slot] * spec[slot].dt : 0.0;
+  return (slot >= 0 && slot < capacity) ? tstart[slot] + (double)nstep[slot] * spec[slot].dt : 0.0;
+}
+
+int Engine::set_time(int slot, double t) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot] || !std::isfinite(t))
+    return fail(TDSE_ERR_ARG, "bad instance or non-finite time");
+  tstart[slot] = t;
+  nstep[slot] = 0;
+  return TDSE_OK;
 }
 
 long long Engine::steps_of(int slot) const { return (slot >= 0 && slot < capacity) ? nstep[slot] : 0; }
@@ -1111,6 +1122,7 @@ int Engine::launch_lists(const std::vector<int> &ids, bool elementwise, int &lis
 namespace {
 
 constexpr long kGraphMinSteps = 3;   // segments this long replay one captured step graph
+constexpr size_t kGraphCache = 8;    // captured step graphs kept across runs
 
 template <int ST, int PF>
 void launch_a_pf(bool mixed, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
@@ -1167,10 +1179,40 @@ void launch_a_vg_st(int pf, unsigned grid, cudaStream_t st, const BatchDev &B, c
 }  // namespace
 
 void Engine::drop_graphs() {
+  last_eager.clear();
   if (graphs.empty()) return;
   cudaStreamSynchronize(stream);
-  for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
+  for (CachedGraph &g : graphs) cudaGraphExecDestroy(g.exec);
   graphs.clear();
+}
+
+// Everything a captured step of this segment depends on: the schedule, the
+// device buffers its launches point into, the segment's list offsets and
+// counts and the chunk lists themselves (the instance descriptors, Krylov
+// dimensions and steps are read on the device when the graph runs).
+std::vector<long long> Engine::segment_key(const Segment &sg) const {
+  std::vector<long long> k;
+  k.reserve(32 + 9 * sg.off.size() + hlists.size());
+  k.push_back(precision);
+  k.push_back(stencil);
+  k.push_back(sched.pf);
+  k.push_back(sched.ring);
+  k.push_back(sched.sblocks);
+  k.push_back(sched.eblocks);
+  k.push_back(capacity);
+  k.push_back(sg.maxm);
+  for (const void *p : {(const void *)inst, (const void *)ls, (const void *)ticket, (const void *)status,
+                        (const void *)m_dev, (const void *)dt_dev, (const void *)E_dev, (const void *)step_dev,
+                        (const void *)lists})
+    k.push_back((long long)(uintptr_t)p);
+  for (const std::vector<int> *v : {&sg.off, &sg.nact, &sg.total, &sg.voff, &sg.vnact, &sg.vtotal, &sg.eoff,
+                                    &sg.enact, &sg.etotal}) {
+    k.push_back((long long)v->size());
+    k.insert(k.end(), v->begin(), v->end());
+  }
+  k.push_back((long long)hlists.size());
+  k.insert(k.end(), hlists.begin(), hlists.end());
+  return k;
 }
 
 BatchDev Engine::device_view() const {
@@ -1344,7 +1386,6 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     kmax = std::max(kmax, steps[q]);
   }
   if (kmax == 0) return TDSE_OK;
-  drop_graphs();
   // launch errors are read with cudaGetLastError: drop an earlier, unrelated
   // non-sticky error of this thread first (a sticky one fails the launches too)
   cudaGetLastError();
@@ -1382,7 +1423,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     const int s = slots[q];
     const tdse_instance_spec &sp = spec[s];
     for (long n = 0; n < steps[q]; ++n) {
-      const double tn = (double)(nstep[s] + n) * sp.dt;
+      const double tn = tstart[s] + (double)(nstep[s] + n) * sp.dt;
       hE[(size_t)n * capacity + s] = pulse_at(sp, tn + 0.5 * sp.dt);
     }
   }
@@ -1390,12 +1431,31 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   if (rc) return rc;
   const BatchDev B = device_view();
   if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) return rc;
+  std::vector<std::vector<long long>> eager;
   for (const Segment &sg : segs) {
     const long nst = sg.n1 - sg.n0;
     int count = 0;
-    if (!profiling && nst >= kGraphMinSteps) {
+    if (profiling) {
+      for (long n = 0; n < nst; ++n) {
+        if ((rc = enqueue_step(B, sg, count))) return rc;
+        launches += count;
+      }
+      continue;
+    }
+    std::vector<long long> key = segment_key(sg);
+    CachedGraph *hit = nullptr;
+    for (CachedGraph &g : graphs)
+      if (g.key == key) hit = &g;
+    bool repeat = false;
+    for (const std::vector<long long> &k : last_eager) repeat = repeat || k == key;
+    if (!hit && (nst >= kGraphMinSteps || repeat)) {
       // capture one step and replay it: the step counter on the device selects
       // each step's field
+      if (graphs.size() >= kGraphCache) {
+        EN_CUDA(cudaStreamSynchronize(stream), "sync before dropping a step graph");
+        cudaGraphExecDestroy(graphs.front().exec);
+        graphs.erase(graphs.begin());
+      }
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
       EN_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -1409,16 +1469,24 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
       const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
       cudaGraphDestroy(g);
       EN_CUDA(ei, "instantiate step graph");
-      graphs.push_back(ge);
-      for (long n = 0; n < nst; ++n) EN_CUDA(cudaGraphLaunch(ge, stream), "step graph launch");
-      launches += (long long)count * nst;
+      graphs.push_back(CachedGraph{std::move(key), ge});
+      hit = &graphs.back();
+      graph_launches_per_step = count;
+      hit->count = count;
+    }
+    if (hit) {
+      for (long n = 0; n < nst; ++n) EN_CUDA(cudaGraphLaunch(hit->exec, stream), "step graph launch");
+      launches += (long long)hit->count * nst;
+      graph_steps += nst;
     } else {
       for (long n = 0; n < nst; ++n) {
         if ((rc = enqueue_step(B, sg, count))) return rc;
         launches += count;
       }
+      eager.push_back(std::move(key));
     }
   }
+  last_eager = std::move(eager);
   for (size_t q = 0; q < slots.size(); ++q) nstep[slots[q]] += steps[q];
   return TDSE_OK;
 }
@@ -1456,7 +1524,7 @@ int Engine::autotune(const std::vector<int> &slots) {
   sg.n1 = 1;
   build_segment(sg, act);
   hE.assign((size_t)capacity, 0.0);
-  for (int s : act) hE[s] = pulse_at(spec[s], (double)nstep[s] * spec[s].dt + 0.5 * spec[s].dt);
+  for (int s : act) hE[s] = pulse_at(spec[s], tstart[s] + (double)nstep[s] * spec[s].dt + 0.5 * spec[s].dt);
   int rc = upload_run((size_t)capacity);
   if (rc) return rc;
   const BatchDev B = device_view();
@@ -1724,6 +1792,12 @@ double tdse_batch_get_time(const tdse_batch_t *b, int i) {
   return (b && i >= 0 && i < b->count) ? b->eng.time_of(i) : 0.0;
 }
 
+int tdse_batch_set_time(tdse_batch_t *b, int i, double t) {
+  if (!b) return TDSE_ERR_ARG;
+  if (i < 0 || i >= b->count) return b->eng.fail(TDSE_ERR_ARG, "instance index out of range");
+  return b->eng.set_time(i, t);
+}
+
 int tdse_batch_propagate(tdse_batch_t *b, long nsteps) {
   TraceRange trace("tdse_batch_propagate");
   if (!b) return TDSE_ERR_ARG;
@@ -1827,6 +1901,7 @@ int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, 
 
 long long tdse_batch_points(const tdse_batch_t *b) { return b ? b->npts : 0; }
 long long tdse_batch_launch_count(const tdse_batch_t *b) { return b ? b->eng.launches : 0; }
+long long tdse_batch_graph_steps(const tdse_batch_t *b) { return b ? b->eng.graph_steps : 0; }
 
 int tdse_batch_profile(tdse_batch_t *b, int enable) { return b ? b->eng.profile(enable) : TDSE_ERR_ARG; }
 

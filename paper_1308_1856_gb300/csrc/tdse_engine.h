@@ -115,6 +115,8 @@ class Engine {
   int autotune(const std::vector<int> &slots);
   int set_schedule(const Schedule &s);
   double time_of(int slot) const;
+  // Put a slot at time t (its step count restarts from there).
+  int set_time(int slot, double t);
   long long steps_of(int slot) const;
   int fail(int code, const std::string &msg);
 
@@ -122,9 +124,12 @@ class Engine {
   Schedule sched;
   std::vector<BatchInst> hinst;
   std::vector<tdse_instance_spec> spec;
-  std::vector<long long> nstep;   // steps taken by each slot (t = nstep * dt)
+  std::vector<long long> nstep;   // steps taken by each slot since tstart (t = tstart + nstep * dt)
+  std::vector<double> tstart;
   std::vector<char> placed, norm_valid;
   long long launches = 0;
+  long long graph_steps = 0;      // segment steps replayed from captured graphs
+  int graph_launches_per_step = 0;
   std::string err;
   bool poisoned = false;
   cudaStream_t own_stream = nullptr, stream = nullptr;
@@ -164,7 +169,19 @@ class Engine {
   double *E_dev = nullptr;
   size_t E_cap = 0;
   int *step_dev = nullptr;       // step counter of the run (BatchDev::step)
-  std::vector<cudaGraphExec_t> graphs;   // step graphs of the last run (freed after a sync)
+  // Captured step graphs, kept across runs: a segment whose launches (lists,
+  // schedule, device buffers) equal a cached one's replays that graph.  A
+  // segment is captured when it runs at least kGraphMinSteps steps or when
+  // the same segment ran uncaptured in the previous run (a caller that
+  // advances one step per call).
+  struct CachedGraph {
+    std::vector<long long> key;
+    cudaGraphExec_t exec;
+    int count;                   // kernels per replayed step
+  };
+  std::vector<CachedGraph> graphs;
+  std::vector<std::vector<long long>> last_eager;   // keys of the previous run's uncaptured segments
+  std::vector<long long> segment_key(const Segment &sg) const;
   int *lists = nullptr;          // chunk lists of the launches of one run
   size_t lists_cap = 0;
   double *obs_partials = nullptr, *obs_out = nullptr;

@@ -114,6 +114,23 @@ struct RkStageArgs {
 cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
                                     const double2 *gin, const double2 *psi, const RkStageArgs &a,
                                     Reduction *red, cudaStream_t st);
+// ---- small grids: a whole run in one cluster launch (tdse_cluster.cu) --------
+// Taylor, RK4 or Lanczos steps of an FP64 length-gauge grid small enough that
+// the state and every work vector fit in the shared memory of one cluster of
+// at most 16 CTAs (one per SM).  plan_small_grid picks the cluster (ctas CTAs,
+// W radial columns each) or returns ok = false.  etab: the mid-step field per
+// step (Taylor, Lanczos) or the fields at t_n, t_n + dt/2, t_n + dt (RK4).
+// The Lanczos run leaves ||psi|| in ls (psinorm, sigma[0]) and red->normsq;
+// a non-finite state sets kStatusNonFinite.
+struct SmallPlan {
+  bool ok = false;
+  int ctas = 0, W = 0;
+  size_t smem = 0;
+};
+SmallPlan plan_small_grid(const Geometry &g, int method, int order);
+cudaError_t launch_small_grid(const SmallPlan &p, const Geometry &g, const OperatorView &op, int method,
+                              int order, double dt, long nsteps, const double *etab, double2 *psi,
+                              LanczosScalars *ls, Reduction *red, int *status, cudaStream_t st);
 // ---- Sec. 4 dipole moments and flux (tdse_kernels_flux.cu) -------------------
 // out[0..2] = <z>, d<z>/dt, d^2<z>/dt^2 of psi (E the field, ac = A/c in the
 // velocity gauge else 0; the acceleration is NaN unless coulomb).  partials:

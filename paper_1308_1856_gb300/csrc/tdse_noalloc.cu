@@ -83,18 +83,20 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < N; i += nbx * kThreads) {
     const size_t idx = (size_t)l * N + i;
     const double2 f = psi[idx];
-    const double a = fma(f.x, f.x, f.y * f.y);
-    const double r = (double)(i + 1) * dr + offset;
+    const double a = __fma_rn(f.x, f.x, __dmul_rn(f.y, f.y));
+    // rounded as the host's grid table (multiply, then add; no fused step), so
+    // that r_j <= r_b decides the same way when r_b falls on a grid point
+    const double r = __dadd_rn(__dmul_rn((double)(i + 1), dr), offset);
     q[0] += a;
     if (r <= r_b) q[1] += a;
     if (l < L) {
       const double2 g = psi[idx + N];
-      q[2] = fma(r, fma(f.x, g.x, f.y * g.y), q[2]);
+      q[2] = __fma_rn(r, __fma_rn(f.x, g.x, __dmul_rn(f.y, g.y)), q[2]);
     }
     if (l == 0 && ref0) {
       const double2 c = ref0[i];
-      q[3] += fma(c.x, f.x, c.y * f.y);
-      q[4] += fma(c.x, f.y, -c.y * f.x);
+      q[3] += __fma_rn(c.x, f.x, __dmul_rn(c.y, f.y));
+      q[4] += __fma_rn(c.x, f.y, __dmul_rn(-c.y, f.x));
     }
   }
   const size_t nb = (size_t)nbx * (L + 1);
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(kThreads)
     out[1] = dip;
     out[2] = 1.0 - dr * inside;
     out[3] = ore * ore + oim * oim;
+    // a state holding Inf or NaN makes the norm sum non-finite
+    out[L + 5] = isfinite(norm) ? 0.0 : 1.0;
     scratch->ticket = 0u;
   }
 }

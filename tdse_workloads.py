@@ -154,6 +154,20 @@ def batched_specs(count: int = 256, seed: int = 1308) -> List[InstanceSpec]:
     return out
 
 
+def converging_dt(N: int, dr: float, lmax: int, krylov: int, stencil: int = 5, E0: float = 0.0,
+                  offset: float = 0.0) -> float:
+    """A step at which a Krylov propagator of dimension `krylov` converges on
+    this grid: rho dt = krylov / 2, with rho a Gershgorin bound on the
+    spectral radius of the operator (the second-difference weights
+    (30 + 32 + 2)/24 or 4/2 over dr^2, the largest centrifugal term at the
+    first point, the Coulomb term there and the coupling r_N E0 (k + k)).
+    This chooses an input (the step); it is not part of the propagation."""
+    r1 = dr + offset
+    lap = (64.0 / 24.0 if stencil == 5 else 2.0) / (dr * dr)
+    rho = lap + lmax * (lmax + 1) / (2.0 * r1 * r1) + 1.0 / r1 + 2.0 * abs(E0) * (N * dr + offset)
+    return 0.5 * krylov / rho
+
+
 def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
     """Arrival times (s) of `count` requests of a Poisson process of the given
     mean rate (req/s): exponential gaps, the first request at t = 0."""

@@ -53,6 +53,33 @@ def test_batch_matches_oracle(precision, tol):
     b.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_batch_set_time_and_state_mid_pulse(precision, tol):
+    """Instances put at a time inside their pulse, with smooth states: the
+    steps take the pulse from there (as oracle.propagate with t0)."""
+    from paper_1308_1856_gb300 import Batch
+    nsteps = 12
+    b = Batch(SPECS, precision=precision)
+    t0s, psis = [], []
+    for i, s in enumerate(SPECS):
+        T = 2 * np.pi * s.get("ncycles", 2.0) / s.get("omega", 0.057)
+        t0s.append(0.37 * T + 0.1 * i)
+        psis.append(W.smooth_state(s["N"], s["dr"], s["lmax"], seed=40 + i))
+        b.set_state(i, psis[-1])
+        b.set_time(i, t0s[-1])
+    b.propagate(nsteps)
+    for i, s in enumerate(SPECS):
+        assert abs(b.time(i) - (t0s[i] + nsteps * s["dt"])) <= 1e-12 * max(1.0, t0s[i])
+        g = oracle.Grid(N=s["N"], h=s["dr"], L=s["lmax"], stencil=5)
+        pulse = oracle.Pulse(E0=s.get("E0", 0.0), omega=s.get("omega", 0.057), ncycles=s.get("ncycles", 2.0),
+                             cep=s.get("cep", 0.0))
+        mask = oracle.Mask(s["absorber_r"]) if "absorber_r" in s else None
+        want, _ = oracle.propagate(g, psis[i], "lanczos", s["krylov"], s["dt"], nsteps, t0=t0s[i], pulse=pulse,
+                                   mask=mask)
+        assert rel_l2(b.get_state(i), want) <= tol, (i, rel_l2(b.get_state(i), want))
+    b.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_alone_equals_in_the_mix(precision):
     """Per-instance reductions are chunked independently of the batch, so an
@@ -95,8 +122,10 @@ def test_batch_schedule_and_graph_replay_do_not_change_results(precision):
     as step-by-step launches with the default schedule."""
     from paper_1308_1856_gb300 import Batch
     ref = Batch(SPECS, precision=precision)
+    ref.profile(True)                       # timed launches: never a graph
     for _ in range(7):
-        ref.propagate(1)                    # one-step runs: no graph
+        ref.propagate(1)
+    assert ref.graph_steps == 0
     want = [ref.get_state(i) for i in range(len(SPECS))]
     ref.close()
     for sch in SCHEDULES:
@@ -106,6 +135,41 @@ def test_batch_schedule_and_graph_replay_do_not_change_results(precision):
         for i in range(len(SPECS)):
             assert np.array_equal(b.get_state(i), want[i]), (sch, i)
         b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_one_step_calls_replay_a_cached_graph(precision):
+    """A caller that advances one step per call: the second call with the same
+    launches is captured, every later one replays the cached graph, and the
+    states equal those of separate launches bitwise.  A schedule change
+    captures a new graph; switching back replays the first one."""
+    from paper_1308_1856_gb300 import Batch
+    ref = Batch(SPECS, precision=precision)
+    ref.profile(True)
+    for _ in range(11):
+        ref.propagate(1)
+    want = [ref.get_state(i) for i in range(len(SPECS))]
+    ref.close()
+    b = Batch(SPECS, precision=precision)
+    b.propagate(1)                          # the norm pass first: another launch list
+    b.propagate(1)
+    assert b.graph_steps == 0
+    for _ in range(5):
+        b.propagate(1)
+    assert b.graph_steps == 5
+    first = b.schedule()
+    b.set_schedule(0, 1, 1)
+    b.propagate(1)                          # new launches: separate launches first
+    b.propagate(1)
+    assert b.graph_steps == 6
+    b.set_schedule(first["prefetch_rows"], first["stencil_blocks_per_sm"], first["elem_blocks_per_sm"],
+                   ring_rows=first["ring_rows"])
+    b.propagate(1)                          # the first schedule's graph is still cached
+    b.propagate(1)
+    assert b.graph_steps == 8
+    for i in range(len(SPECS)):
+        assert np.array_equal(b.get_state(i), want[i]), i
+    b.close()
 
 
 def test_batch_autotune_leaves_the_state_untouched():

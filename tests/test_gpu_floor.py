@@ -34,6 +34,7 @@ def test_full_pulse_small_config(method, order, dt):
     psi0 = W.hydrogen_1s(c.N, c.dr, c.lmax)
     t = make(c.N, c.dr, c.lmax, c.stencil, pulse=pulse)
     t.propagate(method, order, dt, nsteps)
+    assert t.small_grid_path_used      # the whole pulse in one cluster launch
     got = t.get_state()
     ob = t.observables()
     t.close()
@@ -58,6 +59,7 @@ def test_full_pulse_small_config_lanczos_vs_floor():
     psi0 = W.hydrogen_1s(c.N, c.dr, c.lmax)
     t = make(c.N, c.dr, c.lmax, c.stencil, pulse=pulse)
     t.propagate("lanczos", 12, dt, nsteps)
+    assert t.small_grid_path_used      # the whole pulse in one cluster launch
     got = t.get_state()
     ob = t.observables()
     t.close()

@@ -50,13 +50,13 @@ def test_velocity_one_step(method, order, dt, geom):
 
 def test_velocity_full_pulse_and_gauge_invariance():
     """A one-cycle pulse on a small grid from the imaginary-time ground state
-    (5027 Lanczos-10 steps): the velocity-gauge run matches the oracle, and
-    after the pulse its populations match the GPU's length-gauge run to the
-    step error.  Over this many steps an FP64 result depends on the order of
-    its sums at the 1e-10 level: the oracle's own distance to its long-double
-    build is 2e-11, and GPU builds that associate differently (the reduction
-    tree follows the SM count) have landed between 5e-11 and 2e-10 from it.
-    The state is held to 1e-9, the populations to 1e-10."""
+    (5027 Lanczos-10 steps).  Over this many steps an FP64 result depends on
+    the order of its sums: the FP64 oracle itself drifts ~1.5e-11 from its
+    long-double build (the floor).  So, as for every rounding-limited run
+    (tests/test_gpu_floor.py), the GPU state is held to 10 x max(floor, 1e-15)
+    against the long-double oracle, and the populations and p_ground to 1e-10
+    of the long-double oracle's.  After the pulse the velocity-gauge
+    populations match the GPU's length-gauge run to the step error."""
     N, dr, L = 300, 0.1, 6
     pulse = oracle.Pulse(E0=0.05, omega=0.25, ncycles=1)
     dt = 0.005
@@ -73,9 +73,13 @@ def test_velocity_full_pulse_and_gauge_invariance():
         t.close()
     got, ob = out["velocity"]
     g = grid_of(N, dr, L, 5, gauge=1)
-    want, _ = oracle.propagate(g, psi0, "lanczos", 10, dt, n, pulse=pulse)
-    assert rel_l2(got, want) <= 1e-9, rel_l2(got, want)
-    ow = oracle.observables(g, want, psi0[0], r_b=10.0)
+    f64, _ = oracle.propagate(g, psi0, "lanczos", 10, dt, n, pulse=pulse)
+    fld, _ = oracle.propagate(g, psi0, "lanczos", 10, dt, n, pulse=pulse, precision="fld")
+    floor = rel_l2(f64, fld)
+    gpu = rel_l2(got, fld)
+    print(f"velocity full pulse: floor={floor:.3e} gpu_vs_long_double={gpu:.3e} gpu_vs_f64={rel_l2(got, f64):.3e}")
+    assert gpu <= 10 * max(floor, 1e-15), (gpu, floor)
+    ow = oracle.observables(g, fld, psi0[0], r_b=10.0, precision="fld")
     assert abs(ob["p_ground"] - ow["p_ground"]) <= 1e-10 and np.abs(ob["l_pop"] - ow["l_pop"]).max() <= 1e-10
     ol = out["length"][1]
     assert abs(ob["p_ground"] - ol["p_ground"]) <= 1e-4, (ob["p_ground"], ol["p_ground"])
