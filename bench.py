@@ -1013,10 +1013,13 @@ def run_step_observables(D, steps=5, warmup=3, ntheta=180, r_b=10.0):
 def run_probe(D):
     """FP64 and FP32 FMA throughput of this GPU (tdse_fma_throughput)."""
     from paper_1308_1856_gb300 import fma_throughput
-    f64 = fma_throughput(True, D.sptr) / 1e12
-    f32 = fma_throughput(False, D.sptr) / 1e12
+    sampler = ClockSampler(gpu_uuid(D.dev.index))
+    sampler.start()
+    f64 = max(fma_throughput(True, D.sptr) for _ in range(5)) / 1e12
+    f32 = max(fma_throughput(False, D.sptr) for _ in range(3)) / 1e12
+    clocks = sampler.stop()
     clk = SM_MAX_MHZ * 1e6
-    return {"fp64_tflops": f64, "fp32_tflops": f32,
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "clocks": clocks,
             "fp64_fma_per_clk_per_sm_at_max_clock": f64 * 1e12 / 2 / D.sms / clk,
             "fp32_fma_per_clk_per_sm_at_max_clock": f32 * 1e12 / 2 / D.sms / clk,
             "fp64_peak_derived_tflops": D.fp64_peak, "sms": D.sms}

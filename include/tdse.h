@@ -396,6 +396,22 @@ int tdse_sync(tdse_t *h);
  */
 int tdse_fma_throughput(int fp64, double *flops_per_s, void *cuda_stream);
 
+/*
+ * The small exponential of a Lanczos step on its own (Sec. 5 "Lanczos.c",
+ * Appendix "Lanczos methods"): c = exp(-i T dt) e_1 (imag = 1: exp(-T dt) e_1)
+ * for the real symmetric tridiagonal T with diagonal alpha[0..m-1] and
+ * off-diagonal beta[0..m-2] (host arrays), on the GPU with the kernel body
+ * every Lanczos step uses (FP32 Jacobi eigendecomposition, FP64 Ogita-Aishima
+ * refinement, FP64 phases).  The Krylov space is cut at the first j with
+ * beta_j <= 1e-13 max(1, max_{i<=j} |alpha_i|): *kdim (may be NULL) receives
+ * the dimension kept and c_out (host, 2 m doubles, interleaved complex) the
+ * coefficients, zero beyond it.  Synchronous on the legacy default stream;
+ * allocates one small device buffer per call.  Errors: TDSE_ERR_ARG (m outside
+ * 1..TDSE_MAX_KRYLOV, NULL arrays, dt <= 0), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_lanczos_expm(int m, const double *alpha, const double *beta, double dt, int imag, double *c_out,
+                      int *kdim);
+
 /* Number of kernel launches this handle has issued (for launch accounting). */
 long long tdse_launch_count(const tdse_t *h);
 

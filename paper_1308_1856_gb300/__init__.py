@@ -264,6 +264,21 @@ def fma_throughput(fp64: bool = True, stream_ptr: int = 0) -> float:
     return out.value
 
 
+def lanczos_expm(alpha, beta, dt: float, imag: bool = False):
+    """c = exp(-i T dt) e_1 (exp(-T dt) e_1 if imag) for the tridiagonal T of
+    a Lanczos step, on the GPU (tdse_lanczos_expm): (c, Krylov dimension kept)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    m = a.size
+    b = np.ascontiguousarray(beta if m > 1 else np.zeros(1), dtype=np.float64)
+    c = np.zeros(2 * m)
+    k = ctypes.c_int()
+    rc = C.tdse_lanczos_expm(m, a.ctypes.data_as(C._dp), b.ctypes.data_as(C._dp), float(dt), 1 if imag else 0,
+                             c.ctypes.data_as(C._dp), ctypes.byref(k))
+    if rc != 0:
+        raise TDSEError(rc, "tdse_lanczos_expm failed")
+    return c.view(np.complex128).copy(), k.value
+
+
 def _spec_struct(s) -> "C.tdse_instance_spec":
     return C.tdse_instance_spec(int(s["N"]), float(s["dr"]), int(s["lmax"]), float(s.get("Z", 1.0)),
                                 float(s.get("E0", 0.0)), float(s.get("omega", 0.057)),

@@ -101,6 +101,7 @@ SIGNATURES = {
     "tdse_apply_h": (_c_int, [_vp, _c_double, _vp, _vp]),
     "tdse_sync": (_c_int, [_vp]),
     "tdse_fma_throughput": (_c_int, [_c_int, _dp, _vp]),
+    "tdse_lanczos_expm": (_c_int, [_c_int, _dp, _dp, _c_double, _c_int, _dp, ctypes.POINTER(_c_int)]),
     "tdse_set_small_grid_path": (_c_int, [_vp, _c_int]),
     "tdse_small_grid_path_used": (_c_int, [_vp]),
     "tdse_launch_count": (ctypes.c_longlong, [_vp]),
@@ -220,6 +221,7 @@ tdse_observables = _fn("tdse_observables")
 tdse_apply_h = _fn("tdse_apply_h")
 tdse_sync = _fn("tdse_sync")
 tdse_fma_throughput = _fn("tdse_fma_throughput")
+tdse_lanczos_expm = _fn("tdse_lanczos_expm")
 tdse_set_small_grid_path = _fn("tdse_set_small_grid_path")
 tdse_small_grid_path_used = _fn("tdse_small_grid_path_used")
 tdse_launch_count = _fn("tdse_launch_count")

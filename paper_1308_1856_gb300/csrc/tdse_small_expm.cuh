@@ -14,11 +14,14 @@
 //   1. an FP32 cyclic Jacobi method (k/2 rotations per round in parallel,
 //      round-robin pairing) gives an orthonormal basis accurate to FP32
 //      rounding (eigenvectors of close eigenvalues only to ~1e-3);
-//   2. three Ogita-Aishima refinement iterations in FP64 (matrix products,
+//   2. Ogita-Aishima refinement iterations in FP64 (at least three, more
+//      until the correction is negligible; matrix products,
 //      i.e. parallel DFMA throughput rather than latency) make X orthonormal
 //      and the eigenvalues accurate to FP64 rounding; pairs closer than the
 //      iteration's cluster bound are only orthogonalised;
-//   3. phases exp(-i lambda dt) in FP64.
+//   3. phases exp(-i lambda dt) in FP64, with a first-order correction for
+//      what the refinement leaves off the diagonal of X^T T X (rounding and
+//      the coupling inside eigenvalue clusters it cannot separate).
 // The breakdown rule beta_j <= 1e-13 max(1, max_{i<=j} |alpha_i|) fixes k.
 //
 // This header holds the one-block body (expm_body, 256 threads); it is
@@ -37,7 +40,15 @@ namespace {
 constexpr int kEx = 256;
 constexpr int KP = kMaxKrylov;
 constexpr int kJacobiSweeps = 12;
-constexpr int kRefineIters = 3;
+constexpr int kRefineIters = 3;      // refinement iterations always run
+constexpr int kRefineMax = 12;       // and at most this many, while the correction is not negligible
+// An iteration whose correction E has ||E||_F <= kRefineDone leaves X
+// orthonormal and the eigenvalues converged to FP64 rounding (the next
+// correction would be O(||E||^2)).  When the FP32 start mixes eigenvectors
+// whose eigenvalues lie within FP32 rounding of ||T|| of each other (stiff T:
+// ||T|| ~ 1e5 and eigenvalues ~ 1 apart), the first corrections are O(1) and
+// three iterations do not converge; the extra ones do.
+constexpr float kRefineDone = 1e-9f;
 // FP32 Jacobi stops once the off-diagonal mass is below this fraction of the
 // total (off-diagonal norm ~3e-6 relative): the FP64 refinement converges
 // quadratically from there (3e-6 -> 1e-11 -> 1e-22, i.e. FP64 rounding; the
@@ -221,7 +232,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     if (i + 1 < k) tnorm2 += 2.f * (float)be[i] * (float)be[i];
   }
   const double tnorm = (double)sqrtf(block_sum_f(tnorm2, shf));   // ||T||_F (also syncs X)
-  for (int it = 0; it < kRefineIters; ++it) {
+  for (int it = 0; it < kRefineMax; ++it) {
     // W = T X
     for (int w = tid; w < k * 32; w += kEx) {
       const int i = w >> 5, e = w & 31;
@@ -280,6 +291,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     const float rn = sqrtf(block_sum_f(r2, shf));
     const double delta = 2.0 * ((double)sdn + tnorm * (double)rn);
     // E (stored in W); the reciprocal of each gap avoids the ~640-cycle FP64 divide
+    float e2 = 0.f;
     for (int w = tid; w < k * 32; w += kEx) {
       const int a = w >> 5, b = w & 31;
       if (b < k) {
@@ -295,9 +307,10 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
           e = fma(lam[b], R[a][b], S[a][b]) * y;
         }
         W[a][b] = e;
+        e2 = fmaf((float)e, (float)e, e2);
       }
     }
-    __syncthreads();
+    const float en = sqrtf(block_sum_f(e2, shf));   // also the barrier before W is read
     // X <- X + X E   (new X into S, then copy)
     for (int w = tid; w < k * 32; w += kEx) {
       const int i = w >> 5, b = w & 31;
@@ -318,19 +331,93 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       if (b < k) X[i][b] = S[i][b];
     }
     __syncthreads();
+    if (it + 1 >= kRefineIters && en <= kRefineDone) break;   // uniform: en is a block sum
   }
 
-  // ---- c_i = sum_e X_ie X_0e exp(-i lambda_e dt)  (exp(-lambda_e dt) if imag)
-  if (tid < k) {
-    if (imag) {
-      W[0][tid] = X[0][tid] * exp(-lam[tid] * dt);
-      W[1][tid] = 0.0;
-    } else {
-      double sn, cs;
-      sincos(lam[tid] * dt, &sn, &cs);
-      W[0][tid] = X[0][tid] * cs;    // Re
-      W[1][tid] = -X[0][tid] * sn;   // Im
+  // ---- S = X^T T X of the final basis (orthonormal to FP64 rounding), so that
+  // exp(-i T dt) = X exp(-i S dt) X^T.  S = D + F with D its diagonal and F
+  // what the refinement leaves off the diagonal: rounding, and the coupling
+  // inside eigenvalue clusters closer than its cluster bound, which it never
+  // separates (the bound cannot fall below that coupling).  To first order in F
+  //   exp(-i S dt) = exp(-i D dt) + Phi o F,  Phi_ab = (f(d_a) - f(d_b)) / (d_a - d_b),
+  // the divided differences of f(x) = exp(-i x dt) (exp(-x dt) in imaginary
+  // time; the derivative f'(d_a) where d_a = d_b); the O(|F dt|^2) remainder
+  // is below rounding.  M = f(D) + Phi o F goes to R (re) and W (im).
+  for (int w = tid; w < k * 32; w += kEx) {
+    const int i = w >> 5, e = w & 31;
+    if (e < k) {
+      double v = al[i] * X[i][e];
+      if (i > 0) v = fma(be[i - 1], X[i - 1][e], v);
+      if (i + 1 < k) v = fma(be[i], X[i + 1][e], v);
+      W[i][e] = v;
     }
+  }
+  __syncthreads();
+  for (int w = tid; w < k * 32; w += kEx) {
+    const int a = w >> 5, b = w & 31;
+    if (b < k) {
+      double s0 = 0.0, s1 = 0.0;
+      int i = 0;
+      for (; i + 1 < k; i += 2) {
+        s0 = fma(X[i][a], W[i][b], s0);
+        s1 = fma(X[i + 1][a], W[i + 1][b], s1);
+      }
+      if (i < k) s0 = fma(X[i][a], W[i][b], s0);
+      S[a][b] = s0 + s1;
+    }
+  }
+  __syncthreads();
+  for (int w = tid; w < k * 32; w += kEx) {
+    const int a = w >> 5, b = w & 31;
+    if (b < k) {
+      const double da = S[a][a], db = S[b][b];
+      const double mu = 0.5 * (da + db);
+      const double x = 0.5 * (da - db) * dt;      // half the phase difference
+      double mr, mi;
+      if (imag) {
+        double phi;
+        if (fabs(x) < 0.5) {
+          const double shx = (x == 0.0) ? 1.0 : sinh(x) / x;
+          phi = -dt * exp(-mu * dt) * shx;
+        } else {
+          phi = (exp(-da * dt) - exp(-db * dt)) / (da - db);
+        }
+        mr = (a == b) ? exp(-da * dt) : phi * S[a][b];
+        mi = 0.0;
+      } else {
+        // -i dt exp(-i mu dt) sinc(x): sinc is bounded, so no cancellation
+        const double snc = (x == 0.0) ? 1.0 : sin(x) / x;
+        double sn, cs;
+        sincos(mu * dt, &sn, &cs);
+        if (a == b) {
+          mr = cs;
+          mi = -sn;
+        } else {
+          const double f = dt * snc * S[a][b];
+          mr = -f * sn;
+          mi = -f * cs;
+        }
+      }
+      R[a][b] = mr;
+      W[a][b] = mi;
+    }
+  }
+  __syncthreads();
+  // v = M y with y_b = X_0b (the first row of X), into rows 0 and 1 of S
+  if (tid < k) {
+    double vr = 0.0, vi = 0.0;
+    for (int b = 0; b < k; ++b) {
+      const double y = X[0][b];
+      vr = fma(R[tid][b], y, vr);
+      vi = fma(W[tid][b], y, vi);
+    }
+    lam[tid] = vr;
+    al[tid] = vi;    // alpha is no longer needed
+  }
+  __syncthreads();
+  if (tid < k) {
+    W[0][tid] = lam[tid];
+    W[1][tid] = al[tid];
   }
   __syncthreads();
   if (tid < KP) {

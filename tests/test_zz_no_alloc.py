@@ -53,8 +53,8 @@ def _run(N, dr, L, offset, r_b, psi, ref, stream):
     import torch
     t = make(N, dr, L, 5, offset=offset, r_b=r_b)
     t.set_state(psi)
-    if ref is not None:
-        t.set_reference(ref)
+    # the handle's reference defaults to its 1s state: a zero wave stands for "none"
+    t.set_reference(ref if ref is not None else np.zeros(N, dtype=np.complex128))
     finite = bool(np.all(np.isfinite(psi)))
     want = t.observables() if finite else None
     psi_dev = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
