@@ -126,7 +126,7 @@ MIXED_BYTES_PER_GP = {
 MEASURED_TRAFFIC_PER_POINT = {
     ("batched", "fp64", "lanczos_a"): (537.5e6 + 165.8e6) / 10664737,
     ("batched", "fp64", "lanczos_b"): (343.0e6 + 138.5e6) / 10664737,
-    ("batched", "mixed", "lanczos_a"): (296.7e6 + 66.7e6) / 10664737,
+    ("batched", "mixed", "lanczos_a"): (218.7e6 + 56.2e6) / 10664737,
     ("batched", "mixed", "lanczos_b"): (171.2e6 + 52.7e6) / 10664737,
     ("single", "fp64", "taylor_stage"): 20.6e6 / 512000,
 }

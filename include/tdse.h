@@ -575,14 +575,19 @@ int tdse_batch_profile(tdse_batch_t *b, int enable);
 int tdse_batch_profile_read(tdse_batch_t *b, int kind, double *total_ms, long long *launches);
 
 /*
- * Launch schedule of the batched kernels: the rows the stencil kernels
- * prefetch ahead into L2 (0, 3, 6 or 10); for the mixed-precision stencil
- * kernel, the rows staged ahead through a per-warp ring of shared memory by
- * asynchronous copies (0 = off, 3 or 5; the prefetch distance is then
- * unused); and the blocks per SM of the stencil and of the elementwise
- * kernels (1 or 2, of 512 threads).  Results
- * do not depend on the schedule (bitwise): every reduction is split into
- * fixed per-instance chunks whatever the grid.  A run is cut into segments
+ * Launch schedule of the batched kernels.
+ *   prefetch_rows: the rows the FP64 stencil kernel prefetches ahead into L2
+ *     (0, 3, 6 or 10);
+ *   ring_rows: the mixed-precision stencil kernel walks tiles of 256 radial
+ *     columns x 32 partial waves, its rows brought into a ring of shared-memory
+ *     slots by bulk asynchronous copies; 0, 3 or 5 selects a ring of 4, 8 or
+ *     12 slots (1, 5 or 9 rows in flight beyond the three it reads);
+ *   stencil_blocks_per_sm: blocks per SM of the stencil kernels (1 or 2; 3 is
+ *     accepted and used by the mixed tile kernel, whose blocks are smaller);
+ *   elem_blocks_per_sm: blocks per SM of the elementwise kernels (1 or 2, of
+ *     512 threads).
+ * Results do not depend on the schedule (bitwise): every reduction is split
+ * into fixed per-instance chunks (tiles) whatever the grid.  A run is cut into segments
  * where its set of active instances changes; a segment of three or more
  * steps, or one that repeats the previous call's segment (a caller that
  * advances one step per call), runs as a captured CUDA graph of one step,

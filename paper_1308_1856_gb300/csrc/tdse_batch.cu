@@ -46,6 +46,9 @@ using namespace stencil;
 #ifndef TDSE_CHUNK_PTS
 #define TDSE_CHUNK_PTS 2048
 #endif
+#ifndef TDSE_TILE_ROWS
+#define TDSE_TILE_ROWS 32
+#endif
 // Reduction chunks.  Their sizes fix each instance's summation order, so they
 // are compile-time constants (the launch schedule never changes them).
 constexpr int kChunkSegs = TDSE_CHUNK_SEGS;  // 32-point row segments per chunk (stencil kernels)
@@ -414,105 +417,7 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   return in;
 }
 
-template <int ST, int PF>
-__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
-    bt_lanczos_a_mixed(BatchDev B, ChunkList cl, int j) {
-  for_my_chunks(cl, [&](int inst, int ci) {
-    const BatchInst I = B.inst[inst];
-    LanczosScalars *ls = B.ls + inst;
-    const long long G = (long long)I.N * (I.L + 1);
-    const float2 *hi = I.hi, *lo = I.lo;
-    float2 *z = I.mwork;
-    const float2 *uprev = (j >= 2) ? I.mwork + (long long)(j - 1) * G : nullptr;
-    const double sigd = ls->sigma[j];
-    const float sig = (float)sigd;
-    const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
-    PairSum acc;
-    auto epi = [&](int, size_t idx, float2 t, float2 u) {
-      float2 o = make_float2(sig * t.x, sig * t.y);
-      if (j > 0) {
-        float2 up;
-        if (uprev) {
-          up = uprev[idx];
-        } else {
-          const float2 h = hi[idx], l = lo[idx];
-          up = make_float2(h.x + l.x, h.y + l.y);
-        }
-        o.x = fmaf(-cprev, up.x, o.x);
-        o.y = fmaf(-cprev, up.y, o.y);
-      }
-      z[idx] = o;
-      acc.add(fmaf(u.x, o.x, u.y * o.y));
-    };
-    if (j == 0) {
-      const MixedIn in = mixed_in(B, I, inst, hi, lo, nullptr);
-      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false, PF>(in, i, l0, l1, epi); });
-    } else {
-      MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
-      if (uprev) {
-        in.pf0 = uprev;
-      } else {
-        in.pf0 = hi;
-        in.pf1 = lo;
-      }
-      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true, PF>(in, i, l0, l1, epi); });
-    }
-    const double accd = acc.value();
-    double s;
-    if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
-      ls->alpha[j] = s * sigd;
-      ls->acoef[j] = -(s * sigd) * sigd;
-    }
-  });
-}
-
-// Lanczos A (mixed) with the operand rows staged through a per-warp ring of
-// shared memory (staged_walk_rows, depth D); the same arithmetic as
-// bt_lanczos_a_mixed.  MODE 0: j = 0, the operand is the split of psi;
-// MODE 1: j = 1, U_0 (for the ratio term) is the split of psi; MODE 2: j >= 2.
-template <int ST, int D, int MODE>
-__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
-    bt_lanczos_a_mixed_staged(BatchDev B, ChunkList cl, int j) {
-  extern __shared__ float2 ring_smem[];
-  constexpr bool S = MODE == 0;
-  constexpr int NE = MODE == 0 ? 0 : (MODE == 1 ? 2 : 1);
-  float2 *ring = ring_smem + (threadIdx.x >> 5) * (D + 1) * RingLayout<S, !S, NE>::kSlot;
-  for_my_chunks(cl, [&](int inst, int ci) {
-    const BatchInst I = B.inst[inst];
-    LanczosScalars *ls = B.ls + inst;
-    const long long G = (long long)I.N * (I.L + 1);
-    float2 *z = I.mwork;
-    const double sigd = ls->sigma[j];
-    const float sig = (float)sigd;
-    const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
-    PairSum acc;
-    auto epi = [&](int, size_t idx, float2 t, float2 u, float2 e0, float2 e1) {
-      float2 o = make_float2(sig * t.x, sig * t.y);
-      if (MODE > 0) {
-        const float2 up = (MODE == 1) ? make_float2(e0.x + e1.x, e0.y + e1.y) : e0;
-        o.x = fmaf(-cprev, up.x, o.x);
-        o.y = fmaf(-cprev, up.y, o.y);
-      }
-      z[idx] = o;
-      acc.add(fmaf(u.x, o.x, u.y * o.y));
-    };
-    MixedIn in = S ? mixed_in(B, I, inst, I.hi, I.lo, nullptr)
-                   : mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
-    if (MODE == 1) {
-      in.pf0 = I.hi;
-      in.pf1 = I.lo;
-    } else if (MODE == 2) {
-      in.pf0 = I.mwork + (long long)(j - 1) * G;
-    }
-    chunk_groups(I, ci, [&](int jg, int l0, int l1) { staged_walk_rows<ST, S, !S, NE, D>(in, ring, jg, l0, l1, epi); });
-    const double accd = acc.value();
-    double s;
-    if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
-      ls->alpha[j] = s * sigd;
-      ls->acoef[j] = -(s * sigd) * sigd;
-    }
-  });
-}
+#include "tdse_batch_tile.cuh"
 
 // SPLIT: U_j is U_0 = psi, read as its split (j = 0).
 template <bool SPLIT>
@@ -680,10 +585,14 @@ struct Layout {
   size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, ref0, rinv, total;
 };
 
+// Tiles of the mixed tile kernel on an N x (L+1) grid.
+int tile_count(int N, int L) { return ((N + kTileCols - 1) / kTileCols) * ((L + kTileRows) / kTileRows); }
+
 Layout layout_of(const tdse_instance_spec &s, int precision) {
   const size_t N = (size_t)s.N, Lp1 = (size_t)s.lmax + 1, G = N * Lp1, m = (size_t)s.krylov;
   const size_t nseg = ((N + 31) / 32) * Lp1;
-  const size_t nchunk = std::max((nseg + kChunkSegs - 1) / kChunkSegs, (G + kChunkPts - 1) / kChunkPts);
+  const size_t nchunk = std::max({(nseg + kChunkSegs - 1) / kChunkSegs, (G + kChunkPts - 1) / kChunkPts,
+                                  (size_t)tile_count(s.N, s.lmax)});
   const bool mixed = precision == TDSE_MIXED;
   Layout L;
   size_t off = 0;
@@ -852,7 +761,9 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.L = L;
   I.m = s.krylov;
   I.nseg = (int)((size_t)((N + 31) / 32) * (L + 1));
-  I.nchunk = (I.nseg + kChunkSegs - 1) / kChunkSegs;
+  // reduction chunks of the stencil kernel: 64 row segments (FP64), or tiles
+  // of 256 columns x kTileRows rows (the mixed tile kernel)
+  I.nchunk = mixed ? tile_count(N, L) : (I.nseg + kChunkSegs - 1) / kChunkSegs;
   I.nchunk_e = (int)((G + kChunkPts - 1) / kChunkPts);
   const double h2 = s.dr * s.dr;
   double c0;
@@ -1054,6 +965,19 @@ int Engine::profile_read(int kind, double *total_ms, long long *n) {
 int Engine::sync() {
   if (poisoned) return TDSE_ERR_STATE;
   EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  return check_status();
+}
+
+// A wait of the mixed tile kernel that gave up (kStatusTimeout): the results
+// of that launch are not trustworthy, so the engine is poisoned.
+int Engine::check_status() {
+  int st = 0;
+  EN_CUDA(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream), "read status");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync status");
+  if (st & kStatusTimeout) {
+    poisoned = true;
+    return fail(TDSE_ERR_CUDA, "a staged copy of the mixed stencil kernel did not arrive in time");
+  }
   return TDSE_OK;
 }
 
@@ -1125,44 +1049,50 @@ constexpr long kGraphMinSteps = 3;   // segments this long replay one captured s
 constexpr size_t kGraphCache = 8;    // captured step graphs kept across runs
 
 template <int ST, int PF>
-void launch_a_pf(bool mixed, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
-  if (mixed) bt_lanczos_a_mixed<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
-  else bt_lanczos_a_fp64<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
+void launch_a_pf(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  bt_lanczos_a_fp64<ST, PF><<<grid, kBlockJ, 0, st>>>(B, cl, j);
 }
 
-// Staged variant: dynamic shared memory of 16 warps' rings, raised above the
-// 48 KB default once per instantiation.
+// The mixed tile kernel: dynamic shared memory of its ring of D row slots,
+// raised above the 48 KB default once per instantiation.
 template <int ST, int D, int MODE>
-cudaError_t launch_staged_mode(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
-  constexpr bool S = MODE == 0;
-  constexpr int NE = MODE == 0 ? 0 : (MODE == 1 ? 2 : 1);
-  constexpr int bytes = (kBlockJ / 32) * ring_bytes<S, !S, NE, D>();
+cudaError_t launch_tile_mode(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  constexpr int bytes = tile_smem_bytes<MODE, D>();
   static bool configured = false;
   if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(bt_lanczos_a_mixed_staged<ST, D, MODE>,
+    const cudaError_t e = cudaFuncSetAttribute(bt_lanczos_a_mixed_tile<ST, MODE, D>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  bt_lanczos_a_mixed_staged<ST, D, MODE><<<grid, kBlockJ, bytes, st>>>(B, cl, j);
+  bt_lanczos_a_mixed_tile<ST, MODE, D><<<grid, kTileBlock, bytes, st>>>(B, cl, j);
   return cudaGetLastError();
 }
 
 template <int ST, int D>
-cudaError_t launch_staged(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
-  if (j == 0) return launch_staged_mode<ST, D, 0>(grid, st, B, cl, j);
-  if (j == 1) return launch_staged_mode<ST, D, 1>(grid, st, B, cl, j);
-  return launch_staged_mode<ST, D, 2>(grid, st, B, cl, j);
+cudaError_t launch_tile(unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
+  if (j == 0) return launch_tile_mode<ST, D, 0>(grid, st, B, cl, j);
+  if (j == 1) return launch_tile_mode<ST, D, 1>(grid, st, B, cl, j);
+  return launch_tile_mode<ST, D, 2>(grid, st, B, cl, j);
+}
+
+// ring of row slots (schedule ring_rows 0, 3, 5 -> 4, 8, 12 slots: 1, 5 or 9
+// rows in flight beyond the three the stencil holds)
+template <int ST>
+cudaError_t launch_tile_ring(int ring, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl,
+                             int j) {
+  if (ring == 0) return launch_tile<ST, 4>(grid, st, B, cl, j);
+  if (ring == 3) return launch_tile<ST, 8>(grid, st, B, cl, j);
+  return launch_tile<ST, 12>(grid, st, B, cl, j);
 }
 
 template <int ST>
-void launch_a_st(bool mixed, int pf, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl,
-                 int j) {
+void launch_a_st(int pf, unsigned grid, cudaStream_t st, const BatchDev &B, const ChunkList &cl, int j) {
   switch (pf) {
-    case 0: launch_a_pf<ST, 0>(mixed, grid, st, B, cl, j); break;
-    case 3: launch_a_pf<ST, 3>(mixed, grid, st, B, cl, j); break;
-    case 10: launch_a_pf<ST, 10>(mixed, grid, st, B, cl, j); break;
-    default: launch_a_pf<ST, 6>(mixed, grid, st, B, cl, j); break;
+    case 0: launch_a_pf<ST, 0>(grid, st, B, cl, j); break;
+    case 3: launch_a_pf<ST, 3>(grid, st, B, cl, j); break;
+    case 10: launch_a_pf<ST, 10>(grid, st, B, cl, j); break;
+    default: launch_a_pf<ST, 6>(grid, st, B, cl, j); break;
   }
 }
 
@@ -1291,16 +1221,14 @@ int Engine::norm_pass(const BatchDev &B, const std::vector<int> &ids, int off, i
 
 int Engine::launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s) {
   const unsigned grid = (unsigned)(sms * s.sblocks);
-  const bool mixed = precision == TDSE_MIXED;
-  if (mixed && s.ring > 0) {
-    cudaError_t e;
-    if (stencil == 5) e = (s.ring == 3) ? launch_staged<5, 3>(grid, stream, B, cl, j) : launch_staged<5, 5>(grid, stream, B, cl, j);
-    else e = (s.ring == 3) ? launch_staged<3, 3>(grid, stream, B, cl, j) : launch_staged<3, 5>(grid, stream, B, cl, j);
-    EN_CUDA(e, "batch lanczos a (staged)");
+  if (precision == TDSE_MIXED) {
+    const cudaError_t e = (stencil == 5) ? launch_tile_ring<5>(s.ring, grid, stream, B, cl, j)
+                                         : launch_tile_ring<3>(s.ring, grid, stream, B, cl, j);
+    EN_CUDA(e, "batch lanczos a (mixed tiles)");
     return TDSE_OK;
   }
-  if (stencil == 5) launch_a_st<5>(mixed, s.pf, grid, stream, B, cl, j);
-  else launch_a_st<3>(mixed, s.pf, grid, stream, B, cl, j);
+  if (stencil == 5) launch_a_st<5>(s.pf, grid, stream, B, cl, j);
+  else launch_a_st<3>(s.pf, grid, stream, B, cl, j);
   EN_CUDA(cudaGetLastError(), "batch lanczos a");
   return TDSE_OK;
 }
@@ -1495,7 +1423,7 @@ int Engine::set_schedule(const Schedule &s) {
   bool pf_ok = false, ring_ok = false;
   for (int p : kPfChoices) pf_ok = pf_ok || p == s.pf;
   for (int r : kRingChoices) ring_ok = ring_ok || r == s.ring;
-  if (!pf_ok || !ring_ok || s.sblocks < 1 || s.sblocks > kStencilBlocksPerSM || s.eblocks < 1 ||
+  if (!pf_ok || !ring_ok || s.sblocks < 1 || s.sblocks > kTileBlocksPerSM || s.eblocks < 1 ||
       s.eblocks > kElemBlocksPerSM)
     return fail(TDSE_ERR_ARG, "schedule outside the tuned choices");
   sched = s;
@@ -1562,13 +1490,16 @@ int Engine::autotune(const std::vector<int> &slots) {
   };
   Schedule bestS = sched;
   float bestA = 1e30f, bestB = 1e30f;
-  // the staged ring exists for the mixed stencil kernel only
+  // the staged rows are the mixed tile kernel's
   const int nring = precision == TDSE_MIXED ? (int)(sizeof(kRingChoices) / sizeof(int)) : 1;
-  for (int sb = 1; sb <= kStencilBlocksPerSM && !rc; ++sb)
+  // three blocks per SM only for the mixed tile kernel (the FP64 stencil kernel's blocks fill an SM at two)
+  const int sbmax = precision == TDSE_MIXED ? kTileBlocksPerSM : kStencilBlocksPerSM;
+  for (int sb = 1; sb <= sbmax && !rc; ++sb)
     for (int ri = 0; ri < nring && !rc; ++ri)
       for (int pf : kPfChoices) {
         const int ring = kRingChoices[ri];
-        if (ring > 0 && pf != kPfChoices[0]) continue;   // the ring does not use the prefetch distance
+        // the mixed tile kernel stages its rows itself: the prefetch distance is the FP64 kernel's
+        if (precision == TDSE_MIXED && pf != kPfChoices[0]) continue;
         Schedule c = sched;
         c.pf = pf;
         c.ring = ring;
@@ -1636,6 +1567,8 @@ int Engine::observables(int slot, std::vector<double> &out) {
   out.assign(I.L + 5, 0.0);
   EN_CUDA(cudaMemcpyAsync(out.data(), obs_out, sizeof(double) * (I.L + 5), cudaMemcpyDeviceToHost, stream), "read");
   EN_CUDA(cudaStreamSynchronize(stream), "sync");
+  rc = check_status();
+  if (rc) return rc;
   if (!std::isfinite(out[0])) return fail(TDSE_ERR_NONFINITE, "the instance holds Inf/NaN");
   return TDSE_OK;
 }

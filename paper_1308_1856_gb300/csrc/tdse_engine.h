@@ -70,11 +70,12 @@ struct BatchDev {
 struct Schedule {
   int pf = 6;                        // rows the stencil kernels prefetch ahead (kPfChoices)
   int ring = 0;                      // mixed stencil kernel: rows staged ahead in shared memory (0: off)
-  int sblocks = kStencilBlocksPerSM; // blocks per SM of the stencil kernels (1 or 2)
+  int sblocks = kStencilBlocksPerSM; // blocks per SM of the stencil kernels (1 or 2; 3 for the mixed tiles)
   int eblocks = kElemBlocksPerSM;    // blocks per SM of the elementwise kernels (1 or 2)
 };
 constexpr int kPfChoices[] = {0, 3, 6, 10};
 constexpr int kRingChoices[] = {0, 3, 5};
+constexpr int kTileBlocksPerSM = 3;   // the mixed tile kernel's blocks (288 threads) fit three to an SM
 
 // Bytes of device memory one instance needs (every array 256-byte aligned).
 size_t instance_bytes(const tdse_instance_spec &s, int precision);
@@ -106,6 +107,8 @@ class Engine {
   // out with one wait at the end.
   int copy_states(const std::vector<int> &slots, double *F_host, bool to_device);
   int sync();
+  // Synchronous: TDSE_ERR_CUDA (and poisoned) if a kernel reported a wait that gave up.
+  int check_status();
   int set_stream(void *cuda_stream);
   int profile(int enable);
   int profile_read(int kind, double *total_ms, long long *launches);

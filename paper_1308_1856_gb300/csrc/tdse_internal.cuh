@@ -60,7 +60,7 @@ struct Reduction {
 };
 
 // Device-side status word bits.
-enum : int { kStatusNonFinite = 1 };
+enum : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
 struct Geometry {
   int N, L, stencil;

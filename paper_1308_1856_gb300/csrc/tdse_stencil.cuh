@@ -319,164 +319,5 @@ __device__ __forceinline__ void mixed_walk_rows(const MixedIn &in, int i, int l0
 }
 
 
-// ---------------------------------------------------------------------------
-// Staged walk of the mixed operand: the same arithmetic as mixed_walk_rows,
-// with the rows brought into a per-warp ring of shared memory by cp.async
-// (LDGSTS) D rows ahead, so that D rows of loads are in flight per warp
-// without holding registers.  A ring slot holds one row of the warp's
-// 32-column group: each operand part with a two-column halo on both sides
-// (36 complex64 values), the 32 diagonal values and NE extra complex64 rows
-// that the caller's epilogue reads at the same index (f gets them as e0, e1).
-// Rows outside [0, L] and columns outside [0, N) read as zero.
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// 8- or 4-byte asynchronous copy global -> shared; ok = false writes zeros
-// (source size 0: nothing is read, src is only a valid placeholder).
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(ok ? 8 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(ok ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-template <bool S, bool Wp, int NE>
-struct RingLayout {
-  static constexpr int kH = 0;                        // float2 offsets inside a slot
-  static constexpr int kL = kH + (S ? 36 : 0);
-  static constexpr int kW = kL + (S ? 36 : 0);
-  static constexpr int kE = kW + (Wp ? 36 : 0);
-  static constexpr int kD = kE + 32 * NE;             // 32 floats = 16 float2
-  static constexpr int kSlot = kD + 16;               // float2 per slot
-};
-
-// Shared memory (bytes) of one warp's ring of depth D.
-template <bool S, bool Wp, int NE, int D>
-constexpr int ring_bytes() { return (D + 1) * RingLayout<S, Wp, NE>::kSlot * 8; }
-
-template <bool S, bool Wp>
-__device__ __forceinline__ Parts<S, Wp> ring_parts(const float2 *slot, int c) {
-  using RL = RingLayout<S, Wp, 0>;
-  Parts<S, Wp> p;
-  const float2 z = make_float2(0.f, 0.f);
-  p.h = S ? slot[RL::kH + c] : z;
-  p.l = S ? slot[RL::kL + c] : z;
-  p.w = Wp ? slot[RL::kW + c] : z;
-  return p;
-}
-
-// Walk rows [l0, l1) of column group jg; every lane of the warp must call it
-// (lanes whose column is >= N only help with the copies).  ring points at the
-// warp's D + 1 slots.  f(i, idx, Hx, x_center, e0, e1).
-template <int ST, bool S, bool Wp, int NE, int D, typename F>
-__device__ __forceinline__ void staged_walk_rows(const MixedIn &in, float2 *ring, int jg, int l0, int l1, F &&f) {
-  static_assert(D >= 2, "ring depth");
-  using RL = RingLayout<S, Wp, NE>;
-  constexpr int R = D + 1;
-  const int lane = threadIdx.x & 31;
-  const int N = in.N, L = in.L;
-  const int j0 = jg * 32;
-  const int i = j0 + lane;
-  const bool active = i < N;
-  const int last = min(l1, L);   // the last row read (the next row of l1 - 1)
-  // halo columns: lanes 0, 1 -> j0 - 2, j0 - 1 (entries 0, 1); lanes 2, 3 -> j0 + 32, j0 + 33 (34, 35)
-  const int hc = (lane < 2) ? j0 - 2 + lane : j0 + 30 + lane;
-  const int he = (lane < 2) ? lane : 32 + lane;
-  const bool hok = lane < 4 && hc >= 0 && hc < N;
-  auto slot_of = [&](int row) { return ring + ((row % R + R) % R) * RL::kSlot; };
-  auto issue = [&](int row) {
-    float2 *sl = slot_of(row);
-    if (row >= 0 && row <= last) {
-      const size_t base = (size_t)row * N;
-      const size_t ci = base + (active ? i : 0);
-      const size_t ch = base + (hok ? hc : 0);
-      if (S) {
-        cp_async8(sl + RL::kH + 2 + lane, in.hi + ci, active);
-        cp_async8(sl + RL::kL + 2 + lane, in.lo + ci, active);
-        if (lane < 4) {
-          cp_async8(sl + RL::kH + he, in.hi + ch, hok);
-          cp_async8(sl + RL::kL + he, in.lo + ch, hok);
-        }
-      }
-      if (Wp) {
-        cp_async8(sl + RL::kW + 2 + lane, in.w + ci, active);
-        if (lane < 4) cp_async8(sl + RL::kW + he, in.w + ch, hok);
-      }
-      if (row < l1) {   // the diagonal and the epilogue rows only for computed rows
-        cp_async4(reinterpret_cast<float *>(sl + RL::kD) + lane, in.diag + ci, active);
-        if (NE > 0) cp_async8(sl + RL::kE + lane, in.pf0 + ci, active);
-        if (NE > 1) cp_async8(sl + RL::kE + 32 + lane, in.pf1 + ci, active);
-      }
-    } else if (row >= l0 - 1 && row <= l1) {
-      // a row outside [0, L] read as prev or next: zero operand parts
-      const float2 z = make_float2(0.f, 0.f);
-      if (S) {
-        sl[RL::kH + 2 + lane] = z;
-        sl[RL::kL + 2 + lane] = z;
-        if (lane < 4) {
-          sl[RL::kH + he] = z;
-          sl[RL::kL + he] = z;
-        }
-      }
-      if (Wp) {
-        sl[RL::kW + 2 + lane] = z;
-        if (lane < 4) sl[RL::kW + he] = z;
-      }
-    }
-    cp_async_commit();
-  };
-  const float Er = active ? in.E * in.rj[i] : 0.f;
-  for (int q = -1; q < D; ++q) issue(l0 + q);
-  float a_cur = in.kappa[l0] * Er;
-  for (int l = l0; l < l1; ++l) {
-    cp_async_wait<D - 2>();   // rows up to l + 1 have landed
-    __syncwarp();
-    const float a_next = in.kappa[l + 1] * Er;
-    if (active) {
-      const float2 *sp = slot_of(l - 1), *sc = slot_of(l), *sn = slot_of(l + 1);
-      const Parts<S, Wp> prev = ring_parts<S, Wp>(sp + 0, 2 + lane);
-      const Parts<S, Wp> cur = ring_parts<S, Wp>(sc, 2 + lane);
-      const Parts<S, Wp> next = ring_parts<S, Wp>(sn, 2 + lane);
-      const Parts<S, Wp> m1 = ring_parts<S, Wp>(sc, 1 + lane);
-      const Parts<S, Wp> p1 = ring_parts<S, Wp>(sc, 3 + lane);
-      const float2 d1m = diff(m1, cur, in.ws), d1p = diff(p1, cur, in.ws);
-      const float2 vc = value(cur, in.ws), vp = value(prev, in.ws), vn = value(next, in.ws);
-      const float dg = reinterpret_cast<const float *>(sc + RL::kD)[lane];
-      float tx = in.c1 * (d1m.x + d1p.x);
-      float ty = in.c1 * (d1m.y + d1p.y);
-      if (ST == 5) {
-        const Parts<S, Wp> m2 = ring_parts<S, Wp>(sc, lane);
-        const Parts<S, Wp> p2 = ring_parts<S, Wp>(sc, 4 + lane);
-        const float2 d2m = diff(m2, cur, in.ws), d2p = diff(p2, cur, in.ws);
-        tx = fmaf(in.c2, d2m.x + d2p.x, tx);
-        ty = fmaf(in.c2, d2m.y + d2p.y, ty);
-      }
-      tx = fmaf(dg, vc.x, tx);
-      ty = fmaf(dg, vc.y, ty);
-      tx = fmaf(a_cur, vp.x, tx);
-      ty = fmaf(a_cur, vp.y, ty);
-      tx = fmaf(a_next, vn.x, tx);
-      ty = fmaf(a_next, vn.y, ty);
-      const float2 z = make_float2(0.f, 0.f);
-      const float2 e0 = NE > 0 ? sc[RL::kE + lane] : z;
-      const float2 e1 = NE > 1 ? sc[RL::kE + 32 + lane] : z;
-      f(i, (size_t)l * N + i, make_float2(tx, ty), vc, e0, e1);
-    }
-    a_cur = a_next;
-    __syncwarp();             // every lane is done with row l - 1's slot
-    issue(l + D);             // reuses it
-  }
-  cp_async_wait<0>();
-  __syncwarp();
-}
-
 }  // namespace stencil
 }  // namespace tdse_dev

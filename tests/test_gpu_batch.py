@@ -112,7 +112,8 @@ def test_batch_set_state_and_invalid_specs():
 
 
 # (prefetch rows, stencil blocks/SM, elementwise blocks/SM, staged ring rows)
-SCHEDULES = [(6, 2, 2, 0), (0, 2, 2, 0), (3, 1, 2, 0), (10, 2, 1, 0), (0, 1, 1, 0), (0, 2, 2, 3), (0, 1, 2, 5)]
+SCHEDULES = [(6, 2, 2, 0), (0, 2, 2, 0), (3, 1, 2, 0), (10, 2, 1, 0), (0, 1, 1, 0), (0, 2, 2, 3), (0, 1, 2, 5),
+             (0, 3, 2, 5), (0, 3, 1, 3)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -178,7 +179,7 @@ def test_batch_autotune_leaves_the_state_untouched():
     a.propagate(3)
     chosen = a.autotune()
     assert chosen["prefetch_rows"] in (0, 3, 6, 10) and chosen["ring_rows"] in (0, 3, 5)
-    assert chosen["stencil_blocks_per_sm"] in (1, 2) and chosen["elem_blocks_per_sm"] in (1, 2)
+    assert chosen["stencil_blocks_per_sm"] in (1, 2, 3) and chosen["elem_blocks_per_sm"] in (1, 2)
     assert a.schedule() == chosen
     a.propagate(4)
     b = Batch(SPECS, precision="mixed")
@@ -189,7 +190,7 @@ def test_batch_autotune_leaves_the_state_untouched():
     with pytest.raises(TDSEError):
         a.set_schedule(5, 2, 2)
     with pytest.raises(TDSEError):
-        a.set_schedule(6, 3, 2)
+        a.set_schedule(6, 4, 2)
     with pytest.raises(TDSEError):
         a.set_schedule(0, 2, 2, ring_rows=4)
     a.close()
