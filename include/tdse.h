@@ -563,6 +563,24 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in_host, double *F_
 int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, double *dipole,
                            double *yield, double *p_ground);
 
+/*
+ * Record <z>, <zdot> and <zddot> of every instance (as tdse_dipole_moments,
+ * Sec. 4: Eqs. (Dipole), (DipoleVelocity), (DipoleAccel), with no ghost
+ * point) after each of its steps, up to `capacity` entries per instance: one
+ * extra launch per step covers the whole batch, and an instance's entries are
+ * bitwise the same whatever else runs in the batch and however its steps are
+ * split into calls.  Recording stops for an instance whose record is full.
+ * capacity 0 turns recording off; every call discards what was recorded.
+ * The record takes 32 * capacity * count bytes of device memory.
+ * Errors: TDSE_ERR_ARG (capacity < 0 or too large), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_batch_dipole_series(tdse_batch_t *b, long capacity);
+/* Instance i's entries as {t, <z>, <zdot>, <zddot>} (4 doubles each, in step
+ * order): at most max_entries of them into out (may be NULL); *count (may be
+ * NULL) receives the number recorded.  Synchronises the stream.
+ * Errors: TDSE_ERR_ARG (bad index), TDSE_ERR_CUDA. */
+int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_entries, long *count);
+
 /* Total grid points of the batch and kernel launches issued (accounting).
  * tdse_batch_graph_steps: steps (of all instances together) that ran as a
  * replay of a captured step graph rather than as separate launches. */

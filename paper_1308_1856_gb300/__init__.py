@@ -382,6 +382,20 @@ class Batch:
         return {"norm": norm.value, "dipole": dip.value, "yield": yld.value, "p_ground": pg.value,
                 "l_pop": lp}
 
+    def record_dipole(self, capacity: int):
+        """Record every instance's dipole moments after each of its steps (0: off)."""
+        self._check(C.tdse_batch_dipole_series(self.h, int(capacity)))
+
+    def dipole_series(self, i) -> np.ndarray:
+        """(n, 4) array of instance i's {t, <z>, <zdot>, <zddot>} recorded so far."""
+        n = ctypes.c_long()
+        self._check(C.tdse_batch_dipole_series_read(self.h, int(i), None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 4))
+        if n.value:
+            self._check(C.tdse_batch_dipole_series_read(self.h, int(i), out.ctypes.data_as(C._dp), n.value,
+                                                        ctypes.byref(n)))
+        return out
+
     @property
     def points(self) -> int:
         return C.tdse_batch_points(self.h)

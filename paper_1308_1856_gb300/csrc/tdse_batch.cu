@@ -567,6 +567,98 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   });
 }
 
+// ---- Sec. 4: the dipole series ---------------------------------------------
+// f_{l,i} of an instance's FP64 state, zero outside the box (the batched
+// stencils have no ghost point).
+__device__ __forceinline__ double2 psi_at(const BatchInst &I, int l, int i) {
+  return (i >= 0 && i < I.N) ? I.psi[(size_t)l * I.N + i] : make_double2(0.0, 0.0);
+}
+
+// After a step: <z>, <zdot>, <zddot> of every instance still recording
+// (Eqs. (Dipole), (DipoleVelocity), (DipoleAccel)), as the single-instance
+// moments but over fixed per-instance chunks of kChunkSegs row segments.  A
+// lane walks rows l0..l1-1 of its column i, carrying f_{l+1,i} to the next
+// row, and accumulates (w_l = 2 kappa_{l+1} dr)
+//   sn = sum_l |f_l|^2,  sre = sum_l w_l Re(f_l^* f_{l+1}),
+//   sd = sum_l w_l Im(f_{l+1}^* D1raw f_l),  sc = sum_l w_l (l+1) Im(f_{l+1}^* f_l),
+// then adds sn, r sre, d1c sd - sc / r and sre / r^2 to its four sums.  The
+// four chunk partials go to the instance's dpart slots; the warp that
+// finishes the instance's last chunk adds them in chunk order and writes
+//   {t, <z>, <zdot> + (A/c) norm, -E norm - Z <1/r^2 weighted sum>}.
+template <int ST>
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
+    bt_dipole(BatchDev B, ChunkList cl, SeriesDev S) {
+  const int n = *B.step;
+  const int lane = threadIdx.x & 31;
+  for_my_chunks(cl, [&](int inst, int ci) {
+    const long long e = S.base[inst] + n;
+    if (e >= S.cap) return;   // the record is full: every chunk of the instance skips
+    const BatchInst I = B.inst[inst];
+    const int L = I.L;
+    const double two_dr = 2.0 * I.dr;
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    chunk_columns(I, ci, [&](int i, int l0, int l1) {
+      double sn = 0.0, sre = 0.0, sd = 0.0, sc = 0.0;
+      double2 a = psi_at(I, l0, i);
+      for (int l = l0; l < l1; ++l) {
+        sn = __fma_rn(a.x, a.x, __fma_rn(a.y, a.y, sn));
+        if (l < L) {
+          const double2 b = psi_at(I, l + 1, i);
+          const double w = __dmul_rn(two_dr, I.kappa[l + 1]);
+          const double w1 = __dmul_rn((double)(l + 1), w);
+          const double2 p1 = psi_at(I, l, i + 1), m1 = psi_at(I, l, i - 1);
+          double dx = __dsub_rn(p1.x, m1.x), dy = __dsub_rn(p1.y, m1.y);
+          if (ST == 5) {
+            const double2 p2 = psi_at(I, l, i + 2), m2 = psi_at(I, l, i - 2);
+            dx = __dsub_rn(__fma_rn(8.0, dx, m2.x), p2.x);
+            dy = __dsub_rn(__fma_rn(8.0, dy, m2.y), p2.y);
+          }
+          sre = __fma_rn(w, __fma_rn(a.x, b.x, __dmul_rn(a.y, b.y)), sre);
+          sd = __fma_rn(w, __fma_rn(b.x, dy, -__dmul_rn(b.y, dx)), sd);
+          sc = __fma_rn(w1, __fma_rn(b.x, a.y, -__dmul_rn(b.y, a.x)), sc);
+          a = b;
+        }
+      }
+      const double r = I.rj[i];
+      const double rinv = 1.0 / r;
+      q[0] = __dadd_rn(q[0], sn);
+      q[1] = __fma_rn(r, sre, q[1]);
+      q[2] = __dadd_rn(q[2], __fma_rn(I.d1c, sd, -__dmul_rn(rinv, sc)));
+      q[3] = __fma_rn(__dmul_rn(rinv, rinv), sre, q[3]);
+    });
+    const int nd = I.nchunk_d;
+    unsigned last = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = warp_sum(q[k]);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) I.dpart[(size_t)k * nd + ci] = q[k];
+      __threadfence();
+      last = (atomicAdd(&B.ticket[inst], 1u) == (unsigned)(nd - 1)) ? 1u : 0u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double tot[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double v = 0.0;
+      for (int c = lane; c < nd; c += 32) v += __ldcg(&I.dpart[(size_t)k * nd + c]);
+      tot[k] = warp_sum(v);
+    }
+    if (lane == 0) {
+      const double *tb = S.tab + 3 * ((size_t)n * S.slots + inst);
+      const double norm = __dmul_rn(I.dr, tot[0]);
+      double *o = S.out + 4 * ((size_t)inst * S.cap + e);
+      o[0] = tb[0];
+      o[1] = tot[1];
+      o[2] = __fma_rn(tb[2], norm, tot[2]);
+      o[3] = __fma_rn(-tb[1], norm, -__dmul_rn(I.Z, tot[3]));
+      B.ticket[inst] = 0u;
+    }
+  });
+}
+
 }  // namespace
 }  // namespace tdse_dev
 
@@ -582,7 +674,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, ref0, rinv, total;
+  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, dpart, ref0, rinv, total;
 };
 
 // Tiles of the mixed tile kernel on an N x (L+1) grid.
@@ -615,6 +707,7 @@ Layout layout_of(const tdse_instance_spec &s, int precision) {
   L.rjf = mixed ? take(4 * N) : none;
   L.kappaf = mixed ? take(4 * (Lp1 + 1)) : none;
   L.partial = take(8 * nchunk);
+  L.dpart = take(8 * 4 * ((nseg + kChunkSegs - 1) / kChunkSegs));
   L.ref0 = take(16 * N);
   L.rinv = (!mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? take(8 * N) : none;
   L.total = off;
@@ -681,6 +774,9 @@ Engine::~Engine() {
   cudaFree(lists);
   cudaFree(obs_partials);   // obs_out points into this block
   cudaFree(obs_ticket);
+  cudaFree(ser);
+  cudaFree(ser_base);
+  cudaFree(ser_tab);
   for (auto &mk : marks) {
     cudaEventDestroy(mk.a);
     cudaEventDestroy(mk.b);
@@ -709,6 +805,7 @@ int Engine::init(int cap, int st, int prec) {
   tstart.assign(cap, 0.0);
   placed.assign(cap, 0);
   norm_valid.assign(cap, 0);
+  ser_count.assign(cap, 0);
   const bool ok = cudaMalloc(&inst, sizeof(BatchInst) * cap) == cudaSuccess &&
                   cudaMalloc(&ls, sizeof(LanczosScalars) * cap) == cudaSuccess &&
                   cudaMalloc(&ticket, sizeof(unsigned) * cap) == cudaSuccess &&
@@ -765,6 +862,9 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   // of 256 columns x kTileRows rows (the mixed tile kernel)
   I.nchunk = mixed ? tile_count(N, L) : (I.nseg + kChunkSegs - 1) / kChunkSegs;
   I.nchunk_e = (int)((G + kChunkPts - 1) / kChunkPts);
+  I.nchunk_d = (I.nseg + kChunkSegs - 1) / kChunkSegs;
+  I.dr = s.dr;
+  I.Z = s.Z;
   const double h2 = s.dr * s.dr;
   double c0;
   if (stencil == 5) {
@@ -781,6 +881,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.mask = reinterpret_cast<double *>(base + Lo.mask);
   I.kappa = reinterpret_cast<double *>(base + Lo.kappa);
   I.partial = reinterpret_cast<double *>(base + Lo.partial);
+  I.dpart = reinterpret_cast<double *>(base + Lo.dpart);
   I.ref0 = reinterpret_cast<double2 *>(base + Lo.ref0);
   I.gauge = s.gauge;
   I.d1c = (stencil == 5) ? 1.0 / (12.0 * s.dr) : 1.0 / (2.0 * s.dr);
@@ -878,6 +979,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   tstart[slot] = 0.0;
   placed[slot] = 1;
   norm_valid[slot] = 0;
+  ser_count[slot] = 0;
   return TDSE_OK;
 }
 
@@ -1029,15 +1131,16 @@ int Engine::copy_states(const std::vector<int> &slots, double *F, bool to_device
   return TDSE_OK;
 }
 
-// Append the chunk list of `ids` (stencil or elementwise chunks) to the host
+// Append the chunk list of `ids` (stencil, elementwise or dipole chunks) to the host
 // staging; list_off receives its offset, the return value its chunk count.
-int Engine::launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off) {
+int Engine::launch_lists(const std::vector<int> &ids, ListKind kind, int &list_off) {
   list_off = (int)hlists.size();
   hlists.insert(hlists.end(), ids.begin(), ids.end());
   int tot = 0;
   hlists.push_back(0);
   for (int id : ids) {
-    tot += elementwise ? hinst[id].nchunk_e : hinst[id].nchunk;
+    const BatchInst &I = hinst[id];
+    tot += kind == kListElem ? I.nchunk_e : kind == kListRows ? I.nchunk_d : I.nchunk;
     hlists.push_back(tot);
   }
   return tot;
@@ -1133,8 +1236,12 @@ std::vector<long long> Engine::segment_key(const Segment &sg) const {
   k.push_back(sg.maxm);
   for (const void *p : {(const void *)inst, (const void *)ls, (const void *)ticket, (const void *)status,
                         (const void *)m_dev, (const void *)dt_dev, (const void *)E_dev, (const void *)step_dev,
-                        (const void *)lists})
+                        (const void *)lists, (const void *)ser, (const void *)ser_base, (const void *)ser_tab})
     k.push_back((long long)(uintptr_t)p);
+  k.push_back(ser_cap);
+  k.push_back(sg.doff);
+  k.push_back(sg.dnact);
+  k.push_back(sg.dtotal);
   for (const std::vector<int> *v : {&sg.off, &sg.nact, &sg.total, &sg.voff, &sg.vnact, &sg.vtotal, &sg.eoff,
                                     &sg.enact, &sg.etotal}) {
     k.push_back((long long)v->size());
@@ -1143,6 +1250,16 @@ std::vector<long long> Engine::segment_key(const Segment &sg) const {
   k.push_back((long long)hlists.size());
   k.insert(k.end(), hlists.begin(), hlists.end());
   return k;
+}
+
+SeriesDev Engine::series_view() const {
+  SeriesDev S;
+  S.out = ser;
+  S.cap = ser_cap;
+  S.base = ser_base;
+  S.tab = ser_tab;
+  S.slots = capacity;
+  return S;
 }
 
 BatchDev Engine::device_view() const {
@@ -1169,9 +1286,9 @@ void Engine::build_segment(Segment &sg, const std::vector<int> &act) {
         (spec[s].gauge == TDSE_GAUGE_VELOCITY ? ph_vel : ph_len).push_back(s);
       }
     int off = 0, voff = 0, eoff = 0;
-    const int tot = launch_lists(ph_len, false, off);
-    const int vtot = ph_vel.empty() ? 0 : launch_lists(ph_vel, false, voff);
-    const int etot = launch_lists(ph, true, eoff);
+    const int tot = launch_lists(ph_len, kListStencil, off);
+    const int vtot = ph_vel.empty() ? 0 : launch_lists(ph_vel, kListStencil, voff);
+    const int etot = launch_lists(ph, kListElem, eoff);
     sg.off.push_back(off);
     sg.nact.push_back((int)ph_len.size());
     sg.total.push_back(tot);
@@ -1181,6 +1298,10 @@ void Engine::build_segment(Segment &sg, const std::vector<int> &act) {
     sg.eoff.push_back(eoff);
     sg.enact.push_back((int)ph.size());
     sg.etotal.push_back(etot);
+  }
+  if (ser_cap > 0) {
+    sg.dnact = (int)act.size();
+    sg.dtotal = launch_lists(act, kListRows, sg.doff);
   }
 }
 
@@ -1295,6 +1416,17 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
   prof_end(pc);
   ++count;
   EN_CUDA(cudaGetLastError(), "batch combine");
+  if (sg.dtotal > 0) {
+    // the dipole moments of the new states (Sec. 4), recorded per step
+    const ChunkList dl = list_at(lists, sg.doff, sg.dnact, sg.dtotal);
+    const SeriesDev S = series_view();
+    cudaEvent_t pd = prof_begin(TDSE_K_DIPOLE);
+    if (stencil == 5) bt_dipole<5><<<egrid, kElemThreads, 0, stream>>>(B, dl, S);
+    else bt_dipole<3><<<egrid, kElemThreads, 0, stream>>>(B, dl, S);
+    prof_end(pd);
+    ++count;
+    EN_CUDA(cudaGetLastError(), "batch dipole");
+  }
   bt_next_step<<<1, 1, 0, stream>>>(step_dev);
   ++count;
   EN_CUDA(cudaGetLastError(), "batch step counter");
@@ -1330,7 +1462,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     if (steps[q] > 0 && !norm_valid[slots[q]]) need_norm.push_back(slots[q]);
   std::sort(need_norm.begin(), need_norm.end());
   int norm_off = 0, norm_total = 0;
-  if (!need_norm.empty()) norm_total = launch_lists(need_norm, true, norm_off);
+  if (!need_norm.empty()) norm_total = launch_lists(need_norm, kListElem, norm_off);
   long n0 = 0;
   for (long e : ends) {
     Segment sg;
@@ -1357,6 +1489,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   }
   int rc = upload_run(nE);
   if (rc) return rc;
+  if (ser_cap > 0 && (rc = upload_series(slots, steps, nE))) return rc;
   const BatchDev B = device_view();
   if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) return rc;
   std::vector<std::vector<long long>> eager;
@@ -1415,8 +1548,76 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     }
   }
   last_eager = std::move(eager);
-  for (size_t q = 0; q < slots.size(); ++q) nstep[slots[q]] += steps[q];
+  for (size_t q = 0; q < slots.size(); ++q) {
+    nstep[slots[q]] += steps[q];
+    if (ser_cap > 0) ser_count[slots[q]] = std::min(ser_cap, ser_count[slots[q]] + (long long)steps[q]);
+  }
   return TDSE_OK;
+}
+
+// The dipole series' time table of a run (t, E(t) and A(t)/c at the end of
+// every step) and each slot's entry count so far.
+int Engine::upload_series(const std::vector<int> &slots, const std::vector<long> &steps, size_t nE) {
+  hser_tab.assign(3 * nE, 0.0);
+  for (size_t q = 0; q < slots.size(); ++q) {
+    const int s = slots[q];
+    const tdse_instance_spec &sp = spec[s];
+    const PulseParams p{sp.E0, sp.omega, sp.ncycles, sp.cep, sp.pulse_shape};
+    const long todo = (long)std::min<long long>(steps[q], ser_cap - ser_count[s]);
+    for (long n = 0; n < todo; ++n) {
+      const double t = tstart[s] + (double)(nstep[s] + n + 1) * sp.dt;
+      double *e = hser_tab.data() + 3 * ((size_t)n * capacity + s);
+      e[0] = t;
+      e[1] = pulse_field(p, t);
+      e[2] = sp.gauge == TDSE_GAUGE_VELOCITY ? pulse_vecpot(p, t) / kLightAU : 0.0;
+    }
+  }
+  int rc = ensure(reinterpret_cast<void **>(&ser_tab), ser_tab_cap, sizeof(double) * std::max<size_t>(3, 3 * nE),
+                  "dipole series table");
+  if (rc) return rc;
+  if (nE)
+    EN_CUDA(cudaMemcpyAsync(ser_tab, hser_tab.data(), sizeof(double) * 3 * nE, cudaMemcpyHostToDevice, stream),
+            "dipole series table");
+  EN_CUDA(cudaMemcpyAsync(ser_base, ser_count.data(), sizeof(long long) * capacity, cudaMemcpyHostToDevice, stream),
+          "dipole series counts");
+  return TDSE_OK;
+}
+
+int Engine::dipole_series(long long cap) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (cap < 0 || cap > (1LL << 40) / (32LL * capacity)) return fail(TDSE_ERR_ARG, "bad dipole series capacity");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync before the dipole series");
+  cudaFree(ser);
+  ser = nullptr;
+  ser_cap = 0;
+  ser_count.assign(capacity, 0);
+  if (cap == 0) return TDSE_OK;
+  if (!ser_base && cudaMalloc(&ser_base, sizeof(long long) * capacity) != cudaSuccess) {
+    cudaGetLastError();
+    ser_base = nullptr;
+    return fail(TDSE_ERR_OOM, "dipole series counts");
+  }
+  if (cudaMalloc(&ser, sizeof(double) * 4 * (size_t)cap * capacity) != cudaSuccess) {
+    cudaGetLastError();
+    ser = nullptr;
+    return fail(TDSE_ERR_OOM, "dipole series");
+  }
+  ser_cap = cap;
+  return TDSE_OK;
+}
+
+int Engine::dipole_series_read(int slot, double *out, long long max, long long *count) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+  const long long n = ser_cap > 0 ? ser_count[slot] : 0;
+  if (count) *count = n;
+  const long long k = std::min(n, max);
+  if (!out || k <= 0) return TDSE_OK;
+  EN_CUDA(cudaMemcpyAsync(out, ser + 4 * (size_t)slot * ser_cap, sizeof(double) * 4 * (size_t)k,
+                          cudaMemcpyDeviceToHost, stream),
+          "read dipole series");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync dipole series");
+  return check_status();
 }
 
 int Engine::set_schedule(const Schedule &s) {
@@ -1446,7 +1647,7 @@ int Engine::autotune(const std::vector<int> &slots) {
   for (int s : act)
     if (!norm_valid[s]) need_norm.push_back(s);
   int norm_off = 0, norm_total = 0;
-  if (!need_norm.empty()) norm_total = launch_lists(need_norm, true, norm_off);
+  if (!need_norm.empty()) norm_total = launch_lists(need_norm, kListElem, norm_off);
   Segment sg;
   sg.n0 = 0;
   sg.n1 = 1;
@@ -1829,6 +2030,18 @@ int tdse_batch_observables(tdse_batch_t *b, int i, double *norm, double *l_pop, 
   if (yield) *yield = out[2];
   if (p_ground) *p_ground = out[3];
   if (l_pop) std::memcpy(l_pop, out.data() + 4, sizeof(double) * (out.size() - 4));
+  return rc;
+}
+
+int tdse_batch_dipole_series(tdse_batch_t *b, long capacity) {
+  return b ? b->eng.dipole_series(capacity) : TDSE_ERR_ARG;
+}
+
+int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_entries, long *count) {
+  if (!b || i < 0 || i >= b->count) return TDSE_ERR_ARG;
+  long long n = 0;
+  const int rc = b->eng.dipole_series_read(i, out, max_entries, &n);
+  if (count) *count = (long)n;
   return rc;
 }
 

@@ -27,9 +27,11 @@ struct BatchInst {
   int nseg;              // 32-point row segments
   int nchunk;            // reduction chunks of the stencil kernels (row segments)
   int nchunk_e;          // reduction chunks of the elementwise kernels (consecutive points)
+  int nchunk_d;          // reduction chunks of the dipole kernel (kChunkSegs row segments, both precisions)
   int gauge;             // TDSE_GAUGE_LENGTH or TDSE_GAUGE_VELOCITY (FP64 only)
   double c1, c2;         // stencil coefficients (c0 is folded into diag)
   double d1c;            // first-derivative scale of the velocity gauge (1/(12 dr) or 1/(2 dr))
+  double dr, Z;          // grid spacing and nuclear charge (the dipole moments' weights)
   const double *rinv;    // 1/r_j (velocity gauge; null otherwise)
   double2 *psi;          // (L+1) x N state, l-major
   const double *diag;    // FP64: c0 + l(l+1)/(2 r^2) - Z/r
@@ -40,6 +42,7 @@ struct BatchInst {
   double2 *work;         // FP64 Krylov area: slot 0 = z, slots 1..m-1 = U_j
   float2 *mwork;         // mixed Krylov area, same slots
   double *partial;       // max(nchunk, nchunk_e) chunk partial sums
+  double *dpart;         // 4 * nchunk_d chunk partials of the dipole kernel
   double2 *ref0;         // N values: the p_ground reference (1s state of the grid)
 };
 
@@ -50,6 +53,9 @@ struct ChunkList {
   const int *cpre;
   int nact, total;
 };
+
+// Chunk counts a launch list is built from.
+enum ListKind { kListStencil, kListElem, kListRows };
 
 // Per-launch view of the engine's device state.
 struct BatchDev {
@@ -62,6 +68,17 @@ struct BatchDev {
   const int *step;       // step of the run being computed (device counter, so one
                          // captured step graph serves every step of a segment)
   int cap;
+};
+
+// The dipole series of a run (Sec. 4): after every step, entry base[slot] + n
+// of a slot (n = the run's step counter) receives {t, <z>, <zdot>, <zddot>}
+// while it is below cap.
+struct SeriesDev {
+  double *out;            // cap entries of 4 doubles per slot, slot-major
+  long long cap;
+  const long long *base;  // entries each slot held when the run began
+  const double *tab;      // tab[3 (n * slots + slot) + {0,1,2}] = t, E(t), A(t)/c at the end of step n
+  int slots;
 };
 
 // Launch schedule of the batched kernels.  Results do not depend on it
@@ -99,6 +116,11 @@ class Engine {
   void clear(int slot);
   // Advance slots[i] by steps[i] >= 0 Lanczos steps; asynchronous.
   int run(const std::vector<int> &slots, const std::vector<long> &steps);
+  // Record {t, <z>, <zdot>, <zddot>} of every slot after each of its steps,
+  // up to `cap` entries per slot (0: off); every call discards the record.
+  int dipole_series(long long cap);
+  // Entries recorded for a slot (up to max of them into out, 4 doubles each); synchronous.
+  int dipole_series_read(int slot, double *out, long long max, long long *count);
   // {norm, dipole, yield, p_ground, l_pop[0..L]} of a slot; synchronous.
   int observables(int slot, std::vector<double> &out);
   int set_state(int slot, const double *F_host);
@@ -139,7 +161,7 @@ class Engine {
 
  private:
   int ensure(void **p, size_t &cap, size_t bytes, const char *what);
-  int launch_lists(const std::vector<int> &ids, bool elementwise, int &list_off);
+  int launch_lists(const std::vector<int> &ids, ListKind kind, int &list_off);
   // per phase j of a segment: the stencil-chunk list (lanczos_a) and the
   // elementwise one (lanczos_b, combine) of the slots still active in it
   struct Segment {
@@ -148,6 +170,7 @@ class Engine {
     std::vector<int> off, nact, total;      // stencil lists of the length-gauge instances
     std::vector<int> voff, vnact, vtotal;   // stencil lists of the velocity-gauge instances
     std::vector<int> eoff, enact, etotal;   // elementwise lists of every instance
+    int doff = 0, dnact = 0, dtotal = 0;    // dipole-chunk list of every instance
   };
   void build_segment(Segment &sg, const std::vector<int> &act);
   BatchDev device_view() const;
@@ -157,6 +180,8 @@ class Engine {
   int launch_a_velocity(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
   int launch_b(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
   int enqueue_step(const BatchDev &B, const Segment &sg, int &count);
+  SeriesDev series_view() const;
+  int upload_series(const std::vector<int> &slots, const std::vector<long> &steps, size_t nE);
   void drop_graphs();
   cudaEvent_t prof_begin(int kind);
   void prof_end(cudaEvent_t e);
@@ -187,6 +212,14 @@ class Engine {
   std::vector<long long> segment_key(const Segment &sg) const;
   int *lists = nullptr;          // chunk lists of the launches of one run
   size_t lists_cap = 0;
+  // dipole series: the record, per-slot entry counts, the per-run time table
+  double *ser = nullptr;
+  long long ser_cap = 0;
+  std::vector<long long> ser_count;
+  long long *ser_base = nullptr;
+  double *ser_tab = nullptr;
+  size_t ser_tab_cap = 0;
+  std::vector<double> hser_tab;
   double *obs_partials = nullptr, *obs_out = nullptr;
   size_t obs_cap = 0;
   unsigned *obs_ticket = nullptr;

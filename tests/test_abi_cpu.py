@@ -89,7 +89,8 @@ def test_server_instance_bytes(lib):
     for N, L, m in [(1000, 15, 12), (2000, 127, 16), (33, 0, 1), (16000, 63, 8)]:
         G = N * (L + 1)
         nchunk = max(-(-((N + 31) // 32) * (L + 1) // 64), -(-G // 2048))
-        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(16 * N)
+        ndip = -(-((N + 31) // 32) * (L + 1) // 64)    # dipole chunks: 4 partial sums each
+        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(32 * ndip) + up(16 * N)
         fp64 = common + up(8 * G) + up(16 * G * m)
         mixed = common + up(4 * G) + 2 * up(8 * G) + up(8 * G * m) + up(4 * N) + up(4 * (L + 2))
         s = _spec(N=N, lmax=L, krylov=m)
@@ -99,7 +100,8 @@ def test_server_instance_bytes(lib):
     for N, L, m in [(1000, 15, 12), (33, 0, 1)]:
         G = N * (L + 1)
         nchunk = max(-(-((N + 31) // 32) * (L + 1) // 64), -(-G // 2048))
-        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(16 * N)
+        ndip = -(-((N + 31) // 32) * (L + 1) // 64)    # dipole chunks: 4 partial sums each
+        common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(32 * ndip) + up(16 * N)
         s = _spec(N=N, lmax=L, krylov=m, gauge=1)
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == common + up(8 * G) + up(16 * G * m) + up(8 * N)
     bad = _spec(krylov=0)
