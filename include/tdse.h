@@ -581,6 +581,24 @@ int tdse_batch_dipole_series(tdse_batch_t *b, long capacity);
  * Errors: TDSE_ERR_ARG (bad index), TDSE_ERR_CUDA. */
 int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_entries, long *count);
 
+/*
+ * Integrate the flux through the sphere r = r_b of every instance (its
+ * spec's r_b; Sec. 4, Eqs. (flux), (pad), (yield)) at the same ntheta angles
+ * cos_theta[k] in [-1, 1], as tdse_flux_setup: the current states open the
+ * integrals at zero, and after every step one launch over the batch forms
+ * each instance's flux and densities at the new state and advances their
+ * trapezoid-rule time integrals.  The first derivative at r_b is the velocity
+ * gauge's, with zero beyond the box.  ntheta < 0 turns it off (cos_theta
+ * unused); ntheta = 0 integrates the total only.  Synchronous.
+ * Errors: TDSE_ERR_ARG (an r_b outside its instance's box, a cos_theta outside
+ * [-1, 1], a largest lmax above 1535), TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ */
+int tdse_batch_flux_setup(tdse_batch_t *b, int ntheta, const double *cos_theta);
+/* Instance i's flux now, its time integral (the yield through r_b), and the
+ * densities now and integrated (ntheta each; any pointer may be NULL).
+ * Synchronises the stream.  TDSE_ERR_ARG if the flux is not set up. */
+int tdse_batch_flux_read(tdse_batch_t *b, int i, double *flux, double *yield, double *density, double *pad);
+
 /* Total grid points of the batch and kernel launches issued (accounting).
  * tdse_batch_graph_steps: steps (of all instances together) that ran as a
  * replay of a captured step graph rather than as separate launches. */

@@ -396,6 +396,25 @@ class Batch:
                                                         ctypes.byref(n)))
         return out
 
+    def flux_setup(self, cos_theta=None, enable: bool = True):
+        """Integrate every instance's flux through its r_b (and the densities at
+        cos_theta) from now on (Sec. 4); enable=False turns it off."""
+        if not enable:
+            self._check(C.tdse_batch_flux_setup(self.h, -1, None))
+            return
+        ct = np.ascontiguousarray(np.zeros(0) if cos_theta is None else cos_theta, dtype=np.float64)
+        self._flux_nt = len(ct)
+        self._check(C.tdse_batch_flux_setup(self.h, len(ct), ct.ctypes.data_as(C._dp) if len(ct) else None))
+
+    def flux(self, i) -> dict:
+        """{flux, yield, density[ntheta], pad[ntheta]} of instance i."""
+        nt = getattr(self, "_flux_nt", 0)
+        f, y = ctypes.c_double(), ctypes.c_double()
+        dens, pad = np.zeros(max(nt, 1)), np.zeros(max(nt, 1))
+        self._check(C.tdse_batch_flux_read(self.h, int(i), ctypes.byref(f), ctypes.byref(y),
+                                           dens.ctypes.data_as(C._dp), pad.ctypes.data_as(C._dp)))
+        return {"flux": f.value, "yield": y.value, "density": dens[:nt], "pad": pad[:nt]}
+
     @property
     def points(self) -> int:
         return C.tdse_batch_points(self.h)

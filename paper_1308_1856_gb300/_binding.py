@@ -125,6 +125,8 @@ SIGNATURES = {
     "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
     "tdse_batch_dipole_series": (_c_int, [_vp, _c_long]),
     "tdse_batch_dipole_series_read": (_c_int, [_vp, _c_int, _dp, _c_long, ctypes.POINTER(_c_long)]),
+    "tdse_batch_flux_setup": (_c_int, [_vp, _c_int, _dp]),
+    "tdse_batch_flux_read": (_c_int, [_vp, _c_int, _dp, _dp, _dp, _dp]),
     "tdse_batch_points": (ctypes.c_longlong, [_vp]),
     "tdse_batch_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_batch_graph_steps": (ctypes.c_longlong, [_vp]),
@@ -246,6 +248,8 @@ tdse_batch_propagate_io = _fn("tdse_batch_propagate_io")
 tdse_batch_observables = _fn("tdse_batch_observables")
 tdse_batch_dipole_series = _fn("tdse_batch_dipole_series")
 tdse_batch_dipole_series_read = _fn("tdse_batch_dipole_series_read")
+tdse_batch_flux_setup = _fn("tdse_batch_flux_setup")
+tdse_batch_flux_read = _fn("tdse_batch_flux_read")
 tdse_batch_points = _fn("tdse_batch_points")
 tdse_batch_launch_count = _fn("tdse_batch_launch_count")
 tdse_batch_graph_steps = _fn("tdse_batch_graph_steps")

@@ -659,6 +659,89 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   });
 }
 
+// The flux through r = r_b of every listed instance (Eqs. (flux), (pad),
+// (yield)), as the single-instance flux but one block row per instance: at
+// the grid index ib nearest r_b (first derivative D1 as in the velocity
+// gauge, zero beyond the box)
+//   flux  = sum_l Im(f_l^* D1 f_l) [+ 2 (A/c) sum_l kappa_{l+1} Re(f_l^* f_{l+1})],
+//   dens_k = Im(S_k^* P_k) [+ (A/c) cos(theta_k) |S_k|^2],
+//   S_k = sum_l Y_l0(theta_k) f_l(r_b),  P_k = sum_l Y_l0(theta_k) (D1 f_l)(r_b),
+// and the trapezoid rule advances their time integrals by (dt/2)(previous +
+// current); init opens them at zero.  One warp per angle; a warp's lanes
+// split the partial waves and a fixed butterfly adds their shares.  tab holds
+// {t, E, A/c} per (step, slot) (init: per slot, at the current time).
+constexpr int kFluxThreads = 256;
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kFluxThreads)
+    bt_flux(BatchDev B, const int *__restrict__ act, FluxDev F, const double *__restrict__ tab, int init) {
+  extern __shared__ double2 fsm[];
+  const int inst = act[blockIdx.y];
+  const BatchInst I = B.inst[inst];
+  const int L = I.L, N = I.N, ib = F.ib[inst];
+  double2 *fb = fsm, *db = fsm + (L + 1);
+  for (int l = threadIdx.x; l <= L; l += kFluxThreads) {
+    const double2 *row = I.psi + (size_t)l * N;
+    fb[l] = row[ib];
+    const double2 z = make_double2(0.0, 0.0);
+    const double2 p1 = ib + 1 < N ? row[ib + 1] : z, m1 = ib >= 1 ? row[ib - 1] : z;
+    double dx = __dsub_rn(p1.x, m1.x), dy = __dsub_rn(p1.y, m1.y);
+    if (F.stencil == 5) {
+      const double2 p2 = ib + 2 < N ? row[ib + 2] : z, m2 = ib >= 2 ? row[ib - 2] : z;
+      dx = __dsub_rn(__fma_rn(8.0, dx, m2.x), p2.x);
+      dy = __dsub_rn(__fma_rn(8.0, dy, m2.y), p2.y);
+    }
+    db[l] = make_double2(__dmul_rn(dx, I.d1c), __dmul_rn(dy, I.d1c));
+  }
+  __syncthreads();
+  const double *tb = init ? tab + 3 * (size_t)inst : tab + 3 * ((size_t)(*B.step) * F.slots + inst);
+  const double ac = tb[2];
+  const double half_dt = init ? 0.0 : 0.5 * F.dt[inst];
+  double *st = F.state + (size_t)inst * (2 + 2 * (size_t)F.nt);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && warp == 0) {
+    double tot = 0.0;
+    for (int l = lane; l <= L; l += 32) {
+      tot = __fma_rn(fb[l].x, db[l].y, __fma_rn(-fb[l].y, db[l].x, tot));
+      if (ac != 0.0 && l < L)
+        tot = __fma_rn(2.0 * ac * I.kappa[l + 1], __fma_rn(fb[l].x, fb[l + 1].x, __dmul_rn(fb[l].y, fb[l + 1].y)),
+                       tot);
+    }
+    tot = warp_allsum(tot);
+    if (lane == 0) {
+      st[1] = init ? 0.0 : __fma_rn(half_dt, __dadd_rn(st[0], tot), st[1]);
+      st[0] = tot;
+    }
+  }
+  const int k = blockIdx.x * (kFluxThreads / 32) + warp;
+  if (k >= F.nt) return;
+  const double *yk = F.y + (size_t)k * F.ystride;
+  double sx = 0.0, sy = 0.0, px = 0.0, py = 0.0;
+  for (int l = lane; l <= L; l += 32) {
+    const double y = yk[l];
+    sx = __fma_rn(y, fb[l].x, sx);
+    sy = __fma_rn(y, fb[l].y, sy);
+    px = __fma_rn(y, db[l].x, px);
+    py = __fma_rn(y, db[l].y, py);
+  }
+  sx = warp_allsum(sx);
+  sy = warp_allsum(sy);
+  px = warp_allsum(px);
+  py = warp_allsum(py);
+  if (lane == 0) {
+    double dens = __fma_rn(sx, py, -__dmul_rn(sy, px));
+    if (ac != 0.0) dens = __fma_rn(ac * F.ct[k], __fma_rn(sx, sx, __dmul_rn(sy, sy)), dens);
+    double *now = st + 2, *acc = st + 2 + F.nt;
+    acc[k] = init ? 0.0 : __fma_rn(half_dt, __dadd_rn(now[k], dens), acc[k]);
+    now[k] = dens;
+  }
+}
+
 }  // namespace
 }  // namespace tdse_dev
 
@@ -777,6 +860,11 @@ Engine::~Engine() {
   cudaFree(ser);
   cudaFree(ser_base);
   cudaFree(ser_tab);
+  cudaFree(flux_state);
+  cudaFree(flux_y);
+  cudaFree(flux_ct);
+  cudaFree(flux_ib);
+  cudaFree(flux_slots);
   for (auto &mk : marks) {
     cudaEventDestroy(mk.a);
     cudaEventDestroy(mk.b);
@@ -1238,6 +1326,10 @@ std::vector<long long> Engine::segment_key(const Segment &sg) const {
                         (const void *)m_dev, (const void *)dt_dev, (const void *)E_dev, (const void *)step_dev,
                         (const void *)lists, (const void *)ser, (const void *)ser_base, (const void *)ser_tab})
     k.push_back((long long)(uintptr_t)p);
+  for (const void *p : {(const void *)flux_state, (const void *)flux_y, (const void *)flux_ct,
+                        (const void *)flux_ib})
+    k.push_back((long long)(uintptr_t)p);
+  k.push_back(flux_nt);
   k.push_back(ser_cap);
   k.push_back(sg.doff);
   k.push_back(sg.dnact);
@@ -1260,6 +1352,20 @@ SeriesDev Engine::series_view() const {
   S.tab = ser_tab;
   S.slots = capacity;
   return S;
+}
+
+FluxDev Engine::flux_view() const {
+  FluxDev F;
+  F.state = flux_state;
+  F.y = flux_y;
+  F.ct = flux_ct;
+  F.ib = flux_ib;
+  F.dt = dt_dev;
+  F.nt = flux_nt;
+  F.ystride = flux_lmax + 1;
+  F.slots = capacity;
+  F.stencil = stencil;
+  return F;
 }
 
 BatchDev Engine::device_view() const {
@@ -1427,6 +1533,17 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
     ++count;
     EN_CUDA(cudaGetLastError(), "batch dipole");
   }
+  if (flux_nt >= 0) {
+    // the flux through every instance's sphere and its time integrals (Sec. 4)
+    const dim3 fgrid((unsigned)std::max(1, (flux_nt + kFluxThreads / 32 - 1) / (kFluxThreads / 32)),
+                     (unsigned)all.nact);
+    cudaEvent_t pf = prof_begin(TDSE_K_FLUX);
+    bt_flux<<<fgrid, kFluxThreads, sizeof(double2) * 2 * (flux_lmax + 1), stream>>>(B, all.act, flux_view(),
+                                                                                     ser_tab, 0);
+    prof_end(pf);
+    ++count;
+    EN_CUDA(cudaGetLastError(), "batch flux");
+  }
   bt_next_step<<<1, 1, 0, stream>>>(step_dev);
   ++count;
   EN_CUDA(cudaGetLastError(), "batch step counter");
@@ -1489,7 +1606,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   }
   int rc = upload_run(nE);
   if (rc) return rc;
-  if (ser_cap > 0 && (rc = upload_series(slots, steps, nE))) return rc;
+  if (steps_tab() && (rc = upload_series(slots, steps, nE))) return rc;
   const BatchDev B = device_view();
   if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) return rc;
   std::vector<std::vector<long long>> eager;
@@ -1555,15 +1672,15 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   return TDSE_OK;
 }
 
-// The dipole series' time table of a run (t, E(t) and A(t)/c at the end of
-// every step) and each slot's entry count so far.
+// The per-step time table of a run for the dipole series and the flux (t,
+// E(t) and A(t)/c at the end of every step) and each slot's series count so far.
 int Engine::upload_series(const std::vector<int> &slots, const std::vector<long> &steps, size_t nE) {
   hser_tab.assign(3 * nE, 0.0);
   for (size_t q = 0; q < slots.size(); ++q) {
     const int s = slots[q];
     const tdse_instance_spec &sp = spec[s];
     const PulseParams p{sp.E0, sp.omega, sp.ncycles, sp.cep, sp.pulse_shape};
-    const long todo = (long)std::min<long long>(steps[q], ser_cap - ser_count[s]);
+    const long todo = flux_nt >= 0 ? steps[q] : (long)std::min<long long>(steps[q], ser_cap - ser_count[s]);
     for (long n = 0; n < todo; ++n) {
       const double t = tstart[s] + (double)(nstep[s] + n + 1) * sp.dt;
       double *e = hser_tab.data() + 3 * ((size_t)n * capacity + s);
@@ -1578,9 +1695,109 @@ int Engine::upload_series(const std::vector<int> &slots, const std::vector<long>
   if (nE)
     EN_CUDA(cudaMemcpyAsync(ser_tab, hser_tab.data(), sizeof(double) * 3 * nE, cudaMemcpyHostToDevice, stream),
             "dipole series table");
-  EN_CUDA(cudaMemcpyAsync(ser_base, ser_count.data(), sizeof(long long) * capacity, cudaMemcpyHostToDevice, stream),
-          "dipole series counts");
+  if (ser_cap > 0)
+    EN_CUDA(cudaMemcpyAsync(ser_base, ser_count.data(), sizeof(long long) * capacity, cudaMemcpyHostToDevice,
+                            stream),
+            "dipole series counts");
   return TDSE_OK;
+}
+
+int Engine::flux_setup(bool enable, int nt, const double *cos_theta) {
+  if (poisoned) return TDSE_ERR_STATE;
+  EN_CUDA(cudaStreamSynchronize(stream), "sync before the flux setup");
+  cudaFree(flux_state);
+  cudaFree(flux_y);
+  cudaFree(flux_ct);
+  flux_state = flux_y = flux_ct = nullptr;
+  flux_nt = -1;
+  if (!enable) return TDSE_OK;
+  if (nt < 0 || (nt > 0 && !cos_theta)) return fail(TDSE_ERR_ARG, "need ntheta >= 0 and cos_theta for ntheta > 0");
+  std::vector<int> ib(capacity, 0), live;
+  int lmax = 0;
+  for (int s = 0; s < capacity; ++s) {
+    if (!placed[s]) continue;
+    const tdse_instance_spec &sp = spec[s];
+    // the grid point nearest r_b (r_j = (j + 1) dr, j 0-based); a tie goes inwards
+    const double x = sp.r_b / sp.dr - 1.0;
+    if (!(x > -0.5 && x < (double)sp.N - 0.5)) return fail(TDSE_ERR_ARG, "an instance's r_b lies outside its box");
+    ib[s] = std::min(sp.N - 1, std::max(0, (int)std::ceil(x - 0.5)));
+    lmax = std::max(lmax, sp.lmax);
+    live.push_back(s);
+  }
+  if (live.empty()) return fail(TDSE_ERR_ARG, "no instance");
+  if (sizeof(double2) * 2 * (size_t)(lmax + 1) > 48 * 1024) return fail(TDSE_ERR_ARG, "flux: lmax above 1535");
+  // Y_l0(theta_k) = sqrt((2l + 1) / (4 pi)) P_l(cos theta_k), P_l by Bonnet's recurrence
+  const size_t ys = (size_t)lmax + 1;
+  std::vector<double> ct(nt), y(ys * std::max(nt, 1), 0.0);
+  for (int k = 0; k < nt; ++k) {
+    const double c = cos_theta[k];
+    if (!(c >= -1.0 && c <= 1.0)) return fail(TDSE_ERR_ARG, "cos_theta values must lie in [-1, 1]");
+    ct[k] = c;
+    double pm = 0.0, p = 1.0;   // P_{l-1}, P_l
+    for (int l = 0; l <= lmax; ++l) {
+      y[(size_t)k * ys + l] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * p;
+      const double pn = ((2.0 * l + 1.0) * c * p - (double)l * pm) / (double)(l + 1);
+      pm = p;
+      p = pn;
+    }
+  }
+  const size_t nstate = (size_t)capacity * (2 + 2 * (size_t)nt);
+  const bool ok = cudaMalloc(&flux_state, sizeof(double) * nstate) == cudaSuccess &&
+                  cudaMalloc(&flux_y, sizeof(double) * y.size()) == cudaSuccess &&
+                  cudaMalloc(&flux_ct, sizeof(double) * std::max(nt, 1)) == cudaSuccess &&
+                  (flux_ib || cudaMalloc(&flux_ib, sizeof(int) * capacity) == cudaSuccess) &&
+                  (flux_slots || cudaMalloc(&flux_slots, sizeof(int) * capacity) == cudaSuccess);
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(flux_state);
+    cudaFree(flux_y);
+    cudaFree(flux_ct);
+    flux_state = flux_y = flux_ct = nullptr;
+    return fail(TDSE_ERR_OOM, "flux buffers");
+  }
+  EN_CUDA(cudaMemsetAsync(flux_state, 0, sizeof(double) * nstate, stream), "clear flux");
+  EN_CUDA(cudaMemcpyAsync(flux_y, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, stream), "flux table");
+  if (nt) EN_CUDA(cudaMemcpyAsync(flux_ct, ct.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, stream), "angles");
+  EN_CUDA(cudaMemcpyAsync(flux_ib, ib.data(), sizeof(int) * capacity, cudaMemcpyHostToDevice, stream), "flux radii");
+  EN_CUDA(cudaMemcpyAsync(flux_slots, live.data(), sizeof(int) * live.size(), cudaMemcpyHostToDevice, stream),
+          "flux slots");
+  flux_nt = nt;
+  flux_lmax = lmax;
+  // the current states open the integrals at zero: {t, E, A/c} at each slot's time
+  std::vector<double> now(3 * (size_t)capacity, 0.0);
+  for (int s : live) {
+    const tdse_instance_spec &sp = spec[s];
+    const PulseParams p{sp.E0, sp.omega, sp.ncycles, sp.cep, sp.pulse_shape};
+    const double t = time_of(s);
+    now[3 * s] = t;
+    now[3 * s + 1] = pulse_field(p, t);
+    now[3 * s + 2] = sp.gauge == TDSE_GAUGE_VELOCITY ? pulse_vecpot(p, t) / kLightAU : 0.0;
+  }
+  int rc = ensure(reinterpret_cast<void **>(&ser_tab), ser_tab_cap, sizeof(double) * now.size(), "flux times");
+  if (rc) return rc;
+  EN_CUDA(cudaMemcpyAsync(ser_tab, now.data(), sizeof(double) * now.size(), cudaMemcpyHostToDevice, stream),
+          "flux times");
+  const dim3 fgrid((unsigned)std::max(1, (nt + kFluxThreads / 32 - 1) / (kFluxThreads / 32)), (unsigned)live.size());
+  cudaEvent_t pf = prof_begin(TDSE_K_FLUX);
+  bt_flux<<<fgrid, kFluxThreads, sizeof(double2) * 2 * (lmax + 1), stream>>>(device_view(), flux_slots, flux_view(),
+                                                                             ser_tab, 1);
+  prof_end(pf);
+  ++launches;
+  EN_CUDA(cudaGetLastError(), "flux");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync flux setup");
+  return TDSE_OK;
+}
+
+int Engine::flux_read(int slot, std::vector<double> &out) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+  if (flux_nt < 0) return fail(TDSE_ERR_ARG, "the flux is not set up");
+  const size_t w = 2 + 2 * (size_t)flux_nt;
+  out.assign(w, 0.0);
+  EN_CUDA(cudaMemcpyAsync(out.data(), flux_state + w * slot, sizeof(double) * w, cudaMemcpyDeviceToHost, stream),
+          "read flux");
+  EN_CUDA(cudaStreamSynchronize(stream), "sync flux");
+  return check_status();
 }
 
 int Engine::dipole_series(long long cap) {
@@ -2043,6 +2260,24 @@ int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_
   const int rc = b->eng.dipole_series_read(i, out, max_entries, &n);
   if (count) *count = (long)n;
   return rc;
+}
+
+int tdse_batch_flux_setup(tdse_batch_t *b, int ntheta, const double *cos_theta) {
+  if (!b) return TDSE_ERR_ARG;
+  return b->eng.flux_setup(ntheta >= 0, ntheta, cos_theta);
+}
+
+int tdse_batch_flux_read(tdse_batch_t *b, int i, double *flux, double *yield, double *density, double *pad) {
+  if (!b || i < 0 || i >= b->count) return TDSE_ERR_ARG;
+  std::vector<double> v;
+  const int rc = b->eng.flux_read(i, v);
+  if (rc) return rc;
+  const size_t nt = (v.size() - 2) / 2;
+  if (flux) *flux = v[0];
+  if (yield) *yield = v[1];
+  if (density && nt) std::memcpy(density, v.data() + 2, sizeof(double) * nt);
+  if (pad && nt) std::memcpy(pad, v.data() + 2 + nt, sizeof(double) * nt);
+  return TDSE_OK;
 }
 
 long long tdse_batch_points(const tdse_batch_t *b) { return b ? b->npts : 0; }

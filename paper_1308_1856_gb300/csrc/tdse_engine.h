@@ -81,6 +81,17 @@ struct SeriesDev {
   int slots;
 };
 
+// The flux through each instance's sphere r = r_b (Sec. 4): per slot
+// {flux now, its time integral, density[nt] now, its integral[nt]}.
+struct FluxDev {
+  double *state;          // (2 + 2 nt) doubles per slot
+  const double *y;        // Y_l0(theta_k): y[k * ystride + l]
+  const double *ct;       // cos(theta_k)
+  const int *ib;          // per slot: the grid index nearest r_b
+  const double *dt;       // per slot: the step
+  int nt, ystride, slots, stencil;
+};
+
 // Launch schedule of the batched kernels.  Results do not depend on it
 // (chunks and their reduction order are fixed per instance); the autotuner
 // picks the fastest for the resident instances.
@@ -121,6 +132,13 @@ class Engine {
   int dipole_series(long long cap);
   // Entries recorded for a slot (up to max of them into out, 4 doubles each); synchronous.
   int dipole_series_read(int slot, double *out, long long max, long long *count);
+  // Integrate the flux through r = r_b of every placed slot (its spec's r_b)
+  // at nt angles from now on (enable 0: off); synchronous.  The slots must
+  // all be placed before the call.
+  int flux_setup(bool enable, int nt, const double *cos_theta);
+  // {flux, yield, density[nt], pad[nt]} of a slot; synchronous.
+  int flux_read(int slot, std::vector<double> &out);
+  int flux_angles() const { return flux_nt; }
   // {norm, dipole, yield, p_ground, l_pop[0..L]} of a slot; synchronous.
   int observables(int slot, std::vector<double> &out);
   int set_state(int slot, const double *F_host);
@@ -181,6 +199,7 @@ class Engine {
   int launch_b(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s);
   int enqueue_step(const BatchDev &B, const Segment &sg, int &count);
   SeriesDev series_view() const;
+  FluxDev flux_view() const;
   int upload_series(const std::vector<int> &slots, const std::vector<long> &steps, size_t nE);
   void drop_graphs();
   cudaEvent_t prof_begin(int kind);
@@ -220,6 +239,11 @@ class Engine {
   double *ser_tab = nullptr;
   size_t ser_tab_cap = 0;
   std::vector<double> hser_tab;
+  // flux integrals (flux_nt < 0: off)
+  int flux_nt = -1, flux_lmax = 0;
+  double *flux_state = nullptr, *flux_y = nullptr, *flux_ct = nullptr;
+  int *flux_ib = nullptr, *flux_slots = nullptr;
+  bool steps_tab() const { return ser_cap > 0 || flux_nt >= 0; }
   double *obs_partials = nullptr, *obs_out = nullptr;
   size_t obs_cap = 0;
   unsigned *obs_ticket = nullptr;
