@@ -582,6 +582,19 @@ int tdse_batch_dipole_series(tdse_batch_t *b, long capacity);
 int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_entries, long *count);
 
 /*
+ * Imaginary time (Sec. 3) for every instance of an FP64 batch: nsteps
+ * Lanczos steps of dtau = the instance's dt with exp(-T dtau) in place of
+ * exp(-i T dt), no field, and the state renormalised to dr sum |f|^2 = 1
+ * after each step, as tdse_propagate_imag with TDSE_LANCZOS (ground states of
+ * many grids at once).  The instances' times do not change.  energies (count
+ * doubles, may be NULL): each instance's energy estimate of the last step,
+ * -ln(||psi_new|| / ||psi_old||) / dtau (NaN before the first step); the call
+ * is synchronous when it is given.  Errors: TDSE_ERR_ARG (a mixed-precision
+ * batch, nsteps < 0), TDSE_ERR_CUDA.
+ */
+int tdse_batch_propagate_imag(tdse_batch_t *b, long nsteps, double *energies);
+
+/*
  * Integrate the flux through the sphere r = r_b of every instance (its
  * spec's r_b; Sec. 4, Eqs. (flux), (pad), (yield)) at the same ntheta angles
  * cos_theta[k] in [-1, 1], as tdse_flux_setup: the current states open the

@@ -396,6 +396,13 @@ class Batch:
                                                         ctypes.byref(n)))
         return out
 
+    def propagate_imag(self, nsteps: int) -> np.ndarray:
+        """nsteps imaginary-time Lanczos steps of every instance (dtau = its dt,
+        Sec. 3); returns each instance's energy estimate of the last step."""
+        e = np.zeros(len(self.specs))
+        self._check(C.tdse_batch_propagate_imag(self.h, int(nsteps), e.ctypes.data_as(C._dp)))
+        return e
+
     def flux_setup(self, cos_theta=None, enable: bool = True):
         """Integrate every instance's flux through its r_b (and the densities at
         cos_theta) from now on (Sec. 4); enable=False turns it off."""

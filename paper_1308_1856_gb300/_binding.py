@@ -125,6 +125,7 @@ SIGNATURES = {
     "tdse_batch_observables": (_c_int, [_vp, _c_int, _dp, _vp, _dp, _dp, _dp]),
     "tdse_batch_dipole_series": (_c_int, [_vp, _c_long]),
     "tdse_batch_dipole_series_read": (_c_int, [_vp, _c_int, _dp, _c_long, ctypes.POINTER(_c_long)]),
+    "tdse_batch_propagate_imag": (_c_int, [_vp, _c_long, _dp]),
     "tdse_batch_flux_setup": (_c_int, [_vp, _c_int, _dp]),
     "tdse_batch_flux_read": (_c_int, [_vp, _c_int, _dp, _dp, _dp, _dp]),
     "tdse_batch_points": (ctypes.c_longlong, [_vp]),
@@ -248,6 +249,7 @@ tdse_batch_propagate_io = _fn("tdse_batch_propagate_io")
 tdse_batch_observables = _fn("tdse_batch_observables")
 tdse_batch_dipole_series = _fn("tdse_batch_dipole_series")
 tdse_batch_dipole_series_read = _fn("tdse_batch_dipole_series_read")
+tdse_batch_propagate_imag = _fn("tdse_batch_propagate_imag")
 tdse_batch_flux_setup = _fn("tdse_batch_flux_setup")
 tdse_batch_flux_read = _fn("tdse_batch_flux_read")
 tdse_batch_points = _fn("tdse_batch_points")

@@ -324,9 +324,10 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   });
 }
 
-// psi_new = sum_{j<k} coef_j U_j, mask, ||psi_new|| (FP64).
+// psi_new = sum_{j<k} coef_j U_j, mask (unless mask_on is 0: imaginary
+// time), ||psi_new|| (FP64).
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
-    bt_combine_fp64(BatchDev B, ChunkList cl) {
+    bt_combine_fp64(BatchDev B, ChunkList cl, int mask_on) {
   // the chunk's coefficients, one copy per warp
   __shared__ double2 wcoef[kElemThreads / 32][kMaxKrylov];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
 #pragma unroll
       for (int q = 0; q < kCombinePts; ++q) {
         if (q < nq) {
-          if (iq[q] >= I.mask_start) {
+          if (mask_on && iq[q] >= I.mask_start) {
             const double mv = mask[iq[q]];
             ox[q] = __dmul_rn(mv, ox[q]);
             oy[q] = __dmul_rn(mv, oy[q]);
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     double s;
     if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
       const double nrm = sqrt(s);
+      ls->psinorm0 = ls->psinorm;
       ls->psinorm = nrm;
       ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
       if (!isfinite(s)) atomicOr(B.status, kStatusNonFinite);
@@ -560,6 +562,39 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     double s;
     if (chunk_done(B, I, inst, ci, I.nchunk_e, accd, s) && (threadIdx.x & 31) == 0) {
       const double nrm = sqrt(s);
+      ls->psinorm0 = ls->psinorm;
+      ls->psinorm = nrm;
+      ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      if (!isfinite(s)) atomicOr(B.status, kStatusNonFinite);
+    }
+  });
+}
+
+// ---- Sec. 3: imaginary time ------------------------------------------------
+// After the combine of an imaginary-time step (exp(-T dtau) in the small
+// exponential, no field): psi <- psi / sqrt(dr ||psi||^2), so that the norm
+// dr sum |f|^2 is one again; ||psi|| of the normalised state (the next
+// step's sigma_0); and the energy estimate -ln(||psi_new|| / ||psi_old||) / dtau
+// of the step (the decay rate of the norm).
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
+    bt_imag_normalize(BatchDev B, ChunkList cl, const double *__restrict__ dtau, double *energy) {
+  for_my_chunks(cl, [&](int inst, int ci) {
+    const BatchInst I = B.inst[inst];
+    LanczosScalars *ls = B.ls + inst;
+    const double n1 = ls->psinorm;   // every chunk reads it before the last one rewrites it
+    const double sc = 1.0 / (sqrt(I.dr) * n1);
+    double2 *x = I.psi;
+    double acc = 0.0;
+    chunk_points_x4(I, ci, [&](size_t idx) { return x[idx]; }, [&](size_t idx, int, const double2 &v) {
+      const double2 o = make_double2(__dmul_rn(sc, v.x), __dmul_rn(sc, v.y));
+      x[idx] = o;
+      acc = __fma_rn(o.x, o.x, acc);
+      acc = __fma_rn(o.y, o.y, acc);
+    });
+    double s;
+    if (chunk_done(B, I, inst, ci, I.nchunk_e, acc, s) && (threadIdx.x & 31) == 0) {
+      const double nrm = sqrt(s);
+      energy[inst] = -log(n1 / ls->psinorm0) / dtau[inst];
       ls->psinorm = nrm;
       ls->sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
       if (!isfinite(s)) atomicOr(B.status, kStatusNonFinite);
@@ -865,6 +900,7 @@ Engine::~Engine() {
   cudaFree(flux_ct);
   cudaFree(flux_ib);
   cudaFree(flux_slots);
+  cudaFree(imag_e);
   for (auto &mk : marks) {
     cudaEventDestroy(mk.a);
     cudaEventDestroy(mk.b);
@@ -1330,6 +1366,8 @@ std::vector<long long> Engine::segment_key(const Segment &sg) const {
                         (const void *)flux_ib})
     k.push_back((long long)(uintptr_t)p);
   k.push_back(flux_nt);
+  k.push_back(run_imag ? 1 : 0);
+  k.push_back((long long)(uintptr_t)imag_e);
   k.push_back(ser_cap);
   k.push_back(sg.doff);
   k.push_back(sg.dnact);
@@ -1512,17 +1550,24 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
     }
   }
   cudaEvent_t px = prof_begin(TDSE_K_LANCZOS_EXPM);
-  EN_CUDA(launch_lanczos_expm_batched(all.nact, all.act, m_dev, dt_dev, ls, stream), "batch expm");
+  EN_CUDA(launch_lanczos_expm_batched(all.nact, all.act, m_dev, dt_dev, run_imag, ls, stream), "batch expm");
   prof_end(px);
   ++count;
   const unsigned egrid = (unsigned)(sms * sched.eblocks);
   cudaEvent_t pc = prof_begin(TDSE_K_LANCZOS_COMBINE);
   if (precision == TDSE_MIXED) bt_combine_mixed<<<egrid, kElemThreads, 0, stream>>>(B, all);
-  else bt_combine_fp64<<<egrid, kElemThreads, 0, stream>>>(B, all);
+  else bt_combine_fp64<<<egrid, kElemThreads, 0, stream>>>(B, all, run_imag ? 0 : 1);
   prof_end(pc);
   ++count;
   EN_CUDA(cudaGetLastError(), "batch combine");
-  if (sg.dtotal > 0) {
+  if (run_imag) {
+    cudaEvent_t pn = prof_begin(TDSE_K_NORM);
+    bt_imag_normalize<<<egrid, kElemThreads, 0, stream>>>(B, all, dt_dev, imag_e);
+    prof_end(pn);
+    ++count;
+    EN_CUDA(cudaGetLastError(), "batch imaginary-time normalisation");
+  }
+  if (sg.dtotal > 0 && !run_imag) {
     // the dipole moments of the new states (Sec. 4), recorded per step
     const ChunkList dl = list_at(lists, sg.doff, sg.dnact, sg.dtotal);
     const SeriesDev S = series_view();
@@ -1533,7 +1578,7 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
     ++count;
     EN_CUDA(cudaGetLastError(), "batch dipole");
   }
-  if (flux_nt >= 0) {
+  if (flux_nt >= 0 && !run_imag) {
     // the flux through every instance's sphere and its time integrals (Sec. 4)
     const dim3 fgrid((unsigned)std::max(1, (flux_nt + kFluxThreads / 32 - 1) / (kFluxThreads / 32)),
                      (unsigned)all.nact);
@@ -1550,9 +1595,10 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
   return TDSE_OK;
 }
 
-int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
+int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps, bool imag) {
   if (poisoned) return TDSE_ERR_STATE;
   if (slots.size() != steps.size()) return fail(TDSE_ERR_ARG, "slots and steps differ in length");
+  if (imag && precision != TDSE_FP64) return fail(TDSE_ERR_ARG, "imaginary time runs in FP64 batches only");
   long kmax = 0;
   std::vector<char> seen(capacity, 0);
   for (size_t q = 0; q < slots.size(); ++q) {
@@ -1563,6 +1609,15 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     kmax = std::max(kmax, steps[q]);
   }
   if (kmax == 0) return TDSE_OK;
+  if (imag && !imag_e) {
+    if (cudaMalloc(&imag_e, sizeof(double) * capacity) != cudaSuccess) {
+      cudaGetLastError();
+      imag_e = nullptr;
+      return fail(TDSE_ERR_OOM, "imaginary-time energies");
+    }
+    EN_CUDA(cudaMemsetAsync(imag_e, 0xff, sizeof(double) * capacity, stream), "clear energies");   // NaN
+  }
+  run_imag = imag;
   // launch errors are read with cudaGetLastError: drop an earlier, unrelated
   // non-sticky error of this thread first (a sticky one fails the launches too)
   cudaGetLastError();
@@ -1596,7 +1651,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   // field at the mid-point of every step: E[n * capacity + slot]
   const size_t nE = (size_t)kmax * capacity;
   hE.assign(nE, 0.0);
-  for (size_t q = 0; q < slots.size(); ++q) {
+  for (size_t q = 0; q < slots.size() && !imag; ++q) {
     const int s = slots[q];
     const tdse_instance_spec &sp = spec[s];
     for (long n = 0; n < steps[q]; ++n) {
@@ -1606,7 +1661,7 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
   }
   int rc = upload_run(nE);
   if (rc) return rc;
-  if (steps_tab() && (rc = upload_series(slots, steps, nE))) return rc;
+  if (steps_tab() && !imag && (rc = upload_series(slots, steps, nE))) return rc;
   const BatchDev B = device_view();
   if (!need_norm.empty() && (rc = norm_pass(B, need_norm, norm_off, norm_total))) return rc;
   std::vector<std::vector<long long>> eager;
@@ -1665,10 +1720,24 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps) {
     }
   }
   last_eager = std::move(eager);
-  for (size_t q = 0; q < slots.size(); ++q) {
+  for (size_t q = 0; q < slots.size() && !imag; ++q) {
     nstep[slots[q]] += steps[q];
     if (ser_cap > 0) ser_count[slots[q]] = std::min(ser_cap, ser_count[slots[q]] + (long long)steps[q]);
   }
+  return TDSE_OK;
+}
+
+int Engine::imag_energies(const std::vector<int> &slots, double *out) {
+  if (poisoned) return TDSE_ERR_STATE;
+  std::vector<double> e(capacity, std::nan(""));
+  if (imag_e) {
+    EN_CUDA(cudaMemcpyAsync(e.data(), imag_e, sizeof(double) * capacity, cudaMemcpyDeviceToHost, stream),
+            "read energies");
+  }
+  EN_CUDA(cudaStreamSynchronize(stream), "sync energies");
+  int rc = check_status();
+  if (rc) return rc;
+  for (size_t q = 0; q < slots.size(); ++q) out[q] = e[slots[q]];
   return TDSE_OK;
 }
 
@@ -2260,6 +2329,16 @@ int tdse_batch_dipole_series_read(tdse_batch_t *b, int i, double *out, long max_
   const int rc = b->eng.dipole_series_read(i, out, max_entries, &n);
   if (count) *count = (long)n;
   return rc;
+}
+
+int tdse_batch_propagate_imag(tdse_batch_t *b, long nsteps, double *energies) {
+  if (!b) return TDSE_ERR_ARG;
+  if (nsteps < 0) return b->eng.fail(TDSE_ERR_ARG, "nsteps must be >= 0");
+  std::vector<int> slots(b->count);
+  for (int i = 0; i < b->count; ++i) slots[i] = i;
+  int rc = b->eng.run(slots, std::vector<long>(b->count, nsteps), true);
+  if (rc || !energies) return rc;
+  return b->eng.imag_energies(slots, energies);
 }
 
 int tdse_batch_flux_setup(tdse_batch_t *b, int ntheta, const double *cos_theta) {

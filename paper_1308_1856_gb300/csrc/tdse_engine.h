@@ -125,8 +125,13 @@ class Engine {
   int place(int slot, const tdse_instance_spec &s, void *mem);
   // Forget the instance in `slot` (its memory may be reused afterwards).
   void clear(int slot);
-  // Advance slots[i] by steps[i] >= 0 Lanczos steps; asynchronous.
-  int run(const std::vector<int> &slots, const std::vector<long> &steps);
+  // Advance slots[i] by steps[i] >= 0 Lanczos steps; asynchronous.  imag:
+  // imaginary-time steps of dtau = the spec's dt (Sec. 3: no field, exp(-T
+  // dtau), the state renormalised after each step, the time left as it is);
+  // FP64 only.
+  int run(const std::vector<int> &slots, const std::vector<long> &steps, bool imag = false);
+  // The last imaginary-time step's energy estimate of `slots` (synchronous).
+  int imag_energies(const std::vector<int> &slots, double *out);
   // Record {t, <z>, <zdot>, <zddot>} of every slot after each of its steps,
   // up to `cap` entries per slot (0: off); every call discards the record.
   int dipole_series(long long cap);
@@ -239,6 +244,8 @@ class Engine {
   double *ser_tab = nullptr;
   size_t ser_tab_cap = 0;
   std::vector<double> hser_tab;
+  bool run_imag = false;          // the run being enqueued is in imaginary time
+  double *imag_e = nullptr;       // per slot: the last imaginary-time energy estimate
   // flux integrals (flux_nt < 0: off)
   int flux_nt = -1, flux_lmax = 0;
   double *flux_state = nullptr, *flux_y = nullptr, *flux_ct = nullptr;

@@ -46,6 +46,7 @@ struct LanczosScalars {
   double ratio[kMaxKrylov + 1];  // ratio_j = sigma_{j-1} / sigma_j  (= beta_{j-1} sigma_{j-1})
   double acoef[kMaxKrylov];      // -alpha_j sigma_j (coefficient of U_j in U_{j+1})
   double psinorm;                // ||psi|| at the start of the step
+  double psinorm0;               // batch: ||psi|| before the last combine (imaginary-time energy)
   double2 coef[kMaxKrylov];      // psi_new = sum_j coef_j U_j
   int kdim;                      // Krylov dimension kept
   int pad;
@@ -164,7 +165,7 @@ cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const d
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag = false);
 // One block per listed instance: ids[0..count) index m, dt and ls (ids NULL:
 // instances 0..count-1).
-cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt,
+cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt, bool imag,
                                         LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,
                                    double2 *psi, const double2 *work, size_t stride,

@@ -14,9 +14,9 @@ __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, Lan
 // One block per listed instance of a batch (ids[b], or b when ids is null).
 __global__ void __launch_bounds__(kEx)
     lanczos_expm_batched_kernel(const int *__restrict__ ids, const int *__restrict__ m,
-                                const double *__restrict__ dt, LanczosScalars *ls) {
+                                const double *__restrict__ dt, LanczosScalars *ls, int imag) {
   const int i = ids ? ids[blockIdx.x] : (int)blockIdx.x;
-  expm_body(m[i], dt[i], ls + i);
+  expm_body(m[i], dt[i], ls + i, imag != 0);
 }
 
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag) {
@@ -24,10 +24,10 @@ cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt,
+cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt, bool imag,
                                         LanczosScalars *ls, cudaStream_t st) {
   if (count < 1) return cudaSuccess;
-  lanczos_expm_batched_kernel<<<count, kEx, 0, st>>>(ids, m, dt, ls);
+  lanczos_expm_batched_kernel<<<count, kEx, 0, st>>>(ids, m, dt, ls, imag ? 1 : 0);
   return cudaGetLastError();
 }
 
