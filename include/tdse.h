@@ -487,7 +487,7 @@ typedef struct {
   double dt;            /* step                                                   */
   double absorber_r;    /* cos^(1/8) mask for r > absorber_r; >= r_N switches it off */
   double r_b;           /* yield radius                                           */
-  int gauge;            /* TDSE_GAUGE_LENGTH (0) or TDSE_GAUGE_VELOCITY (FP64 batches only) */
+  int gauge;            /* TDSE_GAUGE_LENGTH (0) or TDSE_GAUGE_VELOCITY (1)                   */
   int pulse_shape;      /* TDSE_PULSE_SIN2_E (0) or TDSE_PULSE_SIN2_A, as tdse_set_pulse_shape */
 } tdse_instance_spec;
 

@@ -414,9 +414,61 @@ __device__ __forceinline__ MixedIn mixed_in(const BatchDev &B, const BatchInst &
   in.c1 = (float)I.c1;
   in.c2 = (float)I.c2;
   in.E = (float)field_of(B, inst);
-  in.rinv = nullptr;   // the mixed batch runs the length gauge
-  in.d1c = 0.f;
+  in.rinv = I.rinvf;   // velocity gauge only (null otherwise)
+  in.d1c = (float)I.d1c;
   return in;
+}
+
+// Mixed Lanczos phase A of the velocity-gauge instances of a mixed batch (a
+// launch of its own over their row-segment chunks): the register walker
+// mixed_walk_rows with the (A/c) p_z coupling, in the arithmetic of the tile
+// kernel (z = sigma_j H U_j - ratio_j U_{j-1} in FP32, alpha_j = sigma_j
+// Re<U_j, z> from FP32 products summed in pairs, then FP64).  The operand is
+// the split of psi for j = 0 and the FP32 U_j after.
+template <int ST>
+__global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
+    bt_lanczos_a_mixed_vg(BatchDev B, ChunkList cl, int j) {
+  for_my_chunks(cl, [&](int inst, int ci) {
+    const BatchInst I = B.inst[inst];
+    LanczosScalars *ls = B.ls + inst;
+    const long long G = (long long)I.N * (I.L + 1);
+    const float2 *hi = I.hi, *lo = I.lo;
+    float2 *z = I.mwork;
+    const float2 *uprev = (j >= 2) ? I.mwork + (long long)(j - 1) * G : nullptr;
+    const double sigd = ls->sigma[j];
+    const float sig = (float)sigd;
+    const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
+    PairSum acc;
+    auto epi = [&](int, size_t idx, float2 t, float2 u) {
+      float2 o = make_float2(sig * t.x, sig * t.y);
+      if (j > 0) {
+        float2 up;
+        if (uprev) {
+          up = uprev[idx];
+        } else {
+          const float2 h = hi[idx], l = lo[idx];
+          up = make_float2(h.x + l.x, h.y + l.y);
+        }
+        o.x = fmaf(-cprev, up.x, o.x);
+        o.y = fmaf(-cprev, up.y, o.y);
+      }
+      z[idx] = o;
+      acc.add(fmaf(u.x, o.x, u.y * o.y));
+    };
+    if (j == 0) {
+      const MixedIn in = mixed_in(B, I, inst, hi, lo, nullptr);
+      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, true, false, 0, true>(in, i, l0, l1, epi); });
+    } else {
+      const MixedIn in = mixed_in(B, I, inst, nullptr, nullptr, I.mwork + (long long)j * G);
+      chunk_columns(I, ci, [&](int i, int l0, int l1) { mixed_walk_rows<ST, false, true, 0, true>(in, i, l0, l1, epi); });
+    }
+    const double accd = acc.value();
+    double s;
+    if (chunk_done(B, I, inst, ci, I.nchunk, accd, s) && (threadIdx.x & 31) == 0) {
+      ls->alpha[j] = s * sigd;
+      ls->acoef[j] = -(s * sigd) * sigd;
+    }
+  });
 }
 
 #include "tdse_batch_tile.cuh"
@@ -792,7 +844,8 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, dpart, ref0, rinv, total;
+  size_t psi, diag, diagf, hi, lo, work, mwork, rj, mask, kappa, rjf, kappaf, partial, dpart, ref0, rinv, rinvf,
+      total;
 };
 
 // Tiles of the mixed tile kernel on an N x (L+1) grid.
@@ -828,6 +881,7 @@ Layout layout_of(const tdse_instance_spec &s, int precision) {
   L.dpart = take(8 * 4 * ((nseg + kChunkSegs - 1) / kChunkSegs));
   L.ref0 = take(16 * N);
   L.rinv = (!mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? take(8 * N) : none;
+  L.rinvf = (mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? take(4 * N) : none;
   L.total = off;
   return L;
 }
@@ -972,7 +1026,6 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
     return fail(TDSE_ERR_ARG, "bad slot or unaligned instance memory");
   if (!valid_spec(s)) return fail(TDSE_ERR_ARG, "invalid instance spec");
   const bool mixed = precision == TDSE_MIXED;
-  if (mixed && s.gauge == TDSE_GAUGE_VELOCITY) return fail(TDSE_ERR_ARG, "the velocity gauge runs in FP64 batches only");
   const Layout Lo = layout_of(s, precision);
   char *base = static_cast<char *>(mem);
   const int N = s.N, L = s.lmax;
@@ -982,9 +1035,11 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.L = L;
   I.m = s.krylov;
   I.nseg = (int)((size_t)((N + 31) / 32) * (L + 1));
-  // reduction chunks of the stencil kernel: 64 row segments (FP64), or tiles
-  // of 256 columns x kTileRows rows (the mixed tile kernel)
-  I.nchunk = mixed ? tile_count(N, L) : (I.nseg + kChunkSegs - 1) / kChunkSegs;
+  // reduction chunks of the stencil kernel: 64 row segments (FP64 and the
+  // mixed velocity gauge), or tiles of 256 columns x kTileRows rows (the
+  // mixed tile kernel)
+  const bool vg = s.gauge == TDSE_GAUGE_VELOCITY;
+  I.nchunk = (mixed && !vg) ? tile_count(N, L) : (I.nseg + kChunkSegs - 1) / kChunkSegs;
   I.nchunk_e = (int)((G + kChunkPts - 1) / kChunkPts);
   I.nchunk_d = (I.nseg + kChunkSegs - 1) / kChunkSegs;
   I.dr = s.dr;
@@ -1009,7 +1064,8 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   I.ref0 = reinterpret_cast<double2 *>(base + Lo.ref0);
   I.gauge = s.gauge;
   I.d1c = (stencil == 5) ? 1.0 / (12.0 * s.dr) : 1.0 / (2.0 * s.dr);
-  I.rinv = (!mixed && s.gauge == TDSE_GAUGE_VELOCITY) ? reinterpret_cast<double *>(base + Lo.rinv) : nullptr;
+  I.rinv = (!mixed && vg) ? reinterpret_cast<double *>(base + Lo.rinv) : nullptr;
+  I.rinvf = (mixed && vg) ? reinterpret_cast<float *>(base + Lo.rinvf) : nullptr;
   if (mixed) {
     I.diagf = reinterpret_cast<float *>(base + Lo.diagf);
     I.hi = reinterpret_cast<float2 *>(base + Lo.hi);
@@ -1074,6 +1130,13 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
       }
     }
     for (int j = 0; j < N; ++j) rf[j] = (float)rj[j];
+    if (I.rinvf) {
+      std::vector<float> rif(N);
+      for (int j = 0; j < N; ++j) rif[j] = (float)(1.0 / rj[j]);
+      EN_CUDA(cudaMemcpyAsync((void *)I.rinvf, rif.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st),
+              "1/r table");
+      EN_CUDA(cudaStreamSynchronize(st), "sync 1/r table");
+    }
     for (int l = 0; l < L + 2; ++l) kf[l] = (float)kap[l];
     EN_CUDA(cudaMemcpyAsync((void *)I.diagf, df.data(), sizeof(float) * G, cudaMemcpyHostToDevice, st), "diag");
     EN_CUDA(cudaMemcpyAsync((void *)I.rjf, rf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st), "r table");
@@ -1498,9 +1561,16 @@ int Engine::launch_a(const BatchDev &B, const ChunkList &cl, int j, const Schedu
   return TDSE_OK;
 }
 
-// Velocity-gauge instances (FP64 only): the same kernel with the (A/c) p_z coupling.
+// Velocity-gauge instances: the same FP64 kernel with the (A/c) p_z coupling,
+// or the mixed register walker with it.
 int Engine::launch_a_velocity(const BatchDev &B, const ChunkList &cl, int j, const Schedule &s) {
   const unsigned grid = (unsigned)(sms * s.sblocks);
+  if (precision == TDSE_MIXED) {
+    if (stencil == 5) bt_lanczos_a_mixed_vg<5><<<grid, kBlockJ, 0, stream>>>(B, cl, j);
+    else bt_lanczos_a_mixed_vg<3><<<grid, kBlockJ, 0, stream>>>(B, cl, j);
+    EN_CUDA(cudaGetLastError(), "batch lanczos a (mixed, velocity gauge)");
+    return TDSE_OK;
+  }
   if (stencil == 5) launch_a_vg_st<5>(s.pf, grid, stream, B, cl, j);
   else launch_a_vg_st<3>(s.pf, grid, stream, B, cl, j);
   EN_CUDA(cudaGetLastError(), "batch lanczos a (velocity gauge)");
@@ -1981,7 +2051,7 @@ int Engine::autotune(const std::vector<int> &slots) {
   const int nring = precision == TDSE_MIXED ? (int)(sizeof(kRingChoices) / sizeof(int)) : 1;
   // three blocks per SM only for the mixed tile kernel (the FP64 stencil kernel's blocks fill an SM at two)
   const int sbmax = precision == TDSE_MIXED ? kTileBlocksPerSM : kStencilBlocksPerSM;
-  for (int sb = 1; sb <= sbmax && !rc; ++sb)
+  for (int sb = 1; sb <= sbmax && !rc && sg.total[0] > 0; ++sb)
     for (int ri = 0; ri < nring && !rc; ++ri)
       for (int pf : kPfChoices) {
         const int ring = kRingChoices[ri];

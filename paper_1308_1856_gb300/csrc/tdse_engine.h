@@ -25,14 +25,16 @@ struct BatchInst {
   int N, L, m;
   int mask_start;        // first radial index with mask != 1 (N if none)
   int nseg;              // 32-point row segments
-  int nchunk;            // reduction chunks of the stencil kernels (row segments)
+  int nchunk;            // reduction chunks of the stencil kernels (row segments; tiles for mixed
+                         // length-gauge instances)
   int nchunk_e;          // reduction chunks of the elementwise kernels (consecutive points)
   int nchunk_d;          // reduction chunks of the dipole kernel (kChunkSegs row segments, both precisions)
   int gauge;             // TDSE_GAUGE_LENGTH or TDSE_GAUGE_VELOCITY (FP64 only)
   double c1, c2;         // stencil coefficients (c0 is folded into diag)
   double d1c;            // first-derivative scale of the velocity gauge (1/(12 dr) or 1/(2 dr))
   double dr, Z;          // grid spacing and nuclear charge (the dipole moments' weights)
-  const double *rinv;    // 1/r_j (velocity gauge; null otherwise)
+  const double *rinv;    // 1/r_j (FP64 velocity gauge; null otherwise)
+  const float *rinvf;    // 1/r_j (mixed velocity gauge; null otherwise)
   double2 *psi;          // (L+1) x N state, l-major
   const double *diag;    // FP64: c0 + l(l+1)/(2 r^2) - Z/r
   const float *diagf;    // mixed: l(l+1)/(2 r^2) - Z/r (difference-form stencil)

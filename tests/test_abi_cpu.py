@@ -96,7 +96,7 @@ def test_server_instance_bytes(lib):
         s = _spec(N=N, lmax=L, krylov=m)
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == fp64
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_MIXED) == mixed
-    # a velocity-gauge instance also keeps 1/r (FP64)
+    # a velocity-gauge instance also keeps 1/r
     for N, L, m in [(1000, 15, 12), (33, 0, 1)]:
         G = N * (L + 1)
         nchunk = max(-(-((N + 31) // 32) * (L + 1) // 64), -(-G // 2048))
@@ -104,6 +104,9 @@ def test_server_instance_bytes(lib):
         common = up(16 * G) + up(8 * N) * 2 + up(8 * (L + 2)) + up(8 * nchunk) + up(32 * ndip) + up(16 * N)
         s = _spec(N=N, lmax=L, krylov=m, gauge=1)
         assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_FP64) == common + up(8 * G) + up(16 * G * m) + up(8 * N)
+        # ... and a mixed one keeps it in FP32 (4 bytes)
+        mixed = common + up(4 * G) + 2 * up(8 * G) + up(8 * G * m) + up(4 * N) + up(4 * (L + 2)) + up(4 * N)
+        assert B.tdse_server_instance_bytes(ctypes.byref(s), B.TDSE_MIXED) == mixed
     bad = _spec(krylov=0)
     assert B.tdse_server_instance_bytes(ctypes.byref(bad), B.TDSE_FP64) == 0
     assert B.tdse_server_instance_bytes(ctypes.byref(_spec(gauge=2)), B.TDSE_FP64) == 0
