@@ -1010,6 +1010,65 @@ def run_step_observables(D, steps=5, warmup=3, ntheta=180, r_b=10.0):
     return out
 
 
+def run_batched_observables(D, args, steps=5, warmup=3, ntheta=180):
+    """The batched configuration (FP64) with the Sec. 4 output of every
+    instance after every step (the dipole series and the flux through each
+    instance's r_b with ntheta angles), against the same steps without it;
+    and imaginary-time steps of the whole batch (dtau = each instance's dt,
+    Sec. 3).  L2 flushed before every step."""
+    r = BatchRow("fp64", D.sptr, count=args.batch_count, schedule=args.schedule.get("fp64"))
+    b = r.b
+    ct = np.cos((np.arange(ntheta) + 0.5) * np.pi / ntheta)
+    out = {"workload": f"batched configuration, FP64; dipole series + flux at each r_b with {ntheta} angles "
+                       f"after every step; imaginary-time steps of the same batch; L2 flushed before every step",
+           "gp_per_step": r.gp}
+
+    def timed(call):
+        for _ in range(warmup):
+            D.flush()
+            call()
+        D.sync()
+        evs = D.events(steps)
+        for k in range(steps):
+            D.flush(k)
+            evs[k][0].record(D.stream)
+            call()
+            evs[k][1].record(D.stream)
+        D.sync()
+        return sum(a.elapsed_time(c) for a, c in evs) / steps
+
+    out["ms_per_step_without"] = timed(r.step)
+    b.record_dipole(2 * (steps + warmup) + 8)
+    b.flux_setup(ct)
+    out["ms_per_step_with"] = timed(r.step)
+    out["overhead_frac"] = out["ms_per_step_with"] / out["ms_per_step_without"] - 1.0
+    b.profile(True)
+    for k in range(2):
+        D.flush(k)
+        r.step()
+    prof = b.profile_read()
+    b.profile(False)
+    dms, dn = prof.get("dipole", (0.0, 0))
+    fms, fn = prof.get("flux", (0.0, 0))
+    if dn:
+        ach = DIPOLE_FLOPS_PER_GP * r.gp / (dms / dn * 1e-3) / 1e12
+        out["dipole_kernel"] = {"bound": "alu", "kernel": "bt_dipole (batched, fp64)", "achieved": ach,
+                                "peak": D.fp64_peak, "unit": "TFLOP/s", "frac": ach / D.fp64_peak,
+                                "avg_launch_ms": dms / dn, "launches": dn}
+    out["flux_kernel_avg_ms"] = fms / max(fn, 1)
+    ser = b.dipole_series(0)
+    out["series_entries_instance0"] = int(ser.shape[0])
+    b.record_dipole(0)
+    b.flux_setup(enable=False)
+    from paper_1308_1856_gb300 import _binding as C
+    ms_imag = timed(lambda: C.tdse_batch_propagate_imag(b.h, 1, None))   # asynchronous: no energies read
+    e = b.propagate_imag(1)
+    out["imag"] = {"ms_per_step": ms_imag, "gp_steps_per_s": r.gp / (ms_imag * 1e-3),
+                   "energy_range": [float(np.nanmin(e)), float(np.nanmax(e))]}
+    r.close()
+    return out
+
+
 def run_probe(D):
     """FP64 and FP32 FMA throughput of this GPU (tdse_fma_throughput)."""
     from paper_1308_1856_gb300 import fma_throughput
@@ -1076,6 +1135,11 @@ def compact(res):
         out["hpsi"] = {"f64": {"us": sig(h["fp64"]["us_per_call"], 3), "alu_frac": sig(h["fp64"]["alu_frac"], 3),
                                "hbm_frac": sig(h["fp64"]["hbm_frac"], 3)},
                        "mixed": {"us": sig(h["mixed"]["us_per_call"], 3), "hbm_frac": sig(h["mixed"]["hbm_frac"], 3)}}
+    if "batched_observables" in res:
+        o = res["batched_observables"]
+        out["c4_batched_obs"] = {"overhead_frac": sig(o["overhead_frac"], 3),
+                                 "dipole_frac": sig((o.get("dipole_kernel") or {}).get("frac"), 3),
+                                 "imag_gps": sig(o["imag"]["gp_steps_per_s"])}
     if "fp64_probe" in res:
         out["fp64_probe_tflops"] = sig(res["fp64_probe"]["fp64_tflops"], 4)
     if "cpu_baselines" in res:
@@ -1110,6 +1174,8 @@ def run_ours(args, ws, rank, local):
         res["rk_pairs"] = run_rk_pairs(D)
     if legs in ("all", "obs"):
         res["step_observables"] = run_step_observables(D)
+    if legs in ("all", "batch_obs"):
+        res["batched_observables"] = run_batched_observables(D, args)
     if legs in ("all", "served") and not args.no_serve:
         res["served"] = run_served(args, D.sptr)
     return D, res
@@ -1165,7 +1231,7 @@ def main():
                     help="restrict the batched and at-scale rows to one precision (profiling runs)")
     ap.add_argument("--rows", default="all",
                     choices=["all", "headline", "batched", "single", "hpsi", "small", "accuracy", "converged",
-                             "served", "rk", "obs", "probe"],
+                             "served", "rk", "obs", "batch_obs", "probe"],
                     help="run one leg only (headline: the batched FP64 and mixed rows without the other legs)")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="instances of the batched rows (smaller only for profiling captures)")
