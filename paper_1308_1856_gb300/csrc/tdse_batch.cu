@@ -54,6 +54,7 @@ using namespace stencil;
 constexpr int kChunkSegs = TDSE_CHUNK_SEGS;  // 32-point row segments per chunk (stencil kernels)
 constexpr int kChunkPts = TDSE_CHUNK_PTS;    // consecutive points per chunk (elementwise kernels)
 constexpr int kCombinePts = 2;               // points per lane whose Krylov loads the combines overlap
+constexpr int kMixedCombinePts = 2;          // the same for the mixed combine, two vectors per round
 
 __device__ __forceinline__ double field_of(const BatchDev &B, int inst) {
   return B.E[(size_t)(*B.step) * (size_t)B.cap + inst];
@@ -147,32 +148,36 @@ __device__ __forceinline__ void chunk_points(const BatchInst &I, int ci, F &&f) 
   }
 }
 
-// As chunk_points, four lane-strided points at a time: the loads of all four
+// As chunk_points, NQ lane-strided points at a time: the loads of all NQ
 // (load(idx) -> V) are issued before the first op(idx, i, V), whose stores
 // the compiler could not otherwise move loads across (the arrays may alias as
 // far as it knows).  The points reach op in the same order as in chunk_points.
-template <typename Ld, typename Op>
-__device__ __forceinline__ void chunk_points_x4(const BatchInst &I, int ci, Ld &&load, Op &&op) {
+template <int NQ, typename Ld, typename Op>
+__device__ __forceinline__ void chunk_points_xn(const BatchInst &I, int ci, Ld &&load, Op &&op) {
   const unsigned N = (unsigned)I.N;
   const unsigned G = N * (unsigned)(I.L + 1);
   const unsigned base = (unsigned)ci * kChunkPts + (threadIdx.x & 31);
   const unsigned end = min(G, (unsigned)(ci + 1) * kChunkPts);
   unsigned i = base % N;
   using V = decltype(load((size_t)0));
-  for (unsigned idx = base; idx < end; idx += 128) {
-    V v[4];
-    int iq[4];
+  for (unsigned idx = base; idx < end; idx += 32 * NQ) {
+    V v[NQ];
+    int iq[NQ];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       iq[q] = (int)i;
       if (idx + 32 * q < end) v[q] = load((size_t)(idx + 32 * q));
       i += 32;
       while (i >= N) i -= N;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < NQ; ++q)
       if (idx + 32 * q < end) op((size_t)(idx + 32 * q), iq[q], v[q]);
   }
+}
+template <typename Ld, typename Op>
+__device__ __forceinline__ void chunk_points_x4(const BatchInst &I, int ci, Ld &&load, Op &&op) {
+  chunk_points_xn<4>(I, ci, load, op);
 }
 
 // The points of chunk_points in groups of Q consecutive lane-strided points:
@@ -565,23 +570,45 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     }
     __syncwarp();
     PairSum acc;
-    // kCombinePts points at a time, Krylov vector by Krylov vector
-    chunk_groups_of<kCombinePts>(I, ci, [&](const size_t (&ix)[kCombinePts], const int (&iq)[kCombinePts], int nq) {
-      float cx[kCombinePts], cy[kCombinePts];
+    // kMixedCombinePts points at a time, two Krylov vectors per round (their
+    // loads issued together); each point takes its terms in vector order
+    constexpr int Q = kMixedCombinePts;
+    chunk_groups_of<Q>(I, ci, [&](const size_t (&ix)[Q], const int (&iq)[Q], int nq) {
+      float cx[Q], cy[Q];
 #pragma unroll
-      for (int q = 0; q < kCombinePts; ++q) cx[q] = cy[q] = 0.f;
-      double2 p[kCombinePts];
+      for (int q = 0; q < Q; ++q) cx[q] = cy[q] = 0.f;
+      int jj = 1;
+      for (; jj + 1 < k; jj += 2) {
+        float2 u[Q], u2[Q];
 #pragma unroll
-      for (int q = 0; q < kCombinePts; ++q)
-        if (q < nq) p[q] = psi[ix[q]];
-      for (int jj = 1; jj < k; ++jj) {
-        float2 u[kCombinePts];
+        for (int q = 0; q < Q; ++q)
+          if (q < nq) {
+            u[q] = U1[(size_t)(jj - 1) * G + ix[q]];
+            u2[q] = U1[(size_t)jj * G + ix[q]];
+          }
+        const float2 c = wcoef[wib][jj], c2 = wcoef[wib][jj + 1];
 #pragma unroll
-        for (int q = 0; q < kCombinePts; ++q)
+        for (int q = 0; q < Q; ++q) {
+          if (q < nq) {
+            cx[q] = fmaf(c.x, u[q].x, cx[q]);
+            cx[q] = fmaf(-c.y, u[q].y, cx[q]);
+            cy[q] = fmaf(c.x, u[q].y, cy[q]);
+            cy[q] = fmaf(c.y, u[q].x, cy[q]);
+            cx[q] = fmaf(c2.x, u2[q].x, cx[q]);
+            cx[q] = fmaf(-c2.y, u2[q].y, cx[q]);
+            cy[q] = fmaf(c2.x, u2[q].y, cy[q]);
+            cy[q] = fmaf(c2.y, u2[q].x, cy[q]);
+          }
+        }
+      }
+      if (jj < k) {
+        float2 u[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
           if (q < nq) u[q] = U1[(size_t)(jj - 1) * G + ix[q]];
         const float2 c = wcoef[wib][jj];
 #pragma unroll
-        for (int q = 0; q < kCombinePts; ++q) {
+        for (int q = 0; q < Q; ++q) {
           if (q < nq) {
             cx[q] = fmaf(c.x, u[q].x, cx[q]);
             cx[q] = fmaf(-c.y, u[q].y, cx[q]);
@@ -590,8 +617,12 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
           }
         }
       }
+      double2 p[Q];      // psi after the Krylov terms: not held in registers across them
 #pragma unroll
-      for (int q = 0; q < kCombinePts; ++q) {
+      for (int q = 0; q < Q; ++q)
+        if (q < nq) p[q] = psi[ix[q]];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
         if (q < nq) {
           double ox = fma(c0.x, p[q].x, fma(-c0.y, p[q].y, (double)cx[q]));
           double oy = fma(c0.x, p[q].y, fma(c0.y, p[q].x, (double)cy[q]));
