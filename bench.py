@@ -92,12 +92,16 @@ KERNEL_FLOPS_PER_GP = {
     "rk_stage": H5_FLOPS + 8,                # + g_next and acc updates (stages 1-3)
     "lanczos_a": H5_FLOPS + 6 + 4,           # + sigma H u - c u_prev, + alpha partial
     "lanczos_b": 8,                          # z - a u, + |.|^2
+    # a whole Lanczos-12 step in one launch (tdse_persist.cu): 12 A phases,
+    # 11 B phases and the combine (11 complex terms + c_0 psi, mask, |.|^2)
+    "lanczos_persistent": 12 * (H5_FLOPS + 6 + 4) + 11 * 8 + (11 * 8 + 6 + 4),
 }
 # Algorithmic HBM bytes per grid point of the FP64 kernels (complex128 16 B,
 # diagonal table 8 B; one read of every operand and one write of every output).
 FP64_BYTES_PER_GP = {
     "apply_h": 16 + 8 + 16,                  # x, diag, y
     "taylor_stage": 16 + 16 + 8 + 16,        # v_in, psi, diag, v_out
+    "lanczos_persistent": 12 * 56 + 11 * 48 + (12 * 16 + 16),   # as the phases of the multi-launch path
     "rk_stage": 16 + 16 + 16 + 8 + 16 + 16,  # g, psi, acc_in, diag, acc_out, g_next
     "lanczos_a": 16 + 16 + 8 + 16,           # U_j, U_{j-1}, diag, z
     "lanczos_b": 16 + 16 + 16,               # z, U_j, U_{j+1}

@@ -381,6 +381,23 @@ enum { TDSE_SMALL_GRID_AUTO = 0, TDSE_SMALL_GRID_OFF = 1, TDSE_SMALL_GRID_FORCE 
 int tdse_set_small_grid_path(tdse_t *h, int mode);
 int tdse_small_grid_path_used(const tdse_t *h);
 
+/*
+ * Larger grids: every FP64 length-gauge Lanczos step of a tdse_propagate call
+ * in one cooperative launch (Appendix "Lanczos methods"), when no per-step
+ * observables are set up.  The multi-launch path issues 2 order + 1 launches
+ * per step; here one grid of 2 blocks of 512 threads per SM stays resident,
+ * separates the phases by grid-wide barriers (bounded waits) and has every
+ * block add each reduction's block partials in the multi-launch path's fixed
+ * order, so the results equal that path's bitwise.  The modes are those of
+ * tdse_set_small_grid_path: AUTO (default) takes this path above 16384
+ * points where the device allows the cooperative launch, OFF never, FORCE
+ * at any size (the small-grid path, if it applies, still comes first).
+ * tdse_persistent_path_used returns 1 if the last tdse_propagate ran on it.
+ * Errors: TDSE_ERR_ARG (unknown mode).
+ */
+int tdse_set_persistent_path(tdse_t *h, int mode);
+int tdse_persistent_path_used(const tdse_t *h);
+
 /* Wait for the handle's stream; reports pending TDSE_ERR_NONFINITE. */
 int tdse_sync(tdse_t *h);
 
@@ -419,7 +436,7 @@ long long tdse_launch_count(const tdse_t *h);
 enum {
   TDSE_K_APPLY_H = 0, TDSE_K_TAYLOR_STAGE, TDSE_K_RK_STAGE, TDSE_K_NORM, TDSE_K_LANCZOS_A,
   TDSE_K_LANCZOS_B, TDSE_K_LANCZOS_EXPM, TDSE_K_LANCZOS_COMBINE, TDSE_K_OBSERVABLES,
-  TDSE_K_DIPOLE, TDSE_K_FLUX, TDSE_K_SMALL_GRID, TDSE_K_COUNT
+  TDSE_K_DIPOLE, TDSE_K_FLUX, TDSE_K_SMALL_GRID, TDSE_K_PERSISTENT, TDSE_K_COUNT
 };
 
 /*

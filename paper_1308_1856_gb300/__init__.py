@@ -236,6 +236,15 @@ class TDSE:
     def small_grid_path_used(self) -> bool:
         return C.tdse_small_grid_path_used(self.h) == 1
 
+    def set_persistent_path(self, mode: str = "auto"):
+        """'auto' (default), 'off' or 'force': see tdse_set_persistent_path."""
+        modes = {"auto": C.TDSE_SMALL_GRID_AUTO, "off": C.TDSE_SMALL_GRID_OFF, "force": C.TDSE_SMALL_GRID_FORCE}
+        self._check(C.tdse_set_persistent_path(self.h, modes[mode]))
+
+    @property
+    def persistent_path_used(self) -> bool:
+        return C.tdse_persistent_path_used(self.h) == 1
+
     @property
     def launches(self) -> int:
         return C.tdse_launch_count(self.h)

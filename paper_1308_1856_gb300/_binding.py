@@ -104,6 +104,8 @@ SIGNATURES = {
     "tdse_lanczos_expm": (_c_int, [_c_int, _dp, _dp, _c_double, _c_int, _dp, ctypes.POINTER(_c_int)]),
     "tdse_set_small_grid_path": (_c_int, [_vp, _c_int]),
     "tdse_small_grid_path_used": (_c_int, [_vp]),
+    "tdse_set_persistent_path": (_c_int, [_vp, _c_int]),
+    "tdse_persistent_path_used": (_c_int, [_vp]),
     "tdse_launch_count": (ctypes.c_longlong, [_vp]),
     "tdse_profile": (_c_int, [_vp, _c_int]),
     "tdse_profile_read": (_c_int, [_vp, _c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -229,6 +231,8 @@ tdse_fma_throughput = _fn("tdse_fma_throughput")
 tdse_lanczos_expm = _fn("tdse_lanczos_expm")
 tdse_set_small_grid_path = _fn("tdse_set_small_grid_path")
 tdse_small_grid_path_used = _fn("tdse_small_grid_path_used")
+tdse_set_persistent_path = _fn("tdse_set_persistent_path")
+tdse_persistent_path_used = _fn("tdse_persistent_path_used")
 tdse_launch_count = _fn("tdse_launch_count")
 tdse_profile = _fn("tdse_profile")
 tdse_profile_read = _fn("tdse_profile_read")
@@ -280,4 +284,5 @@ tdse_server_profile = _fn("tdse_server_profile")
 tdse_server_profile_read = _fn("tdse_server_profile_read")
 
 KERNEL_KINDS = ["apply_h", "taylor_stage", "rk_stage", "norm", "lanczos_a", "lanczos_b",
-                "lanczos_expm", "lanczos_combine", "observables", "dipole", "flux", "small_grid"]
+                "lanczos_expm", "lanczos_combine", "observables", "dipole", "flux", "small_grid",
+                "lanczos_persistent"]

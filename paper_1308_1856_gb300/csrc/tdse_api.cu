@@ -77,6 +77,10 @@ struct tdse {
   // small grids: a whole run in one cluster launch (tdse_cluster.cu)
   int small_mode = TDSE_SMALL_GRID_AUTO;
   int small_used = 0;              // the last tdse_propagate ran on that path
+  int persist_mode = TDSE_SMALL_GRID_AUTO;   // one cooperative launch per Lanczos call (larger grids)
+  int persist_used = 0;
+  int persist_fits = -1;           // -1: not yet asked
+  char *pscratch = nullptr;        // its partial buffers and grid barrier
   SmallPlan small_plan;            // cached for (small_method, small_order)
   int small_method = -1, small_order = -1;
   double *etab = nullptr;          // per-step fields of a cluster run
@@ -271,6 +275,7 @@ void free_all(tdse *h) {
   dfree(h, h->rj);
   dfree(h, h->rinv);
   dfree(h, h->etab);
+  dfree(h, h->pscratch);
   dfree(h, h->kappa);
   dfree(h, h->mask);
   dfree(h, h->red);
@@ -555,18 +560,9 @@ int mx_lanczos_steps(tdse *h, int m, double dt, long nsteps) {
 constexpr size_t kSmallGridAutoPoints = 16384;
 
 // Run the steps on the cluster path if it applies; *done tells whether it did.
-int small_grid_steps(tdse *h, int method, int order, double dt, long nsteps, bool *done) {
-  *done = false;
-  if (h->small_mode == TDSE_SMALL_GRID_OFF || nsteps < 1 || nsteps > 0x7fffffffL || hooks_on(h) ||
-      h->opts.precision != TDSE_FP64 || h->g.gauge != 0)
-    return TDSE_OK;
-  if (h->small_mode == TDSE_SMALL_GRID_AUTO && npts(h) > kSmallGridAutoPoints) return TDSE_OK;
-  if (h->small_method != method || h->small_order != order) {
-    h->small_plan = plan_small_grid(h->g, method, order);
-    h->small_method = method;
-    h->small_order = order;
-  }
-  if (!h->small_plan.ok) return TDSE_OK;
+// The coupling at every step of a one-launch run (three per RK4 step: the
+// stage times; one per Taylor or Lanczos step: the mid-point), on the device.
+int upload_etab(tdse *h, int method, double dt, long nsteps) {
   const size_t per = (method == TDSE_RK4) ? 3 : 1;
   const size_t nE = per * (size_t)nsteps;
   if (h->etab_cap < nE) {
@@ -596,6 +592,23 @@ int small_grid_steps(tdse *h, int method, int order, double dt, long nsteps, boo
   // pageable source: the copy is staged before the call returns, so hetab may change afterwards
   TDSE_CUDA(h, cudaMemcpyAsync(h->etab, h->hetab.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, h->stream),
             "field table upload");
+  return TDSE_OK;
+}
+
+int small_grid_steps(tdse *h, int method, int order, double dt, long nsteps, bool *done) {
+  *done = false;
+  if (h->small_mode == TDSE_SMALL_GRID_OFF || nsteps < 1 || nsteps > 0x7fffffffL || hooks_on(h) ||
+      h->opts.precision != TDSE_FP64 || h->g.gauge != 0)
+    return TDSE_OK;
+  if (h->small_mode == TDSE_SMALL_GRID_AUTO && npts(h) > kSmallGridAutoPoints) return TDSE_OK;
+  if (h->small_method != method || h->small_order != order) {
+    h->small_plan = plan_small_grid(h->g, method, order);
+    h->small_method = method;
+    h->small_order = order;
+  }
+  if (!h->small_plan.ok) return TDSE_OK;
+  const int rce = upload_etab(h, method, dt, nsteps);
+  if (rce) return rce;
   TDSE_LAUNCH(h, TDSE_K_SMALL_GRID,
               launch_small_grid(h->small_plan, h->g, view(h), method, order, dt, nsteps, h->etab, h->psi, h->ls,
                                 h->red, h->status, h->stream),
@@ -656,9 +669,44 @@ int rk4_steps(tdse *h, double dt, long nsteps) {
   return TDSE_OK;
 }
 
+// FP64 length-gauge Lanczos steps without per-step observables, on grids the
+// cluster path does not take: every step of the call in one cooperative launch
+// (lanczos_persistent_kernel), bitwise the multi-launch path's result.
+int persistent_steps(tdse *h, int m, double dt, long nsteps, bool *done) {
+  *done = false;
+  if (h->persist_mode == TDSE_SMALL_GRID_OFF || nsteps < 1 || hooks_on(h) || h->opts.precision != TDSE_FP64 ||
+      h->g.gauge != 0)
+    return TDSE_OK;
+  if (h->persist_mode == TDSE_SMALL_GRID_AUTO && npts(h) <= kSmallGridAutoPoints) return TDSE_OK;
+  if (h->persist_fits < 0) h->persist_fits = lanczos_persistent_fits(h->g.stencil) ? 1 : 0;
+  if (!h->persist_fits) return TDSE_OK;
+  int rc = ensure_work(h, (size_t)(m > 1 ? m : 1));
+  if (rc) return rc;
+  if (!h->pscratch) {
+    cudaError_t e = DMALLOC(h, pscratch, lanczos_persistent_scratch_bytes());
+    if (e != cudaSuccess) {
+      h->pscratch = nullptr;
+      cudaGetLastError();
+      return fail(h, TDSE_ERR_OOM, "persistent-step scratch: " + std::string(cudaGetErrorString(e)));
+    }
+  }
+  if ((rc = upload_etab(h, TDSE_LANCZOS, dt, nsteps))) return rc;
+  if (!h->lanczos_norm_valid)
+    TDSE_LAUNCH(h, TDSE_K_NORM, launch_norm(h->g, h->psi, h->red, h->ls, h->status, h->stream), "norm");
+  TDSE_LAUNCH(h, TDSE_K_PERSISTENT,
+              launch_lanczos_persistent(h->g, view(h), m, dt, nsteps, h->etab, h->psi, h->work, h->ls, h->red,
+                                        h->pscratch, h->status, h->stream),
+              "persistent Lanczos run");
+  *done = true;
+  h->persist_used = 1;
+  return TDSE_OK;
+}
+
 int lanczos_steps(tdse *h, int m, double dt, long nsteps) {
   bool done = false;
   int rc = small_grid_steps(h, TDSE_LANCZOS, m, dt, nsteps, &done);
+  if (rc || done) return rc;
+  rc = persistent_steps(h, m, dt, nsteps, &done);
   if (rc || done) return rc;
   // work slot 0: z; slots 1..m-1: U_1..U_{m-1} (U_0 is psi itself)
   rc = ensure_work(h, (size_t)(m > 1 ? m : 1));
@@ -1132,6 +1180,7 @@ int tdse_propagate(tdse_t *h, int method, int order, double dt, long nsteps) {
   if (rc) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, TDSE_ERR_ARG, "need dt > 0 and nsteps >= 0");
   h->small_used = 0;
+  h->persist_used = 0;
   const bool mixed = h->opts.precision == TDSE_MIXED;
   if (nsteps > 0) {
     // each path keeps its own cached norm / split; work in the other one invalidates it
@@ -1594,6 +1643,17 @@ int tdse_set_small_grid_path(tdse_t *h, int mode) {
 }
 
 int tdse_small_grid_path_used(const tdse_t *h) { return h ? h->small_used : 0; }
+
+int tdse_set_persistent_path(tdse_t *h, int mode) {
+  int rc = check_usable(h);
+  if (rc) return rc;
+  if (mode != TDSE_SMALL_GRID_AUTO && mode != TDSE_SMALL_GRID_OFF && mode != TDSE_SMALL_GRID_FORCE)
+    return fail(h, TDSE_ERR_ARG, "persistent path mode must be AUTO, OFF or FORCE");
+  h->persist_mode = mode;
+  return TDSE_OK;
+}
+
+int tdse_persistent_path_used(const tdse_t *h) { return h ? h->persist_used : 0; }
 
 int tdse_sync(tdse_t *h) {
   int rc = check_usable(h);

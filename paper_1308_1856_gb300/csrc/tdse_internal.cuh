@@ -165,6 +165,12 @@ cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const d
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag = false);
 // One block per listed instance: ids[0..count) index m, dt and ls (ids NULL:
 // instances 0..count-1).
+// Every Lanczos step of a call in one cooperative launch (tdse_persist.cu).
+bool lanczos_persistent_fits(int stencil);
+size_t lanczos_persistent_scratch_bytes();
+cudaError_t launch_lanczos_persistent(const Geometry &g, const OperatorView &op, int m, double dt, long nsteps,
+                                      const double *etab, double2 *psi, double2 *work, LanczosScalars *ls,
+                                      Reduction *red, void *scratch, int *status, cudaStream_t st);
 cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt, bool imag,
                                         LanczosScalars *ls, cudaStream_t st);
 cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,

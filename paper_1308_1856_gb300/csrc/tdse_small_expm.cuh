@@ -68,7 +68,19 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // loop needs a runtime integer division; a row's 32 entries then lie in one
 // warp (its lanes), so row sums are warp shuffles.
 // imag: c = exp(-T dt) e_1 (imaginary time) instead of exp(-i T dt) e_1.
-__device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, bool imag = false) {
+// The block barrier of the body: the whole CTA of kEx threads, or (named
+// barrier 1) the first kEx threads of a larger block that runs the body in
+// those threads alone.
+struct ExBlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct ExNamedSync {
+  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"n"(kEx) : "memory"); }
+};
+
+template <typename Sync = ExBlockSync>
+__device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, bool imag = false,
+                                          Sync sync = Sync()) {
   __shared__ double al[KP], be[KP];
   __shared__ float ad[KP], bd[KP];      // FP32 diagonal and couplings of T during the QR steps
   __shared__ float Vf[KP][KP + 1];
@@ -97,7 +109,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     const unsigned bm = __ballot_sync(0xffffffffu, brk);
     if (tid == 0) s_k = bm ? __ffs(bm) : m;
   }
-  __syncthreads();
+  sync();
   const int k = s_k;
 
   // ---- FP32 eigendecomposition: implicit symmetric QR, in warp 0 ---------
@@ -118,7 +130,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     ad[tid] = (tid < k) ? (float)al[tid] : 0.f;
     bd[tid] = (tid + 1 < k) ? (float)be[tid] : 0.f;
   }
-  __syncthreads();
+  sync();
   if (warp == 0 && k > 1) {
     constexpr float eps = 1.2e-7f;
     int m = k - 1;
@@ -175,7 +187,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       __syncwarp();
     }
   }
-  __syncthreads();
+  sync();
 
   // ---- FP64 Ogita-Aishima refinement -------------------------------------
   // An FP64 warp instruction holds its SM sub-partition's FP64 pipe for the
@@ -207,7 +219,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     if (i + 1 < k) tn2 = fmaf(2.f * (float)be[i], (float)be[i], tn2);
   }
   const double tnorm = (double)sqrtf(tn2);
-  __syncthreads();
+  sync();
   for (int it = 0; it < kRefineMax; ++it) {
     // W = T X
     for (int w = tid; w < kk; w += kEx) {
@@ -217,7 +229,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       if (i + 1 < k) v = fma(be[i], Xc[i + 1][e], v);
       W[i][e] = v;
     }
-    __syncthreads();
+    sync();
     // R = I - X^T X and S = X^T T X are symmetric: item (a <= b), its dot
     // products over i = part, part + P, ..., the P parts added by shuffles.
     // lambda_a = S_aa / (1 - R_aa) with |R_aa| <~ 1e-6: 1/(1-r) = 1 + r + r^2 (+ O(1e-18)).
@@ -276,7 +288,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       wpart[warp][0] = sd2;
       wpart[warp][1] = r2;
     }
-    __syncthreads();
+    sync();
     // cluster bound delta = 2 (||S - diag(lambda)|| + ||T|| ||R||) (Frobenius
     // norms): pairs closer than delta are only orthogonalised
     float sdt = 0.f, rt = 0.f;
@@ -306,7 +318,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     }
     e2 = warp_sum_f(e2);
     if (lane == 0) wpart2[warp] = e2;
-    __syncthreads();
+    sync();
     float et = 0.f;
 #pragma unroll
     for (int q = 0; q < kEx / 32; ++q) et += wpart2[q];
@@ -323,7 +335,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       if (a < k) v0 = fma(Xc[i][a], W[a][b], v0);
       Xn[i][b] = v0 + v1;
     }
-    __syncthreads();
+    sync();
     double (*xt)[KP + 1] = Xc;
     Xc = Xn;
     Xn = xt;
@@ -346,7 +358,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     if (i + 1 < k) v = fma(be[i], Xc[i + 1][e], v);
     W[i][e] = v;
   }
-  __syncthreads();
+  sync();
   for (int w = tid; w < kk; w += kEx) {      // S into Xn
     const int a = (int)(((unsigned)w * kinv) >> 16), b = w - a * k;
     double s0 = 0.0, s1 = 0.0;
@@ -358,7 +370,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     if (i < k) s0 = fma(Xc[i][a], W[i][b], s0);
     Xn[a][b] = s0 + s1;
   }
-  __syncthreads();
+  sync();
   // half-step factors h_a = f(d_a / 2), in one warp (a transcendental costs
   // the same per warp instruction however few lanes it serves; warp 1, as
   // warp 0 sums the rows below)
@@ -372,7 +384,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
       hph[lane] = make_double2(cs, -sn);
     }
   }
-  __syncthreads();
+  sync();
   // the terms M_ab y_b, into W (re) and R (im)
   for (int w = tid; w < kk; w += kEx) {
     const int a = (int)(((unsigned)w * kinv) >> 16), b = w - a * k;
@@ -443,7 +455,7 @@ __device__ __forceinline__ void expm_body(int m, double dt, LanczosScalars *ls, 
     W[a][b] = tr;
     R[a][b] = ti;
   }
-  __syncthreads();
+  sync();
   // v = row sums (warp 0, lane a), then c = X v
   if (warp == 0) {
     if (lane < k) {

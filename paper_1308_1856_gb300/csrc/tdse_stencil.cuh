@@ -9,6 +9,11 @@ namespace tdse_dev {
 namespace stencil {
 
 __device__ __forceinline__ double2 ldg2(const double2 *p) { return __ldg(p); }
+// The operand's load: read-only (non-coherent) path, or CG: from L2, for a
+// kernel whose other blocks rewrite the operand between its phases (an SM's
+// L1 is not kept coherent with another SM's stores).
+template <bool CG>
+__device__ __forceinline__ double2 ldx(const double2 *p) { return CG ? __ldcg(p) : __ldg(p); }
 
 // Rows ahead of the current one whose lines the mixed walker asks L2 for.
 // The walk visits one row per iteration with little arithmetic, so a load
@@ -65,20 +70,20 @@ __device__ __forceinline__ StencilIn scaled(StencilIn in, double s) {
 
 // (H x) at (l, i) from the register window; 15 FP64 instructions (5-point).
 // LG = false leaves out the length-gauge coupling (the velocity gauge adds its own).
-template <int ST, bool LG = true>
+template <int ST, bool LG = true, bool CG = false>
 __device__ __forceinline__ double2 h_point(const StencilIn &in, const double2 *row, int i,
                                            double d, double2 prev, double2 cur, double2 next,
                                            double a_cur, double a_next) {
   const double2 z = make_double2(0.0, 0.0);
-  const double2 m1 = (i >= 1) ? ldg2(row + i - 1) : z;
-  const double2 p1 = (i + 1 < in.N) ? ldg2(row + i + 1) : z;
+  const double2 m1 = (i >= 1) ? ldx<CG>(row + i - 1) : z;
+  const double2 p1 = (i + 1 < in.N) ? ldx<CG>(row + i + 1) : z;
   double tx = __dmul_rn(d, cur.x);
   double ty = __dmul_rn(d, cur.y);
   tx = __fma_rn(in.c1, __dadd_rn(m1.x, p1.x), tx);
   ty = __fma_rn(in.c1, __dadd_rn(m1.y, p1.y), ty);
   if (ST == 5) {
-    const double2 m2 = (i >= 2) ? ldg2(row + i - 2) : z;
-    const double2 p2 = (i + 2 < in.N) ? ldg2(row + i + 2) : z;
+    const double2 m2 = (i >= 2) ? ldx<CG>(row + i - 2) : z;
+    const double2 p2 = (i + 2 < in.N) ? ldx<CG>(row + i + 2) : z;
     tx = __fma_rn(in.c2, __dadd_rn(m2.x, p2.x), tx);
     ty = __fma_rn(in.c2, __dadd_rn(m2.y, p2.y), ty);
   }
@@ -188,13 +193,15 @@ __device__ __forceinline__ void split2(double2 v, float2 &h, float2 &lo) {
 // VG: velocity gauge, (A/c) p_z with p_z = -i [ (d/dr - l/r) kappa_l f_{l-1}
 // + (d/dr + (l+1)/r) kappa_{l+1} f_{l+1} ] (the partial-wave form of -i d/dz;
 // the paper prints the l/r terms with the opposite signs) in place of r E kappa.
-template <int ST, int PF = 0, bool SCALED = false, bool VG = false, typename F>
+// CG: the operand's loads go to L2 (see ldx).
+template <int ST, int PF = 0, bool SCALED = false, bool VG = false, bool CG = false, typename F>
 __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, int l1, F &&f) {
+  static_assert(!(VG && CG), "the velocity gauge's first derivatives read through the read-only path");
   const int N = in.N, L = in.L;
   const double2 z = make_double2(0.0, 0.0);
   const double Er = __dmul_rn(in.E, in.rj[i]);
-  double2 prev = (l0 > 0) ? ldg2(in.x + (size_t)(l0 - 1) * N + i) : z;
-  double2 cur = ldg2(in.x + (size_t)l0 * N + i);
+  double2 prev = (l0 > 0) ? ldx<CG>(in.x + (size_t)(l0 - 1) * N + i) : z;
+  double2 cur = ldx<CG>(in.x + (size_t)l0 * N + i);
   double a_cur = __dmul_rn(in.kappa[l0], Er);
   if (PF > 0)
     for (int q = 1; q < PF && l0 + q < l1; ++q) {
@@ -207,10 +214,10 @@ __device__ __forceinline__ void walk_rows(const StencilIn &in, int i, int l0, in
       prefetch_l2(in.x + idx + (size_t)PF * N);
       prefetch_l2(in.diag + idx + (size_t)PF * N);
     }
-    const double2 next = (l < L) ? ldg2(in.x + idx + N) : z;
+    const double2 next = (l < L) ? ldx<CG>(in.x + idx + N) : z;
     const double a_next = __dmul_rn(in.kappa[l + 1], Er);
     const double d = SCALED ? __dmul_rn(in.dscale, __ldg(in.diag + idx)) : __ldg(in.diag + idx);
-    double2 t = h_point<ST, !VG>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
+    double2 t = h_point<ST, !VG, CG>(in, in.x + (size_t)l * N, i, d, prev, cur, next, a_cur, a_next);
     if (VG) {
       const double ri = __ldg(in.rinv + i);
       double wx = 0.0, wy = 0.0;
