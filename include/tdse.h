@@ -389,9 +389,11 @@ int tdse_small_grid_path_used(const tdse_t *h);
  * separates the phases by grid-wide barriers (bounded waits) and has every
  * block add each reduction's block partials in the multi-launch path's fixed
  * order, so the results equal that path's bitwise.  The modes are those of
- * tdse_set_small_grid_path: AUTO (default) takes this path above 16384
- * points where the device allows the cooperative launch, OFF never, FORCE
- * at any size (the small-grid path, if it applies, still comes first).
+ * tdse_set_small_grid_path: FORCE takes this path at any size where the
+ * device allows the cooperative launch (the small-grid path, if it applies,
+ * still comes first); AUTO (default) and OFF keep the multi-launch path,
+ * which is faster on the grids measured (its kernels read the Krylov vectors
+ * through L1; here every read of data another block wrote goes to L2).
  * tdse_persistent_path_used returns 1 if the last tdse_propagate ran on it.
  * Errors: TDSE_ERR_ARG (unknown mode).
  */

@@ -674,10 +674,13 @@ int rk4_steps(tdse *h, double dt, long nsteps) {
 // (lanczos_persistent_kernel), bitwise the multi-launch path's result.
 int persistent_steps(tdse *h, int m, double dt, long nsteps, bool *done) {
   *done = false;
-  if (h->persist_mode == TDSE_SMALL_GRID_OFF || nsteps < 1 || hooks_on(h) || h->opts.precision != TDSE_FP64 ||
+  // AUTO keeps the multi-launch path: measured on the at-scale grid, one
+  // cooperative launch per call is slower (a Lanczos-12 step 0.711 ms against
+  // 0.656 ms), its phases reading the Krylov vectors from L2 rather than L1
+  // and its 2m + 1 grid barriers costing about what the launches did
+  if (h->persist_mode != TDSE_SMALL_GRID_FORCE || nsteps < 1 || hooks_on(h) || h->opts.precision != TDSE_FP64 ||
       h->g.gauge != 0)
     return TDSE_OK;
-  if (h->persist_mode == TDSE_SMALL_GRID_AUTO && npts(h) <= kSmallGridAutoPoints) return TDSE_OK;
   if (h->persist_fits < 0) h->persist_fits = lanczos_persistent_fits(h->g.stencil) ? 1 : 0;
   if (!h->persist_fits) return TDSE_OK;
   int rc = ensure_work(h, (size_t)(m > 1 ? m : 1));

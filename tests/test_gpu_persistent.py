@@ -55,13 +55,12 @@ def test_persistent_equals_multi_launch_bitwise(N, dr, L, st, m, dt, absorber):
 def test_persistent_calls_split_and_scalars_carried():
     """3 + 1 + 4 steps on the one-launch path equal 8 steps in one call and
     8 multi-launch steps (the scalars each call leaves in the handle are
-    the multi-launch path's), and the path is taken by default above 16384
-    points."""
+    the multi-launch path's); by default the multi-launch path runs."""
     N, dr, L, st = 3000, 0.1, 7, 5
     psi = W.smooth_state(N, dr, L, seed=5)
-    a, _, ua = _run(N, dr, L, st, 12, 0.003, [3, 1, 4], "auto", psi, 250.0)
+    a, _, ua = _run(N, dr, L, st, 12, 0.003, [3, 1, 4], "force", psi, 250.0)
     b, _, _ = _run(N, dr, L, st, 12, 0.003, [8], "force", psi, 250.0)
-    c, _, uc = _run(N, dr, L, st, 12, 0.003, [8], "off", psi, 250.0)
+    c, _, uc = _run(N, dr, L, st, 12, 0.003, [8], "auto", psi, 250.0)
     assert ua == [True, True, True] and uc == [False]
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
