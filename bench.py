@@ -437,19 +437,23 @@ def dominant_roofline(D, prof, prec):
     return roofline_of(D, max(keys, key=lambda k: prof[k][0]), prof)
 
 
-def e2e_rows(D: Device, rows, steps, psi0):
+def e2e_rows(D: Device, rows, steps, psi0, warmup=2):
     """The same steps end to end through the C ABI with host buffers: every
     step copies every state in from pinned host memory, advances it, copies
-    it out and reads its observables (one untimed pass first: the first copies
-    through freshly pinned buffers pay one-off mapping costs)."""
+    it out and reads its observables.  Untimed passes first: the first copies
+    through freshly pinned buffers pay one-off mapping costs, and a batch's
+    pipelined copies size their groups by the compute / copy ratio that its
+    previous call measured (tdse_batch_propagate_io), so the second pass is
+    the first with calibrated groups."""
     torch = D.torch
     pins = []
     for r in rows:
         src = psi0 if r.kind == "single" else r.b.get_states()
         pin_in = torch.from_numpy(np.ascontiguousarray(src).view(np.float64).copy()).pin_memory()
         pins.append((pin_in, torch.empty_like(pin_in).pin_memory()))
-    for r, (pi, po) in zip(rows, pins):
-        r.e2e_step(pi, po)
+    for _ in range(warmup):
+        for r, (pi, po) in zip(rows, pins):
+            r.e2e_step(pi, po)
     D.sync()
     per_row = {}
     t0 = time.perf_counter()
@@ -461,7 +465,7 @@ def e2e_rows(D: Device, rows, steps, psi0):
     wall = time.perf_counter() - t0
     gp = sum(r.gp for r in rows) * steps
     return {"value": gp / wall, "unit": UNIT, "h2d_bytes_per_step": sum(r.e2e_bytes[0] for r in rows),
-            "d2h_bytes_per_step": sum(r.e2e_bytes[1] for r in rows), "steps": steps, "warmup": 1,
+            "d2h_bytes_per_step": sum(r.e2e_bytes[1] for r in rows), "steps": steps, "warmup": warmup,
             "ms_per_step_by_row": {k: 1e3 * v / steps for k, v in per_row.items()}}
 
 
@@ -617,7 +621,7 @@ def run_headline(D, args, ws):
         r.b.observables(0)                          # raises on Inf/NaN
         ms_all, units_all = combine_over_ranks(ms, r.gp * steps, ws, D.dev) if p == "fp64" else (ms, r.gp * steps)
         prof = profile_rows(D, [r])
-        e2e = e2e_rows(D, [r], 2, None) if not args.no_e2e else None
+        e2e = e2e_rows(D, [r], 3, None) if not args.no_e2e else None
         out[p] = {"value": units_all / (ms_all * 1e-3), "ms_per_step": ms_all / steps, "steps": steps,
                   "warmup": args.warmup, "gp_per_step": r.gp, "gpu_launches": launches,
                   "launches_per_step": launches / steps, "graph_replayed_steps": graph_steps,
