@@ -546,8 +546,39 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   });
 }
 
-// psi_new = coef_0 psi (FP64) + sum_{j>=1} coef_j U_j (FP32, added in FP64),
-// mask, split, ||psi_new||.
+// Pair ("double-float") arithmetic in FP32: a value held as h + l with
+// |l| <= ulp(h) / 2 carries about 48 bits.  Two-sum and Fast2Sum are Knuth's
+// and Dekker's error-free additions; the product keeps the exact error of
+// h_a h_b (an FMA) and the cross terms.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {   // |a| >= |b| or a = 0
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+  ph = __fmul_rn(ah, bh);
+  pl = __fmaf_rn(ah, bh, -ph);
+  pl = __fmaf_rn(ah, bl, pl);
+  pl = __fmaf_rn(al, bh, pl);
+}
+__device__ __forceinline__ void split1(double v, float &h, float &l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - (double)h);
+}
+
+// psi_new = coef_0 psi + sum_{j>=1} coef_j U_j, mask, ||psi_new||, with psi
+// held as its split (hi + lo): the coef_0 term and the sums in pair
+// arithmetic (about 48 bits), the Krylov terms in FP32 as before, and the new
+// split written directly, so the step needs no FP64 instruction per point
+// (an FP64 warp instruction holds its pipe 64 cycles; the FP64 form of this
+// kernel was FP64-pipe bound).  The FP64 state is formed from the split when
+// it is read (bt_materialize_mixed), or here too when WRITE_PSI (per-step
+// observables read it after every step).
+template <bool WRITE_PSI>
 __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     bt_combine_mixed(BatchDev B, ChunkList cl) {
   // the chunk's FP32 coefficients, converted once and kept per warp
@@ -563,6 +594,9 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     const double *mask = I.mask;
     const int k = ls->kdim;
     const double2 c0 = ls->coef[0];
+    float c0xh, c0xl, c0yh, c0yl;
+    split1(c0.x, c0xh, c0xl);
+    split1(c0.y, c0yh, c0yl);
     __syncwarp();
     if (lane < k) {
       const double2 cd = ls->coef[lane];
@@ -617,27 +651,36 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
           }
         }
       }
-      double2 p[Q];      // psi after the Krylov terms: not held in registers across them
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (q < nq) p[q] = psi[ix[q]];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         if (q < nq) {
-          double ox = fma(c0.x, p[q].x, fma(-c0.y, p[q].y, (double)cx[q]));
-          double oy = fma(c0.x, p[q].y, fma(c0.y, p[q].x, (double)cy[q]));
+          const float2 ph = hi[ix[q]], pl = lo[ix[q]];
+          // Re: c0x px - c0y py + cx;  Im: c0x py + c0y px + cy
+          float a1, a1l, a2, a2l, b1, b1l, b2, b2l;
+          pair_mul(c0xh, c0xl, ph.x, pl.x, a1, a1l);
+          pair_mul(c0yh, c0yl, ph.y, pl.y, a2, a2l);
+          pair_mul(c0xh, c0xl, ph.y, pl.y, b1, b1l);
+          pair_mul(c0yh, c0yl, ph.x, pl.x, b2, b2l);
+          float sx, ex, sx2, ex2, sy, ey, sy2, ey2;
+          two_sum(a1, -a2, sx, ex);
+          two_sum(sx, cx[q], sx2, ex2);
+          two_sum(b1, b2, sy, ey);
+          two_sum(sy, cy[q], sy2, ey2);
+          float oxh, oxl, oyh, oyl;
+          fast_two_sum(sx2, __fadd_rn(__fadd_rn(__fsub_rn(a1l, a2l), ex), ex2), oxh, oxl);
+          fast_two_sum(sy2, __fadd_rn(__fadd_rn(__fadd_rn(b1l, b2l), ey), ey2), oyh, oyl);
           if (iq[q] >= I.mask_start) {
-            const double mv = mask[iq[q]];
-            ox *= mv;
-            oy *= mv;
+            float mh, ml, t, tl;
+            split1(mask[iq[q]], mh, ml);
+            pair_mul(oxh, oxl, mh, ml, t, tl);
+            fast_two_sum(t, tl, oxh, oxl);
+            pair_mul(oyh, oyl, mh, ml, t, tl);
+            fast_two_sum(t, tl, oyh, oyl);
           }
-          const double2 o = make_double2(ox, oy);
-          psi[ix[q]] = o;
-          float2 h, lw;
-          split2(o, h, lw);
-          hi[ix[q]] = h;
-          lo[ix[q]] = lw;
-          acc.add(fmaf(h.x, h.x, h.y * h.y));
+          hi[ix[q]] = make_float2(oxh, oyh);
+          lo[ix[q]] = make_float2(oxl, oyl);
+          if (WRITE_PSI) psi[ix[q]] = make_double2((double)oxh + (double)oxl, (double)oyh + (double)oyl);
+          acc.add(fmaf(oxh, oxh, oyh * oyh));
         }
       }
     });
@@ -651,6 +694,25 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       if (!isfinite(s)) atomicOr(B.status, kStatusNonFinite);
     }
   });
+}
+
+// The FP64 state of mixed instances first .. first + count - 1 from their
+// split: psi = hi + lo (exact in FP64: the parts' mantissas do not overlap).
+// A grid-stride loop per instance: no list to upload, so it queues without
+// waiting for the stream.
+__global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
+    bt_materialize_mixed(BatchDev B, int first, int count) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int inst = first; inst < first + count; ++inst) {
+    const BatchInst I = B.inst[inst];
+    const size_t G = (size_t)I.N * (I.L + 1);
+    const float2 *hi = I.hi, *lo = I.lo;
+    double2 *psi = I.psi;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G; idx += stride) {
+      const float2 h = hi[idx], l = lo[idx];
+      psi[idx] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+  }
 }
 
 // ---- Sec. 3: imaginary time ------------------------------------------------
@@ -1015,6 +1077,7 @@ int Engine::init(int cap, int st, int prec) {
   placed.assign(cap, 0);
   norm_valid.assign(cap, 0);
   ser_count.assign(cap, 0);
+  psi_stale.assign(cap, 0);
   const bool ok = cudaMalloc(&inst, sizeof(BatchInst) * cap) == cudaSuccess &&
                   cudaMalloc(&ls, sizeof(LanczosScalars) * cap) == cudaSuccess &&
                   cudaMalloc(&ticket, sizeof(unsigned) * cap) == cudaSuccess &&
@@ -1198,6 +1261,7 @@ int Engine::place(int slot, const tdse_instance_spec &s, void *mem) {
   placed[slot] = 1;
   norm_valid[slot] = 0;
   ser_count[slot] = 0;
+  psi_stale[slot] = 0;
   return TDSE_OK;
 }
 
@@ -1316,12 +1380,15 @@ int Engine::set_state(int slot, const double *F) {
   EN_CUDA(cudaMemcpyAsync(I.psi, F, sizeof(double2) * G, cudaMemcpyHostToDevice, stream), "set state");
   EN_CUDA(cudaStreamSynchronize(stream), "sync");
   norm_valid[slot] = 0;
+  psi_stale[slot] = 0;
   return TDSE_OK;
 }
 
 int Engine::get_state(int slot, double *F) {
   if (poisoned) return TDSE_ERR_STATE;
   if (slot < 0 || slot >= capacity || !placed[slot] || !F) return fail(TDSE_ERR_ARG, "bad instance or null state");
+  int rc = materialize({slot});
+  if (rc) return rc;
   const BatchInst &I = hinst[slot];
   const size_t G = (size_t)I.N * (I.L + 1);
   EN_CUDA(cudaMemcpyAsync(F, I.psi, sizeof(double2) * G, cudaMemcpyDeviceToHost, stream), "get state");
@@ -1332,6 +1399,12 @@ int Engine::get_state(int slot, double *F) {
 int Engine::copy_states(const std::vector<int> &slots, double *F, bool to_device) {
   if (poisoned) return TDSE_ERR_STATE;
   if (!F) return fail(TDSE_ERR_ARG, "null state buffer");
+  for (int slot : slots)
+    if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+  if (!to_device) {
+    const int rc = materialize(slots);
+    if (rc) return rc;
+  }
   size_t off = 0;
   for (int slot : slots) {
     if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
@@ -1340,12 +1413,37 @@ int Engine::copy_states(const std::vector<int> &slots, double *F, bool to_device
     if (to_device) {
       EN_CUDA(cudaMemcpyAsync(I.psi, F + off, sizeof(double2) * G, cudaMemcpyHostToDevice, stream), "set states");
       norm_valid[slot] = 0;
+      psi_stale[slot] = 0;
     } else {
       EN_CUDA(cudaMemcpyAsync(F + off, I.psi, sizeof(double2) * G, cudaMemcpyDeviceToHost, stream), "get states");
     }
     off += 2 * G;
   }
   EN_CUDA(cudaStreamSynchronize(stream), "sync states");
+  return TDSE_OK;
+}
+
+int Engine::materialize(const std::vector<int> &slots) {
+  if (poisoned) return TDSE_ERR_STATE;
+  if (precision != TDSE_MIXED) return TDSE_OK;
+  std::vector<int> ids;
+  for (int s : slots)
+    if (s >= 0 && s < capacity && placed[s] && psi_stale[s]) ids.push_back(s);
+  if (ids.empty()) return TDSE_OK;
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  const BatchDev B = device_view();
+  const unsigned grid = (unsigned)(sms * sched.eblocks);
+  // one launch per run of consecutive slots
+  for (size_t q = 0; q < ids.size();) {
+    size_t r = q + 1;
+    while (r < ids.size() && ids[r] == ids[r - 1] + 1) ++r;
+    bt_materialize_mixed<<<grid, kElemThreads, 0, stream>>>(B, ids[q], (int)(r - q));
+    ++launches;
+    EN_CUDA(cudaGetLastError(), "materialize");
+    q = r;
+  }
+  for (int id : ids) psi_stale[id] = 0;
   return TDSE_OK;
 }
 
@@ -1656,7 +1754,10 @@ int Engine::enqueue_step(const BatchDev &B, const Segment &sg, int &count) {
   ++count;
   const unsigned egrid = (unsigned)(sms * sched.eblocks);
   cudaEvent_t pc = prof_begin(TDSE_K_LANCZOS_COMBINE);
-  if (precision == TDSE_MIXED) bt_combine_mixed<<<egrid, kElemThreads, 0, stream>>>(B, all);
+  if (precision == TDSE_MIXED) {
+    if (steps_tab()) bt_combine_mixed<true><<<egrid, kElemThreads, 0, stream>>>(B, all);   // per-step observables read psi
+    else bt_combine_mixed<false><<<egrid, kElemThreads, 0, stream>>>(B, all);
+  }
   else bt_combine_fp64<<<egrid, kElemThreads, 0, stream>>>(B, all, run_imag ? 0 : 1);
   prof_end(pc);
   ++count;
@@ -1821,6 +1922,9 @@ int Engine::run(const std::vector<int> &slots, const std::vector<long> &steps, b
     }
   }
   last_eager = std::move(eager);
+  if (precision == TDSE_MIXED)
+    for (size_t q = 0; q < slots.size(); ++q)
+      if (steps[q] > 0) psi_stale[slots[q]] = steps_tab() ? 0 : 1;
   for (size_t q = 0; q < slots.size() && !imag; ++q) {
     nstep[slots[q]] += steps[q];
     if (ser_cap > 0) ser_count[slots[q]] = std::min(ser_cap, ser_count[slots[q]] + (long long)steps[q]);
@@ -1895,6 +1999,10 @@ int Engine::flux_setup(bool enable, int nt, const double *cos_theta) {
     live.push_back(s);
   }
   if (live.empty()) return fail(TDSE_ERR_ARG, "no instance");
+  {
+    const int rcm = materialize(live);   // the opening flux reads the FP64 states
+    if (rcm) return rcm;
+  }
   if (sizeof(double2) * 2 * (size_t)(lmax + 1) > 48 * 1024) return fail(TDSE_ERR_ARG, "flux: lmax above 1535");
   // Y_l0(theta_k) = sqrt((2l + 1) / (4 pi)) P_l(cos theta_k), P_l by Bonnet's recurrence
   const size_t ys = (size_t)lmax + 1;
@@ -2131,6 +2239,10 @@ int Engine::autotune(const std::vector<int> &slots) {
 int Engine::observables(int slot, std::vector<double> &out) {
   if (poisoned) return TDSE_ERR_STATE;
   if (slot < 0 || slot >= capacity || !placed[slot]) return fail(TDSE_ERR_ARG, "bad instance");
+  {
+    const int rcm = materialize({slot});
+    if (rcm) return rcm;
+  }
   const tdse_instance_spec &s = spec[slot];
   const BatchInst &I = hinst[slot];
   Geometry g;
@@ -2363,6 +2475,7 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
         if (cudaMemcpyAsync(e.hinst[i].psi, F_in + off[i], bytes(i), cudaMemcpyHostToDevice, b->io_in) != cudaSuccess)
           return e.fail(TDSE_ERR_CUDA, "input copy");
         e.norm_valid[i] = 0;
+        e.psi_stale[i] = 0;
       }
       if (cudaEventRecord(b->ev[2 * g], b->io_in) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "input event");
     }
@@ -2378,6 +2491,7 @@ int tdse_batch_propagate_io(tdse_batch_t *b, const double *F_in, double *F_out, 
     if (cudaEventRecord(b->tev[2 + 2 * g], e.stream) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "timing event");
     rc = e.run(slots, std::vector<long>(slots.size(), nsteps));
     if (rc) return rc;
+    if (F_out && (rc = e.materialize(slots))) return rc;
     if (cudaEventRecord(b->tev[3 + 2 * g], e.stream) != cudaSuccess) return e.fail(TDSE_ERR_CUDA, "timing event");
     if (F_out) {
       if (cudaEventRecord(b->ev[2 * g + 1], e.stream) != cudaSuccess ||

@@ -150,6 +150,10 @@ class Engine {
   int observables(int slot, std::vector<double> &out);
   int set_state(int slot, const double *F_host);
   int get_state(int slot, double *F_host);
+  // Mixed precision: the steps keep a slot's state as its FP32 split only;
+  // form the FP64 state of the given slots where it is out of date
+  // (asynchronous, on the engine's stream).
+  int materialize(const std::vector<int> &slots);
   // The states of `slots`, back to back in one host buffer (slot order), in or
   // out with one wait at the end.
   int copy_states(const std::vector<int> &slots, double *F_host, bool to_device);
@@ -177,6 +181,7 @@ class Engine {
   std::vector<long long> nstep;   // steps taken by each slot since tstart (t = tstart + nstep * dt)
   std::vector<double> tstart;
   std::vector<char> placed, norm_valid;
+  std::vector<char> psi_stale;    // mixed: the FP64 state lags its split (formed on demand)
   long long launches = 0;
   long long graph_steps = 0;      // segment steps replayed from captured graphs
   int graph_launches_per_step = 0;
