@@ -520,8 +520,11 @@ typedef struct tdse_batch tdse_batch_t;
  * the Lanczos phase of all instances; every reduction is split into fixed
  * per-instance chunks, so an instance's results do not depend on which other
  * instances share the batch (bitwise).  All device memory is owned by the
- * batch.  Errors: TDSE_ERR_ARG (count < 1, an invalid spec, mixed stencils),
- * TDSE_ERR_OOM, TDSE_ERR_CUDA.
+ * batch.  In mixed precision the steps keep each state as two FP32 parts
+ * (about 48 bits) and the FP64 state is formed from them, exactly, whenever
+ * it is read (state and observables calls, the copies out, per-step
+ * observables).  Errors: TDSE_ERR_ARG (count < 1, an invalid spec, mixed
+ * stencils), TDSE_ERR_OOM, TDSE_ERR_CUDA.
  */
 int tdse_batch_create(const tdse_instance_spec *specs, int count, int stencil, int precision,
                       tdse_batch_t **out);
