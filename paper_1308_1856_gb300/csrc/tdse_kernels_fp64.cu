@@ -66,15 +66,16 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM) apply_h_kernel(S
 // Horner stage of the Taylor polynomial (Eq. (Taylor)):
 //   v_out = psi + (-i s) H v_in,  s = dt / k   (IMAG: psi - s H v_in, Sec. 3's
 //   imaginary-time propagation).
-// The last stage (k = 1) writes psi itself and applies the absorber mask.
-template <int ST, bool IMAG, bool VG>
+// The last stage (k = 1, FIN) writes psi itself and applies the absorber
+// mask; the other stages carry no mask code at all (a predicated-off FP64
+// instruction still takes its issue slot on the FP64 pipe).
+template <int ST, bool IMAG, bool VG, bool FIN>
 __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
-                        int mask_start, int final_stage) {
-  const int mstart = final_stage ? mask_start : in.N;
+                        int mask_start) {
   for_my_segments<ST, false, VG>(in, [&](int i, size_t idx, double2 t, double2) {
-    const bool masked = i >= mstart;
+    const bool masked = FIN && i >= mask_start;
     const double2 p = psi[idx];
     double2 o;
     if (IMAG) {
@@ -519,13 +520,16 @@ cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, doubl
                                 bool final_stage, cudaStream_t st, bool imag) {
   const StencilIn in = make_in(g, op, E, v_in);
   const unsigned grid = stencil_blocks(g);
-  const int fin = final_stage ? 1 : 0;
-  const int mstart = imag ? g.N : op.mask_start;   // imaginary time: no absorber, no field
+  const int mstart = op.mask_start;
   dispatch(g, !imag && g.gauge == 1, [&](auto stc, auto vg) {
     constexpr int ST = decltype(stc)::value;
     constexpr bool VG = decltype(vg)::value;
-    if (imag) taylor_stage_kernel<ST, true, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
-    else taylor_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart, fin);
+    if (imag)   // imaginary time: no absorber, no field
+      taylor_stage_kernel<ST, true, false, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
+    else if (final_stage)
+      taylor_stage_kernel<ST, false, VG, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
+    else
+      taylor_stage_kernel<ST, false, VG, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
   });
   return cudaGetLastError();
 }
