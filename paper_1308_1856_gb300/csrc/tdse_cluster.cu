@@ -21,9 +21,13 @@
 //     by every CTA, so that every CTA holds the same bits;
 //   - every CTA forms the small exponential of the Lanczos step itself from
 //     those identical scalars, so no broadcast is needed.
-// The per-point arithmetic is that of the multi-launch kernels
-// (tdse_kernels_fp64.cu): a Taylor or RK4 run gives bitwise the same state on
-// either path; Lanczos differs only in the association of its grid sums.
+// The per-point arithmetic of Taylor and RK4 is that of the multi-launch
+// kernels (tdse_kernels_fp64.cu), so either path gives bitwise the same state;
+// the field couplings kappa_l E r_j of a Taylor step are formed once per step
+// into a table, with the same roundings.  Lanczos applies the unscaled
+// operator and then sigma_j (the multi-launch kernels fold sigma_j into the
+// coefficients), and associates its grid sums differently: it agrees with
+// that path to rounding.
 // The only waits are cluster barriers (hardware), reached the same number of
 // times by every CTA: the control flow is uniform over the cluster.
 #include <cooperative_groups.h>
@@ -46,6 +50,11 @@ constexpr int kCT = 256;   // threads per CTA
 static_assert(kCT == kEx, "the small exponential body runs on the whole CTA");
 constexpr int kMaxCluster = 16;
 
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
+
 struct SmallDev {
   double2 *psi;
   const double *diag, *rj, *kappa, *mask;
@@ -64,6 +73,7 @@ struct Slab {
   double *diag;            // [l][jl]
   double *rj, *mask;       // [jl]
   double *kappa;           // [0, L+1]
+  double *ea;              // [0, L+1][jl]: kappa_l E r_j of the current step
   int VS, W, Wc, j0, N, L;
   int rank;
 };
@@ -80,23 +90,17 @@ __device__ __forceinline__ double2 col(const cg::cluster_group &cl, const Slab &
   return row[q];
 }
 
-// (H x) at (l, jl) with every coefficient scaled as the multi-launch walker
-// does (c1, c2 and E already multiplied by the scale; the diagonal point by
-// point when `scaled`): the FP64 operations of h_point / walk_rows in the
-// same order (length gauge).
+// (H x) at (l, jl), length gauge, given the diagonal d and the two coupling
+// coefficients a_cur (to l - 1) and a_next (to l + 1) of the point: the FP64
+// operations of the multi-launch walker (h_point / walk_rows) in its order.
 template <int ST>
-__device__ __forceinline__ double2 h_at(const cg::cluster_group &cl, const Slab &s, const double2 *x, int l,
-                                        int jl, double c1, double c2, double E, bool scaled, double dscale) {
+__device__ __forceinline__ double2 h_core(const cg::cluster_group &cl, const Slab &s, const double2 *x, int l,
+                                          int jl, double c1, double c2, double d, double a_cur, double a_next) {
   const double2 z = make_double2(0.0, 0.0);
   const double2 *row = x + l * s.W;
-  const double Er = __dmul_rn(E, s.rj[jl]);
   const double2 cur = row[jl];
   const double2 prev = (l > 0) ? row[jl - s.W] : z;
   const double2 next = (l < s.L) ? row[jl + s.W] : z;
-  const double a_cur = __dmul_rn(s.kappa[l], Er);
-  const double a_next = __dmul_rn(s.kappa[l + 1], Er);
-  const double dg = s.diag[l * s.W + jl];
-  const double d = scaled ? __dmul_rn(dscale, dg) : dg;
   const double2 m1 = col(cl, s, row, jl - 1), p1 = col(cl, s, row, jl + 1);
   double tx = __dmul_rn(d, cur.x);
   double ty = __dmul_rn(d, cur.y);
@@ -112,6 +116,37 @@ __device__ __forceinline__ double2 h_at(const cg::cluster_group &cl, const Slab 
   tx = __fma_rn(a_next, next.x, tx);
   ty = __fma_rn(a_next, next.y, ty);
   return make_double2(tx, ty);
+}
+
+// (H x) at (l, jl) in field E, every coefficient formed at the point.
+template <int ST>
+__device__ __forceinline__ double2 h_at(const cg::cluster_group &cl, const Slab &s, const double2 *x, int l,
+                                        int jl, double c1, double c2, double E) {
+  const double Er = __dmul_rn(E, s.rj[jl]);
+  const double a_cur = __dmul_rn(s.kappa[l], Er);
+  const double a_next = __dmul_rn(s.kappa[l + 1], Er);
+  return h_core<ST>(cl, s, x, l, jl, c1, c2, s.diag[l * s.W + jl], a_cur, a_next);
+}
+
+// (H x) at (l, jl) with the coupling coefficients of the step taken from the
+// table ea[l][jl] = kappa_l (E r_j), l = 0 .. L + 1 (filled by fill_coupling):
+// the same values h_at forms point by point, without its three products.
+template <int ST>
+__device__ __forceinline__ double2 h_tab(const cg::cluster_group &cl, const Slab &s, const double2 *x, int l,
+                                         int jl, double c1, double c2, const double *ea) {
+  const int idx = l * s.W + jl;
+  return h_core<ST>(cl, s, x, l, jl, c1, c2, s.diag[idx], ea[idx], ea[idx + s.W]);
+}
+
+// ea[l][jl] = kappa_l (E r_j) for l = 0 .. L + 1 and the slice's columns,
+// in h_at's order of rounding.  Called by every thread of the CTA; the caller
+// orders it against the table's readers with a CTA barrier.
+__device__ __forceinline__ void fill_coupling(const Slab &s, double E) {
+  const int n = (s.L + 2) * s.W;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int l = i / s.W, jl = i - l * s.W;
+    if (jl < s.Wc) s.ea[i] = __dmul_rn(s.kappa[l], __dmul_rn(E, s.rj[jl]));
+  }
 }
 
 // This thread's points of the slice: rows ty, ty + RP, ... and columns
@@ -189,6 +224,7 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
   s.rj = s.diag + s.VS;
   s.mask = s.rj + s.W;
   s.kappa = s.mask + s.W;
+  s.ea = s.kappa + (a.L + 2);
   auto V = [&](int k) { return s.v + (size_t)k * s.VS; };
   double2 *psi = V(0);
 
@@ -217,26 +253,37 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
 
   if constexpr (METHOD == 0) {
     // ---- Taylor polynomial in Horner form (Eq. (Taylor)) ------------------
+    // The field is that of the mid-step for every stage: the coupling table
+    // is formed once per step.  Only the last stage carries the absorber, in
+    // its own instantiation (no mask instructions in the others).
     const int P = a.order;
+    auto stage = [&](auto fin, const double2 *vin, double2 *out, double sk) {
+      for_points(s, ln, [&](int l, int jl, int idx) {
+        const double2 t = h_tab<ST>(cl, s, vin, l, jl, a.c1, a.c2, s.ea);
+        const double2 p = psi[idx];
+        double2 o = make_double2(__fma_rn(sk, t.y, p.x), __fma_rn(-sk, t.x, p.y));
+        if constexpr (decltype(fin)::value) {
+          if (s.j0 + jl >= a.mask_start) {
+            const double mv = s.mask[jl];
+            o.x = __dmul_rn(mv, o.x);
+            o.y = __dmul_rn(mv, o.y);
+          }
+        }
+        out[idx] = o;
+      });
+    };
     for (int n = 0; n < a.nsteps; ++n) {
-      const double E = a.etab[n];
+      fill_coupling(s, a.etab[n]);
+      __syncthreads();
       const double2 *vin = psi;
       for (int k = P; k >= 1; --k) {
         const bool last = (k == 1);
         double2 *out = last ? ((P == 1) ? V(1) : psi) : V(1 + ((P - k) & 1));
         const double sk = a.dt / (double)k;
-        const int mstart = last ? a.mask_start : N;
-        for_points(s, ln, [&](int l, int jl, int idx) {
-          const double2 t = h_at<ST>(cl, s, vin, l, jl, a.c1, a.c2, E, false, 1.0);
-          const double2 p = psi[idx];
-          double2 o = make_double2(__fma_rn(sk, t.y, p.x), __fma_rn(-sk, t.x, p.y));
-          if (s.j0 + jl >= mstart) {
-            const double mv = s.mask[jl];
-            o.x = __dmul_rn(mv, o.x);
-            o.y = __dmul_rn(mv, o.y);
-          }
-          out[idx] = o;
-        });
+        if (last)
+          stage(BoolC<true>{}, vin, out, sk);
+        else
+          stage(BoolC<false>{}, vin, out, sk);
         cl.sync();
         vin = out;
       }
@@ -259,7 +306,7 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
         const double ca = a.dt * an[st], cb = a.dt * bw[st];
         const double2 *accin = (st == 0) ? psi : acc;
         for_points(s, ln, [&](int l, int jl, int idx) {
-          const double2 t = h_at<ST>(cl, s, gin[st], l, jl, a.c1, a.c2, Es[st], false, 1.0);
+          const double2 t = h_at<ST>(cl, s, gin[st], l, jl, a.c1, a.c2, Es[st]);
           const double2 ai = accin[idx];
           if (st < 3) {
             const double2 p = psi[idx];
@@ -295,22 +342,30 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
       __syncthreads();
     }
     for (int n = 0; n < a.nsteps; ++n) {
-      const double E = a.etab[n];
+      // the step's coupling table; its last readers (the previous step's
+      // final iteration) are behind the cluster barriers of its sums
+      fill_coupling(s, a.etab[n]);
+      __syncthreads();
       for (int j = 0; j < m; ++j) {
         // z = sigma_j H U_j - ratio_j U_{j-1};  alpha_j = sigma_j Re <U_j, z>
+        // (H U_j from the unscaled operator and the step's table, then
+        // scaled by sigma_j: fewer FP64 instructions per point than scaling
+        // every coefficient)
         const double sig = s_ls.sigma[j];
         const double cprev = (j > 0) ? s_ls.ratio[j] : 0.0;
-        const double sc1 = __dmul_rn(sig, a.c1), sc2 = __dmul_rn(sig, a.c2), sE = __dmul_rn(sig, E);
         const double2 *u = U(j);
         const double2 *up = (j > 0) ? U(j - 1) : nullptr;
         double acc = 0.0;
         for_points(s, ln, [&](int l, int jl, int idx) {
-          const double2 t = h_at<ST>(cl, s, u, l, jl, sc1, sc2, sE, true, sig);
-          double2 o = t;
+          const double2 t = h_tab<ST>(cl, s, u, l, jl, a.c1, a.c2, s.ea);
+          double2 o;
           if (j > 0) {
             const double2 pv = up[idx];
-            o.x = __fma_rn(-cprev, pv.x, t.x);
-            o.y = __fma_rn(-cprev, pv.y, t.y);
+            o.x = __fma_rn(sig, t.x, __dmul_rn(-cprev, pv.x));
+            o.y = __fma_rn(sig, t.y, __dmul_rn(-cprev, pv.y));
+          } else {
+            o.x = __dmul_rn(sig, t.x);
+            o.y = __dmul_rn(sig, t.y);
           }
           z[idx] = o;
           const double2 uc = u[idx];
@@ -486,7 +541,8 @@ SmallPlan plan_small_grid(const Geometry &g, int method, int order) {
     if (W < 2) W = 2;
     const int C = (g.N + W - 1) / W;
     const size_t VS = (size_t)(g.L + 1) * W;
-    size_t bytes = sizeof(double2) * nv * VS + sizeof(double) * (VS + 2 * (size_t)W + (size_t)g.L + 2);
+    size_t bytes = sizeof(double2) * nv * VS +
+                   sizeof(double) * (VS + 2 * (size_t)W + (size_t)g.L + 2 + (size_t)(g.L + 2) * W);
     bytes = (bytes + 15) & ~(size_t)15;
     const bool ok = (g.stencil == 5) ? fits_m<5>(method, C, bytes) : fits_m<3>(method, C, bytes);
     if (ok) {
