@@ -43,7 +43,6 @@ namespace tdse_dev {
 
 namespace {
 
-using common::block_sum;
 using common::warp_sum;
 
 constexpr int kCT = 256;   // threads per CTA
@@ -163,29 +162,55 @@ __device__ __forceinline__ void for_points(const Slab &s, const Lanes &ln, F &&f
     for (int jl = ln.tx; jl < s.Wc; jl += ln.TW) f(l, jl, l * s.W + jl);
 }
 
-// Sum over the cluster, the same bits in every CTA.  Each CTA publishes its
-// block sum in one of two slots (alternating, so a slot is rewritten only
-// after a later barrier, when every CTA has read it), then warp 0 adds the
-// C slots in a fixed shuffle order.
+// Sum over the cluster, the same bits in every CTA.  Every warp publishes its
+// shuffle-tree sum in one of two slot sets (alternating, so a set is
+// rewritten only after a later cluster barrier, when every CTA has read it);
+// after the cluster barrier warp 0 of every CTA adds the C x 8 warp sums in
+// one fixed order (lane t: the sums t, t + 32, t + 64, t + 96 in pairs, then
+// a shuffle tree), and thread 0 hands the total to `fin`, whose results the
+// closing CTA barrier publishes.  Each FP64 instruction of this dependent
+// chain holds the narrow FP64 pipe for a full pass, so the chain is kept
+// short: 12 additions and one CTA barrier besides the cluster barrier.
+constexpr int kWarps = kCT / 32;
+static_assert(kMaxCluster * kWarps <= 128, "four warp sums per lane of warp 0");
 struct ClusterSum {
-  double *slot;    // [2]
-  double *bcast;
-  double *sh;      // block_sum scratch
+  double *slot;    // [2][kWarps]
   int par;
 };
 
-__device__ __forceinline__ double cluster_sum(const cg::cluster_group &cl, ClusterSum &cs, double v, int C) {
-  const double b = block_sum(v, cs.sh);
-  if (threadIdx.x == 0) cs.slot[cs.par] = b;
+template <typename Fin>
+__device__ __forceinline__ void cluster_sum(const cg::cluster_group &cl, ClusterSum &cs, double v, int C,
+                                            Fin &&fin) {
+  const int lane = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
+  double *set = cs.slot + cs.par * kWarps;
+  v = warp_sum(v);
+  if (lane == 0) set[w] = v;
   cl.sync();
-  if (threadIdx.x < 32) {
-    double p = ((int)threadIdx.x < C) ? *cl.map_shared_rank(cs.slot + cs.par, (int)threadIdx.x) : 0.0;
-    p = warp_sum(p);
-    if (threadIdx.x == 0) *cs.bcast = p;
+  if (w == 0) {
+    double p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;   // warp i % kWarps of CTA i / kWarps
+      p[q] = (i < C * kWarps) ? *cl.map_shared_rank(set + (i % kWarps), i / kWarps) : 0.0;
+    }
+    const double t = warp_sum(__dadd_rn(__dadd_rn(p[0], p[1]), __dadd_rn(p[2], p[3])));
+    if (lane == 0) fin(t);
   }
   __syncthreads();
   cs.par ^= 1;
-  return *cs.bcast;
+}
+
+// ||x|| and 1 / ||x|| from ||x||^2 with one reciprocal square root and one
+// product (about half the dependent FP64 instructions of a square root and a
+// division); 0 gives (0, 0), Inf or NaN gives (sqrt, 0).
+__device__ __forceinline__ void norm_and_inverse(double s2, double &nrm, double &inv) {
+  if (s2 > 0.0 && s2 <= 1.7976931348623157e308) {
+    inv = rsqrt(s2);
+    nrm = __dmul_rn(s2, inv);
+  } else {
+    nrm = sqrt(s2);
+    inv = 0.0;
+  }
 }
 
 // Sum of |x|^2 over this thread's points, in the order of the Lanczos combine.
@@ -203,9 +228,7 @@ template <int ST, int METHOD>
 __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
   const cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  __shared__ double s_red[kCT / 32 + 1];
-  __shared__ double s_slot[2];
-  __shared__ double s_bcast;
+  __shared__ double s_slot[2 * kWarps];
   __shared__ LanczosScalars s_ls;
   __shared__ int s_bad;
 
@@ -233,7 +256,7 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
   ln.RP = kCT / ln.TW;
   ln.tx = (int)threadIdx.x % ln.TW;
   ln.ty = (int)threadIdx.x / ln.TW;
-  ClusterSum cs{s_slot, &s_bcast, s_red, 0};
+  ClusterSum cs{s_slot, 0};
   const int N = a.N;
 
   // ---- this CTA's slice of psi and of the tables --------------------------
@@ -331,16 +354,10 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
     const int m = a.order;
     double2 *z = V(1);
     auto U = [&](int j) { return j == 0 ? psi : V(1 + j); };
-    {
-      const double s2 = cluster_sum(cl, cs, norm_acc(s, ln, psi), C);
-      if (threadIdx.x == 0) {
-        const double nrm = sqrt(s2);
-        s_ls.psinorm = nrm;
-        s_ls.sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-        if (!isfinite(s2)) s_bad = 1;
-      }
-      __syncthreads();
-    }
+    cluster_sum(cl, cs, norm_acc(s, ln, psi), C, [&](double s2) {
+      norm_and_inverse(s2, s_ls.psinorm, s_ls.sigma[0]);
+      if (!isfinite(s2)) s_bad = 1;
+    });
     for (int n = 0; n < a.nsteps; ++n) {
       // the step's coupling table; its last readers (the previous step's
       // final iteration) are behind the cluster barriers of its sums
@@ -372,12 +389,10 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
           acc = __fma_rn(uc.x, o.x, acc);
           acc = __fma_rn(uc.y, o.y, acc);
         });
-        const double sa = cluster_sum(cl, cs, acc, C);
-        if (threadIdx.x == 0) {
+        cluster_sum(cl, cs, acc, C, [&](double sa) {
           s_ls.alpha[j] = sa * sig;
           s_ls.acoef[j] = -(sa * sig) * sig;
-        }
-        __syncthreads();
+        });
         if (j + 1 < m) {
           // U_{j+1} = z - alpha_j sigma_j U_j;  beta_j = ||U_{j+1}||
           const double c = s_ls.acoef[j];
@@ -390,15 +405,13 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
             acc0 = __fma_rn(o.x, o.x, acc0);
             acc1 = __fma_rn(o.y, o.y, acc1);
           });
-          const double sb = cluster_sum(cl, cs, acc0 + acc1, C);
-          if (threadIdx.x == 0) {
-            const double beta = sqrt(sb);
+          cluster_sum(cl, cs, acc0 + acc1, C, [&](double sb) {
+            double beta, sn;
+            norm_and_inverse(sb, beta, sn);
             s_ls.beta[j] = beta;
-            const double sn = (beta > 0.0) ? 1.0 / beta : 0.0;
             s_ls.sigma[j + 1] = sn;
             s_ls.ratio[j + 1] = (sn > 0.0) ? s_ls.sigma[j] * beta : 0.0;
-          }
-          __syncthreads();
+          });
         }
       }
       // c = exp(-i T dt) e_1, formed by every CTA from the same scalars
@@ -429,15 +442,11 @@ __global__ void __launch_bounds__(kCT, 1) small_grid_kernel(SmallDev a) {
         acc = __fma_rn(ox, ox, acc);
         acc = __fma_rn(oy, oy, acc);
       });
-      const double s2 = cluster_sum(cl, cs, acc, C);
-      if (threadIdx.x == 0) {
-        const double nrm = sqrt(s2);
-        s_ls.psinorm = nrm;
-        s_ls.sigma[0] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      cluster_sum(cl, cs, acc, C, [&](double s2) {
+        norm_and_inverse(s2, s_ls.psinorm, s_ls.sigma[0]);
         if (!isfinite(s2)) s_bad = 1;
         if (s.rank == 0) a.red->normsq = s2;
-      }
-      __syncthreads();
+      });
     }
     if (s.rank == 0 && threadIdx.x == 0) {
       a.ls->psinorm = s_ls.psinorm;
