@@ -24,9 +24,14 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   if ((tid & 31) == 0) sh[tid >> 5] = v;
   __syncthreads();
   if (tid < 32) {
-    double s = (tid < (nthreads >> 5)) ? sh[tid] : 0.0;
-    s = warp_sum(s);
-    if (tid == 0) sh[nthreads >> 5] = s;
+    // the tree of warp_sum over the nw warp sums, without the levels whose
+    // partner lanes hold only zeros (adding them changes no value)
+    const int nw = nthreads >> 5;
+    double s = (tid < nw) ? sh[tid] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      if (o < nw) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) sh[nw] = s;
   }
   __syncthreads();
   const double r = sh[nthreads >> 5];

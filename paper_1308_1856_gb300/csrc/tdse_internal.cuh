@@ -217,4 +217,34 @@ cudaError_t launch_observables(const Geometry &g, const OperatorView &op, const 
                                unsigned *ticket, double *out, cudaStream_t st);
 int observables_blocks(const Geometry &g);
 
+// ---- programmatic dependent launch -------------------------------------------
+// The single-instance step is a chain of dependent kernels on one stream.  A
+// kernel of the chain is launched with programmatic stream serialization
+// (launch_pdl): the hardware may start its blocks while the kernel before it
+// is still in its tail (the last block's grid reduction), which hides the
+// launch and the block ramp.  Every such kernel calls pdl_wait() before its
+// first access to device memory, which returns once the previous kernel has
+// completed and its writes are visible (for a kernel launched without the
+// attribute it returns at once); it calls pdl_trigger() when its main loop is
+// done, which lets the next kernel launch.  The trigger always follows the
+// wait, so at most two kernels of the chain are resident at a time.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 }  // namespace tdse_dev

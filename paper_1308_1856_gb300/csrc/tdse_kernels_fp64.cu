@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     taylor_stage_kernel(StencilIn in, double s, const double2 *__restrict__ psi,
                         double2 *__restrict__ out, const double *__restrict__ mask,
                         int mask_start) {
+  pdl_wait();
   for_my_segments<ST, false, VG>(in, [&](int i, size_t idx, double2 t, double2) {
     const bool masked = FIN && i >= mask_start;
     const double2 p = psi[idx];
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     if (masked) { const double mv = mask[i]; o.x = __dmul_rn(mv, o.x); o.y = __dmul_rn(mv, o.y); }
     out[idx] = o;
   });
+  pdl_trigger();
 }
 
 // Stage `stage` (1..4) of classic RK4 (Eq. (RKDeriv)) with k = -i H(t_n + c dt) g:
@@ -102,6 +104,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
                     double2 *__restrict__ psi_out, const double *__restrict__ mask,
                     int mask_start) {
   const int mstart = (stage == 4) ? mask_start : in.N;
+  pdl_wait();
   for_my_segments<ST, false, VG>(in, [&](int i, size_t idx, double2 t, double2) {
     const double2 a = acc_in[idx];
     // c k with k = -i t:  (c t.y, -c t.x);  with k = -t:  (-c t.x, -c t.y)
@@ -119,6 +122,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       psi_out[idx] = o;
     }
   });
+  pdl_trigger();
 }
 
 // Stage a.stage of a general explicit Runge-Kutta method (appendix
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
   constexpr bool FSAL = MODE == 2;
   __shared__ double sh[kBlockJ / 32 + 1];
   double acc = 0.0;
+  pdl_wait();
   for_my_segments<ST, false, VG>(in, [&](int r, size_t idx, double2 t, double2 u) {
     const double2 ki = make_double2(t.y, -t.x);   // -i (tx + i ty)
     double2 kj[NK > 1 ? NK - 1 : 1];
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       a.psi_out[idx] = o;
     }
   });
+  pdl_trigger();
   if (LAST && publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -195,6 +201,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     lanczos_a_kernel(StencilIn in, int j, const double2 *__restrict__ uprev,
                      double2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kBlockJ / 32 + 1];
+  pdl_wait();
   const double sig = ls->sigma[j];
   const double cprev = (j > 0) ? ls->ratio[j] : 0.0;
   double acc = 0.0;
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     acc = __fma_rn(u.x, o.x, acc);
     acc = __fma_rn(u.y, o.y, acc);
   });
+  pdl_trigger();
   if (publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -244,6 +252,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     lanczos_b_kernel(size_t G, int j, const double2 *__restrict__ z, const double2 *__restrict__ u,
                      double2 *__restrict__ unext, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kElemThreads / 32 + 1];
+  pdl_wait();
   const double c = ls->acoef[j];
   double acc0 = 0.0, acc1 = 0.0;
   const int lane = threadIdx.x & 31;
@@ -269,6 +278,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       }
     }
   }
+  pdl_trigger();
   if (publish_block_partial(acc0 + acc1, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -287,6 +297,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     norm_kernel(size_t G, const double2 *__restrict__ x, Reduction *red, LanczosScalars *ls,
                 int *status) {
   __shared__ double sh[kElemThreads / 32 + 1];
+  pdl_wait();
   double acc0 = 0.0, acc1 = 0.0;
   const int lane = threadIdx.x & 31;
   long long g0, g1;
@@ -304,6 +315,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       acc1 = __fma_rn(v[r].y, v[r].y, acc1);
     }
   }
+  pdl_trigger();
   if (publish_block_partial(acc0 + acc1, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -343,6 +355,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   __shared__ double sh[kElemThreads / 32 + 1];
   __shared__ double2 coef[kMaxKrylov];
   __shared__ int s_k;
+  pdl_wait();
   if (threadIdx.x < kMaxKrylov) coef[threadIdx.x] = ls->coef[threadIdx.x];
   if (threadIdx.x == 0) s_k = ls->kdim;
   __syncthreads();
@@ -370,6 +383,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     acc = __fma_rn(ox, ox, acc);
     acc = __fma_rn(oy, oy, acc);
   });
+  pdl_trigger();
   if (publish_block_partial(acc, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
     if (threadIdx.x == 0) {
@@ -521,17 +535,18 @@ cudaError_t launch_taylor_stage(const Geometry &g, const OperatorView &op, doubl
   const StencilIn in = make_in(g, op, E, v_in);
   const unsigned grid = stencil_blocks(g);
   const int mstart = op.mask_start;
+  cudaError_t e = cudaSuccess;
   dispatch(g, !imag && g.gauge == 1, [&](auto stc, auto vg) {
     constexpr int ST = decltype(stc)::value;
     constexpr bool VG = decltype(vg)::value;
     if (imag)   // imaginary time: no absorber, no field
-      taylor_stage_kernel<ST, true, false, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
+      e = launch_pdl(taylor_stage_kernel<ST, true, false, false>, grid, kBlockJ, 0, st, in, s, psi, v_out, op.mask, mstart);
     else if (final_stage)
-      taylor_stage_kernel<ST, false, VG, true><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
+      e = launch_pdl(taylor_stage_kernel<ST, false, VG, true>, grid, kBlockJ, 0, st, in, s, psi, v_out, op.mask, mstart);
     else
-      taylor_stage_kernel<ST, false, VG, false><<<grid, kBlockJ, 0, st>>>(in, s, psi, v_out, op.mask, mstart);
+      e = launch_pdl(taylor_stage_kernel<ST, false, VG, false>, grid, kBlockJ, 0, st, in, s, psi, v_out, op.mask, mstart);
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E, int stage,
@@ -545,15 +560,18 @@ cudaError_t launch_rk_stage(const Geometry &g, const OperatorView &op, double E,
   const unsigned grid = stencil_blocks(g);
   const double ca = dt * a_next[stage - 1], cb = dt * b[stage - 1];
   const int mstart = imag ? g.N : op.mask_start;
+  cudaError_t e = cudaSuccess;
   dispatch(g, !imag && g.gauge == 1, [&](auto stc, auto vg) {
     constexpr int ST = decltype(stc)::value;
     constexpr bool VG = decltype(vg)::value;
     if (imag)
-      rk_stage_kernel<ST, true, false><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+      e = launch_pdl(rk_stage_kernel<ST, true, false>, grid, kBlockJ, 0, st, in, stage, ca, cb, psi, acc_in, acc_out,
+                     g_next, psi_out, op.mask, mstart);
     else
-      rk_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, stage, ca, cb, psi, acc_in, acc_out, g_next, psi_out, op.mask, mstart);
+      e = launch_pdl(rk_stage_kernel<ST, false, VG>, grid, kBlockJ, 0, st, in, stage, ca, cb, psi, acc_in, acc_out,
+                     g_next, psi_out, op.mask, mstart);
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, double E,
@@ -564,6 +582,7 @@ cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, d
   const unsigned grid = stencil_blocks(g);
   const double S = (double)g.N * (double)(g.L + 1);
   const int mode = a.last ? (a.fsal ? 2 : 1) : 0;
+  cudaError_t e = cudaSuccess;
   if (!a.last && a.stage == kRkMaxStages - 1) return cudaErrorInvalidValue;   // no stage after the last
   if (a.fsal && (!a.last || a.stage == 0)) return cudaErrorInvalidValue;
   dispatch(g, g.gauge == 1, [&](auto stc, auto vg) {
@@ -572,13 +591,16 @@ cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, d
     auto go = [&](auto nk) {
       constexpr int NK = decltype(nk)::value;
       if (mode == 1)
-        rk_general_stage_kernel<ST, VG, NK, 1><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+        e = launch_pdl(rk_general_stage_kernel<ST, VG, NK, 1>, grid, kBlockJ, 0, st, in, a, psi, op.mask,
+                       op.mask_start, red, S);
       else if constexpr (NK > 1)
         if (mode == 2)
-          rk_general_stage_kernel<ST, VG, NK, 2><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+          e = launch_pdl(rk_general_stage_kernel<ST, VG, NK, 2>, grid, kBlockJ, 0, st, in, a, psi, op.mask,
+                         op.mask_start, red, S);
       if constexpr (NK < kRkMaxStages)
         if (mode == 0)
-          rk_general_stage_kernel<ST, VG, NK, 0><<<grid, kBlockJ, 0, st>>>(in, a, psi, op.mask, op.mask_start, red, S);
+          e = launch_pdl(rk_general_stage_kernel<ST, VG, NK, 0>, grid, kBlockJ, 0, st, in, a, psi, op.mask,
+                         op.mask_start, red, S);
     };
     switch (a.stage + 1) {
       case 1: go(IC<1>{}); break;
@@ -590,7 +612,7 @@ cudaError_t launch_rk_general_stage(const Geometry &g, const OperatorView &op, d
       default: go(IC<7>{}); break;
     }
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_imag_begin(const Reduction *red, double dr, double *imag_dev, cudaStream_t st) {
@@ -608,8 +630,8 @@ cudaError_t launch_imag_normalize(const Geometry &g, double2 *psi, const Reducti
 cudaError_t launch_norm(const Geometry &g, const double2 *x, Reduction *red,
                         LanczosScalars *ls, int *status, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  norm_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, x, red, ls, status);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(norm_kernel, elem_blocks(g), kElemThreads, 0, st, G, x, red, ls, status);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E, int j,
@@ -617,17 +639,19 @@ cudaError_t launch_lanczos_a(const Geometry &g, const OperatorView &op, double E
                              Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const StencilIn in = make_in(g, op, E, u);
   const unsigned grid = stencil_blocks(g);
+  cudaError_t e = cudaSuccess;
   dispatch(g, g.gauge == 1, [&](auto stc, auto vg) {
-    lanczos_a_kernel<decltype(stc)::value, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(in, j, uprev, z, red, ls);
+    e = launch_pdl(lanczos_a_kernel<decltype(stc)::value, decltype(vg)::value>, grid, kBlockJ, 0, st, in, j, uprev,
+                   z, red, ls);
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_b(const Geometry &g, int j, const double2 *z, const double2 *u,
                              double2 *unext, Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  lanczos_b_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, unext, red, ls);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(lanczos_b_kernel, elem_blocks(g), kElemThreads, 0, st, G, j, z, u, unext, red, ls);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, int m,
@@ -636,9 +660,9 @@ cudaError_t launch_lanczos_combine(const Geometry &g, const OperatorView &op, in
                                    cudaStream_t st) {
   (void)m;
   const size_t G = (size_t)g.N * (g.L + 1);
-  lanczos_combine_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(
-      G, g.N, psi, work, stride, op.mask, op.mask_start, red, ls, status);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(lanczos_combine_kernel, elem_blocks(g), kElemThreads, 0, st, G, g.N, psi, work,
+                                   stride, op.mask, op.mask_start, red, ls, status);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int observables_blocks(const Geometry &g) {

@@ -7,7 +7,12 @@
 
 namespace tdse_dev {
 
+// The single-instance step's kernel chain launches this one with programmatic
+// serialization (launch_pdl): it waits for the Lanczos iterations, then lets
+// the combine's blocks launch at once (they wait for it in turn).
 __global__ void __launch_bounds__(kEx) lanczos_expm_kernel(int m, double dt, LanczosScalars *ls, int imag) {
+  pdl_wait();
+  pdl_trigger();
   expm_body(m, dt, ls, imag != 0);
 }
 
@@ -20,8 +25,12 @@ __global__ void __launch_bounds__(kEx)
 }
 
 cudaError_t launch_lanczos_expm(int m, double dt, LanczosScalars *ls, cudaStream_t st, bool imag) {
-  lanczos_expm_kernel<<<1, kEx, 0, st>>>(m, dt, ls, imag ? 1 : 0);
-  return cudaGetLastError();
+  if (!st) {   // the legacy default stream: an ordinary launch
+    lanczos_expm_kernel<<<1, kEx, 0, st>>>(m, dt, ls, imag ? 1 : 0);
+    return cudaGetLastError();
+  }
+  const cudaError_t e = launch_pdl(lanczos_expm_kernel, 1, kEx, 0, st, m, dt, ls, imag ? 1 : 0);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_expm_batched(int count, const int *ids, const int *m, const double *dt, bool imag,
