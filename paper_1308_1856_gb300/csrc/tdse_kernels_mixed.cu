@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
     mx_split_kernel(size_t G, const double2 *__restrict__ psi, float2 *__restrict__ hi,
                     float2 *__restrict__ lo, Reduction *red, LanczosScalars *ls, int *status) {
   __shared__ double sh[kElemThreads / 32 + 1];
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   long long g0, g1;
   warp_range((long long)((G + 31) >> 5), g0, g1);
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       acc.add(fmaf(h.x, h.x, h.y * h.y));
     }
   }
+  pdl_trigger();
   const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
                         const float2 *__restrict__ prev_hi, const float2 *__restrict__ prev_lo,
                         float2 *__restrict__ z, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kBlockJ / 32 + 1];
+  pdl_wait();
   const double sigd = ls->sigma[j];
   const float sig = (float)sigd;
   const float cprev = (j > 0) ? (float)ls->ratio[j] : 0.f;
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     z[idx] = o;
     acc.add(fmaf(u.x, o.x, u.y * o.y));
   });
+  pdl_trigger();
   const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
                         const float2 *__restrict__ u_hi, const float2 *__restrict__ u_lo,
                         float2 *__restrict__ unext, Reduction *red, LanczosScalars *ls) {
   __shared__ double sh[kElemThreads / 32 + 1];
+  pdl_wait();
   const float c = (float)ls->acoef[j];
   const int lane = threadIdx.x & 31;
   long long g0, g1;
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       acc.add(fmaf(o.x, o.x, o.y * o.y));
     }
   }
+  pdl_trigger();
   const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
   __shared__ float2 coef[kMaxKrylov];
   __shared__ double2 coef0;
   __shared__ int s_k;
+  pdl_wait();
   if (threadIdx.x < kMaxKrylov) {
     const double2 c = ls->coef[threadIdx.x];
     coef[threadIdx.x] = make_float2((float)c.x, (float)c.y);
@@ -263,6 +270,7 @@ __global__ void __launch_bounds__(kElemThreads, kElemBlocksPerSM)
       acc.add(fmaf(h.x, h.x, h.y * h.y));
     }
   }
+  pdl_trigger();
   const double accd = acc.value();
   if (publish_block_partial(accd, red, sh)) {
     const double s = reduce_partials(red, gridDim.x, sh);
@@ -284,6 +292,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     mx_taylor_stage_kernel(MixedIn in, float s, float2 *__restrict__ w_out, int final_stage,
                            double2 *psi, float2 *hi_out, float2 *lo_out,
                            const double *__restrict__ mask, int mask_start) {
+  pdl_wait();
   mixed_segments<ST, true, HAS_W, VG>(in, [&](int i, size_t idx, float2 t, float2) {
     const float2 w = make_float2(s * t.y, -s * t.x);   // (-i s)(tx + i ty)
     if (!final_stage) {
@@ -304,6 +313,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       lo_out[idx] = l;
     }
   });
+  pdl_trigger();
 }
 
 // RK4 stage `stage` (1..4) with k_s = -i H(t_s)(psi + (dt a_s) k_{s-1}):
@@ -315,6 +325,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
     mx_rk_stage_kernel(MixedIn in, int stage, float b, double dtd, float2 *__restrict__ k_out,
                        float2 *acc_hi, float2 *acc_lo, double2 *psi, float2 *hi_out,
                        float2 *lo_out, const double *__restrict__ mask, int mask_start) {
+  pdl_wait();
   mixed_segments<ST, true, HAS_K, VG>(in, [&](int i, size_t idx, float2 t, float2) {
     const float2 kv = make_float2(t.y, -t.x);          // -i H g
     const float2 x = make_float2(b * kv.x, b * kv.y);
@@ -351,6 +362,7 @@ __global__ void __launch_bounds__(kBlockJ, kStencilBlocksPerSM)
       lo_out[idx] = l;
     }
   });
+  pdl_trigger();
 }
 
 MixedIn make_mixed(const Geometry &g, const MixedView &mv, float E, const float2 *hi,
@@ -400,8 +412,8 @@ inline unsigned elem_blocks(const Geometry &g) { return (unsigned)(g.sms * kElem
 cudaError_t launch_mx_split(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo,
                             Reduction *red, LanczosScalars *ls, int *status, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  mx_split_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(G, psi, hi, lo, red, ls, status);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(mx_split_kernel, elem_blocks(g), kElemThreads, 0, st, G, psi, hi, lo, red, ls, status);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_mx_split_plain(const Geometry &g, const double2 *psi, float2 *hi, float2 *lo, cudaStream_t st) {
@@ -428,11 +440,12 @@ cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E
                                 const float2 *uprev, float2 *z, Reduction *red,
                                 LanczosScalars *ls, cudaStream_t st) {
   const unsigned grid = stencil_blocks(g);
+  cudaError_t e = cudaSuccess;
   if (j == 0) {
     const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, nullptr, 0.f);
     dispatch(g, [&](auto stc, auto vg) {
-      mx_lanczos_a_kernel<decltype(stc)::value, true, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(
-          in, j, nullptr, nullptr, nullptr, z, red, ls);
+      e = launch_pdl(mx_lanczos_a_kernel<decltype(stc)::value, true, decltype(vg)::value>, grid, kBlockJ, 0, st, in, j,
+                     nullptr, nullptr, nullptr, z, red, ls);
     });
   } else {
     MixedIn in = make_mixed(g, mv, (float)E, nullptr, nullptr, u, 1.f);
@@ -443,22 +456,21 @@ cudaError_t launch_mx_lanczos_a(const Geometry &g, const MixedView &mv, double E
       in.pf1 = lo;
     }
     dispatch(g, [&](auto stc, auto vg) {
-      mx_lanczos_a_kernel<decltype(stc)::value, false, decltype(vg)::value><<<grid, kBlockJ, 0, st>>>(
-          in, j, uprev, hi, lo, z, red, ls);
+      e = launch_pdl(mx_lanczos_a_kernel<decltype(stc)::value, false, decltype(vg)::value>, grid, kBlockJ, 0, st, in, j,
+                     uprev, hi, lo, z, red, ls);
     });
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_mx_lanczos_b(const Geometry &g, int j, const float2 *z, const float2 *u,
                                 const float2 *hi, const float2 *lo, float2 *unext,
                                 Reduction *red, LanczosScalars *ls, cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  if (u)
-    mx_lanczos_b_kernel<false><<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, hi, lo, unext, red, ls);
-  else
-    mx_lanczos_b_kernel<true><<<elem_blocks(g), kElemThreads, 0, st>>>(G, j, z, u, hi, lo, unext, red, ls);
-  return cudaGetLastError();
+  const cudaError_t e =
+      u ? launch_pdl(mx_lanczos_b_kernel<false>, elem_blocks(g), kElemThreads, 0, st, G, j, z, u, hi, lo, unext, red, ls)
+        : launch_pdl(mx_lanczos_b_kernel<true>, elem_blocks(g), kElemThreads, 0, st, G, j, z, u, hi, lo, unext, red, ls);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_mx_lanczos_combine(const Geometry &g, const OperatorView &op, double2 *psi,
@@ -466,9 +478,9 @@ cudaError_t launch_mx_lanczos_combine(const Geometry &g, const OperatorView &op,
                                       Reduction *red, LanczosScalars *ls, int *status,
                                       cudaStream_t st) {
   const size_t G = (size_t)g.N * (g.L + 1);
-  mx_lanczos_combine_kernel<<<elem_blocks(g), kElemThreads, 0, st>>>(
-      G, g.N, psi, hi, lo, u1, stride, op.mask, op.mask_start, red, ls, status);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(mx_lanczos_combine_kernel, elem_blocks(g), kElemThreads, 0, st, G, g.N, psi, hi, lo,
+                                   u1, stride, op.mask, op.mask_start, red, ls, status);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_mx_taylor_stage(const Geometry &g, const MixedView &mv, const OperatorView &op,
@@ -479,15 +491,18 @@ cudaError_t launch_mx_taylor_stage(const Geometry &g, const MixedView &mv, const
   const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, w_in, 1.f);
   const int mstart = final_stage ? op.mask_start : g.N;
   const int fs = final_stage ? 1 : 0;
+  cudaError_t e = cudaSuccess;
   dispatch(g, [&](auto stc, auto vg) {
     constexpr int ST = decltype(stc)::value;
     constexpr bool VG = decltype(vg)::value;
     if (w_in)
-      mx_taylor_stage_kernel<ST, true, VG><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
+      e = launch_pdl(mx_taylor_stage_kernel<ST, true, VG>, grid, kBlockJ, 0, st, in, (float)s, w_out, fs, psi, hi_out,
+                     lo_out, op.mask, mstart);
     else
-      mx_taylor_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, (float)s, w_out, fs, psi, hi_out, lo_out, op.mask, mstart);
+      e = launch_pdl(mx_taylor_stage_kernel<ST, false, VG>, grid, kBlockJ, 0, st, in, (float)s, w_out, fs, psi, hi_out,
+                     lo_out, op.mask, mstart);
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_mx_rk_stage(const Geometry &g, const MixedView &mv, const OperatorView &op,
@@ -500,15 +515,18 @@ cudaError_t launch_mx_rk_stage(const Geometry &g, const MixedView &mv, const Ope
   const unsigned grid = stencil_blocks(g);
   const MixedIn in = make_mixed(g, mv, (float)E, hi, lo, k_in, (float)(dt * a_in[stage - 1]));
   const int mstart = (stage == 4) ? op.mask_start : g.N;
+  cudaError_t e = cudaSuccess;
   dispatch(g, [&](auto stc, auto vg) {
     constexpr int ST = decltype(stc)::value;
     constexpr bool VG = decltype(vg)::value;
     if (k_in)
-      mx_rk_stage_kernel<ST, true, VG><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
+      e = launch_pdl(mx_rk_stage_kernel<ST, true, VG>, grid, kBlockJ, 0, st, in, stage, b[stage - 1], dt, k_out, acc_hi,
+                     acc_lo, psi, hi_out, lo_out, op.mask, mstart);
     else
-      mx_rk_stage_kernel<ST, false, VG><<<grid, kBlockJ, 0, st>>>(in, stage, b[stage - 1], dt, k_out, acc_hi, acc_lo, psi, hi_out, lo_out, op.mask, mstart);
+      e = launch_pdl(mx_rk_stage_kernel<ST, false, VG>, grid, kBlockJ, 0, st, in, stage, b[stage - 1], dt, k_out, acc_hi,
+                     acc_lo, psi, hi_out, lo_out, op.mask, mstart);
   });
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace tdse_dev
