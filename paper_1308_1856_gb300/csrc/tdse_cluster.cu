@@ -16,9 +16,10 @@
 //     (distributed shared memory); the l-neighbour rows are in the slice;
 //   - a cluster barrier separates the stages: each stage reads the halo of
 //     the vector the previous stage wrote;
-//   - a grid-wide sum (the Lanczos dot products and norms) is a fixed-order
-//     block sum per CTA, a barrier, and the C block sums added in rank order
-//     by every CTA, so that every CTA holds the same bits;
+//   - a grid-wide sum (the Lanczos dot products and norms) is every warp's
+//     shuffle-tree sum, a cluster barrier, and the C x 8 warp sums added in
+//     one fixed order by warp 0 of every CTA, so that every CTA holds the
+//     same bits (cluster_sum);
 //   - every CTA forms the small exponential of the Lanczos step itself from
 //     those identical scalars, so no broadcast is needed.
 // The per-point arithmetic of Taylor and RK4 is that of the multi-launch
