@@ -118,7 +118,16 @@ const char *tdse_last_error(const tdse_t *h);
  */
 int tdse_set_options(tdse_t *h, const tdse_opts *opts);
 
-/* Use the caller's CUDA stream (a cudaStream_t; NULL restores the handle's own). */
+/*
+ * Use the caller's CUDA stream (a cudaStream_t; NULL restores the handle's own).
+ * The kernels of a propagation step are launched on it with programmatic
+ * stream serialization, so each may start while the kernel before it on the
+ * stream finishes.  Each of them waits for that kernel to complete before it
+ * touches memory, so work the caller enqueued earlier on the stream is
+ * complete, as with ordinary launches.  A kernel the caller enqueues after a
+ * call starts after the library's last kernel of that call has completed,
+ * unless the caller gives it that attribute as well.
+ */
 int tdse_set_stream(tdse_t *h, void *cuda_stream);
 
 /*
