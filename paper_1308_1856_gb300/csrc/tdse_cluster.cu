@@ -24,11 +24,11 @@
 //     those identical scalars, so no broadcast is needed.
 // The per-point arithmetic of Taylor and RK4 is that of the multi-launch
 // kernels (tdse_kernels_fp64.cu), so either path gives bitwise the same state;
-// the field couplings kappa_l E r_j of a Taylor step are formed once per step
-// into a table, with the same roundings.  Lanczos applies the unscaled
-// operator and then sigma_j (the multi-launch kernels fold sigma_j into the
-// coefficients), and associates its grid sums differently: it agrees with
-// that path to rounding.
+// the field couplings kappa_l E r_j of a Taylor or Lanczos step are formed
+// once per step into a table, with the walker's roundings.  Lanczos applies
+// the unscaled operator and then sigma_j (the multi-launch kernels fold
+// sigma_j into the coefficients), and associates its grid sums differently:
+// it agrees with that path to rounding.
 // The only waits are cluster barriers (hardware), reached the same number of
 // times by every CTA: the control flow is uniform over the cluster.
 #include <cooperative_groups.h>
