@@ -49,9 +49,11 @@ def test_full_pulse_small_config(method, order, dt):
 
 def test_full_pulse_small_config_lanczos_vs_floor():
     """Lanczos-12 at the stated dt = 0.05 over the whole pulse (4410 steps):
-    rho(H) dt ~ 13.5 exceeds m = 12, and the FP64 oracle itself drifts ~2e-10
-    from its long-double build over the run, so the GPU run is held to 10x
-    that floor against the long-double oracle; observables within 1e-9."""
+    rho(H) dt ~ 13.5 exceeds m = 12, and the FP64 oracle itself drifts 1e-10
+    to 2e-10 from its long-double build over the run (the host's libm and long
+    double set where; ulp-level changes to the Lanczos normalisation move an
+    FP64 run anywhere from 0.3x to 2x that distance), so the GPU run is held
+    to 10x that floor against the long-double oracle; observables within 1e-9."""
     c = W.SMALL
     dt = 0.05
     pulse = oracle.Pulse(E0=c.E0, omega=c.omega, ncycles=c.ncycles)
